@@ -1,0 +1,176 @@
+/*
+ * nlfem — GB300 (sm_103a) assembly of 2D nonlocal finite element operators.
+ *
+ * C ABI of libnlfem.so. All pointers are plain host or device pointers; sizes are
+ * element counts. Every function returns an int status: 0 (NLFEM_OK) or a negative
+ * NLFEM_ERR_* code; nlfem_last_error() then holds a message for the calling thread.
+ * No function aborts, traps or exits the process.
+ *
+ * The operator (arXiv 2207.03921, Sec. 2): for a kernel Psi with horizon delta, the
+ * approximate bilinear form (eq. biFormApprox)
+ *     A_h^#(phi_j, phi_i) = sum_k sum_l int_{E_k} int_{E_l} 1_{B^#(x)}(y)
+ *                           (phi_i(x) - phi_i(y))^T Psi(x,y) (phi_j(x) - phi_j(y)) dy dx
+ * over all ordered element pairs of the base domain, with P1 continuous basis
+ * functions (Sec. 2.2), the ball approximations nocaps / approxcaps (Defs. 2.1, 2.2)
+ * and the quadrature of Alg. 1 and Tab. 1 (Sec. 2.3).
+ */
+#ifndef NLFEM_H
+#define NLFEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define NLFEM_OK 0
+#define NLFEM_ERR_INVALID_ARG (-1)  /* a NULL handle, negative size, unknown enum, delta <= 0 ... */
+#define NLFEM_ERR_BAD_MESH (-2)     /* degenerate triangle, vertex index out of range */
+#define NLFEM_ERR_OOM (-3)          /* a device allocation failed */
+#define NLFEM_ERR_BUDGET (-4)       /* the assembly would exceed params.mem_budget_bytes */
+#define NLFEM_ERR_CUDA (-5)         /* a CUDA runtime call failed */
+#define NLFEM_ERR_NOT_CONVERGED (-6)/* nlfem_solve reached max_iter */
+#define NLFEM_ERR_TIMEOUT (-7)      /* a bounded device wait ran out */
+#define NLFEM_ERR_UNSUPPORTED (-8)  /* a size limit of this implementation was exceeded */
+
+/* kernels of Sec. 3 */
+#define NLFEM_KERNEL_CONSTANT 0     /* gamma = c, c = 4 / (pi delta^4) by default */
+#define NLFEM_KERNEL_FRACTIONAL 1   /* gamma = c |x-y|^(-2-2s), c = (2-2s)/(pi delta^(2-2s)) (eq. fractional-scaling) */
+#define NLFEM_KERNEL_PERIDYNAMIC 2  /* Psi = c (x-y)(x-y)^T / |x-y|^3, c = 3 / delta^3 (eq. ker:peridynamics), 2 dofs per node */
+
+/* ball approximations of the Euclidean ball (Sec. 2.2) */
+#define NLFEM_BALL_NOCAPS 0         /* Def. 2.1 */
+#define NLFEM_BALL_APPROXCAPS 1     /* Def. 2.2 */
+
+/* rule on intersecting element pairs (Tab. 1) */
+#define NLFEM_CLOSE_AUTO 0          /* club for 0 < s < 1, diamond for -1 < s <= 0 and peridynamics, heart otherwise */
+#define NLFEM_CLOSE_DUFFY 1         /* regularising transforms to (0,1)^4 with a tensor Gauss rule */
+#define NLFEM_CLOSE_NOZERODIV 2     /* truncation rule, dropping point pairs with x_p = y_q */
+#define NLFEM_CLOSE_STANDARD 3      /* truncation rule as on disjoint pairs */
+
+/* arithmetic of the separated-pair quadrature */
+#define NLFEM_PREC_FP64 0           /* everything in FP64 */
+#define NLFEM_PREC_FP32_BULK 1      /* truncation quadrature in FP32 (FP64 geometry decisions and
+                                       singular pairs), FP64 result */
+
+typedef struct nlfem_mesh_s* nlfem_mesh_t;
+typedef struct nlfem_system_s* nlfem_system_t;
+
+typedef struct {
+    int kernel;              /* NLFEM_KERNEL_* */
+    double delta;            /* horizon, > 0 */
+    double s;                /* fractional order s in (0,1) for NLFEM_KERNEL_FRACTIONAL; ignored otherwise */
+    double kconst;           /* kernel constant; NaN selects the constant of Sec. 3 for the kernel */
+    int ball;                /* NLFEM_BALL_* */
+    int quad_outer;          /* 7 (Sec. 3.1 rule) or 16 (degree-7 conical product rule) */
+    int quad_inner;          /* 7 or 16 */
+    int duffy_gauss;         /* Gauss points per direction of the singular rule, 1..32 (5 in Sec. 3.1) */
+    int close_rule;          /* NLFEM_CLOSE_* */
+    int precision;           /* NLFEM_PREC_* */
+    int64_t mem_budget_bytes;/* 0 = unlimited; else the assembly fails with NLFEM_ERR_BUDGET beyond it */
+} nlfem_params;
+
+typedef struct {
+    int64_t npairs;          /* ordered interacting element pairs, (k,k) included */
+    int64_t pairs_identical, pairs_edge, pairs_vertex, pairs_separated;
+    int64_t nnz;             /* CSR nonzeros (dof level) */
+    int64_t device_bytes;    /* device memory held by the mesh handle and the system */
+    double ms_pairs;         /* pair search of the last cold assembly (0 when cached) */
+    double ms_pattern;       /* CSR pattern and reduction index (0 when cached) */
+    double ms_quadrature;    /* pair quadrature kernels */
+    double ms_reduce;        /* segmented reduction into CSR */
+    int cached;              /* 1 if the pair list / pattern of the mesh handle were reused */
+} nlfem_assembly_info;
+
+typedef struct {
+    int iterations;          /* inner CG iterations, summed over refinement steps */
+    int refinements;         /* FP64 residual refinement steps */
+    double rel_residual;     /* ||b - A_FF u_F|| / ||b|| in FP64 at exit */
+} nlfem_solve_info;
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* nlfem_last_error(void);
+
+/* Library version string. */
+const char* nlfem_version(void);
+
+/*
+ * Upload a triangle mesh of the base domain (Sec. 2.2): vertices verts [M x 2] (x, y
+ * interleaved, FP64) and triangles elems [K x 3] (vertex indices, any orientation; they
+ * are made counter-clockwise). elem_label [K]: 1 = element of Omega, 0 = of Omega_D; NULL
+ * labels every element Omega (pure Neumann-type base domain). A node is a Dirichlet node
+ * iff it is a vertex of an Omega_D element. ndof_per_node: 1 (scalar kernels) or 2
+ * (peridynamics). Pointers may be host or device memory; the data are copied, the caller
+ * keeps ownership. Work is ordered on stream (a cudaStream_t, NULL = legacy default).
+ * The handle is owned by the library until nlfem_mesh_destroy.
+ * Errors: INVALID_ARG (NULL pointer, M < 3, K < 1, ndof not 1 or 2), BAD_MESH (index out
+ * of range, zero-area triangle), OOM, CUDA.
+ */
+int nlfem_mesh_create(const double* verts, int64_t M, const int32_t* elems, int64_t K,
+                      const int8_t* elem_label, int ndof_per_node, void* stream,
+                      nlfem_mesh_t* out);
+
+void nlfem_mesh_destroy(nlfem_mesh_t mesh);
+
+/* Fill p with the defaults of Sec. 3.1 for the given kernel: delta = 0.1, nocaps,
+ * 7-point rules, 5 Gauss points, automatic close-pair rule, FP64. */
+void nlfem_params_default(nlfem_params* p, int kernel);
+
+/*
+ * Assemble the stiffness matrix A_h^# over all dofs of the base domain (full Neumann-type
+ * matrix, symmetric to the last bit) and the load vector F_i = int_Omega f phi_i computed
+ * with the outer rule from the P1 interpolant of f_nodal [M x ndof] (host or device, NULL
+ * means f = 0). The interaction graph, CSR pattern and reduction index are built on the
+ * first call and cached in the mesh handle for later calls with the same delta, ball,
+ * outer rule and close-pair class (see nlfem_assembly_info.cached).
+ * Work is ordered on stream; the call returns after the result is complete on the
+ * device. The system handle is owned by the library until nlfem_system_destroy.
+ * Errors: INVALID_ARG, UNSUPPORTED (more than 8192 partners per element, or a row
+ * referring to more than 2^32 / 84 pairs), BUDGET, OOM, CUDA.
+ */
+int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* f_nodal,
+                   void* stream, nlfem_system_t* out);
+
+/* Borrowed device pointers of the CSR matrix (valid until nlfem_system_destroy):
+ * row_ptr [nrows + 1] int64, col [nnz] int32 (sorted per row), val [nnz] FP64. Dof d of
+ * node m is row m * ndof + d. */
+int nlfem_system_csr(nlfem_system_t sys, const int64_t** row_ptr, const int32_t** col,
+                     const double** val, int64_t* nrows, int64_t* nnz);
+
+/* Borrowed device pointer to the load vector F [nrows]. */
+int nlfem_system_rhs(nlfem_system_t sys, const double** F);
+
+/* Borrowed device pointer to the Dirichlet node flags [M] (int8, 1 = Dirichlet). */
+int nlfem_system_dirichlet(nlfem_system_t sys, const int8_t** flags);
+
+int nlfem_system_info(nlfem_system_t sys, nlfem_assembly_info* info);
+
+/* Device pointers to the interaction graph of the cached pair list: k [npairs], l [npairs]
+ * (int32, sorted by (k, l)). Valid until the next nlfem_assemble with other parameters
+ * or nlfem_mesh_destroy. */
+int nlfem_mesh_pairs(nlfem_mesh_t mesh, const int32_t** k, const int32_t** l, int64_t* npairs);
+
+/*
+ * Solve the nonlocal Dirichlet problem A_FF u_F = F_F - A_FD g (eq.
+ * inhomogeneousDirichletData): F = free dofs, D = dofs of Dirichlet nodes. g_nodal
+ * [nrows] holds the Dirichlet data (values at free dofs are ignored; NULL = 0).
+ * Conjugate gradients on A_FF in FP32, wrapped in FP64 residual refinement until
+ * ||b - A_FF u_F|| <= tol_rel ||b|| (FP64). u_out [nrows], device, caller-owned: on
+ * return holds u_F at free dofs and g at Dirichlet dofs. g_nodal may be host or device.
+ * Errors: INVALID_ARG, NOT_CONVERGED (max_iter inner iterations reached; u_out holds the
+ * last iterate and info the residual), OOM, CUDA.
+ */
+int nlfem_solve(nlfem_system_t sys, const double* g_nodal, double tol_rel, int max_iter,
+                double* u_out, nlfem_solve_info* info, void* stream);
+
+void nlfem_system_destroy(nlfem_system_t sys);
+
+/* Device memory held by a mesh handle and its cached pair list / pattern, in bytes. */
+int64_t nlfem_mesh_device_bytes(nlfem_mesh_t mesh);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLFEM_H */

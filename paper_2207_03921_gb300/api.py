@@ -1,0 +1,133 @@
+"""Python front end: meshes, assembly and solve as torch tensors on the GPU.
+
+Thin wrappers over the C ABI in :mod:`binding`; torch provides device memory and
+streams. Matrices come back as CSR tensors (row_ptr int64, col int32, val float64)
+over all dofs of the base domain; :meth:`System.csr` copies them out of the library,
+:meth:`System.csr_views` returns zero-copy views valid while the System lives.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding as B
+
+
+class _DevView:
+    """__cuda_array_interface__ over a library-owned device buffer (keeps the owner alive)."""
+
+    def __init__(self, ptr, n, typestr, owner):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr or 0), False),
+                                         "version": 3, "strides": None}
+        self._owner = owner
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _as_dev(x, dtype):
+    """Host/device array -> contiguous torch CUDA tensor of dtype."""
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        return x.to(device="cuda", dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype).cuda()
+
+
+class Mesh:
+    """A triangle mesh of the base domain uploaded to the GPU (nlfem_mesh_create)."""
+
+    def __init__(self, verts, elems, elem_label=None, ndof_per_node=1, stream=None):
+        torch = _torch()
+        self.verts = _as_dev(verts, torch.float64)
+        self.elems = _as_dev(elems, torch.int32)
+        self.elem_label = None if elem_label is None else _as_dev(elem_label, torch.int8)
+        self.M = int(self.verts.shape[0])
+        self.K = int(self.elems.shape[0])
+        self.ndof = int(ndof_per_node)
+        self.handle = B.nlfem_mesh_create(self.verts, self.elems, self.elem_label, self.ndof, stream)
+
+    @classmethod
+    def from_synth(cls, m, ndof_per_node=1, stream=None):
+        return cls(m.verts, m.elems, m.elem_label, ndof_per_node, stream)
+
+    def pairs(self):
+        """(k, l) int32 tensors of the cached interaction graph (copies)."""
+        torch = _torch()
+        kp, lp, n = B.nlfem_mesh_pairs(self.handle)
+        k = torch.as_tensor(_DevView(kp, n, "<i4", self), device="cuda").clone()
+        l = torch.as_tensor(_DevView(lp, n, "<i4", self), device="cuda").clone()
+        return k, l
+
+    def device_bytes(self) -> int:
+        return B.nlfem_mesh_device_bytes(self.handle)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            B.nlfem_mesh_destroy(h)
+            self.handle = None
+
+
+class System:
+    """An assembled stiffness matrix and load vector (nlfem_assemble)."""
+
+    def __init__(self, mesh: Mesh, handle):
+        self.mesh = mesh
+        self.handle = handle
+        rp, col, val, n, nnz = B.nlfem_system_csr(handle)
+        self.N, self.nnz = n, nnz
+        self._ptrs = (rp, col, val)
+
+    def csr_views(self):
+        torch = _torch()
+        rp, col, val = self._ptrs
+        return (torch.as_tensor(_DevView(rp, self.N + 1, "<i8", self), device="cuda"),
+                torch.as_tensor(_DevView(col, self.nnz, "<i4", self), device="cuda"),
+                torch.as_tensor(_DevView(val, self.nnz, "<f8", self), device="cuda"))
+
+    def csr(self):
+        return tuple(t.clone() for t in self.csr_views())
+
+    def rhs(self):
+        torch = _torch()
+        return torch.as_tensor(_DevView(B.nlfem_system_rhs(self.handle), self.N, "<f8", self), device="cuda").clone()
+
+    def dirichlet(self):
+        torch = _torch()
+        return torch.as_tensor(_DevView(B.nlfem_system_dirichlet(self.handle), self.mesh.M, "|i1", self),
+                               device="cuda").clone().bool()
+
+    def info(self) -> dict:
+        return B.nlfem_system_info(self.handle)
+
+    def to_torch_sparse(self):
+        torch = _torch()
+        rp, col, val = self.csr()
+        return torch.sparse_csr_tensor(rp, col.long(), val, size=(self.N, self.N))
+
+    def solve(self, g_nodal=None, tol_rel=1e-10, max_iter=20000, stream=None):
+        """u with A_FF u_F = F_F - A_FD g and u = g at Dirichlet dofs (nlfem_solve)."""
+        torch = _torch()
+        u = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        g = None if g_nodal is None else _as_dev(g_nodal, torch.float64).reshape(-1)
+        info = B.nlfem_solve(self.handle, g, tol_rel, max_iter, u, stream)
+        return u, info
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            B.nlfem_system_destroy(h)
+            self.handle = None
+
+
+def assemble(mesh: Mesh, kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7,
+             quad_inner=7, duffy_gauss=5, close_rule="auto", precision="fp64", f_nodal=None,
+             mem_budget_bytes=0, stream=None) -> System:
+    """Assemble A_h^# and F on the GPU (nlfem_assemble)."""
+    torch = _torch()
+    p = B.make_params(kernel, delta, s, kconst, ball, quad_outer, quad_inner, duffy_gauss, close_rule,
+                      precision, mem_budget_bytes)
+    f = None if f_nodal is None else _as_dev(f_nodal, torch.float64).reshape(-1)
+    h = B.nlfem_assemble(mesh.handle, p, f, stream)
+    return System(mesh, h)

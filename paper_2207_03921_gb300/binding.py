@@ -1,0 +1,224 @@
+"""ctypes binding of libnlfem.so (include/nlfem.h).
+
+The functions below carry the C names and only marshal arguments: torch tensors or
+numpy arrays in, device pointers and CUDA stream handles out. Every computation runs
+in the CUDA library; if the shared library cannot be loaded, import fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import re
+import threading
+
+import importlib
+
+_build = importlib.import_module(__package__ + ".build")
+
+_lib = None
+_lock = threading.Lock()
+
+NLFEM_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "BAD_MESH", -3: "OOM", -4: "BUDGET", -5: "CUDA", -6: "NOT_CONVERGED",
+          -7: "TIMEOUT", -8: "UNSUPPORTED"}
+KERNELS = {"constant": 0, "fractional": 1, "peridynamic": 2}
+BALLS = {"nocaps": 0, "approxcaps": 1}
+CLOSE_RULES = {"auto": 0, "duffy": 1, "nozerodiv": 2, "standard": 3}
+PRECISIONS = {"fp64": 0, "fp32_bulk": 1}
+
+
+class NlfemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nlfem error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class nlfem_params(C.Structure):
+    _fields_ = [("kernel", C.c_int), ("delta", C.c_double), ("s", C.c_double), ("kconst", C.c_double),
+                ("ball", C.c_int), ("quad_outer", C.c_int), ("quad_inner", C.c_int), ("duffy_gauss", C.c_int),
+                ("close_rule", C.c_int), ("precision", C.c_int), ("mem_budget_bytes", C.c_int64)]
+
+
+class nlfem_assembly_info(C.Structure):
+    _fields_ = [("npairs", C.c_int64), ("pairs_identical", C.c_int64), ("pairs_edge", C.c_int64),
+                ("pairs_vertex", C.c_int64), ("pairs_separated", C.c_int64), ("nnz", C.c_int64),
+                ("device_bytes", C.c_int64), ("ms_pairs", C.c_double), ("ms_pattern", C.c_double),
+                ("ms_quadrature", C.c_double), ("ms_reduce", C.c_double), ("cached", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class nlfem_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libnlfem.so (building it first if it is missing and nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError(f"libnlfem.so not built at {_build.LIB}")
+            _build.build()
+        lib = C.CDLL(_build.LIB)
+        vp, i64, ip, dp = C.c_void_p, C.c_int64, C.c_int, C.c_double
+        lib.nlfem_last_error.restype = C.c_char_p
+        lib.nlfem_version.restype = C.c_char_p
+        lib.nlfem_mesh_create.argtypes = [vp, i64, vp, i64, vp, ip, vp, C.POINTER(vp)]
+        lib.nlfem_mesh_destroy.argtypes = [vp]
+        lib.nlfem_mesh_destroy.restype = None
+        lib.nlfem_params_default.argtypes = [C.POINTER(nlfem_params), ip]
+        lib.nlfem_params_default.restype = None
+        lib.nlfem_assemble.argtypes = [vp, C.POINTER(nlfem_params), vp, vp, C.POINTER(vp)]
+        lib.nlfem_system_csr.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i64),
+                                         C.POINTER(i64)]
+        lib.nlfem_system_rhs.argtypes = [vp, C.POINTER(vp)]
+        lib.nlfem_system_dirichlet.argtypes = [vp, C.POINTER(vp)]
+        lib.nlfem_system_info.argtypes = [vp, C.POINTER(nlfem_assembly_info)]
+        lib.nlfem_mesh_pairs.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
+        lib.nlfem_solve.argtypes = [vp, vp, dp, ip, vp, C.POINTER(nlfem_solve_info), vp]
+        lib.nlfem_system_destroy.argtypes = [vp]
+        lib.nlfem_system_destroy.restype = None
+        lib.nlfem_mesh_device_bytes.argtypes = [vp]
+        lib.nlfem_mesh_device_bytes.restype = i64
+        _lib = lib
+    return _lib
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions declared in include/nlfem.h."""
+    hdr = os.path.join(os.path.dirname(_build.HERE), "include", "nlfem.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"\b(nlfem_[a-z_]+)\s*\(", txt)))
+
+
+def _check(code):
+    if code != NLFEM_OK:
+        raise NlfemError(code, load().nlfem_last_error().decode())
+
+
+def _ptr(x):
+    """Device or host pointer of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ---- the C ABI, one Python function per C function ----------------------------------------
+
+def nlfem_mesh_create(verts, elems, elem_label=None, ndof_per_node=1, stream=None):
+    lib = load()
+    h = C.c_void_p()
+    M = int(verts.shape[0])
+    K = int(elems.shape[0])
+    _check(lib.nlfem_mesh_create(_ptr(verts), M, _ptr(elems), K, _ptr(elem_label), int(ndof_per_node),
+                                 _stream(stream), C.byref(h)))
+    return h
+
+
+def nlfem_mesh_destroy(mesh):
+    load().nlfem_mesh_destroy(mesh)
+
+
+def nlfem_params_default(kernel: int) -> nlfem_params:
+    p = nlfem_params()
+    load().nlfem_params_default(C.byref(p), int(kernel))
+    return p
+
+
+def nlfem_assemble(mesh, params: nlfem_params, f_nodal=None, stream=None):
+    h = C.c_void_p()
+    _check(load().nlfem_assemble(mesh, C.byref(params), _ptr(f_nodal), _stream(stream), C.byref(h)))
+    return h
+
+
+def nlfem_system_csr(sys):
+    rp, col, val = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    n, nnz = C.c_int64(), C.c_int64()
+    _check(load().nlfem_system_csr(sys, C.byref(rp), C.byref(col), C.byref(val), C.byref(n), C.byref(nnz)))
+    return rp.value, col.value, val.value, n.value, nnz.value
+
+
+def nlfem_system_rhs(sys):
+    F = C.c_void_p()
+    _check(load().nlfem_system_rhs(sys, C.byref(F)))
+    return F.value
+
+
+def nlfem_system_dirichlet(sys):
+    d = C.c_void_p()
+    _check(load().nlfem_system_dirichlet(sys, C.byref(d)))
+    return d.value
+
+
+def nlfem_system_info(sys) -> dict:
+    info = nlfem_assembly_info()
+    _check(load().nlfem_system_info(sys, C.byref(info)))
+    return info.as_dict()
+
+
+def nlfem_mesh_pairs(mesh):
+    k, l, n = C.c_void_p(), C.c_void_p(), C.c_int64()
+    _check(load().nlfem_mesh_pairs(mesh, C.byref(k), C.byref(l), C.byref(n)))
+    return k.value, l.value, n.value
+
+
+def nlfem_solve(sys, g_nodal, tol_rel, max_iter, u_out, stream=None) -> dict:
+    info = nlfem_solve_info()
+    code = load().nlfem_solve(sys, _ptr(g_nodal), float(tol_rel), int(max_iter), _ptr(u_out),
+                              C.byref(info), _stream(stream))
+    out = {"iterations": info.iterations, "refinements": info.refinements, "rel_residual": info.rel_residual,
+           "status": code}
+    if code not in (NLFEM_OK, -6):
+        _check(code)
+    return out
+
+
+def nlfem_system_destroy(sys):
+    load().nlfem_system_destroy(sys)
+
+
+def nlfem_mesh_device_bytes(mesh) -> int:
+    return int(load().nlfem_mesh_device_bytes(mesh))
+
+
+def nlfem_last_error() -> str:
+    return load().nlfem_last_error().decode()
+
+
+def nlfem_version() -> str:
+    return load().nlfem_version().decode()
+
+
+def make_params(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7, quad_inner=7,
+                duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0) -> nlfem_params:
+    p = nlfem_params()
+    p.kernel = KERNELS[kernel]
+    p.delta = float(delta)
+    p.s = float(s)
+    p.kconst = math.nan if kconst is None else float(kconst)
+    p.ball = BALLS[ball]
+    p.quad_outer = int(quad_outer)
+    p.quad_inner = int(quad_inner)
+    p.duffy_gauss = int(duffy_gauss)
+    p.close_rule = CLOSE_RULES[close_rule]
+    p.precision = PRECISIONS[precision]
+    p.mem_budget_bytes = int(mem_budget_bytes)
+    return p

@@ -1,0 +1,392 @@
+// C ABI of libnlfem.so (declared in include/nlfem.h): handles, argument checks, the
+// assembly driver with its per-mesh cache, and thread-local error messages.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "nlfem_internal.cuh"
+#include "rules_table.h"
+
+namespace nlfem {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static void upload(DBuf<T>& dst, const void* src, size_t count, cudaStream_t st) {
+    dst.alloc(count, st);
+    if (!count) return;
+    cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(dst.p, src, count * sizeof(T), kind, st));
+}
+
+static void fill_rule(Rule& r, int n) {
+    const double(*tab)[4] = n == 7 ? NLFEM_RULE7 : NLFEM_RULE16;
+    r.n = n;
+    for (int i = 0; i < n; ++i) {
+        r.l[i][0] = tab[i][0];
+        r.l[i][1] = tab[i][1];
+        r.l[i][2] = tab[i][2];
+        r.w[i] = tab[i][3];
+    }
+}
+
+static void fill_gauss(DuffyRule& d, int n) {
+    d.n = n;
+    if (n == 5) {
+        for (int i = 0; i < 5; ++i) {
+            d.x[i] = NLFEM_GAUSS5_X[i];
+            d.w[i] = NLFEM_GAUSS5_W[i];
+        }
+    } else {
+        // Gauss-Legendre on (0,1) by Newton iteration on P_n (any n up to 32)
+        for (int i = 0; i < n; ++i) {
+            double x = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+            double dp = 1.0;
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1.0, p1 = x;
+                for (int k = 2; k <= n; ++k) {
+                    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                dp = n * (x * p1 - p0) / (x * x - 1.0);
+                double dx = p1 / dp;
+                x -= dx;
+                if (std::fabs(dx) < 1e-17) break;
+            }
+            d.x[n - 1 - i] = 0.5 * (x + 1.0);
+            d.w[n - 1 - i] = 1.0 / ((1.0 - x * x) * dp * dp);
+        }
+    }
+    d.sum_w = 0.0;
+    d.sum_wx = 0.0;
+    for (int i = 0; i < n; ++i) {
+        d.sum_w += d.w[i];
+        d.sum_wx += d.w[i] * d.x[i];
+    }
+}
+
+static Params make_params(const nlfem_params& p, int ndof) {
+    NLFEM_CHECK(p.kernel >= 0 && p.kernel <= 2, NLFEM_ERR_INVALID_ARG, "unknown kernel");
+    NLFEM_CHECK(p.delta > 0 && std::isfinite(p.delta), NLFEM_ERR_INVALID_ARG, "delta must be > 0");
+    NLFEM_CHECK(p.ball == NLFEM_BALL_NOCAPS || p.ball == NLFEM_BALL_APPROXCAPS, NLFEM_ERR_INVALID_ARG,
+                "unknown ball approximation");
+    NLFEM_CHECK((p.quad_outer == 7 || p.quad_outer == 16) && (p.quad_inner == 7 || p.quad_inner == 16),
+                NLFEM_ERR_INVALID_ARG, "quadrature rules must have 7 or 16 points");
+    NLFEM_CHECK(p.close_rule >= 0 && p.close_rule <= 3, NLFEM_ERR_INVALID_ARG, "unknown close-pair rule");
+    NLFEM_CHECK(p.precision == NLFEM_PREC_FP64 || p.precision == NLFEM_PREC_FP32_BULK, NLFEM_ERR_INVALID_ARG,
+                "unknown precision");
+    NLFEM_CHECK(p.duffy_gauss >= 1 && p.duffy_gauss <= 32, NLFEM_ERR_INVALID_ARG,
+                "duffy_gauss must be in 1..32");
+    int need = p.kernel == NLFEM_KERNEL_PERIDYNAMIC ? 2 : 1;
+    NLFEM_CHECK(need == ndof, NLFEM_ERR_INVALID_ARG, "the mesh was created with the wrong dofs per node for this kernel");
+    if (p.kernel == NLFEM_KERNEL_FRACTIONAL)
+        NLFEM_CHECK(p.s > 0.0 && p.s < 1.0, NLFEM_ERR_INVALID_ARG, "fractional kernel needs 0 < s < 1");
+    Params P;
+    std::memset(&P, 0, sizeof P);
+    P.kernel = p.kernel;
+    P.ball = p.ball;
+    P.close_rule = p.close_rule;
+    P.precision = p.precision;
+    P.ndof = ndof;
+    P.delta = p.delta;
+    P.delta2 = p.delta * p.delta;
+    P.s = p.kernel == NLFEM_KERNEL_FRACTIONAL ? p.s : (p.kernel == NLFEM_KERNEL_PERIDYNAMIC ? -0.5 : -1.0);
+    if (!std::isnan(p.kconst)) P.c = p.kconst;
+    else if (p.kernel == NLFEM_KERNEL_CONSTANT) P.c = 4.0 / (M_PI * p.delta * p.delta * p.delta * p.delta);
+    else if (p.kernel == NLFEM_KERNEL_FRACTIONAL) P.c = (2.0 - 2.0 * p.s) / (M_PI * std::pow(p.delta, 2.0 - 2.0 * p.s));
+    else P.c = 3.0 / (p.delta * p.delta * p.delta);
+    fill_rule(P.ro, p.quad_outer);
+    fill_rule(P.ri, p.quad_inner);
+    fill_gauss(P.dr, p.duffy_gauss);
+    // Tab. 1: club for 0 < s < 1, diamond for -1 < s <= 0 (peridynamics: s = -1/2), heart for s <= -1
+    if (p.close_rule == NLFEM_CLOSE_AUTO) {
+        P.singular = p.kernel == NLFEM_KERNEL_FRACTIONAL;
+        P.nozerodiv = p.kernel == NLFEM_KERNEL_PERIDYNAMIC;
+    } else {
+        P.singular = p.close_rule == NLFEM_CLOSE_DUFFY;
+        P.nozerodiv = p.close_rule == NLFEM_CLOSE_NOZERODIV;
+    }
+    NLFEM_CHECK(!(P.singular && ndof == 2), NLFEM_ERR_UNSUPPORTED,
+                "the singular rule is implemented for scalar kernels only");
+    return P;
+}
+
+}  // namespace nlfem
+
+using namespace nlfem;
+
+struct nlfem_mesh_s {
+    Mesh m;
+};
+struct nlfem_system_s {
+    System s;
+};
+
+#define NLFEM_API_BEGIN try {
+#define NLFEM_API_END                                   \
+    }                                                   \
+    catch (const ::nlfem::Error& e) {                   \
+        set_error(e.msg);                               \
+        return e.code;                                  \
+    }                                                   \
+    catch (const std::bad_alloc&) {                     \
+        set_error("host allocation failed");            \
+        return NLFEM_ERR_OOM;                           \
+    }                                                   \
+    catch (...) {                                       \
+        set_error("unexpected exception");              \
+        return NLFEM_ERR_CUDA;                          \
+    }
+
+extern "C" {
+
+const char* nlfem_last_error(void) { return g_err.c_str(); }
+
+const char* nlfem_version(void) { return "nlfem-gb300 0.1 (sm_103a)"; }
+
+void nlfem_params_default(nlfem_params* p, int kernel) {
+    if (!p) return;
+    p->kernel = kernel;
+    p->delta = 0.1;
+    p->s = 0.5;
+    p->kconst = NAN;
+    p->ball = NLFEM_BALL_NOCAPS;
+    p->quad_outer = 7;
+    p->quad_inner = 7;
+    p->duffy_gauss = 5;
+    p->close_rule = NLFEM_CLOSE_AUTO;
+    p->precision = NLFEM_PREC_FP64;
+    p->mem_budget_bytes = 0;
+}
+
+int nlfem_mesh_create(const double* verts, int64_t M, const int32_t* elems, int64_t K,
+                      const int8_t* elem_label, int ndof_per_node, void* stream, nlfem_mesh_t* out) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(out != nullptr, NLFEM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    NLFEM_CHECK(verts && elems, NLFEM_ERR_INVALID_ARG, "verts and elems must not be NULL");
+    NLFEM_CHECK(M >= 3 && K >= 1, NLFEM_ERR_INVALID_ARG, "need M >= 3 vertices and K >= 1 triangles");
+    NLFEM_CHECK(M < (1ll << 31) && K < (1ll << 31) / 3, NLFEM_ERR_UNSUPPORTED, "mesh too large for 32-bit indices");
+    NLFEM_CHECK(ndof_per_node == 1 || ndof_per_node == 2, NLFEM_ERR_INVALID_ARG, "ndof_per_node must be 1 or 2");
+    cudaStream_t st = (cudaStream_t)stream;
+    nlfem_mesh_s* h = new nlfem_mesh_s();
+    try {
+        Mesh& m = h->m;
+        m.M = M;
+        m.K = K;
+        m.ndof = ndof_per_node;
+        upload(m.X, verts, (size_t)M, st);
+        DBuf<int> T3;
+        upload(T3, elems, (size_t)(3 * K), st);
+        DBuf<int8_t> lab;
+        if (elem_label) upload(lab, elem_label, (size_t)K, st);
+        mesh_prepare(m, T3.p, elem_label ? lab.p : nullptr, st);
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    *out = h;
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+void nlfem_mesh_destroy(nlfem_mesh_t mesh) {
+    if (!mesh) return;
+    mesh->m.cache.reset();
+    delete mesh;
+}
+
+int64_t nlfem_mesh_device_bytes(nlfem_mesh_t mesh) { return mesh ? mesh->m.device_bytes() : 0; }
+
+int nlfem_mesh_pairs(nlfem_mesh_t mesh, const int32_t** k, const int32_t** l, int64_t* npairs) {
+    NLFEM_API_BEGIN
+    NLFEM_CHECK(mesh && k && l && npairs, NLFEM_ERR_INVALID_ARG, "NULL argument");
+    NLFEM_CHECK(mesh->m.cache != nullptr, NLFEM_ERR_INVALID_ARG, "no pair list yet: call nlfem_assemble first");
+    *k = mesh->m.cache->pk.p;
+    *l = mesh->m.cache->pl.p;
+    *npairs = mesh->m.cache->npairs;
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* f_nodal, void* stream,
+                   nlfem_system_t* out) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(mesh && params && out, NLFEM_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    Mesh& m = mesh->m;
+    cudaStream_t st = (cudaStream_t)stream;
+    Params P = make_params(*params, m.ndof);
+    cudaEvent_t ev[6];
+    for (int i = 0; i < 6; ++i) NLFEM_CUDA_TRY(cudaEventCreate(&ev[i]));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 6; ++i) cudaEventDestroy(e[i]);
+        }
+    } guard{ev};
+    std::shared_ptr<PairCache> pc = m.cache;
+    bool cached = pc && pc->delta == P.delta && pc->ball == P.ball && pc->nqo == P.ro.n &&
+                  pc->ndof == P.ndof && pc->close_singular == (int)P.singular;
+    double t_pairs = 0, t_pattern = 0;
+    if (!cached) {
+        m.cache.reset();
+        pc = std::make_shared<PairCache>();
+        {
+            pc->delta = P.delta;
+            pc->ball = P.ball;
+            pc->nqo = P.ro.n;
+            pc->ndof = P.ndof;
+            pc->close_singular = (int)P.singular;
+            NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+            build_pairs(m, P, *pc, st);
+            NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+            build_pattern(m, *pc, st);
+            NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
+            NLFEM_CUDA_TRY(cudaEventSynchronize(ev[2]));
+            t_pairs = elapsed_ms(ev[0], ev[1]);
+            t_pattern = elapsed_ms(ev[1], ev[2]);
+            pc->t_pairs_ms = t_pairs;
+            pc->t_pattern_ms = t_pattern;
+        }
+        m.cache = pc;
+    }
+    const int64_t NE = contrib_entries(P.ndof);
+    const size_t esz = P.precision == NLFEM_PREC_FP32_BULK ? sizeof(float) : sizeof(double);
+    int64_t need = (int64_t)(pc->npairs * NE * esz) + pc->nnz * 8 + pc->N * 8 + m.device_bytes();
+    if (params->mem_budget_bytes > 0 && need > params->mem_budget_bytes)
+        throw Error{NLFEM_ERR_BUDGET, "assembly needs " + std::to_string(need) + " device bytes, budget is " +
+                                          std::to_string(params->mem_budget_bytes)};
+    nlfem_system_s* h = new nlfem_system_s();
+    try {
+        System& S = h->s;
+        S.mesh = &m;
+        S.pc = pc;
+        S.prm = P;
+        S.N = pc->N;
+        S.nnz = pc->nnz;
+        S.val.alloc(pc->nnz, st);
+        S.F.alloc(pc->N, st);
+        if (P.precision == NLFEM_PREC_FP32_BULK) S.contrib32.alloc(pc->npairs * NE, st);
+        else S.contrib64.alloc(pc->npairs * NE, st);
+        DBuf<double> fdev;
+        const double* fptr = nullptr;
+        if (f_nodal) {
+            if (is_device_ptr(f_nodal)) fptr = f_nodal;
+            else {
+                upload(fdev, f_nodal, (size_t)(m.M * P.ndof), st);
+                fptr = fdev.p;
+            }
+        }
+        NLFEM_CUDA_TRY(cudaEventRecord(ev[3], st));
+        run_quadrature(m, *pc, P, S, st);
+        NLFEM_CUDA_TRY(cudaEventRecord(ev[4], st));
+        run_reduction(m, *pc, P, S, st);
+        NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
+        run_load(m, P, fptr, S, st);
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        // contributions are no longer needed once reduced
+        S.contrib32.release();
+        S.contrib64.release();
+        nlfem_assembly_info& I = S.info;
+        std::memset(&I, 0, sizeof I);
+        I.npairs = pc->npairs;
+        I.pairs_separated = pc->counts[0];
+        I.pairs_vertex = pc->counts[1];
+        I.pairs_edge = pc->counts[2];
+        I.pairs_identical = pc->counts[3];
+        I.nnz = pc->nnz;
+        I.device_bytes = m.device_bytes() + (int64_t)(S.val.bytes() + S.F.bytes());
+        I.ms_pairs = t_pairs;
+        I.ms_pattern = t_pattern;
+        I.ms_quadrature = elapsed_ms(ev[3], ev[4]);
+        I.ms_reduce = elapsed_ms(ev[4], ev[5]);
+        I.cached = cached ? 1 : 0;
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    *out = h;
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+int nlfem_system_csr(nlfem_system_t sys, const int64_t** row_ptr, const int32_t** col, const double** val,
+                     int64_t* nrows, int64_t* nnz) {
+    NLFEM_API_BEGIN
+    NLFEM_CHECK(sys != nullptr, NLFEM_ERR_INVALID_ARG, "NULL system");
+    PairCache* pc = sys->s.pc.get();
+    if (row_ptr) *row_ptr = pc->row_ptr.p;
+    if (col) *col = pc->col.p;
+    if (val) *val = sys->s.val.p;
+    if (nrows) *nrows = sys->s.N;
+    if (nnz) *nnz = sys->s.nnz;
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+int nlfem_system_rhs(nlfem_system_t sys, const double** F) {
+    NLFEM_API_BEGIN
+    NLFEM_CHECK(sys && F, NLFEM_ERR_INVALID_ARG, "NULL argument");
+    *F = sys->s.F.p;
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+int nlfem_system_dirichlet(nlfem_system_t sys, const int8_t** flags) {
+    NLFEM_API_BEGIN
+    NLFEM_CHECK(sys && flags, NLFEM_ERR_INVALID_ARG, "NULL argument");
+    *flags = sys->s.mesh->dir.p;
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+int nlfem_system_info(nlfem_system_t sys, nlfem_assembly_info* info) {
+    NLFEM_API_BEGIN
+    NLFEM_CHECK(sys && info, NLFEM_ERR_INVALID_ARG, "NULL argument");
+    *info = sys->s.info;
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+int nlfem_solve(nlfem_system_t sys, const double* g_nodal, double tol_rel, int max_iter, double* u_out,
+                nlfem_solve_info* info, void* stream) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(sys && u_out, NLFEM_ERR_INVALID_ARG, "NULL argument");
+    NLFEM_CHECK(tol_rel > 0 && max_iter > 0, NLFEM_ERR_INVALID_ARG, "need tol_rel > 0 and max_iter > 0");
+    NLFEM_CHECK(is_device_ptr(u_out), NLFEM_ERR_INVALID_ARG, "u_out must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    DBuf<double> gdev;
+    const double* g = nullptr;
+    if (g_nodal) {
+        if (is_device_ptr(g_nodal)) g = g_nodal;
+        else {
+            upload(gdev, g_nodal, (size_t)sys->s.N, st);
+            g = gdev.p;
+        }
+    }
+    return solve_system(sys->s, g, tol_rel, max_iter, u_out, info, st);
+    NLFEM_API_END
+}
+
+void nlfem_system_destroy(nlfem_system_t sys) { delete sys; }
+
+}  // extern "C"

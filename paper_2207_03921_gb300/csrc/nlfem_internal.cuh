@@ -1,0 +1,322 @@
+// Internal declarations of the nlfem CUDA library (sm_103a).
+// The public C ABI is include/nlfem.h; everything here is private to the .so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/nlfem.h"
+
+// ------------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------------
+namespace nlfem {
+
+void set_error(const std::string& msg);
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define NLFEM_CUDA_TRY(expr)                                                                  \
+    do {                                                                                      \
+        cudaError_t e__ = (expr);                                                             \
+        if (e__ != cudaSuccess)                                                               \
+            throw ::nlfem::Error{NLFEM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e__)}; \
+    } while (0)
+
+#define NLFEM_CHECK(cond, code, msg)                                                           \
+    do {                                                                                      \
+        if (!(cond)) throw ::nlfem::Error{(code), (msg)};                                     \
+    } while (0)
+
+#define NLFEM_LAUNCH_CHECK() NLFEM_CUDA_TRY(cudaGetLastError())
+
+// stream-ordered device buffer
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count, cudaStream_t st) {
+        release();
+        s = st;
+        n = count;
+        if (count == 0) return;
+        cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), st);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            n = 0;
+            (void)cudaGetLastError();
+            throw Error{NLFEM_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+        }
+    }
+    void zero(cudaStream_t st) {
+        if (n) NLFEM_CUDA_TRY(cudaMemsetAsync(p, 0, n * sizeof(T), st));
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// ------------------------------------------------------------------------------------------
+// mesh and system handles
+// ------------------------------------------------------------------------------------------
+struct PairCache;
+
+struct Mesh {
+    int64_t M = 0, K = 0;
+    int ndof = 1;
+    DBuf<double2> X;      // vertices [M]
+    DBuf<int4> T;         // CCW triangles [K] (w unused)
+    DBuf<double> det;     // |det J_k| = 2 |E_k| [K]
+    DBuf<int8_t> lab;     // element label, 1 = Omega [K]
+    DBuf<int8_t> dir;     // node is Dirichlet [M]
+    DBuf<int> ne_ptr;     // node -> elements CSR [M + 1]
+    DBuf<int> ne_idx;     // [3K], sorted per node
+    double bbox[4] = {0, 0, 0, 0};  // xmin, ymin, xmax, ymax
+    double rmax = 0;      // max element radius (centroid to vertex)
+    DBuf<double2> cen;    // centroids [K]
+    DBuf<double> rad;     // radii [K]
+    std::shared_ptr<PairCache> cache;  // pair list, pattern and slot index of the last (delta, ball, rule)
+    int64_t device_bytes() const;
+};
+
+// rule table passed by value to the kernels
+struct Rule {
+    int n;
+    double l[16][3];
+    double w[16];
+};
+
+struct DuffyRule {
+    int n;
+    double x[32], w[32];
+    double sum_w, sum_wx;  // sums of the 1D rule (exact 1 and 1/2 up to rounding)
+};
+
+struct Params {
+    int kernel, ball, close_rule, precision, ndof;
+    double delta, delta2, s, c;
+    Rule ro, ri;
+    DuffyRule dr;
+    bool singular;    // Tab. 1 club rule on intersecting pairs
+    bool nozerodiv;   // Tab. 1 diamond rule on intersecting pairs
+};
+
+// Interaction graph, CSR pattern and reduction index of one (mesh, delta, ball, outer rule, ndof).
+struct PairCache {
+    double delta = -1;
+    int ball = -1, nqo = -1, ndof = -1, close_singular = -1;
+    int64_t npairs = 0;
+    DBuf<int64_t> pair_ptr;  // [K + 1]
+    DBuf<int> pk, pl;        // [P], sorted by (k, l)
+    DBuf<int8_t> pcls;       // shared vertex count [P]
+    DBuf<int64_t> pT_ptr;    // [K + 1] pairs grouped by l
+    DBuf<int> pT_id;         // [P] pair ids, sorted per l
+    DBuf<int> duffy_ids;     // pairs that take the singular rule
+    int64_t nduffy = 0;
+    int64_t counts[4] = {0, 0, 0, 0};  // separated, vertex, edge, identical
+    // node-level pattern
+    DBuf<int64_t> nrow_ptr;  // [M + 1]
+    DBuf<int> ncol;          // [nnz_node]
+    int64_t nnz_node = 0;
+    int max_row = 0;
+    // dof-level CSR
+    int64_t N = 0, nnz = 0;
+    DBuf<int64_t> row_ptr;   // [N + 1]
+    DBuf<int> col;           // [nnz]
+    DBuf<int64_t> tpos;      // [nnz] position of the transposed entry
+    DBuf<int64_t> seg_ptr;   // [nnz + 1] contribution segments per CSR slot (upper slots only)
+    DBuf<uint32_t> idx;      // [ncontrib] packed (pair - pbase[row]) * NE + entry
+    DBuf<int64_t> pbase;     // [M] first pair id a node row refers to
+    int64_t ncontrib = 0;
+    double t_pairs_ms = 0, t_pattern_ms = 0;
+};
+
+struct SolveState;
+
+struct System {
+    Mesh* mesh = nullptr;
+    std::shared_ptr<PairCache> pc;  // the pattern this system was assembled on
+    Params prm;
+    int64_t N = 0, nnz = 0;
+    DBuf<double> val;        // [nnz]
+    DBuf<double> F;          // [N]
+    DBuf<float> contrib32;   // [P * NE]
+    DBuf<double> contrib64;
+    nlfem_assembly_info info;
+    std::shared_ptr<SolveState> solver;
+};
+
+// ------------------------------------------------------------------------------------------
+// host-side entry points of the translation units
+// ------------------------------------------------------------------------------------------
+void mesh_prepare(Mesh& m, const int* T3_dev, const int8_t* lab_dev, cudaStream_t st);
+void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st);
+void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st);
+void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st);
+void run_reduction(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st);
+void run_load(Mesh& m, const Params& prm, const double* f_nodal, System& sys, cudaStream_t st);
+int64_t contrib_entries(int ndof);
+int solve_system(System& S, const double* g, double tol, int max_iter, double* u_out, nlfem_solve_info* info,
+                 cudaStream_t st);
+
+// exclusive scan of int64 counts in place (n values -> n + 1 offsets in out)
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+// segmented sort of int keys (with an optional int payload) within [ptr[s], ptr[s + 1])
+void segmented_sort_i32(int* keys, int* vals, const int64_t* ptr, int64_t nseg, int max_len,
+                        cudaStream_t st);
+
+double elapsed_ms(cudaEvent_t a, cudaEvent_t b);
+
+}  // namespace nlfem
+
+// ------------------------------------------------------------------------------------------
+// canonical FP64 geometry (shared by all kernels of this library)
+//
+// Every operation is an explicitly rounded IEEE operation (no FMA contraction), so
+// the interaction decisions are the ones of the written-out arithmetic:
+//   point on triangle:  x = (l0*v0 + l1*v1) + l2*v2
+//   vertex in ball:     dx = vx - cx, dy = vy - cy, (dx*dx + dy*dy) <= delta*delta
+//   edge crossings:     u = b - a, e = a - c, A = u.u, B = e.u, C = e.e - delta2,
+//                       disc = B*B - A*C > 0, t = (-B -+ sqrt(disc)) / A in (0, 1);
+//                       t < 1e-12 or t > 1 - 1e-12 means the circle passes through
+//                       the edge's end vertex, which is emitted instead
+//   cap centre:         q = Q - P, len = sqrt(q.q) > 1e-9 delta,
+//                       m = (cx + delta*(qy/len), cy + delta*(-qx/len))
+// (Sec. 2.2, Defs. 2.1 and 2.2, with the tie rules spelled out above).
+// ------------------------------------------------------------------------------------------
+#define NLFEM_TAU 1e-12
+#define NLFEM_CAP_MIN 1e-9
+#define NLFEM_MAXPOLY 16
+
+struct CPt {
+    double x, y;   // absolute coordinates
+    double b1, b2; // barycentric coordinates w.r.t. the inner element (b0 = 1 - b1 - b2)
+    int e;         // boundary edge index
+    double t;      // parameter on that edge (0 for vertices)
+    int vert;
+};
+
+__device__ __forceinline__ double2 nl_map(const double2 V[3], double l0, double l1, double l2) {
+    double x = __dadd_rn(__dadd_rn(__dmul_rn(l0, V[0].x), __dmul_rn(l1, V[1].x)), __dmul_rn(l2, V[2].x));
+    double y = __dadd_rn(__dadd_rn(__dmul_rn(l0, V[0].y), __dmul_rn(l1, V[1].y)), __dmul_rn(l2, V[2].y));
+    return make_double2(x, y);
+}
+
+__device__ __forceinline__ double nl_d2(double2 v, double2 c) {
+    double dx = __dsub_rn(v.x, c.x), dy = __dsub_rn(v.y, c.y);
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+__device__ __forceinline__ bool nl_joined(const CPt& P, const CPt& Q) {
+    if (Q.e == P.e && Q.t > P.t) return true;
+    if (Q.vert && Q.e == (P.e + 1) % 3) return true;
+    return false;
+}
+
+__device__ __forceinline__ void nl_push(CPt* raw, int& n, const CPt& c) {
+    if (n > 0 && raw[n - 1].x == c.x && raw[n - 1].y == c.y) {
+        if (raw[n - 1].vert && !c.vert) return;  // keep the vertex
+        raw[n - 1] = c;                          // keep the later one
+    } else if (n < NLFEM_MAXPOLY) {              // at most 6 points reach here (2 per edge)
+        raw[n++] = c;
+    }
+}
+
+// E_l = V cut by the ball approximation around c. Returns the number of polygon points
+// written to out (with barycentric coordinates); full = all three vertices inside.
+// With out == nullptr only the count is returned (interaction predicate).
+__device__ __forceinline__ int nl_clip(const double2 V[3], double2 c, double delta, double delta2,
+                                       bool caps, CPt* out, bool& full) {
+    bool ins[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ins[a] = nl_d2(V[a], c) <= delta2;
+    if (ins[0] && ins[1] && ins[2]) {
+        full = true;
+        return 3;
+    }
+    full = false;
+    CPt raw[NLFEM_MAXPOLY];
+    int n = 0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int eb = (e + 1) % 3;
+        const double2 A_ = V[e], B_ = V[eb];
+        const double bA1 = (e == 1) ? 1.0 : 0.0, bA2 = (e == 2) ? 1.0 : 0.0;
+        const double bB1 = (eb == 1) ? 1.0 : 0.0, bB2 = (eb == 2) ? 1.0 : 0.0;
+        if (ins[e]) nl_push(raw, n, CPt{A_.x, A_.y, bA1, bA2, e, 0.0, 1});
+        double ux = __dsub_rn(B_.x, A_.x), uy = __dsub_rn(B_.y, A_.y);
+        double ex = __dsub_rn(A_.x, c.x), ey = __dsub_rn(A_.y, c.y);
+        double A = __dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy));
+        double B = __dadd_rn(__dmul_rn(ex, ux), __dmul_rn(ey, uy));
+        double C = __dsub_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), delta2);
+        double disc = __dsub_rn(__dmul_rn(B, B), __dmul_rn(A, C));
+        if (disc > 0.0) {
+            double r = __dsqrt_rn(disc);
+            double ts[2] = {__ddiv_rn(__dsub_rn(-B, r), A), __ddiv_rn(__dadd_rn(-B, r), A)};
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                double t = ts[j];
+                if (!(t > 0.0 && t < 1.0)) continue;
+                if (t < NLFEM_TAU) {
+                    nl_push(raw, n, CPt{A_.x, A_.y, bA1, bA2, e, 0.0, 1});
+                } else if (t > 1.0 - NLFEM_TAU) {
+                    nl_push(raw, n, CPt{B_.x, B_.y, bB1, bB2, eb, 0.0, 1});
+                } else {
+                    double px = __dadd_rn(A_.x, __dmul_rn(t, ux));
+                    double py = __dadd_rn(A_.y, __dmul_rn(t, uy));
+                    // barycentric: (1 - t) at vertex e, t at vertex eb
+                    double b1 = (e == 1 ? 1.0 - t : 0.0) + (eb == 1 ? t : 0.0);
+                    double b2 = (e == 2 ? 1.0 - t : 0.0) + (eb == 2 ? t : 0.0);
+                    nl_push(raw, n, CPt{px, py, b1, b2, e, t, 0});
+                }
+            }
+        }
+    }
+    if (n >= 2 && raw[n - 1].x == raw[0].x && raw[n - 1].y == raw[0].y) {
+        if (raw[n - 1].vert && !raw[0].vert) raw[0] = raw[n - 1];
+        --n;
+    }
+    // inverse map of E_l for cap centres
+    double ex1 = V[1].x - V[0].x, ey1 = V[1].y - V[0].y, ex2 = V[2].x - V[0].x, ey2 = V[2].y - V[0].y;
+    double dj = ex1 * ey2 - ey1 * ex2;
+    int m = 0;
+    for (int i = 0; i < n && m < NLFEM_MAXPOLY; ++i) {
+        if (out) out[m] = raw[i];
+        ++m;
+        if (caps && n >= 2 && m < NLFEM_MAXPOLY) {
+            const CPt& P = raw[i];
+            const CPt& Q = raw[(i + 1) % n];
+            if (!nl_joined(P, Q)) {
+                double qx = __dsub_rn(Q.x, P.x), qy = __dsub_rn(Q.y, P.y);
+                double len = __dsqrt_rn(__dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)));
+                if (len > NLFEM_CAP_MIN * delta) {
+                    if (out) {
+                        double mx = __dadd_rn(c.x, __dmul_rn(delta, __ddiv_rn(qy, len)));
+                        double my = __dadd_rn(c.y, __dmul_rn(delta, __ddiv_rn(-qx, len)));
+                        double px = mx - V[0].x, py = my - V[0].y;
+                        double b1 = (px * ey2 - py * ex2) / dj;
+                        double b2 = (ex1 * py - ey1 * px) / dj;
+                        out[m] = CPt{mx, my, b1, b2, -1, 0.0, 0};
+                    }
+                    ++m;
+                }
+            }
+        }
+    }
+    return m;
+}

@@ -1,0 +1,282 @@
+// Element-pair search within the horizon (the interaction graph T_S of Sec. 2.4).
+//
+// The paper finds the partners of E_k by a breadth-first traversal of the adjacency
+// graph (Alg. 2). Here the same set is found data-parallel: elements are binned into a
+// uniform grid of cell size >= delta + 2 r_max, every candidate in the 3 x 3 cell block
+// is tested with the exact FP64 predicate, and the survivors are compacted with a
+// prefix sum. The predicate: E_l interacts with E_k iff they share a vertex (intersecting
+// pairs always interact; T_adj spans T_S) or some outer quadrature point x_p of E_k sees
+// a polygon of >= 3 points when E_l is cut by the ball approximation around x_p.
+#include <algorithm>
+
+#include "nlfem_internal.cuh"
+
+namespace nlfem {
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+struct Grid {
+    double x0, y0, cs;
+    int nx, ny;
+};
+
+__global__ void k_bin_count(const double2* cen, int64_t K, Grid g, int64_t* cnt, int* cell_of) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double2 c = cen[k];
+    int cx = min(g.nx - 1, max(0, (int)floor((c.x - g.x0) / g.cs)));
+    int cy = min(g.ny - 1, max(0, (int)floor((c.y - g.y0) / g.cs)));
+    int cell = cy * g.nx + cx;
+    cell_of[k] = cell;
+    atomicAdd((unsigned long long*)&cnt[cell], 1ull);
+}
+
+__global__ void k_bin_fill(const int* cell_of, int64_t K, const int64_t* start, int* cursor, int* list) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    int cell = cell_of[k];
+    int pos = atomicAdd(&cursor[cell], 1);
+    list[start[cell] + pos] = (int)k;
+}
+
+__device__ __forceinline__ int shared_count(int4 a, int4 b) {
+    int c = 0;
+    c += (a.x == b.x) + (a.x == b.y) + (a.x == b.z);
+    c += (a.y == b.x) + (a.y == b.y) + (a.y == b.z);
+    c += (a.z == b.x) + (a.z == b.y) + (a.z == b.z);
+    return c;
+}
+
+struct SearchArgs {
+    const double2* X;
+    const int4* T;
+    const double2* cen;
+    const double* rad;
+    const int* cell_of;
+    const int64_t* cell_start;
+    const int* cell_list;
+    Grid g;
+    int64_t K;
+    double delta, delta2;
+    int caps;
+    Rule ro;
+};
+
+__device__ bool interacts(const SearchArgs& a, int k, int l, int4 tk, const double2 Vk[3], double2 ck, double rk) {
+    int4 tl = a.T[l];
+    if (shared_count(tk, tl) > 0) return true;
+    double2 cl = a.cen[l];
+    double rl = a.rad[l];
+    double dx = cl.x - ck.x, dy = cl.y - ck.y;
+    double dist = sqrt(dx * dx + dy * dy);
+    if (dist - rk - rl > a.delta * (1.0 + 1e-9)) return false;
+    if (dist + rk + rl <= a.delta * (1.0 - 1e-9)) return true;  // E_l inside the ball of every x in E_k
+    double2 Vl[3] = {a.X[tl.x], a.X[tl.y], a.X[tl.z]};
+    for (int p = 0; p < a.ro.n; ++p) {
+        double2 xp = nl_map(Vk, a.ro.l[p][0], a.ro.l[p][1], a.ro.l[p][2]);
+        bool full;
+        if (nl_clip(Vl, xp, a.delta, a.delta2, a.caps != 0, nullptr, full) >= 3) return true;
+    }
+    return false;
+}
+
+// One warp per outer element k. FILL = false: count partners; true: write them.
+template <bool FILL>
+__global__ void k_search(SearchArgs a, int64_t* count, const int64_t* ptr, int* out_l) {
+    int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (k >= a.K) return;
+    int4 tk = a.T[k];
+    double2 Vk[3] = {a.X[tk.x], a.X[tk.y], a.X[tk.z]};
+    double2 ck = a.cen[k];
+    double rk = a.rad[k];
+    int cell = a.cell_of[k];
+    int cx = cell % a.g.nx, cy = cell / a.g.nx;
+    int64_t n = 0;
+    int64_t base = FILL ? ptr[k] : 0;
+    for (int dyc = -1; dyc <= 1; ++dyc) {
+        int yy = cy + dyc;
+        if (yy < 0 || yy >= a.g.ny) continue;
+        for (int dxc = -1; dxc <= 1; ++dxc) {
+            int xx = cx + dxc;
+            if (xx < 0 || xx >= a.g.nx) continue;
+            int c = yy * a.g.nx + xx;
+            int64_t s = a.cell_start[c], e = a.cell_start[c + 1];
+            for (int64_t j0 = s; j0 < e; j0 += 32) {
+                int64_t j = j0 + lane;
+                bool ok = false;
+                int l = -1;
+                if (j < e) {
+                    l = a.cell_list[j];
+                    ok = interacts(a, (int)k, l, tk, Vk, ck, rk);
+                }
+                unsigned m = __ballot_sync(0xffffffffu, ok);
+                if (FILL && ok) out_l[base + n + __popc(m & ((1u << lane) - 1u))] = l;
+                n += __popc(m);
+            }
+        }
+    }
+    if (!FILL && lane == 0) count[k] = n;
+}
+
+__global__ void k_fill_k(const int64_t* ptr, int64_t K, int* pk) {
+    int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (k >= K) return;
+    for (int64_t p = ptr[k] + lane; p < ptr[k + 1]; p += 32) pk[p] = (int)k;
+}
+
+__global__ void k_classify(const int* pk, const int* pl, int64_t P, const int4* T, int8_t* cls,
+                           unsigned long long* counts, int64_t* tcount) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    int l = pl[p];
+    int c = shared_count(T[pk[p]], T[l]);
+    cls[p] = (int8_t)c;
+    atomicAdd(&counts[c], 1ull);
+    atomicAdd((unsigned long long*)&tcount[l], 1ull);
+}
+
+__global__ void k_fill_T(const int* pl, int64_t P, const int64_t* tptr, int* cursor, int* tid) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    int l = pl[p];
+    int pos = atomicAdd(&cursor[l], 1);
+    tid[tptr[l] + pos] = (int)p;
+}
+
+__global__ void k_flag_duffy(const int8_t* cls, int64_t P, int64_t* flag) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) flag[p] = cls[p] > 0;
+}
+
+__global__ void k_compact_duffy(const int64_t* flag, const int64_t* pos, int64_t P, int* ids) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P && flag[p]) ids[pos[p]] = (int)p;
+}
+
+__global__ void k_max_seg64(const int64_t* ptr, int64_t n, unsigned long long* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, (unsigned long long)(ptr[i + 1] - ptr[i]));
+}
+
+static int64_t max_segment(const int64_t* ptr, int64_t n, cudaStream_t st) {
+    DBuf<unsigned long long> mx;
+    mx.alloc(1, st);
+    mx.zero(st);
+    if (n > 0) {
+        k_max_seg64<<<nblk(n, 256), 256, 0, st>>>(ptr, n, mx.p);
+        NLFEM_LAUNCH_CHECK();
+    }
+    unsigned long long h = 0;
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, mx.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    return (int64_t)h;
+}
+
+void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
+    const int64_t K = m.K;
+    Grid g;
+    g.cs = (prm.delta + 2.0 * m.rmax) * (1.0 + 1e-9) + 1e-300;
+    double W = m.bbox[2] - m.bbox[0], H = m.bbox[3] - m.bbox[1];
+    g.nx = std::max(1, (int)std::ceil(W / g.cs));
+    g.ny = std::max(1, (int)std::ceil(H / g.cs));
+    // cap the grid at 2^24 cells by enlarging the cells (coarser cells stay correct)
+    while ((int64_t)g.nx * g.ny > (1 << 24)) {
+        g.cs *= 2.0;
+        g.nx = std::max(1, (int)std::ceil(W / g.cs));
+        g.ny = std::max(1, (int)std::ceil(H / g.cs));
+    }
+    g.x0 = m.bbox[0];
+    g.y0 = m.bbox[1];
+    const int64_t ncell = (int64_t)g.nx * g.ny;
+    DBuf<int64_t> ccount, cstart;
+    DBuf<int> cell_of, cursor, clist;
+    ccount.alloc(ncell, st);
+    ccount.zero(st);
+    cstart.alloc(ncell + 1, st);
+    cell_of.alloc(K, st);
+    clist.alloc(K, st);
+    cursor.alloc(ncell, st);
+    cursor.zero(st);
+    k_bin_count<<<nblk(K, 256), 256, 0, st>>>(m.cen.p, K, g, ccount.p, cell_of.p);
+    NLFEM_LAUNCH_CHECK();
+    exclusive_scan_i64(ccount.p, cstart.p, ncell, st);
+    k_bin_fill<<<nblk(K, 256), 256, 0, st>>>(cell_of.p, K, cstart.p, cursor.p, clist.p);
+    NLFEM_LAUNCH_CHECK();
+
+    SearchArgs a;
+    a.X = m.X.p; a.T = m.T.p; a.cen = m.cen.p; a.rad = m.rad.p; a.cell_of = cell_of.p;
+    a.cell_start = cstart.p; a.cell_list = clist.p; a.g = g; a.K = K;
+    a.delta = prm.delta; a.delta2 = prm.delta2; a.caps = prm.ball == NLFEM_BALL_APPROXCAPS; a.ro = prm.ro;
+
+    DBuf<int64_t> cnt;
+    cnt.alloc(K, st);
+    pc.pair_ptr.alloc(K + 1, st);
+    k_search<false><<<nblk(K * 32, 128), 128, 0, st>>>(a, cnt.p, nullptr, nullptr);
+    NLFEM_LAUNCH_CHECK();
+    exclusive_scan_i64(cnt.p, pc.pair_ptr.p, K, st);
+    int64_t P = 0;
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&P, pc.pair_ptr.p + K, sizeof P, cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    NLFEM_CHECK(P < ((int64_t)1 << 31), NLFEM_ERR_UNSUPPORTED, "more than 2^31 element pairs");
+    pc.npairs = P;
+    pc.pl.alloc(P, st);
+    pc.pk.alloc(P, st);
+    k_search<true><<<nblk(K * 32, 128), 128, 0, st>>>(a, nullptr, pc.pair_ptr.p, pc.pl.p);
+    NLFEM_LAUNCH_CHECK();
+    int64_t mx = max_segment(pc.pair_ptr.p, K, st);
+    segmented_sort_i32(pc.pl.p, nullptr, pc.pair_ptr.p, K, (int)std::min<int64_t>(mx, 1 << 30), st);
+    k_fill_k<<<nblk(K * 32, 256), 256, 0, st>>>(pc.pair_ptr.p, K, pc.pk.p);
+    NLFEM_LAUNCH_CHECK();
+
+    // classification and the transposed index
+    pc.pcls.alloc(P, st);
+    DBuf<unsigned long long> counts;
+    counts.alloc(4, st);
+    counts.zero(st);
+    DBuf<int64_t> tcount;
+    tcount.alloc(K, st);
+    tcount.zero(st);
+    if (P) {
+        k_classify<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, P, m.T.p, pc.pcls.p, counts.p, tcount.p);
+        NLFEM_LAUNCH_CHECK();
+    }
+    pc.pT_ptr.alloc(K + 1, st);
+    exclusive_scan_i64(tcount.p, pc.pT_ptr.p, K, st);
+    pc.pT_id.alloc(P, st);
+    DBuf<int> tcur;
+    tcur.alloc(K, st);
+    tcur.zero(st);
+    if (P) {
+        k_fill_T<<<nblk(P, 256), 256, 0, st>>>(pc.pl.p, P, pc.pT_ptr.p, tcur.p, pc.pT_id.p);
+        NLFEM_LAUNCH_CHECK();
+    }
+    int64_t mxT = max_segment(pc.pT_ptr.p, K, st);
+    segmented_sort_i32(pc.pT_id.p, nullptr, pc.pT_ptr.p, K, (int)std::min<int64_t>(mxT, 1 << 30), st);
+    unsigned long long hc[4];
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(hc, counts.p, sizeof hc, cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < 4; ++i) pc.counts[i] = (int64_t)hc[i];
+
+    // pairs that take the singular rule: every intersecting pair
+    pc.nduffy = 0;
+    pc.duffy_ids.release();
+    if (prm.singular && P) {
+        DBuf<int64_t> flag, pos;
+        flag.alloc(P, st);
+        pos.alloc(P + 1, st);
+        k_flag_duffy<<<nblk(P, 256), 256, 0, st>>>(pc.pcls.p, P, flag.p);
+        NLFEM_LAUNCH_CHECK();
+        exclusive_scan_i64(flag.p, pos.p, P, st);
+        int64_t nd = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&nd, pos.p + P, sizeof nd, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        pc.nduffy = nd;
+        pc.duffy_ids.alloc(nd, st);
+        k_compact_duffy<<<nblk(P, 256), 256, 0, st>>>(flag.p, pos.p, P, pc.duffy_ids.p);
+        NLFEM_LAUNCH_CHECK();
+    }
+}
+
+}  // namespace nlfem

@@ -1,0 +1,502 @@
+// CSR pattern, slot index and deterministic segmented reduction.
+//
+// The paper avoids write conflicts on the CPU with one sub-matrix per thread that are
+// summed at the end (Sec. 3.4). Here every ordered pair writes its local block on its
+// union vertices (pair-major, upper triangle) and a slot index, built once per mesh,
+// lists for every upper CSR entry the contributions that belong to it in a fixed order.
+// The reduction sums each list in that order and writes the value to both (i,j) and
+// (j,i), so A is symmetric to the last bit and identical from run to run.
+//
+// Contributions of one pair: entry E(a,b), 0 <= a <= b < 6, of the union block
+// (union = vertices of E_k, then the vertices of E_l not in E_k). Scalar: 21 values per
+// pair; peridynamics: 4 components (c1, c2) per entry, 84 values per pair.
+#include <algorithm>
+
+#include "nlfem_internal.cuh"
+
+namespace nlfem {
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+__device__ __constant__ int c_E1[6][6] = {
+    {0, 1, 2, 3, 4, 5}, {1, 6, 7, 8, 9, 10}, {2, 7, 11, 12, 13, 14},
+    {3, 8, 12, 15, 16, 17}, {4, 9, 13, 16, 18, 19}, {5, 10, 14, 17, 19, 20}};
+
+int64_t contrib_entries(int ndof) { return ndof == 1 ? 21 : 84; }
+
+static constexpr int MAX_NE = 32;  // elements per node handled by the row enumeration
+
+struct RowEnum {
+    const int* ne_ptr;
+    const int* ne_idx;
+    const int64_t* pair_ptr;
+    const int64_t* pT_ptr;
+    const int* pT_id;
+    const int* pk;
+    const int* pl;
+    const int4* T;
+};
+
+// Per-warp description of node i's contributing pairs: for e in ne(i): the pairs
+// (e, *) (x side), then for e in ne(i): the pairs (*, e) whose outer element does not
+// contain i (y side). cum[s] = first flattened index of range s.
+struct RowRanges {
+    int nne;
+    int ne[MAX_NE];
+    int64_t cum[2 * MAX_NE + 1];
+};
+
+__device__ __forceinline__ void row_ranges(const RowEnum& R, int i, RowRanges& rr) {
+    int b = R.ne_ptr[i], e = R.ne_ptr[i + 1];
+    rr.nne = min(e - b, MAX_NE);
+    for (int t = 0; t < rr.nne; ++t) rr.ne[t] = R.ne_idx[b + t];
+    rr.cum[0] = 0;
+    for (int t = 0; t < rr.nne; ++t)
+        rr.cum[t + 1] = rr.cum[t] + (R.pair_ptr[rr.ne[t] + 1] - R.pair_ptr[rr.ne[t]]);
+    for (int t = 0; t < rr.nne; ++t)
+        rr.cum[rr.nne + t + 1] = rr.cum[rr.nne + t] + (R.pT_ptr[rr.ne[t] + 1] - R.pT_ptr[rr.ne[t]]);
+}
+
+// pair id of flattened index f, or -1 if the pair is a y-side duplicate
+__device__ __forceinline__ int row_pair(const RowEnum& R, const RowRanges& rr, int64_t f, int i) {
+    int s = 0;
+    while (rr.cum[s + 1] <= f) ++s;
+    int64_t off = f - rr.cum[s];
+    if (s < rr.nne) return (int)(R.pair_ptr[rr.ne[s]] + off);
+    int e = rr.ne[s - rr.nne];
+    int p = R.pT_id[R.pT_ptr[e] + off];
+    int4 tk = R.T[R.pk[p]];
+    if (tk.x == i || tk.y == i || tk.z == i) return -1;  // already on the x side
+    return p;
+}
+
+// union vertices of pair p and the position of node i in it
+__device__ __forceinline__ int pair_union(const RowEnum& R, int p, int i, int u[6], int& ai) {
+    int4 tk = R.T[R.pk[p]], tl = R.T[R.pl[p]];
+    u[0] = tk.x; u[1] = tk.y; u[2] = tk.z;
+    int U = 3;
+    int lv[3] = {tl.x, tl.y, tl.z};
+    for (int b = 0; b < 3; ++b) {
+        if (lv[b] != u[0] && lv[b] != u[1] && lv[b] != u[2]) u[U++] = lv[b];
+    }
+    ai = -1;
+    for (int a = 0; a < U; ++a)
+        if (u[a] == i) ai = a;
+    return U;
+}
+
+// ------------------------------------------------------------------------------------------
+// pattern: per node row, the union vertices of every pair containing the node
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool hash_insert(int* tab, int cap, int key, int* count) {
+    unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(cap - 1);
+    for (int probe = 0; probe < cap; ++probe) {
+        int old = atomicCAS(&tab[h], -1, key);
+        if (old == -1) {
+            atomicAdd(count, 1);
+            return true;
+        }
+        if (old == key) return true;
+        h = (h + 1) & (unsigned)(cap - 1);
+    }
+    return false;
+}
+
+template <bool FILL>
+__global__ void k_pattern(RowEnum R, int64_t M, int cap, int64_t* rowcnt, const int64_t* rowptr,
+                          int* cols, int* overflow) {
+    extern __shared__ int sm[];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    int* tab = sm + warp * (cap + 1);
+    int* count = tab + cap;
+    if (i >= M) return;
+    for (int t = lane; t < cap; t += 32) tab[t] = -1;
+    if (lane == 0) *count = 0;
+    __syncwarp();
+    RowRanges rr;
+    row_ranges(R, (int)i, rr);
+    int64_t total = rr.cum[2 * rr.nne];
+    bool ok = true;
+    for (int64_t f0 = 0; f0 < total; f0 += 32) {
+        int64_t f = f0 + lane;
+        if (f < total) {
+            int p = row_pair(R, rr, f, (int)i);
+            if (p >= 0) {
+                int u[6], ai;
+                int U = pair_union(R, p, (int)i, u, ai);
+                for (int b = 0; b < U; ++b) ok &= hash_insert(tab, cap, u[b], count);
+            }
+        }
+    }
+    __syncwarp();
+    bool good = __all_sync(0xffffffffu, ok) && *count <= cap / 2;
+    if (!good) {
+        if (lane == 0) atomicOr(overflow, 1);
+        return;
+    }
+    int n = *count;
+    if (!FILL) {
+        if (lane == 0) rowcnt[i] = n;
+        return;
+    }
+    // compact the keys to the front of the table, then bitonic sort them
+    __syncwarp();
+    int w = 0;
+    for (int t0 = 0; t0 < cap; t0 += 32) {
+        int key = tab[t0 + lane];
+        unsigned m = __ballot_sync(0xffffffffu, key != -1);
+        __syncwarp();
+        if (key != -1) tab[w + __popc(m & ((1u << lane) - 1u))] = key;
+        w += __popc(m);
+        __syncwarp();
+    }
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    for (int t = n + lane; t < n2; t += 32) tab[t] = 0x7fffffff;
+    __syncwarp();
+    for (int size = 2; size <= n2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < n2; t += 32) {
+                int j = t ^ stride;
+                if (j > t) {
+                    bool up = (t & size) == 0;
+                    int a = tab[t], b = tab[j];
+                    if ((a > b) == up) {
+                        tab[t] = b;
+                        tab[j] = a;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    int64_t base = rowptr[i];
+    for (int t = lane; t < n; t += 32) cols[base + t] = tab[t];
+}
+
+// dof-level CSR from the node-level pattern (dofs of a node are interleaved)
+__global__ void k_expand_rows(const int64_t* nptr, int64_t M, int ndof, int64_t* row_ptr) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > M) return;
+    if (i == M) {
+        row_ptr[M * ndof] = (int64_t)ndof * ndof * nptr[M];
+        return;
+    }
+    int64_t n = nptr[i + 1] - nptr[i];
+    for (int c = 0; c < ndof; ++c) row_ptr[i * ndof + c] = (int64_t)ndof * ndof * nptr[i] + c * ndof * n;
+}
+
+__device__ __forceinline__ int64_t find_col(const int* col, int64_t b, int64_t e, int key) {
+    while (b < e) {
+        int64_t mid = (b + e) >> 1;
+        if (col[mid] < key) b = mid + 1;
+        else e = mid;
+    }
+    return b;
+}
+
+// dof columns and the transpose map (thread per node-pattern entry)
+__global__ void k_expand_cols(const int64_t* nptr, const int* ncol, int64_t M, int ndof,
+                              const int64_t* row_ptr, int* col, int64_t* tpos, int* err) {
+    int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (i >= M) return;
+    int64_t b = nptr[i], e = nptr[i + 1];
+    for (int64_t t = b + lane; t < e; t += 32) {
+        int j = ncol[t];
+        int64_t r = t - b;
+        int64_t rt = find_col(ncol, nptr[j], nptr[j + 1], (int)i) - nptr[j];  // rank of i in row j
+        if (rt >= nptr[j + 1] - nptr[j] || ncol[nptr[j] + rt] != (int)i) {  // the pattern is symmetric
+            atomicOr(err, 1);
+            rt = 0;
+        }
+        for (int c1 = 0; c1 < ndof; ++c1)
+            for (int c2 = 0; c2 < ndof; ++c2) {
+                int64_t s = row_ptr[i * ndof + c1] + ndof * r + c2;
+                col[s] = j * ndof + c2;
+                tpos[s] = row_ptr[(int64_t)j * ndof + c2] + ndof * rt + c1;
+            }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// slot index: for every node-level upper entry (i, j >= i) the list of (pair, entry)
+// contributions, in the fixed order of the row enumeration
+// ------------------------------------------------------------------------------------------
+template <bool FILL>
+__global__ void k_slots(RowEnum R, int64_t M, const int64_t* nptr, const int* ncol, int maxrow,
+                        int64_t* seg_cnt, const int64_t* seg_ptr, uint32_t* idx, int64_t* pbase,
+                        int* overflow) {
+    extern __shared__ int sm[];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    int* rcols = sm + warp * 2 * maxrow;
+    int* cur = rcols + maxrow;
+    if (i >= M) return;
+    int64_t rb = nptr[i], re = nptr[i + 1];
+    int n = (int)(re - rb);
+    for (int t = lane; t < n; t += 32) {
+        rcols[t] = ncol[rb + t];
+        cur[t] = 0;
+    }
+    __syncwarp();
+    RowRanges rr;
+    row_ranges(R, (int)i, rr);
+    int64_t total = rr.cum[2 * rr.nne];
+    // first pair id the row refers to
+    long long pmin = 0x7fffffffffffffffll;
+    for (int64_t f0 = 0; f0 < total; f0 += 32) {
+        int64_t f = f0 + lane;
+        if (f < total) {
+            int p = row_pair(R, rr, f, (int)i);
+            if (p >= 0) pmin = min(pmin, (long long)p);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) pmin = min(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
+    if (!FILL && lane == 0) pbase[i] = pmin;
+    int64_t pb = FILL ? pbase[i] : pmin;
+    bool bad = false;
+    for (int64_t f0 = 0; f0 < total; f0 += 32) {
+        int64_t f = f0 + lane;
+        int p = -1;
+        if (f < total) p = row_pair(R, rr, f, (int)i);
+        int u[6] = {0, 0, 0, 0, 0, 0}, ai = 0, U = 0;
+        if (p >= 0) U = pair_union(R, p, (int)i, u, ai);
+        for (int b = 0; b < 6; ++b) {
+            int key = -1;
+            if (b < U && u[b] >= (int)i) {
+                key = (int)(find_col(rcols, 0, n, u[b]));
+                if (key >= n || rcols[key] != u[b]) {  // every union vertex is in the row
+                    bad = true;
+                    key = -1;
+                }
+            }
+            unsigned act = __ballot_sync(0xffffffffu, key >= 0);
+            if (!act) continue;
+            unsigned grp = __match_any_sync(0xffffffffu, key);
+            if (key >= 0) {
+                int leader = __ffs(grp) - 1;
+                int rank = __popc(grp & ((1u << lane) - 1u));
+                if (!FILL) {
+                    if (lane == leader) cur[key] += __popc(grp);
+                } else {
+                    int base = 0;
+                    if (lane == leader) {
+                        base = cur[key];
+                        cur[key] = base + __popc(grp);
+                    }
+                    base = __shfl_sync(grp, base, leader);
+                    int a = ai, bb = b;
+                    uint32_t tflag = 0;
+                    if (a > bb) {
+                        int tt = a; a = bb; bb = tt;
+                        tflag = 1;
+                    }
+                    int64_t rel = (int64_t)p - pb;
+                    if (rel < 0 || rel >= (1ll << 26)) bad = true;
+                    idx[seg_ptr[rb + key] + base + rank] =
+                        ((uint32_t)rel << 6) | (tflag << 5) | (uint32_t)c_E1[a][bb];
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (bad) atomicOr(overflow, 2);  // a pair too far from the row's first pair, or a missing column
+    __syncwarp();
+    if (!FILL)
+        for (int t = lane; t < n; t += 32) seg_cnt[rb + t] = cur[t];
+}
+
+// ------------------------------------------------------------------------------------------
+// segmented reduction (thread per node-level upper entry)
+// ------------------------------------------------------------------------------------------
+template <typename R, int NDOF>
+__global__ void k_reduce(int64_t M, const int64_t* nptr, const int* ncol, const int64_t* seg_ptr,
+                         const uint32_t* idx, const int64_t* pbase, const R* contrib,
+                         const int64_t* row_ptr, const int64_t* tpos, double* val) {
+    int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (i >= M) return;
+    const int NE = NDOF == 1 ? 21 : 84;
+    int64_t rb = nptr[i], re = nptr[i + 1];
+    int64_t pb = pbase[i];
+    for (int64_t t = rb + lane; t < re; t += 32) {
+        int j = ncol[t];
+        if (j < i) continue;
+        int64_t s0 = seg_ptr[t], s1 = seg_ptr[t + 1];
+        if (NDOF == 1) {
+            double v;
+            if (sizeof(R) == 4) {
+                // compensated FP32 summation (TwoSum), exact to about 2^-48 relative
+                float hi = 0.f, lo = 0.f;
+                for (int64_t q = s0; q < s1; ++q) {
+                    uint32_t e = idx[q];
+                    float x = (float)contrib[(pb + (e >> 6)) * NE + (e & 31)];
+                    float sum = hi + x;
+                    float bp = sum - hi;
+                    lo += (hi - (sum - bp)) + (x - bp);
+                    hi = sum;
+                }
+                v = (double)hi + (double)lo;
+            } else {
+                v = 0.0;
+                for (int64_t q = s0; q < s1; ++q) {
+                    uint32_t e = idx[q];
+                    v += (double)contrib[(pb + (e >> 6)) * NE + (e & 31)];
+                }
+            }
+            int64_t s = row_ptr[i] + (t - rb);
+            val[s] = v;
+            val[tpos[s]] = v;
+        } else {
+            double v[4] = {0, 0, 0, 0};
+            float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+            for (int64_t q = s0; q < s1; ++q) {
+                uint32_t e = idx[q];
+                const R* c = contrib + (pb + (e >> 6)) * NE + (e & 31) * 4;
+                bool tr = (e >> 5) & 1;
+                R x[4] = {c[0], tr ? c[2] : c[1], tr ? c[1] : c[2], c[3]};
+                for (int k = 0; k < 4; ++k) {
+                    if (sizeof(R) == 4) {
+                        float sum = hi[k] + (float)x[k];
+                        float bp = sum - hi[k];
+                        lo[k] += (hi[k] - (sum - bp)) + ((float)x[k] - bp);
+                        hi[k] = sum;
+                    } else {
+                        v[k] += (double)x[k];
+                    }
+                }
+            }
+            if (sizeof(R) == 4)
+                for (int k = 0; k < 4; ++k) v[k] = (double)hi[k] + (double)lo[k];
+            int64_t r = t - rb;
+            for (int c1 = 0; c1 < 2; ++c1)
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    if (j == i && c2 < c1) continue;  // the diagonal node block: upper dofs only
+                    int64_t s = row_ptr[i * 2 + c1] + 2 * r + c2;
+                    double x = v[c1 * 2 + c2];
+                    val[s] = x;
+                    val[tpos[s]] = x;
+                }
+        }
+    }
+}
+
+__global__ void k_row_max(const int64_t* ptr, int64_t n, int* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, (int)(ptr[i + 1] - ptr[i]));
+}
+
+void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
+    const int64_t M = m.M;
+    RowEnum R{m.ne_ptr.p, m.ne_idx.p, pc.pair_ptr.p, pc.pT_ptr.p, pc.pT_id.p, pc.pk.p, pc.pl.p, m.T.p};
+    DBuf<int> ovf;
+    ovf.alloc(1, st);
+    DBuf<int64_t> rowcnt;
+    rowcnt.alloc(M, st);
+    pc.nrow_ptr.alloc(M + 1, st);
+    int cap = 1024;
+    for (;;) {
+        ovf.zero(st);
+        int warps = std::max(1, std::min(8, (int)(160 * 1024 / ((cap + 1) * 4))));
+        size_t smem = (size_t)warps * (cap + 1) * sizeof(int);
+        NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_pattern<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_pattern<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        k_pattern<false><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, cap, rowcnt.p, nullptr, nullptr, ovf.p);
+        NLFEM_LAUNCH_CHECK();
+        int h = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, ovf.p, sizeof h, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!h) {
+            exclusive_scan_i64(rowcnt.p, pc.nrow_ptr.p, M, st);
+            NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.nnz_node, pc.nrow_ptr.p + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+            pc.ncol.alloc(pc.nnz_node, st);
+            k_pattern<true><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, cap, rowcnt.p, pc.nrow_ptr.p, pc.ncol.p, ovf.p);
+            NLFEM_LAUNCH_CHECK();
+            break;
+        }
+        cap *= 4;
+        NLFEM_CHECK(cap <= 32768, NLFEM_ERR_UNSUPPORTED, "a CSR row would exceed 16384 columns");
+    }
+    // row length statistics
+    {
+        DBuf<int> mx;
+        mx.alloc(1, st);
+        mx.zero(st);
+        k_row_max<<<nblk(M, 256), 256, 0, st>>>(pc.nrow_ptr.p, M, mx.p);
+        NLFEM_LAUNCH_CHECK();
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.max_row, mx.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    const int nd = pc.ndof;
+    pc.N = M * nd;
+    pc.nnz = pc.nnz_node * nd * nd;
+    pc.row_ptr.alloc(pc.N + 1, st);
+    k_expand_rows<<<nblk(M + 1, 256), 256, 0, st>>>(pc.nrow_ptr.p, M, nd, pc.row_ptr.p);
+    NLFEM_LAUNCH_CHECK();
+    pc.col.alloc(pc.nnz, st);
+    pc.tpos.alloc(pc.nnz, st);
+    ovf.zero(st);
+    k_expand_cols<<<nblk(M, 8), 256, 0, st>>>(pc.nrow_ptr.p, pc.ncol.p, M, nd, pc.row_ptr.p, pc.col.p, pc.tpos.p,
+                                              ovf.p);
+    NLFEM_LAUNCH_CHECK();
+    {
+        int h = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, ovf.p, sizeof h, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        NLFEM_CHECK(!h, NLFEM_ERR_CUDA, "internal error: the CSR pattern is not symmetric");
+    }
+    // slot index
+    DBuf<int64_t> segcnt;
+    segcnt.alloc(pc.nnz_node, st);
+    pc.seg_ptr.alloc(pc.nnz_node + 1, st);
+    pc.pbase.alloc(M, st);
+    int maxrow = std::max(pc.max_row, 1);
+    int warps = std::max(1, std::min(8, (int)(180 * 1024 / (2 * maxrow * 4))));
+    size_t smem = (size_t)warps * 2 * maxrow * sizeof(int);
+    NLFEM_CHECK(smem <= 200 * 1024, NLFEM_ERR_UNSUPPORTED, "CSR row too long for the slot index");
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_slots<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_slots<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    ovf.zero(st);
+    k_slots<false><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, pc.nrow_ptr.p, pc.ncol.p, maxrow, segcnt.p,
+                                                             nullptr, nullptr, pc.pbase.p, ovf.p);
+    NLFEM_LAUNCH_CHECK();
+    exclusive_scan_i64(segcnt.p, pc.seg_ptr.p, pc.nnz_node, st);
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.ncontrib, pc.seg_ptr.p + pc.nnz_node, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    pc.idx.alloc(pc.ncontrib, st);
+    k_slots<true><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, pc.nrow_ptr.p, pc.ncol.p, maxrow, nullptr,
+                                                            pc.seg_ptr.p, pc.idx.p, pc.pbase.p, ovf.p);
+    NLFEM_LAUNCH_CHECK();
+    int h = 0;
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, ovf.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    NLFEM_CHECK(!(h & 2), NLFEM_ERR_UNSUPPORTED,
+                "a CSR row refers to pairs more than 2^26 apart (or misses a column)");
+}
+
+void run_reduction(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st) {
+    const int64_t M = m.M;
+    NLFEM_CUDA_TRY(cudaMemsetAsync(sys.val.p, 0, sys.val.bytes(), st));
+    unsigned g = nblk(M, 8);
+    if (prm.precision == NLFEM_PREC_FP32_BULK) {
+        if (pc.ndof == 1)
+            k_reduce<float, 1><<<g, 256, 0, st>>>(M, pc.nrow_ptr.p, pc.ncol.p, pc.seg_ptr.p, pc.idx.p, pc.pbase.p,
+                                                 sys.contrib32.p, pc.row_ptr.p, pc.tpos.p, sys.val.p);
+        else
+            k_reduce<float, 2><<<g, 256, 0, st>>>(M, pc.nrow_ptr.p, pc.ncol.p, pc.seg_ptr.p, pc.idx.p, pc.pbase.p,
+                                                 sys.contrib32.p, pc.row_ptr.p, pc.tpos.p, sys.val.p);
+    } else {
+        if (pc.ndof == 1)
+            k_reduce<double, 1><<<g, 256, 0, st>>>(M, pc.nrow_ptr.p, pc.ncol.p, pc.seg_ptr.p, pc.idx.p, pc.pbase.p,
+                                                  sys.contrib64.p, pc.row_ptr.p, pc.tpos.p, sys.val.p);
+        else
+            k_reduce<double, 2><<<g, 256, 0, st>>>(M, pc.nrow_ptr.p, pc.ncol.p, pc.seg_ptr.p, pc.idx.p, pc.pbase.p,
+                                                  sys.contrib64.p, pc.row_ptr.p, pc.tpos.p, sys.val.p);
+    }
+    NLFEM_LAUNCH_CHECK();
+}
+
+}  // namespace nlfem

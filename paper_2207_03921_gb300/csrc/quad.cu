@@ -1,0 +1,508 @@
+// Pair quadrature (Sec. 2.3): Alg. 1 per ordered pair (E_k, E_l).
+//
+// k_trunc: the truncation quadrature (eq. discrete-inner) for every pair that does not
+//   take the singular rule. For each outer point x_p of E_k the inner element E_l is cut
+//   by the ball approximation around x_p (canonical FP64 geometry, see
+//   nlfem_internal.cuh), the cut polygon is fan-triangulated and the inner rule is put
+//   on every sub-triangle; basis values are interpolated from the sub-triangle vertices'
+//   barycentric coordinates. One thread per pair. The integrand is accumulated in R
+//   (FP32 in the bulk path, FP64 in the plain path) from vectors relative to x_p, so
+//   the FP32 path never subtracts absolute coordinates.
+// k_duffy: the singular rule (Tab. 1 "club") for intersecting pairs: regularising maps
+//   of S x S to (0,1)^4 and a tensor Gauss rule, in FP64. One warp per pair.
+//   Directions along which the integrand is constant are summed in closed form (the
+//   same tensor sum, reordered).
+// k_load: F_i = sum over Omega elements of sum_p a_p f(x_p) phi_i(x_p), thread per node.
+#include <algorithm>
+
+#include "nlfem_internal.cuh"
+
+namespace nlfem {
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+__device__ __constant__ int q_E1[6][6] = {
+    {0, 1, 2, 3, 4, 5}, {1, 6, 7, 8, 9, 10}, {2, 7, 11, 12, 13, 14},
+    {3, 8, 12, 15, 16, 17}, {4, 9, 13, 16, 18, 19}, {5, 10, 14, 17, 19, 20}};
+
+struct QuadArgs {
+    const int* pk;
+    const int* pl;
+    const int8_t* pcls;
+    int64_t npairs;
+    const double2* X;
+    const int4* T;
+    const double* det;
+    Params prm;
+};
+
+template <typename R>
+__device__ __forceinline__ R rsqrt_r(R x);
+template <>
+__device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
+
+// scalar kernel value (constant / fractional); d2 = |z|^2
+template <typename R, int KER>
+__device__ __forceinline__ R gamma_s(R d2, const Params& P) {
+    if (KER == NLFEM_KERNEL_CONSTANT) return (R)P.c;
+    if (P.s == 0.5) {
+        R r = rsqrt_r<R>(d2);
+        return (R)P.c * r * r * r;
+    }
+    if (sizeof(R) == 4) return (R)P.c * exp2f(log2f((float)d2) * (float)(-1.0 - P.s));
+    return (R)P.c * (R)pow((double)d2, -1.0 - P.s);
+}
+
+// union of the vertex lists: E_k's vertices, then E_l's vertices not in E_k
+__device__ __forceinline__ int union_pos(int4 tk, int4 tl, int posl[3], int u[6]) {
+    u[0] = tk.x; u[1] = tk.y; u[2] = tk.z;
+    int U = 3;
+    int lv[3] = {tl.x, tl.y, tl.z};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        int f = -1;
+        if (lv[b] == tk.x) f = 0;
+        if (lv[b] == tk.y) f = 1;
+        if (lv[b] == tk.z) f = 2;
+        if (f >= 0) posl[b] = f;
+        else { u[U] = lv[b]; posl[b] = U; ++U; }
+    }
+    return U;
+}
+
+// Accumulators of one pair: kk (sym 3x3, 6), kl (3x3, 9), ll (sym, 6); NC components
+// (1 scalar, 3 = xx, xy, yy for peridynamics).
+template <typename R, int NC>
+struct Acc {
+    R kk[6][NC], kl[9][NC], ll[6][NC];
+};
+
+__device__ __forceinline__ int sym3(int a, int b) {  // index of (a, b) in a packed symmetric 3x3
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+}
+
+template <typename R, int KER, int NQI>
+__global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contrib) {
+    constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
+    constexpr int NE = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 84 : 21;
+    const Params& P = A.prm;
+    const bool caps = P.ball == NLFEM_BALL_APPROXCAPS;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.npairs;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int cls = A.pcls[p];
+        if (cls > 0 && P.singular) continue;  // k_duffy writes this pair
+        const int k = A.pk[p], l = A.pl[p];
+        const int4 tk = A.T[k], tl = A.T[l];
+        const double2 Vk[3] = {A.X[tk.x], A.X[tk.y], A.X[tk.z]};
+        const double2 Vl[3] = {A.X[tl.x], A.X[tl.y], A.X[tl.z]};
+        const double dk = A.det[k], dl = A.det[l];
+        const bool nzd = cls > 0 && P.nozerodiv;
+        Acc<R, NC> acc;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc.kk[i][c] = acc.ll[i][c] = (R)0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc.kl[i][c] = (R)0;
+
+        for (int q0 = 0; q0 < P.ro.n; ++q0) {
+            const double2 xp = nl_map(Vk, P.ro.l[q0][0], P.ro.l[q0][1], P.ro.l[q0][2]);
+            CPt poly[NLFEM_MAXPOLY];
+            bool full;
+            const int np = nl_clip(Vl, xp, P.delta, P.delta2, caps, poly, full);
+            if (np < 3) continue;
+            // inner sums for this x_p: g = sum w, h_j = sum w Q_j, m_ij = sum w Q_i Q_j
+            R g[NC], h[3][NC], mm[6][NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                g[c] = (R)0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) h[j][c] = (R)0;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) mm[j][c] = (R)0;
+            }
+            const int ntri = full ? 1 : np - 2;
+            for (int t = 0; t < ntri; ++t) {
+                double2 tv[3];
+                R bq[3][3];  // barycentric coordinates (w.r.t. E_l) of the sub-triangle vertices
+                double dT;
+                if (full) {
+                    tv[0] = Vl[0]; tv[1] = Vl[1]; tv[2] = Vl[2];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) bq[a][b] = (R)(a == b ? 1.0 : 0.0);
+                    dT = dl;
+                } else {
+                    const CPt* c3[3] = {&poly[0], &poly[t + 1], &poly[t + 2]};
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        tv[a] = make_double2(c3[a]->x, c3[a]->y);
+                        bq[a][1] = (R)c3[a]->b1;
+                        bq[a][2] = (R)c3[a]->b2;
+                        bq[a][0] = (R)(1.0 - c3[a]->b1 - c3[a]->b2);
+                    }
+                    dT = fabs((tv[1].x - tv[0].x) * (tv[2].y - tv[0].y) -
+                              (tv[1].y - tv[0].y) * (tv[2].x - tv[0].x));
+                }
+                // sub-triangle vertices relative to x_p (FP64 difference, rounded once)
+                R rx[3], ry[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    rx[a] = (R)(tv[a].x - xp.x);
+                    ry[a] = (R)(tv[a].y - xp.y);
+                }
+#pragma unroll
+                for (int q = 0; q < NQI; ++q) {
+                    const R l0 = (R)P.ri.l[q][0], l1 = (R)P.ri.l[q][1], l2 = (R)P.ri.l[q][2];
+                    if (nzd) {
+                        // Tab. 1 diamond: drop x_p = y_q, decided on the canonical FP64 point
+                        double2 yq = nl_map(tv, P.ri.l[q][0], P.ri.l[q][1], P.ri.l[q][2]);
+                        if (yq.x == xp.x && yq.y == xp.y) continue;
+                    }
+                    const R zx = l0 * rx[0] + l1 * rx[1] + l2 * rx[2];
+                    const R zy = l0 * ry[0] + l1 * ry[1] + l2 * ry[2];
+                    const R d2 = zx * zx + zy * zy;
+                    const R wq = (R)(P.ri.w[q] * dT);
+                    R Q[3];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) Q[j] = l0 * bq[0][j] + l1 * bq[1][j] + l2 * bq[2][j];
+                    R wc[NC];
+                    if (KER == NLFEM_KERNEL_PERIDYNAMIC) {
+                        const R r = rsqrt_r<R>(d2);
+                        const R s = wq * (R)P.c * r * r * r;
+                        wc[0] = s * zx * zx;
+                        if (NC > 1) {
+                            wc[1 % NC] = s * zx * zy;
+                            wc[2 % NC] = s * zy * zy;
+                        }
+                    } else {
+                        wc[0] = wq * gamma_s<R, KER>(d2, P);
+                    }
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        g[c] += wc[c];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) h[j][c] += wc[c] * Q[j];
+                        mm[0][c] += wc[c] * Q[0] * Q[0];
+                        mm[1][c] += wc[c] * Q[0] * Q[1];
+                        mm[2][c] += wc[c] * Q[0] * Q[2];
+                        mm[3][c] += wc[c] * Q[1] * Q[1];
+                        mm[4][c] += wc[c] * Q[1] * Q[2];
+                        mm[5][c] += wc[c] * Q[2] * Q[2];
+                    }
+                }
+            }
+            const R ap = (R)(P.ro.w[q0] * dk);
+            const R Pa[3] = {(R)P.ro.l[q0][0], (R)P.ro.l[q0][1], (R)P.ro.l[q0][2]};
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const R ag = ap * g[c];
+                acc.kk[0][c] += ag * Pa[0] * Pa[0];
+                acc.kk[1][c] += ag * Pa[0] * Pa[1];
+                acc.kk[2][c] += ag * Pa[0] * Pa[2];
+                acc.kk[3][c] += ag * Pa[1] * Pa[1];
+                acc.kk[4][c] += ag * Pa[1] * Pa[2];
+                acc.kk[5][c] += ag * Pa[2] * Pa[2];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) acc.kl[a * 3 + b][c] -= ap * Pa[a] * h[b][c];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) acc.ll[j][c] += ap * mm[j][c];
+            }
+        }
+        // fold the four blocks into the union block and write its upper triangle
+        int posl[3], u[6];
+        union_pos(tk, tl, posl, u);
+        R* out = contrib + p * NE;
+        R blk[6][6][NC];
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int b = 0; b < 6; ++b)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) blk[a][b][c] = (R)0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    blk[a][b][c] += acc.kk[sym3(a, b)][c];
+                    blk[a][posl[b]][c] += acc.kl[a * 3 + b][c];
+                    blk[posl[b]][a][c] += acc.kl[a * 3 + b][c];
+                    blk[posl[a]][posl[b]][c] += acc.ll[sym3(a, b)][c];
+                }
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int b = a; b < 6; ++b) {
+                if (NC == 1) {
+                    out[q_E1[a][b]] = blk[a][b][0];
+                } else {
+                    // components (c1, c2) of Gamma: xx, xy, yx, yy
+                    R* o = out + q_E1[a][b] * 4;
+                    o[0] = blk[a][b][0];
+                    o[1] = blk[a][b][1 % NC];
+                    o[2] = blk[a][b][1 % NC];
+                    o[3] = blk[a][b][2 % NC];
+                }
+            }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// singular rule for intersecting pairs (FP64), warp per pair
+// ------------------------------------------------------------------------------------------
+struct DuffyArgs {
+    const int* ids;
+    int64_t n;
+    const int* pk;
+    const int* pl;
+    const double2* X;
+    const int4* T;
+    const double* det;
+    Params prm;
+};
+
+__device__ __forceinline__ double gamma_d(double d2, const Params& P) {
+    if (P.kernel == NLFEM_KERNEL_CONSTANT) return P.c;
+    if (P.s == 0.5) return P.c / (d2 * sqrt(d2));
+    return P.c * pow(d2, -1.0 - P.s);
+}
+
+// add w * D D^T (scalar) into the packed upper union block
+__device__ __forceinline__ void duffy_add(double* acc, const double* D, int U, double w) {
+    int e = 0;
+    for (int a = 0; a < 5; ++a)
+        for (int b = a; b < 5; ++b) {
+            if (a < U && b < U) acc[e] += w * D[a] * D[b];
+            ++e;
+        }
+}
+
+__global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__ contrib64,
+                                               float* __restrict__ contrib32) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wi >= A.n) return;
+    const Params& P = A.prm;
+    const int p = A.ids[wi];
+    const int k = A.pk[p], l = A.pl[p];
+    const int4 tk4 = A.T[k], tl4 = A.T[l];
+    const int tk[3] = {tk4.x, tk4.y, tk4.z}, tl[3] = {tl4.x, tl4.y, tl4.z};
+    int shared = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) shared += tk[a] == tl[b];
+    int ak[3], bl[3] = {0, 1, 2};
+    if (shared == 3) {
+        ak[0] = 0; ak[1] = 1; ak[2] = 2;
+    } else if (shared == 2) {
+        int s0 = -1, s1 = -1, sl0 = -1, sl1 = -1;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (tk[a] == tl[b]) {
+                    if (s0 < 0) { s0 = a; sl0 = b; } else { s1 = a; sl1 = b; }
+                }
+        ak[0] = s0; ak[1] = s1; ak[2] = 3 - s0 - s1;
+        bl[0] = sl0; bl[1] = sl1; bl[2] = 3 - sl0 - sl1;
+    } else {
+        int s0 = 0, sl0 = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (tk[a] == tl[b]) { s0 = a; sl0 = b; }
+        ak[0] = s0; ak[1] = (s0 + 1) % 3; ak[2] = (s0 + 2) % 3;
+        bl[0] = sl0; bl[1] = (sl0 + 1) % 3; bl[2] = (sl0 + 2) % 3;
+    }
+    double2 Av[3], Bv[3];
+    for (int a = 0; a < 3; ++a) {
+        Av[a] = A.X[tk[ak[a]]];
+        Bv[a] = A.X[tl[bl[a]]];
+    }
+    const int U = shared == 3 ? 3 : (shared == 2 ? 4 : 5);
+    int uorder[5];
+    for (int a = 0; a < 3; ++a) uorder[a] = tk[ak[a]];
+    if (shared == 2) uorder[3] = tl[bl[2]];
+    if (shared == 1) { uorder[3] = tl[bl[1]]; uorder[4] = tl[bl[2]]; }
+    int posl[3], u[6];
+    union_pos(tk4, tl4, posl, u);
+    int upos[5];
+    for (int a = 0; a < U; ++a) {
+        upos[a] = 0;
+        for (int v = 0; v < U; ++v)
+            if (u[v] == uorder[a]) upos[a] = v;
+    }
+    const double scale = A.det[k] * A.det[l];
+    const double e10x = Av[1].x - Av[0].x, e10y = Av[1].y - Av[0].y;
+    const double e21x = Av[2].x - Av[1].x, e21y = Av[2].y - Av[1].y;
+    const int n = P.dr.n;
+    double acc[15];
+    for (int e = 0; e < 15; ++e) acc[e] = 0.0;
+    double D[5];
+    if (shared == 3) {
+        // identical: the integrand depends on (xi, e1) only; e2, e3 sum to sum_wx * sum_w
+        const double fac = P.dr.sum_wx * P.dr.sum_w;
+        const int npts = 6 * n * n;
+        for (int t = lane; t < npts; t += 32) {
+            const int r = t / (n * n), i0 = (t / n) % n, i1 = t % n;
+            const double xi = P.dr.x[i0], e1 = P.dr.x[i1];
+            const double w = P.dr.w[i0] * P.dr.w[i1] * fac;
+            const double L = 1.0 - xi;
+            // (P_r, Q_r): the six triangles tiling the hexagon S - S
+            const double PQ[6][4] = {{0, 1, 1, 1}, {1, 0, 1, 1}, {1, 0, 0, -1},
+                                     {0, 1, -1, 0}, {-1, 0, -1, -1}, {0, -1, -1, -1}};
+            const double h1 = (1.0 - e1) * PQ[r][0] + e1 * PQ[r][2];
+            const double h2 = (1.0 - e1) * PQ[r][1] + e1 * PQ[r][3];
+            const double zx = xi * (h1 * e10x + h2 * e21x), zy = xi * (h1 * e10y + h2 * e21y);
+            D[0] = D[1] = D[2] = D[3] = D[4] = 0.0;
+            D[upos[0]] = xi * h1;
+            D[upos[1]] = xi * (h2 - h1);
+            D[upos[2]] = -xi * h2;
+            const double g = gamma_d(zx * zx + zy * zy, P);
+            duffy_add(acc, D, U, w * scale * xi * L * L * g);
+        }
+    } else if (shared == 2) {
+        // common edge: constant along e3
+        const double fx = Bv[2].x - Av[1].x, fy = Bv[2].y - Av[1].y;
+        const int npts = 4 * n * n * n;
+        for (int t = lane; t < npts; t += 32) {
+            const int r = t / (n * n * n), i0 = (t / (n * n)) % n, i1 = (t / n) % n, i2 = t % n;
+            const double xi = P.dr.x[i0], e1 = P.dr.x[i1], e2 = P.dr.x[i2];
+            const double w = P.dr.w[i0] * P.dr.w[i1] * P.dr.w[i2] * P.dr.sum_w;
+            const double L = 1.0 - xi;
+            double hu, hx2, hy2, wr;
+            if (r == 0) { hu = 1.0 - e1; hx2 = e1; hy2 = e2; wr = 1.0; }
+            else if (r == 1) { hu = e1 * (1.0 - e2); hx2 = e1 * e2; hy2 = 1.0; wr = e1; }
+            else if (r == 2) { hu = -e1 * (1.0 - e2); hx2 = 1.0; hy2 = e1 * e2; wr = e1; }
+            else { hu = e1 - 1.0; hx2 = e2; hy2 = e1; wr = 1.0; }
+            const double uu = xi * hu, x2 = xi * hx2, y2 = xi * hy2;
+            const double zx = xi * (hu * e10x + hy2 * fx - hx2 * e21x);
+            const double zy = xi * (hu * e10y + hy2 * fy - hx2 * e21y);
+            D[0] = D[1] = D[2] = D[3] = D[4] = 0.0;
+            D[upos[0]] = uu;
+            D[upos[1]] = -uu - x2 + y2;
+            D[upos[2]] = x2;
+            D[upos[3]] = -y2;
+            const double g = gamma_d(zx * zx + zy * zy, P);
+            duffy_add(acc, D, U, w * scale * xi * xi * L * wr * g);
+        }
+    } else {
+        // common vertex: all four directions matter
+        const double g10x = Bv[1].x - Av[0].x, g10y = Bv[1].y - Av[0].y;
+        const double g21x = Bv[2].x - Bv[1].x, g21y = Bv[2].y - Bv[1].y;
+        const int npts = 2 * n * n * n * n;
+        for (int t = lane; t < npts; t += 32) {
+            const int r = t / (n * n * n * n);
+            const int i0 = (t / (n * n * n)) % n, i1 = (t / (n * n)) % n, i2 = (t / n) % n, i3 = t % n;
+            const double xi = P.dr.x[i0], e1 = P.dr.x[i1], e2 = P.dr.x[i2], e3 = P.dr.x[i3];
+            const double w = P.dr.w[i0] * P.dr.w[i1] * P.dr.w[i2] * P.dr.w[i3];
+            const double hx1 = r == 0 ? 1.0 : e2, hy1 = r == 0 ? e2 : 1.0;
+            const double x1 = xi * hx1, y1 = xi * hy1;
+            const double zx = y1 * (g10x + e3 * g21x) - x1 * (e10x + e1 * e21x);
+            const double zy = y1 * (g10y + e3 * g21y) - x1 * (e10y + e1 * e21y);
+            D[upos[0]] = y1 - x1;
+            D[upos[1]] = x1 * (1.0 - e1);
+            D[upos[2]] = x1 * e1;
+            D[upos[3]] = -y1 * (1.0 - e3);
+            D[upos[4]] = -y1 * e3;
+            const double g = gamma_d(zx * zx + zy * zy, P);
+            duffy_add(acc, D, U, w * scale * xi * xi * xi * e2 * g);
+        }
+    }
+    // warp reduction in a fixed tree (deterministic)
+    for (int e = 0; e < 15; ++e)
+        for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+    if (lane == 0) {
+        int e;
+        // write all 21 entries of the union block (unused ones are zero)
+        double blk[6][6];
+        for (int a = 0; a < 6; ++a)
+            for (int b = 0; b < 6; ++b) blk[a][b] = 0.0;
+        e = 0;
+        for (int a = 0; a < 5; ++a)
+            for (int b = a; b < 5; ++b) {
+                if (a < U && b < U) {
+                    blk[a][b] = acc[e];
+                    blk[b][a] = acc[e];
+                }
+                ++e;
+            }
+        for (int a = 0; a < 6; ++a)
+            for (int b = a; b < 6; ++b) {
+                if (contrib64) contrib64[(int64_t)p * 21 + q_E1[a][b]] = blk[a][b];
+                else contrib32[(int64_t)p * 21 + q_E1[a][b]] = (float)blk[a][b];
+            }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// load vector: F_i = sum_{E_k in Omega, i in E_k} sum_p a_p f(x_p) phi_i(x_p), f in P1
+// ------------------------------------------------------------------------------------------
+__global__ void k_load(int64_t M, int ndof, const int* ne_ptr, const int* ne_idx, const int4* T,
+                       const int8_t* lab, const double* det, const double* f, Rule ro, double* F) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    for (int c = 0; c < ndof; ++c) {
+        double acc = 0.0;
+        for (int t = ne_ptr[i]; t < ne_ptr[i + 1]; ++t) {
+            int k = ne_idx[t];
+            if (!lab[k]) continue;
+            int4 tk = T[k];
+            int a = tk.x == i ? 0 : (tk.y == i ? 1 : 2);
+            double fv[3] = {f[(int64_t)tk.x * ndof + c], f[(int64_t)tk.y * ndof + c], f[(int64_t)tk.z * ndof + c]};
+            for (int p = 0; p < ro.n; ++p) {
+                double fx = ro.l[p][0] * fv[0] + ro.l[p][1] * fv[1] + ro.l[p][2] * fv[2];
+                acc += ro.w[p] * det[k] * fx * ro.l[p][a];
+            }
+        }
+        F[i * ndof + c] = acc;
+    }
+}
+
+template <typename R>
+static void launch_trunc(const QuadArgs& a, R* out, cudaStream_t st) {
+    const int NQI = a.prm.ri.n;
+    const int K = a.prm.kernel;
+    unsigned grid = (unsigned)std::min<int64_t>(nblk(a.npairs, 128), 152 * 64);
+    if (grid == 0) return;
+#define NLFEM_TR(KK, NQ) k_trunc<R, KK, NQ><<<grid, 128, 0, st>>>(a, out)
+    if (K == NLFEM_KERNEL_CONSTANT) {
+        if (NQI == 7) NLFEM_TR(NLFEM_KERNEL_CONSTANT, 7); else NLFEM_TR(NLFEM_KERNEL_CONSTANT, 16);
+    } else if (K == NLFEM_KERNEL_FRACTIONAL) {
+        if (NQI == 7) NLFEM_TR(NLFEM_KERNEL_FRACTIONAL, 7); else NLFEM_TR(NLFEM_KERNEL_FRACTIONAL, 16);
+    } else {
+        if (NQI == 7) NLFEM_TR(NLFEM_KERNEL_PERIDYNAMIC, 7); else NLFEM_TR(NLFEM_KERNEL_PERIDYNAMIC, 16);
+    }
+#undef NLFEM_TR
+    NLFEM_LAUNCH_CHECK();
+}
+
+void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st) {
+    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, pc.npairs, m.X.p, m.T.p, m.det.p, prm};
+    if (prm.precision == NLFEM_PREC_FP32_BULK) launch_trunc<float>(a, sys.contrib32.p, st);
+    else launch_trunc<double>(a, sys.contrib64.p, st);
+    if (prm.singular && pc.nduffy > 0) {
+        DuffyArgs d{pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
+        k_duffy<<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(
+            d, prm.precision == NLFEM_PREC_FP32_BULK ? nullptr : sys.contrib64.p, sys.contrib32.p);
+        NLFEM_LAUNCH_CHECK();
+    }
+}
+
+void run_load(Mesh& m, const Params& prm, const double* f_nodal, System& sys, cudaStream_t st) {
+    if (!f_nodal) {
+        NLFEM_CUDA_TRY(cudaMemsetAsync(sys.F.p, 0, sys.F.bytes(), st));
+        return;
+    }
+    k_load<<<nblk(m.M, 128), 128, 0, st>>>(m.M, prm.ndof, m.ne_ptr.p, m.ne_idx.p, m.T.p, m.lab.p, m.det.p,
+                                           f_nodal, prm.ro, sys.F.p);
+    NLFEM_LAUNCH_CHECK();
+}
+
+}  // namespace nlfem

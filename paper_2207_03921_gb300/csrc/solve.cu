@@ -1,0 +1,232 @@
+// Solve of the nonlocal Dirichlet problem (eq. inhomogeneousDirichletData):
+//   A_FF u_F = F_F - A_FD g,
+// with the columns of A split into free dofs and Dirichlet dofs. The paper returns the
+// CSR matrix and leaves the solve to the user; here conjugate gradients run in FP32
+// on A_FF inside an FP64 residual-refinement loop, which recovers FP64 accuracy of u_F.
+// All scalars (alpha, beta, residual norms) stay on the device; the host reads the
+// residual only every CHECK_EVERY iterations. Dot products are reduced in a fixed order.
+#include <cmath>
+
+#include "nlfem_internal.cuh"
+
+namespace nlfem {
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+struct SolveState {
+    int64_t N = 0;
+    DBuf<float> val32;    // FP32 copy of A
+    DBuf<int8_t> freem;   // dof is free
+    DBuf<double> b, x, r64, y64;
+    DBuf<float> r, p, q, d;
+    DBuf<double> part;    // partial sums of dot products
+    DBuf<double> sc;      // device scalars: [0] rho, [1] p.q, [2] rho_new, [3] |r64|^2, [4] |b|^2
+};
+
+static constexpr int DOT_BLOCKS = 1024;
+static constexpr int DOT_THREADS = 256;
+
+__global__ void k_to_f32(const double* a, float* b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_freemask(const int8_t* dir, int64_t N, int ndof, int8_t* freem) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) freem[i] = dir[i / ndof] ? 0 : 1;
+}
+
+// y = A x on free rows (x is zero at Dirichlet dofs); warp per row, fixed shuffle tree
+template <typename T, typename V>
+__global__ void k_spmv(const int64_t* rp, const int* col, const V* val, const T* x, T* y, const int8_t* freem,
+                       int64_t N) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    T s = 0;
+    if (freem[i])
+        for (int64_t t = rp[i] + lane; t < rp[i + 1]; t += 32) s += (T)val[t] * x[col[t]];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[i] = freem[i] ? s : (T)0;
+}
+
+// b = F - A x with x = g at Dirichlet dofs and 0 elsewhere; zero at Dirichlet rows
+__global__ void k_rhs(const int64_t* rp, const int* col, const double* val, const double* g, const double* F,
+                      const int8_t* freem, double* b, int64_t N) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    double s = 0;
+    if (freem[i] && g)
+        for (int64_t t = rp[i] + lane; t < rp[i + 1]; t += 32) {
+            int j = col[t];
+            if (!freem[j]) s += val[t] * g[j];
+        }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) b[i] = freem[i] ? F[i] - s : 0.0;
+}
+
+template <typename T1, typename T2>
+__global__ void k_dot_part(const T1* a, const T2* b, int64_t n, double* part) {
+    __shared__ double sh[DOT_THREADS];
+    double s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)a[i] * (double)b[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = DOT_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_dot_final(const double* part, double* out) {
+    __shared__ double sh[DOT_BLOCKS];
+    for (int i = threadIdx.x; i < DOT_BLOCKS; i += blockDim.x) sh[i] = part[i];
+    __syncthreads();
+    for (int o = DOT_BLOCKS / 2; o > 0; o >>= 1) {
+        for (int i = threadIdx.x; i < o; i += blockDim.x) sh[i] += sh[i + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+template <typename T1, typename T2>
+static void dot(const T1* a, const T2* b, int64_t n, double* part, double* out, cudaStream_t st) {
+    k_dot_part<T1, T2><<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(a, b, n, part);
+    k_dot_final<<<1, 1024, 0, st>>>(part, out);
+}
+
+// CG updates with device scalars: alpha = rho / pq
+__global__ void k_cg_update(float* d, float* r, const float* p, const float* q, const double* sc, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double pq = sc[1];
+    float alpha = pq != 0.0 ? (float)(sc[0] / pq) : 0.f;
+    d[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+}
+
+__global__ void k_cg_dir(float* p, const float* r, double* sc, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float beta = sc[0] != 0.0 ? (float)(sc[2] / sc[0]) : 0.f;
+    p[i] = r[i] + beta * p[i];
+}
+
+__global__ void k_roll(double* sc) { sc[0] = sc[2]; }
+
+__global__ void k_start(float* r, float* p, float* d, const double* r64, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v = (float)r64[i];
+    r[i] = v;
+    p[i] = v;
+    d[i] = 0.f;
+}
+
+__global__ void k_add_corr(double* x, const float* d, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += (double)d[i];
+}
+
+__global__ void k_sub(const double* b, const double* y, double* r, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = b[i] - y[i];
+}
+
+__global__ void k_final_u(const double* x, const double* g, const int8_t* freem, double* u, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) u[i] = freem[i] ? x[i] : (g ? g[i] : 0.0);
+}
+
+int solve_system(System& S, const double* g, double tol, int max_iter, double* u_out, nlfem_solve_info* info,
+                 cudaStream_t st) {
+    const int64_t N = S.N;
+    PairCache& pc = *S.pc;
+    if (!S.solver) {
+        auto ss = std::make_shared<SolveState>();
+        ss->N = N;
+        ss->val32.alloc(S.nnz, st);
+        k_to_f32<<<nblk(S.nnz, 256), 256, 0, st>>>(S.val.p, ss->val32.p, S.nnz);
+        NLFEM_LAUNCH_CHECK();
+        ss->freem.alloc(N, st);
+        k_freemask<<<nblk(N, 256), 256, 0, st>>>(S.mesh->dir.p, N, S.prm.ndof, ss->freem.p);
+        NLFEM_LAUNCH_CHECK();
+        ss->b.alloc(N, st); ss->x.alloc(N, st); ss->r64.alloc(N, st); ss->y64.alloc(N, st);
+        ss->r.alloc(N, st); ss->p.alloc(N, st); ss->q.alloc(N, st); ss->d.alloc(N, st);
+        ss->part.alloc(DOT_BLOCKS, st);
+        ss->sc.alloc(8, st);
+        S.solver = ss;
+    }
+    SolveState& W = *S.solver;
+    const unsigned gw = nblk(N * 32, 256), ge = nblk(N, 256);
+    k_rhs<<<gw, 256, 0, st>>>(pc.row_ptr.p, pc.col.p, S.val.p, g, S.F.p, W.freem.p, W.b.p, N);
+    NLFEM_LAUNCH_CHECK();
+    W.x.zero(st);
+    dot(W.b.p, W.b.p, N, W.part.p, W.sc.p + 4, st);
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(W.r64.p, W.b.p, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double bb = 0;
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&bb, W.sc.p + 4, sizeof bb, cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    const double bnorm = std::sqrt(bb);
+    int iters = 0, refs = 0;
+    double rel = bnorm > 0 ? 1.0 : 0.0;
+    const int CHECK_EVERY = 8;
+    while (rel > tol && iters < max_iter) {
+        // inner FP32 CG on A_FF d = r64, to a relative tolerance of 1e-4 of |r64|
+        k_start<<<ge, 256, 0, st>>>(W.r.p, W.p.p, W.d.p, W.r64.p, N);
+        NLFEM_LAUNCH_CHECK();
+        dot(W.r.p, W.r.p, N, W.part.p, W.sc.p + 0, st);
+        double rho0 = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&rho0, W.sc.p, sizeof rho0, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        const double inner_tol2 = rho0 * 1e-8;
+        int it = 0;
+        while (iters < max_iter) {
+            k_spmv<float, float><<<gw, 256, 0, st>>>(pc.row_ptr.p, pc.col.p, W.val32.p, W.p.p, W.q.p, W.freem.p, N);
+            dot(W.p.p, W.q.p, N, W.part.p, W.sc.p + 1, st);
+            k_cg_update<<<ge, 256, 0, st>>>(W.d.p, W.r.p, W.p.p, W.q.p, W.sc.p, N);
+            dot(W.r.p, W.r.p, N, W.part.p, W.sc.p + 2, st);
+            k_cg_dir<<<ge, 256, 0, st>>>(W.p.p, W.r.p, W.sc.p, N);
+            k_roll<<<1, 1, 0, st>>>(W.sc.p);
+            NLFEM_LAUNCH_CHECK();
+            ++it;
+            ++iters;
+            if (it % CHECK_EVERY == 0) {
+                double rho = 0;
+                NLFEM_CUDA_TRY(cudaMemcpyAsync(&rho, W.sc.p, sizeof rho, cudaMemcpyDeviceToHost, st));
+                NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+                if (!(rho > inner_tol2) || it >= 2000) break;
+            }
+        }
+        // x += d; r64 = b - A_FF x in FP64
+        k_add_corr<<<ge, 256, 0, st>>>(W.x.p, W.d.p, N);
+        k_spmv<double, double><<<gw, 256, 0, st>>>(pc.row_ptr.p, pc.col.p, S.val.p, W.x.p, W.y64.p, W.freem.p, N);
+        k_sub<<<ge, 256, 0, st>>>(W.b.p, W.y64.p, W.r64.p, N);
+        NLFEM_LAUNCH_CHECK();
+        dot(W.r64.p, W.r64.p, N, W.part.p, W.sc.p + 3, st);
+        double rr = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&rr, W.sc.p + 3, sizeof rr, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        rel = std::sqrt(rr) / bnorm;
+        ++refs;
+        if (refs > 50) break;
+    }
+    k_final_u<<<ge, 256, 0, st>>>(W.x.p, g, W.freem.p, u_out, N);
+    NLFEM_LAUNCH_CHECK();
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (info) {
+        info->iterations = iters;
+        info->refinements = refs;
+        info->rel_residual = rel;
+    }
+    if (rel > tol) {
+        set_error("CG did not reach the tolerance: relative residual " + std::to_string(rel));
+        return NLFEM_ERR_NOT_CONVERGED;
+    }
+    return NLFEM_OK;
+}
+
+}  // namespace nlfem
