@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark: element-pair assemblies per second of the nonlocal FEM assembly on GB300.
+
+Workload (default): the 720,000-triangle structured mesh of [-0.01, 1.01]^2 (600 x 600
+cells split by their "/" diagonal), constant kernel 4/(pi delta^4) with delta = 0.01,
+nocaps ball, 7-point outer and inner rules, FP32-bulk arithmetic. One step = one
+nlfem_assemble on the resident mesh with its cached pair list and pattern (values
+only: quadrature of every ordered pair, segmented reduction into CSR, load vector).
+The pair list, contributions and index (tens of GB) are far larger than L2, so every
+step streams from HBM. Also reported: the same step in plain FP64, the cold assembly
+(pair search + pattern + values), an end-to-end step through the C ABI with host
+buffers, the roofline of the quadrature kernel and the FP64 CPU oracle on a sample.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+Under torchrun (N > 1) every rank assembles its own replica of the workload (no
+collective on the data path); value = pairs of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "720k": dict(mesh="cfg720k", kernel="constant", delta=0.01, ball="nocaps", quad_outer=7, quad_inner=7,
+                 desc="structured 600x600 cells on [-0.01,1.01]^2 (720,000 triangles), constant kernel, "
+                      "delta=0.01, nocaps, 7-point outer/inner rules"),
+    "720k_small": dict(mesh="s200", kernel="constant", delta=0.03, ball="nocaps", quad_outer=7, quad_inner=7,
+                       desc="structured 200x200 cells on [-0.01,1.01]^2 (80,000 triangles), constant kernel, "
+                            "delta=0.03 (the delta/h of the 720k workload), nocaps, 7-point rules"),
+    "cfg5": dict(mesh="cfg5", kernel="constant", delta=0.01, ball="nocaps", quad_outer=7, quad_inner=7,
+                 desc="structured h=0.002 on [-0.01,1.01]^2 (520,200 triangles), constant kernel, delta=0.01, "
+                      "nocaps, 7-point rules"),
+    "cfg2": dict(mesh="cfg2", kernel="fractional", s=0.5, delta=0.1, ball="approxcaps", quad_outer=16,
+                 quad_inner=16,
+                 desc="jittered Delaunay h=0.01 on [-0.1,1.1]^2 (~29k triangles), fractional s=0.5, delta=0.1, "
+                      "approxcaps, 16-point rules, singular rule (5^4 Gauss) on touching pairs"),
+    "cfg3": dict(mesh="cfg3", kernel="peridynamic", delta=0.02, ball="nocaps", quad_outer=7, quad_inner=7,
+                 desc="structured h=0.005 on [-0.02,1.02]^2 (86,528 triangles), bond-based peridynamics, "
+                      "delta=0.02, 2 dofs per node, 7-point rules"),
+    "cfg1": dict(mesh="cfg1", kernel="constant", delta=0.1, ball="nocaps", quad_outer=7, quad_inner=7,
+                 desc="structured h=0.05 on [-0.1,1.1]^2 (1152 triangles), constant kernel, delta=0.1"),
+}
+
+# algorithmic FLOPs of the truncation quadrature (fixed model)
+FLOPS_PER_EVAL = {"constant": 57, "fractional": 60, "peridynamic": 3 * 55 + 9}
+FLOPS_PER_OUTER = 58
+FP64_FLOPS_PER_OUTER = 25       # x_p (10) and three vertex-in-ball tests (15)
+FP64_FLOPS_PER_CUT = 80         # edge quadratics, roots, crossing points, cap centres
+FP64_FLOPS_PER_DUFFY_POINT = 60
+
+
+def make_mesh(name):
+    from synth import meshes
+    if name == "s200":
+        return meshes.structured(-0.01, 1.01, 200, name="structured200")
+    return {"cfg720k": meshes.cfg720k_mesh, "cfg5": meshes.cfg5_mesh, "cfg2": meshes.cfg2_mesh,
+            "cfg3": meshes.cfg3_mesh, "cfg1": meshes.cfg1_mesh}[name]()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(ngpus):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(fn, steps, warmup, ws, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    outs = [fn() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return max_over_ranks(ms, ws), outs
+
+
+def oracle_sample(m, wl, seconds_target=15.0, threads=0):
+    """Time the FP64 oracle on a bounded sample of outer elements; returns (pairs/s, desc, cores)."""
+    import oracle
+    kw = {k: wl[k] for k in ("kernel", "delta", "ball", "quad_outer", "quad_inner") if k in wl}
+    if "s" in wl:
+        kw["s"] = wl["s"]
+    stride = max(1, m.K // 1500)
+    sub = np.arange(0, m.K, stride, dtype=np.int32)
+    t = time.perf_counter()
+    S = oracle.assemble(m, elem_subset=sub, threads=threads, **kw)
+    dt = time.perf_counter() - t
+    rate = S.counts["pairs"] / dt
+    if dt < seconds_target / 4 and stride > 1:   # grow the sample to ~seconds_target of CPU work
+        stride = max(1, int(stride * dt / seconds_target))
+        sub = np.arange(0, m.K, stride, dtype=np.int32)
+        t = time.perf_counter()
+        S = oracle.assemble(m, elem_subset=sub, threads=threads, **kw)
+        dt = time.perf_counter() - t
+        rate = S.counts["pairs"] / dt
+    cores = threads if threads > 0 else (os.cpu_count() or 1)
+    desc = (f"outer elements k = 0 mod {stride} ({len(sub)} of {m.K}), {S.counts['pairs']} ordered pairs, "
+            f"{dt:.1f} s")
+    return rate, desc, cores, dt
+
+
+def traffic_from_profiles(kernel_name, workload):
+    """dram bytes per launch recorded in profiles/ for this kernel and workload (None if absent)."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_name}_{workload}.json")
+    try:
+        d = json.load(open(p))
+        return d.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    """The oracle (the reference arm of this project): FP64 CPU assembly on a bounded sample."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    m = make_mesh(wl["mesh"])
+    vals = []
+    desc = cores = None
+    for _ in range(args.warmup):
+        oracle_sample(m, wl, seconds_target=3.0)
+    for _ in range(args.steps):
+        rate, desc, cores, dt = oracle_sample(m, wl, seconds_target=6.0)
+        vals.append(rate)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": "element-pair assemblies/s", "value": v, "unit": "pairs/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"]},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="720k", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile"],
+                    help="profile: one cold and one cached FP32-bulk assembly, nothing else (for ncu)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2207_03921_gb300 import Mesh, assemble, binding
+
+    ws, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    wl = WORKLOADS[args.workload]
+    m = make_mesh(wl["mesh"])
+    ndof = 2 if wl["kernel"] == "peridynamic" else 1
+    kw = {k: wl[k] for k in ("kernel", "delta", "ball", "quad_outer", "quad_inner") if k in wl}
+    if "s" in wl:
+        kw["s"] = wl["s"]
+    rng = np.random.default_rng(0)
+    f = torch.as_tensor(rng.standard_normal(m.M * ndof)).cuda()
+    mesh = Mesh.from_synth(m, ndof)
+
+    if args.mode == "profile":
+        for prec in ("fp32_bulk", "fp32_bulk"):
+            assemble(mesh, precision=prec, f_nodal=f, **kw)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "profile", "workload": args.workload}), flush=True)
+        return
+
+    # cold assembly: pair search + pattern + values
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = assemble(mesh, precision="fp32_bulk", f_nodal=f, **kw)
+    torch.cuda.synchronize()
+    cold_ms = (time.perf_counter() - t0) * 1e3
+    info0 = S.info()
+    census = S.census()
+    npairs = info0["npairs"]
+    del S
+
+    # steady FP32-bulk steps
+    infos = []
+
+    def step():
+        s = assemble(mesh, precision="fp32_bulk", f_nodal=f, **kw)
+        infos.append(s.info())
+        return None
+
+    with ClockSampler(local) as clk:
+        ms, _ = time_steps(step, args.steps, args.warmup, ws, stream)
+    timed = infos[args.warmup:]
+    ms_step = ms / args.steps
+    value = npairs * ws / (ms_step * 1e-3)
+    quad_ms = statistics.mean(i["ms_quadrature"] for i in timed)
+    red_ms = statistics.mean(i["ms_reduce"] for i in timed)
+
+    # plain FP64 on the same GPU
+    infos.clear()
+    ms64, _ = time_steps(lambda: infos.append(assemble(mesh, precision="fp64", f_nodal=f, **kw).info()),
+                         args.fp64_steps, 1, ws, stream)
+    ms64_step = ms64 / args.fp64_steps
+    quad64_ms = statistics.mean(i["ms_quadrature"] for i in infos[1:])
+
+    # end to end through the C ABI with host buffers: pinned verts/elems/labels/f -> mesh, assemble,
+    # CSR values + load vector back to pinned host memory
+    hv = torch.as_tensor(m.verts).pin_memory()
+    he = torch.as_tensor(m.elems).pin_memory()
+    hl = torch.as_tensor(m.elem_label).pin_memory()
+    hf = f.cpu().pin_memory()
+    p = binding.make_params(precision="fp32_bulk", **kw)
+    e2e_steps = max(1, min(3, args.steps))
+    out_val = out_F = None
+    h2d = hv.numel() * 8 + he.numel() * 4 + hl.numel() + hf.numel() * 8
+    d2h = 0
+
+    def e2e_step():
+        nonlocal out_val, out_F, d2h
+        mh = binding.nlfem_mesh_create(hv, he, hl, ndof, stream)
+        sh = binding.nlfem_assemble(mh, p, hf, stream)
+        rp, col, val, n, nnz = binding.nlfem_system_csr(sh)
+        if out_val is None:
+            out_val = torch.empty(nnz, dtype=torch.float64).pin_memory()
+            out_F = torch.empty(n, dtype=torch.float64).pin_memory()
+        # device -> pinned host copies of the result through torch views
+        from paper_2207_03921_gb300.api import _DevView
+        vv = torch.as_tensor(_DevView(val, nnz, "<f8", None), device="cuda")
+        fv = torch.as_tensor(_DevView(binding.nlfem_system_rhs(sh), n, "<f8", None), device="cuda")
+        out_val.copy_(vv, non_blocking=True)
+        out_F.copy_(fv, non_blocking=True)
+        torch.cuda.synchronize()
+        d2h = nnz * 8 + n * 8
+        binding.nlfem_system_destroy(sh)
+        binding.nlfem_mesh_destroy(mh)
+        return None
+
+    e2e_ms, _ = time_steps(e2e_step, e2e_steps, 1, ws, stream)
+    e2e_value = npairs * ws / (e2e_ms / e2e_steps * 1e-3)
+
+    # roofline of the dominant kernel (the truncation quadrature, k_trunc)
+    pk = peaks()
+    clk_sum = clk.summary()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s from unit counts and the max clock
+    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
+    evals, outer = census["evals"], census["full_points"] + census["cut_points"]
+    fp32_flops = evals * FLOPS_PER_EVAL[wl["kernel"]] + outer * FLOPS_PER_OUTER
+    fp64_flops = census["outer_points"] * FP64_FLOPS_PER_OUTER + census["cut_points"] * FP64_FLOPS_PER_CUT
+    a32 = fp32_flops / (quad_ms * 1e-3) / 1e12
+    a64 = fp64_flops / (quad_ms * 1e-3) / 1e12
+    if a64 / fp64_peak >= a32 / fp32_peak:
+        roof = {"bound": "alu", "pipe": "fp64", "achieved": a64, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": a64 / fp64_peak}
+    else:
+        roof = {"bound": "alu", "pipe": "fp32", "achieved": a32, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": a32 / fp32_peak}
+    roof["kernel"] = "k_trunc"
+    roof["peak_source"] = "derived: 152 SMs x (128 FP32 | 2 FP64) FMA lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)"
+    roof["other_pipe"] = {"fp32_tflops": a32, "fp32_frac": a32 / fp32_peak, "fp64_tflops": a64,
+                          "fp64_frac": a64 / fp64_peak}
+    roof["traffic"] = traffic_from_profiles("k_trunc", args.workload)
+    roof["ms_per_launch"] = quad_ms
+
+    line = {
+        "metric": "element-pair assemblies/s", "value": value, "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (quadrature) + f64 (geometry, singular pairs, CSR)",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "precision": "fp32_bulk",
+                   "step": "nlfem_assemble with cached pair list and pattern",
+                   "l2": "working set larger than L2 (pair list, per-pair contributions and slot index stream from HBM)",
+                   "pairs": npairs, "nnz": info0["nnz"], "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": roof,
+        "fp64_plain": {"value": npairs * ws / (ms64_step * 1e-3), "ms_per_step": ms64_step,
+                       "quadrature_ms": quad64_ms, "speedup_fp32_bulk_over_fp64": ms64_step / ms_step},
+        "breakdown_ms": {"quadrature": quad_ms, "reduce": red_ms, "cold_total": cold_ms,
+                         "pairs_search": info0["ms_pairs"], "pattern_and_index": info0["ms_pattern"]},
+        "cold": {"value": npairs / (cold_ms * 1e-3), "ms": cold_ms},
+        "census": census,
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "pinned host mesh -> nlfem_mesh_create -> nlfem_assemble (cold) -> CSR values and F to host"},
+        "gpu_launches": args.steps * (2 + (1 if census["singular_pairs"] else 0) + 1),
+        "clocks": clk_sum,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, desc, cores, dt = oracle_sample(m, wl)
+        line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

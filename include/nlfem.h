@@ -164,6 +164,18 @@ int nlfem_mesh_pairs(nlfem_mesh_t mesh, const int32_t** k, const int32_t** l, in
 int nlfem_solve(nlfem_system_t sys, const double* g_nodal, double tol_rel, int max_iter,
                 double* u_out, nlfem_solve_info* info, void* stream);
 
+/*
+ * Work of the assembly that produced sys, counted on the device with the same geometry
+ * (for FLOP accounting; it does not change sys). counts[9] receives: [0] kernel
+ * evaluations of the truncation quadrature, [1] outer points whose inner element lies
+ * fully in the ball, [2] outer points whose inner element was cut and retriangulated,
+ * [3] sub-triangles of the cut polygons, [4] points evaluated by the singular rule,
+ * [5] pairs on the truncation path, [6] pairs on the singular path, [7] outer points
+ * with an empty intersection, [8] outer points visited. The mesh's cached pair list must
+ * still be the one sys was assembled on. Errors: INVALID_ARG, CUDA.
+ */
+int nlfem_system_census(nlfem_system_t sys, int64_t counts[9], void* stream);
+
 void nlfem_system_destroy(nlfem_system_t sys);
 
 /* Device memory held by a mesh handle and its cached pair list / pattern, in bytes. */

@@ -101,6 +101,9 @@ class System:
     def info(self) -> dict:
         return B.nlfem_system_info(self.handle)
 
+    def census(self) -> dict:
+        return B.nlfem_system_census(self.handle)
+
     def to_torch_sparse(self):
         torch = _torch()
         rp, col, val = self.csr()

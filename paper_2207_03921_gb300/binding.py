@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
         lib.nlfem_system_info.argtypes = [vp, C.POINTER(nlfem_assembly_info)]
         lib.nlfem_mesh_pairs.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
         lib.nlfem_solve.argtypes = [vp, vp, dp, ip, vp, C.POINTER(nlfem_solve_info), vp]
+        lib.nlfem_system_census.argtypes = [vp, C.POINTER(C.c_int64), vp]
         lib.nlfem_system_destroy.argtypes = [vp]
         lib.nlfem_system_destroy.restype = None
         lib.nlfem_mesh_device_bytes.argtypes = [vp]
@@ -189,6 +190,16 @@ def nlfem_solve(sys, g_nodal, tol_rel, max_iter, u_out, stream=None) -> dict:
     if code not in (NLFEM_OK, -6):
         _check(code)
     return out
+
+
+CENSUS = ["evals", "full_points", "cut_points", "subtris", "duffy_points", "trunc_pairs", "singular_pairs",
+          "empty_points", "outer_points"]
+
+
+def nlfem_system_census(sys, stream=None) -> dict:
+    c = (C.c_int64 * 9)()
+    _check(load().nlfem_system_census(sys, c, _stream(stream)))
+    return dict(zip(CENSUS, (int(v) for v in c)))
 
 
 def nlfem_system_destroy(sys):

@@ -387,6 +387,14 @@ int nlfem_solve(nlfem_system_t sys, const double* g_nodal, double tol_rel, int m
     NLFEM_API_END
 }
 
+int nlfem_system_census(nlfem_system_t sys, int64_t counts[9], void* stream) {
+    NLFEM_API_BEGIN
+    NLFEM_CHECK(sys && counts, NLFEM_ERR_INVALID_ARG, "NULL argument");
+    run_census(*sys->s.mesh, *sys->s.pc, sys->s.prm, counts, (cudaStream_t)stream);
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
 void nlfem_system_destroy(nlfem_system_t sys) { delete sys; }
 
 }  // extern "C"

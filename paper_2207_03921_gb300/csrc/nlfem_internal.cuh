@@ -171,6 +171,7 @@ void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cuda
 void run_reduction(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st);
 void run_load(Mesh& m, const Params& prm, const double* f_nodal, System& sys, cudaStream_t st);
 int64_t contrib_entries(int ndof);
+void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStream_t st);
 int solve_system(System& S, const double* g, double tol, int max_iter, double* u_out, nlfem_solve_info* info,
                  cudaStream_t st);
 

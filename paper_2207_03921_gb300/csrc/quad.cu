@@ -506,3 +506,76 @@ void run_load(Mesh& m, const Params& prm, const double* f_nodal, System& sys, cu
 }
 
 }  // namespace nlfem
+
+// ------------------------------------------------------------------------------------------
+// census: the work of the last assembly, counted on the device with the same geometry
+// ------------------------------------------------------------------------------------------
+namespace nlfem {
+
+__device__ __forceinline__ void warp_add(unsigned long long* c, unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(c, v);
+}
+
+__global__ void k_census(QuadArgs A, unsigned long long* cnt) {
+    const Params& P = A.prm;
+    const bool caps = P.ball == NLFEM_BALL_APPROXCAPS;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_iter = (A.npairs + stride - 1) / stride;
+    for (int64_t it = 0; it < n_iter; ++it) {
+        int64_t p = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        unsigned long long evals = 0, full = 0, cut = 0, sub = 0, empty = 0, tp = 0, sp = 0, outer = 0;
+        if (p < A.npairs) {
+            const int cls = A.pcls[p];
+            if (cls > 0 && P.singular) {
+                sp = 1;
+            } else {
+                tp = 1;
+                const int4 tk = A.T[A.pk[p]], tl = A.T[A.pl[p]];
+                const double2 Vk[3] = {A.X[tk.x], A.X[tk.y], A.X[tk.z]};
+                const double2 Vl[3] = {A.X[tl.x], A.X[tl.y], A.X[tl.z]};
+                for (int q0 = 0; q0 < P.ro.n; ++q0) {
+                    const double2 xp = nl_map(Vk, P.ro.l[q0][0], P.ro.l[q0][1], P.ro.l[q0][2]);
+                    bool f;
+                    const int np = nl_clip(Vl, xp, P.delta, P.delta2, caps, nullptr, f);
+                    ++outer;
+                    if (np < 3) { ++empty; continue; }
+                    if (f) { ++full; evals += P.ri.n; }
+                    else { ++cut; sub += np - 2; evals += (unsigned long long)(np - 2) * P.ri.n; }
+                }
+            }
+        }
+        warp_add(&cnt[0], evals);
+        warp_add(&cnt[1], full);
+        warp_add(&cnt[2], cut);
+        warp_add(&cnt[3], sub);
+        warp_add(&cnt[5], tp);
+        warp_add(&cnt[6], sp);
+        warp_add(&cnt[7], empty);
+        warp_add(&cnt[8], outer);
+    }
+}
+
+void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStream_t st) {
+    DBuf<unsigned long long> c;
+    c.alloc(16, st);
+    c.zero(st);
+    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, pc.npairs, m.X.p, m.T.p, m.det.p, prm};
+    unsigned grid = (unsigned)std::min<int64_t>(nblk(pc.npairs, 256), 152 * 32);
+    if (grid) {
+        k_census<<<grid, 256, 0, st>>>(a, c.p);
+        NLFEM_LAUNCH_CHECK();
+    }
+    unsigned long long h[16];
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(h, c.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    // singular-rule points actually evaluated: 6 n^2 (identical), 4 n^3 (edge), 2 n^4 (vertex)
+    const int64_t n = prm.dr.n;
+    int64_t duffy = 0;
+    if (prm.singular)
+        duffy = pc.counts[3] * 6 * n * n + pc.counts[2] * 4 * n * n * n + pc.counts[1] * 2 * n * n * n * n;
+    h[4] = (unsigned long long)duffy;
+    for (int i = 0; i < 9; ++i) out[i] = (int64_t)h[i];
+}
+
+}  // namespace nlfem
