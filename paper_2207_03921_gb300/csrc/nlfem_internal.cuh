@@ -89,6 +89,8 @@ struct Mesh {
     double bbox[4] = {0, 0, 0, 0};  // xmin, ymin, xmax, ymax
     double rmax = 0;      // max element radius (centroid to vertex)
     DBuf<double2> cen;    // centroids [K]
+    DBuf<float4> E32;     // FP32 edge vectors (v1 - v0, v2 - v0) [K], each rounded once from FP64
+    DBuf<float> det32;    // |det J_k| in FP32 [K]
     DBuf<double> rad;     // radii [K]
     std::shared_ptr<PairCache> cache;  // pair list, pattern and slot index of the last (delta, ball, rule)
     int64_t device_bytes() const;
@@ -126,7 +128,7 @@ struct PairCache {
     DBuf<int8_t> pcls;       // shared vertex count [P]
     DBuf<int64_t> pT_ptr;    // [K + 1] pairs grouped by l
     DBuf<int> pT_id;         // [P] pair ids, sorted per l
-    DBuf<int> duffy_ids;     // pairs that take the singular rule
+    DBuf<int> duffy_ids;     // intersecting pairs (shared vertex), in pair order
     int64_t nduffy = 0;
     int64_t counts[4] = {0, 0, 0, 0};  // separated, vertex, edge, identical
     // node-level pattern
@@ -143,6 +145,9 @@ struct PairCache {
     DBuf<uint32_t> idx;      // [ncontrib] packed (pair - pbase[row]) * NE + entry
     DBuf<int64_t> pbase;     // [M] first pair id a node row refers to
     int64_t ncontrib = 0;
+    DBuf<int64_t> up_pos;    // node-level upper entries (i, j >= i): pattern position
+    DBuf<int> up_row;        //   and row i
+    int64_t n_upper = 0;
     double t_pairs_ms = 0, t_pattern_ms = 0;
 };
 
@@ -172,6 +177,7 @@ void run_reduction(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaS
 void run_load(Mesh& m, const Params& prm, const double* f_nodal, System& sys, cudaStream_t st);
 int64_t contrib_entries(int ndof);
 void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStream_t st);
+void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st);
 int solve_system(System& S, const double* g, double tol, int max_iter, double* u_out, nlfem_solve_info* info,
                  cudaStream_t st);
 
@@ -320,4 +326,94 @@ __device__ __forceinline__ int nl_clip(const double2 V[3], double2 c, double del
         }
     }
     return m;
+}
+
+// ------------------------------------------------------------------------------------------
+// FP32 geometry with exact decisions (bulk quadrature and the pair-search predicate)
+//
+// R[m] = vertex m of E_l relative to x_p in FP32, C[m] = |R[m]|^2 - delta^2. eps bounds the
+// absolute FP32 error of the R components. Each decision the canonical FP64 clip takes is
+// taken here only if its margin exceeds a first-order error bound:
+//   vertex in ball:    |C| > floor2 + 2 |R|_1 eps
+//   chord (both ends outside): |B^2 - A C| > bound(A, B, C, eps)
+// nl_decide32 returns false when some decision is too close to call (the caller then uses
+// the canonical FP64 clip). Otherwise g holds, per edge, the number of crossings and their
+// parameters (increasing); no root snaps or point merges can occur in that case.
+// ------------------------------------------------------------------------------------------
+struct Geo32 {
+    float ta[3], tb[3];
+    int nc[3];
+    bool in[3];
+};
+
+__device__ __forceinline__ bool nl_decide32(const float Rx[3], const float Ry[3], const float C[3], float eps,
+                                            float floor2, float d2, Geo32& g) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        if (fabsf(C[m]) <= floor2 + 2.f * (fabsf(Rx[m]) + fabsf(Ry[m])) * eps) return false;
+        g.in[m] = C[m] < 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int b = (e + 1) % 3;
+        g.nc[e] = 0;
+        g.ta[e] = g.tb[e] = 0.f;
+        if (g.in[e] && g.in[b]) continue;
+        const float ux = Rx[b] - Rx[e], uy = Ry[b] - Ry[e];
+        const float Aq = ux * ux + uy * uy;
+        const float Bq = Rx[e] * ux + Ry[e] * uy;
+        const float Cq = C[e];
+        const float disc = Bq * Bq - Aq * Cq;
+        if (g.in[e] != g.in[b]) {
+            // exactly one crossing; stable roots, take the one in (0,1)
+            const float sq = sqrtf(fmaxf(disc, 0.f));
+            const float qq = -(Bq + copysignf(sq, Bq));
+            const float r1 = qq / Aq, r2 = Cq / qq;
+            g.ta[e] = g.in[e] ? fmaxf(r1, r2) : fminf(r1, r2);
+            g.nc[e] = 1;
+        } else {
+            const float e1n = fabsf(Rx[e]) + fabsf(Ry[e]), u1n = fabsf(ux) + fabsf(uy);
+            const float bound = 2.f * fabsf(Bq) * (u1n + 2.f * e1n) * eps + Aq * (2.f * e1n * eps + 1e-6f * d2) +
+                                fabsf(Cq) * 4.f * u1n * eps + 1e-6f * (Bq * Bq + fabsf(Aq * Cq));
+            if (fabsf(disc) <= bound) return false;
+            if (disc > 0.f) {
+                const float tc = -Bq / Aq;
+                if (tc > 0.f && tc < 1.f) {
+                    const float sq = sqrtf(disc);
+                    const float qq = -(Bq + copysignf(sq, Bq));
+                    const float r1 = qq / Aq, r2 = Cq / qq;
+                    g.ta[e] = fminf(r1, r2);
+                    g.tb[e] = fmaxf(r1, r2);
+                    g.nc[e] = 2;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// Number of polygon points of a decided configuration (vertices inside, crossings, and
+// with caps one cap per consecutive pair not joined along one edge).
+__device__ __forceinline__ int nl_count32(const Geo32& g, bool caps) {
+    if (g.in[0] && g.in[1] && g.in[2]) return 3;
+    int nraw = 0, ncap = 0;
+    int fe = 0, fv = 0, le = 0, lv = 0;  // first / last raw point: edge and vertex flag
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int cnt = (g.in[e] ? 1 : 0) + g.nc[e];
+        for (int j = 0; j < cnt; ++j) {
+            const int v = (j == 0 && g.in[e]) ? 1 : 0;
+            // consecutive points on the same edge are joined; else Q must be the next edge's vertex
+            if (nraw > 0 && le != e && !(v && e == (le + 1) % 3)) ++ncap;
+            if (nraw == 0) { fe = e; fv = v; }
+            le = e;
+            lv = v;
+            ++nraw;
+        }
+    }
+    (void)lv;
+    // wrap-around last -> first: joined only if first is the vertex that starts the edge after
+    // last's (on one edge the first point never has the larger parameter)
+    if (nraw >= 2 && !(fv && fe == (le + 1) % 3)) ++ncap;
+    return nraw + (caps && nraw >= 2 ? ncap : 0);
 }

@@ -50,6 +50,9 @@ __device__ __forceinline__ int shared_count(int4 a, int4 b) {
 struct SearchArgs {
     const double2* X;
     const int4* T;
+    const float4* E32;
+    float ol[16][2];  // outer rule barycentrics (l1, l2) in FP32
+    float delta32, d2f;
     const double2* cen;
     const double* rad;
     const int* cell_of;
@@ -67,15 +70,36 @@ __device__ bool interacts(const SearchArgs& a, int k, int l, int4 tk, const doub
     if (shared_count(tk, tl) > 0) return true;
     double2 cl = a.cen[l];
     double rl = a.rad[l];
-    double dx = cl.x - ck.x, dy = cl.y - ck.y;
-    double dist = sqrt(dx * dx + dy * dy);
+    double cdx = cl.x - ck.x, cdy = cl.y - ck.y;
+    double dist = sqrt(cdx * cdx + cdy * cdy);
     if (dist - rk - rl > a.delta * (1.0 + 1e-9)) return false;
     if (dist + rk + rl <= a.delta * (1.0 - 1e-9)) return true;  // E_l inside the ball of every x in E_k
-    double2 Vl[3] = {a.X[tl.x], a.X[tl.y], a.X[tl.z]};
+    // FP32 geometry with exact decisions; the canonical FP64 clip only for near ties
+    const double2 v0l = a.X[tl.x];
+    const float dx = (float)(v0l.x - Vk[0].x), dy = (float)(v0l.y - Vk[0].y);
+    const float4 Ek = a.E32[k], El = a.E32[l];
+    const float span = fabsf(dx) + fabsf(dy) + fabsf(Ek.x) + fabsf(Ek.y) + fabsf(Ek.z) + fabsf(Ek.w) +
+                       fabsf(El.x) + fabsf(El.y) + fabsf(El.z) + fabsf(El.w);
+    const float eps = 4.8e-7f * span, floor2 = 1e-5f * a.d2f;
+    const float Wx[3] = {dx, dx + El.x, dx + El.z}, Wy[3] = {dy, dy + El.y, dy + El.w};
     for (int p = 0; p < a.ro.n; ++p) {
-        double2 xp = nl_map(Vk, a.ro.l[p][0], a.ro.l[p][1], a.ro.l[p][2]);
-        bool full;
-        if (nl_clip(Vl, xp, a.delta, a.delta2, a.caps != 0, nullptr, full) >= 3) return true;
+        const float Xx = a.ol[p][0] * Ek.x + a.ol[p][1] * Ek.z, Xy = a.ol[p][0] * Ek.y + a.ol[p][1] * Ek.w;
+        float Rx[3], Ry[3], C[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            Rx[m] = Wx[m] - Xx;
+            Ry[m] = Wy[m] - Xy;
+            C[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - a.d2f;
+        }
+        Geo32 G;
+        if (nl_decide32(Rx, Ry, C, eps, floor2, a.d2f, G)) {
+            if (nl_count32(G, a.caps != 0) >= 3) return true;
+        } else {
+            const double2 Vl[3] = {v0l, a.X[tl.y], a.X[tl.z]};
+            const double2 xp = nl_map(Vk, a.ro.l[p][0], a.ro.l[p][1], a.ro.l[p][2]);
+            bool full;
+            if (nl_clip(Vl, xp, a.delta, a.delta2, a.caps != 0, nullptr, full) >= 3) return true;
+        }
     }
     return false;
 }
@@ -129,12 +153,18 @@ __global__ void k_fill_k(const int64_t* ptr, int64_t K, int* pk) {
 __global__ void k_classify(const int* pk, const int* pl, int64_t P, const int4* T, int8_t* cls,
                            unsigned long long* counts, int64_t* tcount) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    int l = pl[p];
-    int c = shared_count(T[pk[p]], T[l]);
-    cls[p] = (int8_t)c;
-    atomicAdd(&counts[c], 1ull);
-    atomicAdd((unsigned long long*)&tcount[l], 1ull);
+    int c = -1;
+    if (p < P) {
+        int l = pl[p];
+        c = shared_count(T[pk[p]], T[l]);
+        cls[p] = (int8_t)c;
+        atomicAdd((unsigned long long*)&tcount[l], 1ull);
+    }
+    // class counts, aggregated per warp
+    for (int v = 0; v < 4; ++v) {
+        unsigned m = __ballot_sync(0xffffffffu, c == v);
+        if ((threadIdx.x & 31) == 0 && m) atomicAdd(&counts[v], (unsigned long long)__popc(m));
+    }
 }
 
 __global__ void k_fill_T(const int* pl, int64_t P, const int64_t* tptr, int* cursor, int* tid) {
@@ -209,6 +239,13 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     a.X = m.X.p; a.T = m.T.p; a.cen = m.cen.p; a.rad = m.rad.p; a.cell_of = cell_of.p;
     a.cell_start = cstart.p; a.cell_list = clist.p; a.g = g; a.K = K;
     a.delta = prm.delta; a.delta2 = prm.delta2; a.caps = prm.ball == NLFEM_BALL_APPROXCAPS; a.ro = prm.ro;
+    a.E32 = m.E32.p;
+    for (int i = 0; i < 16; ++i) {
+        a.ol[i][0] = i < prm.ro.n ? (float)prm.ro.l[i][1] : 0.f;
+        a.ol[i][1] = i < prm.ro.n ? (float)prm.ro.l[i][2] : 0.f;
+    }
+    a.delta32 = (float)prm.delta;
+    a.d2f = (float)prm.delta * (float)prm.delta;
 
     DBuf<int64_t> cnt;
     cnt.alloc(K, st);
@@ -259,10 +296,10 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
     for (int i = 0; i < 4; ++i) pc.counts[i] = (int64_t)hc[i];
 
-    // pairs that take the singular rule: every intersecting pair
+    // intersecting pairs (the singular rule, or the canonical truncation kernel, takes them)
     pc.nduffy = 0;
     pc.duffy_ids.release();
-    if (prm.singular && P) {
+    if (P) {
         DBuf<int64_t> flag, pos;
         flag.alloc(P, st);
         pos.alloc(P + 1, st);

@@ -11,6 +11,7 @@
 // (union = vertices of E_k, then the vertices of E_l not in E_k). Scalar: 21 values per
 // pair; peridynamics: 4 components (c1, c2) per entry, 84 values per pair.
 #include <algorithm>
+#include <cmath>
 
 #include "nlfem_internal.cuh"
 
@@ -309,78 +310,169 @@ __global__ void k_slots(RowEnum R, int64_t M, const int64_t* nptr, const int* nc
 }
 
 // ------------------------------------------------------------------------------------------
-// segmented reduction (thread per node-level upper entry)
+// segmented reduction: one warp per node-level upper CSR entry (i, j >= i). Lanes read the
+// segment's index entries coalesced and gather the contributions; each lane sums its
+// strided share (TwoSum-compensated in FP32 for the bulk path, FP64 for the plain path),
+// and the 32 partial sums are combined in a fixed butterfly, so the result is the same on
+// every run. The value is written to (i, j) and (j, i).
 // ------------------------------------------------------------------------------------------
+struct CSum {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum_add(CSum& a, float x) {
+    float s = a.hi + x;
+    float bp = s - a.hi;
+    a.lo += (a.hi - (s - bp)) + (x - bp);
+    a.hi = s;
+}
+
+__device__ __forceinline__ void two_sum_merge(CSum& a, const CSum& b) {
+    two_sum_add(a, b.hi);
+    a.lo += b.lo;
+}
+
+template <typename R>
+__device__ __forceinline__ double warp_total(R v);
+
+template <>
+__device__ __forceinline__ double warp_total<double>(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_total_c(CSum c) {
+    for (int o = 16; o > 0; o >>= 1) {
+        CSum d;
+        d.hi = __shfl_xor_sync(0xffffffffu, c.hi, o);
+        d.lo = __shfl_xor_sync(0xffffffffu, c.lo, o);
+        // combine in a lane-independent order so all lanes agree bit for bit
+        CSum a = (threadIdx.x & o) ? d : c, b = (threadIdx.x & o) ? c : d;
+        two_sum_merge(a, b);
+        c = a;
+    }
+    return (double)c.hi + (double)c.lo;
+}
+
 template <typename R, int NDOF>
-__global__ void k_reduce(int64_t M, const int64_t* nptr, const int* ncol, const int64_t* seg_ptr,
-                         const uint32_t* idx, const int64_t* pbase, const R* contrib,
-                         const int64_t* row_ptr, const int64_t* tpos, double* val) {
-    int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (i >= M) return;
+__global__ void __launch_bounds__(256) k_reduce(int64_t n_upper, const int64_t* __restrict__ up_pos,
+                                                const int* __restrict__ up_row, const int64_t* __restrict__ nptr,
+                                                const int* __restrict__ ncol, const int64_t* __restrict__ seg_ptr,
+                                                const uint32_t* __restrict__ idx, const int64_t* __restrict__ pbase,
+                                                const R* __restrict__ contrib, const int64_t* __restrict__ row_ptr,
+                                                const int64_t* __restrict__ tpos, double* __restrict__ val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int NE = NDOF == 1 ? 21 : 84;
-    int64_t rb = nptr[i], re = nptr[i + 1];
-    int64_t pb = pbase[i];
-    for (int64_t t = rb + lane; t < re; t += 32) {
-        int j = ncol[t];
-        if (j < i) continue;
-        int64_t s0 = seg_ptr[t], s1 = seg_ptr[t + 1];
+    for (int64_t u = wid; u < n_upper; u += nw) {
+        const int64_t t = up_pos[u];  // node-level pattern position
+        const int i = up_row[u];
+        const int j = ncol[t];
+        const int64_t s0 = seg_ptr[t], s1 = seg_ptr[t + 1];
+        const int64_t pb = pbase[i];
         if (NDOF == 1) {
             double v;
             if (sizeof(R) == 4) {
-                // compensated FP32 summation (TwoSum), exact to about 2^-48 relative
-                float hi = 0.f, lo = 0.f;
-                for (int64_t q = s0; q < s1; ++q) {
-                    uint32_t e = idx[q];
-                    float x = (float)contrib[(pb + (e >> 6)) * NE + (e & 31)];
-                    float sum = hi + x;
-                    float bp = sum - hi;
-                    lo += (hi - (sum - bp)) + (x - bp);
-                    hi = sum;
+                CSum c{0.f, 0.f};
+                for (int64_t q = s0 + lane; q < s1; q += 32) {
+                    const uint32_t e = idx[q];
+                    two_sum_add(c, (float)contrib[(pb + (e >> 6)) * NE + (e & 31)]);
                 }
-                v = (double)hi + (double)lo;
+                v = warp_total_c(c);
             } else {
-                v = 0.0;
-                for (int64_t q = s0; q < s1; ++q) {
-                    uint32_t e = idx[q];
-                    v += (double)contrib[(pb + (e >> 6)) * NE + (e & 31)];
+                double a = 0.0;
+                for (int64_t q = s0 + lane; q < s1; q += 32) {
+                    const uint32_t e = idx[q];
+                    a += (double)contrib[(pb + (e >> 6)) * NE + (e & 31)];
                 }
+                v = warp_total<double>(a);
             }
-            int64_t s = row_ptr[i] + (t - rb);
-            val[s] = v;
-            val[tpos[s]] = v;
+            if (lane == 0) {
+                const int64_t s = row_ptr[i] + (t - nptr[i]);
+                val[s] = v;
+                val[tpos[s]] = v;
+            }
         } else {
-            double v[4] = {0, 0, 0, 0};
-            float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
-            for (int64_t q = s0; q < s1; ++q) {
-                uint32_t e = idx[q];
-                const R* c = contrib + (pb + (e >> 6)) * NE + (e & 31) * 4;
-                bool tr = (e >> 5) & 1;
-                R x[4] = {c[0], tr ? c[2] : c[1], tr ? c[1] : c[2], c[3]};
+            CSum c[4];
+            double a[4] = {0, 0, 0, 0};
+            for (int k = 0; k < 4; ++k) c[k] = CSum{0.f, 0.f};
+            for (int64_t q = s0 + lane; q < s1; q += 32) {
+                const uint32_t e = idx[q];
+                const R* cp = contrib + (pb + (e >> 6)) * NE + (e & 31) * 4;
+                const bool tr = (e >> 5) & 1;
+                const R x[4] = {cp[0], tr ? cp[2] : cp[1], tr ? cp[1] : cp[2], cp[3]};
                 for (int k = 0; k < 4; ++k) {
-                    if (sizeof(R) == 4) {
-                        float sum = hi[k] + (float)x[k];
-                        float bp = sum - hi[k];
-                        lo[k] += (hi[k] - (sum - bp)) + ((float)x[k] - bp);
-                        hi[k] = sum;
-                    } else {
-                        v[k] += (double)x[k];
-                    }
+                    if (sizeof(R) == 4) two_sum_add(c[k], (float)x[k]);
+                    else a[k] += (double)x[k];
                 }
             }
-            if (sizeof(R) == 4)
-                for (int k = 0; k < 4; ++k) v[k] = (double)hi[k] + (double)lo[k];
-            int64_t r = t - rb;
-            for (int c1 = 0; c1 < 2; ++c1)
-                for (int c2 = 0; c2 < 2; ++c2) {
-                    if (j == i && c2 < c1) continue;  // the diagonal node block: upper dofs only
-                    int64_t s = row_ptr[i * 2 + c1] + 2 * r + c2;
-                    double x = v[c1 * 2 + c2];
-                    val[s] = x;
-                    val[tpos[s]] = x;
-                }
+            double v[4];
+            for (int k = 0; k < 4; ++k) v[k] = sizeof(R) == 4 ? warp_total_c(c[k]) : warp_total<double>(a[k]);
+            if (lane == 0) {
+                const int64_t r = t - nptr[i];
+                for (int c1 = 0; c1 < 2; ++c1)
+                    for (int c2 = 0; c2 < 2; ++c2) {
+                        if (j == i && c2 < c1) continue;  // the diagonal node block: upper dofs only
+                        const int64_t s = row_ptr[(int64_t)i * 2 + c1] + 2 * r + c2;
+                        val[s] = v[c1 * 2 + c2];
+                        val[tpos[s]] = v[c1 * 2 + c2];
+                    }
+            }
         }
     }
+}
+
+// list of node-level upper entries (i, j >= i): pattern position and row
+__global__ void k_upper_count(const int64_t* nptr, const int* ncol, int64_t M, int64_t* cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    int64_t b = nptr[i], e = nptr[i + 1];
+    int64_t c = 0;
+    for (int64_t t = b; t < e; ++t) c += ncol[t] >= (int)i;
+    cnt[i] = c;
+}
+
+// node rows in the order of 2D tiles (cells of a uniform grid over the mesh, rows of a
+// cell by node index): warps running at the same time then touch the contributions of a
+// compact patch of elements, which stays in L2
+__global__ void k_node_cell(const double2* X, int64_t M, double x0, double y0, double cs, int nx, int ny,
+                            int64_t* cnt, int* cell) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    double2 v = X[i];
+    int cx = min(nx - 1, max(0, (int)floor((v.x - x0) / cs)));
+    int cy = min(ny - 1, max(0, (int)floor((v.y - y0) / cs)));
+    int c = cy * nx + cx;
+    cell[i] = c;
+    atomicAdd((unsigned long long*)&cnt[c], 1ull);
+}
+
+__global__ void k_node_place(const int* cell, int64_t M, const int64_t* start, int* cursor, int* order) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    int pos = atomicAdd(&cursor[cell[i]], 1);
+    order[start[cell[i]] + pos] = (int)i;
+}
+
+__global__ void k_gather_i64(const int64_t* a, const int* order, int64_t n, int64_t* b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[order[i]];
+}
+
+__global__ void k_upper_fill(const int64_t* nptr, const int* ncol, int64_t M, const int64_t* off, int64_t* up_pos,
+                             int* up_row, const int* order) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    const int64_t i = order[r];
+    int64_t b = nptr[i], e = nptr[i + 1];
+    int64_t o = off[r];
+    for (int64_t t = b; t < e; ++t)
+        if (ncol[t] >= (int)i) {
+            up_pos[o] = t;
+            up_row[o] = (int)i;
+            ++o;
+        }
 }
 
 __global__ void k_row_max(const int64_t* ptr, int64_t n, int* out) {
@@ -475,27 +567,81 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
     NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
     NLFEM_CHECK(!(h & 2), NLFEM_ERR_UNSUPPORTED,
                 "a CSR row refers to pairs more than 2^26 apart (or misses a column)");
+    // node-level upper entries, the work items of the reduction, in 2D tile order of the rows
+    DBuf<int> order;
+    order.alloc(M, st);
+    {
+        const double W = m.bbox[2] - m.bbox[0], H = m.bbox[3] - m.bbox[1];
+        double cs = std::sqrt(std::max(W * H, 1e-300) / (double)M) * 16.0;  // about 256 nodes per tile
+        if (!(cs > 0)) cs = 1.0;
+        int nx = std::max(1, (int)std::ceil(W / cs)), ny = std::max(1, (int)std::ceil(H / cs));
+        while ((int64_t)nx * ny > (1 << 22)) {
+            cs *= 2.0;
+            nx = std::max(1, (int)std::ceil(W / cs));
+            ny = std::max(1, (int)std::ceil(H / cs));
+        }
+        const int64_t nc = (int64_t)nx * ny;
+        DBuf<int64_t> ccnt, cstart;
+        DBuf<int> cell, cur;
+        ccnt.alloc(nc, st);
+        ccnt.zero(st);
+        cstart.alloc(nc + 1, st);
+        cell.alloc(M, st);
+        cur.alloc(nc, st);
+        cur.zero(st);
+        k_node_cell<<<nblk(M, 256), 256, 0, st>>>(m.X.p, M, m.bbox[0], m.bbox[1], cs, nx, ny, ccnt.p, cell.p);
+        NLFEM_LAUNCH_CHECK();
+        exclusive_scan_i64(ccnt.p, cstart.p, nc, st);
+        k_node_place<<<nblk(M, 256), 256, 0, st>>>(cell.p, M, cstart.p, cur.p, order.p);
+        NLFEM_LAUNCH_CHECK();
+        DBuf<unsigned long long> mx;
+        DBuf<int> mxi;
+        mxi.alloc(1, st);
+        mxi.zero(st);
+        k_row_max<<<nblk(nc, 256), 256, 0, st>>>(cstart.p, nc, mxi.p);
+        NLFEM_LAUNCH_CHECK();
+        int hm = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&hm, mxi.p, sizeof hm, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        segmented_sort_i32(order.p, nullptr, cstart.p, nc, hm, st);  // deterministic order within a tile
+    }
+    DBuf<int64_t> ucnt, ucnt_o, uoff;
+    ucnt.alloc(M, st);
+    ucnt_o.alloc(M, st);
+    uoff.alloc(M + 1, st);
+    k_upper_count<<<nblk(M, 256), 256, 0, st>>>(pc.nrow_ptr.p, pc.ncol.p, M, ucnt.p);
+    NLFEM_LAUNCH_CHECK();
+    k_gather_i64<<<nblk(M, 256), 256, 0, st>>>(ucnt.p, order.p, M, ucnt_o.p);
+    NLFEM_LAUNCH_CHECK();
+    exclusive_scan_i64(ucnt_o.p, uoff.p, M, st);
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.n_upper, uoff.p + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    pc.up_pos.alloc(pc.n_upper, st);
+    pc.up_row.alloc(pc.n_upper, st);
+    k_upper_fill<<<nblk(M, 256), 256, 0, st>>>(pc.nrow_ptr.p, pc.ncol.p, M, uoff.p, pc.up_pos.p, pc.up_row.p,
+                                               order.p);
+    NLFEM_LAUNCH_CHECK();
 }
 
 void run_reduction(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st) {
-    const int64_t M = m.M;
+    (void)m;
     NLFEM_CUDA_TRY(cudaMemsetAsync(sys.val.p, 0, sys.val.bytes(), st));
-    unsigned g = nblk(M, 8);
+    if (pc.n_upper == 0) return;
+    // one warp per entry, blocks dispatched in order: the entries in flight stay a compact set
+    // of tiles (a grid-stride loop would scatter them over the whole mesh)
+    const unsigned g = (unsigned)std::min<int64_t>(nblk(pc.n_upper * 32, 256), 0x7fffffffll);
+#define NLFEM_RED(R, ND, C)                                                                             \
+    k_reduce<R, ND><<<g, 256, 0, st>>>(pc.n_upper, pc.up_pos.p, pc.up_row.p, pc.nrow_ptr.p, pc.ncol.p,  \
+                                       pc.seg_ptr.p, pc.idx.p, pc.pbase.p, C, pc.row_ptr.p, pc.tpos.p, \
+                                       sys.val.p)
     if (prm.precision == NLFEM_PREC_FP32_BULK) {
-        if (pc.ndof == 1)
-            k_reduce<float, 1><<<g, 256, 0, st>>>(M, pc.nrow_ptr.p, pc.ncol.p, pc.seg_ptr.p, pc.idx.p, pc.pbase.p,
-                                                 sys.contrib32.p, pc.row_ptr.p, pc.tpos.p, sys.val.p);
-        else
-            k_reduce<float, 2><<<g, 256, 0, st>>>(M, pc.nrow_ptr.p, pc.ncol.p, pc.seg_ptr.p, pc.idx.p, pc.pbase.p,
-                                                 sys.contrib32.p, pc.row_ptr.p, pc.tpos.p, sys.val.p);
+        if (pc.ndof == 1) NLFEM_RED(float, 1, sys.contrib32.p);
+        else NLFEM_RED(float, 2, sys.contrib32.p);
     } else {
-        if (pc.ndof == 1)
-            k_reduce<double, 1><<<g, 256, 0, st>>>(M, pc.nrow_ptr.p, pc.ncol.p, pc.seg_ptr.p, pc.idx.p, pc.pbase.p,
-                                                  sys.contrib64.p, pc.row_ptr.p, pc.tpos.p, sys.val.p);
-        else
-            k_reduce<double, 2><<<g, 256, 0, st>>>(M, pc.nrow_ptr.p, pc.ncol.p, pc.seg_ptr.p, pc.idx.p, pc.pbase.p,
-                                                  sys.contrib64.p, pc.row_ptr.p, pc.tpos.p, sys.val.p);
+        if (pc.ndof == 1) NLFEM_RED(double, 1, sys.contrib64.p);
+        else NLFEM_RED(double, 2, sys.contrib64.p);
     }
+#undef NLFEM_RED
     NLFEM_LAUNCH_CHECK();
 }
 

@@ -29,7 +29,8 @@ struct QuadArgs {
     const int* pk;
     const int* pl;
     const int8_t* pcls;
-    int64_t npairs;
+    int64_t npairs;        // number of pairs to process (of ids, if given)
+    const int* ids;        // optional list of pair ids
     const double2* X;
     const int4* T;
     const double* det;
@@ -90,8 +91,9 @@ __global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contr
     constexpr int NE = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 84 : 21;
     const Params& P = A.prm;
     const bool caps = P.ball == NLFEM_BALL_APPROXCAPS;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.npairs;
-         p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pi < A.npairs;
+         pi += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = A.ids ? (int64_t)A.ids[pi] : pi;
         const int cls = A.pcls[p];
         if (cls > 0 && P.singular) continue;  // k_duffy writes this pair
         const int k = A.pk[p], l = A.pl[p];
@@ -484,9 +486,17 @@ static void launch_trunc(const QuadArgs& a, R* out, cudaStream_t st) {
 }
 
 void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st) {
-    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, pc.npairs, m.X.p, m.T.p, m.det.p, prm};
-    if (prm.precision == NLFEM_PREC_FP32_BULK) launch_trunc<float>(a, sys.contrib32.p, st);
-    else launch_trunc<double>(a, sys.contrib64.p, st);
+    if (prm.precision == NLFEM_PREC_FP32_BULK) {
+        // separated pairs: FP32 geometry with exact decisions; intersecting pairs: canonical
+        launch_trunc_fast(m, pc, prm, sys.contrib32.p, st);
+        if (!prm.singular && pc.nduffy > 0) {
+            QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, pc.nduffy, pc.duffy_ids.p, m.X.p, m.T.p, m.det.p, prm};
+            launch_trunc<float>(c, sys.contrib32.p, st);
+        }
+    } else {
+        QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, pc.npairs, nullptr, m.X.p, m.T.p, m.det.p, prm};
+        launch_trunc<double>(a, sys.contrib64.p, st);
+    }
     if (prm.singular && pc.nduffy > 0) {
         DuffyArgs d{pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
         k_duffy<<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(
@@ -560,7 +570,7 @@ void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStr
     DBuf<unsigned long long> c;
     c.alloc(16, st);
     c.zero(st);
-    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, pc.npairs, m.X.p, m.T.p, m.det.p, prm};
+    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, pc.npairs, nullptr, m.X.p, m.T.p, m.det.p, prm};
     unsigned grid = (unsigned)std::min<int64_t>(nblk(pc.npairs, 256), 152 * 32);
     if (grid) {
         k_census<<<grid, 256, 0, st>>>(a, c.p);
