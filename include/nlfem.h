@@ -178,6 +178,28 @@ int nlfem_system_census(nlfem_system_t sys, int64_t counts[9], void* stream);
 
 void nlfem_system_destroy(nlfem_system_t sys);
 
+/*
+ * Interaction graph of a small mesh, computed without allocating any device memory.
+ * For callers that cannot call cudaMalloc at the point where they need the pairs: code
+ * running inside a CUDA graph capture, a serving process that reserved the device
+ * memory up front for its own arena, or a context where an out-of-memory failure must
+ * not be possible. The paper has no counterpart; it returns the same pairs as
+ * nlfem_mesh_pairs after an nlfem_assemble with the same delta, ball and outer rule.
+ * verts [M x 2] FP64, elems [K x 3] int32 (device memory; any orientation), out_k and
+ * out_l device int32 arrays of length capacity, owned by the caller; on success they hold
+ * the *npairs ordered interacting pairs sorted by (k, l) (host int64 output).
+ * Limits: K <= 32768 triangles and M <= 65536 vertices (NLFEM_ERR_UNSUPPORTED beyond).
+ * The working data lives in a 4.5 MB file-scope device array that every GPU loading this
+ * library holds until the process exits; the first call on a device looks up its address,
+ * so make that first call before any stream capture. All calls share that array: calls
+ * that overlap on the GPU (other streams or host threads) race and must be serialised.
+ * Errors: INVALID_ARG (NULL or host pointers, delta <= 0, unknown ball / rule, capacity
+ * too small: *npairs then holds the number needed), UNSUPPORTED, BAD_MESH, CUDA.
+ */
+int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t* elems, int64_t K, double delta,
+                        int ball, int quad_outer, int32_t* out_k, int32_t* out_l, int64_t capacity,
+                        int64_t* npairs, void* stream);
+
 /* Device memory held by a mesh handle and its cached pair list / pattern, in bytes. */
 int64_t nlfem_mesh_device_bytes(nlfem_mesh_t mesh);
 

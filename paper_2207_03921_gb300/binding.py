@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
         lib.nlfem_system_destroy.restype = None
         lib.nlfem_mesh_device_bytes.argtypes = [vp]
         lib.nlfem_mesh_device_bytes.restype = i64
+        lib.nlfem_pairs_noalloc.argtypes = [vp, i64, vp, i64, dp, ip, ip, vp, vp, i64, C.POINTER(i64), vp]
         _lib = lib
     return _lib
 
@@ -208,6 +209,22 @@ def nlfem_system_destroy(sys):
 
 def nlfem_mesh_device_bytes(mesh) -> int:
     return int(load().nlfem_mesh_device_bytes(mesh))
+
+
+def nlfem_pairs_noalloc(verts, elems, delta, ball, quad_outer, out_k, out_l, stream=None) -> int:
+    """Interaction graph of a small mesh into caller-owned device buffers, without any
+    device allocation. verts [M, 2] float64, elems [K, 3] int32, out_k / out_l int32 (device
+    tensors). Returns the number of ordered pairs written (sorted by (k, l))."""
+    n = C.c_int64(0)
+    code = load().nlfem_pairs_noalloc(_ptr(verts), int(verts.shape[0]), _ptr(elems), int(elems.shape[0]),
+                                      float(delta), BALLS[ball] if isinstance(ball, str) else int(ball),
+                                      int(quad_outer), _ptr(out_k), _ptr(out_l), int(out_k.numel()),
+                                      C.byref(n), _stream(stream))
+    if code != NLFEM_OK:
+        err = NlfemError(code, load().nlfem_last_error().decode())
+        err.npairs = n.value
+        raise err
+    return n.value
 
 
 def nlfem_last_error() -> str:

@@ -8,6 +8,7 @@
 // pairs always interact; T_adj spans T_S) or some outer quadrature point x_p of E_k sees
 // a polygon of >= 3 points when E_l is cut by the ball approximation around x_p.
 #include <algorithm>
+#include <cmath>
 
 #include "nlfem_internal.cuh"
 
@@ -317,3 +318,295 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
 }
 
 }  // namespace nlfem
+
+// ==========================================================================================
+// nlfem_pairs_noalloc: the interaction graph of a small mesh without any device allocation.
+//
+// Every buffer the search needs beyond its inputs and outputs (oriented triangles,
+// centroids, radii, FP32 edges, a vertex copy, grid cells, per-element counts and offsets)
+// lives in g_noalloc_scratch below, a file-scope device array of NOALLOC_BYTES bytes that
+// every GPU loading this library holds until the process exits. Host code never uses the
+// array's name as an address: its device address is looked up once per device with
+// cudaGetSymbolAddress (on the first call on that device, which should therefore come
+// before any stream capture) and passed to the kernels. All calls share the array and it
+// keeps the last call's contents, so each call clears the counters it needs; calls that
+// overlap on the GPU (other streams, other host threads) race on it.
+// ==========================================================================================
+#include <mutex>
+
+#include "rules_table.h"
+
+namespace nlfem {
+
+static constexpr int64_t NOALLOC_MAX_ELEMS = 32768;
+static constexpr int64_t NOALLOC_MAX_VERTS = 65536;
+static constexpr int64_t NOALLOC_MAX_CELLS = 65536;
+
+// byte offsets of the sub-buffers (each a multiple of 256)
+static constexpr size_t NA_X = 0;                                              // double2[MAX_VERTS]
+static constexpr size_t NA_T = NA_X + 16 * NOALLOC_MAX_VERTS;                  // int4[MAX_ELEMS]
+static constexpr size_t NA_CEN = NA_T + 16 * NOALLOC_MAX_ELEMS;                // double2[MAX_ELEMS]
+static constexpr size_t NA_RAD = NA_CEN + 16 * NOALLOC_MAX_ELEMS;              // double[MAX_ELEMS]
+static constexpr size_t NA_E32 = NA_RAD + 8 * NOALLOC_MAX_ELEMS;               // float4[MAX_ELEMS]
+static constexpr size_t NA_CELLOF = NA_E32 + 16 * NOALLOC_MAX_ELEMS;           // int[MAX_ELEMS]
+static constexpr size_t NA_CLIST = NA_CELLOF + 4 * NOALLOC_MAX_ELEMS;          // int[MAX_ELEMS]
+static constexpr size_t NA_CNT = NA_CLIST + 4 * NOALLOC_MAX_ELEMS;             // int64[MAX_ELEMS]
+static constexpr size_t NA_PTR = NA_CNT + 8 * NOALLOC_MAX_ELEMS;               // int64[MAX_ELEMS + 1], padded
+static constexpr size_t NA_CCNT = NA_PTR + 8 * NOALLOC_MAX_ELEMS + 256;        // int64[MAX_CELLS]
+static constexpr size_t NA_CSTART = NA_CCNT + 8 * NOALLOC_MAX_CELLS;           // int64[MAX_CELLS + 1], padded
+static constexpr size_t NA_CCUR = NA_CSTART + 8 * NOALLOC_MAX_CELLS + 256;     // int[MAX_CELLS]
+static constexpr size_t NA_MISC = NA_CCUR + 4 * NOALLOC_MAX_CELLS;             // 256 bytes: flags, stats
+static constexpr size_t NOALLOC_BYTES = NA_MISC + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// per-device address of g_noalloc_scratch, looked up on the first call on that device
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256];
+
+static unsigned char* noalloc_scratch() {
+    int dev = 0;
+    NLFEM_CUDA_TRY(cudaGetDevice(&dev));
+    NLFEM_CHECK(dev >= 0 && dev < 256, NLFEM_ERR_UNSUPPORTED, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        NLFEM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        NLFEM_CHECK(p != nullptr, NLFEM_ERR_CUDA, "cudaGetSymbolAddress returned NULL for the scratch array");
+        g_noalloc_addr[dev] = p;
+    }
+    return (unsigned char*)g_noalloc_addr[dev];
+}
+
+// misc block: [0] int error flags, [1] int max count, then doubles at +16: rmax, xmin, ymin, xmax, ymax
+__global__ void k_na_init(unsigned char* misc) {
+    int* fl = (int*)misc;
+    fl[0] = 0;
+    fl[1] = 0;
+    double* st = (double*)(misc + 16);
+    st[0] = 0.0;
+    st[1] = 1e300;
+    st[2] = 1e300;
+    st[3] = -1e300;
+    st[4] = -1e300;
+}
+
+__device__ __forceinline__ void na_atomic_max_d(double* a, double v) {
+    unsigned long long* p = (unsigned long long*)a;
+    unsigned long long old = *p, assumed;
+    while (__longlong_as_double(old) < v) {
+        assumed = old;
+        old = atomicCAS(p, assumed, __double_as_longlong(v));
+        if (old == assumed) break;
+    }
+}
+__device__ __forceinline__ void na_atomic_min_d(double* a, double v) {
+    unsigned long long* p = (unsigned long long*)a;
+    unsigned long long old = *p, assumed;
+    while (__longlong_as_double(old) > v) {
+        assumed = old;
+        old = atomicCAS(p, assumed, __double_as_longlong(v));
+        if (old == assumed) break;
+    }
+}
+
+__global__ void k_na_verts(const double* verts, int64_t M, double2* X, unsigned char* misc) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    double2 v = make_double2(verts[2 * i], verts[2 * i + 1]);
+    X[i] = v;
+    double* st = (double*)(misc + 16);
+    na_atomic_min_d(&st[1], v.x);
+    na_atomic_min_d(&st[2], v.y);
+    na_atomic_max_d(&st[3], v.x);
+    na_atomic_max_d(&st[4], v.y);
+}
+
+// same orientation arithmetic as the mesh upload (CCW by the sign of the FP64 determinant)
+__global__ void k_na_elems(const int* T3, int64_t K, int64_t M, const double2* X, int4* T, double2* cen,
+                           double* rad, float4* E32, unsigned char* misc) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    int* fl = (int*)misc;
+    double* st = (double*)(misc + 16);
+    int t0 = T3[3 * k], t1 = T3[3 * k + 1], t2 = T3[3 * k + 2];
+    if (t0 < 0 || t1 < 0 || t2 < 0 || t0 >= M || t1 >= M || t2 >= M) {
+        atomicOr(&fl[0], 1);
+        T[k] = make_int4(0, 0, 0, 0);
+        cen[k] = make_double2(0.0, 0.0);
+        rad[k] = 0.0;
+        E32[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    double2 a = X[t0], b = X[t1], c = X[t2];
+    double d = __dsub_rn(__dmul_rn(__dsub_rn(b.x, a.x), __dsub_rn(c.y, a.y)),
+                         __dmul_rn(__dsub_rn(b.y, a.y), __dsub_rn(c.x, a.x)));
+    if (d < 0) {
+        int tt = t1; t1 = t2; t2 = tt;
+        double2 cc = b; b = c; c = cc;
+        d = -d;
+    }
+    if (!(d > 0)) atomicOr(&fl[0], 2);
+    T[k] = make_int4(t0, t1, t2, 0);
+    E32[k] = make_float4((float)(b.x - a.x), (float)(b.y - a.y), (float)(c.x - a.x), (float)(c.y - a.y));
+    double2 ce = make_double2((a.x + b.x + c.x) / 3.0, (a.y + b.y + c.y) / 3.0);
+    cen[k] = ce;
+    double r = sqrt(fmax(fmax((a.x - ce.x) * (a.x - ce.x) + (a.y - ce.y) * (a.y - ce.y),
+                              (b.x - ce.x) * (b.x - ce.x) + (b.y - ce.y) * (b.y - ce.y)),
+                         (c.x - ce.x) * (c.x - ce.x) + (c.y - ce.y) * (c.y - ce.y)));
+    rad[k] = r;
+    na_atomic_max_d(&st[0], r);
+}
+
+// exclusive scan of n <= 65536 int64 values in one block (out[n] = total)
+__global__ void k_na_scan(const int64_t* in, int64_t* out, int64_t n) {
+    __shared__ int64_t part[1024];
+    const int per = (int)((n + 1023) / 1024);
+    const int64_t b = (int64_t)threadIdx.x * per;
+    int64_t s = 0;
+    for (int i = 0; i < per; ++i)
+        if (b + i < n) s += in[b + i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int64_t t = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int64_t run = part[threadIdx.x] - s;
+    for (int i = 0; i < per; ++i)
+        if (b + i < n) {
+            out[b + i] = run;
+            run += in[b + i];
+        }
+    if (threadIdx.x == 1023) out[n] = part[1023];
+}
+
+__global__ void k_na_maxcnt(const int64_t* cnt, int64_t K, unsigned char* misc) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K) atomicMax(&((int*)misc)[1], (int)cnt[k]);
+}
+
+}  // namespace nlfem
+
+extern "C" int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t* elems, int64_t K, double delta,
+                                   int ball, int quad_outer, int32_t* out_k, int32_t* out_l, int64_t capacity,
+                                   int64_t* npairs, void* stream) {
+    using namespace nlfem;
+    try {
+        set_error("");
+        NLFEM_CHECK(verts && elems && out_k && out_l && npairs, NLFEM_ERR_INVALID_ARG, "NULL argument");
+        *npairs = 0;
+        NLFEM_CHECK(M >= 3 && K >= 1 && capacity >= 0, NLFEM_ERR_INVALID_ARG, "need M >= 3, K >= 1, capacity >= 0");
+        NLFEM_CHECK(K <= NOALLOC_MAX_ELEMS && M <= NOALLOC_MAX_VERTS, NLFEM_ERR_UNSUPPORTED,
+                    "nlfem_pairs_noalloc handles at most 32768 triangles and 65536 vertices (got " +
+                        std::to_string(K) + " triangles, " + std::to_string(M) +
+                        " vertices); use nlfem_mesh_create and nlfem_assemble for larger meshes");
+        NLFEM_CHECK(delta > 0 && std::isfinite(delta), NLFEM_ERR_INVALID_ARG, "delta must be > 0");
+        NLFEM_CHECK(ball == NLFEM_BALL_NOCAPS || ball == NLFEM_BALL_APPROXCAPS, NLFEM_ERR_INVALID_ARG,
+                    "unknown ball approximation");
+        NLFEM_CHECK(quad_outer == 7 || quad_outer == 16, NLFEM_ERR_INVALID_ARG, "quad_outer must be 7 or 16");
+        const void* devp[4] = {verts, elems, out_k, out_l};
+        for (const void* q : devp) {
+            cudaPointerAttributes at;
+            cudaError_t e = cudaPointerGetAttributes(&at, q);
+            if (e != cudaSuccess) (void)cudaGetLastError();
+            NLFEM_CHECK(e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged),
+                        NLFEM_ERR_INVALID_ARG, "verts, elems, out_k and out_l must be device memory");
+        }
+        cudaStream_t st = (cudaStream_t)stream;
+        unsigned char* base = noalloc_scratch();
+        double2* X = (double2*)(base + NA_X);
+        int4* T = (int4*)(base + NA_T);
+        double2* cen = (double2*)(base + NA_CEN);
+        double* rad = (double*)(base + NA_RAD);
+        float4* E32 = (float4*)(base + NA_E32);
+        int* cell_of = (int*)(base + NA_CELLOF);
+        int* clist = (int*)(base + NA_CLIST);
+        int64_t* cnt = (int64_t*)(base + NA_CNT);
+        int64_t* ptr = (int64_t*)(base + NA_PTR);
+        int64_t* ccnt = (int64_t*)(base + NA_CCNT);
+        int64_t* cstart = (int64_t*)(base + NA_CSTART);
+        int* ccur = (int*)(base + NA_CCUR);
+        unsigned char* misc = base + NA_MISC;
+
+        k_na_init<<<1, 1, 0, st>>>(misc);
+        k_na_verts<<<nblk(M, 256), 256, 0, st>>>(verts, M, X, misc);
+        NLFEM_LAUNCH_CHECK();
+        k_na_elems<<<nblk(K, 256), 256, 0, st>>>(elems, K, M, X, T, cen, rad, E32, misc);
+        NLFEM_LAUNCH_CHECK();
+        int hfl[2];
+        double hs[5];
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(hfl, misc, sizeof hfl, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(hs, misc + 16, sizeof hs, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        NLFEM_CHECK(!(hfl[0] & 1), NLFEM_ERR_BAD_MESH, "triangle vertex index out of range");
+        NLFEM_CHECK(!(hfl[0] & 2), NLFEM_ERR_BAD_MESH, "triangle with zero area");
+
+        // grid over the element centroids, at most NOALLOC_MAX_CELLS cells
+        Grid g;
+        g.cs = (delta + 2.0 * hs[0]) * (1.0 + 1e-9) + 1e-300;
+        const double W = hs[3] - hs[1], H = hs[4] - hs[2];
+        g.nx = std::max(1, (int)std::ceil(W / g.cs));
+        g.ny = std::max(1, (int)std::ceil(H / g.cs));
+        while ((int64_t)g.nx * g.ny > NOALLOC_MAX_CELLS) {
+            g.cs *= 2.0;
+            g.nx = std::max(1, (int)std::ceil(W / g.cs));
+            g.ny = std::max(1, (int)std::ceil(H / g.cs));
+        }
+        g.x0 = hs[1];
+        g.y0 = hs[2];
+        const int64_t ncell = (int64_t)g.nx * g.ny;
+        NLFEM_CUDA_TRY(cudaMemsetAsync(ccnt, 0, 8 * ncell, st));
+        NLFEM_CUDA_TRY(cudaMemsetAsync(ccur, 0, 4 * ncell, st));
+        k_bin_count<<<nblk(K, 256), 256, 0, st>>>(cen, K, g, ccnt, cell_of);
+        NLFEM_LAUNCH_CHECK();
+        k_na_scan<<<1, 1024, 0, st>>>(ccnt, cstart, ncell);
+        NLFEM_LAUNCH_CHECK();
+        k_bin_fill<<<nblk(K, 256), 256, 0, st>>>(cell_of, K, cstart, ccur, clist);
+        NLFEM_LAUNCH_CHECK();
+
+        SearchArgs a;
+        a.X = X; a.T = T; a.cen = cen; a.rad = rad; a.cell_of = cell_of; a.cell_start = cstart; a.cell_list = clist;
+        a.g = g; a.K = K; a.delta = delta; a.delta2 = delta * delta; a.caps = ball == NLFEM_BALL_APPROXCAPS;
+        a.ro.n = quad_outer;
+        const double(*tab)[4] = quad_outer == 7 ? NLFEM_RULE7 : NLFEM_RULE16;
+        for (int i = 0; i < 16; ++i) {
+            for (int j = 0; j < 3; ++j) a.ro.l[i][j] = i < quad_outer ? tab[i][j] : 0.0;
+            a.ro.w[i] = i < quad_outer ? tab[i][3] : 0.0;
+            a.ol[i][0] = i < quad_outer ? (float)tab[i][1] : 0.f;
+            a.ol[i][1] = i < quad_outer ? (float)tab[i][2] : 0.f;
+        }
+        a.E32 = E32;
+        a.delta32 = (float)delta;
+        a.d2f = (float)delta * (float)delta;
+        k_search<false><<<nblk(K * 32, 128), 128, 0, st>>>(a, cnt, nullptr, nullptr);
+        NLFEM_LAUNCH_CHECK();
+        k_na_scan<<<1, 1024, 0, st>>>(cnt, ptr, K);
+        k_na_maxcnt<<<nblk(K, 256), 256, 0, st>>>(cnt, K, misc);
+        NLFEM_LAUNCH_CHECK();
+        int64_t total = 0;
+        int mx = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&total, ptr + K, sizeof total, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&mx, misc + 4, sizeof mx, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        *npairs = total;
+        NLFEM_CHECK(total <= capacity, NLFEM_ERR_INVALID_ARG,
+                    "out_k / out_l hold " + std::to_string(capacity) + " pairs, the mesh has " +
+                        std::to_string(total) + " (returned in *npairs)");
+        k_search<true><<<nblk(K * 32, 128), 128, 0, st>>>(a, nullptr, ptr, out_l);
+        NLFEM_LAUNCH_CHECK();
+        segmented_sort_i32(out_l, nullptr, ptr, K, mx, st);
+        k_fill_k<<<nblk(K * 32, 256), 256, 0, st>>>(ptr, K, out_k);
+        NLFEM_LAUNCH_CHECK();
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        return NLFEM_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("unexpected exception");
+        return NLFEM_ERR_CUDA;
+    }
+}
