@@ -130,6 +130,9 @@ struct PairCache {
     DBuf<int> pT_id;         // [P] pair ids, sorted per l
     DBuf<int> duffy_ids;     // intersecting pairs (shared vertex), in pair order
     int64_t nduffy = 0;
+    DBuf<int> whole_ids;     // separated pairs with E_l inside the ball of every point of E_k
+    DBuf<int> cut_ids;       // the other separated pairs
+    int64_t nwhole = 0, ncut = 0;
     int64_t counts[4] = {0, 0, 0, 0};  // separated, vertex, edge, identical
     // node-level pattern
     DBuf<int64_t> nrow_ptr;  // [M + 1]

@@ -181,6 +181,31 @@ __global__ void k_flag_duffy(const int8_t* cls, int64_t P, int64_t* flag) {
     if (p < P) flag[p] = cls[p] > 0;
 }
 
+// Separated pairs whose inner element lies in the ball of every point of the outer
+// element: the largest vertex-to-vertex distance is below delta with a relative margin
+// of 1e-6 (far above FP64 rounding), so the canonical clip finds all three vertices
+// inside at every outer point. flag_whole / flag_cut select the two lists.
+__global__ void k_flag_whole(const int* pk, const int* pl, const int8_t* cls, int64_t P, const double2* X,
+                             const int4* T, double delta2, int64_t* flag_whole, int64_t* flag_cut) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    int64_t w = 0, c = 0;
+    if (cls[p] == 0) {
+        const int4 a = T[pk[p]], b = T[pl[p]];
+        const double2 va[3] = {X[a.x], X[a.y], X[a.z]}, vb[3] = {X[b.x], X[b.y], X[b.z]};
+        double mx = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                const double dx = vb[j].x - va[i].x, dy = vb[j].y - va[i].y;
+                mx = fmax(mx, dx * dx + dy * dy);
+            }
+        if (mx <= delta2 * (1.0 - 1e-6)) w = 1;
+        else c = 1;
+    }
+    flag_whole[p] = w;
+    flag_cut[p] = c;
+}
+
 __global__ void k_compact_duffy(const int64_t* flag, const int64_t* pos, int64_t P, int* ids) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < P && flag[p]) ids[pos[p]] = (int)p;
@@ -296,6 +321,31 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     NLFEM_CUDA_TRY(cudaMemcpyAsync(hc, counts.p, sizeof hc, cudaMemcpyDeviceToHost, st));
     NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
     for (int i = 0; i < 4; ++i) pc.counts[i] = (int64_t)hc[i];
+
+    // separated pairs split into wholly-inside pairs and the rest (the bulk kernels' work lists)
+    pc.nwhole = pc.ncut = 0;
+    pc.whole_ids.release();
+    pc.cut_ids.release();
+    if (P) {
+        DBuf<int64_t> fw, fc, pw, pcut;
+        fw.alloc(P, st);
+        fc.alloc(P, st);
+        pw.alloc(P + 1, st);
+        pcut.alloc(P + 1, st);
+        k_flag_whole<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, pc.pcls.p, P, m.X.p, m.T.p, prm.delta2, fw.p,
+                                                   fc.p);
+        NLFEM_LAUNCH_CHECK();
+        exclusive_scan_i64(fw.p, pw.p, P, st);
+        exclusive_scan_i64(fc.p, pcut.p, P, st);
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.nwhole, pw.p + P, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.ncut, pcut.p + P, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        pc.whole_ids.alloc(pc.nwhole, st);
+        pc.cut_ids.alloc(pc.ncut, st);
+        k_compact_duffy<<<nblk(P, 256), 256, 0, st>>>(fw.p, pw.p, P, pc.whole_ids.p);
+        k_compact_duffy<<<nblk(P, 256), 256, 0, st>>>(fc.p, pcut.p, P, pc.cut_ids.p);
+        NLFEM_LAUNCH_CHECK();
+    }
 
     // intersecting pairs (the singular rule, or the canonical truncation kernel, takes them)
     pc.nduffy = 0;

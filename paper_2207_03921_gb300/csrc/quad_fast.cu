@@ -5,17 +5,18 @@
 // (pair, x_p) would dominate the bulk path. Here the geometry runs in FP32 on vectors
 // relative to x_p (the pair offset v0_l - v0_k is formed once in FP64 and rounded once;
 // element edges are stored in FP32), and every decision the canonical FP64 geometry
-// takes — vertex in ball, number of crossings on an edge — is taken in FP32 only when
-// its margin exceeds a bound on the FP32 error. Otherwise the outer point falls back
-// to the canonical FP64 clip (nl_clip). The interaction pattern and the polygon
-// topology therefore equal the FP64 ones; crossing points, cap centres and sub-triangle
-// areas carry FP32 rounding (about 1e-7 relative), well inside the 1e-5 bar.
-// Without near ties no root snaps, no points merge and no cap is skipped, so the
-// canonical tie rules never need to be reproduced in FP32.
+// takes — vertex in ball, number of crossings on an edge, a cap on a chord — is taken in
+// FP32 only when its margin exceeds a bound on the FP32 error (nl_decide32). Otherwise
+// the outer point falls back to the canonical FP64 clip (nl_clip). The interaction
+// pattern and the polygon topology therefore equal the FP64 ones; crossing points, cap
+// centres and sub-triangle areas carry FP32 rounding (about 1e-7 relative).
 //
-// The cut polygon is never stored: its points are emitted in boundary order and fed to
-// a fan triangulation that integrates triangle (P0, P_prev, P) as soon as P arrives.
-// One thread per ordered pair; intersecting pairs go to the canonical kernels.
+// Work layout: one thread per ordered pair. Pairs whose inner element lies in the ball of
+// every outer point (decided at pair-search time) take k_trunc_whole: no geometry, fully
+// uniform. The others take k_trunc_fast: the geometry of a chunk of outer points runs in
+// lockstep across the warp, then a drain loop integrates one fan triangle per lane and
+// iteration, so the inner rule runs with (nearly) the whole warp and exists once in the
+// code.
 #include <algorithm>
 
 #include "nlfem_internal.cuh"
@@ -28,7 +29,8 @@ struct FastArgs {
     const int* pk;
     const int* pl;
     const int8_t* pcls;
-    int64_t npairs;
+    const int* ids;   // the pairs to process
+    int64_t npairs;   // number of ids
     const double2* X;
     const int4* T;
     const float4* E32;
@@ -40,17 +42,16 @@ struct FastArgs {
     int caps;
 };
 
-// accumulators of the inner sums for one x_p
 template <int NC>
 struct Inner {
     float g[NC], h[3][NC], m[6][NC];
 };
 
-template <int KER, int NQI>
-__device__ __forceinline__ void tri_quad(const FastArgs& A, Inner<(KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1>& I,
-                                         float ax, float ay, float a1, float a2, float bx, float by, float b1,
-                                         float b2, float cx, float cy, float c1, float c2) {
-    constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
+// the inner rule on triangle (a, b, c): positions relative to x_p, barycentric (b1, b2) w.r.t. E_l
+template <int KER, int NQI, int NC>
+__device__ __forceinline__ void tri_quad(const FastArgs& A, Inner<NC>& I, float ax, float ay, float a1, float a2,
+                                         float bx, float by, float b1, float b2, float cx, float cy, float c1,
+                                         float c2) {
     const float dT = fabsf((bx - ax) * (cy - ay) - (by - ay) * (cx - ax));
     const float a0 = 1.f - a1 - a2, b0 = 1.f - b1 - b2, c0 = 1.f - c1 - c2;
 #pragma unroll
@@ -99,96 +100,118 @@ __device__ __forceinline__ void tri_quad(const FastArgs& A, Inner<(KER == NLFEM_
     }
 }
 
-// fan triangulation state: first point and previous point (position relative to x_p,
-// barycentric coordinates b1, b2 w.r.t. E_l)
-struct Fan {
-    float x0, y0, p1, p2;
-    float xp, yp, q1, q2;
-    int n;
-};
+static constexpr int FAST_THREADS = 128;
 
-template <int KER, int NQI>
-__device__ __forceinline__ void fan_emit(const FastArgs& A, Fan& F, Inner<(KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1>& I,
-                                         float x, float y, float b1, float b2) {
-    if (F.n == 0) {
-        F.x0 = x; F.y0 = y; F.p1 = b1; F.p2 = b2;
-    } else {
-        if (F.n >= 2) tri_quad<KER, NQI>(A, I, F.x0, F.y0, F.p1, F.p2, F.xp, F.yp, F.q1, F.q2, x, y, b1, b2);
+// kk += a_p g P P^T, kl -= a_p P h^T, ll += a_p m for outer point q0 (P = its barycentrics)
+template <int NC>
+__device__ __forceinline__ void outer_update(const FastArgs& A, int q0, float dk, const Inner<NC>& I,
+                                             float (&kk)[6][NC], float (&kl)[9][NC], float (&ll)[6][NC]) {
+    const float ap = A.ow[q0] * dk;
+    const float Pa[3] = {A.ol[q0][0], A.ol[q0][1], A.ol[q0][2]};
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float ag = ap * I.g[c];
+        kk[0][c] += ag * Pa[0] * Pa[0];
+        kk[1][c] += ag * Pa[0] * Pa[1];
+        kk[2][c] += ag * Pa[0] * Pa[2];
+        kk[3][c] += ag * Pa[1] * Pa[1];
+        kk[4][c] += ag * Pa[1] * Pa[2];
+        kk[5][c] += ag * Pa[2] * Pa[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) kl[a * 3 + b][c] -= ap * Pa[a] * I.h[b][c];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) ll[j][c] += ap * I.m[j][c];
     }
-    F.xp = x; F.yp = y; F.q1 = b1; F.q2 = b2;
-    ++F.n;
 }
 
-// raw boundary point with its position tags (edge, parameter, vertex flag)
-struct Raw {
-    float x, y, b1, b2, t;
-    int e, vert;
-};
-
-__device__ __forceinline__ bool joined_r(const Raw& P, const Raw& Q) {
-    if (Q.e == P.e && Q.t > P.t) return true;
-    if (Q.vert && Q.e == (P.e + 1) % 3) return true;
-    return false;
+// union block of a separated pair, [[kk, kl], [kl^T, ll]]: its upper triangle in entry order
+// E(a, b), a <= b over (k0 k1 k2 l0 l1 l2); peridynamics: components xx, xy, yx, yy
+template <int NC, int NE>
+__device__ __forceinline__ void write_block(float* out, const float (&kk)[6][NC], const float (&kl)[9][NC],
+                                            const float (&ll)[6][NC]) {
+    const int kkI[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    int e = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int b = a; b < 6; ++b) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float v;
+                if (b < 3) v = kk[kkI[a][b]][c];
+                else if (a < 3) v = kl[a * 3 + (b - 3)][c];
+                else v = ll[kkI[a - 3][b - 3]][c];
+                if (NC == 1) {
+                    out[e] = v;
+                } else if (c == 0) {
+                    out[e * 4 + 0] = v;
+                } else if (c == 1) {
+                    out[e * 4 + 1] = v;
+                    out[e * 4 + 2] = v;
+                } else {
+                    out[e * 4 + 3] = v;
+                }
+            }
+            ++e;
+        }
 }
 
-struct Walk {
-    Raw first, last;
-    int nraw;
-};
-
-// cap centre between raw points P -> Q: x + delta * (right-hand unit normal of the chord)
-template <int KER, int NQI>
-__device__ __forceinline__ void emit_cap(const FastArgs& A, Fan& F, Inner<(KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1>& I,
-                                         const Raw& P, const Raw& Q, float Xx, float Xy, float W0x, float W0y,
-                                         float4 El, float detE) {
-    const float qx = Q.x - P.x, qy = Q.y - P.y;
-    const float len = sqrtf(qx * qx + qy * qy);
-    if (!(len > 1e-9f * A.delta)) return;
-    const float mx = A.delta * (qy / len), my = A.delta * (-qx / len);
-    // barycentric coordinates of the cap centre: relative to v0_l, through E_l's inverse map
-    const float rx = mx + Xx - W0x, ry = my + Xy - W0y;
-    const float b1 = (rx * El.w - ry * El.z) / detE;
-    const float b2 = (El.x * ry - El.y * rx) / detE;
-    fan_emit<KER, NQI>(A, F, I, mx, my, b1, b2);
-}
-
-template <int KER, int NQI>
-__device__ __forceinline__ void walk_raw(const FastArgs& A, Walk& Wk, Fan& F,
-                                         Inner<(KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1>& I, const Raw& B, float Xx,
-                                         float Xy, float W0x, float W0y, float4 El, float detE) {
-    if (A.caps && Wk.nraw >= 1 && !joined_r(Wk.last, B))
-        emit_cap<KER, NQI>(A, F, I, Wk.last, B, Xx, Xy, W0x, W0y, El, detE);
-    fan_emit<KER, NQI>(A, F, I, B.x, B.y, B.b1, B.b2);
-    if (Wk.nraw == 0) Wk.first = B;
-    Wk.last = B;
-    ++Wk.nraw;
-}
+// Cut pairs: outer points are processed in chunks of CHUNK. Phase A sets up every outer
+// point of the chunk in lockstep across the warp (decisions, polygon positions into
+// shared memory; 4 bits per outer point record the number of points). Phase B drains the
+// fan triangles: each iteration integrates one triangle per lane, walking through the
+// lane's outer points in order, and applies that triangle's inner sums with its outer
+// point's factors. Barycentric coordinates are recomputed from positions with E_l's
+// inverse map.
+static constexpr int CHUNK = 8;
+static constexpr int MAXPTS = 9;
 
 template <int KER, int NQI>
-__global__ void __launch_bounds__(128) k_trunc_fast(FastArgs A, float* __restrict__ contrib) {
+__global__ void __launch_bounds__(FAST_THREADS) k_trunc_fast(FastArgs A, float* __restrict__ contrib) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
     constexpr int NE = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 84 : 21;
+    extern __shared__ float s_pts[];  // [CHUNK][MAXPTS][2][FAST_THREADS]
+    float* my = s_pts + threadIdx.x;
+    auto put = [&](int q, int slot, float x, float y) {
+        if (slot < MAXPTS) {
+            my[((q * MAXPTS + slot) * 2 + 0) * FAST_THREADS] = x;
+            my[((q * MAXPTS + slot) * 2 + 1) * FAST_THREADS] = y;
+        }
+    };
     const Params& P = A.prm;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.npairs;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        if (A.pcls[p] != 0) continue;  // intersecting pairs: canonical kernels
-        const int k = A.pk[p], l = A.pl[p];
-        const int4 tk = A.T[k], tl = A.T[l];
-        const double2 v0k = A.X[tk.x], v0l = A.X[tl.x];
-        const float dx = (float)(v0l.x - v0k.x), dy = (float)(v0l.y - v0k.y);
-        const float4 Ek = A.E32[k], El = A.E32[l];
-        const float dk = A.det32[k];
+    const int nqo = P.ro.n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < A.npairs; p0 += stride) {
+        const int64_t pi = p0 + threadIdx.x;
+        const bool valid = pi < A.npairs;
+        const int64_t p = valid ? (int64_t)A.ids[pi] : 0;
+        int4 tk = make_int4(0, 0, 0, 0), tl = make_int4(0, 0, 0, 0);
+        double2 v0k = make_double2(0, 0), v0l = make_double2(0, 0);
+        float4 Ek = make_float4(0, 0, 0, 0), El = make_float4(1, 0, 0, 1);
+        float dk = 0.f, dx = 0.f, dy = 0.f;
+        if (valid) {
+            const int k = A.pk[p], l = A.pl[p];
+            tk = A.T[k];
+            tl = A.T[l];
+            v0k = A.X[tk.x];
+            v0l = A.X[tl.x];
+            dx = (float)(v0l.x - v0k.x);
+            dy = (float)(v0l.y - v0k.y);
+            Ek = A.E32[k];
+            El = A.E32[l];
+            dk = A.det32[k];
+        }
         const float detE = El.x * El.w - El.y * El.z;
-        // E_l's vertices relative to v0_k
+        const float idet = 1.f / detE;
         const float W0x = dx, W0y = dy;
         const float W1x = dx + El.x, W1y = dy + El.y, W2x = dx + El.z, W2y = dy + El.w;
-        // eps bounds the absolute FP32 error of every vertex-relative coordinate R = W - X:
-        // each is a short chain (one rounding of v0_l - v0_k, edge vectors rounded once, two
-        // FMAs for x_p, one subtraction) of magnitudes <= span; 8 units of 2^-24 each, times 4
         const float span = fabsf(dx) + fabsf(dy) + fabsf(Ek.x) + fabsf(Ek.y) + fabsf(Ek.z) + fabsf(Ek.w) +
                            fabsf(El.x) + fabsf(El.y) + fabsf(El.z) + fabsf(El.w);
-        const float eps = 4.8e-7f * span;
-        const float floor2 = 1e-5f * A.d2;  // floor of the vertex margin (see nl_decide32)
+        const float eps = 4.8e-7f * span;    // bound on the FP32 error of the relative coordinates
+        const float floor2 = 1e-5f * A.d2;   // floor of the vertex margin (see nl_decide32)
+
         float kk[6][NC], kl[9][NC], ll[6][NC];
 #pragma unroll
         for (int i = 0; i < 6; ++i)
@@ -199,14 +222,156 @@ __global__ void __launch_bounds__(128) k_trunc_fast(FastArgs A, float* __restric
 #pragma unroll
             for (int c = 0; c < NC; ++c) kl[i][c] = 0.f;
 
-        for (int q0 = 0; q0 < P.ro.n; ++q0) {
-            const float l1o = A.ol[q0][1], l2o = A.ol[q0][2];
-            const float Xx = l1o * Ek.x + l2o * Ek.z, Xy = l1o * Ek.y + l2o * Ek.w;  // x_p - v0_k
-            const float R0x = W0x - Xx, R0y = W0y - Xy, R1x = W1x - Xx, R1y = W1y - Xy;
-            const float R2x = W2x - Xx, R2y = W2y - Xy;
-            const float c0 = R0x * R0x + R0y * R0y - A.d2;
-            const float c1 = R1x * R1x + R1y * R1y - A.d2;
-            const float c2 = R2x * R2x + R2y * R2y - A.d2;
+#pragma unroll 1
+        for (int qb = 0; qb < nqo; qb += CHUNK) {
+            const int qn = min(CHUNK, nqo - qb);
+            // ---- phase A: polygons of outer points qb .. qb + qn - 1, in lockstep
+            unsigned long long counts = 0;  // 4 bits per outer point: number of polygon points
+#pragma unroll 1
+            for (int q = 0; q < qn; ++q) {
+                const int q0 = qb + q;
+                const float l1o = A.ol[q0][1], l2o = A.ol[q0][2];
+                const float Xx = l1o * Ek.x + l2o * Ek.z;  // x_p - v0_k
+                const float Xy = l1o * Ek.y + l2o * Ek.w;
+                const float Rx[3] = {W0x - Xx, W1x - Xx, W2x - Xx}, Ry[3] = {W0y - Xy, W1y - Xy, W2y - Xy};
+                float Cc[3];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - A.d2;
+                int n = 0;
+                if (valid) {
+                    Geo32 G;
+                    n = -1;
+                    if (nl_decide32(Rx, Ry, Cc, eps, floor2, A.d2, G)) {
+                        if (G.in[0] && G.in[1] && G.in[2]) {
+#pragma unroll
+                            for (int m = 0; m < 3; ++m) put(q, m, Rx[m], Ry[m]);
+                            n = 3;
+                        } else {
+                            // decided polygon: vertices inside, crossings, caps
+                            int nraw = 0, fe = 0, fv = 0, le = 0;
+                            float fx = 0, fy = 0, lx = 0, ly = 0;
+                            bool bad = false;
+                            n = 0;
+                            auto cap = [&](float px, float py, float qx, float qy) {
+                                const float cx = qx - px, cy = qy - py;
+                                const float len = sqrtf(cx * cx + cy * cy);
+                                if (!(len > 1e-6f * A.delta)) {
+                                    bad = true;
+                                    return;
+                                }
+                                put(q, n++, A.delta * (cy / len), A.delta * (-cx / len));
+                            };
+                            auto raw = [&](float x, float y, int e, int v) {
+                                if (A.caps && nraw >= 1 && !((e == le) || (v && e == (le + 1) % 3)))
+                                    cap(lx, ly, x, y);
+                                put(q, n++, x, y);
+                                if (nraw == 0) { fx = x; fy = y; fe = e; fv = v; }
+                                lx = x; ly = y; le = e;
+                                ++nraw;
+                            };
+#pragma unroll
+                            for (int e = 0; e < 3; ++e) {
+                                const int b = (e + 1) % 3;
+                                if (G.in[e]) raw(Rx[e], Ry[e], e, 1);
+                                if (G.nc[e] >= 1)
+                                    raw(Rx[e] + G.ta[e] * (Rx[b] - Rx[e]), Ry[e] + G.ta[e] * (Ry[b] - Ry[e]), e, 0);
+                                if (G.nc[e] >= 2)
+                                    raw(Rx[e] + G.tb[e] * (Rx[b] - Rx[e]), Ry[e] + G.tb[e] * (Ry[b] - Ry[e]), e, 0);
+                            }
+                            if (A.caps && nraw >= 2 && !(fv && fe == (le + 1) % 3)) cap(lx, ly, fx, fy);
+                            if (bad) n = -1;
+                        }
+                    }
+                    if (n < 0) {
+                        // canonical FP64 geometry for this outer point (near ties)
+                        const double2 Vk[3] = {v0k, A.X[tk.y], A.X[tk.z]};
+                        const double2 Vl[3] = {v0l, A.X[tl.y], A.X[tl.z]};
+                        const double2 xp = nl_map(Vk, P.ro.l[q0][0], P.ro.l[q0][1], P.ro.l[q0][2]);
+                        CPt poly[NLFEM_MAXPOLY];
+                        bool full;
+                        n = nl_clip(Vl, xp, P.delta, P.delta2, A.caps != 0, poly, full);
+                        if (full) {
+                            for (int m = 0; m < 3; ++m) put(q, m, (float)(Vl[m].x - xp.x), (float)(Vl[m].y - xp.y));
+                        } else {
+                            n = min(n, MAXPTS);
+                            for (int m = 0; m < n; ++m) put(q, m, (float)(poly[m].x - xp.x), (float)(poly[m].y - xp.y));
+                        }
+                    }
+                    n = min(n, MAXPTS);
+                }
+                counts |= (unsigned long long)(n < 3 ? 0 : n) << (4 * q);
+            }
+            // ---- phase B: one fan triangle per lane and iteration
+            int qc = 0, sc = 2;
+            while (qc < qn && ((counts >> (4 * qc)) & 15) == 0) ++qc;
+            while (__any_sync(0xffffffffu, qc < qn)) {
+                if (qc < qn) {
+                    const int q0 = qb + qc;
+                    const float l1o = A.ol[q0][1], l2o = A.ol[q0][2];
+                    // x_p - v0_l, for the barycentric coordinates of the points
+                    const float Bx = l1o * Ek.x + l2o * Ek.z - W0x, By = l1o * Ek.y + l2o * Ek.w - W0y;
+                    float px[3], py[3], b1[3], b2[3];
+                    const int slot[3] = {0, sc - 1, sc};
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        px[t] = my[((qc * MAXPTS + slot[t]) * 2 + 0) * FAST_THREADS];
+                        py[t] = my[((qc * MAXPTS + slot[t]) * 2 + 1) * FAST_THREADS];
+                        const float rx = px[t] + Bx, ry = py[t] + By;
+                        b1[t] = (rx * El.w - ry * El.z) * idet;
+                        b2[t] = (El.x * ry - El.y * rx) * idet;
+                    }
+                    Inner<NC> I;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        I.g[c] = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) I.h[j][c] = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) I.m[j][c] = 0.f;
+                    }
+                    tri_quad<KER, NQI, NC>(A, I, px[0], py[0], b1[0], b2[0], px[1], py[1], b1[1], b2[1], px[2], py[2],
+                                           b1[2], b2[2]);
+                    outer_update<NC>(A, q0, dk, I, kk, kl, ll);
+                    if (++sc >= (int)((counts >> (4 * qc)) & 15)) {
+                        sc = 2;
+                        ++qc;
+                        while (qc < qn && ((counts >> (4 * qc)) & 15) == 0) ++qc;
+                    }
+                }
+            }
+        }
+        if (valid) write_block<NC, NE>(contrib + p * NE, kk, kl, ll);
+    }
+}
+
+// Separated pairs with E_l inside the ball of every point of E_k: the whole inner element
+// at every outer point, no geometry at all.
+template <int KER, int NQI>
+__global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(FastArgs A, float* __restrict__ contrib) {
+    constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
+    constexpr int NE = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 84 : 21;
+    const int nqo = A.prm.ro.n;
+    for (int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pi < A.npairs;
+         pi += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = A.ids[pi];
+        const int k = A.pk[p], l = A.pl[p];
+        const int4 tk = A.T[k], tl = A.T[l];
+        const double2 v0k = A.X[tk.x], v0l = A.X[tl.x];
+        const float dx = (float)(v0l.x - v0k.x), dy = (float)(v0l.y - v0k.y);
+        const float4 Ek = A.E32[k], El = A.E32[l];
+        const float dk = A.det32[k];
+        float kk[6][NC], kl[9][NC], ll[6][NC];
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) kk[i][c] = ll[i][c] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) kl[i][c] = 0.f;
+        for (int q0 = 0; q0 < nqo; ++q0) {
+            const float Xx = A.ol[q0][1] * Ek.x + A.ol[q0][2] * Ek.z;
+            const float Xy = A.ol[q0][1] * Ek.y + A.ol[q0][2] * Ek.w;
             Inner<NC> I;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -216,121 +381,17 @@ __global__ void __launch_bounds__(128) k_trunc_fast(FastArgs A, float* __restric
 #pragma unroll
                 for (int j = 0; j < 6; ++j) I.m[j][c] = 0.f;
             }
-            bool any = false;
-            const float Rx[3] = {R0x, R1x, R2x}, Ry[3] = {R0y, R1y, R2y}, Cc[3] = {c0, c1, c2};
-            Geo32 G;
-            bool tie = !nl_decide32(Rx, Ry, Cc, eps, floor2, A.d2, G);
-            if (!tie && G.in[0] && G.in[1] && G.in[2]) {
-                tri_quad<KER, NQI>(A, I, R0x, R0y, 0.f, 0.f, R1x, R1y, 1.f, 0.f, R2x, R2y, 0.f, 1.f);
-                any = true;
-            } else if (!tie) {
-                const bool* in = G.in;
-                const int* nc = G.nc;
-                const float* ta = G.ta;
-                const float* tb = G.tb;
-                {
-                    Fan F;
-                    F.n = 0;
-                    Walk Wk;
-                    Wk.nraw = 0;
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const int b = (e + 1) % 3;
-                        const float e1 = (e == 1) ? 1.f : 0.f, e2 = (e == 2) ? 1.f : 0.f;
-                        const float f1 = (b == 1) ? 1.f : 0.f, f2 = (b == 2) ? 1.f : 0.f;
-                        if (in[e]) {
-                            Raw V{Rx[e], Ry[e], e1, e2, 0.f, e, 1};
-                            walk_raw<KER, NQI>(A, Wk, F, I, V, Xx, Xy, W0x, W0y, El, detE);
-                        }
-                        for (int j = 0; j < nc[e]; ++j) {
-                            const float t = j == 0 ? ta[e] : tb[e];
-                            const float ux = Rx[b] - Rx[e], uy = Ry[b] - Ry[e];
-                            Raw Cp{Rx[e] + t * ux, Ry[e] + t * uy, e1 + t * (f1 - e1), e2 + t * (f2 - e2), t, e, 0};
-                            walk_raw<KER, NQI>(A, Wk, F, I, Cp, Xx, Xy, W0x, W0y, El, detE);
-                        }
-                    }
-                    if (A.caps && Wk.nraw >= 2 && !joined_r(Wk.last, Wk.first))
-                        emit_cap<KER, NQI>(A, F, I, Wk.last, Wk.first, Xx, Xy, W0x, W0y, El, detE);
-                    any = F.n >= 3;
-                }
-            }
-            if (tie) {
-                // canonical FP64 geometry for this outer point
-                const double2 Vk[3] = {v0k, A.X[tk.y], A.X[tk.z]};
-                const double2 Vl[3] = {v0l, A.X[tl.y], A.X[tl.z]};
-                const double2 xp = nl_map(Vk, P.ro.l[q0][0], P.ro.l[q0][1], P.ro.l[q0][2]);
-                CPt poly[NLFEM_MAXPOLY];
-                bool full;
-                const int np = nl_clip(Vl, xp, P.delta, P.delta2, A.caps != 0, poly, full);
-                if (np >= 3) {
-                    any = true;
-                    if (full) {
-                        tri_quad<KER, NQI>(A, I, (float)(Vl[0].x - xp.x), (float)(Vl[0].y - xp.y), 0.f, 0.f,
-                                           (float)(Vl[1].x - xp.x), (float)(Vl[1].y - xp.y), 1.f, 0.f,
-                                           (float)(Vl[2].x - xp.x), (float)(Vl[2].y - xp.y), 0.f, 1.f);
-                    } else {
-                        Fan F;
-                        F.n = 0;
-                        for (int i = 0; i < np; ++i)
-                            fan_emit<KER, NQI>(A, F, I, (float)(poly[i].x - xp.x), (float)(poly[i].y - xp.y),
-                                               (float)poly[i].b1, (float)poly[i].b2);
-                    }
-                }
-            }
-            if (!any) continue;
-            const float ap = A.ow[q0] * dk;
-            const float Pa[3] = {A.ol[q0][0], l1o, l2o};
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const float ag = ap * I.g[c];
-                kk[0][c] += ag * Pa[0] * Pa[0];
-                kk[1][c] += ag * Pa[0] * Pa[1];
-                kk[2][c] += ag * Pa[0] * Pa[2];
-                kk[3][c] += ag * Pa[1] * Pa[1];
-                kk[4][c] += ag * Pa[1] * Pa[2];
-                kk[5][c] += ag * Pa[2] * Pa[2];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) kl[a * 3 + b][c] -= ap * Pa[a] * I.h[b][c];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) ll[j][c] += ap * I.m[j][c];
-            }
+            tri_quad<KER, NQI, NC>(A, I, dx - Xx, dy - Xy, 0.f, 0.f, dx + El.x - Xx, dy + El.y - Xy, 1.f, 0.f,
+                                   dx + El.z - Xx, dy + El.w - Xy, 0.f, 1.f);
+            outer_update<NC>(A, q0, dk, I, kk, kl, ll);
         }
-        // union block of a separated pair: [[kk, kl], [kl^T, ll]]; write its upper triangle
-        float* out = contrib + p * NE;
-        // entry order E(a,b), a <= b over the union (k0 k1 k2 l0 l1 l2)
-        const int kkI[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-        int e = 0;
-#pragma unroll
-        for (int a = 0; a < 6; ++a)
-#pragma unroll
-            for (int b = a; b < 6; ++b) {
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    float v;
-                    if (b < 3) v = kk[kkI[a][b]][c];
-                    else if (a < 3) v = kl[a * 3 + (b - 3)][c];
-                    else v = ll[kkI[a - 3][b - 3]][c];
-                    if (NC == 1) {
-                        out[e] = v;
-                    } else if (c == 0) {
-                        out[e * 4 + 0] = v;
-                    } else if (c == 1) {
-                        out[e * 4 + 1] = v;
-                        out[e * 4 + 2] = v;
-                    } else {
-                        out[e * 4 + 3] = v;
-                    }
-                }
-                ++e;
-            }
+        write_block<NC, NE>(contrib + p * NE, kk, kl, ll);
     }
 }
 
 void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st) {
     FastArgs a;
-    a.pk = pc.pk.p; a.pl = pc.pl.p; a.pcls = pc.pcls.p; a.npairs = pc.npairs;
+    a.pk = pc.pk.p; a.pl = pc.pl.p; a.pcls = pc.pcls.p;
     a.X = m.X.p; a.T = m.T.p; a.E32 = m.E32.p; a.det32 = m.det32.p;
     a.prm = prm;
     for (int i = 0; i < 16; ++i) {
@@ -346,18 +407,33 @@ void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib
     a.c = (float)prm.c;
     a.s = (float)prm.s;
     a.caps = prm.ball == NLFEM_BALL_APPROXCAPS;
-    unsigned grid = (unsigned)std::min<int64_t>(nblk(pc.npairs, 128), 152 * 64);
-    if (!grid) return;
-#define NLFEM_TF(KK, NQ) k_trunc_fast<KK, NQ><<<grid, 128, 0, st>>>(a, contrib)
-    if (prm.kernel == NLFEM_KERNEL_CONSTANT) {
-        if (prm.ri.n == 7) NLFEM_TF(NLFEM_KERNEL_CONSTANT, 7); else NLFEM_TF(NLFEM_KERNEL_CONSTANT, 16);
-    } else if (prm.kernel == NLFEM_KERNEL_FRACTIONAL) {
-        if (prm.ri.n == 7) NLFEM_TF(NLFEM_KERNEL_FRACTIONAL, 7); else NLFEM_TF(NLFEM_KERNEL_FRACTIONAL, 16);
-    } else {
-        if (prm.ri.n == 7) NLFEM_TF(NLFEM_KERNEL_PERIDYNAMIC, 7); else NLFEM_TF(NLFEM_KERNEL_PERIDYNAMIC, 16);
-    }
+    const size_t FAST_SMEM = sizeof(float) * CHUNK * MAXPTS * 2 * FAST_THREADS;
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_CONSTANT, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_CONSTANT, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_FRACTIONAL, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_FRACTIONAL, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_PERIDYNAMIC, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_PERIDYNAMIC, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
+    for (int pass = 0; pass < 2; ++pass) {
+        a.ids = pass == 0 ? pc.whole_ids.p : pc.cut_ids.p;
+        a.npairs = pass == 0 ? pc.nwhole : pc.ncut;
+        unsigned grid = (unsigned)std::min<int64_t>(nblk(a.npairs, FAST_THREADS), 152 * 64);
+        if (!grid) continue;
+#define NLFEM_TF(KK, NQ)                                                                  \
+    do {                                                                                  \
+        if (pass == 0) k_trunc_whole<KK, NQ><<<grid, FAST_THREADS, 0, st>>>(a, contrib);  \
+        else k_trunc_fast<KK, NQ><<<grid, FAST_THREADS, FAST_SMEM, st>>>(a, contrib);     \
+    } while (0)
+        if (prm.kernel == NLFEM_KERNEL_CONSTANT) {
+            if (prm.ri.n == 7) NLFEM_TF(NLFEM_KERNEL_CONSTANT, 7); else NLFEM_TF(NLFEM_KERNEL_CONSTANT, 16);
+        } else if (prm.kernel == NLFEM_KERNEL_FRACTIONAL) {
+            if (prm.ri.n == 7) NLFEM_TF(NLFEM_KERNEL_FRACTIONAL, 7); else NLFEM_TF(NLFEM_KERNEL_FRACTIONAL, 16);
+        } else {
+            if (prm.ri.n == 7) NLFEM_TF(NLFEM_KERNEL_PERIDYNAMIC, 7); else NLFEM_TF(NLFEM_KERNEL_PERIDYNAMIC, 16);
+        }
 #undef NLFEM_TF
-    NLFEM_LAUNCH_CHECK();
+        NLFEM_LAUNCH_CHECK();
+    }
 }
 
 }  // namespace nlfem
