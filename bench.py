@@ -53,12 +53,13 @@ WORKLOADS = {
                  desc="structured h=0.05 on [-0.1,1.1]^2 (1152 triangles), constant kernel, delta=0.1"),
 }
 
-# algorithmic FLOPs of the truncation quadrature (fixed model)
+# algorithmic work model of the assembly kernels (fixed before measurement)
 FLOPS_PER_EVAL = {"constant": 57, "fractional": 60, "peridynamic": 3 * 55 + 9}
-FLOPS_PER_OUTER = 58
-FP64_FLOPS_PER_OUTER = 25       # x_p (10) and three vertex-in-ball tests (15)
-FP64_FLOPS_PER_CUT = 80         # edge quadratics, roots, crossing points, cap centres
-FP64_FLOPS_PER_DUFFY_POINT = 60
+FLOPS_PER_OUTER = 58            # kk/kl/ll updates of an outer point with a nonempty polygon
+GEOM_FLOPS_PER_OUTER = 25       # x_p (10) and three vertex-in-ball tests (15)
+GEOM_FLOPS_PER_CUT = 80         # edge quadratics, roots, crossing points, cap centres
+GEOM_FLOPS_PER_SUBTRI = 10      # fan triangle edge vectors and area
+CONTRIB_ENTRIES = {1: 21, 2: 84}
 
 
 def make_mesh(name):
@@ -344,29 +345,49 @@ def main():
     e2e_ms, _ = time_steps(e2e_step, e2e_steps, 1, ws, stream)
     e2e_value = npairs * ws / (e2e_ms / e2e_steps * 1e-3)
 
-    # roofline of the dominant kernel (the truncation quadrature, k_trunc)
+    # roofline of the dominant kernel: the longest of the whole-pair and cut-pair quadrature
+    # kernels (FP32 ALU) and the reduction (HBM)
     pk = peaks()
     clk_sum = clk.summary()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s from unit counts and the max clock
-    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
-    evals, outer = census["evals"], census["full_points"] + census["cut_points"]
-    fp32_flops = evals * FLOPS_PER_EVAL[wl["kernel"]] + outer * FLOPS_PER_OUTER
-    fp64_flops = census["outer_points"] * FP64_FLOPS_PER_OUTER + census["cut_points"] * FP64_FLOPS_PER_CUT
-    a32 = fp32_flops / (quad_ms * 1e-3) / 1e12
-    a64 = fp64_flops / (quad_ms * 1e-3) / 1e12
-    if a64 / fp64_peak >= a32 / fp32_peak:
-        roof = {"bound": "alu", "pipe": "fp64", "achieved": a64, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": a64 / fp64_peak}
-    else:
-        roof = {"bound": "alu", "pipe": "fp32", "achieved": a32, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": a32 / fp32_peak}
-    roof["kernel"] = "k_trunc"
-    roof["peak_source"] = "derived: 152 SMs x (128 FP32 | 2 FP64) FMA lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)"
-    roof["other_pipe"] = {"fp32_tflops": a32, "fp32_frac": a32 / fp32_peak, "fp64_tflops": a64,
-                          "fp64_frac": a64 / fp64_peak}
-    roof["traffic"] = traffic_from_profiles("k_trunc", args.workload)
-    roof["ms_per_launch"] = quad_ms
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    fpe = FLOPS_PER_EVAL[wl["kernel"]]
+    nqi = wl["quad_inner"]
+    ms_whole = statistics.mean(i["ms_whole"] for i in timed)
+    ms_cut = statistics.mean(i["ms_cut"] for i in timed)
+    ms_close = statistics.mean(i["ms_close"] for i in timed)
+    ev_whole, ev_close = census["evals_whole"], census["evals_close"]
+    ev_cut = census["evals"] - ev_whole - ev_close
+    flops_whole = ev_whole * fpe + (ev_whole // nqi) * FLOPS_PER_OUTER
+    nonempty_cut = census["full_points"] + census["cut_points"] - ev_whole // nqi
+    flops_cut = (ev_cut * fpe + nonempty_cut * FLOPS_PER_OUTER + census["outer_points_cut"] * GEOM_FLOPS_PER_OUTER
+                 + census["cut_points"] * GEOM_FLOPS_PER_CUT + census["subtris"] * GEOM_FLOPS_PER_SUBTRI)
+    ne = CONTRIB_ENTRIES[ndof]
+    red_bytes = (info0["n_contrib"] * (4 + 4)                 # slot index + FP32 contribution
+                 + info0["n_upper"] * (8 + 4 + 4 + 16 + 8 + 8 + 8)  # up_pos, up_row, ncol, seg_ptr, pbase, nptr, row_ptr
+                 + info0["nnz"] * (8 + 8))                    # tpos read, value written
+    kernels = {
+        "k_trunc_whole": {"bound": "alu", "ms": ms_whole, "units": info0["pairs_whole"],
+                          "achieved": flops_whole / (ms_whole * 1e-3) / 1e12 if ms_whole else 0.0,
+                          "peak": fp32_peak, "unit": "TFLOP/s"},
+        "k_trunc_fast": {"bound": "alu", "ms": ms_cut,
+                         "units": info0["pairs_separated"] - info0["pairs_whole"],
+                         "achieved": flops_cut / (ms_cut * 1e-3) / 1e12 if ms_cut else 0.0,
+                         "peak": fp32_peak, "unit": "TFLOP/s"},
+        "k_reduce": {"bound": "hbm", "ms": red_ms, "units": info0["n_upper"],
+                     "achieved": red_bytes / (red_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s"},
+    }
+    for k in kernels.values():
+        k["frac"] = k["achieved"] / k["peak"]
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    d = kernels[dom]
+    roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+            "frac": d["frac"], "traffic": traffic_from_profiles(dom, args.workload), "kernel": dom,
+            "ms_per_launch": d["ms"],
+            "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock" if d["bound"] == "alu"
+                            else "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in pk else "fallback 6.8 TB/s"),
+            "kernels": kernels, "ms_close_pairs": ms_close}
 
     line = {
         "metric": "element-pair assemblies/s", "value": value, "unit": "pairs/s", "n_gpus": ws,
@@ -380,13 +401,15 @@ def main():
         "roofline": roof,
         "fp64_plain": {"value": npairs * ws / (ms64_step * 1e-3), "ms_per_step": ms64_step,
                        "quadrature_ms": quad64_ms, "speedup_fp32_bulk_over_fp64": ms64_step / ms_step},
-        "breakdown_ms": {"quadrature": quad_ms, "reduce": red_ms, "cold_total": cold_ms,
+        "breakdown_ms": {"quadrature": quad_ms, "whole_pairs": ms_whole, "cut_pairs": ms_cut,
+                         "intersecting_pairs": ms_close, "reduce": red_ms, "cold_total": cold_ms,
                          "pairs_search": info0["ms_pairs"], "pattern_and_index": info0["ms_pattern"]},
         "cold": {"value": npairs / (cold_ms * 1e-3), "ms": cold_ms},
         "census": census,
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "pinned host mesh -> nlfem_mesh_create -> nlfem_assemble (cold) -> CSR values and F to host"},
-        "gpu_launches": args.steps * (2 + (1 if census["singular_pairs"] else 0) + 1),
+        # per step: whole-pair and cut-pair quadrature, intersecting pairs, reduction, load vector
+        "gpu_launches": args.steps * (2 + (1 if census["singular_pairs"] or census["evals_close"] else 0) + 2),
         "clocks": clk_sum,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -44,7 +44,9 @@ class nlfem_assembly_info(C.Structure):
     _fields_ = [("npairs", C.c_int64), ("pairs_identical", C.c_int64), ("pairs_edge", C.c_int64),
                 ("pairs_vertex", C.c_int64), ("pairs_separated", C.c_int64), ("nnz", C.c_int64),
                 ("device_bytes", C.c_int64), ("ms_pairs", C.c_double), ("ms_pattern", C.c_double),
-                ("ms_quadrature", C.c_double), ("ms_reduce", C.c_double), ("cached", C.c_int)]
+                ("ms_quadrature", C.c_double), ("ms_reduce", C.c_double), ("cached", C.c_int),
+                ("ms_whole", C.c_double), ("ms_cut", C.c_double), ("ms_close", C.c_double),
+                ("pairs_whole", C.c_int64), ("n_upper", C.c_int64), ("n_contrib", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -194,11 +196,11 @@ def nlfem_solve(sys, g_nodal, tol_rel, max_iter, u_out, stream=None) -> dict:
 
 
 CENSUS = ["evals", "full_points", "cut_points", "subtris", "duffy_points", "trunc_pairs", "singular_pairs",
-          "empty_points", "outer_points"]
+          "empty_points", "outer_points", "evals_whole", "evals_close", "outer_points_cut"]
 
 
 def nlfem_system_census(sys, stream=None) -> dict:
-    c = (C.c_int64 * 9)()
+    c = (C.c_int64 * 12)()
     _check(load().nlfem_system_census(sys, c, _stream(stream)))
     return dict(zip(CENSUS, (int(v) for v in c)))
 

@@ -234,12 +234,12 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
     Mesh& m = mesh->m;
     cudaStream_t st = (cudaStream_t)stream;
     Params P = make_params(*params, m.ndof);
-    cudaEvent_t ev[6];
-    for (int i = 0; i < 6; ++i) NLFEM_CUDA_TRY(cudaEventCreate(&ev[i]));
+    cudaEvent_t ev[10];  // [0..5] phases, [6..9] the quadrature kernels
+    for (int i = 0; i < 10; ++i) NLFEM_CUDA_TRY(cudaEventCreate(&ev[i]));
     struct EvGuard {
         cudaEvent_t* e;
         ~EvGuard() {
-            for (int i = 0; i < 6; ++i) cudaEventDestroy(e[i]);
+            for (int i = 0; i < 10; ++i) cudaEventDestroy(e[i]);
         }
     } guard{ev};
     std::shared_ptr<PairCache> pc = m.cache;
@@ -296,7 +296,7 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
             }
         }
         NLFEM_CUDA_TRY(cudaEventRecord(ev[3], st));
-        run_quadrature(m, *pc, P, S, st);
+        run_quadrature(m, *pc, P, S, st, ev + 6);
         NLFEM_CUDA_TRY(cudaEventRecord(ev[4], st));
         run_reduction(m, *pc, P, S, st);
         NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
@@ -317,6 +317,12 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
         I.ms_pairs = t_pairs;
         I.ms_pattern = t_pattern;
         I.ms_quadrature = elapsed_ms(ev[3], ev[4]);
+        I.ms_whole = elapsed_ms(ev[6], ev[7]);
+        I.ms_cut = elapsed_ms(ev[7], ev[8]);
+        I.ms_close = elapsed_ms(ev[8], ev[9]);
+        I.pairs_whole = pc->nwhole;
+        I.n_upper = pc->n_upper;
+        I.n_contrib = pc->ncontrib;
         I.ms_reduce = elapsed_ms(ev[4], ev[5]);
         I.cached = cached ? 1 : 0;
     } catch (...) {
@@ -387,7 +393,7 @@ int nlfem_solve(nlfem_system_t sys, const double* g_nodal, double tol_rel, int m
     NLFEM_API_END
 }
 
-int nlfem_system_census(nlfem_system_t sys, int64_t counts[9], void* stream) {
+int nlfem_system_census(nlfem_system_t sys, int64_t counts[12], void* stream) {
     NLFEM_API_BEGIN
     NLFEM_CHECK(sys && counts, NLFEM_ERR_INVALID_ARG, "NULL argument");
     run_census(*sys->s.mesh, *sys->s.pc, sys->s.prm, counts, (cudaStream_t)stream);

@@ -175,12 +175,14 @@ struct System {
 void mesh_prepare(Mesh& m, const int* T3_dev, const int8_t* lab_dev, cudaStream_t st);
 void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st);
 void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st);
-void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st);
+// ev[0..3] are recorded on st around the whole-pair, cut-pair and intersecting-pair kernels
+void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev);
 void run_reduction(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st);
 void run_load(Mesh& m, const Params& prm, const double* f_nodal, System& sys, cudaStream_t st);
 int64_t contrib_entries(int ndof);
 void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStream_t st);
-void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st);
+void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st,
+                       cudaEvent_t* ev);
 int solve_system(System& S, const double* g, double tol, int max_iter, double* u_out, nlfem_solve_info* info,
                  cudaStream_t st);
 

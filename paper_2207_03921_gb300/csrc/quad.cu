@@ -29,6 +29,7 @@ struct QuadArgs {
     const int* pk;
     const int* pl;
     const int8_t* pcls;
+    const int8_t* whole;   // census only: pair is in the whole-pair list
     int64_t npairs;        // number of pairs to process (of ids, if given)
     const int* ids;        // optional list of pair ids
     const double2* X;
@@ -485,17 +486,20 @@ static void launch_trunc(const QuadArgs& a, R* out, cudaStream_t st) {
     NLFEM_LAUNCH_CHECK();
 }
 
-void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st) {
+void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {
     if (prm.precision == NLFEM_PREC_FP32_BULK) {
         // separated pairs: FP32 geometry with exact decisions; intersecting pairs: canonical
-        launch_trunc_fast(m, pc, prm, sys.contrib32.p, st);
+        launch_trunc_fast(m, pc, prm, sys.contrib32.p, st, ev);
         if (!prm.singular && pc.nduffy > 0) {
-            QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, pc.nduffy, pc.duffy_ids.p, m.X.p, m.T.p, m.det.p, prm};
+            QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nduffy, pc.duffy_ids.p, m.X.p, m.T.p, m.det.p, prm};
             launch_trunc<float>(c, sys.contrib32.p, st);
         }
     } else {
-        QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, pc.npairs, nullptr, m.X.p, m.T.p, m.det.p, prm};
+        NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+        NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+        QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.npairs, nullptr, m.X.p, m.T.p, m.det.p, prm};
         launch_trunc<double>(a, sys.contrib64.p, st);
+        NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
     }
     if (prm.singular && pc.nduffy > 0) {
         DuffyArgs d{pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
@@ -503,6 +507,7 @@ void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cuda
             d, prm.precision == NLFEM_PREC_FP32_BULK ? nullptr : sys.contrib64.p, sys.contrib32.p);
         NLFEM_LAUNCH_CHECK();
     }
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[3], st));
 }
 
 void run_load(Mesh& m, const Params& prm, const double* f_nodal, System& sys, cudaStream_t st) {
@@ -535,11 +540,13 @@ __global__ void k_census(QuadArgs A, unsigned long long* cnt) {
     for (int64_t it = 0; it < n_iter; ++it) {
         int64_t p = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         unsigned long long evals = 0, full = 0, cut = 0, sub = 0, empty = 0, tp = 0, sp = 0, outer = 0;
+        int whole = 0, clsv = 0;
         if (p < A.npairs) {
             const int cls = A.pcls[p];
             if (cls > 0 && P.singular) {
                 sp = 1;
             } else {
+                whole = A.whole ? A.whole[p] : 0;
                 tp = 1;
                 const int4 tk = A.T[A.pk[p]], tl = A.T[A.pl[p]];
                 const double2 Vk[3] = {A.X[tk.x], A.X[tk.y], A.X[tk.z]};
@@ -553,8 +560,12 @@ __global__ void k_census(QuadArgs A, unsigned long long* cnt) {
                     if (f) { ++full; evals += P.ri.n; }
                     else { ++cut; sub += np - 2; evals += (unsigned long long)(np - 2) * P.ri.n; }
                 }
+                clsv = cls;
             }
         }
+        warp_add(&cnt[9], whole ? evals : 0ull);
+        warp_add(&cnt[10], (!whole && clsv > 0) ? evals : 0ull);
+        warp_add(&cnt[11], (!whole && clsv == 0 && tp) ? outer : 0ull);
         warp_add(&cnt[0], evals);
         warp_add(&cnt[1], full);
         warp_add(&cnt[2], cut);
@@ -566,11 +577,23 @@ __global__ void k_census(QuadArgs A, unsigned long long* cnt) {
     }
 }
 
+__global__ void k_mark(const int* ids, int64_t n, int8_t* flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[ids[i]] = 1;
+}
+
 void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStream_t st) {
     DBuf<unsigned long long> c;
     c.alloc(16, st);
     c.zero(st);
-    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, pc.npairs, nullptr, m.X.p, m.T.p, m.det.p, prm};
+    DBuf<int8_t> wflag;
+    wflag.alloc(pc.npairs, st);
+    wflag.zero(st);
+    if (pc.nwhole > 0) {
+        k_mark<<<nblk(pc.nwhole, 256), 256, 0, st>>>(pc.whole_ids.p, pc.nwhole, wflag.p);
+        NLFEM_LAUNCH_CHECK();
+    }
+    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, wflag.p, pc.npairs, nullptr, m.X.p, m.T.p, m.det.p, prm};
     unsigned grid = (unsigned)std::min<int64_t>(nblk(pc.npairs, 256), 152 * 32);
     if (grid) {
         k_census<<<grid, 256, 0, st>>>(a, c.p);
@@ -585,7 +608,7 @@ void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStr
     if (prm.singular)
         duffy = pc.counts[3] * 6 * n * n + pc.counts[2] * 4 * n * n * n + pc.counts[1] * 2 * n * n * n * n;
     h[4] = (unsigned long long)duffy;
-    for (int i = 0; i < 9; ++i) out[i] = (int64_t)h[i];
+    for (int i = 0; i < 12; ++i) out[i] = (int64_t)h[i];
 }
 
 }  // namespace nlfem

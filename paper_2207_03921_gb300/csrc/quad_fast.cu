@@ -389,7 +389,8 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(FastArgs A, float*
     }
 }
 
-void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st) {
+void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st,
+                       cudaEvent_t* ev) {
     FastArgs a;
     a.pk = pc.pk.p; a.pl = pc.pl.p; a.pcls = pc.pcls.p;
     a.X = m.X.p; a.T = m.T.p; a.E32 = m.E32.p; a.det32 = m.det32.p;
@@ -417,6 +418,7 @@ void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib
     for (int pass = 0; pass < 2; ++pass) {
         a.ids = pass == 0 ? pc.whole_ids.p : pc.cut_ids.p;
         a.npairs = pass == 0 ? pc.nwhole : pc.ncut;
+        NLFEM_CUDA_TRY(cudaEventRecord(ev[pass], st));  // ev[0..2] bracket the two launches
         unsigned grid = (unsigned)std::min<int64_t>(nblk(a.npairs, FAST_THREADS), 152 * 64);
         if (!grid) continue;
 #define NLFEM_TF(KK, NQ)                                                                  \
@@ -434,6 +436,7 @@ void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib
 #undef NLFEM_TF
         NLFEM_LAUNCH_CHECK();
     }
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
 }
 
 }  // namespace nlfem
