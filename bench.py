@@ -53,12 +53,14 @@ WORKLOADS = {
                  desc="structured h=0.05 on [-0.1,1.1]^2 (1152 triangles), constant kernel, delta=0.1"),
 }
 
-# algorithmic work model of the assembly kernels (fixed before measurement)
-FLOPS_PER_EVAL = {"constant": 57, "fractional": 60, "peridynamic": 3 * 55 + 9}
-FLOPS_PER_OUTER = 58            # kk/kl/ll updates of an outer point with a nonempty polygon
-GEOM_FLOPS_PER_OUTER = 25       # x_p (10) and three vertex-in-ball tests (15)
-GEOM_FLOPS_PER_CUT = 80         # edge quadratics, roots, crossing points, cap centres
-GEOM_FLOPS_PER_SUBTRI = 10      # fan triangle edge vectors and area
+# algorithmic work per unit (FMA = 2 flops, a MUFU op = 1): the fixed weights of the
+# measurement plan, counted on the device by nlfem_system_census
+FLOPS_PER_EVAL = {"constant": 14, "fractional": 14 + 3, "peridynamic": 14 + 7 + 2 * 8}  # per (x_p, y_q)
+FLOPS_PER_OUTER = 90            # kk / kl finalisation of an outer point with a nonempty polygon
+FLOPS_VERTEX_TESTS = 15         # three vertex-in-ball tests per (x_p, E_l) of a cut pair
+FLOPS_EDGES = 3 * 23            # three edge quadratics (with sqrt) per cut (x_p, E_l)
+FLOPS_CAPS = 3 * 14             # up to three cap centres per cut (x_p, E_l), approxcaps only
+FLOPS_SUBTRI_POINT = 8 + 6      # point mapping and barycentric basis per point of a sub-triangle
 CONTRIB_ENTRIES = {1: 21, 2: 84}
 
 
@@ -357,12 +359,11 @@ def main():
     ms_whole = statistics.mean(i["ms_whole"] for i in timed)
     ms_cut = statistics.mean(i["ms_cut"] for i in timed)
     ms_close = statistics.mean(i["ms_close"] for i in timed)
-    ev_whole, ev_close = census["evals_whole"], census["evals_close"]
-    ev_cut = census["evals"] - ev_whole - ev_close
-    flops_whole = ev_whole * fpe + (ev_whole // nqi) * FLOPS_PER_OUTER
-    nonempty_cut = census["full_points"] + census["cut_points"] - ev_whole // nqi
-    flops_cut = (ev_cut * fpe + nonempty_cut * FLOPS_PER_OUTER + census["outer_points_cut"] * GEOM_FLOPS_PER_OUTER
-                 + census["cut_points"] * GEOM_FLOPS_PER_CUT + census["subtris"] * GEOM_FLOPS_PER_SUBTRI)
+    flops_whole = census["evals_whole"] * fpe + (census["evals_whole"] // nqi) * FLOPS_PER_OUTER
+    flops_cut = (census["evals_cut"] * fpe + census["nonempty_points_cut"] * FLOPS_PER_OUTER
+                 + census["outer_points_cut"] * FLOPS_VERTEX_TESTS
+                 + census["cut_points_cut"] * (FLOPS_EDGES + (FLOPS_CAPS if wl["ball"] == "approxcaps" else 0))
+                 + census["subtri_evals_cut"] * FLOPS_SUBTRI_POINT)
     ne = CONTRIB_ENTRIES[ndof]
     red_bytes = (info0["n_contrib"] * (4 + 4)                 # slot index + FP32 contribution
                  + info0["n_upper"] * (8 + 4 + 4 + 16 + 8 + 8 + 8)  # up_pos, up_row, ncol, seg_ptr, pbase, nptr, row_ptr
@@ -371,8 +372,8 @@ def main():
         "k_trunc_whole": {"bound": "alu", "ms": ms_whole, "units": info0["pairs_whole"],
                           "achieved": flops_whole / (ms_whole * 1e-3) / 1e12 if ms_whole else 0.0,
                           "peak": fp32_peak, "unit": "TFLOP/s"},
-        "k_trunc_fast": {"bound": "alu", "ms": ms_cut,
-                         "units": info0["pairs_separated"] - info0["pairs_whole"],
+        "k_trunc_cut": {"bound": "alu", "ms": ms_cut,
+                         "units": census["outer_points_cut"] // wl["quad_outer"],
                          "achieved": flops_cut / (ms_cut * 1e-3) / 1e12 if ms_cut else 0.0,
                          "peak": fp32_peak, "unit": "TFLOP/s"},
         "k_reduce": {"bound": "hbm", "ms": red_ms, "units": info0["n_upper"],
@@ -392,7 +393,7 @@ def main():
     line = {
         "metric": "element-pair assemblies/s", "value": value, "unit": "pairs/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (quadrature) + f64 (geometry, singular pairs, CSR)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (quadrature and geometry with exact decisions) + f64 (near ties, singular pairs, CSR)",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "precision": "fp32_bulk",
                    "step": "nlfem_assemble with cached pair list and pattern",
@@ -409,7 +410,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "pinned host mesh -> nlfem_mesh_create -> nlfem_assemble (cold) -> CSR values and F to host"},
         # per step: whole-pair and cut-pair quadrature, intersecting pairs, reduction, load vector
-        "gpu_launches": args.steps * (2 + (1 if census["singular_pairs"] or census["evals_close"] else 0) + 2),
+        "gpu_launches": args.steps * (2 + (1 if census["singular_pairs"] or census["evals_canonical"] else 0) + 2),
         "clocks": clk_sum,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -81,10 +81,10 @@ typedef struct {
     double ms_quadrature;    /* pair quadrature kernels */
     double ms_reduce;        /* segmented reduction into CSR */
     int cached;              /* 1 if the pair list / pattern of the mesh handle were reused */
-    double ms_whole;         /* FP32 bulk: pairs with E_l in the ball of every outer point */
-    double ms_cut;           /* FP32 bulk: the other separated pairs (FP64 plain: all pairs) */
-    double ms_close;         /* intersecting pairs (singular rule or canonical truncation) */
-    int64_t pairs_whole;     /* separated pairs with E_l in the ball of every point of E_k */
+    double ms_whole;         /* FP32 bulk: standard-rule pairs with E_l in the ball of every outer point */
+    double ms_cut;           /* FP32 bulk: the other standard-rule pairs (FP64 plain: all pairs) */
+    double ms_close;         /* intersecting pairs under the singular or the diamond rule */
+    int64_t pairs_whole;     /* standard-rule pairs with E_l in the ball of every point of E_k */
     int64_t n_upper;         /* node-level upper pattern entries (one reduction unit each) */
     int64_t n_contrib;       /* contributions gathered by the reduction (slot index length) */
 } nlfem_assembly_info;
@@ -171,17 +171,20 @@ int nlfem_solve(nlfem_system_t sys, const double* g_nodal, double tol_rel, int m
                 double* u_out, nlfem_solve_info* info, void* stream);
 
 /*
- * Work of the assembly that produced sys, counted on the device with the same geometry
- * (for FLOP accounting; it does not change sys). counts[12] receives: [0] kernel
+ * Work of the assembly that produced sys, counted on the device with the canonical FP64
+ * geometry (for FLOP accounting; it does not change sys). counts[16] receives: [0] kernel
  * evaluations of the truncation quadrature, [1] outer points whose inner element lies
  * fully in the ball, [2] outer points whose inner element was cut and retriangulated,
  * [3] sub-triangles of the cut polygons, [4] points evaluated by the singular rule,
  * [5] pairs on the truncation path, [6] pairs on the singular path, [7] outer points
- * with an empty intersection, [8] outer points visited, [9] evaluations on pairs with
- * E_l inside every outer point's ball, [10] evaluations on intersecting pairs,
- * [11] outer points of the other separated pairs. Errors: INVALID_ARG, CUDA.
+ * with an empty intersection, [8] outer points visited; split by the FP32-bulk kernels:
+ * [9] evaluations of the whole-pair kernel, [10] evaluations of the cut-pair kernel,
+ * [11] outer points, [12] cut outer points, [13] nonempty outer points and
+ * [14] evaluations on sub-triangles of the cut-pair kernel, [15] evaluations of the
+ * canonical truncation kernel. The mesh's cached pair list must still be the one sys was
+ * assembled on. Errors: INVALID_ARG, CUDA.
  */
-int nlfem_system_census(nlfem_system_t sys, int64_t counts[12], void* stream);
+int nlfem_system_census(nlfem_system_t sys, int64_t counts[16], void* stream);
 
 void nlfem_system_destroy(nlfem_system_t sys);
 

@@ -196,11 +196,12 @@ def nlfem_solve(sys, g_nodal, tol_rel, max_iter, u_out, stream=None) -> dict:
 
 
 CENSUS = ["evals", "full_points", "cut_points", "subtris", "duffy_points", "trunc_pairs", "singular_pairs",
-          "empty_points", "outer_points", "evals_whole", "evals_close", "outer_points_cut"]
+          "empty_points", "outer_points", "evals_whole", "evals_cut", "outer_points_cut", "cut_points_cut",
+          "nonempty_points_cut", "subtri_evals_cut", "evals_canonical"]
 
 
 def nlfem_system_census(sys, stream=None) -> dict:
-    c = (C.c_int64 * 12)()
+    c = (C.c_int64 * 16)()
     _check(load().nlfem_system_census(sys, c, _stream(stream)))
     return dict(zip(CENSUS, (int(v) for v in c)))
 

@@ -244,7 +244,7 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
     } guard{ev};
     std::shared_ptr<PairCache> pc = m.cache;
     bool cached = pc && pc->delta == P.delta && pc->ball == P.ball && pc->nqo == P.ro.n &&
-                  pc->ndof == P.ndof && pc->close_singular == (int)P.singular;
+                  pc->ndof == P.ndof && pc->close_mode == close_mode(P);
     double t_pairs = 0, t_pattern = 0;
     if (!cached) {
         m.cache.reset();
@@ -254,9 +254,10 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
             pc->ball = P.ball;
             pc->nqo = P.ro.n;
             pc->ndof = P.ndof;
-            pc->close_singular = (int)P.singular;
+            pc->close_mode = close_mode(P);
             NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
             build_pairs(m, P, *pc, st);
+            order_cut_pairs(m, *pc, P, st);
             NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
             build_pattern(m, *pc, st);
             NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
@@ -393,7 +394,7 @@ int nlfem_solve(nlfem_system_t sys, const double* g_nodal, double tol_rel, int m
     NLFEM_API_END
 }
 
-int nlfem_system_census(nlfem_system_t sys, int64_t counts[12], void* stream) {
+int nlfem_system_census(nlfem_system_t sys, int64_t counts[16], void* stream) {
     NLFEM_API_BEGIN
     NLFEM_CHECK(sys && counts, NLFEM_ERR_INVALID_ARG, "NULL argument");
     run_census(*sys->s.mesh, *sys->s.pc, sys->s.prm, counts, (cudaStream_t)stream);

@@ -69,6 +69,11 @@ struct DBuf {
         if (n) NLFEM_CUDA_TRY(cudaMemsetAsync(p, 0, n * sizeof(T), st));
     }
     size_t bytes() const { return n * sizeof(T); }
+    void swap_with(DBuf& o) {
+        std::swap(p, o.p);
+        std::swap(n, o.n);
+        std::swap(s, o.s);
+    }
 };
 
 // ------------------------------------------------------------------------------------------
@@ -121,17 +126,17 @@ struct Params {
 // Interaction graph, CSR pattern and reduction index of one (mesh, delta, ball, outer rule, ndof).
 struct PairCache {
     double delta = -1;
-    int ball = -1, nqo = -1, ndof = -1, close_singular = -1;
+    int ball = -1, nqo = -1, ndof = -1, close_mode = -1;  // close_mode: 0 standard, 1 singular, 2 diamond
     int64_t npairs = 0;
     DBuf<int64_t> pair_ptr;  // [K + 1]
     DBuf<int> pk, pl;        // [P], sorted by (k, l)
     DBuf<int8_t> pcls;       // shared vertex count [P]
     DBuf<int64_t> pT_ptr;    // [K + 1] pairs grouped by l
     DBuf<int> pT_id;         // [P] pair ids, sorted per l
-    DBuf<int> duffy_ids;     // intersecting pairs (shared vertex), in pair order
+    DBuf<int> duffy_ids;     // intersecting pairs under the singular or diamond rule, in pair order
     int64_t nduffy = 0;
-    DBuf<int> whole_ids;     // separated pairs with E_l inside the ball of every point of E_k
-    DBuf<int> cut_ids;       // the other separated pairs
+    DBuf<int> whole_ids;     // pairs on the standard rule with E_l inside the ball of every point of E_k
+    DBuf<int> cut_ids;       // the other pairs on the standard rule, ordered by fan-triangle count
     int64_t nwhole = 0, ncut = 0;
     int64_t counts[4] = {0, 0, 0, 0};  // separated, vertex, edge, identical
     // node-level pattern
@@ -183,6 +188,8 @@ int64_t contrib_entries(int ndof);
 void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStream_t st);
 void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st,
                        cudaEvent_t* ev);
+void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st);
+inline int close_mode(const Params& P) { return P.singular ? 1 : (P.nozerodiv ? 2 : 0); }
 int solve_system(System& S, const double* g, double tol, int max_iter, double* u_out, nlfem_solve_info* info,
                  cudaStream_t st);
 

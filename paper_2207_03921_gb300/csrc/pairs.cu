@@ -176,21 +176,22 @@ __global__ void k_fill_T(const int* pl, int64_t P, const int64_t* tptr, int* cur
     tid[tptr[l] + pos] = (int)p;
 }
 
-__global__ void k_flag_duffy(const int8_t* cls, int64_t P, int64_t* flag) {
+__global__ void k_flag_duffy(const int8_t* cls, int64_t P, int std_close, int64_t* flag) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < P) flag[p] = cls[p] > 0;
+    if (p < P) flag[p] = cls[p] > 0 && !std_close;
 }
 
-// Separated pairs whose inner element lies in the ball of every point of the outer
-// element: the largest vertex-to-vertex distance is below delta with a relative margin
-// of 1e-6 (far above FP64 rounding), so the canonical clip finds all three vertices
-// inside at every outer point. flag_whole / flag_cut select the two lists.
+// Pairs on the standard rule (separated pairs, and intersecting pairs when the close rule
+// is the standard one) split by whether the inner element lies in the ball of every point
+// of the outer element: the largest vertex-to-vertex distance is below delta with a
+// relative margin of 1e-6 (far above FP64 rounding), so the canonical clip finds all three
+// vertices inside at every outer point. flag_whole / flag_cut select the two lists.
 __global__ void k_flag_whole(const int* pk, const int* pl, const int8_t* cls, int64_t P, const double2* X,
-                             const int4* T, double delta2, int64_t* flag_whole, int64_t* flag_cut) {
+                             const int4* T, double delta2, int std_close, int64_t* flag_whole, int64_t* flag_cut) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     int64_t w = 0, c = 0;
-    if (cls[p] == 0) {
+    if (cls[p] == 0 || std_close) {
         const int4 a = T[pk[p]], b = T[pl[p]];
         const double2 va[3] = {X[a.x], X[a.y], X[a.z]}, vb[3] = {X[b.x], X[b.y], X[b.z]};
         double mx = 0.0;
@@ -322,7 +323,7 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
     for (int i = 0; i < 4; ++i) pc.counts[i] = (int64_t)hc[i];
 
-    // separated pairs split into wholly-inside pairs and the rest (the bulk kernels' work lists)
+    // standard-rule pairs split into wholly-inside pairs and the rest (the bulk kernels' work lists)
     pc.nwhole = pc.ncut = 0;
     pc.whole_ids.release();
     pc.cut_ids.release();
@@ -332,8 +333,8 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
         fc.alloc(P, st);
         pw.alloc(P + 1, st);
         pcut.alloc(P + 1, st);
-        k_flag_whole<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, pc.pcls.p, P, m.X.p, m.T.p, prm.delta2, fw.p,
-                                                   fc.p);
+        k_flag_whole<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, pc.pcls.p, P, m.X.p, m.T.p, prm.delta2,
+                                                   close_mode(prm) == 0, fw.p, fc.p);
         NLFEM_LAUNCH_CHECK();
         exclusive_scan_i64(fw.p, pw.p, P, st);
         exclusive_scan_i64(fc.p, pcut.p, P, st);
@@ -347,14 +348,14 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
         NLFEM_LAUNCH_CHECK();
     }
 
-    // intersecting pairs (the singular rule, or the canonical truncation kernel, takes them)
+    // intersecting pairs under the singular rule (k_duffy) or the diamond rule (canonical k_trunc)
     pc.nduffy = 0;
     pc.duffy_ids.release();
     if (P) {
         DBuf<int64_t> flag, pos;
         flag.alloc(P, st);
         pos.alloc(P + 1, st);
-        k_flag_duffy<<<nblk(P, 256), 256, 0, st>>>(pc.pcls.p, P, flag.p);
+        k_flag_duffy<<<nblk(P, 256), 256, 0, st>>>(pc.pcls.p, P, close_mode(prm) == 0, flag.p);
         NLFEM_LAUNCH_CHECK();
         exclusive_scan_i64(flag.p, pos.p, P, st);
         int64_t nd = 0;

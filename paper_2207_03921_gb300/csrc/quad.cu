@@ -29,7 +29,7 @@ struct QuadArgs {
     const int* pk;
     const int* pl;
     const int8_t* pcls;
-    const int8_t* whole;   // census only: pair is in the whole-pair list
+    const int8_t* whole;   // census only: 1 if the pair is in the whole-pair list, 2 in the cut list
     int64_t npairs;        // number of pairs to process (of ids, if given)
     const int* ids;        // optional list of pair ids
     const double2* X;
@@ -540,13 +540,13 @@ __global__ void k_census(QuadArgs A, unsigned long long* cnt) {
     for (int64_t it = 0; it < n_iter; ++it) {
         int64_t p = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         unsigned long long evals = 0, full = 0, cut = 0, sub = 0, empty = 0, tp = 0, sp = 0, outer = 0;
-        int whole = 0, clsv = 0;
+        int list = 0;  // 1: whole-pair kernel, 2: cut-pair kernel, 0: canonical kernels
         if (p < A.npairs) {
             const int cls = A.pcls[p];
             if (cls > 0 && P.singular) {
                 sp = 1;
             } else {
-                whole = A.whole ? A.whole[p] : 0;
+                list = A.whole ? A.whole[p] : 0;
                 tp = 1;
                 const int4 tk = A.T[A.pk[p]], tl = A.T[A.pl[p]];
                 const double2 Vk[3] = {A.X[tk.x], A.X[tk.y], A.X[tk.z]};
@@ -560,12 +560,8 @@ __global__ void k_census(QuadArgs A, unsigned long long* cnt) {
                     if (f) { ++full; evals += P.ri.n; }
                     else { ++cut; sub += np - 2; evals += (unsigned long long)(np - 2) * P.ri.n; }
                 }
-                clsv = cls;
             }
         }
-        warp_add(&cnt[9], whole ? evals : 0ull);
-        warp_add(&cnt[10], (!whole && clsv > 0) ? evals : 0ull);
-        warp_add(&cnt[11], (!whole && clsv == 0 && tp) ? outer : 0ull);
         warp_add(&cnt[0], evals);
         warp_add(&cnt[1], full);
         warp_add(&cnt[2], cut);
@@ -574,12 +570,19 @@ __global__ void k_census(QuadArgs A, unsigned long long* cnt) {
         warp_add(&cnt[6], sp);
         warp_add(&cnt[7], empty);
         warp_add(&cnt[8], outer);
+        warp_add(&cnt[9], list == 1 ? evals : 0ull);
+        warp_add(&cnt[10], list == 2 ? evals : 0ull);
+        warp_add(&cnt[11], list == 2 ? outer : 0ull);
+        warp_add(&cnt[12], list == 2 ? cut : 0ull);
+        warp_add(&cnt[13], list == 2 ? full + cut : 0ull);
+        warp_add(&cnt[14], list == 2 ? sub * P.ri.n : 0ull);
+        warp_add(&cnt[15], list == 0 ? evals : 0ull);
     }
 }
 
-__global__ void k_mark(const int* ids, int64_t n, int8_t* flag) {
+__global__ void k_mark(const int* ids, int64_t n, int8_t v, int8_t* flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[ids[i]] = 1;
+    if (i < n) flag[ids[i]] = v;
 }
 
 void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStream_t st) {
@@ -590,7 +593,11 @@ void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStr
     wflag.alloc(pc.npairs, st);
     wflag.zero(st);
     if (pc.nwhole > 0) {
-        k_mark<<<nblk(pc.nwhole, 256), 256, 0, st>>>(pc.whole_ids.p, pc.nwhole, wflag.p);
+        k_mark<<<nblk(pc.nwhole, 256), 256, 0, st>>>(pc.whole_ids.p, pc.nwhole, 1, wflag.p);
+        NLFEM_LAUNCH_CHECK();
+    }
+    if (pc.ncut > 0) {
+        k_mark<<<nblk(pc.ncut, 256), 256, 0, st>>>(pc.cut_ids.p, pc.ncut, 2, wflag.p);
         NLFEM_LAUNCH_CHECK();
     }
     QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, wflag.p, pc.npairs, nullptr, m.X.p, m.T.p, m.det.p, prm};
@@ -608,7 +615,7 @@ void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStr
     if (prm.singular)
         duffy = pc.counts[3] * 6 * n * n + pc.counts[2] * 4 * n * n * n + pc.counts[1] * 2 * n * n * n * n;
     h[4] = (unsigned long long)duffy;
-    for (int i = 0; i < 12; ++i) out[i] = (int64_t)h[i];
+    for (int i = 0; i < 16; ++i) out[i] = (int64_t)h[i];
 }
 
 }  // namespace nlfem

@@ -13,7 +13,7 @@
 //
 // Work layout: one thread per ordered pair. Pairs whose inner element lies in the ball of
 // every outer point (decided at pair-search time) take k_trunc_whole: no geometry, fully
-// uniform. The others take k_trunc_fast: the geometry of a chunk of outer points runs in
+// uniform. The others take k_trunc_cut: the geometry of a chunk of outer points runs in
 // lockstep across the warp, then a drain loop integrates one fan triangle per lane and
 // iteration, so the inner rule runs with (nearly) the whole warp and exists once in the
 // code.
@@ -24,6 +24,8 @@
 namespace nlfem {
 
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+static constexpr int FAST_THREADS = 128;
 
 struct FastArgs {
     const int* pk;
@@ -100,8 +102,6 @@ __device__ __forceinline__ void tri_quad(const FastArgs& A, Inner<NC>& I, float 
     }
 }
 
-static constexpr int FAST_THREADS = 128;
-
 // kk += a_p g P P^T, kl -= a_p P h^T, ll += a_p m for outer point q0 (P = its barycentrics)
 template <int NC>
 __device__ __forceinline__ void outer_update(const FastArgs& A, int q0, float dk, const Inner<NC>& I,
@@ -158,28 +158,161 @@ __device__ __forceinline__ void write_block(float* out, const float (&kk)[6][NC]
         }
 }
 
-// Cut pairs: outer points are processed in chunks of CHUNK. Phase A sets up every outer
-// point of the chunk in lockstep across the warp (decisions, polygon positions into
-// shared memory; 4 bits per outer point record the number of points). Phase B drains the
-// fan triangles: each iteration integrates one triangle per lane, walking through the
-// lane's outer points in order, and applies that triangle's inner sums with its outer
-// point's factors. Barycentric coordinates are recomputed from positions with E_l's
-// inverse map.
-static constexpr int CHUNK = 8;
-static constexpr int MAXPTS = 9;
+template <int NC>
+struct PairBlock {
+    float kk[6][NC], kl[9][NC], ll[6][NC];
+};
 
-template <int KER, int NQI>
-__global__ void __launch_bounds__(FAST_THREADS) k_trunc_fast(FastArgs A, float* __restrict__ contrib) {
-    constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
-    constexpr int NE = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 84 : 21;
-    extern __shared__ float s_pts[];  // [CHUNK][MAXPTS][2][FAST_THREADS]
-    float* my = s_pts + threadIdx.x;
-    auto put = [&](int q, int slot, float x, float y) {
-        if (slot < MAXPTS) {
-            my[((q * MAXPTS + slot) * 2 + 0) * FAST_THREADS] = x;
-            my[((q * MAXPTS + slot) * 2 + 1) * FAST_THREADS] = y;
+// Intersecting pairs: a node shared by E_k and E_l takes one position of the union block
+// (k0 k1 k2, then the unshared nodes of E_l in order), so the kl terms of a shared node
+// pair land on the diagonal twice and the rest of the block folds onto fewer entries.
+// Rare (a few percent of the pairs), so kept out of line; sequential, hence deterministic.
+template <int NC, int NE>
+__device__ __noinline__ void write_block_union(float* out, int4 tk, int4 tl, PairBlock<NC> B) {
+    int posl[3];
+    const int lv[3] = {tl.x, tl.y, tl.z};
+    int U = 3;
+    for (int b = 0; b < 3; ++b) {
+        int f = -1;
+        if (lv[b] == tk.x) f = 0;
+        if (lv[b] == tk.y) f = 1;
+        if (lv[b] == tk.z) f = 2;
+        posl[b] = f >= 0 ? f : U++;
+    }
+    for (int i = 0; i < NE; ++i) out[i] = 0.f;
+    auto add = [&](int a, int b, int c, float v) {
+        const int lo = min(a, b), hi = max(a, b);
+        const int e = lo * 6 - lo * (lo - 1) / 2 + (hi - lo);  // entry of (lo, hi) in the upper triangle
+        if (NC == 1) {
+            out[e] += v;
+        } else if (c == 0) {
+            out[e * 4] += v;
+        } else if (c == 1) {
+            out[e * 4 + 1] += v;
+            out[e * 4 + 2] += v;
+        } else {
+            out[e * 4 + 3] += v;
         }
     };
+    const int kkI[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    for (int c = 0; c < NC; ++c)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                if (a <= b) add(a, b, c, B.kk[kkI[a][b]][c]);
+                add(a, posl[b], c, B.kl[a * 3 + b][c]);
+                if (a == posl[b]) add(a, a, c, B.kl[a * 3 + b][c]);
+                if (a <= b) add(posl[a], posl[b], c, B.ll[kkI[a][b]][c]);
+            }
+}
+
+template <int NC, int NE>
+__device__ __forceinline__ void write_pair(float* out, bool shared, int4 tk, int4 tl, const float (&kk)[6][NC],
+                                           const float (&kl)[9][NC], const float (&ll)[6][NC]) {
+    if (!shared) {
+        write_block<NC, NE>(out, kk, kl, ll);
+        return;
+    }
+    PairBlock<NC> B;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            B.kk[i][c] = kk[i][c];
+            B.ll[i][c] = ll[i][c];
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) B.kl[i][c] = kl[i][c];
+    }
+    write_block_union<NC, NE>(out, tk, tl, B);
+}
+
+// FP32 decisions of one outer point, all evaluated (no early exit, so a warp stays
+// converged). Same margins and outcomes as nl_decide32; ok = false where a decision is too
+// close to call. For two crossings on one edge, both ends outside, the vertex of the
+// quadratic t_c = -B/A must lie in (0, 1): tested as 0 < -B < A (no division). Where disc is
+// decided positive and both ends are decided outside, t_c is bounded away from 0 and 1 by
+// sqrt(floor2 / A), so the test cannot flip under rounding.
+struct GeoF {
+    float ta[3], tb[3];
+    int nc[3];
+    bool in[3];
+};
+
+__device__ __forceinline__ bool decide_flat(const float Rx[3], const float Ry[3], const float C[3], float eps,
+                                            float floor2, float d2, GeoF& g) {
+    bool ok = true;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        ok &= fabsf(C[m]) > floor2 + 2.f * (fabsf(Rx[m]) + fabsf(Ry[m])) * eps;
+        g.in[m] = C[m] < 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int b = (e + 1) % 3;
+        const float ux = Rx[b] - Rx[e], uy = Ry[b] - Ry[e];
+        const float Aq = ux * ux + uy * uy;
+        const float Bq = Rx[e] * ux + Ry[e] * uy;
+        const float Cq = C[e];
+        const float disc = Bq * Bq - Aq * Cq;
+        const bool one = g.in[e] != g.in[b];
+        const bool out2 = !g.in[e] && !g.in[b];
+        const float e1n = fabsf(Rx[e]) + fabsf(Ry[e]), u1n = fabsf(ux) + fabsf(uy);
+        const float bound = 2.f * fabsf(Bq) * (u1n + 2.f * e1n) * eps + Aq * (2.f * e1n * eps + 1e-6f * d2) +
+                            fabsf(Cq) * 4.f * u1n * eps + 1e-6f * (Bq * Bq + fabsf(Aq * Cq));
+        ok &= !(out2 && fabsf(disc) <= bound);
+        // stable roots; qq != 0 whenever a crossing exists (disc > 0)
+        const float sq = sqrtf(fmaxf(disc, 0.f));
+        const float qq = -(Bq + copysignf(sq, Bq));
+        const float r1 = __fdividef(qq, Aq), r2 = __fdividef(Cq, qq);
+        const float lo = fminf(r1, r2), hi = fmaxf(r1, r2);
+        const bool two = out2 && disc > 0.f && Bq < 0.f && -Bq < Aq;
+        g.nc[e] = one ? 1 : (two ? 2 : 0);
+        g.ta[e] = (one && g.in[e]) ? hi : lo;
+        g.tb[e] = hi;
+    }
+    return ok;
+}
+
+// canonical FP64 clip of one outer point (near ties), written relative to x_p; kept out of
+// line so that its registers do not weigh on the common path
+__device__ __noinline__ int clip_canonical(const double2* __restrict__ X, int4 tk, int4 tl, double o0, double o1,
+                                           double o2, double delta, double delta2, bool caps, float2* dst,
+                                           int maxp) {
+    const double2 Vk[3] = {X[tk.x], X[tk.y], X[tk.z]};
+    const double2 Vl[3] = {X[tl.x], X[tl.y], X[tl.z]};
+    const double2 xp = nl_map(Vk, o0, o1, o2);
+    CPt poly[NLFEM_MAXPOLY];
+    bool full;
+    int n = nl_clip(Vl, xp, delta, delta2, caps, poly, full);
+    if (full) {
+        for (int m = 0; m < 3; ++m)
+            dst[m * FAST_THREADS] = make_float2((float)(Vl[m].x - xp.x), (float)(Vl[m].y - xp.y));
+        return 3;
+    }
+    n = min(n, maxp);
+    for (int m = 0; m < n; ++m)
+        dst[m * FAST_THREADS] = make_float2((float)(poly[m].x - xp.x), (float)(poly[m].y - xp.y));
+    return n;
+}
+
+// Cut pairs: the outer points are processed in chunks of CHUNK. Phase A sets up every
+// outer point of the chunk in lockstep across the warp (decisions, polygon points relative
+// to x_p into shared memory; 4 bits per outer point record the number of points). Phase B
+// drains the fan triangles: each iteration integrates one triangle per lane, walking
+// through the lane's outer points in order, and applies that triangle's inner sums with its
+// outer point's factors. Barycentric coordinates are recomputed from positions with E_l's
+// inverse map. The cut list is ordered by fan-triangle count (order_cut_pairs), so the
+// lanes of a warp drain about the same number of triangles.
+static constexpr int CHUNK = 8;
+
+template <int KER, int NQI, bool CAPS>
+__global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A, float* __restrict__ contrib) {
+    constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
+    constexpr int NE = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 84 : 21;
+    constexpr int MAXP = CAPS ? 9 : 6;  // polygon points: 6 raw, plus up to 3 cap centres
+    extern __shared__ float2 s_pts[];   // [CHUNK][MAXP][FAST_THREADS]
+    float2* my = s_pts + threadIdx.x;
+    auto put = [&](int q, int slot, float x, float y) { my[(q * MAXP + slot) * FAST_THREADS] = make_float2(x, y); };
     const Params& P = A.prm;
     const int nqo = P.ro.n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -188,23 +321,22 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_fast(FastArgs A, float* 
         const bool valid = pi < A.npairs;
         const int64_t p = valid ? (int64_t)A.ids[pi] : 0;
         int4 tk = make_int4(0, 0, 0, 0), tl = make_int4(0, 0, 0, 0);
-        double2 v0k = make_double2(0, 0), v0l = make_double2(0, 0);
         float4 Ek = make_float4(0, 0, 0, 0), El = make_float4(1, 0, 0, 1);
         float dk = 0.f, dx = 0.f, dy = 0.f;
+        bool shared = false;
         if (valid) {
             const int k = A.pk[p], l = A.pl[p];
+            shared = A.pcls[p] > 0;
             tk = A.T[k];
             tl = A.T[l];
-            v0k = A.X[tk.x];
-            v0l = A.X[tl.x];
+            const double2 v0k = A.X[tk.x], v0l = A.X[tl.x];
             dx = (float)(v0l.x - v0k.x);
             dy = (float)(v0l.y - v0k.y);
             Ek = A.E32[k];
             El = A.E32[l];
             dk = A.det32[k];
         }
-        const float detE = El.x * El.w - El.y * El.z;
-        const float idet = 1.f / detE;
+        const float idet = 1.f / (El.x * El.w - El.y * El.z);
         const float W0x = dx, W0y = dy;
         const float W1x = dx + El.x, W1y = dy + El.y, W2x = dx + El.z, W2y = dy + El.w;
         const float span = fabsf(dx) + fabsf(dy) + fabsf(Ek.x) + fabsf(Ek.y) + fabsf(Ek.z) + fabsf(Ek.w) +
@@ -237,68 +369,57 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_fast(FastArgs A, float* 
                 float Cc[3];
 #pragma unroll
                 for (int m = 0; m < 3; ++m) Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - A.d2;
+                GeoF G;
+                bool ok = decide_flat(Rx, Ry, Cc, eps, floor2, A.d2, G);
                 int n = 0;
-                if (valid) {
-                    Geo32 G;
-                    n = -1;
-                    if (nl_decide32(Rx, Ry, Cc, eps, floor2, A.d2, G)) {
-                        if (G.in[0] && G.in[1] && G.in[2]) {
+                if (!CAPS) {
+                    // vertices inside and crossings in boundary order; predicated stores
 #pragma unroll
-                            for (int m = 0; m < 3; ++m) put(q, m, Rx[m], Ry[m]);
-                            n = 3;
-                        } else {
-                            // decided polygon: vertices inside, crossings, caps
-                            int nraw = 0, fe = 0, fv = 0, le = 0;
-                            float fx = 0, fy = 0, lx = 0, ly = 0;
-                            bool bad = false;
-                            n = 0;
-                            auto cap = [&](float px, float py, float qx, float qy) {
-                                const float cx = qx - px, cy = qy - py;
-                                const float len = sqrtf(cx * cx + cy * cy);
-                                if (!(len > 1e-6f * A.delta)) {
-                                    bad = true;
-                                    return;
-                                }
-                                put(q, n++, A.delta * (cy / len), A.delta * (-cx / len));
-                            };
-                            auto raw = [&](float x, float y, int e, int v) {
-                                if (A.caps && nraw >= 1 && !((e == le) || (v && e == (le + 1) % 3)))
-                                    cap(lx, ly, x, y);
-                                put(q, n++, x, y);
-                                if (nraw == 0) { fx = x; fy = y; fe = e; fv = v; }
-                                lx = x; ly = y; le = e;
-                                ++nraw;
-                            };
+                    for (int e = 0; e < 3; ++e) {
+                        const int b = (e + 1) % 3;
+                        const float ux = Rx[b] - Rx[e], uy = Ry[b] - Ry[e];
+                        if (G.in[e]) put(q, n, Rx[e], Ry[e]);
+                        n += G.in[e];
+                        if (G.nc[e] >= 1) put(q, n, fmaf(G.ta[e], ux, Rx[e]), fmaf(G.ta[e], uy, Ry[e]));
+                        n += G.nc[e] >= 1;
+                        if (G.nc[e] >= 2) put(q, n, fmaf(G.tb[e], ux, Rx[e]), fmaf(G.tb[e], uy, Ry[e]));
+                        n += G.nc[e] >= 2;
+                    }
+                } else if (ok) {
+                    // with caps: a cap centre between consecutive points not joined along an edge
+                    int nraw = 0, fe = 0, fv = 0, le = 0;
+                    float fx = 0, fy = 0, lx = 0, ly = 0;
+                    auto cap = [&](float px, float py, float qx, float qy) {
+                        const float cx = qx - px, cy = qy - py;
+                        const float len = sqrtf(cx * cx + cy * cy);
+                        ok &= len > 1e-6f * A.delta;
+                        const float sc = __fdividef(A.delta, len);
+                        put(q, min(n, MAXP - 1), sc * cy, -sc * cx);
+                        ++n;
+                    };
+                    auto raw = [&](float x, float y, int e, int v) {
+                        if (nraw >= 1 && !((e == le) || (v && e == (le + 1) % 3))) cap(lx, ly, x, y);
+                        put(q, min(n, MAXP - 1), x, y);
+                        ++n;
+                        if (nraw == 0) { fx = x; fy = y; fe = e; fv = v; }
+                        lx = x; ly = y; le = e;
+                        ++nraw;
+                    };
 #pragma unroll
-                            for (int e = 0; e < 3; ++e) {
-                                const int b = (e + 1) % 3;
-                                if (G.in[e]) raw(Rx[e], Ry[e], e, 1);
-                                if (G.nc[e] >= 1)
-                                    raw(Rx[e] + G.ta[e] * (Rx[b] - Rx[e]), Ry[e] + G.ta[e] * (Ry[b] - Ry[e]), e, 0);
-                                if (G.nc[e] >= 2)
-                                    raw(Rx[e] + G.tb[e] * (Rx[b] - Rx[e]), Ry[e] + G.tb[e] * (Ry[b] - Ry[e]), e, 0);
-                            }
-                            if (A.caps && nraw >= 2 && !(fv && fe == (le + 1) % 3)) cap(lx, ly, fx, fy);
-                            if (bad) n = -1;
-                        }
+                    for (int e = 0; e < 3; ++e) {
+                        const int b = (e + 1) % 3;
+                        const float ux = Rx[b] - Rx[e], uy = Ry[b] - Ry[e];
+                        if (G.in[e]) raw(Rx[e], Ry[e], e, 1);
+                        if (G.nc[e] >= 1) raw(fmaf(G.ta[e], ux, Rx[e]), fmaf(G.ta[e], uy, Ry[e]), e, 0);
+                        if (G.nc[e] >= 2) raw(fmaf(G.tb[e], ux, Rx[e]), fmaf(G.tb[e], uy, Ry[e]), e, 0);
                     }
-                    if (n < 0) {
-                        // canonical FP64 geometry for this outer point (near ties)
-                        const double2 Vk[3] = {v0k, A.X[tk.y], A.X[tk.z]};
-                        const double2 Vl[3] = {v0l, A.X[tl.y], A.X[tl.z]};
-                        const double2 xp = nl_map(Vk, P.ro.l[q0][0], P.ro.l[q0][1], P.ro.l[q0][2]);
-                        CPt poly[NLFEM_MAXPOLY];
-                        bool full;
-                        n = nl_clip(Vl, xp, P.delta, P.delta2, A.caps != 0, poly, full);
-                        if (full) {
-                            for (int m = 0; m < 3; ++m) put(q, m, (float)(Vl[m].x - xp.x), (float)(Vl[m].y - xp.y));
-                        } else {
-                            n = min(n, MAXPTS);
-                            for (int m = 0; m < n; ++m) put(q, m, (float)(poly[m].x - xp.x), (float)(poly[m].y - xp.y));
-                        }
-                    }
-                    n = min(n, MAXPTS);
+                    if (!(G.in[0] && G.in[1] && G.in[2]) && nraw >= 2 && !(fv && fe == (le + 1) % 3))
+                        cap(lx, ly, fx, fy);
                 }
+                if (!valid) n = 0;
+                else if (!ok)
+                    n = clip_canonical(A.X, tk, tl, P.ro.l[q0][0], P.ro.l[q0][1], P.ro.l[q0][2], P.delta, P.delta2,
+                                       CAPS, my + q * MAXP * FAST_THREADS, MAXP);
                 counts |= (unsigned long long)(n < 3 ? 0 : n) << (4 * q);
             }
             // ---- phase B: one fan triangle per lane and iteration
@@ -314,9 +435,10 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_fast(FastArgs A, float* 
                     const int slot[3] = {0, sc - 1, sc};
 #pragma unroll
                     for (int t = 0; t < 3; ++t) {
-                        px[t] = my[((qc * MAXPTS + slot[t]) * 2 + 0) * FAST_THREADS];
-                        py[t] = my[((qc * MAXPTS + slot[t]) * 2 + 1) * FAST_THREADS];
-                        const float rx = px[t] + Bx, ry = py[t] + By;
+                        const float2 pt = my[(qc * MAXP + slot[t]) * FAST_THREADS];
+                        px[t] = pt.x;
+                        py[t] = pt.y;
+                        const float rx = pt.x + Bx, ry = pt.y + By;
                         b1[t] = (rx * El.w - ry * El.z) * idet;
                         b2[t] = (El.x * ry - El.y * rx) * idet;
                     }
@@ -340,8 +462,52 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_fast(FastArgs A, float* 
                 }
             }
         }
-        if (valid) write_block<NC, NE>(contrib + p * NE, kk, kl, ll);
+        if (valid) write_pair<NC, NE>(contrib + p * NE, shared, tk, tl, kk, kl, ll);
     }
+}
+
+// Fan triangles of a cut pair summed over its outer points, from the same FP32 decisions
+// (an undecided outer point counts its FP32 outcome; the count only orders the work).
+__global__ void k_cut_tris(FastArgs A, int* __restrict__ key) {
+    const int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= A.npairs) return;
+    const int64_t p = A.ids[pi];
+    const int k = A.pk[p], l = A.pl[p];
+    const int4 tk = A.T[k], tl = A.T[l];
+    const double2 v0k = A.X[tk.x], v0l = A.X[tl.x];
+    const float dx = (float)(v0l.x - v0k.x), dy = (float)(v0l.y - v0k.y);
+    const float4 Ek = A.E32[k], El = A.E32[l];
+    const float Wx[3] = {dx, dx + El.x, dx + El.z}, Wy[3] = {dy, dy + El.y, dy + El.w};
+    const int nqo = A.prm.ro.n;
+    int tris = 0;
+    for (int q0 = 0; q0 < nqo; ++q0) {
+        const float Xx = A.ol[q0][1] * Ek.x + A.ol[q0][2] * Ek.z;
+        const float Xy = A.ol[q0][1] * Ek.y + A.ol[q0][2] * Ek.w;
+        float Rx[3], Ry[3], Cc[3];
+        for (int m = 0; m < 3; ++m) {
+            Rx[m] = Wx[m] - Xx;
+            Ry[m] = Wy[m] - Xy;
+            Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - A.d2;
+        }
+        GeoF G;
+        decide_flat(Rx, Ry, Cc, 0.f, 0.f, A.d2, G);
+        int n = 0;
+        for (int e = 0; e < 3; ++e) n += (int)G.in[e] + G.nc[e];
+        if (A.caps && n >= 2 && !(G.in[0] && G.in[1] && G.in[2])) n += 1;  // at least one cap
+        tris += n >= 3 ? n - 2 : 0;
+    }
+    key[pi] = tris;
+}
+
+__global__ void k_bucket_flag(const int* __restrict__ key, int64_t n, int lo, int hi, int64_t* __restrict__ flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = key[i] >= lo && key[i] < hi;
+}
+
+__global__ void k_bucket_scatter(const int* __restrict__ ids, const int64_t* __restrict__ flag,
+                                 const int64_t* __restrict__ pos, int64_t n, int64_t base, int* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[base + pos[i]] = ids[i];
 }
 
 // Separated pairs with E_l inside the ball of every point of E_k: the whole inner element
@@ -385,12 +551,11 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(FastArgs A, float*
                                    dx + El.z - Xx, dy + El.w - Xy, 0.f, 1.f);
             outer_update<NC>(A, q0, dk, I, kk, kl, ll);
         }
-        write_block<NC, NE>(contrib + p * NE, kk, kl, ll);
+        write_pair<NC, NE>(contrib + p * NE, A.pcls[p] > 0, tk, tl, kk, kl, ll);
     }
 }
 
-void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st,
-                       cudaEvent_t* ev) {
+static FastArgs fast_args(Mesh& m, PairCache& pc, const Params& prm) {
     FastArgs a;
     a.pk = pc.pk.p; a.pl = pc.pl.p; a.pcls = pc.pcls.p;
     a.X = m.X.p; a.T = m.T.p; a.E32 = m.E32.p; a.det32 = m.det32.p;
@@ -408,32 +573,80 @@ void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib
     a.c = (float)prm.c;
     a.s = (float)prm.s;
     a.caps = prm.ball == NLFEM_BALL_APPROXCAPS;
-    const size_t FAST_SMEM = sizeof(float) * CHUNK * MAXPTS * 2 * FAST_THREADS;
-    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_CONSTANT, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
-    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_CONSTANT, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
-    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_FRACTIONAL, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
-    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_FRACTIONAL, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
-    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_PERIDYNAMIC, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
-    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_fast<NLFEM_KERNEL_PERIDYNAMIC, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FAST_SMEM));
+    a.ids = nullptr;
+    a.npairs = 0;
+    return a;
+}
+
+// Stable reorder of the cut list by fan-triangle count in 16 bands (pattern time).
+void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st) {
+    const int64_t n = pc.ncut;
+    if (n < 2) return;
+    FastArgs a = fast_args(m, pc, prm);
+    a.ids = pc.cut_ids.p;
+    a.npairs = n;
+    DBuf<int> key, out;
+    DBuf<int64_t> flag, pos;
+    key.alloc(n, st);
+    out.alloc(n, st);
+    flag.alloc(n, st);
+    pos.alloc(n + 1, st);
+    k_cut_tris<<<nblk(n, 256), 256, 0, st>>>(a, key.p);
+    NLFEM_LAUNCH_CHECK();
+    const int maxt = prm.ro.n * ((a.caps ? 9 : 6) - 2);
+    const int width = (maxt + 16) / 16;
+    int64_t base = 0;
+    for (int b = 0; b < 16; ++b) {
+        const int lo = b == 0 ? -1 : b * width, hi = b == 15 ? (1 << 30) : (b + 1) * width;
+        k_bucket_flag<<<nblk(n, 256), 256, 0, st>>>(key.p, n, lo, hi, flag.p);
+        NLFEM_LAUNCH_CHECK();
+        exclusive_scan_i64(flag.p, pos.p, n, st);
+        k_bucket_scatter<<<nblk(n, 256), 256, 0, st>>>(pc.cut_ids.p, flag.p, pos.p, n, base, out.p);
+        NLFEM_LAUNCH_CHECK();
+        int64_t cnt = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&cnt, pos.p + n, sizeof cnt, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        base += cnt;
+    }
+    if (base != n) throw Error{NLFEM_ERR_CUDA, "cut-pair ordering lost pairs"};
+    pc.cut_ids.swap_with(out);
+}
+
+template <int KER, int NQI, bool CAPS>
+static void launch_cut(const FastArgs& a, float* contrib, unsigned grid, cudaStream_t st) {
+    constexpr int MAXP = CAPS ? 9 : 6;
+    const size_t smem = sizeof(float2) * CHUNK * MAXP * FAST_THREADS;
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_cut<KER, NQI, CAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    k_trunc_cut<KER, NQI, CAPS><<<grid, FAST_THREADS, smem, st>>>(a, contrib);
+}
+
+template <int KER, int NQI>
+static void launch_pair_kernels(int pass, const FastArgs& a, float* contrib, unsigned grid, cudaStream_t st) {
+    if (pass == 0) k_trunc_whole<KER, NQI><<<grid, FAST_THREADS, 0, st>>>(a, contrib);
+    else if (a.caps) launch_cut<KER, NQI, true>(a, contrib, grid, st);
+    else launch_cut<KER, NQI, false>(a, contrib, grid, st);
+}
+
+void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st,
+                       cudaEvent_t* ev) {
+    FastArgs a = fast_args(m, pc, prm);
     for (int pass = 0; pass < 2; ++pass) {
         a.ids = pass == 0 ? pc.whole_ids.p : pc.cut_ids.p;
         a.npairs = pass == 0 ? pc.nwhole : pc.ncut;
         NLFEM_CUDA_TRY(cudaEventRecord(ev[pass], st));  // ev[0..2] bracket the two launches
-        unsigned grid = (unsigned)std::min<int64_t>(nblk(a.npairs, FAST_THREADS), 152 * 64);
+        const unsigned grid = (unsigned)std::min<int64_t>(nblk(a.npairs, FAST_THREADS), 152 * 64);
         if (!grid) continue;
-#define NLFEM_TF(KK, NQ)                                                                  \
-    do {                                                                                  \
-        if (pass == 0) k_trunc_whole<KK, NQ><<<grid, FAST_THREADS, 0, st>>>(a, contrib);  \
-        else k_trunc_fast<KK, NQ><<<grid, FAST_THREADS, FAST_SMEM, st>>>(a, contrib);     \
-    } while (0)
         if (prm.kernel == NLFEM_KERNEL_CONSTANT) {
-            if (prm.ri.n == 7) NLFEM_TF(NLFEM_KERNEL_CONSTANT, 7); else NLFEM_TF(NLFEM_KERNEL_CONSTANT, 16);
+            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_CONSTANT, 7>(pass, a, contrib, grid, st);
+            else launch_pair_kernels<NLFEM_KERNEL_CONSTANT, 16>(pass, a, contrib, grid, st);
         } else if (prm.kernel == NLFEM_KERNEL_FRACTIONAL) {
-            if (prm.ri.n == 7) NLFEM_TF(NLFEM_KERNEL_FRACTIONAL, 7); else NLFEM_TF(NLFEM_KERNEL_FRACTIONAL, 16);
+            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_FRACTIONAL, 7>(pass, a, contrib, grid, st);
+            else launch_pair_kernels<NLFEM_KERNEL_FRACTIONAL, 16>(pass, a, contrib, grid, st);
         } else {
-            if (prm.ri.n == 7) NLFEM_TF(NLFEM_KERNEL_PERIDYNAMIC, 7); else NLFEM_TF(NLFEM_KERNEL_PERIDYNAMIC, 16);
+            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_PERIDYNAMIC, 7>(pass, a, contrib, grid, st);
+            else launch_pair_kernels<NLFEM_KERNEL_PERIDYNAMIC, 16>(pass, a, contrib, grid, st);
         }
-#undef NLFEM_TF
         NLFEM_LAUNCH_CHECK();
     }
     NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
