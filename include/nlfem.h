@@ -213,6 +213,15 @@ int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t* elems, in
 /* Device memory held by a mesh handle and its cached pair list / pattern, in bytes. */
 int64_t nlfem_mesh_device_bytes(nlfem_mesh_t mesh);
 
+/*
+ * Working buffers are taken from the current device's default CUDA memory pool, which
+ * the library sets to keep freed blocks for reuse (no unmapping at every synchronisation).
+ * nlfem_trim_memory synchronises stream and returns every unused block of that pool to
+ * the driver. No counterpart in the paper (memory management of this implementation).
+ * Errors: CUDA.
+ */
+int nlfem_trim_memory(void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
         lib.nlfem_system_destroy.restype = None
         lib.nlfem_mesh_device_bytes.argtypes = [vp]
         lib.nlfem_mesh_device_bytes.restype = i64
+        lib.nlfem_trim_memory.argtypes = [vp]
         lib.nlfem_pairs_noalloc.argtypes = [vp, i64, vp, i64, dp, ip, ip, vp, vp, i64, C.POINTER(i64), vp]
         _lib = lib
     return _lib
@@ -212,6 +213,11 @@ def nlfem_system_destroy(sys):
 
 def nlfem_mesh_device_bytes(mesh) -> int:
     return int(load().nlfem_mesh_device_bytes(mesh))
+
+
+def nlfem_trim_memory(stream=None) -> None:
+    """Return the unused blocks of the device memory pool the library allocates from."""
+    _check(load().nlfem_trim_memory(_stream(stream)))
 
 
 def nlfem_pairs_noalloc(verts, elems, delta, ball, quad_outer, out_k, out_l, stream=None) -> int:

@@ -4,6 +4,9 @@
 #include <cstring>
 #include <new>
 
+#include <mutex>
+#include <vector>
+#include <algorithm>
 #include "nlfem_internal.cuh"
 #include "rules_table.h"
 
@@ -173,6 +176,37 @@ void nlfem_params_default(nlfem_params* p, int kernel) {
     p->mem_budget_bytes = 0;
 }
 
+// The library allocates its working buffers from the device's default memory pool
+// (stream-ordered). Freed blocks are kept in the pool for the next assembly instead of
+// being unmapped at every synchronisation (the pool's default); nlfem_trim_memory hands
+// them back.
+static void keep_pool_memory() {
+    int dev = 0;
+    NLFEM_CUDA_TRY(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> g(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+    cudaMemPool_t pool;
+    NLFEM_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t keep = UINT64_MAX;
+    NLFEM_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    done.push_back(dev);
+}
+
+int nlfem_trim_memory(void* stream) {
+    NLFEM_API_BEGIN
+    set_error("");
+    int dev = 0;
+    NLFEM_CUDA_TRY(cudaGetDevice(&dev));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    cudaMemPool_t pool;
+    NLFEM_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    NLFEM_CUDA_TRY(cudaMemPoolTrimTo(pool, 0));
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
 int nlfem_mesh_create(const double* verts, int64_t M, const int32_t* elems, int64_t K,
                       const int8_t* elem_label, int ndof_per_node, void* stream, nlfem_mesh_t* out) {
     NLFEM_API_BEGIN
@@ -184,6 +218,7 @@ int nlfem_mesh_create(const double* verts, int64_t M, const int32_t* elems, int6
     NLFEM_CHECK(M < (1ll << 31) && K < (1ll << 31) / 3, NLFEM_ERR_UNSUPPORTED, "mesh too large for 32-bit indices");
     NLFEM_CHECK(ndof_per_node == 1 || ndof_per_node == 2, NLFEM_ERR_INVALID_ARG, "ndof_per_node must be 1 or 2");
     cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_memory();
     nlfem_mesh_s* h = new nlfem_mesh_s();
     try {
         Mesh& m = h->m;
@@ -260,6 +295,7 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
             order_cut_pairs(m, *pc, P, st);
             NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
             build_pattern(m, *pc, st);
+            build_bulk_index(m, *pc, st);
             NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
             NLFEM_CUDA_TRY(cudaEventSynchronize(ev[2]));
             t_pairs = elapsed_ms(ev[0], ev[1]);
@@ -270,8 +306,13 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
         m.cache = pc;
     }
     const int64_t NE = contrib_entries(P.ndof);
-    const size_t esz = P.precision == NLFEM_PREC_FP32_BULK ? sizeof(float) : sizeof(double);
-    int64_t need = (int64_t)(pc->npairs * NE * esz) + pc->nnz * 8 + pc->N * 8 + m.device_bytes();
+    // working memory of the values: per-pair records (FP64 plain) or the fixed-point upper
+    // entries plus the close-list records (FP32 bulk)
+    const int64_t work = P.precision == NLFEM_PREC_FP32_BULK
+                             ? pc->n_upper * (P.ndof == 1 ? 1 : 3) * 8 + pc->nduffy * NE * 4 +
+                                   pc->npairs * 12 * (P.ndof == 1 ? 1 : 3) * 4
+                             : pc->npairs * NE * 8;
+    int64_t need = work + pc->nnz * 8 + pc->N * 8 + m.device_bytes();
     if (params->mem_budget_bytes > 0 && need > params->mem_budget_bytes)
         throw Error{NLFEM_ERR_BUDGET, "assembly needs " + std::to_string(need) + " device bytes, budget is " +
                                           std::to_string(params->mem_budget_bytes)};
@@ -285,8 +326,7 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
         S.nnz = pc->nnz;
         S.val.alloc(pc->nnz, st);
         S.F.alloc(pc->N, st);
-        if (P.precision == NLFEM_PREC_FP32_BULK) S.contrib32.alloc(pc->npairs * NE, st);
-        else S.contrib64.alloc(pc->npairs * NE, st);
+        if (P.precision != NLFEM_PREC_FP32_BULK) S.contrib64.alloc(pc->npairs * NE, st);
         DBuf<double> fdev;
         const double* fptr = nullptr;
         if (f_nodal) {
@@ -306,6 +346,7 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
         // contributions are no longer needed once reduced
         S.contrib32.release();
         S.contrib64.release();
+        S.acc.release();
         nlfem_assembly_info& I = S.info;
         std::memset(&I, 0, sizeof I);
         I.npairs = pc->npairs;

@@ -154,8 +154,14 @@ struct PairCache {
     DBuf<int64_t> pbase;     // [M] first pair id a node row refers to
     int64_t ncontrib = 0;
     DBuf<int64_t> up_pos;    // node-level upper entries (i, j >= i): pattern position
-    DBuf<int> up_row;        //   and row i
+    DBuf<int> up_row;        //   and row i (built with the slot index, for the ordered reduction)
     int64_t n_upper = 0;
+    bool slots_built = false;
+    // FP32-bulk accumulation index: upper entries numbered row by row in node order
+    DBuf<int64_t> up_start;  // [M + 1] first upper entry of each node row
+    DBuf<int> epos;          // [K * 6] upper entry of each node pair of an element
+    DBuf<uint16_t> klr_whole, klr_cut;  // [9][list length] rank of (k_a, l_b) in row min(k_a, l_b)
+    int64_t acc_terms = 0;   // bound on the number of values added into one upper entry
     double t_pairs_ms = 0, t_pattern_ms = 0;
 };
 
@@ -168,8 +174,11 @@ struct System {
     int64_t N = 0, nnz = 0;
     DBuf<double> val;        // [nnz]
     DBuf<double> F;          // [N]
-    DBuf<float> contrib32;   // [P * NE]
-    DBuf<double> contrib64;
+    DBuf<float> contrib32;   // records [P * NE] (FP32 bulk: only the close-list pairs, in list order)
+    DBuf<double> contrib64;  // records [P * NE] (FP64 plain)
+    DBuf<unsigned long long> acc;  // FP32 bulk: fixed-point upper entries [n_upper * NC]
+    DBuf<float> kkll;        // FP32 bulk: kk and ll of every pair [P * 12 NC]
+    int acc_shift = 0;       // FP32 bulk: the values were scaled by 2^acc_shift
     nlfem_assembly_info info;
     std::shared_ptr<SolveState> solver;
 };
@@ -184,10 +193,24 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st);
 void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev);
 void run_reduction(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st);
 void run_load(Mesh& m, const Params& prm, const double* f_nodal, System& sys, cudaStream_t st);
+// per-pair contribution record: 21 scalar entries padded to 24, 84 peridynamic components
+// padded to 88, so that in FP32 and FP64 a record covers whole 32-byte sectors
+constexpr int NLFEM_REC1 = 24, NLFEM_REC2 = 88;
 int64_t contrib_entries(int ndof);
 void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStream_t st);
-void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st,
+// fixed-point accumulation of the FP32-bulk kernels; acc == nullptr: pilot pass that only
+// records the largest |value| of every pstride-th pair
+struct BulkAcc {
+    unsigned long long* acc;
+    float* kkll;  // [P][12 NC] per-pair kk and ll records
+    float scale;
+    unsigned int* maxabs;
+    int64_t pstride;
+};
+void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, const BulkAcc& b, cudaStream_t st,
                        cudaEvent_t* ev);
+void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st);
+void build_slots(Mesh& m, PairCache& pc, cudaStream_t st);
 void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st);
 inline int close_mode(const Params& P) { return P.singular ? 1 : (P.nozerodiv ? 2 : 0); }
 int solve_system(System& S, const double* g, double tol, int max_iter, double* u_out, nlfem_solve_info* info,
@@ -200,8 +223,29 @@ void segmented_sort_i32(int* keys, int* vals, const int64_t* ptr, int64_t nseg, 
                         cudaStream_t st);
 
 double elapsed_ms(cudaEvent_t a, cudaEvent_t b);
+// largest ptr[i + 1] - ptr[i] over i < n
+int64_t max_segment_i64(const int64_t* ptr, int64_t n, cudaStream_t st);
 
 }  // namespace nlfem
+
+// rank of column hi among the columns >= lo of node row lo of the node-level pattern (the
+// diagonal has rank 0); -1 if the column is missing
+__device__ __forceinline__ int upper_rank(const int64_t* __restrict__ nptr, const int* __restrict__ ncol, int lo,
+                                          int hi) {
+    const int64_t b = nptr[lo], e = nptr[lo + 1];
+    auto lower = [&](int v) {
+        int64_t a = b, c = e;
+        while (a < c) {
+            const int64_t mid = (a + c) >> 1;
+            if (ncol[mid] < v) a = mid + 1;
+            else c = mid;
+        }
+        return a;
+    };
+    const int64_t ph = lower(hi), pd = lower(lo);
+    if (ph >= e || ncol[ph] != hi || pd >= e || ncol[pd] != lo) return -1;
+    return (int)(ph - pd);
+}
 
 // ------------------------------------------------------------------------------------------
 // canonical FP64 geometry (shared by all kernels of this library)
@@ -409,7 +453,7 @@ __device__ __forceinline__ bool nl_decide32(const float Rx[3], const float Ry[3]
 __device__ __forceinline__ int nl_count32(const Geo32& g, bool caps) {
     if (g.in[0] && g.in[1] && g.in[2]) return 3;
     int nraw = 0, ncap = 0;
-    int fe = 0, fv = 0, le = 0, lv = 0;  // first / last raw point: edge and vertex flag
+    int fe = 0, fv = 0, le = 0;  // first / last raw point: edge and vertex flag
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         const int cnt = (g.in[e] ? 1 : 0) + g.nc[e];
@@ -419,11 +463,9 @@ __device__ __forceinline__ int nl_count32(const Geo32& g, bool caps) {
             if (nraw > 0 && le != e && !(v && e == (le + 1) % 3)) ++ncap;
             if (nraw == 0) { fe = e; fv = v; }
             le = e;
-            lv = v;
             ++nraw;
         }
     }
-    (void)lv;
     // wrap-around last -> first: joined only if first is the vertex that starts the edge after
     // last's (on one edge the first point never has the larger parameter)
     if (nraw >= 2 && !(fv && fe == (le + 1) % 3)) ++ncap;

@@ -217,7 +217,7 @@ __global__ void k_max_seg64(const int64_t* ptr, int64_t n, unsigned long long* o
     if (i < n) atomicMax(out, (unsigned long long)(ptr[i + 1] - ptr[i]));
 }
 
-static int64_t max_segment(const int64_t* ptr, int64_t n, cudaStream_t st) {
+int64_t max_segment_i64(const int64_t* ptr, int64_t n, cudaStream_t st) {
     DBuf<unsigned long long> mx;
     mx.alloc(1, st);
     mx.zero(st);
@@ -289,7 +289,7 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     pc.pk.alloc(P, st);
     k_search<true><<<nblk(K * 32, 128), 128, 0, st>>>(a, nullptr, pc.pair_ptr.p, pc.pl.p);
     NLFEM_LAUNCH_CHECK();
-    int64_t mx = max_segment(pc.pair_ptr.p, K, st);
+    int64_t mx = max_segment_i64(pc.pair_ptr.p, K, st);
     segmented_sort_i32(pc.pl.p, nullptr, pc.pair_ptr.p, K, (int)std::min<int64_t>(mx, 1 << 30), st);
     k_fill_k<<<nblk(K * 32, 256), 256, 0, st>>>(pc.pair_ptr.p, K, pc.pk.p);
     NLFEM_LAUNCH_CHECK();
@@ -316,7 +316,7 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
         k_fill_T<<<nblk(P, 256), 256, 0, st>>>(pc.pl.p, P, pc.pT_ptr.p, tcur.p, pc.pT_id.p);
         NLFEM_LAUNCH_CHECK();
     }
-    int64_t mxT = max_segment(pc.pT_ptr.p, K, st);
+    int64_t mxT = max_segment_i64(pc.pT_ptr.p, K, st);
     segmented_sort_i32(pc.pT_id.p, nullptr, pc.pT_ptr.p, K, (int)std::min<int64_t>(mxT, 1 << 30), st);
     unsigned long long hc[4];
     NLFEM_CUDA_TRY(cudaMemcpyAsync(hc, counts.p, sizeof hc, cudaMemcpyDeviceToHost, st));

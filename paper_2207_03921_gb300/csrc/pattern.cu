@@ -9,9 +9,11 @@
 //
 // Contributions of one pair: entry E(a,b), 0 <= a <= b < 6, of the union block
 // (union = vertices of E_k, then the vertices of E_l not in E_k). Scalar: 21 values per
-// pair; peridynamics: 4 components (c1, c2) per entry, 84 values per pair.
+// pair; peridynamics: 4 components (c1, c2) per entry, 84 values per pair. Records are
+// padded to 24 / 88 values so that no two pairs share a 32-byte sector.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "nlfem_internal.cuh"
 
@@ -23,7 +25,7 @@ __device__ __constant__ int c_E1[6][6] = {
     {0, 1, 2, 3, 4, 5}, {1, 6, 7, 8, 9, 10}, {2, 7, 11, 12, 13, 14},
     {3, 8, 12, 15, 16, 17}, {4, 9, 13, 16, 18, 19}, {5, 10, 14, 17, 19, 20}};
 
-int64_t contrib_entries(int ndof) { return ndof == 1 ? 21 : 84; }
+int64_t contrib_entries(int ndof) { return ndof == 1 ? NLFEM_REC1 : NLFEM_REC2; }
 
 static constexpr int MAX_NE = 32;  // elements per node handled by the row enumeration
 
@@ -354,6 +356,9 @@ __device__ __forceinline__ double warp_total_c(CSum c) {
     return (double)c.hi + (double)c.lo;
 }
 
+// Half a warp per upper entry (two entries per warp in flight); each lane issues the loads
+// of its first four contributions before summing them, so a lane keeps up to eight
+// independent loads in flight. The order of the sum is fixed by the slot index.
 template <typename R, int NDOF>
 __global__ void __launch_bounds__(256) k_reduce(int64_t n_upper, const int64_t* __restrict__ up_pos,
                                                 const int* __restrict__ up_row, const int64_t* __restrict__ nptr,
@@ -361,65 +366,115 @@ __global__ void __launch_bounds__(256) k_reduce(int64_t n_upper, const int64_t* 
                                                 const uint32_t* __restrict__ idx, const int64_t* __restrict__ pbase,
                                                 const R* __restrict__ contrib, const int64_t* __restrict__ row_ptr,
                                                 const int64_t* __restrict__ tpos, double* __restrict__ val) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int NE = NDOF == 1 ? 21 : 84;
-    for (int64_t u = wid; u < n_upper; u += nw) {
-        const int64_t t = up_pos[u];  // node-level pattern position
-        const int i = up_row[u];
-        const int j = ncol[t];
-        const int64_t s0 = seg_ptr[t], s1 = seg_ptr[t + 1];
-        const int64_t pb = pbase[i];
-        if (NDOF == 1) {
-            double v;
-            if (sizeof(R) == 4) {
-                CSum c{0.f, 0.f};
-                for (int64_t q = s0 + lane; q < s1; q += 32) {
-                    const uint32_t e = idx[q];
-                    two_sum_add(c, (float)contrib[(pb + (e >> 6)) * NE + (e & 31)]);
-                }
-                v = warp_total_c(c);
-            } else {
-                double a = 0.0;
-                for (int64_t q = s0 + lane; q < s1; q += 32) {
-                    const uint32_t e = idx[q];
-                    a += (double)contrib[(pb + (e >> 6)) * NE + (e & 31)];
-                }
-                v = warp_total<double>(a);
-            }
-            if (lane == 0) {
-                const int64_t s = row_ptr[i] + (t - nptr[i]);
-                val[s] = v;
-                val[tpos[s]] = v;
-            }
+    constexpr int SUB = 16;
+    constexpr int NS = NDOF == 1 ? NLFEM_REC1 : NLFEM_REC2;  // record stride
+    constexpr int NCOMP = NDOF == 1 ? 1 : 4;
+    constexpr int UNR = 4;
+    const int sl = threadIdx.x & (SUB - 1);
+    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB;
+    const bool live = u < n_upper;  // every lane reaches the shuffles below
+    int64_t t = 0, s0 = 0, s1 = 0, pb = 0;
+    int i = 0;
+    if (live) {
+        t = up_pos[u];
+        i = up_row[u];
+        s0 = seg_ptr[t];
+        s1 = seg_ptr[t + 1];
+        pb = pbase[i];
+    }
+    using Acc = typename std::conditional<sizeof(R) == 4, CSum, double>::type;
+    Acc acc[NCOMP];
+#pragma unroll
+    for (int k = 0; k < NCOMP; ++k) {
+        if constexpr (sizeof(R) == 4) acc[k] = CSum{0.f, 0.f};
+        else acc[k] = 0.0;
+    }
+    auto load = [&](uint32_t e, R (&x)[NCOMP]) {
+        const R* cp = contrib + (pb + (int64_t)(e >> 6)) * NS + (e & 31) * NCOMP;
+        if constexpr (NDOF == 1) {
+            x[0] = cp[0];
         } else {
-            CSum c[4];
-            double a[4] = {0, 0, 0, 0};
-            for (int k = 0; k < 4; ++k) c[k] = CSum{0.f, 0.f};
-            for (int64_t q = s0 + lane; q < s1; q += 32) {
-                const uint32_t e = idx[q];
-                const R* cp = contrib + (pb + (e >> 6)) * NE + (e & 31) * 4;
-                const bool tr = (e >> 5) & 1;
-                const R x[4] = {cp[0], tr ? cp[2] : cp[1], tr ? cp[1] : cp[2], cp[3]};
-                for (int k = 0; k < 4; ++k) {
-                    if (sizeof(R) == 4) two_sum_add(c[k], (float)x[k]);
-                    else a[k] += (double)x[k];
-                }
+            const bool tr = (e >> 5) & 1;  // the entry was stored for (j, i): swap xy and yx
+            R y[4];
+            if constexpr (sizeof(R) == 4) {
+                const float4 f = *reinterpret_cast<const float4*>(cp);
+                y[0] = f.x; y[1] = f.y; y[2] = f.z; y[3] = f.w;
+            } else {
+                y[0] = cp[0]; y[1] = cp[1]; y[2] = cp[2]; y[3] = cp[3];
             }
-            double v[4];
-            for (int k = 0; k < 4; ++k) v[k] = sizeof(R) == 4 ? warp_total_c(c[k]) : warp_total<double>(a[k]);
-            if (lane == 0) {
-                const int64_t r = t - nptr[i];
-                for (int c1 = 0; c1 < 2; ++c1)
-                    for (int c2 = 0; c2 < 2; ++c2) {
-                        if (j == i && c2 < c1) continue;  // the diagonal node block: upper dofs only
-                        const int64_t s = row_ptr[(int64_t)i * 2 + c1] + 2 * r + c2;
-                        val[s] = v[c1 * 2 + c2];
-                        val[tpos[s]] = v[c1 * 2 + c2];
-                    }
-            }
+            x[0] = y[0];
+            x[1] = tr ? y[2] : y[1];
+            x[2] = tr ? y[1] : y[2];
+            x[3] = y[3];
         }
+    };
+    auto add = [&](const R (&x)[NCOMP]) {
+#pragma unroll
+        for (int k = 0; k < NCOMP; ++k) {
+            if constexpr (sizeof(R) == 4) two_sum_add(acc[k], x[k]);
+            else acc[k] += x[k];
+        }
+    };
+    {
+        uint32_t e[UNR];
+#pragma unroll
+        for (int r = 0; r < UNR; ++r) {
+            const int64_t q = s0 + sl + (int64_t)SUB * r;
+            e[r] = q < s1 ? idx[q] : 0u;
+        }
+        R x[UNR][NCOMP];
+#pragma unroll
+        for (int r = 0; r < UNR; ++r)
+            if (s0 + sl + (int64_t)SUB * r < s1) load(e[r], x[r]);
+#pragma unroll
+        for (int r = 0; r < UNR; ++r)
+            if (s0 + sl + (int64_t)SUB * r < s1) add(x[r]);
+    }
+    for (int64_t q = s0 + sl + (int64_t)SUB * UNR; q < s1; q += SUB) {
+        R x[NCOMP];
+        load(idx[q], x);
+        add(x);
+    }
+    // fixed butterfly over the half warp; the two operands are combined in a lane-independent
+    // order, so all lanes agree to the last bit
+    double v[NCOMP];
+#pragma unroll
+    for (int k = 0; k < NCOMP; ++k) {
+        if constexpr (sizeof(R) == 4) {
+            CSum c = acc[k];
+#pragma unroll
+            for (int o = SUB / 2; o > 0; o >>= 1) {
+                CSum d;
+                d.hi = __shfl_xor_sync(0xffffffffu, c.hi, o);
+                d.lo = __shfl_xor_sync(0xffffffffu, c.lo, o);
+                CSum a = (sl & o) ? d : c, b = (sl & o) ? c : d;
+                two_sum_merge(a, b);
+                c = a;
+            }
+            v[k] = 0.0;
+            if (sl == 0) v[k] = (double)c.hi + (double)c.lo;
+        } else {
+            double a = acc[k];
+#pragma unroll
+            for (int o = SUB / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            v[k] = a;
+        }
+    }
+    if (!live || sl != 0) return;
+    if constexpr (NDOF == 1) {
+        const int64_t s = row_ptr[i] + (t - nptr[i]);
+        val[s] = v[0];
+        val[tpos[s]] = v[0];
+    } else {
+        const int j = ncol[t];
+        const int64_t r = t - nptr[i];
+        for (int c1 = 0; c1 < 2; ++c1)
+            for (int c2 = 0; c2 < 2; ++c2) {
+                if (j == i && c2 < c1) continue;  // the diagonal node block: upper dofs only
+                const int64_t s = row_ptr[(int64_t)i * 2 + c1] + 2 * r + c2;
+                val[s] = v[c1 * 2 + c2];
+                val[tpos[s]] = v[c1 * 2 + c2];
+            }
     }
 }
 
@@ -433,17 +488,20 @@ __global__ void k_upper_count(const int64_t* nptr, const int* ncol, int64_t M, i
     cnt[i] = c;
 }
 
-// node rows in the order of 2D tiles (cells of a uniform grid over the mesh, rows of a
-// cell by node index): warps running at the same time then touch the contributions of a
-// compact patch of elements, which stays in L2
-__global__ void k_node_cell(const double2* X, int64_t M, double x0, double y0, double cs, int nx, int ny,
+// node rows in strip-sweep order: cells of a uniform grid about one node spacing wide are
+// grouped into vertical strips of SW cells, the strips are taken left to right and each is
+// swept bottom to top row of cells by row of cells (rows of a cell by node index). The
+// entries in flight then lie in a band a few cell rows high inside one strip, and the
+// rows of any pair's nodes (at most delta + 2h apart) are reached within a few strip
+// widths of rows of each other, so the pair's contributions are re-read from L2.
+__global__ void k_node_cell(const double2* X, int64_t M, double x0, double y0, double cs, int nx, int ny, int sw,
                             int64_t* cnt, int* cell) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     double2 v = X[i];
     int cx = min(nx - 1, max(0, (int)floor((v.x - x0) / cs)));
     int cy = min(ny - 1, max(0, (int)floor((v.y - y0) / cs)));
-    int c = cy * nx + cx;
+    int c = ((cx / sw) * ny + cy) * sw + (cx % sw);
     cell[i] = c;
     atomicAdd((unsigned long long*)&cnt[c], 1ull);
 }
@@ -540,6 +598,27 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
         NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
         NLFEM_CHECK(!h, NLFEM_ERR_CUDA, "internal error: the CSR pattern is not symmetric");
     }
+    // upper entries per row (node order): the numbering of the FP32-bulk accumulators
+    {
+        DBuf<int64_t> ucnt;
+        ucnt.alloc(M, st);
+        k_upper_count<<<nblk(M, 256), 256, 0, st>>>(pc.nrow_ptr.p, pc.ncol.p, M, ucnt.p);
+        NLFEM_LAUNCH_CHECK();
+        pc.up_start.alloc(M + 1, st);
+        exclusive_scan_i64(ucnt.p, pc.up_start.p, M, st);
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.n_upper, pc.up_start.p + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    pc.slots_built = false;
+}
+
+// Slot index and the ordered list of upper entries of the ordered reduction (FP64 path),
+// built on first use.
+void build_slots(Mesh& m, PairCache& pc, cudaStream_t st) {
+    const int64_t M = m.M;
+    RowEnum R{m.ne_ptr.p, m.ne_idx.p, pc.pair_ptr.p, pc.pT_ptr.p, pc.pT_id.p, pc.pk.p, pc.pl.p, m.T.p};
+    DBuf<int> ovf;
+    ovf.alloc(1, st);
     // slot index
     DBuf<int64_t> segcnt;
     segcnt.alloc(pc.nnz_node, st);
@@ -572,7 +651,7 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
     order.alloc(M, st);
     {
         const double W = m.bbox[2] - m.bbox[0], H = m.bbox[3] - m.bbox[1];
-        double cs = std::sqrt(std::max(W * H, 1e-300) / (double)M) * 16.0;  // about 256 nodes per tile
+        double cs = std::sqrt(std::max(W * H, 1e-300) / (double)M);  // about one node per cell
         if (!(cs > 0)) cs = 1.0;
         int nx = std::max(1, (int)std::ceil(W / cs)), ny = std::max(1, (int)std::ceil(H / cs));
         while ((int64_t)nx * ny > (1 << 22)) {
@@ -580,7 +659,8 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
             nx = std::max(1, (int)std::ceil(W / cs));
             ny = std::max(1, (int)std::ceil(H / cs));
         }
-        const int64_t nc = (int64_t)nx * ny;
+        const int sw = std::min(nx, 128);  // strip width in cells
+        const int64_t nc = (int64_t)((nx + sw - 1) / sw) * ny * sw;
         DBuf<int64_t> ccnt, cstart;
         DBuf<int> cell, cur;
         ccnt.alloc(nc, st);
@@ -589,7 +669,7 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
         cell.alloc(M, st);
         cur.alloc(nc, st);
         cur.zero(st);
-        k_node_cell<<<nblk(M, 256), 256, 0, st>>>(m.X.p, M, m.bbox[0], m.bbox[1], cs, nx, ny, ccnt.p, cell.p);
+        k_node_cell<<<nblk(M, 256), 256, 0, st>>>(m.X.p, M, m.bbox[0], m.bbox[1], cs, nx, ny, sw, ccnt.p, cell.p);
         NLFEM_LAUNCH_CHECK();
         exclusive_scan_i64(ccnt.p, cstart.p, nc, st);
         k_node_place<<<nblk(M, 256), 256, 0, st>>>(cell.p, M, cstart.p, cur.p, order.p);
@@ -614,34 +694,169 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
     k_gather_i64<<<nblk(M, 256), 256, 0, st>>>(ucnt.p, order.p, M, ucnt_o.p);
     NLFEM_LAUNCH_CHECK();
     exclusive_scan_i64(ucnt_o.p, uoff.p, M, st);
-    NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.n_upper, uoff.p + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
     pc.up_pos.alloc(pc.n_upper, st);
     pc.up_row.alloc(pc.n_upper, st);
     k_upper_fill<<<nblk(M, 256), 256, 0, st>>>(pc.nrow_ptr.p, pc.ncol.p, M, uoff.p, pc.up_pos.p, pc.up_row.p,
                                                order.p);
     NLFEM_LAUNCH_CHECK();
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    pc.slots_built = true;
+}
+
+// ------------------------------------------------------------------------------------------
+// FP32-bulk accumulation index and the conversion of the fixed-point sums into CSR values
+// ------------------------------------------------------------------------------------------
+__global__ void k_epos(const int4* __restrict__ T, int64_t K, const int64_t* __restrict__ nptr,
+                       const int* __restrict__ ncol, const int64_t* __restrict__ up_start, int* __restrict__ epos,
+                       int* ovf) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int4 t = T[k];
+    const int n[3] = {t.x, t.y, t.z};
+    const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+    for (int e = 0; e < 6; ++e) {
+        const int i = n[pa[e]], j = n[pb[e]], lo = min(i, j), hi = max(i, j);
+        const int r = upper_rank(nptr, ncol, lo, hi);
+        if (r < 0) atomicOr(ovf, 1);
+        const int64_t u = up_start[lo] + max(r, 0);
+        if (u > 0x7fffffffll) atomicOr(ovf, 4);
+        epos[k * 6 + e] = (int)u;
+    }
+}
+
+__global__ void k_klr(const int* __restrict__ ids, int64_t n, const int* __restrict__ pk, const int* __restrict__ pl,
+                      const int4* __restrict__ T, const int64_t* __restrict__ nptr, const int* __restrict__ ncol,
+                      uint16_t* __restrict__ klr, int* ovf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = ids[i];
+    const int4 a4 = T[pk[p]], b4 = T[pl[p]];
+    const int kn[3] = {a4.x, a4.y, a4.z}, ln[3] = {b4.x, b4.y, b4.z};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const int x = kn[a], y = ln[b];
+            const int r = upper_rank(nptr, ncol, min(x, y), max(x, y));
+            if (r < 0) atomicOr(ovf, 1);
+            if (r > 65535) atomicOr(ovf, 2);
+            klr[(int64_t)(a * 3 + b) * n + i] = (uint16_t)min(max(r, 0), 65535);
+        }
+}
+
+__global__ void k_max_deg(const int* ne_ptr, int64_t M, int* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) atomicMax(out, ne_ptr[i + 1] - ne_ptr[i]);
+}
+
+void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st) {
+    const int64_t K = m.K;
+    DBuf<int> ovf;
+    ovf.alloc(1, st);
+    ovf.zero(st);
+    pc.epos.alloc(K * 6, st);
+    k_epos<<<nblk(K, 256), 256, 0, st>>>(m.T.p, K, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, pc.epos.p, ovf.p);
+    NLFEM_LAUNCH_CHECK();
+    pc.klr_whole.alloc(pc.nwhole * 9, st);
+    pc.klr_cut.alloc(pc.ncut * 9, st);
+    if (pc.nwhole > 0) {
+        k_klr<<<nblk(pc.nwhole, 256), 256, 0, st>>>(pc.whole_ids.p, pc.nwhole, pc.pk.p, pc.pl.p, m.T.p, pc.nrow_ptr.p,
+                                                    pc.ncol.p, pc.klr_whole.p, ovf.p);
+        NLFEM_LAUNCH_CHECK();
+    }
+    if (pc.ncut > 0) {
+        k_klr<<<nblk(pc.ncut, 256), 256, 0, st>>>(pc.cut_ids.p, pc.ncut, pc.pk.p, pc.pl.p, m.T.p, pc.nrow_ptr.p,
+                                                  pc.ncol.p, pc.klr_cut.p, ovf.p);
+        NLFEM_LAUNCH_CHECK();
+    }
+    // bound on the values added into one entry: every pair with the node in E_k or in E_l
+    // adds at most three values (kk, ll, kl) into a diagonal entry, fewer elsewhere
+    DBuf<int> md;
+    md.alloc(1, st);
+    md.zero(st);
+    k_max_deg<<<nblk(m.M, 256), 256, 0, st>>>(m.ne_ptr.p, m.M, md.p);
+    NLFEM_LAUNCH_CHECK();
+    int h[2] = {0, 0};
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&h[0], ovf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&h[1], md.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    NLFEM_CHECK(!(h[0] & 1), NLFEM_ERR_CUDA, "internal error: a pair's node pair is missing from the CSR pattern");
+    NLFEM_CHECK(!(h[0] & 2), NLFEM_ERR_UNSUPPORTED, "a CSR row has more than 65536 upper entries");
+    NLFEM_CHECK(!(h[0] & 4), NLFEM_ERR_UNSUPPORTED, "more than 2^31 upper CSR entries");
+    const int64_t maxp = std::max(max_segment_i64(pc.pair_ptr.p, K, st), max_segment_i64(pc.pT_ptr.p, K, st));
+    pc.acc_terms = 3 * (int64_t)std::max(h[1], 1) * 2 * std::max<int64_t>(maxp, 1);
+}
+
+// fixed-point upper entries -> CSR values (and their mirrors); warp per node row
+template <int NDOF>
+__global__ void k_acc_to_csr(int64_t M, const int64_t* __restrict__ nptr, const int* __restrict__ ncol,
+                             const int64_t* __restrict__ up_start, const unsigned long long* __restrict__ acc,
+                             double inv_scale, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tpos,
+                             double* __restrict__ val) {
+    constexpr int NC = NDOF == 1 ? 1 : 3;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= M) return;
+    const int64_t b = nptr[i], e = nptr[i + 1];
+    // position of the diagonal: the first column >= i
+    int64_t a = b, c = e;
+    while (a < c) {
+        const int64_t mid = (a + c) >> 1;
+        if (ncol[mid] < (int)i) a = mid + 1;
+        else c = mid;
+    }
+    const int64_t td = a, u0 = up_start[i];
+    for (int64_t t = td + lane; t < e; t += 32) {
+        const int64_t u = u0 + (t - td);
+        double v[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) v[q] = (double)(long long)acc[u * NC + q] * inv_scale;
+        if (NDOF == 1) {
+            const int64_t s = row_ptr[i] + (t - b);
+            val[s] = v[0];
+            val[tpos[s]] = v[0];
+        } else {
+            const int j = ncol[t];
+            const int64_t r = t - b;
+            const double comp[4] = {v[0], v[1], v[1], v[2]};  // xx, xy, yx, yy
+            for (int c1 = 0; c1 < 2; ++c1)
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    if (j == (int)i && c2 < c1) continue;  // the diagonal node block: upper dofs only
+                    const int64_t s = row_ptr[i * 2 + c1] + 2 * r + c2;
+                    val[s] = comp[c1 * 2 + c2];
+                    val[tpos[s]] = comp[c1 * 2 + c2];
+                }
+        }
+    }
 }
 
 void run_reduction(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st) {
-    (void)m;
+    if (prm.precision == NLFEM_PREC_FP32_BULK) {
+        // every upper entry is written with its mirror, so val needs no clearing
+        const double inv = std::ldexp(1.0, -sys.acc_shift);
+        const unsigned g = nblk(m.M * 32, 256);
+        if (m.M == 0) return;
+        if (pc.ndof == 1)
+            k_acc_to_csr<1><<<g, 256, 0, st>>>(m.M, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, sys.acc.p, inv,
+                                               pc.row_ptr.p, pc.tpos.p, sys.val.p);
+        else
+            k_acc_to_csr<2><<<g, 256, 0, st>>>(m.M, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, sys.acc.p, inv,
+                                               pc.row_ptr.p, pc.tpos.p, sys.val.p);
+        NLFEM_LAUNCH_CHECK();
+        return;
+    }
+    if (!pc.slots_built) build_slots(m, pc, st);
     NLFEM_CUDA_TRY(cudaMemsetAsync(sys.val.p, 0, sys.val.bytes(), st));
     if (pc.n_upper == 0) return;
-    // one warp per entry, blocks dispatched in order: the entries in flight stay a compact set
-    // of tiles (a grid-stride loop would scatter them over the whole mesh)
-    const unsigned g = (unsigned)std::min<int64_t>(nblk(pc.n_upper * 32, 256), 0x7fffffffll);
-#define NLFEM_RED(R, ND, C)                                                                             \
-    k_reduce<R, ND><<<g, 256, 0, st>>>(pc.n_upper, pc.up_pos.p, pc.up_row.p, pc.nrow_ptr.p, pc.ncol.p,  \
-                                       pc.seg_ptr.p, pc.idx.p, pc.pbase.p, C, pc.row_ptr.p, pc.tpos.p, \
-                                       sys.val.p)
-    if (prm.precision == NLFEM_PREC_FP32_BULK) {
-        if (pc.ndof == 1) NLFEM_RED(float, 1, sys.contrib32.p);
-        else NLFEM_RED(float, 2, sys.contrib32.p);
-    } else {
-        if (pc.ndof == 1) NLFEM_RED(double, 1, sys.contrib64.p);
-        else NLFEM_RED(double, 2, sys.contrib64.p);
-    }
-#undef NLFEM_RED
+    // half a warp per entry, blocks dispatched in order: the entries in flight stay a compact
+    // band of the strip-ordered rows (a grid-stride loop would scatter them over the mesh)
+    const unsigned g = (unsigned)std::min<int64_t>(nblk(pc.n_upper * 16, 256), 0x7fffffffll);
+    if (pc.ndof == 1)
+        k_reduce<double, 1><<<g, 256, 0, st>>>(pc.n_upper, pc.up_pos.p, pc.up_row.p, pc.nrow_ptr.p, pc.ncol.p,
+                                               pc.seg_ptr.p, pc.idx.p, pc.pbase.p, sys.contrib64.p, pc.row_ptr.p,
+                                               pc.tpos.p, sys.val.p);
+    else
+        k_reduce<double, 2><<<g, 256, 0, st>>>(pc.n_upper, pc.up_pos.p, pc.up_row.p, pc.nrow_ptr.p, pc.ncol.p,
+                                               pc.seg_ptr.p, pc.idx.p, pc.pbase.p, sys.contrib64.p, pc.row_ptr.p,
+                                               pc.tpos.p, sys.val.p);
     NLFEM_LAUNCH_CHECK();
 }
 

@@ -15,6 +15,8 @@
 // k_load: F_i = sum over Omega elements of sum_p a_p f(x_p) phi_i(x_p), thread per node.
 #include <algorithm>
 
+#include <cstring>
+
 #include "nlfem_internal.cuh"
 
 namespace nlfem {
@@ -32,6 +34,7 @@ struct QuadArgs {
     const int8_t* whole;   // census only: 1 if the pair is in the whole-pair list, 2 in the cut list
     int64_t npairs;        // number of pairs to process (of ids, if given)
     const int* ids;        // optional list of pair ids
+    int compact;           // records at the list position instead of the pair id
     const double2* X;
     const int4* T;
     const double* det;
@@ -89,7 +92,7 @@ __device__ __forceinline__ int sym3(int a, int b) {  // index of (a, b) in a pac
 template <typename R, int KER, int NQI>
 __global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contrib) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
-    constexpr int NE = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 84 : 21;
+    constexpr int NS = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? NLFEM_REC2 : NLFEM_REC1;  // record stride
     const Params& P = A.prm;
     const bool caps = P.ball == NLFEM_BALL_APPROXCAPS;
     for (int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pi < A.npairs;
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contr
         // fold the four blocks into the union block and write its upper triangle
         int posl[3], u[6];
         union_pos(tk, tl, posl, u);
-        R* out = contrib + p * NE;
+        R* out = contrib + (A.compact ? pi : p) * NS;
         R blk[6][6][NC];
 #pragma unroll
         for (int a = 0; a < 6; ++a)
@@ -266,6 +269,7 @@ __global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contr
 struct DuffyArgs {
     const int* ids;
     int64_t n;
+    int compact;  // records at the list position instead of the pair id
     const int* pk;
     const int* pl;
     const double2* X;
@@ -436,10 +440,11 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
                 }
                 ++e;
             }
+        const int64_t r = A.compact ? wi : (int64_t)p;
         for (int a = 0; a < 6; ++a)
             for (int b = a; b < 6; ++b) {
-                if (contrib64) contrib64[(int64_t)p * 21 + q_E1[a][b]] = blk[a][b];
-                else contrib32[(int64_t)p * 21 + q_E1[a][b]] = (float)blk[a][b];
+                if (contrib64) contrib64[r * NLFEM_REC1 + q_E1[a][b]] = blk[a][b];
+                else contrib32[r * NLFEM_REC1 + q_E1[a][b]] = (float)blk[a][b];
             }
     }
 }
@@ -486,25 +491,191 @@ static void launch_trunc(const QuadArgs& a, R* out, cudaStream_t st) {
     NLFEM_LAUNCH_CHECK();
 }
 
-void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {
-    if (prm.precision == NLFEM_PREC_FP32_BULK) {
-        // separated pairs: FP32 geometry with exact decisions; intersecting pairs: canonical
-        launch_trunc_fast(m, pc, prm, sys.contrib32.p, st, ev);
-        if (!prm.singular && pc.nduffy > 0) {
-            QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nduffy, pc.duffy_ids.p, m.X.p, m.T.p, m.det.p, prm};
+// Close-list records (singular or diamond rule, FP32 in list order) into the fixed-point
+// accumulators: each upper entry E(a, b) of the folded union block goes to the upper CSR
+// entry of the node pair (u_a, u_b). acc == nullptr: only the largest |value| is recorded.
+template <int NDOF>
+__global__ void k_close_acc(const int* __restrict__ ids, int64_t n, const int* __restrict__ pk,
+                            const int* __restrict__ pl, const int4* __restrict__ T, const float* __restrict__ rec,
+                            const int64_t* __restrict__ nptr, const int* __restrict__ ncol,
+                            const int64_t* __restrict__ up_start, unsigned long long* acc, float scale,
+                            unsigned int* maxabs) {
+    constexpr int NS = NDOF == 1 ? NLFEM_REC1 : NLFEM_REC2;
+    constexpr int NCOMP = NDOF == 1 ? 1 : 4;
+    constexpr int NC = NDOF == 1 ? 1 : 3;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float vmax = 0.f;
+    if (i < n) {
+        const int p = ids[i];
+        int posl[3], u[6];
+        const int U = union_pos(T[pk[p]], T[pl[p]], posl, u);
+        const float* r = rec + i * NS;
+        for (int a = 0; a < U; ++a)
+            for (int b = a; b < U; ++b) {
+                const int lo = min(u[a], u[b]), hi = max(u[a], u[b]);
+                const int64_t up = acc ? up_start[lo] + max(upper_rank(nptr, ncol, lo, hi), 0) : 0;
+                const float* v = r + q_E1[a][b] * NCOMP;
+                const float comp[3] = {v[0], v[NCOMP > 1 ? 1 : 0], v[NCOMP > 1 ? 3 : 0]};
+                for (int c = 0; c < NC; ++c) {
+                    vmax = fmaxf(vmax, fabsf(comp[c]));
+                    const long long q = __float2ll_rn(comp[c] * scale);
+                    if (acc && q) atomicAdd(acc + up * NC + c, (unsigned long long)q);
+                }
+            }
+    }
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(maxabs, __float_as_uint(vmax));
+}
+
+// kk of every element summed over its pairs (k, .) in pair order (LL = false), or ll over
+// its pairs (., l) in the order of the transposed index (LL = true): a warp per element,
+// a fixed butterfly, then one fixed-point add per node pair of the element. Pairs of the
+// close list (singular or diamond rule) have no record and are skipped.
+template <int NC, bool LL>
+__global__ void k_elem_sums(int64_t K, const int64_t* __restrict__ ptr, const int* __restrict__ perm,
+                            const int8_t* __restrict__ pcls, int skip_close, const float* __restrict__ kkll,
+                            const int* __restrict__ epos, unsigned long long* __restrict__ acc, float scale) {
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= K) return;  // whole warps leave together
+    float s[6 * NC];
+#pragma unroll
+    for (int x = 0; x < 6 * NC; ++x) s[x] = 0.f;
+    for (int64_t j = ptr[e] + lane; j < ptr[e + 1]; j += 32) {
+        const int64_t p = perm ? (int64_t)perm[j] : j;
+        if (skip_close && pcls[p] > 0) continue;
+        const float2* r = reinterpret_cast<const float2*>(kkll + p * (6 * NC));
+#pragma unroll
+        for (int x = 0; x < 3 * NC; ++x) {
+            const float2 v = r[x];
+            s[2 * x] += v.x;
+            s[2 * x + 1] += v.y;
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 6 * NC; ++x)
+        for (int o = 16; o > 0; o >>= 1) s[x] += __shfl_xor_sync(0xffffffffu, s[x], o);
+    if (lane == 0)
+#pragma unroll
+        for (int x = 0; x < 6; ++x) {
+            const int64_t u = epos[e * 6 + x];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const long long q = __float2ll_rn(s[c * 6 + x] * scale);
+                if (q) atomicAdd(acc + u * NC + c, (unsigned long long)q);
+            }
+        }
+}
+
+static void elem_sums(Mesh& m, PairCache& pc, const Params& prm, System& sys, float scale, cudaStream_t st) {
+    const int skip = close_mode(prm) != 0;
+    const unsigned g = nblk(m.K * 32, 256);
+    if (m.K == 0) return;
+    if (pc.ndof == 1) {
+        k_elem_sums<1, false><<<g, 256, 0, st>>>(m.K, pc.pair_ptr.p, nullptr, pc.pcls.p, skip, sys.kkll.p,
+                                                  pc.epos.p, sys.acc.p, scale);
+        k_elem_sums<1, true><<<g, 256, 0, st>>>(m.K, pc.pT_ptr.p, pc.pT_id.p, pc.pcls.p, skip,
+                                                 sys.kkll.p + pc.npairs * 6, pc.epos.p, sys.acc.p, scale);
+    } else {
+        k_elem_sums<3, false><<<g, 256, 0, st>>>(m.K, pc.pair_ptr.p, nullptr, pc.pcls.p, skip, sys.kkll.p,
+                                                  pc.epos.p, sys.acc.p, scale);
+        k_elem_sums<3, true><<<g, 256, 0, st>>>(m.K, pc.pT_ptr.p, pc.pT_id.p, pc.pcls.p, skip,
+                                                 sys.kkll.p + pc.npairs * 18, pc.epos.p, sys.acc.p, scale);
+    }
+    NLFEM_LAUNCH_CHECK();
+}
+
+// Scale of the fixed-point accumulation: 2^S with S such that terms * maxabs * 2^S < 2^62
+// (no partial sum can overflow) with 2^8 of headroom for an estimated maxabs.
+static int acc_shift(double maxabs, int64_t terms, int headroom_bits) {
+    if (!(maxabs > 0)) return 0;
+    const int e = (int)std::ceil(std::log2(maxabs * (double)std::max<int64_t>(terms, 1)));
+    return std::max(-120, std::min(120, 62 - e - headroom_bits));
+}
+
+static void close_acc(Mesh& m, PairCache& pc, const System& sys, unsigned long long* acc, float scale,
+                      unsigned int* maxabs, cudaStream_t st) {
+    if (pc.nduffy == 0) return;
+    if (pc.ndof == 1)
+        k_close_acc<1><<<nblk(pc.nduffy, 128), 128, 0, st>>>(pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.T.p,
+                                                             sys.contrib32.p, pc.nrow_ptr.p, pc.ncol.p,
+                                                             pc.up_start.p, acc, scale, maxabs);
+    else
+        k_close_acc<2><<<nblk(pc.nduffy, 128), 128, 0, st>>>(pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.T.p,
+                                                             sys.contrib32.p, pc.nrow_ptr.p, pc.ncol.p,
+                                                             pc.up_start.p, acc, scale, maxabs);
+    NLFEM_LAUNCH_CHECK();
+}
+
+// FP32-bulk path: (1) the close list (singular rule in FP64, or the canonical truncation
+// kernel) writes compact records; (2) a pilot pass over every 61st pair of the whole and
+// cut lists, plus the close records, estimates the largest |value| and fixes the scale;
+// (3) the bulk kernels add kl into the fixed-point accumulators and write kk / ll records,
+// which k_elem_sums sums per element, and the close records are added, recording the
+// exact largest |value|; (4) if that value could overflow a sum, or leaves more than 2^16
+// of unused range, (3) runs again with the scale from the exact value. The scale is a
+// function of the inputs alone, so the result is the same in every run.
+static void run_bulk(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {
+    const int NC = pc.ndof == 1 ? 1 : 3;
+    if (pc.nduffy > 0) {
+        sys.contrib32.alloc(pc.nduffy * contrib_entries(pc.ndof), st);
+        if (prm.singular) {
+            DuffyArgs d{pc.duffy_ids.p, pc.nduffy, 1, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
+            k_duffy<<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, nullptr, sys.contrib32.p);
+            NLFEM_LAUNCH_CHECK();
+        } else {
+            QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nduffy, pc.duffy_ids.p, 1, m.X.p, m.T.p, m.det.p, prm};
             launch_trunc<float>(c, sys.contrib32.p, st);
         }
-    } else {
-        NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
-        NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
-        QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.npairs, nullptr, m.X.p, m.T.p, m.det.p, prm};
-        launch_trunc<double>(a, sys.contrib64.p, st);
-        NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
     }
+    DBuf<unsigned int> mx;
+    mx.alloc(2, st);
+    mx.zero(st);
+    launch_trunc_fast(m, pc, prm, BulkAcc{nullptr, nullptr, 1.f, mx.p, 61}, st, nullptr);
+    close_acc(m, pc, sys, nullptr, 1.f, mx.p, st);
+    unsigned int h = 0;
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, mx.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    float pilot;
+    std::memcpy(&pilot, &h, sizeof pilot);
+    int S = acc_shift(pilot, pc.acc_terms, 8);
+    sys.acc.alloc(std::max<int64_t>(pc.n_upper * NC, 1), st);
+    sys.kkll.alloc(pc.npairs * 12 * NC, st);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        sys.acc.zero(st);
+        NLFEM_CUDA_TRY(cudaMemsetAsync(mx.p + 1, 0, sizeof(unsigned int), st));
+        const float scale = std::ldexp(1.f, S);
+        launch_trunc_fast(m, pc, prm, BulkAcc{sys.acc.p, sys.kkll.p, scale, mx.p + 1, 1}, st, ev);
+        elem_sums(m, pc, prm, sys, scale, st);
+        close_acc(m, pc, sys, sys.acc.p, scale, mx.p + 1, st);
+        NLFEM_CUDA_TRY(cudaEventRecord(ev[3], st));
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, mx.p + 1, sizeof h, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        float exact;
+        std::memcpy(&exact, &h, sizeof exact);
+        const int S_exact = acc_shift(exact, pc.acc_terms, 0);
+        if (S <= S_exact && S >= S_exact - 16) break;  // no overflow possible, resolution kept
+        NLFEM_CHECK(attempt == 0, NLFEM_ERR_CUDA, "internal error: fixed-point scale did not settle");
+        S = S_exact;
+    }
+    sys.acc_shift = S;
+    sys.contrib32.release();
+    sys.kkll.release();
+}
+
+void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {
+    if (prm.precision == NLFEM_PREC_FP32_BULK) {
+        run_bulk(m, pc, prm, sys, st, ev);
+        return;
+    }
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.npairs, nullptr, 0, m.X.p, m.T.p, m.det.p, prm};
+    launch_trunc<double>(a, sys.contrib64.p, st);
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
     if (prm.singular && pc.nduffy > 0) {
-        DuffyArgs d{pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
-        k_duffy<<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(
-            d, prm.precision == NLFEM_PREC_FP32_BULK ? nullptr : sys.contrib64.p, sys.contrib32.p);
+        DuffyArgs d{pc.duffy_ids.p, pc.nduffy, 0, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
+        k_duffy<<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, sys.contrib64.p, nullptr);
         NLFEM_LAUNCH_CHECK();
     }
     NLFEM_CUDA_TRY(cudaEventRecord(ev[3], st));
@@ -600,7 +771,7 @@ void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStr
         k_mark<<<nblk(pc.ncut, 256), 256, 0, st>>>(pc.cut_ids.p, pc.ncut, 2, wflag.p);
         NLFEM_LAUNCH_CHECK();
     }
-    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, wflag.p, pc.npairs, nullptr, m.X.p, m.T.p, m.det.p, prm};
+    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, wflag.p, pc.npairs, nullptr, 0, m.X.p, m.T.p, m.det.p, prm};
     unsigned grid = (unsigned)std::min<int64_t>(nblk(pc.npairs, 256), 152 * 32);
     if (grid) {
         k_census<<<grid, 256, 0, st>>>(a, c.p);

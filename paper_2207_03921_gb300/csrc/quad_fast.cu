@@ -42,6 +42,16 @@ struct FastArgs {
     float il[16][3], iw[16];  // inner rule in FP32
     float delta, d2, c, s;
     int caps;
+    // fixed-point accumulation into the upper CSR entries (see accumulate_pair)
+    unsigned long long* acc;  // [n_upper][NC] int64 two's complement sums; nullptr: pilot (max only)
+    float* kkll;              // [2][P][6 NC] kk, then ll, of every pair, by pair id
+    int64_t npairs_all;       // P
+    const int64_t* up_start;  // [M + 1] first upper entry of each node row
+    const int* epos;          // [K][6] upper entries of an element's node pairs (kkI order)
+    const uint16_t* klr;      // [9][npairs] rank of the kl node pair in its upper row, list order
+    float scale;              // 2^S
+    unsigned int* maxabs;     // bits of the largest |value| seen (a positive float), atomicMax
+    int64_t pstride;          // pair i of this launch is ids[i * pstride] (pilot samples)
 };
 
 template <int NC>
@@ -126,104 +136,64 @@ __device__ __forceinline__ void outer_update(const FastArgs& A, int q0, float dk
     }
 }
 
-// union block of a separated pair, [[kk, kl], [kl^T, ll]]: its upper triangle in entry order
-// E(a, b), a <= b over (k0 k1 k2 l0 l1 l2); peridynamics: components xx, xy, yx, yy
-template <int NC, int NE>
-__device__ __forceinline__ void write_block(float* out, const float (&kk)[6][NC], const float (&kl)[9][NC],
-                                            const float (&ll)[6][NC]) {
-    const int kkI[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-    int e = 0;
-#pragma unroll
-    for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int b = a; b < 6; ++b) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                float v;
-                if (b < 3) v = kk[kkI[a][b]][c];
-                else if (a < 3) v = kl[a * 3 + (b - 3)][c];
-                else v = ll[kkI[a - 3][b - 3]][c];
-                if (NC == 1) {
-                    out[e] = v;
-                } else if (c == 0) {
-                    out[e * 4 + 0] = v;
-                } else if (c == 1) {
-                    out[e * 4 + 1] = v;
-                    out[e * 4 + 2] = v;
-                } else {
-                    out[e * 4 + 3] = v;
-                }
-            }
-            ++e;
-        }
+// Accumulation of a pair's block [[kk, kl], [kl^T, ll]].
+// kk and ll only involve the nodes of one element: they are written to the pair's record
+// (kk of pair p at kkll[p], ll at kkll[P + p], 6 values per component) and summed per
+// element later in a fixed order
+// (k_elem_sums). kl[a][b] belongs to the node pair (k_a, l_b); it is rounded once to a signed
+// 64-bit fixed-point number v * 2^S and added to that upper CSR entry with an integer atomic
+// (counted twice when the two nodes coincide: both mirrored entries of the symmetric block
+// are diagonal). Integer addition is associative, so the sums are the same bits in every
+// run whatever order the pairs are processed in. Peridynamics: NC = 3 components xx, xy, yy
+// (the block of a node pair is symmetric).
+__device__ __forceinline__ long long to_fixed(const FastArgs& A, float v, float& vmax) {
+    vmax = fmaxf(vmax, fabsf(v));
+    return __float2ll_rn(v * A.scale);
 }
 
 template <int NC>
-struct PairBlock {
-    float kk[6][NC], kl[9][NC], ll[6][NC];
-};
-
-// Intersecting pairs: a node shared by E_k and E_l takes one position of the union block
-// (k0 k1 k2, then the unshared nodes of E_l in order), so the kl terms of a shared node
-// pair land on the diagonal twice and the rest of the block folds onto fewer entries.
-// Rare (a few percent of the pairs), so kept out of line; sequential, hence deterministic.
-template <int NC, int NE>
-__device__ __noinline__ void write_block_union(float* out, int4 tk, int4 tl, PairBlock<NC> B) {
-    int posl[3];
-    const int lv[3] = {tl.x, tl.y, tl.z};
-    int U = 3;
-    for (int b = 0; b < 3; ++b) {
-        int f = -1;
-        if (lv[b] == tk.x) f = 0;
-        if (lv[b] == tk.y) f = 1;
-        if (lv[b] == tk.z) f = 2;
-        posl[b] = f >= 0 ? f : U++;
-    }
-    for (int i = 0; i < NE; ++i) out[i] = 0.f;
-    auto add = [&](int a, int b, int c, float v) {
-        const int lo = min(a, b), hi = max(a, b);
-        const int e = lo * 6 - lo * (lo - 1) / 2 + (hi - lo);  // entry of (lo, hi) in the upper triangle
-        if (NC == 1) {
-            out[e] += v;
-        } else if (c == 0) {
-            out[e * 4] += v;
-        } else if (c == 1) {
-            out[e * 4 + 1] += v;
-            out[e * 4 + 2] += v;
-        } else {
-            out[e * 4 + 3] += v;
-        }
-    };
-    const int kkI[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+__device__ __forceinline__ void accumulate_pair(const FastArgs& A, int64_t pi, int64_t p, int4 tk, int4 tl,
+                                                const float (&kk)[6][NC], const float (&kl)[9][NC],
+                                                const float (&ll)[6][NC], float& vmax) {
+    const int kn[3] = {tk.x, tk.y, tk.z}, ln[3] = {tl.x, tl.y, tl.z};
+#pragma unroll
     for (int c = 0; c < NC; ++c)
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-                if (a <= b) add(a, b, c, B.kk[kkI[a][b]][c]);
-                add(a, posl[b], c, B.kl[a * 3 + b][c]);
-                if (a == posl[b]) add(a, a, c, B.kl[a * 3 + b][c]);
-                if (a <= b) add(posl[a], posl[b], c, B.ll[kkI[a][b]][c]);
-            }
-}
-
-template <int NC, int NE>
-__device__ __forceinline__ void write_pair(float* out, bool shared, int4 tk, int4 tl, const float (&kk)[6][NC],
-                                           const float (&kl)[9][NC], const float (&ll)[6][NC]) {
-    if (!shared) {
-        write_block<NC, NE>(out, kk, kl, ll);
+#pragma unroll
+        for (int e = 0; e < 6; ++e) vmax = fmaxf(vmax, fmaxf(fabsf(kk[e][c]), fabsf(ll[e][c])));
+    if (!A.acc) {  // pilot
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int e = 0; e < 9; ++e) vmax = fmaxf(vmax, fabsf(kl[e][c]) * (kn[e / 3] == ln[e % 3] ? 2.f : 1.f));
         return;
     }
-    PairBlock<NC> B;
+    float2* rk = reinterpret_cast<float2*>(A.kkll + p * (6 * NC));
+    float2* rl = reinterpret_cast<float2*>(A.kkll + (A.npairs_all + p) * (6 * NC));
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
+    for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            B.kk[i][c] = kk[i][c];
-            B.ll[i][c] = ll[i][c];
+        for (int x = 0; x < 3; ++x) {
+            rk[3 * c + x] = make_float2(kk[2 * x][c], kk[2 * x + 1][c]);
+            rl[3 * c + x] = make_float2(ll[2 * x][c], ll[2 * x + 1][c]);
         }
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B.kl[i][c] = kl[i][c];
-    }
-    write_block_union<NC, NE>(out, tk, tl, B);
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int i = kn[a], j = ln[b];
+            const float f = i == j ? 2.f : 1.f;
+            const int64_t u = A.up_start[min(i, j)] + A.klr[(int64_t)(a * 3 + b) * A.npairs + pi];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const long long q = to_fixed(A, f * kl[a * 3 + b][c], vmax);
+                if (q) atomicAdd(A.acc + u * NC + c, (unsigned long long)q);
+            }
+        }
+}
+
+__device__ __forceinline__ void flush_max(const FastArgs& A, float vmax) {
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(A.maxabs, __float_as_uint(vmax));
 }
 
 // FP32 decisions of one outer point, all evaluated (no early exit, so a warp stays
@@ -306,9 +276,8 @@ __device__ __noinline__ int clip_canonical(const double2* __restrict__ X, int4 t
 static constexpr int CHUNK = 8;
 
 template <int KER, int NQI, bool CAPS>
-__global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A, float* __restrict__ contrib) {
+__global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
-    constexpr int NE = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 84 : 21;
     constexpr int MAXP = CAPS ? 9 : 6;  // polygon points: 6 raw, plus up to 3 cap centres
     extern __shared__ float2 s_pts[];   // [CHUNK][MAXP][FAST_THREADS]
     float2* my = s_pts + threadIdx.x;
@@ -316,17 +285,18 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A, float* _
     const Params& P = A.prm;
     const int nqo = P.ro.n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float vmax = 0.f;
     for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < A.npairs; p0 += stride) {
         const int64_t pi = p0 + threadIdx.x;
         const bool valid = pi < A.npairs;
-        const int64_t p = valid ? (int64_t)A.ids[pi] : 0;
+        const int64_t p = valid ? (int64_t)A.ids[pi * A.pstride] : 0;
         int4 tk = make_int4(0, 0, 0, 0), tl = make_int4(0, 0, 0, 0);
         float4 Ek = make_float4(0, 0, 0, 0), El = make_float4(1, 0, 0, 1);
         float dk = 0.f, dx = 0.f, dy = 0.f;
-        bool shared = false;
+        int k = 0, l = 0;
         if (valid) {
-            const int k = A.pk[p], l = A.pl[p];
-            shared = A.pcls[p] > 0;
+            k = A.pk[p];
+            l = A.pl[p];
             tk = A.T[k];
             tl = A.T[l];
             const double2 v0k = A.X[tk.x], v0l = A.X[tl.x];
@@ -462,8 +432,9 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A, float* _
                 }
             }
         }
-        if (valid) write_pair<NC, NE>(contrib + p * NE, shared, tk, tl, kk, kl, ll);
+        if (valid) accumulate_pair<NC>(A, pi, p, tk, tl, kk, kl, ll, vmax);
     }
+    flush_max(A, vmax);
 }
 
 // Fan triangles of a cut pair summed over its outer points, from the same FP32 decisions
@@ -499,27 +470,29 @@ __global__ void k_cut_tris(FastArgs A, int* __restrict__ key) {
     key[pi] = tris;
 }
 
-__global__ void k_bucket_flag(const int* __restrict__ key, int64_t n, int lo, int hi, int64_t* __restrict__ flag) {
+// sort key within a window of the cut list: fan triangles, then the position in the window
+__global__ void k_window_key(int* key, int64_t n, int wbits) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = key[i] >= lo && key[i] < hi;
+    if (i < n) key[i] = (key[i] << wbits) | (int)(i & ((1 << wbits) - 1));
 }
 
-__global__ void k_bucket_scatter(const int* __restrict__ ids, const int64_t* __restrict__ flag,
-                                 const int64_t* __restrict__ pos, int64_t n, int64_t base, int* __restrict__ out) {
+__global__ void k_window_ptr(int64_t* ptr, int64_t nwin, int64_t n, int w) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && flag[i]) out[base + pos[i]] = ids[i];
+    if (i <= nwin) ptr[i] = i * w < n ? i * w : n;
 }
 
-// Separated pairs with E_l inside the ball of every point of E_k: the whole inner element
-// at every outer point, no geometry at all.
+// Pairs with E_l inside the ball of every point of E_k: the whole inner element at every
+// outer point, no geometry at all.
 template <int KER, int NQI>
-__global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(FastArgs A, float* __restrict__ contrib) {
+__global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(FastArgs A) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
-    constexpr int NE = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 84 : 21;
     const int nqo = A.prm.ro.n;
-    for (int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pi < A.npairs;
-         pi += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = A.ids[pi];
+    float vmax = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < A.npairs; p0 += stride) {
+        const int64_t pi = p0 + threadIdx.x;
+        const bool valid = pi < A.npairs;
+        const int64_t p = valid ? (int64_t)A.ids[pi * A.pstride] : 0;
         const int k = A.pk[p], l = A.pl[p];
         const int4 tk = A.T[k], tl = A.T[l];
         const double2 v0k = A.X[tk.x], v0l = A.X[tl.x];
@@ -551,8 +524,9 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(FastArgs A, float*
                                    dx + El.z - Xx, dy + El.w - Xy, 0.f, 1.f);
             outer_update<NC>(A, q0, dk, I, kk, kl, ll);
         }
-        write_pair<NC, NE>(contrib + p * NE, A.pcls[p] > 0, tk, tl, kk, kl, ll);
+        if (valid) accumulate_pair<NC>(A, pi, p, tk, tl, kk, kl, ll, vmax);
     }
+    flush_max(A, vmax);
 }
 
 static FastArgs fast_args(Mesh& m, PairCache& pc, const Params& prm) {
@@ -575,81 +549,91 @@ static FastArgs fast_args(Mesh& m, PairCache& pc, const Params& prm) {
     a.caps = prm.ball == NLFEM_BALL_APPROXCAPS;
     a.ids = nullptr;
     a.npairs = 0;
+    a.acc = nullptr;
+    a.kkll = nullptr;
+    a.npairs_all = pc.npairs;
+    a.up_start = nullptr;
+    a.epos = nullptr;
+    a.klr = nullptr;
+    a.scale = 1.f;
+    a.maxabs = nullptr;
+    a.pstride = 1;
     return a;
 }
 
-// Stable reorder of the cut list by fan-triangle count in 16 bands (pattern time).
+// Reorder of the cut list by fan-triangle count within windows of FAST_THREADS consecutive
+// pairs, one block's share of a grid-stride step (pattern time): the lanes of a warp then
+// drain similar work, and a warp's pairs still share their outer element, so their
+// accumulator entries stay in L2.
 void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st) {
     const int64_t n = pc.ncut;
     if (n < 2) return;
+    constexpr int WBITS = 7, W = 1 << WBITS;
+    static_assert(W == FAST_THREADS, "sort windows are the blocks' pair ranges");
     FastArgs a = fast_args(m, pc, prm);
     a.ids = pc.cut_ids.p;
     a.npairs = n;
-    DBuf<int> key, out;
-    DBuf<int64_t> flag, pos;
+    DBuf<int> key;
     key.alloc(n, st);
-    out.alloc(n, st);
-    flag.alloc(n, st);
-    pos.alloc(n + 1, st);
     k_cut_tris<<<nblk(n, 256), 256, 0, st>>>(a, key.p);
     NLFEM_LAUNCH_CHECK();
-    const int maxt = prm.ro.n * ((a.caps ? 9 : 6) - 2);
-    const int width = (maxt + 16) / 16;
-    int64_t base = 0;
-    for (int b = 0; b < 16; ++b) {
-        const int lo = b == 0 ? -1 : b * width, hi = b == 15 ? (1 << 30) : (b + 1) * width;
-        k_bucket_flag<<<nblk(n, 256), 256, 0, st>>>(key.p, n, lo, hi, flag.p);
-        NLFEM_LAUNCH_CHECK();
-        exclusive_scan_i64(flag.p, pos.p, n, st);
-        k_bucket_scatter<<<nblk(n, 256), 256, 0, st>>>(pc.cut_ids.p, flag.p, pos.p, n, base, out.p);
-        NLFEM_LAUNCH_CHECK();
-        int64_t cnt = 0;
-        NLFEM_CUDA_TRY(cudaMemcpyAsync(&cnt, pos.p + n, sizeof cnt, cudaMemcpyDeviceToHost, st));
-        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
-        base += cnt;
-    }
-    if (base != n) throw Error{NLFEM_ERR_CUDA, "cut-pair ordering lost pairs"};
-    pc.cut_ids.swap_with(out);
+    k_window_key<<<nblk(n, 256), 256, 0, st>>>(key.p, n, WBITS);
+    NLFEM_LAUNCH_CHECK();
+    const int64_t nwin = (n + W - 1) / W;
+    DBuf<int64_t> ptr;
+    ptr.alloc(nwin + 1, st);
+    k_window_ptr<<<nblk(nwin + 1, 256), 256, 0, st>>>(ptr.p, nwin, n, W);
+    NLFEM_LAUNCH_CHECK();
+    segmented_sort_i32(key.p, pc.cut_ids.p, ptr.p, nwin, (int)std::min<int64_t>(n, W), st);
 }
 
 template <int KER, int NQI, bool CAPS>
-static void launch_cut(const FastArgs& a, float* contrib, unsigned grid, cudaStream_t st) {
+static void launch_cut(const FastArgs& a, unsigned grid, cudaStream_t st) {
     constexpr int MAXP = CAPS ? 9 : 6;
     const size_t smem = sizeof(float2) * CHUNK * MAXP * FAST_THREADS;
     NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_cut<KER, NQI, CAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
-    k_trunc_cut<KER, NQI, CAPS><<<grid, FAST_THREADS, smem, st>>>(a, contrib);
+    k_trunc_cut<KER, NQI, CAPS><<<grid, FAST_THREADS, smem, st>>>(a);
 }
 
 template <int KER, int NQI>
-static void launch_pair_kernels(int pass, const FastArgs& a, float* contrib, unsigned grid, cudaStream_t st) {
-    if (pass == 0) k_trunc_whole<KER, NQI><<<grid, FAST_THREADS, 0, st>>>(a, contrib);
-    else if (a.caps) launch_cut<KER, NQI, true>(a, contrib, grid, st);
-    else launch_cut<KER, NQI, false>(a, contrib, grid, st);
+static void launch_pair_kernels(int pass, const FastArgs& a, unsigned grid, cudaStream_t st) {
+    if (pass == 0) k_trunc_whole<KER, NQI><<<grid, FAST_THREADS, 0, st>>>(a);
+    else if (a.caps) launch_cut<KER, NQI, true>(a, grid, st);
+    else launch_cut<KER, NQI, false>(a, grid, st);
 }
 
-void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, float* contrib, cudaStream_t st,
+void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, const BulkAcc& b, cudaStream_t st,
                        cudaEvent_t* ev) {
     FastArgs a = fast_args(m, pc, prm);
+    a.acc = b.acc;
+    a.kkll = b.kkll;
+    a.up_start = pc.up_start.p;
+    a.epos = pc.epos.p;
+    a.scale = b.scale;
+    a.maxabs = b.maxabs;
+    a.pstride = b.pstride;
     for (int pass = 0; pass < 2; ++pass) {
         a.ids = pass == 0 ? pc.whole_ids.p : pc.cut_ids.p;
-        a.npairs = pass == 0 ? pc.nwhole : pc.ncut;
-        NLFEM_CUDA_TRY(cudaEventRecord(ev[pass], st));  // ev[0..2] bracket the two launches
+        const int64_t n = pass == 0 ? pc.nwhole : pc.ncut;
+        a.klr = pass == 0 ? pc.klr_whole.p : pc.klr_cut.p;
+        a.npairs = (n + b.pstride - 1) / b.pstride;
+        if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[pass], st));  // ev[0..2] bracket the two launches
         const unsigned grid = (unsigned)std::min<int64_t>(nblk(a.npairs, FAST_THREADS), 152 * 64);
         if (!grid) continue;
         if (prm.kernel == NLFEM_KERNEL_CONSTANT) {
-            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_CONSTANT, 7>(pass, a, contrib, grid, st);
-            else launch_pair_kernels<NLFEM_KERNEL_CONSTANT, 16>(pass, a, contrib, grid, st);
+            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_CONSTANT, 7>(pass, a, grid, st);
+            else launch_pair_kernels<NLFEM_KERNEL_CONSTANT, 16>(pass, a, grid, st);
         } else if (prm.kernel == NLFEM_KERNEL_FRACTIONAL) {
-            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_FRACTIONAL, 7>(pass, a, contrib, grid, st);
-            else launch_pair_kernels<NLFEM_KERNEL_FRACTIONAL, 16>(pass, a, contrib, grid, st);
+            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_FRACTIONAL, 7>(pass, a, grid, st);
+            else launch_pair_kernels<NLFEM_KERNEL_FRACTIONAL, 16>(pass, a, grid, st);
         } else {
-            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_PERIDYNAMIC, 7>(pass, a, contrib, grid, st);
-            else launch_pair_kernels<NLFEM_KERNEL_PERIDYNAMIC, 16>(pass, a, contrib, grid, st);
+            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_PERIDYNAMIC, 7>(pass, a, grid, st);
+            else launch_pair_kernels<NLFEM_KERNEL_PERIDYNAMIC, 16>(pass, a, grid, st);
         }
         NLFEM_LAUNCH_CHECK();
     }
-    NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
+    if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
 }
 
 }  // namespace nlfem
