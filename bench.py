@@ -61,6 +61,7 @@ FLOPS_VERTEX_TESTS = 15         # three vertex-in-ball tests per (x_p, E_l) of a
 FLOPS_EDGES = 3 * 23            # three edge quadratics (with sqrt) per cut (x_p, E_l)
 FLOPS_CAPS = 3 * 14             # up to three cap centres per cut (x_p, E_l), approxcaps only
 FLOPS_SUBTRI_POINT = 8 + 6      # point mapping and barycentric basis per point of a sub-triangle
+FLOPS_DUFFY_POINT = 40          # FP64 flops per point of the singular rule (plus one pow / rsqrt)
 CONTRIB_ENTRIES = {1: 21, 2: 84}
 
 
@@ -347,70 +348,82 @@ def main():
     e2e_ms, _ = time_steps(e2e_step, e2e_steps, 1, ws, stream)
     e2e_value = npairs * ws / (e2e_ms / e2e_steps * 1e-3)
 
-    # roofline of the dominant kernel: the longest of the whole-pair and cut-pair quadrature
-    # kernels (FP32 ALU) and the reduction (HBM)
+    # roofline of the dominant kernel: the longest of the bulk quadrature kernels (FP32 ALU),
+    # the close-list kernel (FP64 ALU, singular rule), the per-element sums and the conversion
+    # of the fixed-point entries into CSR (HBM)
     pk = peaks()
     clk_sum = clk.summary()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s from unit counts and the max clock
+    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12        # 2 FP64 FMA lanes per SM and clock
     hbm_peak = pk.get("hbm_gbs", 6800.0)
     fpe = FLOPS_PER_EVAL[wl["kernel"]]
     nqi = wl["quad_inner"]
-    ms_whole = statistics.mean(i["ms_whole"] for i in timed)
-    ms_cut = statistics.mean(i["ms_cut"] for i in timed)
-    ms_close = statistics.mean(i["ms_close"] for i in timed)
+
+    def mean(key):
+        return statistics.mean(i[key] for i in timed)
+
+    ms_whole, ms_cut, ms_close, ms_sums = mean("ms_whole"), mean("ms_cut"), mean("ms_close"), mean("ms_sums")
     flops_whole = census["evals_whole"] * fpe + (census["evals_whole"] // nqi) * FLOPS_PER_OUTER
     flops_cut = (census["evals_cut"] * fpe + census["nonempty_points_cut"] * FLOPS_PER_OUTER
                  + census["outer_points_cut"] * FLOPS_VERTEX_TESTS
                  + census["cut_points_cut"] * (FLOPS_EDGES + (FLOPS_CAPS if wl["ball"] == "approxcaps" else 0))
                  + census["subtri_evals_cut"] * FLOPS_SUBTRI_POINT)
-    ne = CONTRIB_ENTRIES[ndof]
-    red_bytes = (info0["n_contrib"] * (4 + 4)                 # slot index + FP32 contribution
-                 + info0["n_upper"] * (8 + 4 + 4 + 16 + 8 + 8 + 8)  # up_pos, up_row, ncol, seg_ptr, pbase, nptr, row_ptr
-                 + info0["nnz"] * (8 + 8))                    # tpos read, value written
+    flops_duffy = census["duffy_points"] * FLOPS_DUFFY_POINT
+    nc = 1 if ndof == 1 else 3
+    sums_bytes = npairs * (24 + 24 + 4) * nc                     # kk records, ll records (gathered), pT ids
+    conv_bytes = (info0["n_upper"] * 8 * nc + info0["nnz"] // (ndof * ndof) * 4  # fixed-point entries, columns
+                  + info0["nnz"] // 2 * 8 + info0["nnz"] * 8)     # transposed positions, values written
+
+    def rate(x, ms, scale):
+        return x / (ms * 1e-3) / scale if ms > 0 else 0.0
+
     kernels = {
         "k_trunc_whole": {"bound": "alu", "ms": ms_whole, "units": info0["pairs_whole"],
-                          "achieved": flops_whole / (ms_whole * 1e-3) / 1e12 if ms_whole else 0.0,
-                          "peak": fp32_peak, "unit": "TFLOP/s"},
-        "k_trunc_cut": {"bound": "alu", "ms": ms_cut,
-                         "units": census["outer_points_cut"] // wl["quad_outer"],
-                         "achieved": flops_cut / (ms_cut * 1e-3) / 1e12 if ms_cut else 0.0,
-                         "peak": fp32_peak, "unit": "TFLOP/s"},
-        "k_reduce": {"bound": "hbm", "ms": red_ms, "units": info0["n_upper"],
-                     "achieved": red_bytes / (red_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s"},
+                          "achieved": rate(flops_whole, ms_whole, 1e12), "peak": fp32_peak, "unit": "TFLOP/s"},
+        "k_trunc_cut": {"bound": "alu", "ms": ms_cut, "units": census["outer_points_cut"] // wl["quad_outer"],
+                        "achieved": rate(flops_cut, ms_cut, 1e12), "peak": fp32_peak, "unit": "TFLOP/s"},
+        "k_elem_sums": {"bound": "hbm", "ms": ms_sums, "units": npairs,
+                        "achieved": rate(sums_bytes, ms_sums, 1e9), "peak": hbm_peak, "unit": "GB/s"},
+        "k_acc_to_csr": {"bound": "hbm", "ms": red_ms, "units": info0["n_upper"],
+                         "achieved": rate(conv_bytes, red_ms, 1e9), "peak": hbm_peak, "unit": "GB/s"},
     }
+    if census["singular_pairs"]:
+        kernels["k_duffy"] = {"bound": "alu", "ms": ms_close, "units": census["singular_pairs"],
+                              "achieved": rate(flops_duffy, ms_close, 1e12), "peak": fp64_peak, "unit": "TFLOP/s"}
     for k in kernels.values():
         k["frac"] = k["achieved"] / k["peak"]
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
+    peak_src = {"alu": "derived: 152 SMs x (128 FP32 | 2 FP64) lanes x 2 x max SM clock",
+                "hbm": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in pk else "fallback 6.8 TB/s"}
     roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
             "frac": d["frac"], "traffic": traffic_from_profiles(dom, args.workload), "kernel": dom,
-            "ms_per_launch": d["ms"],
-            "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock" if d["bound"] == "alu"
-                            else "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in pk else "fallback 6.8 TB/s"),
-            "kernels": kernels, "ms_close_pairs": ms_close}
+            "ms_per_launch": d["ms"], "peak_source": peak_src[d["bound"]], "kernels": kernels}
 
     line = {
         "metric": "element-pair assemblies/s", "value": value, "unit": "pairs/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (quadrature and geometry with exact decisions) + f64 (near ties, singular pairs, CSR)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (quadrature, geometry with exact decisions) + i64 fixed-point sums + f64 (near ties, singular pairs, CSR)",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "precision": "fp32_bulk",
                    "step": "nlfem_assemble with cached pair list and pattern",
-                   "l2": "working set larger than L2 (pair list, per-pair contributions and slot index stream from HBM)",
+                   "l2": "working set larger than L2 (pair lists, kl ranks and per-pair kk/ll records stream from HBM)",
                    "pairs": npairs, "nnz": info0["nnz"], "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": roof,
         "fp64_plain": {"value": npairs * ws / (ms64_step * 1e-3), "ms_per_step": ms64_step,
                        "quadrature_ms": quad64_ms, "speedup_fp32_bulk_over_fp64": ms64_step / ms_step},
         "breakdown_ms": {"quadrature": quad_ms, "whole_pairs": ms_whole, "cut_pairs": ms_cut,
-                         "intersecting_pairs": ms_close, "reduce": red_ms, "cold_total": cold_ms,
+                         "close_list": ms_close, "element_sums": ms_sums, "to_csr": red_ms, "cold_total": cold_ms,
                          "pairs_search": info0["ms_pairs"], "pattern_and_index": info0["ms_pattern"]},
         "cold": {"value": npairs / (cold_ms * 1e-3), "ms": cold_ms},
         "census": census,
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "pinned host mesh -> nlfem_mesh_create -> nlfem_assemble (cold) -> CSR values and F to host"},
-        # per step: whole-pair and cut-pair quadrature, intersecting pairs, reduction, load vector
-        "gpu_launches": args.steps * (2 + (1 if census["singular_pairs"] or census["evals_canonical"] else 0) + 2),
+        # per step: pilot and main whole-pair and cut-pair kernels, two element sums, fixed point to
+        # CSR, load vector; with a close list also its kernel and two close-record passes
+        "gpu_launches": args.steps * (8 + (3 if census["singular_pairs"] or census["evals_canonical"] else 0)),
         "clocks": clk_sum,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -86,7 +86,8 @@ typedef struct {
     double ms_close;         /* intersecting pairs under the singular or the diamond rule */
     int64_t pairs_whole;     /* standard-rule pairs with E_l in the ball of every point of E_k */
     int64_t n_upper;         /* node-level upper pattern entries (one reduction unit each) */
-    int64_t n_contrib;       /* contributions gathered by the reduction (slot index length) */
+    int64_t n_contrib;       /* contributions gathered by the ordered reduction (FP64 path; 0 before) */
+    double ms_sums;          /* FP32 bulk: per-element kk / ll sums and close-list adds */
 } nlfem_assembly_info;
 
 typedef struct {

@@ -46,7 +46,8 @@ class nlfem_assembly_info(C.Structure):
                 ("device_bytes", C.c_int64), ("ms_pairs", C.c_double), ("ms_pattern", C.c_double),
                 ("ms_quadrature", C.c_double), ("ms_reduce", C.c_double), ("cached", C.c_int),
                 ("ms_whole", C.c_double), ("ms_cut", C.c_double), ("ms_close", C.c_double),
-                ("pairs_whole", C.c_int64), ("n_upper", C.c_int64), ("n_contrib", C.c_int64)]
+                ("pairs_whole", C.c_int64), ("n_upper", C.c_int64), ("n_contrib", C.c_int64),
+                ("ms_sums", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

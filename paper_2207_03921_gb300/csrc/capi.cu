@@ -269,12 +269,12 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
     Mesh& m = mesh->m;
     cudaStream_t st = (cudaStream_t)stream;
     Params P = make_params(*params, m.ndof);
-    cudaEvent_t ev[10];  // [0..5] phases, [6..9] the quadrature kernels
-    for (int i = 0; i < 10; ++i) NLFEM_CUDA_TRY(cudaEventCreate(&ev[i]));
+    cudaEvent_t ev[12];  // [0..5] phases, [6..11] the quadrature kernels
+    for (int i = 0; i < 12; ++i) NLFEM_CUDA_TRY(cudaEventCreate(&ev[i]));
     struct EvGuard {
         cudaEvent_t* e;
         ~EvGuard() {
-            for (int i = 0; i < 10; ++i) cudaEventDestroy(e[i]);
+            for (int i = 0; i < 12; ++i) cudaEventDestroy(e[i]);
         }
     } guard{ev};
     std::shared_ptr<PairCache> pc = m.cache;
@@ -359,9 +359,10 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
         I.ms_pairs = t_pairs;
         I.ms_pattern = t_pattern;
         I.ms_quadrature = elapsed_ms(ev[3], ev[4]);
-        I.ms_whole = elapsed_ms(ev[6], ev[7]);
-        I.ms_cut = elapsed_ms(ev[7], ev[8]);
-        I.ms_close = elapsed_ms(ev[8], ev[9]);
+        I.ms_close = elapsed_ms(ev[6], ev[7]);
+        I.ms_whole = elapsed_ms(ev[8], ev[9]);
+        I.ms_cut = elapsed_ms(ev[9], ev[10]);
+        I.ms_sums = elapsed_ms(ev[10], ev[11]);
         I.pairs_whole = pc->nwhole;
         I.n_upper = pc->n_upper;
         I.n_contrib = pc->ncontrib;

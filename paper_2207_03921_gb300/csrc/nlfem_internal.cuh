@@ -189,7 +189,9 @@ struct System {
 void mesh_prepare(Mesh& m, const int* T3_dev, const int8_t* lab_dev, cudaStream_t st);
 void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st);
 void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st);
-// ev[0..3] are recorded on st around the whole-pair, cut-pair and intersecting-pair kernels
+// ev[0..5] are recorded on st: [0, 1] around the close-list kernel (singular or diamond
+// rule), [2, 3] whole-pair kernel, [3, 4] cut-pair kernel (FP64: every pair), [4, 5] element
+// sums and close-list adds
 void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev);
 void run_reduction(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st);
 void run_load(Mesh& m, const Params& prm, const double* f_nodal, System& sys, cudaStream_t st);
