@@ -176,7 +176,7 @@ int nlfem_solve(nlfem_system_t sys, const double* g_nodal, double tol_rel, int m
  * geometry (for FLOP accounting; it does not change sys). counts[16] receives: [0] kernel
  * evaluations of the truncation quadrature, [1] outer points whose inner element lies
  * fully in the ball, [2] outer points whose inner element was cut and retriangulated,
- * [3] sub-triangles of the cut polygons, [4] points evaluated by the singular rule,
+ * [3] sub-triangles of the cut polygons, [4] kernel evaluations of the singular rule,
  * [5] pairs on the truncation path, [6] pairs on the singular path, [7] outer points
  * with an empty intersection, [8] outer points visited; split by the FP32-bulk kernels:
  * [9] evaluations of the whole-pair kernel, [10] evaluations of the cut-pair kernel,

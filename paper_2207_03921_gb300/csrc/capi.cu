@@ -115,6 +115,18 @@ static Params make_params(const nlfem_params& p, int ndof) {
     fill_rule(P.ro, p.quad_outer);
     fill_rule(P.ri, p.quad_inner);
     fill_gauss(P.dr, p.duffy_gauss);
+    {
+        // xi factor of the singular rule's integrand: Jacobian x D D^T x gamma's homogeneity
+        // (gamma(xi z) = xi^alpha gamma(z), alpha = -2 - 2s, 0 for the constant kernel)
+        const double alpha = p.kernel == NLFEM_KERNEL_FRACTIONAL ? -2.0 - 2.0 * p.s : 0.0;
+        for (int c = 0; c < 3; ++c) P.dr.sxi[c] = 0.0;
+        for (int i = 0; i < P.dr.n; ++i) {
+            const double x = P.dr.x[i], w = P.dr.w[i];
+            P.dr.sxi[0] += w * std::pow(x, 3.0 + alpha) * (1.0 - x) * (1.0 - x);  // identical
+            P.dr.sxi[1] += w * std::pow(x, 4.0 + alpha) * (1.0 - x);              // common edge
+            P.dr.sxi[2] += w * std::pow(x, 5.0 + alpha);                          // common vertex
+        }
+    }
     // Tab. 1: club for 0 < s < 1, diamond for -1 < s <= 0 (peridynamics: s = -1/2), heart for s <= -1
     if (p.close_rule == NLFEM_CLOSE_AUTO) {
         P.singular = p.kernel == NLFEM_KERNEL_FRACTIONAL;

@@ -112,6 +112,7 @@ struct DuffyRule {
     int n;
     double x[32], w[32];
     double sum_w, sum_wx;  // sums of the 1D rule (exact 1 and 1/2 up to rounding)
+    double sxi[3];         // xi sums of the singular rule: identical, edge, vertex (set with the kernel)
 };
 
 struct Params {

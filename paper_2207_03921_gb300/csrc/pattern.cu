@@ -91,15 +91,21 @@ __device__ __forceinline__ int pair_union(const RowEnum& R, int p, int i, int u[
 // ------------------------------------------------------------------------------------------
 // pattern: per node row, the union vertices of every pair containing the node
 // ------------------------------------------------------------------------------------------
+// Most inserts repeat a key already present (a node is shared by many pairs of the row), so
+// the slot is read first and the compare-and-swap is only issued on an empty slot.
 __device__ __forceinline__ bool hash_insert(int* tab, int cap, int key, int* count) {
     unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(cap - 1);
     for (int probe = 0; probe < cap; ++probe) {
-        int old = atomicCAS(&tab[h], -1, key);
-        if (old == -1) {
-            atomicAdd(count, 1);
-            return true;
+        int cur = tab[h];
+        if (cur == key) return true;
+        if (cur == -1) {
+            cur = atomicCAS(&tab[h], -1, key);
+            if (cur == -1) {
+                atomicAdd(count, 1);
+                return true;
+            }
+            if (cur == key) return true;
         }
-        if (old == key) return true;
         h = (h + 1) & (unsigned)(cap - 1);
     }
     return false;
@@ -121,14 +127,23 @@ __global__ void k_pattern(RowEnum R, int64_t M, int cap, int64_t* rowcnt, const 
     row_ranges(R, (int)i, rr);
     int64_t total = rr.cum[2 * rr.nne];
     bool ok = true;
+    // the union vertices of every pair containing i: the nodes of i's own elements once, and
+    // per pair the nodes of its other element (E_l on the x side, E_k on the y side)
+    for (int t = lane; t < rr.nne; t += 32) {
+        const int4 te = R.T[rr.ne[t]];
+        ok &= hash_insert(tab, cap, te.x, count);
+        ok &= hash_insert(tab, cap, te.y, count);
+        ok &= hash_insert(tab, cap, te.z, count);
+    }
     for (int64_t f0 = 0; f0 < total; f0 += 32) {
         int64_t f = f0 + lane;
         if (f < total) {
             int p = row_pair(R, rr, f, (int)i);
             if (p >= 0) {
-                int u[6], ai;
-                int U = pair_union(R, p, (int)i, u, ai);
-                for (int b = 0; b < U; ++b) ok &= hash_insert(tab, cap, u[b], count);
+                const int4 to = f < rr.cum[rr.nne] ? R.T[R.pl[p]] : R.T[R.pk[p]];
+                ok &= hash_insert(tab, cap, to.x, count);
+                ok &= hash_insert(tab, cap, to.y, count);
+                ok &= hash_insert(tab, cap, to.z, count);
             }
         }
     }
@@ -546,7 +561,11 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
     DBuf<int64_t> rowcnt;
     rowcnt.alloc(M, st);
     pc.nrow_ptr.alloc(M + 1, st);
+    // table capacity: twice the node count of a row's pairs is an upper bound on its columns
+    // (at most 3 new nodes per partner element); start from the largest partner list
+    const int64_t maxp = std::max(max_segment_i64(pc.pair_ptr.p, m.K, st), max_segment_i64(pc.pT_ptr.p, m.K, st));
     int cap = 1024;
+    while (cap < 32768 && cap < 2 * maxp) cap *= 2;
     for (;;) {
         ovf.zero(st);
         int warps = std::max(1, std::min(8, (int)(160 * 1024 / ((cap + 1) * 4))));
