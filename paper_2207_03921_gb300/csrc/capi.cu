@@ -354,11 +354,27 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
         run_reduction(m, *pc, P, S, st);
         NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
         run_load(m, P, fptr, S, st);
+        int redo = 0;
+        if (P.precision == NLFEM_PREC_FP32_BULK)
+            NLFEM_CUDA_TRY(cudaMemcpyAsync(&redo, &S.fix.p->redo, sizeof redo, cudaMemcpyDeviceToHost, st));
         NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (redo) {
+            // the pilot's estimate of the largest value was off by more than the headroom:
+            // the accumulation runs again with the scale of the exact value (rare)
+            NLFEM_CUDA_TRY(cudaEventRecord(ev[3], st));
+            bulk_redo(m, *pc, P, S, st, ev + 6);
+            NLFEM_CUDA_TRY(cudaEventRecord(ev[4], st));
+            run_reduction(m, *pc, P, S, st);
+            NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
+            NLFEM_CUDA_TRY(cudaMemcpyAsync(&redo, &S.fix.p->redo, sizeof redo, cudaMemcpyDeviceToHost, st));
+            NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+            NLFEM_CHECK(!redo, NLFEM_ERR_CUDA, "internal error: fixed-point scale did not settle");
+        }
         // contributions are no longer needed once reduced
         S.contrib32.release();
         S.contrib64.release();
         S.acc.release();
+        S.kkll.release();
         nlfem_assembly_info& I = S.info;
         std::memset(&I, 0, sizeof I);
         I.npairs = pc->npairs;

@@ -168,6 +168,29 @@ struct PairCache {
 
 struct SolveState;
 
+// Fixed-point scale of one FP32-bulk assembly, chosen on the device (no host round trip):
+// a pilot pass records max_pilot, the scale 2^shift follows; the main pass records
+// max_exact, and redo = 1 if shift could overflow a sum or wastes more than 2^16 of range.
+struct FixState {
+    unsigned int max_pilot;  // bits of a positive float
+    unsigned int max_exact;
+    int shift, shift_exact, redo, pad;
+    float scale;             // 2^shift
+    float pad2;
+};
+
+// S with terms * maxabs * 2^S <= 2^62 (headroom_bits more below that), from the exact binary
+// exponent of maxabs * terms; the same function on the host and the device
+__host__ __device__ inline int fix_shift(float maxabs, int64_t terms, int headroom_bits) {
+    if (!(maxabs > 0.f)) return 0;
+    const double x = (double)maxabs * (double)(terms > 0 ? terms : 1);  // exact: 24 + 40 bits < 53 + 11
+    int e = 0;
+    const double mant = frexp(x, &e);  // x = mant 2^e, mant in [0.5, 1)
+    const int c = mant == 0.5 ? e - 1 : e;  // ceil(log2(x))
+    const int S = 62 - c - headroom_bits;
+    return S < -120 ? -120 : (S > 120 ? 120 : S);
+}
+
 struct System {
     Mesh* mesh = nullptr;
     std::shared_ptr<PairCache> pc;  // the pattern this system was assembled on
@@ -179,7 +202,7 @@ struct System {
     DBuf<double> contrib64;  // records [P * NE] (FP64 plain)
     DBuf<unsigned long long> acc;  // FP32 bulk: fixed-point upper entries [n_upper * NC]
     DBuf<float> kkll;        // FP32 bulk: kk and ll of every pair [P * 12 NC]
-    int acc_shift = 0;       // FP32 bulk: the values were scaled by 2^acc_shift
+    DBuf<FixState> fix;      // FP32 bulk: the fixed-point scale
     nlfem_assembly_info info;
     std::shared_ptr<SolveState> solver;
 };
@@ -205,11 +228,14 @@ void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStr
 // records the largest |value| of every pstride-th pair
 struct BulkAcc {
     unsigned long long* acc;
-    float* kkll;  // [P][12 NC] per-pair kk and ll records
-    float scale;
+    float* kkll;            // [P][12 NC] per-pair kk and ll records
+    const float* scale_p;   // 2^S in device memory
     unsigned int* maxabs;
     int64_t pstride;
 };
+// FP32 bulk: after the quadrature, read FixState.redo (with the final synchronisation) and
+// call bulk_redo if it is set
+void bulk_redo(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev);
 void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, const BulkAcc& b, cudaStream_t st,
                        cudaEvent_t* ev);
 void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st);

@@ -808,9 +808,10 @@ void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st) {
 template <int NDOF>
 __global__ void k_acc_to_csr(int64_t M, const int64_t* __restrict__ nptr, const int* __restrict__ ncol,
                              const int64_t* __restrict__ up_start, const unsigned long long* __restrict__ acc,
-                             double inv_scale, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ tpos,
-                             double* __restrict__ val) {
+                             const FixState* __restrict__ fix, const int64_t* __restrict__ row_ptr,
+                             const int64_t* __restrict__ tpos, double* __restrict__ val) {
     constexpr int NC = NDOF == 1 ? 1 : 3;
+    const double inv_scale = ldexp(1.0, -fix->shift);
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= M) return;
@@ -850,14 +851,13 @@ __global__ void k_acc_to_csr(int64_t M, const int64_t* __restrict__ nptr, const 
 void run_reduction(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st) {
     if (prm.precision == NLFEM_PREC_FP32_BULK) {
         // every upper entry is written with its mirror, so val needs no clearing
-        const double inv = std::ldexp(1.0, -sys.acc_shift);
         const unsigned g = nblk(m.M * 32, 256);
         if (m.M == 0) return;
         if (pc.ndof == 1)
-            k_acc_to_csr<1><<<g, 256, 0, st>>>(m.M, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, sys.acc.p, inv,
+            k_acc_to_csr<1><<<g, 256, 0, st>>>(m.M, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, sys.acc.p, sys.fix.p,
                                                pc.row_ptr.p, pc.tpos.p, sys.val.p);
         else
-            k_acc_to_csr<2><<<g, 256, 0, st>>>(m.M, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, sys.acc.p, inv,
+            k_acc_to_csr<2><<<g, 256, 0, st>>>(m.M, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, sys.acc.p, sys.fix.p,
                                                pc.row_ptr.p, pc.tpos.p, sys.val.p);
         NLFEM_LAUNCH_CHECK();
         return;

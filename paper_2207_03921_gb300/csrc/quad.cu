@@ -500,13 +500,14 @@ template <int NDOF>
 __global__ void k_close_acc(const int* __restrict__ ids, int64_t n, const int* __restrict__ pk,
                             const int* __restrict__ pl, const int4* __restrict__ T, const float* __restrict__ rec,
                             const int64_t* __restrict__ nptr, const int* __restrict__ ncol,
-                            const int64_t* __restrict__ up_start, unsigned long long* acc, float scale,
-                            unsigned int* maxabs) {
+                            const int64_t* __restrict__ up_start, unsigned long long* acc,
+                            const float* __restrict__ scale_p, unsigned int* maxabs) {
     constexpr int NS = NDOF == 1 ? NLFEM_REC1 : NLFEM_REC2;
     constexpr int NCOMP = NDOF == 1 ? 1 : 4;
     constexpr int NC = NDOF == 1 ? 1 : 3;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float vmax = 0.f;
+    const float scale = acc ? *scale_p : 1.f;
     if (i < n) {
         const int p = ids[i];
         int posl[3], u[6];
@@ -536,7 +537,8 @@ __global__ void k_close_acc(const int* __restrict__ ids, int64_t n, const int* _
 template <int NC, bool LL>
 __global__ void k_elem_sums(int64_t K, const int64_t* __restrict__ ptr, const int* __restrict__ perm,
                             const int8_t* __restrict__ pcls, int skip_close, const float* __restrict__ kkll,
-                            const int* __restrict__ epos, unsigned long long* __restrict__ acc, float scale) {
+                            const int* __restrict__ epos, unsigned long long* __restrict__ acc,
+                            const float* __restrict__ scale_p) {
     const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (e >= K) return;  // whole warps leave together
@@ -557,6 +559,7 @@ __global__ void k_elem_sums(int64_t K, const int64_t* __restrict__ ptr, const in
 #pragma unroll
     for (int x = 0; x < 6 * NC; ++x)
         for (int o = 16; o > 0; o >>= 1) s[x] += __shfl_xor_sync(0xffffffffu, s[x], o);
+    const float scale = *scale_p;
     if (lane == 0)
 #pragma unroll
         for (int x = 0; x < 6; ++x) {
@@ -569,7 +572,7 @@ __global__ void k_elem_sums(int64_t K, const int64_t* __restrict__ ptr, const in
         }
 }
 
-static void elem_sums(Mesh& m, PairCache& pc, const Params& prm, System& sys, float scale, cudaStream_t st) {
+static void elem_sums(Mesh& m, PairCache& pc, const Params& prm, System& sys, const float* scale, cudaStream_t st) {
     const int skip = close_mode(prm) != 0;
     const unsigned g = nblk(m.K * 32, 256);
     if (m.K == 0) return;
@@ -587,15 +590,7 @@ static void elem_sums(Mesh& m, PairCache& pc, const Params& prm, System& sys, fl
     NLFEM_LAUNCH_CHECK();
 }
 
-// Scale of the fixed-point accumulation: 2^S with S such that terms * maxabs * 2^S < 2^62
-// (no partial sum can overflow) with 2^8 of headroom for an estimated maxabs.
-static int acc_shift(double maxabs, int64_t terms, int headroom_bits) {
-    if (!(maxabs > 0)) return 0;
-    const int e = (int)std::ceil(std::log2(maxabs * (double)std::max<int64_t>(terms, 1)));
-    return std::max(-120, std::min(120, 62 - e - headroom_bits));
-}
-
-static void close_acc(Mesh& m, PairCache& pc, const System& sys, unsigned long long* acc, float scale,
+static void close_acc(Mesh& m, PairCache& pc, const System& sys, unsigned long long* acc, const float* scale,
                       unsigned int* maxabs, cudaStream_t st) {
     if (pc.nduffy == 0) return;
     if (pc.ndof == 1)
@@ -609,14 +604,49 @@ static void close_acc(Mesh& m, PairCache& pc, const System& sys, unsigned long l
     NLFEM_LAUNCH_CHECK();
 }
 
-// FP32-bulk path: (1) the close list (singular rule in FP64, or the canonical truncation
-// kernel) writes compact records; (2) a pilot pass over every 61st pair of the whole and
-// cut lists, plus the close records, estimates the largest |value| and fixes the scale;
-// (3) the bulk kernels add kl into the fixed-point accumulators and write kk / ll records,
-// which k_elem_sums sums per element, and the close records are added, recording the
-// exact largest |value|; (4) if that value could overflow a sum, or leaves more than 2^16
-// of unused range, (3) runs again with the scale from the exact value. The scale is a
-// function of the inputs alone, so the result is the same in every run.
+// the scale from the pilot's largest |value|, with 2^8 of headroom
+__global__ void k_fix_pick(FixState* f, int64_t terms) {
+    const int S = fix_shift(__uint_as_float(f->max_pilot), terms, 8);
+    f->shift = S;
+    f->scale = ldexpf(1.f, S);
+    f->max_exact = 0u;
+    f->redo = 0;
+}
+
+// the main pass may keep its scale if no sum could overflow and at most 2^16 of range is unused
+__global__ void k_fix_check(FixState* f, int64_t terms) {
+    const int Se = fix_shift(__uint_as_float(f->max_exact), terms, 0);
+    f->shift_exact = Se;
+    f->redo = (f->shift <= Se && f->shift >= Se - 16) ? 0 : 1;
+}
+
+__global__ void k_fix_exact(FixState* f) {
+    f->shift = f->shift_exact;
+    f->scale = ldexpf(1.f, f->shift);
+    f->max_exact = 0u;
+    f->redo = 0;
+}
+
+static void bulk_main(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {
+    FixState* f = sys.fix.p;
+    sys.acc.zero(st);
+    launch_trunc_fast(m, pc, prm, BulkAcc{sys.acc.p, sys.kkll.p, &f->scale, &f->max_exact, 1}, st, ev + 2);
+    elem_sums(m, pc, prm, sys, &f->scale, st);
+    close_acc(m, pc, sys, sys.acc.p, &f->scale, &f->max_exact, st);
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
+    k_fix_check<<<1, 1, 0, st>>>(f, pc.acc_terms);
+    NLFEM_LAUNCH_CHECK();
+}
+
+// FP32-bulk path, stream-ordered with no host round trip: (1) the close list (singular rule
+// in FP64, or the canonical truncation kernel) writes compact records; (2) a pilot pass over
+// every 61st pair of the whole and cut lists, plus the close records, records the largest
+// |value| and k_fix_pick fixes the scale 2^S; (3) the bulk kernels add kl into the
+// fixed-point accumulators and write kk / ll records, which k_elem_sums sums per element,
+// and the close records are added, recording the exact largest |value|; (4) k_fix_check
+// flags the assembly if that value could overflow a sum or leaves more than 2^16 of unused
+// range; the caller then runs bulk_redo (3 again with the scale from the exact value). S is
+// a function of the inputs alone, so the result is the same in every run.
 static void run_bulk(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {
     const int NC = pc.ndof == 1 ? 1 : 3;
     NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
@@ -632,39 +662,22 @@ static void run_bulk(Mesh& m, PairCache& pc, const Params& prm, System& sys, cud
         }
     }
     NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
-    DBuf<unsigned int> mx;
-    mx.alloc(2, st);
-    mx.zero(st);
-    launch_trunc_fast(m, pc, prm, BulkAcc{nullptr, nullptr, 1.f, mx.p, 61}, st, nullptr);
-    close_acc(m, pc, sys, nullptr, 1.f, mx.p, st);
-    unsigned int h = 0;
-    NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, mx.p, sizeof h, cudaMemcpyDeviceToHost, st));
-    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
-    float pilot;
-    std::memcpy(&pilot, &h, sizeof pilot);
-    int S = acc_shift(pilot, pc.acc_terms, 8);
+    sys.fix.alloc(1, st);
+    sys.fix.zero(st);
+    FixState* f = sys.fix.p;
+    launch_trunc_fast(m, pc, prm, BulkAcc{nullptr, nullptr, nullptr, &f->max_pilot, 61}, st, nullptr);
+    close_acc(m, pc, sys, nullptr, nullptr, &f->max_pilot, st);
+    k_fix_pick<<<1, 1, 0, st>>>(f, pc.acc_terms);
+    NLFEM_LAUNCH_CHECK();
     sys.acc.alloc(std::max<int64_t>(pc.n_upper * NC, 1), st);
     sys.kkll.alloc(pc.npairs * 12 * NC, st);
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        sys.acc.zero(st);
-        NLFEM_CUDA_TRY(cudaMemsetAsync(mx.p + 1, 0, sizeof(unsigned int), st));
-        const float scale = std::ldexp(1.f, S);
-        launch_trunc_fast(m, pc, prm, BulkAcc{sys.acc.p, sys.kkll.p, scale, mx.p + 1, 1}, st, ev + 2);
-        elem_sums(m, pc, prm, sys, scale, st);
-        close_acc(m, pc, sys, sys.acc.p, scale, mx.p + 1, st);
-        NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
-        NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, mx.p + 1, sizeof h, cudaMemcpyDeviceToHost, st));
-        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
-        float exact;
-        std::memcpy(&exact, &h, sizeof exact);
-        const int S_exact = acc_shift(exact, pc.acc_terms, 0);
-        if (S <= S_exact && S >= S_exact - 16) break;  // no overflow possible, resolution kept
-        NLFEM_CHECK(attempt == 0, NLFEM_ERR_CUDA, "internal error: fixed-point scale did not settle");
-        S = S_exact;
-    }
-    sys.acc_shift = S;
-    sys.contrib32.release();
-    sys.kkll.release();
+    bulk_main(m, pc, prm, sys, st, ev);
+}
+
+void bulk_redo(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {
+    k_fix_exact<<<1, 1, 0, st>>>(sys.fix.p);
+    NLFEM_LAUNCH_CHECK();
+    bulk_main(m, pc, prm, sys, st, ev);
 }
 
 void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {

@@ -18,6 +18,7 @@
 // iteration, so the inner rule runs with (nearly) the whole warp and exists once in the
 // code.
 #include <algorithm>
+#include <cstring>
 
 #include "nlfem_internal.cuh"
 
@@ -27,31 +28,50 @@ static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / 
 
 static constexpr int FAST_THREADS = 128;
 
-struct FastArgs {
+// Arguments shared by every pair of a launch: the quadrature rules (one kernel class).
+struct FastRule {
+    float ol[16][3], ow[16];  // outer rule in FP32
+    float il[16][3], iw[16];  // inner rule in FP32
+    double ro[16][3];         // outer barycentrics in FP64 (canonical fallback)
+    int nqo;
+};
+
+// Arguments of one request (one mesh and parameter set), read from a device table so that
+// one launch can serve the pairs of many requests.
+struct FastReq {
     const int* pk;
     const int* pl;
     const int8_t* pcls;
-    const int* ids;   // the pairs to process
-    int64_t npairs;   // number of ids
+    const int* ids;           // the work list (whole or cut pairs)
+    int64_t npairs;           // its length
     const double2* X;
     const int4* T;
     const float4* E32;
     const float* det32;
-    Params prm;
-    float ol[16][3], ow[16];  // outer rule in FP32
-    float il[16][3], iw[16];  // inner rule in FP32
     float delta, d2, c, s;
+    double delta64, delta2_64;
     int caps;
     // fixed-point accumulation into the upper CSR entries (see accumulate_pair)
-    unsigned long long* acc;  // [n_upper][NC] int64 two's complement sums; nullptr: pilot (max only)
+    unsigned long long* acc;  // [n_upper][NC] int64 two's complement sums
     float* kkll;              // [2][P][6 NC] kk, then ll, of every pair, by pair id
     int64_t npairs_all;       // P
     const int64_t* up_start;  // [M + 1] first upper entry of each node row
     const int* epos;          // [K][6] upper entries of an element's node pairs (kkI order)
     const uint16_t* klr;      // [9][npairs] rank of the kl node pair in its upper row, list order
-    float scale;              // 2^S
+    const float* scale_p;     // 2^S (device memory)
     unsigned int* maxabs;     // bits of the largest |value| seen (a positive float), atomicMax
-    int64_t pstride;          // pair i of this launch is ids[i * pstride] (pilot samples)
+};
+
+// A launch processes tiles of 32 consecutive list positions of one request, one warp per
+// tile (warps never wait for each other): tile t = (request, first position); without a
+// table, tile t of request 0 starts at 32 t. pilot > 0: only every pilot-th pair of each
+// list, largest |value| only.
+struct FastLaunch {
+    const FastReq* reqs;  // batched launches: the request table (device memory)
+    const int2* tiles;
+    int64_t ntiles;
+    int pilot;
+    FastReq one;          // single-request launches: the request itself (constant bank)
 };
 
 template <int NC>
@@ -61,35 +81,36 @@ struct Inner {
 
 // the inner rule on triangle (a, b, c): positions relative to x_p, barycentric (b1, b2) w.r.t. E_l
 template <int KER, int NQI, int NC>
-__device__ __forceinline__ void tri_quad(const FastArgs& A, Inner<NC>& I, float ax, float ay, float a1, float a2,
+__device__ __forceinline__ void tri_quad(const FastRule& R, const FastReq& Q, Inner<NC>& I, float ax, float ay,
+                                         float a1, float a2,
                                          float bx, float by, float b1, float b2, float cx, float cy, float c1,
                                          float c2) {
     const float dT = fabsf((bx - ax) * (cy - ay) - (by - ay) * (cx - ax));
     const float a0 = 1.f - a1 - a2, b0 = 1.f - b1 - b2, c0 = 1.f - c1 - c2;
 #pragma unroll
     for (int q = 0; q < NQI; ++q) {
-        const float l0 = A.il[q][0], l1 = A.il[q][1], l2 = A.il[q][2];
+        const float l0 = R.il[q][0], l1 = R.il[q][1], l2 = R.il[q][2];
         const float zx = l0 * ax + l1 * bx + l2 * cx;
         const float zy = l0 * ay + l1 * by + l2 * cy;
         const float Q0 = l0 * a0 + l1 * b0 + l2 * c0;
         const float Q1 = l0 * a1 + l1 * b1 + l2 * c1;
         const float Q2 = l0 * a2 + l1 * b2 + l2 * c2;
-        const float wq = A.iw[q] * dT;
+        const float wq = R.iw[q] * dT;
         float wc[NC];
         if (KER == NLFEM_KERNEL_CONSTANT) {
-            wc[0] = wq * A.c;
+            wc[0] = wq * Q.c;
         } else if (KER == NLFEM_KERNEL_FRACTIONAL) {
             const float r2 = zx * zx + zy * zy;
-            if (A.s == 0.5f) {
+            if (Q.s == 0.5f) {
                 const float r = rsqrtf(r2);
-                wc[0] = wq * A.c * r * r * r;
+                wc[0] = wq * Q.c * r * r * r;
             } else {
-                wc[0] = wq * A.c * exp2f(log2f(r2) * (-1.f - A.s));
+                wc[0] = wq * Q.c * exp2f(log2f(r2) * (-1.f - Q.s));
             }
         } else {
             const float r2 = zx * zx + zy * zy;
             const float r = rsqrtf(r2);
-            const float sc = wq * A.c * r * r * r;
+            const float sc = wq * Q.c * r * r * r;
             wc[0] = sc * zx * zx;
             wc[1 % NC] = sc * zx * zy;
             wc[2 % NC] = sc * zy * zy;
@@ -114,10 +135,10 @@ __device__ __forceinline__ void tri_quad(const FastArgs& A, Inner<NC>& I, float 
 
 // kk += a_p g P P^T, kl -= a_p P h^T, ll += a_p m for outer point q0 (P = its barycentrics)
 template <int NC>
-__device__ __forceinline__ void outer_update(const FastArgs& A, int q0, float dk, const Inner<NC>& I,
+__device__ __forceinline__ void outer_update(const FastRule& R, int q0, float dk, const Inner<NC>& I,
                                              float (&kk)[6][NC], float (&kl)[9][NC], float (&ll)[6][NC]) {
-    const float ap = A.ow[q0] * dk;
-    const float Pa[3] = {A.ol[q0][0], A.ol[q0][1], A.ol[q0][2]};
+    const float ap = R.ow[q0] * dk;
+    const float Pa[3] = {R.ol[q0][0], R.ol[q0][1], R.ol[q0][2]};
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const float ag = ap * I.g[c];
@@ -146,13 +167,14 @@ __device__ __forceinline__ void outer_update(const FastArgs& A, int q0, float dk
 // are diagonal). Integer addition is associative, so the sums are the same bits in every
 // run whatever order the pairs are processed in. Peridynamics: NC = 3 components xx, xy, yy
 // (the block of a node pair is symmetric).
-__device__ __forceinline__ long long to_fixed(const FastArgs& A, float v, float& vmax) {
+__device__ __forceinline__ long long to_fixed(float sc, float v, float& vmax) {
     vmax = fmaxf(vmax, fabsf(v));
-    return __float2ll_rn(v * A.scale);
+    return __float2ll_rn(v * sc);
 }
 
 template <int NC>
-__device__ __forceinline__ void accumulate_pair(const FastArgs& A, int64_t pi, int64_t p, int4 tk, int4 tl,
+__device__ __forceinline__ void accumulate_pair(const FastReq& Q, bool pilot, float sc, int64_t pi, int64_t p, int4 tk,
+                                                int4 tl,
                                                 const float (&kk)[6][NC], const float (&kl)[9][NC],
                                                 const float (&ll)[6][NC], float& vmax) {
     const int kn[3] = {tk.x, tk.y, tk.z}, ln[3] = {tl.x, tl.y, tl.z};
@@ -160,15 +182,15 @@ __device__ __forceinline__ void accumulate_pair(const FastArgs& A, int64_t pi, i
     for (int c = 0; c < NC; ++c)
 #pragma unroll
         for (int e = 0; e < 6; ++e) vmax = fmaxf(vmax, fmaxf(fabsf(kk[e][c]), fabsf(ll[e][c])));
-    if (!A.acc) {  // pilot
+    if (pilot) {
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int e = 0; e < 9; ++e) vmax = fmaxf(vmax, fabsf(kl[e][c]) * (kn[e / 3] == ln[e % 3] ? 2.f : 1.f));
         return;
     }
-    float2* rk = reinterpret_cast<float2*>(A.kkll + p * (6 * NC));
-    float2* rl = reinterpret_cast<float2*>(A.kkll + (A.npairs_all + p) * (6 * NC));
+    float2* rk = reinterpret_cast<float2*>(Q.kkll + p * (6 * NC));
+    float2* rl = reinterpret_cast<float2*>(Q.kkll + (Q.npairs_all + p) * (6 * NC));
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -182,18 +204,38 @@ __device__ __forceinline__ void accumulate_pair(const FastArgs& A, int64_t pi, i
         for (int b = 0; b < 3; ++b) {
             const int i = kn[a], j = ln[b];
             const float f = i == j ? 2.f : 1.f;
-            const int64_t u = A.up_start[min(i, j)] + A.klr[(int64_t)(a * 3 + b) * A.npairs + pi];
+            const int64_t u = Q.up_start[min(i, j)] + Q.klr[(int64_t)(a * 3 + b) * Q.npairs + pi];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const long long q = to_fixed(A, f * kl[a * 3 + b][c], vmax);
-                if (q) atomicAdd(A.acc + u * NC + c, (unsigned long long)q);
+                const long long q = to_fixed(sc, f * kl[a * 3 + b][c], vmax);
+                if (q) atomicAdd(Q.acc + u * NC + c, (unsigned long long)q);
             }
         }
 }
 
-__device__ __forceinline__ void flush_max(const FastArgs& A, float vmax) {
+__device__ __forceinline__ void flush_max(unsigned int* maxabs, float vmax) {
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(A.maxabs, __float_as_uint(vmax));
+    if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(maxabs, __float_as_uint(vmax));
+}
+
+static constexpr int FAST_WARPS = FAST_THREADS / 32;
+
+// tile t of a launch: its request and first list position
+__device__ __forceinline__ int2 tile_of(const FastLaunch& L, int64_t t) {
+    return L.tiles ? L.tiles[t] : make_int2(0, (int)(t * 32));
+}
+
+// the request of a tile into the warp's shared-memory copy (all lanes of the warp call it;
+// the copy is reloaded only when the request changes)
+__device__ __forceinline__ void load_req(FastReq& sq, int& cur, const FastReq* reqs, int r) {
+    __syncwarp();
+    constexpr int W = (int)(sizeof(FastReq) / sizeof(int));
+    static_assert(sizeof(FastReq) % sizeof(int) == 0, "FastReq is copied in 4-byte words");
+    const int* src = reinterpret_cast<const int*>(reqs + r);
+    int* dst = reinterpret_cast<int*>(&sq);
+    for (int w = threadIdx.x & 31; w < W; w += 32) dst[w] = src[w];
+    __syncwarp();
+    cur = r;
 }
 
 // FP32 decisions of one outer point, all evaluated (no early exit, so a warp stays
@@ -275,36 +317,50 @@ __device__ __noinline__ int clip_canonical(const double2* __restrict__ X, int4 t
 // lanes of a warp drain about the same number of triangles.
 static constexpr int CHUNK = 8;
 
-template <int KER, int NQI, bool CAPS>
-__global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A) {
+template <int KER, int NQI, bool CAPS, bool BATCH>
+__global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(const __grid_constant__ FastRule R,
+                                                           const __grid_constant__ FastLaunch L) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
     constexpr int MAXP = CAPS ? 9 : 6;  // polygon points: 6 raw, plus up to 3 cap centres
     extern __shared__ float2 s_pts[];   // [CHUNK][MAXP][FAST_THREADS]
     float2* my = s_pts + threadIdx.x;
     auto put = [&](int q, int slot, float x, float y) { my[(q * MAXP + slot) * FAST_THREADS] = make_float2(x, y); };
-    const Params& P = A.prm;
-    const int nqo = P.ro.n;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    float vmax = 0.f;
-    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < A.npairs; p0 += stride) {
-        const int64_t pi = p0 + threadIdx.x;
-        const bool valid = pi < A.npairs;
-        const int64_t p = valid ? (int64_t)A.ids[pi * A.pstride] : 0;
+    __shared__ FastReq sq[BATCH ? FAST_WARPS : 1];
+    const int nqo = R.nqo;
+    const bool pilot = L.pilot > 0;
+    const int warp = threadIdx.x >> 5;
+    int cur = -1;
+    float vmax = 0.f;            // largest |value| of this warp's pairs of request cur
+    unsigned int* vdst = nullptr;
+    for (int64_t t = (int64_t)blockIdx.x * FAST_WARPS + warp; t < L.ntiles; t += (int64_t)gridDim.x * FAST_WARPS) {
+        const int2 tile = tile_of(L, t);
+        if (BATCH && tile.x != cur) {  // warp-uniform
+            if (vdst) flush_max(vdst, vmax);
+            vmax = 0.f;
+            load_req(sq[warp], cur, L.reqs, tile.x);
+        }
+        const FastReq& Q = BATCH ? sq[warp] : L.one;
+        vdst = Q.maxabs;
+        const float sc = pilot ? 1.f : *Q.scale_p;
+        const int64_t pi = (int64_t)tile.y + (threadIdx.x & 31);
+        const int64_t nlist = pilot ? (Q.npairs + L.pilot - 1) / L.pilot : Q.npairs;
+        const bool valid = pi < nlist;
+        const int64_t p = valid ? (int64_t)Q.ids[pilot ? pi * L.pilot : pi] : 0;
         int4 tk = make_int4(0, 0, 0, 0), tl = make_int4(0, 0, 0, 0);
         float4 Ek = make_float4(0, 0, 0, 0), El = make_float4(1, 0, 0, 1);
         float dk = 0.f, dx = 0.f, dy = 0.f;
         int k = 0, l = 0;
         if (valid) {
-            k = A.pk[p];
-            l = A.pl[p];
-            tk = A.T[k];
-            tl = A.T[l];
-            const double2 v0k = A.X[tk.x], v0l = A.X[tl.x];
+            k = Q.pk[p];
+            l = Q.pl[p];
+            tk = Q.T[k];
+            tl = Q.T[l];
+            const double2 v0k = Q.X[tk.x], v0l = Q.X[tl.x];
             dx = (float)(v0l.x - v0k.x);
             dy = (float)(v0l.y - v0k.y);
-            Ek = A.E32[k];
-            El = A.E32[l];
-            dk = A.det32[k];
+            Ek = Q.E32[k];
+            El = Q.E32[l];
+            dk = Q.det32[k];
         }
         const float idet = 1.f / (El.x * El.w - El.y * El.z);
         const float W0x = dx, W0y = dy;
@@ -312,7 +368,7 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A) {
         const float span = fabsf(dx) + fabsf(dy) + fabsf(Ek.x) + fabsf(Ek.y) + fabsf(Ek.z) + fabsf(Ek.w) +
                            fabsf(El.x) + fabsf(El.y) + fabsf(El.z) + fabsf(El.w);
         const float eps = 4.8e-7f * span;    // bound on the FP32 error of the relative coordinates
-        const float floor2 = 1e-5f * A.d2;   // floor of the vertex margin (see nl_decide32)
+        const float floor2 = 1e-5f * Q.d2;   // floor of the vertex margin (see nl_decide32)
 
         float kk[6][NC], kl[9][NC], ll[6][NC];
 #pragma unroll
@@ -332,15 +388,15 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A) {
 #pragma unroll 1
             for (int q = 0; q < qn; ++q) {
                 const int q0 = qb + q;
-                const float l1o = A.ol[q0][1], l2o = A.ol[q0][2];
+                const float l1o = R.ol[q0][1], l2o = R.ol[q0][2];
                 const float Xx = l1o * Ek.x + l2o * Ek.z;  // x_p - v0_k
                 const float Xy = l1o * Ek.y + l2o * Ek.w;
                 const float Rx[3] = {W0x - Xx, W1x - Xx, W2x - Xx}, Ry[3] = {W0y - Xy, W1y - Xy, W2y - Xy};
                 float Cc[3];
 #pragma unroll
-                for (int m = 0; m < 3; ++m) Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - A.d2;
+                for (int m = 0; m < 3; ++m) Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - Q.d2;
                 GeoF G;
-                bool ok = decide_flat(Rx, Ry, Cc, eps, floor2, A.d2, G);
+                bool ok = decide_flat(Rx, Ry, Cc, eps, floor2, Q.d2, G);
                 int n = 0;
                 if (!CAPS) {
                     // vertices inside and crossings in boundary order; predicated stores
@@ -362,8 +418,8 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A) {
                     auto cap = [&](float px, float py, float qx, float qy) {
                         const float cx = qx - px, cy = qy - py;
                         const float len = sqrtf(cx * cx + cy * cy);
-                        ok &= len > 1e-6f * A.delta;
-                        const float sc = __fdividef(A.delta, len);
+                        ok &= len > 1e-6f * Q.delta;
+                        const float sc = __fdividef(Q.delta, len);
                         put(q, min(n, MAXP - 1), sc * cy, -sc * cx);
                         ++n;
                     };
@@ -388,7 +444,7 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A) {
                 }
                 if (!valid) n = 0;
                 else if (!ok)
-                    n = clip_canonical(A.X, tk, tl, P.ro.l[q0][0], P.ro.l[q0][1], P.ro.l[q0][2], P.delta, P.delta2,
+                    n = clip_canonical(Q.X, tk, tl, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2], Q.delta64, Q.delta2_64,
                                        CAPS, my + q * MAXP * FAST_THREADS, MAXP);
                 counts |= (unsigned long long)(n < 3 ? 0 : n) << (4 * q);
             }
@@ -398,7 +454,7 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A) {
             while (__any_sync(0xffffffffu, qc < qn)) {
                 if (qc < qn) {
                     const int q0 = qb + qc;
-                    const float l1o = A.ol[q0][1], l2o = A.ol[q0][2];
+                    const float l1o = R.ol[q0][1], l2o = R.ol[q0][2];
                     // x_p - v0_l, for the barycentric coordinates of the points
                     const float Bx = l1o * Ek.x + l2o * Ek.z - W0x, By = l1o * Ek.y + l2o * Ek.w - W0y;
                     float px[3], py[3], b1[3], b2[3];
@@ -421,9 +477,9 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A) {
 #pragma unroll
                         for (int j = 0; j < 6; ++j) I.m[j][c] = 0.f;
                     }
-                    tri_quad<KER, NQI, NC>(A, I, px[0], py[0], b1[0], b2[0], px[1], py[1], b1[1], b2[1], px[2], py[2],
+                    tri_quad<KER, NQI, NC>(R, Q, I, px[0], py[0], b1[0], b2[0], px[1], py[1], b1[1], b2[1], px[2], py[2],
                                            b1[2], b2[2]);
-                    outer_update<NC>(A, q0, dk, I, kk, kl, ll);
+                    outer_update<NC>(R, q0, dk, I, kk, kl, ll);
                     if (++sc >= (int)((counts >> (4 * qc)) & 15)) {
                         sc = 2;
                         ++qc;
@@ -432,39 +488,39 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(FastArgs A) {
                 }
             }
         }
-        if (valid) accumulate_pair<NC>(A, pi, p, tk, tl, kk, kl, ll, vmax);
+        if (valid) accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, kk, kl, ll, vmax);
     }
-    flush_max(A, vmax);
+    if (vdst) flush_max(vdst, vmax);
 }
 
 // Fan triangles of a cut pair summed over its outer points, from the same FP32 decisions
 // (an undecided outer point counts its FP32 outcome; the count only orders the work).
-__global__ void k_cut_tris(FastArgs A, int* __restrict__ key) {
+__global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key) {
     const int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pi >= A.npairs) return;
-    const int64_t p = A.ids[pi];
-    const int k = A.pk[p], l = A.pl[p];
-    const int4 tk = A.T[k], tl = A.T[l];
-    const double2 v0k = A.X[tk.x], v0l = A.X[tl.x];
+    if (pi >= Q.npairs) return;
+    const int64_t p = Q.ids[pi];
+    const int k = Q.pk[p], l = Q.pl[p];
+    const int4 tk = Q.T[k], tl = Q.T[l];
+    const double2 v0k = Q.X[tk.x], v0l = Q.X[tl.x];
     const float dx = (float)(v0l.x - v0k.x), dy = (float)(v0l.y - v0k.y);
-    const float4 Ek = A.E32[k], El = A.E32[l];
+    const float4 Ek = Q.E32[k], El = Q.E32[l];
     const float Wx[3] = {dx, dx + El.x, dx + El.z}, Wy[3] = {dy, dy + El.y, dy + El.w};
-    const int nqo = A.prm.ro.n;
+    const int nqo = R.nqo;
     int tris = 0;
     for (int q0 = 0; q0 < nqo; ++q0) {
-        const float Xx = A.ol[q0][1] * Ek.x + A.ol[q0][2] * Ek.z;
-        const float Xy = A.ol[q0][1] * Ek.y + A.ol[q0][2] * Ek.w;
+        const float Xx = R.ol[q0][1] * Ek.x + R.ol[q0][2] * Ek.z;
+        const float Xy = R.ol[q0][1] * Ek.y + R.ol[q0][2] * Ek.w;
         float Rx[3], Ry[3], Cc[3];
         for (int m = 0; m < 3; ++m) {
             Rx[m] = Wx[m] - Xx;
             Ry[m] = Wy[m] - Xy;
-            Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - A.d2;
+            Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - Q.d2;
         }
         GeoF G;
-        decide_flat(Rx, Ry, Cc, 0.f, 0.f, A.d2, G);
+        decide_flat(Rx, Ry, Cc, 0.f, 0.f, Q.d2, G);
         int n = 0;
         for (int e = 0; e < 3; ++e) n += (int)G.in[e] + G.nc[e];
-        if (A.caps && n >= 2 && !(G.in[0] && G.in[1] && G.in[2])) n += 1;  // at least one cap
+        if (Q.caps && n >= 2 && !(G.in[0] && G.in[1] && G.in[2])) n += 1;  // at least one cap
         tris += n >= 3 ? n - 2 : 0;
     }
     key[pi] = tris;
@@ -483,82 +539,104 @@ __global__ void k_window_ptr(int64_t* ptr, int64_t nwin, int64_t n, int w) {
 
 // Pairs with E_l inside the ball of every point of E_k: the whole inner element at every
 // outer point, no geometry at all.
-template <int KER, int NQI>
-__global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(FastArgs A) {
+template <int KER, int NQI, bool BATCH>
+__global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(const __grid_constant__ FastRule R,
+                                                             const __grid_constant__ FastLaunch L) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
-    const int nqo = A.prm.ro.n;
-    float vmax = 0.f;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < A.npairs; p0 += stride) {
-        const int64_t pi = p0 + threadIdx.x;
-        const bool valid = pi < A.npairs;
-        const int64_t p = valid ? (int64_t)A.ids[pi * A.pstride] : 0;
-        const int k = A.pk[p], l = A.pl[p];
-        const int4 tk = A.T[k], tl = A.T[l];
-        const double2 v0k = A.X[tk.x], v0l = A.X[tl.x];
-        const float dx = (float)(v0l.x - v0k.x), dy = (float)(v0l.y - v0k.y);
-        const float4 Ek = A.E32[k], El = A.E32[l];
-        const float dk = A.det32[k];
-        float kk[6][NC], kl[9][NC], ll[6][NC];
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) kk[i][c] = ll[i][c] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) kl[i][c] = 0.f;
-        for (int q0 = 0; q0 < nqo; ++q0) {
-            const float Xx = A.ol[q0][1] * Ek.x + A.ol[q0][2] * Ek.z;
-            const float Xy = A.ol[q0][1] * Ek.y + A.ol[q0][2] * Ek.w;
-            Inner<NC> I;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                I.g[c] = 0.f;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) I.h[j][c] = 0.f;
-#pragma unroll
-                for (int j = 0; j < 6; ++j) I.m[j][c] = 0.f;
-            }
-            tri_quad<KER, NQI, NC>(A, I, dx - Xx, dy - Xy, 0.f, 0.f, dx + El.x - Xx, dy + El.y - Xy, 1.f, 0.f,
-                                   dx + El.z - Xx, dy + El.w - Xy, 0.f, 1.f);
-            outer_update<NC>(A, q0, dk, I, kk, kl, ll);
+    __shared__ FastReq sq[BATCH ? FAST_WARPS : 1];
+    const int nqo = R.nqo;
+    const bool pilot = L.pilot > 0;
+    const int warp = threadIdx.x >> 5;
+    int cur = -1;
+    float vmax = 0.f;            // largest |value| of this warp's pairs of request cur
+    unsigned int* vdst = nullptr;
+    for (int64_t t = (int64_t)blockIdx.x * FAST_WARPS + warp; t < L.ntiles; t += (int64_t)gridDim.x * FAST_WARPS) {
+        const int2 tile = tile_of(L, t);
+        if (BATCH && tile.x != cur) {  // warp-uniform
+            if (vdst) flush_max(vdst, vmax);
+            vmax = 0.f;
+            load_req(sq[warp], cur, L.reqs, tile.x);
         }
-        if (valid) accumulate_pair<NC>(A, pi, p, tk, tl, kk, kl, ll, vmax);
+        const FastReq& Q = BATCH ? sq[warp] : L.one;
+        vdst = Q.maxabs;
+        const float sc = pilot ? 1.f : *Q.scale_p;
+        const int64_t pi = (int64_t)tile.y + (threadIdx.x & 31);
+        const int64_t nlist = pilot ? (Q.npairs + L.pilot - 1) / L.pilot : Q.npairs;
+        if (pi < nlist) {
+            const int64_t p = Q.ids[pilot ? pi * L.pilot : pi];
+            const int k = Q.pk[p], l = Q.pl[p];
+            const int4 tk = Q.T[k], tl = Q.T[l];
+            const double2 v0k = Q.X[tk.x], v0l = Q.X[tl.x];
+            const float dx = (float)(v0l.x - v0k.x), dy = (float)(v0l.y - v0k.y);
+            const float4 Ek = Q.E32[k], El = Q.E32[l];
+            const float dk = Q.det32[k];
+            float kk[6][NC], kl[9][NC], ll[6][NC];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) kk[i][c] = ll[i][c] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) kl[i][c] = 0.f;
+            for (int q0 = 0; q0 < nqo; ++q0) {
+                const float Xx = R.ol[q0][1] * Ek.x + R.ol[q0][2] * Ek.z;
+                const float Xy = R.ol[q0][1] * Ek.y + R.ol[q0][2] * Ek.w;
+                Inner<NC> I;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    I.g[c] = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) I.h[j][c] = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) I.m[j][c] = 0.f;
+                }
+                tri_quad<KER, NQI, NC>(R, Q, I, dx - Xx, dy - Xy, 0.f, 0.f, dx + El.x - Xx, dy + El.y - Xy, 1.f, 0.f,
+                                       dx + El.z - Xx, dy + El.w - Xy, 0.f, 1.f);
+                outer_update<NC>(R, q0, dk, I, kk, kl, ll);
+            }
+            accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, kk, kl, ll, vmax);
+        }
     }
-    flush_max(A, vmax);
+    if (vdst) flush_max(vdst, vmax);
 }
 
-static FastArgs fast_args(Mesh& m, PairCache& pc, const Params& prm) {
-    FastArgs a;
-    a.pk = pc.pk.p; a.pl = pc.pl.p; a.pcls = pc.pcls.p;
-    a.X = m.X.p; a.T = m.T.p; a.E32 = m.E32.p; a.det32 = m.det32.p;
-    a.prm = prm;
+static FastRule make_rule(const Params& prm) {
+    FastRule r;
     for (int i = 0; i < 16; ++i) {
         for (int j = 0; j < 3; ++j) {
-            a.ol[i][j] = i < prm.ro.n ? (float)prm.ro.l[i][j] : 0.f;
-            a.il[i][j] = i < prm.ri.n ? (float)prm.ri.l[i][j] : 0.f;
+            r.ol[i][j] = i < prm.ro.n ? (float)prm.ro.l[i][j] : 0.f;
+            r.il[i][j] = i < prm.ri.n ? (float)prm.ri.l[i][j] : 0.f;
+            r.ro[i][j] = i < prm.ro.n ? prm.ro.l[i][j] : 0.0;
         }
-        a.ow[i] = i < prm.ro.n ? (float)prm.ro.w[i] : 0.f;
-        a.iw[i] = i < prm.ri.n ? (float)prm.ri.w[i] : 0.f;
+        r.ow[i] = i < prm.ro.n ? (float)prm.ro.w[i] : 0.f;
+        r.iw[i] = i < prm.ri.n ? (float)prm.ri.w[i] : 0.f;
     }
-    a.delta = (float)prm.delta;
-    a.d2 = (float)prm.delta * (float)prm.delta;
-    a.c = (float)prm.c;
-    a.s = (float)prm.s;
-    a.caps = prm.ball == NLFEM_BALL_APPROXCAPS;
-    a.ids = nullptr;
-    a.npairs = 0;
-    a.acc = nullptr;
-    a.kkll = nullptr;
-    a.npairs_all = pc.npairs;
-    a.up_start = nullptr;
-    a.epos = nullptr;
-    a.klr = nullptr;
-    a.scale = 1.f;
-    a.maxabs = nullptr;
-    a.pstride = 1;
-    return a;
+    r.nqo = prm.ro.n;
+    return r;
+}
+
+// the request of one (mesh, parameters) for a work list (0: whole pairs, 1: cut pairs)
+FastReq make_req(Mesh& m, PairCache& pc, const Params& prm, int list) {
+    FastReq q;
+    std::memset(&q, 0, sizeof q);
+    q.pk = pc.pk.p; q.pl = pc.pl.p; q.pcls = pc.pcls.p;
+    q.ids = list == 0 ? pc.whole_ids.p : pc.cut_ids.p;
+    q.npairs = list == 0 ? pc.nwhole : pc.ncut;
+    q.klr = list == 0 ? pc.klr_whole.p : pc.klr_cut.p;
+    q.X = m.X.p; q.T = m.T.p; q.E32 = m.E32.p; q.det32 = m.det32.p;
+    q.delta = (float)prm.delta;
+    q.d2 = (float)prm.delta * (float)prm.delta;
+    q.c = (float)prm.c;
+    q.s = (float)prm.s;
+    q.delta64 = prm.delta;
+    q.delta2_64 = prm.delta2;
+    q.caps = prm.ball == NLFEM_BALL_APPROXCAPS;
+    q.npairs_all = pc.npairs;
+    q.up_start = pc.up_start.p;
+    q.epos = pc.epos.p;
+    q.scale_p = nullptr;
+    return q;
 }
 
 // Reorder of the cut list by fan-triangle count within windows of FAST_THREADS consecutive
@@ -570,12 +648,11 @@ void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st)
     if (n < 2) return;
     constexpr int WBITS = 7, W = 1 << WBITS;
     static_assert(W == FAST_THREADS, "sort windows are the blocks' pair ranges");
-    FastArgs a = fast_args(m, pc, prm);
-    a.ids = pc.cut_ids.p;
-    a.npairs = n;
+    const FastRule r = make_rule(prm);
+    const FastReq q = make_req(m, pc, prm, 1);
     DBuf<int> key;
     key.alloc(n, st);
-    k_cut_tris<<<nblk(n, 256), 256, 0, st>>>(a, key.p);
+    k_cut_tris<<<nblk(n, 256), 256, 0, st>>>(r, q, key.p);
     NLFEM_LAUNCH_CHECK();
     k_window_key<<<nblk(n, 256), 256, 0, st>>>(key.p, n, WBITS);
     NLFEM_LAUNCH_CHECK();
@@ -587,51 +664,71 @@ void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st)
     segmented_sort_i32(key.p, pc.cut_ids.p, ptr.p, nwin, (int)std::min<int64_t>(n, W), st);
 }
 
-template <int KER, int NQI, bool CAPS>
-static void launch_cut(const FastArgs& a, unsigned grid, cudaStream_t st) {
+template <int KER, int NQI, bool CAPS, bool BATCH>
+static void launch_cut(const FastRule& r, const FastLaunch& L, unsigned grid, cudaStream_t st) {
     constexpr int MAXP = CAPS ? 9 : 6;
     const size_t smem = sizeof(float2) * CHUNK * MAXP * FAST_THREADS;
-    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_cut<KER, NQI, CAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-    k_trunc_cut<KER, NQI, CAPS><<<grid, FAST_THREADS, smem, st>>>(a);
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_cut<KER, NQI, CAPS, BATCH>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_trunc_cut<KER, NQI, CAPS, BATCH><<<grid, FAST_THREADS, smem, st>>>(r, L);
 }
 
-template <int KER, int NQI>
-static void launch_pair_kernels(int pass, const FastArgs& a, unsigned grid, cudaStream_t st) {
-    if (pass == 0) k_trunc_whole<KER, NQI><<<grid, FAST_THREADS, 0, st>>>(a);
-    else if (a.caps) launch_cut<KER, NQI, true>(a, grid, st);
-    else launch_cut<KER, NQI, false>(a, grid, st);
+template <int KER, int NQI, bool BATCH>
+static void launch_class(int list, bool caps, const FastRule& r, const FastLaunch& L, unsigned grid,
+                         cudaStream_t st) {
+    if (list == 0) k_trunc_whole<KER, NQI, BATCH><<<grid, FAST_THREADS, 0, st>>>(r, L);
+    else if (caps) launch_cut<KER, NQI, true, BATCH>(r, L, grid, st);
+    else launch_cut<KER, NQI, false, BATCH>(r, L, grid, st);
+}
+
+template <bool BATCH>
+static void launch_kernel(const Params& prm, int list, const FastRule& r, const FastLaunch& L, unsigned grid,
+                          cudaStream_t st) {
+    const bool caps = prm.ball == NLFEM_BALL_APPROXCAPS;
+    if (prm.kernel == NLFEM_KERNEL_CONSTANT) {
+        if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_CONSTANT, 7, BATCH>(list, caps, r, L, grid, st);
+        else launch_class<NLFEM_KERNEL_CONSTANT, 16, BATCH>(list, caps, r, L, grid, st);
+    } else if (prm.kernel == NLFEM_KERNEL_FRACTIONAL) {
+        if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_FRACTIONAL, 7, BATCH>(list, caps, r, L, grid, st);
+        else launch_class<NLFEM_KERNEL_FRACTIONAL, 16, BATCH>(list, caps, r, L, grid, st);
+    } else {
+        if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_PERIDYNAMIC, 7, BATCH>(list, caps, r, L, grid, st);
+        else launch_class<NLFEM_KERNEL_PERIDYNAMIC, 16, BATCH>(list, caps, r, L, grid, st);
+    }
+    NLFEM_LAUNCH_CHECK();
+}
+
+// one launch of the whole-pair (list 0) or cut-pair (list 1) kernel over the tiles of L:
+// a request table (L.reqs, L.tiles) or the single request L.one
+void launch_fast_list(const Params& prm, int list, const FastLaunch& L, cudaStream_t st) {
+    const unsigned grid = (unsigned)std::min<int64_t>((L.ntiles + FAST_WARPS - 1) / FAST_WARPS, 152 * 64);
+    if (!grid) return;
+    const FastRule r = make_rule(prm);
+    if (L.reqs) launch_kernel<true>(prm, list, r, L, grid, st);
+    else launch_kernel<false>(prm, list, r, L, grid, st);
 }
 
 void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, const BulkAcc& b, cudaStream_t st,
                        cudaEvent_t* ev) {
-    FastArgs a = fast_args(m, pc, prm);
-    a.acc = b.acc;
-    a.kkll = b.kkll;
-    a.up_start = pc.up_start.p;
-    a.epos = pc.epos.p;
-    a.scale = b.scale;
-    a.maxabs = b.maxabs;
-    a.pstride = b.pstride;
-    for (int pass = 0; pass < 2; ++pass) {
-        a.ids = pass == 0 ? pc.whole_ids.p : pc.cut_ids.p;
-        const int64_t n = pass == 0 ? pc.nwhole : pc.ncut;
-        a.klr = pass == 0 ? pc.klr_whole.p : pc.klr_cut.p;
-        a.npairs = (n + b.pstride - 1) / b.pstride;
-        if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[pass], st));  // ev[0..2] bracket the two launches
-        const unsigned grid = (unsigned)std::min<int64_t>(nblk(a.npairs, FAST_THREADS), 152 * 64);
-        if (!grid) continue;
-        if (prm.kernel == NLFEM_KERNEL_CONSTANT) {
-            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_CONSTANT, 7>(pass, a, grid, st);
-            else launch_pair_kernels<NLFEM_KERNEL_CONSTANT, 16>(pass, a, grid, st);
-        } else if (prm.kernel == NLFEM_KERNEL_FRACTIONAL) {
-            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_FRACTIONAL, 7>(pass, a, grid, st);
-            else launch_pair_kernels<NLFEM_KERNEL_FRACTIONAL, 16>(pass, a, grid, st);
-        } else {
-            if (prm.ri.n == 7) launch_pair_kernels<NLFEM_KERNEL_PERIDYNAMIC, 7>(pass, a, grid, st);
-            else launch_pair_kernels<NLFEM_KERNEL_PERIDYNAMIC, 16>(pass, a, grid, st);
-        }
-        NLFEM_LAUNCH_CHECK();
+    FastReq q[2];
+    for (int list = 0; list < 2; ++list) {
+        q[list] = make_req(m, pc, prm, list);
+        q[list].acc = b.acc;
+        q[list].kkll = b.kkll;
+        q[list].scale_p = b.scale_p;
+        q[list].maxabs = b.maxabs;
+    }
+    const int pilot = b.pstride > 1 ? (int)b.pstride : 0;
+    for (int list = 0; list < 2; ++list) {
+        if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[list], st));  // ev[0..2] bracket the two launches
+        const int64_t n = pilot ? (q[list].npairs + pilot - 1) / pilot : q[list].npairs;
+        FastLaunch L;
+        L.reqs = nullptr;
+        L.tiles = nullptr;
+        L.ntiles = (n + 31) / 32;
+        L.pilot = pilot;
+        L.one = q[list];
+        launch_fast_list(prm, list, L, st);
     }
     if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
 }
