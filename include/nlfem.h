@@ -139,6 +139,21 @@ void nlfem_params_default(nlfem_params* p, int kernel);
 int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* f_nodal,
                    void* stream, nlfem_system_t* out);
 
+/*
+ * Batched assembly: the same result as n calls of nlfem_assemble (every system is the same
+ * bits), with the whole-pair and cut-pair kernels of all FP32-bulk items of one kernel class
+ * (kernel type, outer and inner rule, ball) fused into one persistent launch each, so many
+ * small meshes keep the GPU busy (a batching of the work of Sec. 3.4 across problems; the
+ * paper assembles one problem at a time). meshes: n distinct mesh handles; params: n
+ * parameter sets; f_nodal: NULL or n pointers (each NULL, host or device, as for
+ * nlfem_assemble); out: n system handles, owned by the caller as for nlfem_assemble. FP64
+ * items are assembled one after the other in the same call. The ms_* fields of every
+ * system's info describe the whole batch. Errors: INVALID_ARG (NULL, n < 0, a mesh twice),
+ * UNSUPPORTED, BUDGET (per item), OOM, CUDA; on error no system is returned.
+ */
+int nlfem_batch_assemble(const nlfem_mesh_t* meshes, const nlfem_params* params, const double* const* f_nodal,
+                         int n, void* stream, nlfem_system_t* out);
+
 /* Borrowed device pointers of the CSR matrix (valid until nlfem_system_destroy):
  * row_ptr [nrows + 1] int64, col [nnz] int32 (sorted per row), val [nnz] FP64. Dof d of
  * node m is row m * ndof + d. */

@@ -134,3 +134,27 @@ def assemble(mesh: Mesh, kernel="constant", delta=0.1, s=0.5, kconst=None, ball=
     f = None if f_nodal is None else _as_dev(f_nodal, torch.float64).reshape(-1)
     h = B.nlfem_assemble(mesh.handle, p, f, stream)
     return System(mesh, h)
+
+
+def assemble_batch(meshes, params, f_nodal=None, stream=None) -> list:
+    """Assemble several systems with fused bulk launches (nlfem_batch_assemble).
+
+    meshes: distinct Mesh objects; params: one dict of assemble() keyword arguments per mesh
+    (kernel, delta, s, ball, quad_outer, quad_inner, precision, ...); f_nodal: None or a list
+    of nodal load arrays (or None). Every System equals the one assemble() gives.
+    """
+    torch = _torch()
+    ps = []
+    for p in params:
+        q = dict(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7, quad_inner=7,
+                 duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0)
+        q.update(p)
+        ps.append(B.make_params(q["kernel"], q["delta"], q["s"], q["kconst"], q["ball"], q["quad_outer"],
+                                q["quad_inner"], q["duffy_gauss"], q["close_rule"], q["precision"],
+                                q["mem_budget_bytes"]))
+    fs = None
+    if f_nodal is not None:
+        fs = [None if f is None else _as_dev(f, torch.float64).reshape(-1) for f in f_nodal]
+    hs = B.nlfem_batch_assemble([m.handle for m in meshes], ps, fs, stream)
+    return [System(m, h) for m, h in zip(meshes, hs)]
+

@@ -94,6 +94,8 @@ def load(build_if_missing: bool = True):
         lib.nlfem_mesh_device_bytes.argtypes = [vp]
         lib.nlfem_mesh_device_bytes.restype = i64
         lib.nlfem_trim_memory.argtypes = [vp]
+        lib.nlfem_batch_assemble.argtypes = [C.POINTER(vp), C.POINTER(nlfem_params), C.POINTER(vp), ip, vp,
+                                             C.POINTER(vp)]
         lib.nlfem_pairs_noalloc.argtypes = [vp, i64, vp, i64, dp, ip, ip, vp, vp, i64, C.POINTER(i64), vp]
         _lib = lib
     return _lib
@@ -153,6 +155,20 @@ def nlfem_assemble(mesh, params: nlfem_params, f_nodal=None, stream=None):
     h = C.c_void_p()
     _check(load().nlfem_assemble(mesh, C.byref(params), _ptr(f_nodal), _stream(stream), C.byref(h)))
     return h
+
+
+def nlfem_batch_assemble(meshes, params, f_nodal=None, stream=None):
+    """n systems with fused bulk launches; f_nodal: None or a list of (None | tensor)."""
+    n = len(meshes)
+    vp = C.c_void_p
+    mh = (vp * n)(*[m.value if isinstance(m, C.c_void_p) else m for m in meshes])
+    pa = (nlfem_params * n)(*params)
+    fp = None
+    if f_nodal is not None:
+        fp = (vp * n)(*[_ptr(f) for f in f_nodal])
+    out = (vp * n)()
+    _check(load().nlfem_batch_assemble(mh, pa, fp, n, _stream(stream), out))
+    return [C.c_void_p(h) for h in out]
 
 
 def nlfem_system_csr(sys):

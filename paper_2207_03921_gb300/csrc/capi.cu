@@ -272,6 +272,66 @@ int nlfem_mesh_pairs(nlfem_mesh_t mesh, const int32_t** k, const int32_t** l, in
     NLFEM_API_END
 }
 
+// The pair list, pattern and accumulation index of (mesh, delta, ball, outer rule, close
+// rule), built unless the mesh handle holds them already.
+static std::shared_ptr<PairCache> ensure_cache(Mesh& m, const Params& P, cudaStream_t st, cudaEvent_t* ev,
+                                               double& t_pairs, double& t_pattern, bool& cached) {
+    std::shared_ptr<PairCache> pc = m.cache;
+    cached = pc && pc->delta == P.delta && pc->ball == P.ball && pc->nqo == P.ro.n && pc->ndof == P.ndof &&
+             pc->close_mode == close_mode(P);
+    t_pairs = t_pattern = 0;
+    if (cached) return pc;
+    m.cache.reset();
+    pc = std::make_shared<PairCache>();
+    pc->delta = P.delta;
+    pc->ball = P.ball;
+    pc->nqo = P.ro.n;
+    pc->ndof = P.ndof;
+    pc->close_mode = close_mode(P);
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+    build_pairs(m, P, *pc, st);
+    order_cut_pairs(m, *pc, P, st);
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+    build_pattern(m, *pc, st);
+    build_bulk_index(m, *pc, st);
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
+    NLFEM_CUDA_TRY(cudaEventSynchronize(ev[2]));
+    t_pairs = elapsed_ms(ev[0], ev[1]);
+    t_pattern = elapsed_ms(ev[1], ev[2]);
+    pc->t_pairs_ms = t_pairs;
+    pc->t_pattern_ms = t_pattern;
+    m.cache = pc;
+    return pc;
+}
+
+// device bytes an assembly of (m, pc, P) needs beyond what the mesh handle holds
+static int64_t assembly_bytes(const Mesh& m, const PairCache& pc, const Params& P) {
+    const int64_t NE = contrib_entries(P.ndof);
+    const int64_t nc = P.ndof == 1 ? 1 : 3;
+    const int64_t work = P.precision == NLFEM_PREC_FP32_BULK
+                             ? pc.n_upper * nc * 8 + pc.nduffy * NE * 4 + pc.npairs * 12 * nc * 4
+                             : pc.npairs * NE * 8;
+    return work + pc.nnz * 8 + pc.N * 8;
+}
+
+static void fill_info(System& S, Mesh& m, const PairCache& pc, double t_pairs, double t_pattern, bool cached) {
+    nlfem_assembly_info& I = S.info;
+    std::memset(&I, 0, sizeof I);
+    I.npairs = pc.npairs;
+    I.pairs_separated = pc.counts[0];
+    I.pairs_vertex = pc.counts[1];
+    I.pairs_edge = pc.counts[2];
+    I.pairs_identical = pc.counts[3];
+    I.nnz = pc.nnz;
+    I.device_bytes = m.device_bytes() + (int64_t)(S.val.bytes() + S.F.bytes());
+    I.ms_pairs = t_pairs;
+    I.ms_pattern = t_pattern;
+    I.pairs_whole = pc.nwhole;
+    I.n_upper = pc.n_upper;
+    I.n_contrib = pc.ncontrib;
+    I.cached = cached ? 1 : 0;
+}
+
 int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* f_nodal, void* stream,
                    nlfem_system_t* out) {
     NLFEM_API_BEGIN
@@ -289,42 +349,11 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
             for (int i = 0; i < 12; ++i) cudaEventDestroy(e[i]);
         }
     } guard{ev};
-    std::shared_ptr<PairCache> pc = m.cache;
-    bool cached = pc && pc->delta == P.delta && pc->ball == P.ball && pc->nqo == P.ro.n &&
-                  pc->ndof == P.ndof && pc->close_mode == close_mode(P);
     double t_pairs = 0, t_pattern = 0;
-    if (!cached) {
-        m.cache.reset();
-        pc = std::make_shared<PairCache>();
-        {
-            pc->delta = P.delta;
-            pc->ball = P.ball;
-            pc->nqo = P.ro.n;
-            pc->ndof = P.ndof;
-            pc->close_mode = close_mode(P);
-            NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
-            build_pairs(m, P, *pc, st);
-            order_cut_pairs(m, *pc, P, st);
-            NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
-            build_pattern(m, *pc, st);
-            build_bulk_index(m, *pc, st);
-            NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
-            NLFEM_CUDA_TRY(cudaEventSynchronize(ev[2]));
-            t_pairs = elapsed_ms(ev[0], ev[1]);
-            t_pattern = elapsed_ms(ev[1], ev[2]);
-            pc->t_pairs_ms = t_pairs;
-            pc->t_pattern_ms = t_pattern;
-        }
-        m.cache = pc;
-    }
+    bool cached = false;
+    std::shared_ptr<PairCache> pc = ensure_cache(m, P, st, ev, t_pairs, t_pattern, cached);
     const int64_t NE = contrib_entries(P.ndof);
-    // working memory of the values: per-pair records (FP64 plain) or the fixed-point upper
-    // entries plus the close-list records (FP32 bulk)
-    const int64_t work = P.precision == NLFEM_PREC_FP32_BULK
-                             ? pc->n_upper * (P.ndof == 1 ? 1 : 3) * 8 + pc->nduffy * NE * 4 +
-                                   pc->npairs * 12 * (P.ndof == 1 ? 1 : 3) * 4
-                             : pc->npairs * NE * 8;
-    int64_t need = work + pc->nnz * 8 + pc->N * 8 + m.device_bytes();
+    const int64_t need = assembly_bytes(m, *pc, P) + m.device_bytes();
     if (params->mem_budget_bytes > 0 && need > params->mem_budget_bytes)
         throw Error{NLFEM_ERR_BUDGET, "assembly needs " + std::to_string(need) + " device bytes, budget is " +
                                           std::to_string(params->mem_budget_bytes)};
@@ -375,32 +404,136 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
         S.contrib64.release();
         S.acc.release();
         S.kkll.release();
+        fill_info(S, m, *pc, t_pairs, t_pattern, cached);
         nlfem_assembly_info& I = S.info;
-        std::memset(&I, 0, sizeof I);
-        I.npairs = pc->npairs;
-        I.pairs_separated = pc->counts[0];
-        I.pairs_vertex = pc->counts[1];
-        I.pairs_edge = pc->counts[2];
-        I.pairs_identical = pc->counts[3];
-        I.nnz = pc->nnz;
-        I.device_bytes = m.device_bytes() + (int64_t)(S.val.bytes() + S.F.bytes());
-        I.ms_pairs = t_pairs;
-        I.ms_pattern = t_pattern;
         I.ms_quadrature = elapsed_ms(ev[3], ev[4]);
         I.ms_close = elapsed_ms(ev[6], ev[7]);
         I.ms_whole = elapsed_ms(ev[8], ev[9]);
         I.ms_cut = elapsed_ms(ev[9], ev[10]);
         I.ms_sums = elapsed_ms(ev[10], ev[11]);
-        I.pairs_whole = pc->nwhole;
-        I.n_upper = pc->n_upper;
-        I.n_contrib = pc->ncontrib;
         I.ms_reduce = elapsed_ms(ev[4], ev[5]);
-        I.cached = cached ? 1 : 0;
     } catch (...) {
         delete h;
         throw;
     }
     *out = h;
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+int nlfem_batch_assemble(const nlfem_mesh_t* meshes, const nlfem_params* params, const double* const* f_nodal,
+                         int n, void* stream, nlfem_system_t* out) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(meshes && params && out && n >= 0, NLFEM_ERR_INVALID_ARG, "NULL argument or n < 0");
+    for (int i = 0; i < n; ++i) {
+        out[i] = nullptr;
+        NLFEM_CHECK(meshes[i] != nullptr, NLFEM_ERR_INVALID_ARG, "NULL mesh handle");
+        for (int j = 0; j < i; ++j)
+            NLFEM_CHECK(meshes[j] != meshes[i], NLFEM_ERR_INVALID_ARG,
+                        "a mesh handle appears twice in one batch (its pair list belongs to one parameter set)");
+    }
+    if (n == 0) return NLFEM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[12];
+    for (int i = 0; i < 12; ++i) NLFEM_CUDA_TRY(cudaEventCreate(&ev[i]));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 12; ++i) cudaEventDestroy(e[i]);
+        }
+    } guard{ev};
+    std::vector<std::unique_ptr<nlfem_system_s>> hs(n);
+    std::vector<Params> P(n);
+    std::vector<std::shared_ptr<PairCache>> pcs(n);
+    std::vector<double> tp(n), tq(n);
+    std::vector<char> cached(n);
+    std::vector<DBuf<double>> fdev(n);
+    std::vector<const double*> fptr(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        Mesh& m = meshes[i]->m;
+        P[i] = make_params(params[i], m.ndof);
+        bool c = false;
+        pcs[i] = ensure_cache(m, P[i], st, ev, tp[i], tq[i], c);
+        cached[i] = c;
+        const int64_t need = assembly_bytes(m, *pcs[i], P[i]) + m.device_bytes();
+        if (params[i].mem_budget_bytes > 0 && need > params[i].mem_budget_bytes)
+            throw Error{NLFEM_ERR_BUDGET, "batch item " + std::to_string(i) + " needs " + std::to_string(need) +
+                                              " device bytes, budget is " + std::to_string(params[i].mem_budget_bytes)};
+        hs[i].reset(new nlfem_system_s());
+        System& S = hs[i]->s;
+        S.mesh = &m;
+        S.pc = pcs[i];
+        S.prm = P[i];
+        S.N = pcs[i]->N;
+        S.nnz = pcs[i]->nnz;
+        S.val.alloc(pcs[i]->nnz, st);
+        S.F.alloc(pcs[i]->N, st);
+        if (f_nodal && f_nodal[i]) {
+            if (is_device_ptr(f_nodal[i])) fptr[i] = f_nodal[i];
+            else {
+                upload(fdev[i], f_nodal[i], (size_t)(m.M * P[i].ndof), st);
+                fptr[i] = fdev[i].p;
+            }
+        }
+    }
+    // FP64 systems one by one; FP32-bulk systems with fused launches
+    std::vector<BatchSys> bulk;
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[3], st));
+    for (int i = 0; i < n; ++i) {
+        Mesh& m = meshes[i]->m;
+        System& S = hs[i]->s;
+        if (P[i].precision == NLFEM_PREC_FP32_BULK) {
+            bulk.push_back(BatchSys{&m, pcs[i].get(), P[i], &S});
+            continue;
+        }
+        S.contrib64.alloc(pcs[i]->npairs * contrib_entries(P[i].ndof), st);
+        run_quadrature(m, *pcs[i], P[i], S, st, ev + 6);
+        run_reduction(m, *pcs[i], P[i], S, st);
+        run_load(m, P[i], fptr[i], S, st);
+        S.contrib64.release();
+    }
+    if (!bulk.empty()) run_bulk_batch(bulk, st, ev + 6);
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[4], st));
+    std::vector<int> redo(n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (P[i].precision != NLFEM_PREC_FP32_BULK) continue;
+        Mesh& m = meshes[i]->m;
+        System& S = hs[i]->s;
+        run_reduction(m, *pcs[i], P[i], S, st);
+        run_load(m, P[i], fptr[i], S, st);
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&redo[i], &S.fix.p->redo, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    const double ms_q = elapsed_ms(ev[3], ev[4]), ms_r = elapsed_ms(ev[4], ev[5]);
+    const bool any_bulk = !bulk.empty();
+    for (int i = 0; i < n; ++i) {
+        Mesh& m = meshes[i]->m;
+        System& S = hs[i]->s;
+        if (redo[i]) {
+            bulk_redo(m, *pcs[i], P[i], S, st, ev + 6);
+            run_reduction(m, *pcs[i], P[i], S, st);
+            int again = 0;
+            NLFEM_CUDA_TRY(cudaMemcpyAsync(&again, &S.fix.p->redo, sizeof again, cudaMemcpyDeviceToHost, st));
+            NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+            NLFEM_CHECK(!again, NLFEM_ERR_CUDA, "internal error: fixed-point scale did not settle");
+        }
+        S.contrib32.release();
+        S.acc.release();
+        S.kkll.release();
+        fill_info(S, m, *pcs[i], tp[i], tq[i], cached[i] != 0);
+        // times of the whole batch: the fused launches serve every system
+        S.info.ms_quadrature = ms_q;
+        S.info.ms_reduce = ms_r;
+        if (any_bulk) {
+            S.info.ms_close = elapsed_ms(ev[6], ev[7]);
+            S.info.ms_whole = elapsed_ms(ev[8], ev[9]);
+            S.info.ms_cut = elapsed_ms(ev[9], ev[10]);
+            S.info.ms_sums = elapsed_ms(ev[10], ev[11]);
+        }
+    }
+    for (int i = 0; i < n; ++i) out[i] = hs[i].release();
     return NLFEM_OK;
     NLFEM_API_END
 }

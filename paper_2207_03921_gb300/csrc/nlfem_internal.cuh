@@ -238,6 +238,23 @@ struct BulkAcc {
 void bulk_redo(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev);
 void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, const BulkAcc& b, cudaStream_t st,
                        cudaEvent_t* ev);
+// one request of a batched launch (all items of one call share the kernel class: kernel
+// type, outer and inner rule, ball)
+struct BulkItem {
+    Mesh* m;
+    PairCache* pc;
+    Params prm;
+    BulkAcc b;
+};
+void launch_trunc_fast_batch(const std::vector<BulkItem>& items, int list, int pilot, cudaStream_t st);
+// FP32-bulk assembly of several systems with fused bulk launches (quad.cu)
+struct BatchSys {
+    Mesh* m;
+    PairCache* pc;
+    Params prm;
+    System* sys;
+};
+void run_bulk_batch(std::vector<BatchSys>& items, cudaStream_t st, cudaEvent_t* ev);
 void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st);
 void build_slots(Mesh& m, PairCache& pc, cudaStream_t st);
 void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st);

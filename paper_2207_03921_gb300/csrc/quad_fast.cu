@@ -19,6 +19,7 @@
 // code.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "nlfem_internal.cuh"
 
@@ -67,11 +68,12 @@ struct FastReq {
 // table, tile t of request 0 starts at 32 t. pilot > 0: only every pilot-th pair of each
 // list, largest |value| only.
 struct FastLaunch {
-    const FastReq* reqs;  // batched launches: the request table (device memory)
-    const int2* tiles;
+    const FastReq* reqs;      // batched launches: the request table (device memory)
+    const int64_t* tile_off;  //   and the first tile of each request [nreq + 1]
+    int nreq;
     int64_t ntiles;
     int pilot;
-    FastReq one;          // single-request launches: the request itself (constant bank)
+    FastReq one;              // single-request launches: the request itself (constant bank)
 };
 
 template <int NC>
@@ -220,9 +222,17 @@ __device__ __forceinline__ void flush_max(unsigned int* maxabs, float vmax) {
 
 static constexpr int FAST_WARPS = FAST_THREADS / 32;
 
-// tile t of a launch: its request and first list position
+// tile t of a launch: its request (binary search over the requests' first tiles) and first
+// list position
 __device__ __forceinline__ int2 tile_of(const FastLaunch& L, int64_t t) {
-    return L.tiles ? L.tiles[t] : make_int2(0, (int)(t * 32));
+    if (!L.reqs) return make_int2(0, (int)(t * 32));
+    int lo = 0, hi = L.nreq - 1;  // the last request whose first tile is <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.tile_off[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return make_int2(lo, (int)((t - L.tile_off[lo]) * 32));
 }
 
 // the request of a tile into the warp's shared-memory copy (all lanes of the warp call it;
@@ -699,13 +709,60 @@ static void launch_kernel(const Params& prm, int list, const FastRule& r, const 
 }
 
 // one launch of the whole-pair (list 0) or cut-pair (list 1) kernel over the tiles of L:
-// a request table (L.reqs, L.tiles) or the single request L.one
+// a request table (L.reqs, L.tile_off) or the single request L.one
 void launch_fast_list(const Params& prm, int list, const FastLaunch& L, cudaStream_t st) {
     const unsigned grid = (unsigned)std::min<int64_t>((L.ntiles + FAST_WARPS - 1) / FAST_WARPS, 152 * 64);
     if (!grid) return;
     const FastRule r = make_rule(prm);
     if (L.reqs) launch_kernel<true>(prm, list, r, L, grid, st);
     else launch_kernel<false>(prm, list, r, L, grid, st);
+}
+
+// One launch of list `list` (0 whole, 1 cut) over the pairs of several requests of one kernel
+// class (the rules and kernel type of prm; per-request delta, constants and buffers in reqs).
+void launch_fast_batch(const Params& prm, int list, const std::vector<FastReq>& reqs, int pilot, cudaStream_t st) {
+    const int n = (int)reqs.size();
+    if (n == 0) return;
+    std::vector<int64_t> off(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        const int64_t np = pilot ? (reqs[i].npairs + pilot - 1) / pilot : reqs[i].npairs;
+        off[i + 1] = off[i] + (np + 31) / 32;
+    }
+    if (off[n] == 0) return;
+    DBuf<FastReq> dq;
+    DBuf<int64_t> doff;
+    dq.alloc(n, st);
+    doff.alloc(n + 1, st);
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(dq.p, reqs.data(), sizeof(FastReq) * n, cudaMemcpyHostToDevice, st));
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+    FastLaunch L;
+    std::memset(&L, 0, sizeof L);
+    L.reqs = dq.p;
+    L.tile_off = doff.p;
+    L.nreq = n;
+    L.ntiles = off[n];
+    L.pilot = pilot;
+    launch_fast_list(prm, list, L, st);
+    // copies from pageable host memory are staged before cudaMemcpyAsync returns, and the
+    // device tables are freed in stream order after the launch
+}
+
+// the whole-pair (list 0) or cut-pair (list 1) launch of a batch of one kernel class
+// (items[0]'s rules)
+void launch_trunc_fast_batch(const std::vector<BulkItem>& items, int list, int pilot, cudaStream_t st) {
+    {
+        std::vector<FastReq> reqs;
+        reqs.reserve(items.size());
+        for (const BulkItem& it : items) {
+            FastReq q = make_req(*it.m, *it.pc, it.prm, list);
+            q.acc = it.b.acc;
+            q.kkll = it.b.kkll;
+            q.scale_p = it.b.scale_p;
+            q.maxabs = it.b.maxabs;
+            reqs.push_back(q);
+        }
+        launch_fast_batch(items[0].prm, list, reqs, pilot, st);
+    }
 }
 
 void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, const BulkAcc& b, cudaStream_t st,
@@ -724,7 +781,8 @@ void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, const BulkAcc&
         const int64_t n = pilot ? (q[list].npairs + pilot - 1) / pilot : q[list].npairs;
         FastLaunch L;
         L.reqs = nullptr;
-        L.tiles = nullptr;
+        L.tile_off = nullptr;
+        L.nreq = 1;
         L.ntiles = (n + 31) / 32;
         L.pilot = pilot;
         L.one = q[list];

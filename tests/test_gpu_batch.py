@@ -1,0 +1,62 @@
+"""Batched assembly (nlfem_batch_assemble): every system equals its single assembly bit for
+bit, across kernel classes (constant nocaps, fractional approxcaps with the singular rule,
+peridynamics) and with an FP64 item in the same call; error cases."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2207_03921_gb300 import Mesh, NlfemError, assemble, assemble_batch  # noqa: E402
+from synth import meshes  # noqa: E402
+
+
+def _items():
+    specs = [s for s in meshes.serving_requests(n_requests=128) if s["K_target"] <= 3000][:6]
+    out = []
+    for sp in specs:
+        m = meshes.request_mesh(sp)
+        kw = dict(kernel=sp["kernel"], delta=sp["delta"], s=sp["s"],
+                  ball="approxcaps" if sp["kernel"] == "fractional" else "nocaps", precision="fp32_bulk")
+        out.append((m, 1, kw))
+    # a peridynamic item and an FP64 item
+    m3 = meshes.structured(-0.1, 1.1, 24, name="s24")
+    out.append((m3, 2, dict(kernel="peridynamic", delta=0.1, precision="fp32_bulk")))
+    out.append((meshes.structured(-0.1, 1.1, 24, name="s24b"), 1, dict(kernel="constant", delta=0.1, precision="fp64")))
+    return out
+
+
+def _host(S):
+    rp, col, val = (t.cpu().numpy() for t in S.csr())
+    return rp, col, val, S.rhs().cpu().numpy()
+
+
+def test_batch_equals_single_bitwise():
+    items = _items()
+    assert len({(kw["kernel"], kw.get("ball")) for _, _, kw in items}) >= 3
+    single = []
+    for m, nd, kw in items:
+        mesh = Mesh.from_synth(m, nd)
+        f = np.linspace(-1.0, 1.0, m.M * nd)
+        single.append(_host(assemble(mesh, f_nodal=f, **kw)))
+    ms = [Mesh.from_synth(m, nd) for m, nd, _ in items]
+    fs = [np.linspace(-1.0, 1.0, m.M * nd) for m, nd, _ in items]
+    systems = assemble_batch(ms, [kw for _, _, kw in items], fs)
+    for (rp0, col0, val0, F0), S in zip(single, systems):
+        rp, col, val, F = _host(S)
+        assert np.array_equal(rp, rp0) and np.array_equal(col, col0)
+        assert np.array_equal(val, val0)
+        assert np.array_equal(F, F0)
+
+
+def test_batch_cached_second_call_and_errors():
+    m = meshes.structured(-0.1, 1.1, 20, name="s20")
+    a, b = Mesh.from_synth(m), Mesh.from_synth(m)
+    kw = dict(kernel="constant", delta=0.1, precision="fp32_bulk")
+    first = assemble_batch([a, b], [kw, kw])
+    again = assemble_batch([a, b], [kw, kw])  # pair lists and patterns cached in the handles
+    assert again[0].info()["cached"] == 1
+    assert np.array_equal(first[0].csr()[2].cpu().numpy(), again[1].csr()[2].cpu().numpy())
+    with pytest.raises(NlfemError):
+        assemble_batch([a, a], [kw, kw])
+    assert assemble_batch([], []) == []
