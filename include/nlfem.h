@@ -56,6 +56,7 @@ extern "C" {
 
 typedef struct nlfem_mesh_s* nlfem_mesh_t;
 typedef struct nlfem_system_s* nlfem_system_t;
+typedef struct nlfem_batch_s* nlfem_batch_t;
 
 typedef struct {
     int kernel;              /* NLFEM_KERNEL_* */
@@ -138,6 +139,24 @@ void nlfem_params_default(nlfem_params* p, int kernel);
  */
 int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* f_nodal,
                    void* stream, nlfem_system_t* out);
+
+/*
+ * Persistent batch plan (FP32 bulk only): the systems of n meshes stay on the device and
+ * their values are re-assembled in place by replaying one CUDA graph (close lists, pilot,
+ * scale, fused bulk launches, element sums, conversion to CSR, load vectors), so repeated
+ * assemblies of many small problems pay no per-kernel launch cost. nlfem_batch_create does
+ * the cold work and one assembly, then captures the graph (the load data f_nodal is copied
+ * into the plan); nlfem_batch_run replays it on stream (ms, if not NULL, receives its device
+ * time); nlfem_batch_system returns system i, owned by the plan (valid until
+ * nlfem_batch_destroy; do not pass it to nlfem_system_destroy). Every run gives the same
+ * bits as nlfem_assemble. The paper has no counterpart (execution strategy of this
+ * implementation). Errors: as nlfem_batch_assemble; UNSUPPORTED for an FP64 item.
+ */
+int nlfem_batch_create(const nlfem_mesh_t* meshes, const nlfem_params* params, const double* const* f_nodal,
+                       int n, void* stream, nlfem_batch_t* out);
+int nlfem_batch_run(nlfem_batch_t batch, void* stream, double* ms);
+int nlfem_batch_system(nlfem_batch_t batch, int i, nlfem_system_t* out);
+void nlfem_batch_destroy(nlfem_batch_t batch);
 
 /*
  * Batched assembly: the same result as n calls of nlfem_assemble (every system is the same

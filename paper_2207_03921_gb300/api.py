@@ -72,9 +72,10 @@ class Mesh:
 class System:
     """An assembled stiffness matrix and load vector (nlfem_assemble)."""
 
-    def __init__(self, mesh: Mesh, handle):
+    def __init__(self, mesh: Mesh, handle, owner=None):
         self.mesh = mesh
         self.handle = handle
+        self._owner = owner  # a BatchPlan that owns the handle, or None
         rp, col, val, n, nnz = B.nlfem_system_csr(handle)
         self.N, self.nnz = n, nnz
         self._ptrs = (rp, col, val)
@@ -119,9 +120,9 @@ class System:
 
     def __del__(self):
         h = getattr(self, "handle", None)
-        if h:
+        if h and getattr(self, "_owner", None) is None:
             B.nlfem_system_destroy(h)
-            self.handle = None
+        self.handle = None
 
 
 def assemble(mesh: Mesh, kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7,
@@ -144,6 +145,15 @@ def assemble_batch(meshes, params, f_nodal=None, stream=None) -> list:
     of nodal load arrays (or None). Every System equals the one assemble() gives.
     """
     torch = _torch()
+    ps = _params_list(params)
+    fs = None
+    if f_nodal is not None:
+        fs = [None if f is None else _as_dev(f, torch.float64).reshape(-1) for f in f_nodal]
+    hs = B.nlfem_batch_assemble([m.handle for m in meshes], ps, fs, stream)
+    return [System(m, h) for m, h in zip(meshes, hs)]
+
+
+def _params_list(params):
     ps = []
     for p in params:
         q = dict(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7, quad_inner=7,
@@ -152,9 +162,32 @@ def assemble_batch(meshes, params, f_nodal=None, stream=None) -> list:
         ps.append(B.make_params(q["kernel"], q["delta"], q["s"], q["kconst"], q["ball"], q["quad_outer"],
                                 q["quad_inner"], q["duffy_gauss"], q["close_rule"], q["precision"],
                                 q["mem_budget_bytes"]))
-    fs = None
-    if f_nodal is not None:
-        fs = [None if f is None else _as_dev(f, torch.float64).reshape(-1) for f in f_nodal]
-    hs = B.nlfem_batch_assemble([m.handle for m in meshes], ps, fs, stream)
-    return [System(m, h) for m, h in zip(meshes, hs)]
+    return ps
+
+
+class BatchPlan:
+    """Systems of several meshes kept on the GPU and re-assembled by one CUDA graph replay
+    (nlfem_batch_create / nlfem_batch_run). FP32 bulk only."""
+
+    def __init__(self, meshes, params, f_nodal=None, stream=None):
+        torch = _torch()
+        self.meshes = list(meshes)
+        fs = None
+        if f_nodal is not None:
+            fs = [None if f is None else _as_dev(f, torch.float64).reshape(-1) for f in f_nodal]
+        self.handle = B.nlfem_batch_create([m.handle for m in self.meshes], _params_list(params), fs, stream)
+        self.systems = [System(m, B.nlfem_batch_system(self.handle, i), owner=self)
+                        for i, m in enumerate(self.meshes)]
+
+    def run(self, stream=None) -> float:
+        """Re-assemble every system in place; returns the device time of the replay in ms."""
+        return B.nlfem_batch_run(self.handle, stream)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            for s in getattr(self, "systems", []):
+                s.handle = None
+            B.nlfem_batch_destroy(h)
+            self.handle = None
 

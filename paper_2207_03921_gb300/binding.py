@@ -96,6 +96,12 @@ def load(build_if_missing: bool = True):
         lib.nlfem_trim_memory.argtypes = [vp]
         lib.nlfem_batch_assemble.argtypes = [C.POINTER(vp), C.POINTER(nlfem_params), C.POINTER(vp), ip, vp,
                                              C.POINTER(vp)]
+        lib.nlfem_batch_create.argtypes = [C.POINTER(vp), C.POINTER(nlfem_params), C.POINTER(vp), ip, vp,
+                                           C.POINTER(vp)]
+        lib.nlfem_batch_run.argtypes = [vp, vp, C.POINTER(C.c_double)]
+        lib.nlfem_batch_system.argtypes = [vp, ip, C.POINTER(vp)]
+        lib.nlfem_batch_destroy.argtypes = [vp]
+        lib.nlfem_batch_destroy.restype = None
         lib.nlfem_pairs_noalloc.argtypes = [vp, i64, vp, i64, dp, ip, ip, vp, vp, i64, C.POINTER(i64), vp]
         _lib = lib
     return _lib
@@ -169,6 +175,33 @@ def nlfem_batch_assemble(meshes, params, f_nodal=None, stream=None):
     out = (vp * n)()
     _check(load().nlfem_batch_assemble(mh, pa, fp, n, _stream(stream), out))
     return [C.c_void_p(h) for h in out]
+
+
+def nlfem_batch_create(meshes, params, f_nodal=None, stream=None):
+    n = len(meshes)
+    vp = C.c_void_p
+    mh = (vp * n)(*[m.value if isinstance(m, C.c_void_p) else m for m in meshes])
+    pa = (nlfem_params * n)(*params)
+    fp = None if f_nodal is None else (vp * n)(*[_ptr(f) for f in f_nodal])
+    h = C.c_void_p()
+    _check(load().nlfem_batch_create(mh, pa, fp, n, _stream(stream), C.byref(h)))
+    return h
+
+
+def nlfem_batch_run(batch, stream=None) -> float:
+    ms = C.c_double(0.0)
+    _check(load().nlfem_batch_run(batch, _stream(stream), C.byref(ms)))
+    return ms.value
+
+
+def nlfem_batch_system(batch, i: int):
+    h = C.c_void_p()
+    _check(load().nlfem_batch_system(batch, int(i), C.byref(h)))
+    return h
+
+
+def nlfem_batch_destroy(batch):
+    load().nlfem_batch_destroy(batch)
 
 
 def nlfem_system_csr(sys):

@@ -150,6 +150,20 @@ struct nlfem_mesh_s {
 struct nlfem_system_s {
     System s;
 };
+struct nlfem_batch_s {
+    std::vector<std::unique_ptr<nlfem_system_s>> sys;
+    std::vector<DBuf<double>> f;  // the load data, kept on the device
+    std::vector<const double*> fptr;
+    BatchExec exec;
+    cudaStream_t cap = nullptr;   // capture stream (the legacy stream cannot be captured)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec_graph = nullptr;
+    ~nlfem_batch_s() {
+        if (exec_graph) cudaGraphExecDestroy(exec_graph);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
 
 #define NLFEM_API_BEGIN try {
 #define NLFEM_API_END                                   \
@@ -537,6 +551,137 @@ int nlfem_batch_assemble(const nlfem_mesh_t* meshes, const nlfem_params* params,
     return NLFEM_OK;
     NLFEM_API_END
 }
+
+// redo flags of the plan's systems after a run, and the redo of the flagged ones (rare)
+static void batch_settle(nlfem_batch_s& b, cudaStream_t st, cudaEvent_t* ev) {
+    const size_t n = b.exec.items.size();
+    std::vector<int> redo(n, 0);
+    for (size_t i = 0; i < n; ++i)
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&redo[i], &b.exec.items[i].sys->fix.p->redo, sizeof(int),
+                                       cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < n; ++i) {
+        if (!redo[i]) continue;
+        BatchSys& it = b.exec.items[i];
+        bulk_redo(*it.m, *it.pc, it.prm, *it.sys, st, ev);
+        run_reduction(*it.m, *it.pc, it.prm, *it.sys, st);
+        int again = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&again, &it.sys->fix.p->redo, sizeof again, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        NLFEM_CHECK(!again, NLFEM_ERR_CUDA, "internal error: fixed-point scale did not settle");
+    }
+}
+
+int nlfem_batch_create(const nlfem_mesh_t* meshes, const nlfem_params* params, const double* const* f_nodal,
+                       int n, void* stream, nlfem_batch_t* out) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(meshes && params && out && n >= 1, NLFEM_ERR_INVALID_ARG, "NULL argument or n < 1");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        NLFEM_CHECK(meshes[i] != nullptr, NLFEM_ERR_INVALID_ARG, "NULL mesh handle");
+        NLFEM_CHECK(params[i].precision == NLFEM_PREC_FP32_BULK, NLFEM_ERR_UNSUPPORTED,
+                    "a batch plan holds FP32-bulk assemblies only");
+        for (int j = 0; j < i; ++j)
+            NLFEM_CHECK(meshes[j] != meshes[i], NLFEM_ERR_INVALID_ARG, "a mesh handle appears twice in one batch");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[12];
+    for (int i = 0; i < 12; ++i) NLFEM_CUDA_TRY(cudaEventCreate(&ev[i]));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 12; ++i) cudaEventDestroy(e[i]);
+        }
+    } guard{ev};
+    std::unique_ptr<nlfem_batch_s> b(new nlfem_batch_s());
+    b->sys.resize(n);
+    b->f.resize(n);
+    b->fptr.assign(n, nullptr);
+    std::vector<double> tp(n), tq(n);
+    std::vector<char> cached(n);
+    for (int i = 0; i < n; ++i) {
+        Mesh& m = meshes[i]->m;
+        const Params P = make_params(params[i], m.ndof);
+        bool c = false;
+        std::shared_ptr<PairCache> pc = ensure_cache(m, P, st, ev, tp[i], tq[i], c);
+        cached[i] = c;
+        const int64_t need = assembly_bytes(m, *pc, P) + m.device_bytes();
+        if (params[i].mem_budget_bytes > 0 && need > params[i].mem_budget_bytes)
+            throw Error{NLFEM_ERR_BUDGET, "batch item " + std::to_string(i) + " needs " + std::to_string(need) +
+                                              " device bytes, budget is " + std::to_string(params[i].mem_budget_bytes)};
+        b->sys[i].reset(new nlfem_system_s());
+        System& S = b->sys[i]->s;
+        S.mesh = &m;
+        S.pc = pc;
+        S.prm = P;
+        S.N = pc->N;
+        S.nnz = pc->nnz;
+        S.val.alloc(pc->nnz, st);
+        S.F.alloc(pc->N, st);
+        if (f_nodal && f_nodal[i]) {
+            upload(b->f[i], f_nodal[i], (size_t)(m.M * P.ndof), st);  // copied: the plan owns its load data
+            b->fptr[i] = b->f[i].p;
+        }
+        b->exec.items.push_back(BatchSys{&m, pc.get(), P, &S});
+    }
+    b->exec.prepare(st);
+    b->exec.record(st, nullptr, true, b->fptr);
+    batch_settle(*b, st, ev + 6);
+    // capture the value assembly once; runs replay it
+    NLFEM_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    NLFEM_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    try {
+        b->exec.record(b->cap, nullptr, true, b->fptr);
+    } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(b->cap, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    NLFEM_CUDA_TRY(cudaStreamEndCapture(b->cap, &b->graph));
+    NLFEM_CUDA_TRY(cudaGraphInstantiate(&b->exec_graph, b->graph, 0));
+    for (int i = 0; i < n; ++i) {
+        System& S = b->sys[i]->s;
+        fill_info(S, meshes[i]->m, *S.pc, tp[i], tq[i], cached[i] != 0);
+    }
+    *out = b.release();
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+int nlfem_batch_run(nlfem_batch_t b, void* stream, double* ms) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(b != nullptr, NLFEM_ERR_INVALID_ARG, "NULL batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[8];
+    for (int i = 0; i < 8; ++i) NLFEM_CUDA_TRY(cudaEventCreate(&ev[i]));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 8; ++i) cudaEventDestroy(e[i]);
+        }
+    } guard{ev};
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[6], st));
+    NLFEM_CUDA_TRY(cudaGraphLaunch(b->exec_graph, st));
+    NLFEM_CUDA_TRY(cudaEventRecord(ev[7], st));
+    batch_settle(*b, st, ev);
+    if (ms) *ms = elapsed_ms(ev[6], ev[7]);
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+int nlfem_batch_system(nlfem_batch_t b, int i, nlfem_system_t* out) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(b && out && i >= 0 && i < (int)b->sys.size(), NLFEM_ERR_INVALID_ARG, "bad batch or index");
+    *out = b->sys[i].get();
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+void nlfem_batch_destroy(nlfem_batch_t b) { delete b; }
 
 int nlfem_system_csr(nlfem_system_t sys, const int64_t** row_ptr, const int32_t** col, const double** val,
                      int64_t* nrows, int64_t* nnz) {

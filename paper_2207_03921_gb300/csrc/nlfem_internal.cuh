@@ -46,6 +46,21 @@ struct DBuf {
     DBuf() = default;
     DBuf(const DBuf&) = delete;
     DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) {
+        o.p = nullptr;
+        o.n = 0;
+    }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            n = o.n;
+            s = o.s;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
     ~DBuf() { release(); }
     void release() {
         if (p) cudaFreeAsync(p, s);
@@ -69,6 +84,11 @@ struct DBuf {
         if (n) NLFEM_CUDA_TRY(cudaMemsetAsync(p, 0, n * sizeof(T), st));
     }
     size_t bytes() const { return n * sizeof(T); }
+    // keep the buffer if it already has count elements (no stream operation then)
+    void ensure(size_t count, cudaStream_t st) {
+        if (p && n == count) return;
+        alloc(count, st);
+    }
     void swap_with(DBuf& o) {
         std::swap(p, o.p);
         std::swap(n, o.n);
@@ -246,13 +266,29 @@ struct BulkItem {
     Params prm;
     BulkAcc b;
 };
-void launch_trunc_fast_batch(const std::vector<BulkItem>& items, int list, int pilot, cudaStream_t st);
+// a fused launch over the items' pairs of one list (0 whole, 1 cut): the request table is
+// uploaded by make_fused, run_fused only launches (capturable into a CUDA graph)
+struct FusedLaunch;
+std::shared_ptr<FusedLaunch> make_fused(const std::vector<BulkItem>& items, int list, int pilot, cudaStream_t st);
+void run_fused(const FusedLaunch& f, cudaStream_t st);
+void set_fast_attributes();  // shared-memory limits of the cut-pair kernels (once per device)
 // FP32-bulk assembly of several systems with fused bulk launches (quad.cu)
 struct BatchSys {
     Mesh* m;
     PairCache* pc;
     Params prm;
     System* sys;
+};
+// The FP32-bulk value assembly of several systems: prepare() allocates the per-system
+// working buffers and uploads the fused launches' request tables; record() enqueues every
+// step (close lists, pilot, scale, fused bulk launches, element sums, check, and with finish
+// also the conversion to CSR and the load vector) with stream operations only, so that it can
+// be captured into a CUDA graph and replayed.
+struct BatchExec {
+    std::vector<BatchSys> items;
+    std::vector<std::shared_ptr<FusedLaunch>> pilot, whole, cut;
+    void prepare(cudaStream_t st);
+    void record(cudaStream_t st, cudaEvent_t* ev, bool finish, const std::vector<const double*>& f);
 };
 void run_bulk_batch(std::vector<BatchSys>& items, cudaStream_t st, cudaEvent_t* ev);
 void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st);

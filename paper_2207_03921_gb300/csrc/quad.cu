@@ -278,10 +278,17 @@ struct DuffyArgs {
     Params prm;
 };
 
+// c |z|^(-2-2s) from d2 = |z|^2: square roots for s in {1/4, 1/2, 3/4} (each correctly rounded),
+// exp2 / log2 otherwise (a relative error of a few 1e-15, far below the rule's)
 __device__ __forceinline__ double gamma_d(double d2, const Params& P) {
     if (P.kernel == NLFEM_KERNEL_CONSTANT) return P.c;
     if (P.s == 0.5) return P.c / (d2 * sqrt(d2));
-    return P.c * pow(d2, -1.0 - P.s);
+    if (P.s == 0.25) return P.c / (d2 * sqrt(sqrt(d2)));
+    if (P.s == 0.75) {
+        const double q = sqrt(d2);
+        return P.c / (d2 * q * sqrt(q));
+    }
+    return P.c * exp2((-1.0 - P.s) * log2(d2));
 }
 
 // add w * D D^T (scalar) into the packed upper union block
@@ -683,22 +690,56 @@ void bulk_redo(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStrea
 // FP32-bulk assembly of several systems: the same steps as run_bulk, with the whole- and
 // cut-pair kernels of all requests of one kernel class fused into one launch each (pilot and
 // main pass). Each system's scale is chosen from its own pilot values, so every system is
-// the same bits as when it is assembled alone. Events: [0, 1] close-list kernels, [2, 3]
-// fused whole-pair launches, [3, 4] fused cut-pair launches, [4, 5] element sums and
+// the same bits as when it is assembled alone. Events (optional): [0, 1] close-list kernels,
+// [2, 3] fused whole-pair launches, [3, 4] fused cut-pair launches, [4, 5] element sums and
 // close-list adds.
-void run_bulk_batch(std::vector<BatchSys>& items, cudaStream_t st, cudaEvent_t* ev) {
-    auto class_key = [](const Params& p) {
-        return ((int64_t)p.kernel * 64 + p.ro.n) * 64 * 8 + (int64_t)p.ri.n * 8 + (p.ball == NLFEM_BALL_APPROXCAPS);
-    };
-    NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+static int64_t class_key(const Params& p) {
+    return ((int64_t)p.kernel * 64 + p.ro.n) * 64 * 8 + (int64_t)p.ri.n * 8 + (p.ball == NLFEM_BALL_APPROXCAPS);
+}
+
+void BatchExec::prepare(cudaStream_t st) {
+    set_fast_attributes();
+    for (BatchSys& it : items) {
+        PairCache& pc = *it.pc;
+        System& sys = *it.sys;
+        const int NC = pc.ndof == 1 ? 1 : 3;
+        if (pc.nduffy > 0) sys.contrib32.ensure(pc.nduffy * contrib_entries(pc.ndof), st);
+        sys.fix.ensure(1, st);
+        sys.acc.ensure(std::max<int64_t>(pc.n_upper * NC, 1), st);
+        sys.kkll.ensure(pc.npairs * 12 * NC, st);
+    }
+    std::vector<int64_t> keys;  // kernel classes, in the order of first appearance
+    for (BatchSys& it : items) {
+        const int64_t k = class_key(it.prm);
+        if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
+    }
+    pilot.clear();
+    whole.clear();
+    cut.clear();
+    for (int64_t key : keys) {
+        std::vector<BulkItem> gp, gm;
+        for (BatchSys& it : items) {
+            if (class_key(it.prm) != key) continue;
+            FixState* f = it.sys->fix.p;
+            gp.push_back(BulkItem{it.m, it.pc, it.prm, BulkAcc{nullptr, nullptr, nullptr, &f->max_pilot, 61}});
+            gm.push_back(BulkItem{it.m, it.pc, it.prm, BulkAcc{it.sys->acc.p, it.sys->kkll.p, &f->scale,
+                                                               &f->max_exact, 1}});
+        }
+        pilot.push_back(make_fused(gp, 0, 61, st));
+        pilot.push_back(make_fused(gp, 1, 61, st));
+        whole.push_back(make_fused(gm, 0, 0, st));
+        cut.push_back(make_fused(gm, 1, 0, st));
+    }
+}
+
+void BatchExec::record(cudaStream_t st, cudaEvent_t* ev, bool finish, const std::vector<const double*>& f) {
+    if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
     for (BatchSys& it : items) {
         Mesh& m = *it.m;
         PairCache& pc = *it.pc;
         System& sys = *it.sys;
         const Params& prm = it.prm;
-        const int NC = pc.ndof == 1 ? 1 : 3;
         if (pc.nduffy > 0) {
-            sys.contrib32.alloc(pc.nduffy * contrib_entries(pc.ndof), st);
             if (prm.singular) {
                 DuffyArgs d{pc.duffy_ids.p, pc.nduffy, 1, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
                 k_duffy<<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, nullptr, sys.contrib32.p);
@@ -709,55 +750,42 @@ void run_bulk_batch(std::vector<BatchSys>& items, cudaStream_t st, cudaEvent_t* 
                 launch_trunc<float>(c, sys.contrib32.p, st);
             }
         }
-        sys.fix.alloc(1, st);
         sys.fix.zero(st);
-        sys.acc.alloc(std::max<int64_t>(pc.n_upper * NC, 1), st);
-        sys.kkll.alloc(pc.npairs * 12 * NC, st);
     }
-    NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
-    // kernel classes, in the order of first appearance
-    std::vector<int64_t> keys;
-    for (BatchSys& it : items) {
-        const int64_t k = class_key(it.prm);
-        if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
-    }
-    auto group = [&](int64_t key, bool pilot) {
-        std::vector<BulkItem> g;
-        for (BatchSys& it : items) {
-            if (class_key(it.prm) != key) continue;
-            FixState* f = it.sys->fix.p;
-            BulkAcc b = pilot ? BulkAcc{nullptr, nullptr, nullptr, &f->max_pilot, 61}
-                              : BulkAcc{it.sys->acc.p, it.sys->kkll.p, &f->scale, &f->max_exact, 1};
-            g.push_back(BulkItem{it.m, it.pc, it.prm, b});
-        }
-        return g;
-    };
-    // pilot
-    for (int64_t key : keys) {
-        const std::vector<BulkItem> g = group(key, true);
-        launch_trunc_fast_batch(g, 0, 61, st);
-        launch_trunc_fast_batch(g, 1, 61, st);
-    }
+    if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+    for (const auto& fl : pilot) run_fused(*fl, st);
     for (BatchSys& it : items) {
         close_acc(*it.m, *it.pc, *it.sys, nullptr, nullptr, &it.sys->fix.p->max_pilot, st);
         k_fix_pick<<<1, 1, 0, st>>>(it.sys->fix.p, it.pc->acc_terms);
         NLFEM_LAUNCH_CHECK();
         it.sys->acc.zero(st);
     }
-    // main pass
-    NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
-    for (int64_t key : keys) launch_trunc_fast_batch(group(key, false), 0, 0, st);
-    NLFEM_CUDA_TRY(cudaEventRecord(ev[3], st));
-    for (int64_t key : keys) launch_trunc_fast_batch(group(key, false), 1, 0, st);
-    NLFEM_CUDA_TRY(cudaEventRecord(ev[4], st));
+    if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
+    for (const auto& fl : whole) run_fused(*fl, st);
+    if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[3], st));
+    for (const auto& fl : cut) run_fused(*fl, st);
+    if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[4], st));
     for (BatchSys& it : items) {
-        FixState* f = it.sys->fix.p;
-        elem_sums(*it.m, *it.pc, it.prm, *it.sys, &f->scale, st);
-        close_acc(*it.m, *it.pc, *it.sys, it.sys->acc.p, &f->scale, &f->max_exact, st);
-        k_fix_check<<<1, 1, 0, st>>>(f, it.pc->acc_terms);
+        FixState* fx = it.sys->fix.p;
+        elem_sums(*it.m, *it.pc, it.prm, *it.sys, &fx->scale, st);
+        close_acc(*it.m, *it.pc, *it.sys, it.sys->acc.p, &fx->scale, &fx->max_exact, st);
+        k_fix_check<<<1, 1, 0, st>>>(fx, it.pc->acc_terms);
         NLFEM_LAUNCH_CHECK();
     }
-    NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
+    if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
+    if (!finish) return;
+    for (size_t i = 0; i < items.size(); ++i) {
+        BatchSys& it = items[i];
+        run_reduction(*it.m, *it.pc, it.prm, *it.sys, st);
+        run_load(*it.m, it.prm, f.empty() ? nullptr : f[i], *it.sys, st);
+    }
+}
+
+void run_bulk_batch(std::vector<BatchSys>& items, cudaStream_t st, cudaEvent_t* ev) {
+    BatchExec e;
+    e.items = items;
+    e.prepare(st);
+    e.record(st, ev, false, {});
 }
 
 void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {

@@ -19,6 +19,7 @@
 // code.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "nlfem_internal.cuh"
@@ -678,9 +679,40 @@ template <int KER, int NQI, bool CAPS, bool BATCH>
 static void launch_cut(const FastRule& r, const FastLaunch& L, unsigned grid, cudaStream_t st) {
     constexpr int MAXP = CAPS ? 9 : 6;
     const size_t smem = sizeof(float2) * CHUNK * MAXP * FAST_THREADS;
+    k_trunc_cut<KER, NQI, CAPS, BATCH><<<grid, FAST_THREADS, smem, st>>>(r, L);
+}
+
+template <int KER, int NQI, bool CAPS, bool BATCH>
+static void cut_attr() {
+    constexpr int MAXP = CAPS ? 9 : 6;
+    const size_t smem = sizeof(float2) * CHUNK * MAXP * FAST_THREADS;
     NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_cut<KER, NQI, CAPS, BATCH>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_trunc_cut<KER, NQI, CAPS, BATCH><<<grid, FAST_THREADS, smem, st>>>(r, L);
+}
+
+template <int KER, int NQI>
+static void cut_attrs() {
+    cut_attr<KER, NQI, false, false>();
+    cut_attr<KER, NQI, true, false>();
+    cut_attr<KER, NQI, false, true>();
+    cut_attr<KER, NQI, true, true>();
+}
+
+// cudaFuncSetAttribute is not a stream operation: done once per device, outside any capture
+void set_fast_attributes() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    NLFEM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+    cut_attrs<NLFEM_KERNEL_CONSTANT, 7>();
+    cut_attrs<NLFEM_KERNEL_CONSTANT, 16>();
+    cut_attrs<NLFEM_KERNEL_FRACTIONAL, 7>();
+    cut_attrs<NLFEM_KERNEL_FRACTIONAL, 16>();
+    cut_attrs<NLFEM_KERNEL_PERIDYNAMIC, 7>();
+    cut_attrs<NLFEM_KERNEL_PERIDYNAMIC, 16>();
+    done.push_back(dev);
 }
 
 template <int KER, int NQI, bool BATCH>
@@ -711,6 +743,7 @@ static void launch_kernel(const Params& prm, int list, const FastRule& r, const 
 // one launch of the whole-pair (list 0) or cut-pair (list 1) kernel over the tiles of L:
 // a request table (L.reqs, L.tile_off) or the single request L.one
 void launch_fast_list(const Params& prm, int list, const FastLaunch& L, cudaStream_t st) {
+    set_fast_attributes();
     const unsigned grid = (unsigned)std::min<int64_t>((L.ntiles + FAST_WARPS - 1) / FAST_WARPS, 152 * 64);
     if (!grid) return;
     const FastRule r = make_rule(prm);
@@ -719,50 +752,50 @@ void launch_fast_list(const Params& prm, int list, const FastLaunch& L, cudaStre
 }
 
 // One launch of list `list` (0 whole, 1 cut) over the pairs of several requests of one kernel
-// class (the rules and kernel type of prm; per-request delta, constants and buffers in reqs).
-void launch_fast_batch(const Params& prm, int list, const std::vector<FastReq>& reqs, int pilot, cudaStream_t st) {
-    const int n = (int)reqs.size();
-    if (n == 0) return;
+// class (the rules and kernel type of prm; per-request delta, constants and buffers in the
+// table).
+struct FusedLaunch {
+    Params prm;
+    int list = 0;
+    FastLaunch L;
+    DBuf<FastReq> reqs;
+    DBuf<int64_t> off;
+};
+
+std::shared_ptr<FusedLaunch> make_fused(const std::vector<BulkItem>& items, int list, int pilot, cudaStream_t st) {
+    auto f = std::make_shared<FusedLaunch>();
+    const int n = (int)items.size();
+    f->prm = items[0].prm;
+    f->list = list;
+    std::memset(&f->L, 0, sizeof f->L);
+    std::vector<FastReq> reqs;
     std::vector<int64_t> off(n + 1, 0);
     for (int i = 0; i < n; ++i) {
-        const int64_t np = pilot ? (reqs[i].npairs + pilot - 1) / pilot : reqs[i].npairs;
+        const BulkItem& it = items[i];
+        FastReq q = make_req(*it.m, *it.pc, it.prm, list);
+        q.acc = it.b.acc;
+        q.kkll = it.b.kkll;
+        q.scale_p = it.b.scale_p;
+        q.maxabs = it.b.maxabs;
+        reqs.push_back(q);
+        const int64_t np = pilot ? (q.npairs + pilot - 1) / pilot : q.npairs;
         off[i + 1] = off[i] + (np + 31) / 32;
     }
-    if (off[n] == 0) return;
-    DBuf<FastReq> dq;
-    DBuf<int64_t> doff;
-    dq.alloc(n, st);
-    doff.alloc(n + 1, st);
-    NLFEM_CUDA_TRY(cudaMemcpyAsync(dq.p, reqs.data(), sizeof(FastReq) * n, cudaMemcpyHostToDevice, st));
-    NLFEM_CUDA_TRY(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
-    FastLaunch L;
-    std::memset(&L, 0, sizeof L);
-    L.reqs = dq.p;
-    L.tile_off = doff.p;
-    L.nreq = n;
-    L.ntiles = off[n];
-    L.pilot = pilot;
-    launch_fast_list(prm, list, L, st);
-    // copies from pageable host memory are staged before cudaMemcpyAsync returns, and the
-    // device tables are freed in stream order after the launch
+    f->reqs.alloc(n, st);
+    f->off.alloc(n + 1, st);
+    // copies from pageable host memory are staged before cudaMemcpyAsync returns
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(f->reqs.p, reqs.data(), sizeof(FastReq) * n, cudaMemcpyHostToDevice, st));
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(f->off.p, off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+    f->L.reqs = f->reqs.p;
+    f->L.tile_off = f->off.p;
+    f->L.nreq = n;
+    f->L.ntiles = off[n];
+    f->L.pilot = pilot;
+    return f;
 }
 
-// the whole-pair (list 0) or cut-pair (list 1) launch of a batch of one kernel class
-// (items[0]'s rules)
-void launch_trunc_fast_batch(const std::vector<BulkItem>& items, int list, int pilot, cudaStream_t st) {
-    {
-        std::vector<FastReq> reqs;
-        reqs.reserve(items.size());
-        for (const BulkItem& it : items) {
-            FastReq q = make_req(*it.m, *it.pc, it.prm, list);
-            q.acc = it.b.acc;
-            q.kkll = it.b.kkll;
-            q.scale_p = it.b.scale_p;
-            q.maxabs = it.b.maxabs;
-            reqs.push_back(q);
-        }
-        launch_fast_batch(items[0].prm, list, reqs, pilot, st);
-    }
+void run_fused(const FusedLaunch& f, cudaStream_t st) {
+    if (f.L.ntiles > 0) launch_fast_list(f.prm, f.list, f.L, st);
 }
 
 void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, const BulkAcc& b, cudaStream_t st,

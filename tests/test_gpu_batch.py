@@ -60,3 +60,20 @@ def test_batch_cached_second_call_and_errors():
     with pytest.raises(NlfemError):
         assemble_batch([a, a], [kw, kw])
     assert assemble_batch([], []) == []
+
+
+def test_batch_plan_graph_replay_equals_single():
+    items = [it for it in _items() if it[2]["precision"] == "fp32_bulk"]
+    ms = [Mesh.from_synth(m, nd) for m, nd, _ in items]
+    fs = [np.linspace(-1.0, 1.0, m.M * nd) for m, nd, _ in items]
+    single = [_host(assemble(Mesh.from_synth(m, nd), f_nodal=f, **kw)) for (m, nd, kw), f in zip(items, fs)]
+    from paper_2207_03921_gb300 import BatchPlan
+    plan = BatchPlan(ms, [kw for _, _, kw in items], fs)
+    for rep in range(2):
+        t = plan.run()
+        assert t > 0
+        for (rp0, col0, val0, F0), S in zip(single, plan.systems):
+            rp, col, val, F = _host(S)
+            assert np.array_equal(val, val0) and np.array_equal(F, F0)
+    with pytest.raises(NlfemError):
+        BatchPlan(ms[:1], [dict(items[0][2], precision="fp64")])
