@@ -159,6 +159,16 @@ int nlfem_batch_system(nlfem_batch_t batch, int i, nlfem_system_t* out);
 void nlfem_batch_destroy(nlfem_batch_t batch);
 
 /*
+ * Autotuner of the FP32-bulk launch shape: for the kernel class of params (kernel type,
+ * rules, ball) it times the whole-pair and the cut-pair kernels on mesh with every candidate
+ * grid size (2 ... 64 resident blocks of 4 warps per SM; each warp takes 32-pair tiles) and
+ * keeps the fastest for the rest of the process; best receives the chosen blocks per SM for
+ * the whole and the cut list. The results of every assembly are the same bits whatever the
+ * grid. The paper has no counterpart. Errors: INVALID_ARG, UNSUPPORTED (FP64), OOM, CUDA.
+ */
+int nlfem_autotune(nlfem_mesh_t mesh, const nlfem_params* params, void* stream, int32_t best[2]);
+
+/*
  * Batched assembly: the same result as n calls of nlfem_assemble (every system is the same
  * bits), with the whole-pair and cut-pair kernels of all FP32-bulk items of one kernel class
  * (kernel type, outer and inner rule, ball) fused into one persistent launch each, so many

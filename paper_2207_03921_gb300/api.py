@@ -191,3 +191,11 @@ class BatchPlan:
             B.nlfem_batch_destroy(h)
             self.handle = None
 
+
+def autotune(mesh: Mesh, stream=None, **params) -> tuple:
+    """Pick the FP32-bulk grid size for this kernel class on mesh (nlfem_autotune); returns
+    the blocks per SM chosen for the whole-pair and the cut-pair kernel."""
+    q = dict(precision="fp32_bulk")
+    q.update(params)
+    return B.nlfem_autotune(mesh.handle, _params_list([q])[0], stream)
+

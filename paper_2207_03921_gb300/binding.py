@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         lib.nlfem_batch_system.argtypes = [vp, ip, C.POINTER(vp)]
         lib.nlfem_batch_destroy.argtypes = [vp]
         lib.nlfem_batch_destroy.restype = None
+        lib.nlfem_autotune.argtypes = [vp, C.POINTER(nlfem_params), vp, C.POINTER(C.c_int32)]
         lib.nlfem_pairs_noalloc.argtypes = [vp, i64, vp, i64, dp, ip, ip, vp, vp, i64, C.POINTER(i64), vp]
         _lib = lib
     return _lib
@@ -186,6 +187,12 @@ def nlfem_batch_create(meshes, params, f_nodal=None, stream=None):
     h = C.c_void_p()
     _check(load().nlfem_batch_create(mh, pa, fp, n, _stream(stream), C.byref(h)))
     return h
+
+
+def nlfem_autotune(mesh, params: nlfem_params, stream=None) -> tuple:
+    best = (C.c_int32 * 2)()
+    _check(load().nlfem_autotune(mesh, C.byref(params), _stream(stream), best))
+    return int(best[0]), int(best[1])
 
 
 def nlfem_batch_run(batch, stream=None) -> float:

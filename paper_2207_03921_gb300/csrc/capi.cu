@@ -683,6 +683,64 @@ int nlfem_batch_system(nlfem_batch_t b, int i, nlfem_system_t* out) {
 
 void nlfem_batch_destroy(nlfem_batch_t b) { delete b; }
 
+int nlfem_autotune(nlfem_mesh_t mesh, const nlfem_params* params, void* stream, int32_t best[2]) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(mesh && params && best, NLFEM_ERR_INVALID_ARG, "NULL argument");
+    NLFEM_CHECK(params->precision == NLFEM_PREC_FP32_BULK, NLFEM_ERR_UNSUPPORTED,
+                "the autotuner sets the FP32-bulk launch shapes");
+    Mesh& m = mesh->m;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Params P = make_params(*params, m.ndof);
+    cudaEvent_t ev[12];
+    for (int i = 0; i < 12; ++i) NLFEM_CUDA_TRY(cudaEventCreate(&ev[i]));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 12; ++i) cudaEventDestroy(e[i]);
+        }
+    } guard{ev};
+    double tp = 0, tq = 0;
+    bool cached = false;
+    std::shared_ptr<PairCache> pc = ensure_cache(m, P, st, ev, tp, tq, cached);
+    // scratch accumulators: the values are discarded, the launches are the real ones
+    const int NC = pc->ndof == 1 ? 1 : 3;
+    DBuf<unsigned long long> acc;
+    DBuf<float> kkll;
+    DBuf<FixState> fix;
+    acc.alloc(std::max<int64_t>(pc->n_upper * NC, 1), st);
+    kkll.alloc(pc->npairs * 12 * NC, st);
+    fix.alloc(1, st);
+    fix.zero(st);
+    pick_scale(m, *pc, P, fix.p, st);  // the real scale, so that the atomics are the real ones too
+    const int cand[] = {2, 4, 8, 16, 32, 64};
+    for (int list = 0; list < 2; ++list) {
+        const int64_t key = fast_tune_key(P, list);
+        double best_ms = 1e300;
+        int best_c = fast_blocks_per_sm(key);
+        for (int c : cand) {
+            set_fast_blocks_per_sm(key, c);
+            double t = 1e300;
+            for (int rep = 0; rep < 2; ++rep) {
+                NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+                launch_trunc_fast(m, *pc, P, BulkAcc{acc.p, kkll.p, &fix.p->scale, &fix.p->max_exact, 1}, st,
+                                  ev + 2);
+                NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+                NLFEM_CUDA_TRY(cudaEventSynchronize(ev[1]));
+                t = std::min(t, elapsed_ms(ev[2 + list], ev[3 + list]));
+            }
+            if (t < best_ms) {
+                best_ms = t;
+                best_c = c;
+            }
+        }
+        set_fast_blocks_per_sm(key, best_c);
+        best[list] = best_c;
+    }
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
 int nlfem_system_csr(nlfem_system_t sys, const int64_t** row_ptr, const int32_t** col, const double** val,
                      int64_t* nrows, int64_t* nnz) {
     NLFEM_API_BEGIN

@@ -256,6 +256,8 @@ struct BulkAcc {
 // FP32 bulk: after the quadrature, read FixState.redo (with the final synchronisation) and
 // call bulk_redo if it is set
 void bulk_redo(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev);
+// pilot pass and scale choice into f (f zeroed by the caller)
+void pick_scale(Mesh& m, PairCache& pc, const Params& prm, FixState* f, cudaStream_t st);
 void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, const BulkAcc& b, cudaStream_t st,
                        cudaEvent_t* ev);
 // one request of a batched launch (all items of one call share the kernel class: kernel
@@ -272,6 +274,10 @@ struct FusedLaunch;
 std::shared_ptr<FusedLaunch> make_fused(const std::vector<BulkItem>& items, int list, int pilot, cudaStream_t st);
 void run_fused(const FusedLaunch& f, cudaStream_t st);
 void set_fast_attributes();  // shared-memory limits of the cut-pair kernels (once per device)
+// grid size of the bulk launches: blocks per SM for (kernel class, list); set by the autotuner
+int64_t fast_tune_key(const Params& prm, int list);
+int fast_blocks_per_sm(int64_t key);
+void set_fast_blocks_per_sm(int64_t key, int bps);
 // FP32-bulk assembly of several systems with fused bulk launches (quad.cu)
 struct BatchSys {
     Mesh* m;

@@ -620,6 +620,12 @@ __global__ void k_fix_pick(FixState* f, int64_t terms) {
     f->redo = 0;
 }
 
+void pick_scale(Mesh& m, PairCache& pc, const Params& prm, FixState* f, cudaStream_t st) {
+    launch_trunc_fast(m, pc, prm, BulkAcc{nullptr, nullptr, nullptr, &f->max_pilot, 61}, st, nullptr);
+    k_fix_pick<<<1, 1, 0, st>>>(f, pc.acc_terms);
+    NLFEM_LAUNCH_CHECK();
+}
+
 // the main pass may keep its scale if no sum could overflow and at most 2^16 of range is unused
 __global__ void k_fix_check(FixState* f, int64_t terms) {
     const int Se = fix_shift(__uint_as_float(f->max_exact), terms, 0);

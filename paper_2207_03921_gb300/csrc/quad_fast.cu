@@ -742,9 +742,46 @@ static void launch_kernel(const Params& prm, int list, const FastRule& r, const 
 
 // one launch of the whole-pair (list 0) or cut-pair (list 1) kernel over the tiles of L:
 // a request table (L.reqs, L.tile_off) or the single request L.one
+// ---- grid size of the bulk launches (the tile shape the autotuner picks) -------------------
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        NLFEM_CUDA_TRY(cudaGetDevice(&dev));
+        NLFEM_CUDA_TRY(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return n;
+}
+
+static std::mutex g_tune_mu;
+static std::vector<std::pair<int64_t, int>> g_tune;  // (kernel class and list, blocks per SM)
+
+int64_t fast_tune_key(const Params& prm, int list) {
+    return ((((int64_t)prm.kernel * 64 + prm.ro.n) * 64 + prm.ri.n) * 2 + (prm.ball == NLFEM_BALL_APPROXCAPS)) * 2 +
+           list;
+}
+
+int fast_blocks_per_sm(int64_t key) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    for (auto& e : g_tune)
+        if (e.first == key) return e.second;
+    return 64;  // untuned: oversubscribe; warps take 32-pair tiles in a grid-stride loop
+}
+
+void set_fast_blocks_per_sm(int64_t key, int bps) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    for (auto& e : g_tune)
+        if (e.first == key) {
+            e.second = bps;
+            return;
+        }
+    g_tune.emplace_back(key, bps);
+}
+
 void launch_fast_list(const Params& prm, int list, const FastLaunch& L, cudaStream_t st) {
     set_fast_attributes();
-    const unsigned grid = (unsigned)std::min<int64_t>((L.ntiles + FAST_WARPS - 1) / FAST_WARPS, 152 * 64);
+    const int64_t cap = (int64_t)sm_count() * fast_blocks_per_sm(fast_tune_key(prm, list));
+    const unsigned grid = (unsigned)std::min<int64_t>((L.ntiles + FAST_WARPS - 1) / FAST_WARPS, cap);
     if (!grid) return;
     const FastRule r = make_rule(prm);
     if (L.reqs) launch_kernel<true>(prm, list, r, L, grid, st);

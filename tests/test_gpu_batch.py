@@ -77,3 +77,15 @@ def test_batch_plan_graph_replay_equals_single():
             assert np.array_equal(val, val0) and np.array_equal(F, F0)
     with pytest.raises(NlfemError):
         BatchPlan(ms[:1], [dict(items[0][2], precision="fp64")])
+
+
+def test_autotune_keeps_results():
+    from paper_2207_03921_gb300 import autotune
+    m = meshes.structured(-0.1, 1.1, 40, name="s40")
+    mesh = Mesh.from_synth(m)
+    kw = dict(kernel="constant", delta=0.1, precision="fp32_bulk")
+    before = assemble(mesh, **kw).csr()[2].cpu().numpy()
+    best = autotune(mesh, **kw)
+    assert all(b in (2, 4, 8, 16, 32, 64) for b in best)
+    after = assemble(mesh, **kw).csr()[2].cpu().numpy()
+    assert np.array_equal(before, after)
