@@ -69,12 +69,23 @@ struct SearchArgs {
 __device__ bool interacts(const SearchArgs& a, int k, int l, int4 tk, const double2 Vk[3], double2 ck, double rk) {
     int4 tl = a.T[l];
     if (shared_count(tk, tl) > 0) return true;
-    double2 cl = a.cen[l];
-    double rl = a.rad[l];
-    double cdx = cl.x - ck.x, cdy = cl.y - ck.y;
-    double dist = sqrt(cdx * cdx + cdy * cdy);
-    if (dist - rk - rl > a.delta * (1.0 + 1e-9)) return false;
-    if (dist + rk + rl <= a.delta * (1.0 - 1e-9)) return true;  // E_l inside the ball of every x in E_k
+    const double2 cl = a.cen[l];
+    const double rl = a.rad[l];
+    const double cdx = cl.x - ck.x, cdy = cl.y - ck.y;
+    // centroid tests: decided in FP32 on squared distances when the margin (1e-5 relative,
+    // far above the FP32 error of about 3e-7) allows, else by the FP64 expressions below
+    const float d2f = (float)cdx * (float)cdx + (float)cdy * (float)cdy;
+    const float far = (float)(rk + rl + a.delta * (1.0 + 1e-9));
+    const double inner = a.delta * (1.0 - 1e-9) - rk - rl;
+    const float nearf = inner > 0 ? (float)inner : -1.f;
+    if (d2f > far * far * (1.f + 1e-5f)) return false;
+    if (nearf > 0.f && d2f < nearf * nearf * (1.f - 1e-5f)) return true;  // E_l inside the ball of every x in E_k
+    // within the margin of either threshold: the FP64 tests decide
+    if (d2f >= far * far * (1.f - 1e-5f) || (nearf > 0.f && d2f <= nearf * nearf * (1.f + 1e-5f))) {
+        const double dist = sqrt(cdx * cdx + cdy * cdy);
+        if (dist - rk - rl > a.delta * (1.0 + 1e-9)) return false;
+        if (dist + rk + rl <= a.delta * (1.0 - 1e-9)) return true;
+    }
     // FP32 geometry with exact decisions; the canonical FP64 clip only for near ties
     const double2 v0l = a.X[tl.x];
     const float dx = (float)(v0l.x - Vk[0].x), dy = (float)(v0l.y - Vk[0].y);
@@ -105,9 +116,11 @@ __device__ bool interacts(const SearchArgs& a, int k, int l, int4 tk, const doub
     return false;
 }
 
-// One warp per outer element k. FILL = false: count partners; true: write them.
-template <bool FILL>
-__global__ void k_search(SearchArgs a, int64_t* count, const int64_t* ptr, int* out_l) {
+// One warp per outer element k. FILL = false: count partners; true: write them at ptr[k].
+// SLOTS: write them at k * cap (cap = the largest candidate count) and count them, in one
+// pass; k_compact_slots then packs the slots.
+template <bool FILL, bool SLOTS = false>
+__global__ void k_search(SearchArgs a, int64_t* count, const int64_t* ptr, int* out_l, int64_t cap = 0) {
     int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (k >= a.K) return;
@@ -118,7 +131,7 @@ __global__ void k_search(SearchArgs a, int64_t* count, const int64_t* ptr, int* 
     int cell = a.cell_of[k];
     int cx = cell % a.g.nx, cy = cell / a.g.nx;
     int64_t n = 0;
-    int64_t base = FILL ? ptr[k] : 0;
+    int64_t base = SLOTS ? k * cap : (FILL ? ptr[k] : 0);
     for (int dyc = -1; dyc <= 1; ++dyc) {
         int yy = cy + dyc;
         if (yy < 0 || yy >= a.g.ny) continue;
@@ -136,12 +149,37 @@ __global__ void k_search(SearchArgs a, int64_t* count, const int64_t* ptr, int* 
                     ok = interacts(a, (int)k, l, tk, Vk, ck, rk);
                 }
                 unsigned m = __ballot_sync(0xffffffffu, ok);
-                if (FILL && ok) out_l[base + n + __popc(m & ((1u << lane) - 1u))] = l;
+                if ((FILL || SLOTS) && ok) out_l[base + n + __popc(m & ((1u << lane) - 1u))] = l;
                 n += __popc(m);
             }
         }
     }
-    if (!FILL && lane == 0) count[k] = n;
+    if ((!FILL || SLOTS) && lane == 0) count[k] = n;
+}
+
+// the largest number of candidates of an element (its 3 x 3 cell block)
+__global__ void k_max_cand(const int* cell_of, int64_t K, Grid g, const int64_t* cell_start,
+                           unsigned long long* out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int cell = cell_of[k];
+    const int cx = cell % g.nx, cy = cell / g.nx;
+    int64_t n = 0;
+    for (int yy = max(cy - 1, 0); yy <= min(cy + 1, g.ny - 1); ++yy)
+        for (int xx = max(cx - 1, 0); xx <= min(cx + 1, g.nx - 1); ++xx) {
+            const int c = yy * g.nx + xx;
+            n += cell_start[c + 1] - cell_start[c];
+        }
+    atomicMax(out, (unsigned long long)n);
+}
+
+// pack the per-element slots into the pair list (warp per element, order kept)
+__global__ void k_compact_slots(const int* slots, int64_t K, int64_t cap, const int64_t* ptr, int* out) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= K) return;
+    const int64_t b = ptr[k], n = ptr[k + 1] - b;
+    for (int64_t j = lane; j < n; j += 32) out[b + j] = slots[k * cap + j];
 }
 
 __global__ void k_fill_k(const int64_t* ptr, int64_t K, int* pk) {
@@ -194,13 +232,28 @@ __global__ void k_flag_whole(const int* pk, const int* pl, const int8_t* cls, in
     if (cls[p] == 0 || std_close) {
         const int4 a = T[pk[p]], b = T[pl[p]];
         const double2 va[3] = {X[a.x], X[a.y], X[a.z]}, vb[3] = {X[b.x], X[b.y], X[b.z]};
-        double mx = 0.0;
+        // the nine vertex distances in FP32 (differences rounded once from FP64); decided
+        // there unless within 1e-5 of the threshold, then in FP64
+        float mxf = 0.f;
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) {
-                const double dx = vb[j].x - va[i].x, dy = vb[j].y - va[i].y;
-                mx = fmax(mx, dx * dx + dy * dy);
+                const float dx = (float)(vb[j].x - va[i].x), dy = (float)(vb[j].y - va[i].y);
+                mxf = fmaxf(mxf, dx * dx + dy * dy);
             }
-        if (mx <= delta2 * (1.0 - 1e-6)) w = 1;
+        const float thr = (float)(delta2 * (1.0 - 1e-6));
+        bool whole;
+        if (mxf < thr * (1.f - 1e-5f)) whole = true;
+        else if (mxf > thr * (1.f + 1e-5f)) whole = false;
+        else {
+            double mx = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    const double dx = vb[j].x - va[i].x, dy = vb[j].y - va[i].y;
+                    mx = fmax(mx, dx * dx + dy * dy);
+                }
+            whole = mx <= delta2 * (1.0 - 1e-6);
+        }
+        if (whole) w = 1;
         else c = 1;
     }
     flag_whole[p] = w;
@@ -277,7 +330,27 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     DBuf<int64_t> cnt;
     cnt.alloc(K, st);
     pc.pair_ptr.alloc(K + 1, st);
-    k_search<false><<<nblk(K * 32, 128), 128, 0, st>>>(a, cnt.p, nullptr, nullptr);
+    // one pass into per-element slots when they fit (8 GB), else a count pass and a fill pass
+    int64_t cap = 0;
+    {
+        DBuf<unsigned long long> mc;
+        mc.alloc(1, st);
+        mc.zero(st);
+        k_max_cand<<<nblk(K, 256), 256, 0, st>>>(cell_of.p, K, g, cstart.p, mc.p);
+        NLFEM_LAUNCH_CHECK();
+        unsigned long long h = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, mc.p, sizeof h, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        cap = (int64_t)h;
+    }
+    const bool slots = K * cap * (int64_t)sizeof(int) <= ((int64_t)8 << 30);
+    DBuf<int> slot_buf;
+    if (slots) {
+        slot_buf.alloc(std::max<int64_t>(K * cap, 1), st);
+        k_search<false, true><<<nblk(K * 32, 128), 128, 0, st>>>(a, cnt.p, nullptr, slot_buf.p, cap);
+    } else {
+        k_search<false><<<nblk(K * 32, 128), 128, 0, st>>>(a, cnt.p, nullptr, nullptr);
+    }
     NLFEM_LAUNCH_CHECK();
     exclusive_scan_i64(cnt.p, pc.pair_ptr.p, K, st);
     int64_t P = 0;
@@ -287,7 +360,12 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     pc.npairs = P;
     pc.pl.alloc(P, st);
     pc.pk.alloc(P, st);
-    k_search<true><<<nblk(K * 32, 128), 128, 0, st>>>(a, nullptr, pc.pair_ptr.p, pc.pl.p);
+    if (slots) {
+        k_compact_slots<<<nblk(K * 32, 128), 128, 0, st>>>(slot_buf.p, K, cap, pc.pair_ptr.p, pc.pl.p);
+        slot_buf.release();
+    } else {
+        k_search<true><<<nblk(K * 32, 128), 128, 0, st>>>(a, nullptr, pc.pair_ptr.p, pc.pl.p);
+    }
     NLFEM_LAUNCH_CHECK();
     int64_t mx = max_segment_i64(pc.pair_ptr.p, K, st);
     segmented_sort_i32(pc.pl.p, nullptr, pc.pair_ptr.p, K, (int)std::min<int64_t>(mx, 1 << 30), st);
