@@ -159,7 +159,7 @@ __device__ __forceinline__ void atomic_min_d(double* a, double v) {
 // Orient counter-clockwise exactly as the FP64 determinant's sign says; store |det J|.
 __global__ void k_prepare_elems(const int* T3, int64_t K, int64_t M, const double2* X, int4* T,
                                 double* det, double2* cen, double* rad, int* err, double* stats,
-                                float4* E32, float* det32) {
+                                float4* E32, float* det32, ElemRec* rec) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     int t0 = T3[3 * k], t1 = T3[3 * k + 1], t2 = T3[3 * k + 2];
@@ -169,6 +169,7 @@ __global__ void k_prepare_elems(const int* T3, int64_t K, int64_t M, const doubl
         det[k] = 0.0;
         E32[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         det32[k] = 0.f;
+        rec[k] = ElemRec{make_double2(0, 0), make_float4(0.f, 0.f, 0.f, 0.f), 0, 0, 0, 0.f};
         return;
     }
     double2 a = X[t0], b = X[t1], c = X[t2];
@@ -184,6 +185,7 @@ __global__ void k_prepare_elems(const int* T3, int64_t K, int64_t M, const doubl
     det[k] = d;
     E32[k] = make_float4((float)(b.x - a.x), (float)(b.y - a.y), (float)(c.x - a.x), (float)(c.y - a.y));
     det32[k] = (float)d;
+    rec[k] = ElemRec{a, E32[k], t0, t1, t2, (float)d};
     double2 ce = make_double2((a.x + b.x + c.x) / 3.0, (a.y + b.y + c.y) / 3.0);
     cen[k] = ce;
     double r = sqrt(fmax(fmax((a.x - ce.x) * (a.x - ce.x) + (a.y - ce.y) * (a.y - ce.y),
@@ -248,7 +250,7 @@ __global__ void k_max_seg(const int64_t* ptr, int64_t n, int* out) {
 
 int64_t Mesh::device_bytes() const {
     int64_t b = X.bytes() + T.bytes() + det.bytes() + lab.bytes() + dir.bytes() + ne_ptr.bytes() +
-                ne_idx.bytes() + cen.bytes() + rad.bytes() + E32.bytes() + det32.bytes();
+                ne_idx.bytes() + cen.bytes() + rad.bytes() + E32.bytes() + det32.bytes() + rec.bytes();
     if (cache) {
         const PairCache& c = *cache;
         b += c.pair_ptr.bytes() + c.pk.bytes() + c.pl.bytes() + c.pcls.bytes() + c.pT_ptr.bytes() +
@@ -276,6 +278,7 @@ void mesh_prepare(Mesh& m, const int* T3_dev, const int8_t* lab_dev, cudaStream_
     m.rad.alloc(K, st);
     m.E32.alloc(K, st);
     m.det32.alloc(K, st);
+    m.rec.alloc(K, st);
     m.lab.alloc(K, st);
     m.dir.alloc(M, st);
     m.dir.zero(st);
@@ -287,7 +290,7 @@ void mesh_prepare(Mesh& m, const int* T3_dev, const int8_t* lab_dev, cudaStream_
     double init[5] = {0.0, 1e300, 1e300, -1e300, -1e300};
     NLFEM_CUDA_TRY(cudaMemcpyAsync(stats.p, init, sizeof init, cudaMemcpyHostToDevice, st));
     k_prepare_elems<<<nblk(K, 256), 256, 0, st>>>(T3_dev, K, M, m.X.p, m.T.p, m.det.p, m.cen.p, m.rad.p,
-                                                  err.p, stats.p, m.E32.p, m.det32.p);
+                                                  err.p, stats.p, m.E32.p, m.det32.p, m.rec.p);
     NLFEM_LAUNCH_CHECK();
     k_bbox<<<nblk(M, 256), 256, 0, st>>>(m.X.p, M, stats.p);
     NLFEM_LAUNCH_CHECK();

@@ -101,6 +101,16 @@ struct DBuf {
 // ------------------------------------------------------------------------------------------
 struct PairCache;
 
+// Everything the bulk quadrature reads of an element, in one 48-byte record (three 16-byte
+// loads): vertex 0 in FP64, the FP32 edge vectors, the nodes and |det J| in FP32.
+struct __align__(16) ElemRec {
+    double2 v0;
+    float4 E;        // (v1 - v0, v2 - v0)
+    int n0, n1, n2;  // counter-clockwise
+    float det;
+};
+static_assert(sizeof(ElemRec) == 48, "ElemRec is three 16-byte words");
+
 struct Mesh {
     int64_t M = 0, K = 0;
     int ndof = 1;
@@ -116,6 +126,7 @@ struct Mesh {
     DBuf<double2> cen;    // centroids [K]
     DBuf<float4> E32;     // FP32 edge vectors (v1 - v0, v2 - v0) [K], each rounded once from FP64
     DBuf<float> det32;    // |det J_k| in FP32 [K]
+    DBuf<ElemRec> rec;    // packed element records [K]
     DBuf<double> rad;     // radii [K]
     std::shared_ptr<PairCache> cache;  // pair list, pattern and slot index of the last (delta, ball, rule)
     int64_t device_bytes() const;

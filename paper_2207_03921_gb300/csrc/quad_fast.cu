@@ -50,6 +50,7 @@ struct FastReq {
     const int4* T;
     const float4* E32;
     const float* det32;
+    const ElemRec* rec;
     float delta, d2, c, s;
     double delta64, delta2_64;
     int caps;
@@ -364,14 +365,14 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(const __grid_constan
         if (valid) {
             k = Q.pk[p];
             l = Q.pl[p];
-            tk = Q.T[k];
-            tl = Q.T[l];
-            const double2 v0k = Q.X[tk.x], v0l = Q.X[tl.x];
-            dx = (float)(v0l.x - v0k.x);
-            dy = (float)(v0l.y - v0k.y);
-            Ek = Q.E32[k];
-            El = Q.E32[l];
-            dk = Q.det32[k];
+            const ElemRec rk = Q.rec[k], rl = Q.rec[l];
+            tk = make_int4(rk.n0, rk.n1, rk.n2, 0);
+            tl = make_int4(rl.n0, rl.n1, rl.n2, 0);
+            dx = (float)(rl.v0.x - rk.v0.x);
+            dy = (float)(rl.v0.y - rk.v0.y);
+            Ek = rk.E;
+            El = rl.E;
+            dk = rk.det;
         }
         const float idet = 1.f / (El.x * El.w - El.y * El.z);
         const float W0x = dx, W0y = dy;
@@ -576,11 +577,11 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(const __grid_const
         if (pi < nlist) {
             const int64_t p = Q.ids[pilot ? pi * L.pilot : pi];
             const int k = Q.pk[p], l = Q.pl[p];
-            const int4 tk = Q.T[k], tl = Q.T[l];
-            const double2 v0k = Q.X[tk.x], v0l = Q.X[tl.x];
-            const float dx = (float)(v0l.x - v0k.x), dy = (float)(v0l.y - v0k.y);
-            const float4 Ek = Q.E32[k], El = Q.E32[l];
-            const float dk = Q.det32[k];
+            const ElemRec rk = Q.rec[k], rl = Q.rec[l];
+            const int4 tk = make_int4(rk.n0, rk.n1, rk.n2, 0), tl = make_int4(rl.n0, rl.n1, rl.n2, 0);
+            const float dx = (float)(rl.v0.x - rk.v0.x), dy = (float)(rl.v0.y - rk.v0.y);
+            const float4 Ek = rk.E, El = rl.E;
+            const float dk = rk.det;
             float kk[6][NC], kl[9][NC], ll[6][NC];
 #pragma unroll
             for (int i = 0; i < 6; ++i)
@@ -635,7 +636,7 @@ FastReq make_req(Mesh& m, PairCache& pc, const Params& prm, int list) {
     q.ids = list == 0 ? pc.whole_ids.p : pc.cut_ids.p;
     q.npairs = list == 0 ? pc.nwhole : pc.ncut;
     q.klr = list == 0 ? pc.klr_whole.p : pc.klr_cut.p;
-    q.X = m.X.p; q.T = m.T.p; q.E32 = m.E32.p; q.det32 = m.det32.p;
+    q.X = m.X.p; q.T = m.T.p; q.E32 = m.E32.p; q.det32 = m.det32.p; q.rec = m.rec.p;
     q.delta = (float)prm.delta;
     q.d2 = (float)prm.delta * (float)prm.delta;
     q.c = (float)prm.c;
