@@ -178,7 +178,7 @@ __device__ __forceinline__ long long to_fixed(float sc, float v, float& vmax) {
 
 template <int NC>
 __device__ __forceinline__ void accumulate_pair(const FastReq& Q, bool pilot, float sc, int64_t pi, int64_t p, int4 tk,
-                                                int4 tl,
+                                                int4 tl, const int* upos,
                                                 const float (&kk)[6][NC], const float (&kl)[9][NC],
                                                 const float (&ll)[6][NC], float& vmax) {
     const int kn[3] = {tk.x, tk.y, tk.z}, ln[3] = {tl.x, tl.y, tl.z};
@@ -208,7 +208,8 @@ __device__ __forceinline__ void accumulate_pair(const FastReq& Q, bool pilot, fl
         for (int b = 0; b < 3; ++b) {
             const int i = kn[a], j = ln[b];
             const float f = i == j ? 2.f : 1.f;
-            const int64_t u = Q.up_start[min(i, j)] + Q.klr[(int64_t)(a * 3 + b) * Q.npairs + pi];
+            const int64_t u = upos ? (int64_t)upos[a * 3 + b]
+                                   : Q.up_start[min(i, j)] + Q.klr[(int64_t)(a * 3 + b) * Q.npairs + pi];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const long long q = to_fixed(sc, f * kl[a * 3 + b][c], vmax);
@@ -365,6 +366,10 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(const __grid_constan
         if (valid) {
             k = Q.pk[p];
             l = Q.pl[p];
+            if (!pilot)  // the kl ranks are read after the quadrature: bring their lines into L2 now
+#pragma unroll
+                for (int e = 0; e < 9; ++e)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(Q.klr + (int64_t)e * Q.npairs + pi));
             const ElemRec rk = Q.rec[k], rl = Q.rec[l];
             tk = make_int4(rk.n0, rk.n1, rk.n2, 0);
             tl = make_int4(rl.n0, rl.n1, rl.n2, 0);
@@ -500,7 +505,7 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(const __grid_constan
                 }
             }
         }
-        if (valid) accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, kk, kl, ll, vmax);
+        if (valid) accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, nullptr, kk, kl, ll, vmax);
     }
     if (vdst) flush_max(vdst, vmax);
 }
@@ -582,6 +587,18 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(const __grid_const
             const float dx = (float)(rl.v0.x - rk.v0.x), dy = (float)(rl.v0.y - rk.v0.y);
             const float4 Ek = rk.E, El = rl.E;
             const float dk = rk.det;
+            // the upper entries of the nine kl node pairs, loaded now so that their latency
+            // hides behind the quadrature
+            int upos[9];
+            if (!pilot) {
+                const int kn[3] = {rk.n0, rk.n1, rk.n2}, ln[3] = {rl.n0, rl.n1, rl.n2};
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b)
+                        upos[a * 3 + b] = (int)(Q.up_start[min(kn[a], ln[b])] +
+                                                Q.klr[(int64_t)(a * 3 + b) * Q.npairs + pi]);
+            }
             float kk[6][NC], kl[9][NC], ll[6][NC];
 #pragma unroll
             for (int i = 0; i < 6; ++i)
@@ -607,7 +624,7 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(const __grid_const
                                        dx + El.z - Xx, dy + El.w - Xy, 0.f, 1.f);
                 outer_update<NC>(R, q0, dk, I, kk, kl, ll);
             }
-            accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, kk, kl, ll, vmax);
+            accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, upos, kk, kl, ll, vmax);
         }
     }
     if (vdst) flush_max(vdst, vmax);
