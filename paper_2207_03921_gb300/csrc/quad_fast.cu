@@ -263,8 +263,30 @@ struct GeoF {
     bool in[3];
 };
 
-__device__ __forceinline__ bool decide_flat(const float Rx[3], const float Ry[3], const float C[3], float eps,
-                                            float floor2, float d2, GeoF& g) {
+// Edge vectors of E_l (u_e = v_{e+1} - v_e, from the FP32 edge vectors E = (v1 - v0, v2 - v0))
+// with their squared lengths and 1-norms: the same for every outer point of a pair.
+struct EdgesF {
+    float ux[3], uy[3], A[3], n1[3];
+};
+
+__device__ __forceinline__ EdgesF edges_of(float4 El) {
+    EdgesF g;
+    g.ux[0] = El.x;
+    g.uy[0] = El.y;
+    g.ux[1] = El.z - El.x;
+    g.uy[1] = El.w - El.y;
+    g.ux[2] = -El.z;
+    g.uy[2] = -El.w;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        g.A[e] = g.ux[e] * g.ux[e] + g.uy[e] * g.uy[e];
+        g.n1[e] = fabsf(g.ux[e]) + fabsf(g.uy[e]);
+    }
+    return g;
+}
+
+__device__ __forceinline__ bool decide_flat(const float Rx[3], const float Ry[3], const float C[3], const EdgesF& E,
+                                            float eps, float floor2, float d2, GeoF& g) {
     bool ok = true;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -274,14 +296,14 @@ __device__ __forceinline__ bool decide_flat(const float Rx[3], const float Ry[3]
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         const int b = (e + 1) % 3;
-        const float ux = Rx[b] - Rx[e], uy = Ry[b] - Ry[e];
-        const float Aq = ux * ux + uy * uy;
+        const float ux = E.ux[e], uy = E.uy[e];
+        const float Aq = E.A[e];
         const float Bq = Rx[e] * ux + Ry[e] * uy;
         const float Cq = C[e];
         const float disc = Bq * Bq - Aq * Cq;
         const bool one = g.in[e] != g.in[b];
         const bool out2 = !g.in[e] && !g.in[b];
-        const float e1n = fabsf(Rx[e]) + fabsf(Ry[e]), u1n = fabsf(ux) + fabsf(uy);
+        const float e1n = fabsf(Rx[e]) + fabsf(Ry[e]), u1n = E.n1[e];
         const float bound = 2.f * fabsf(Bq) * (u1n + 2.f * e1n) * eps + Aq * (2.f * e1n * eps + 1e-6f * d2) +
                             fabsf(Cq) * 4.f * u1n * eps + 1e-6f * (Bq * Bq + fabsf(Aq * Cq));
         ok &= !(out2 && fabsf(disc) <= bound);
@@ -331,7 +353,7 @@ __device__ __noinline__ int clip_canonical(const double2* __restrict__ X, int4 t
 static constexpr int CHUNK = 8;
 
 template <int KER, int NQI, bool CAPS, bool BATCH>
-__global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(const __grid_constant__ FastRule R,
+__global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_constant__ FastRule R,
                                                            const __grid_constant__ FastLaunch L) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
     constexpr int MAXP = CAPS ? 9 : 6;  // polygon points: 6 raw, plus up to 3 cap centres
@@ -386,6 +408,7 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(const __grid_constan
                            fabsf(El.x) + fabsf(El.y) + fabsf(El.z) + fabsf(El.w);
         const float eps = 4.8e-7f * span;    // bound on the FP32 error of the relative coordinates
         const float floor2 = 1e-5f * Q.d2;   // floor of the vertex margin (see nl_decide32)
+        const EdgesF Ed = edges_of(El);
 
         float kk[6][NC], kl[9][NC], ll[6][NC];
 #pragma unroll
@@ -413,14 +436,13 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(const __grid_constan
 #pragma unroll
                 for (int m = 0; m < 3; ++m) Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - Q.d2;
                 GeoF G;
-                bool ok = decide_flat(Rx, Ry, Cc, eps, floor2, Q.d2, G);
+                bool ok = decide_flat(Rx, Ry, Cc, Ed, eps, floor2, Q.d2, G);
                 int n = 0;
                 if (!CAPS) {
                     // vertices inside and crossings in boundary order; predicated stores
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
-                        const int b = (e + 1) % 3;
-                        const float ux = Rx[b] - Rx[e], uy = Ry[b] - Ry[e];
+                        const float ux = Ed.ux[e], uy = Ed.uy[e];
                         if (G.in[e]) put(q, n, Rx[e], Ry[e]);
                         n += G.in[e];
                         if (G.nc[e] >= 1) put(q, n, fmaf(G.ta[e], ux, Rx[e]), fmaf(G.ta[e], uy, Ry[e]));
@@ -450,8 +472,7 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_cut(const __grid_constan
                     };
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
-                        const int b = (e + 1) % 3;
-                        const float ux = Rx[b] - Rx[e], uy = Ry[b] - Ry[e];
+                        const float ux = Ed.ux[e], uy = Ed.uy[e];
                         if (G.in[e]) raw(Rx[e], Ry[e], e, 1);
                         if (G.nc[e] >= 1) raw(fmaf(G.ta[e], ux, Rx[e]), fmaf(G.ta[e], uy, Ry[e]), e, 0);
                         if (G.nc[e] >= 2) raw(fmaf(G.tb[e], ux, Rx[e]), fmaf(G.tb[e], uy, Ry[e]), e, 0);
@@ -534,7 +555,7 @@ __global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key) {
             Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - Q.d2;
         }
         GeoF G;
-        decide_flat(Rx, Ry, Cc, 0.f, 0.f, Q.d2, G);
+        decide_flat(Rx, Ry, Cc, edges_of(El), 0.f, 0.f, Q.d2, G);
         int n = 0;
         for (int e = 0; e < 3; ++e) n += (int)G.in[e] + G.nc[e];
         if (Q.caps && n >= 2 && !(G.in[0] && G.in[1] && G.in[2])) n += 1;  // at least one cap
