@@ -225,26 +225,33 @@ __global__ void k_flag_duffy(const int8_t* cls, int64_t P, int std_close, int64_
 // relative margin of 1e-6 (far above FP64 rounding), so the canonical clip finds all three
 // vertices inside at every outer point. flag_whole / flag_cut select the two lists.
 __global__ void k_flag_whole(const int* pk, const int* pl, const int8_t* cls, int64_t P, const double2* X,
-                             const int4* T, double delta2, int std_close, int64_t* flag_whole, int64_t* flag_cut) {
+                             const int4* T, const ElemRec* rec, double delta2, int std_close, int64_t* flag_whole,
+                             int64_t* flag_cut) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     int64_t w = 0, c = 0;
     if (cls[p] == 0 || std_close) {
-        const int4 a = T[pk[p]], b = T[pl[p]];
-        const double2 va[3] = {X[a.x], X[a.y], X[a.z]}, vb[3] = {X[b.x], X[b.y], X[b.z]};
-        // the nine vertex distances in FP32 (differences rounded once from FP64); decided
-        // there unless within 1e-5 of the threshold, then in FP64
+        const int k = pk[p], l = pl[p];
+        const ElemRec rk = rec[k], rl = rec[l];
+        // vertices relative to vertex 0 of E_k in FP32 (the offset rounded once from FP64, the
+        // edge vectors as stored): decided there unless within 1e-4 of the threshold, then from
+        // the FP64 vertices
+        const float ox = (float)(rl.v0.x - rk.v0.x), oy = (float)(rl.v0.y - rk.v0.y);
+        const float kx[3] = {0.f, rk.E.x, rk.E.z}, ky[3] = {0.f, rk.E.y, rk.E.w};
+        const float lx[3] = {ox, ox + rl.E.x, ox + rl.E.z}, ly[3] = {oy, oy + rl.E.y, oy + rl.E.w};
         float mxf = 0.f;
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) {
-                const float dx = (float)(vb[j].x - va[i].x), dy = (float)(vb[j].y - va[i].y);
+                const float dx = lx[j] - kx[i], dy = ly[j] - ky[i];
                 mxf = fmaxf(mxf, dx * dx + dy * dy);
             }
         const float thr = (float)(delta2 * (1.0 - 1e-6));
         bool whole;
-        if (mxf < thr * (1.f - 1e-5f)) whole = true;
-        else if (mxf > thr * (1.f + 1e-5f)) whole = false;
+        if (mxf < thr * (1.f - 1e-4f)) whole = true;
+        else if (mxf > thr * (1.f + 1e-4f)) whole = false;
         else {
+            const int4 a = T[k], b = T[l];
+            const double2 va[3] = {X[a.x], X[a.y], X[a.z]}, vb[3] = {X[b.x], X[b.y], X[b.z]};
             double mx = 0.0;
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j) {
@@ -411,8 +418,8 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
         fc.alloc(P, st);
         pw.alloc(P + 1, st);
         pcut.alloc(P + 1, st);
-        k_flag_whole<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, pc.pcls.p, P, m.X.p, m.T.p, prm.delta2,
-                                                   close_mode(prm) == 0, fw.p, fc.p);
+        k_flag_whole<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, pc.pcls.p, P, m.X.p, m.T.p, m.rec.p,
+                                                   prm.delta2, close_mode(prm) == 0, fw.p, fc.p);
         NLFEM_LAUNCH_CHECK();
         exclusive_scan_i64(fw.p, pw.p, P, st);
         exclusive_scan_i64(fc.p, pcut.p, P, st);

@@ -111,7 +111,9 @@ __device__ __forceinline__ bool hash_insert(int* tab, int cap, int key, int* cou
     return false;
 }
 
-template <bool FILL>
+// FILL = false: count the columns of each row; true: write the sorted columns at rowptr[i],
+// or with SLOTS at i * cap / 2 and count them (one pass; k_compact_rows packs the slots)
+template <bool FILL, bool SLOTS = false>
 __global__ void k_pattern(RowEnum R, int64_t M, int cap, int64_t* rowcnt, const int64_t* rowptr,
                           int* cols, int* overflow) {
     extern __shared__ int sm[];
@@ -154,9 +156,9 @@ __global__ void k_pattern(RowEnum R, int64_t M, int cap, int64_t* rowcnt, const 
         return;
     }
     int n = *count;
-    if (!FILL) {
+    if (!FILL || SLOTS) {
         if (lane == 0) rowcnt[i] = n;
-        return;
+        if (!FILL) return;
     }
     // compact the keys to the front of the table, then bitonic sort them
     __syncwarp();
@@ -189,8 +191,16 @@ __global__ void k_pattern(RowEnum R, int64_t M, int cap, int64_t* rowcnt, const 
             __syncwarp();
         }
     }
-    int64_t base = rowptr[i];
+    int64_t base = SLOTS ? i * (int64_t)(cap / 2) : rowptr[i];
     for (int t = lane; t < n; t += 32) cols[base + t] = tab[t];
+}
+
+__global__ void k_compact_rows(const int* slots, int64_t M, int64_t width, const int64_t* ptr, int* out) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= M) return;
+    const int64_t b = ptr[i], n = ptr[i + 1] - b;
+    for (int64_t j = lane; j < n; j += 32) out[b + j] = slots[i * width + j];
 }
 
 // dof-level CSR from the node-level pattern (dofs of a node are interleaved)
@@ -572,7 +582,18 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
         size_t smem = (size_t)warps * (cap + 1) * sizeof(int);
         NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_pattern<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_pattern<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        k_pattern<false><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, cap, rowcnt.p, nullptr, nullptr, ovf.p);
+        NLFEM_CUDA_TRY(
+            cudaFuncSetAttribute(k_pattern<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        // one pass into per-row slots (a row has at most cap / 2 columns) when they fit in 4 GB
+        const bool slots = M * (int64_t)(cap / 2) * (int64_t)sizeof(int) <= ((int64_t)4 << 30);
+        DBuf<int> slot_buf;
+        if (slots) {
+            slot_buf.alloc(M * (int64_t)(cap / 2), st);
+            k_pattern<true, true><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, cap, rowcnt.p, nullptr, slot_buf.p,
+                                                                            ovf.p);
+        } else {
+            k_pattern<false><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, cap, rowcnt.p, nullptr, nullptr, ovf.p);
+        }
         NLFEM_LAUNCH_CHECK();
         int h = 0;
         NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, ovf.p, sizeof h, cudaMemcpyDeviceToHost, st));
@@ -582,7 +603,12 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
             NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.nnz_node, pc.nrow_ptr.p + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
             NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
             pc.ncol.alloc(pc.nnz_node, st);
-            k_pattern<true><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, cap, rowcnt.p, pc.nrow_ptr.p, pc.ncol.p, ovf.p);
+            if (slots) {
+                k_compact_rows<<<nblk(M * 32, 256), 256, 0, st>>>(slot_buf.p, M, cap / 2, pc.nrow_ptr.p, pc.ncol.p);
+            } else {
+                k_pattern<true><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, cap, rowcnt.p, pc.nrow_ptr.p,
+                                                                          pc.ncol.p, ovf.p);
+            }
             NLFEM_LAUNCH_CHECK();
             break;
         }
@@ -725,6 +751,34 @@ void build_slots(Mesh& m, PairCache& pc, cudaStream_t st) {
 // ------------------------------------------------------------------------------------------
 // FP32-bulk accumulation index and the conversion of the fixed-point sums into CSR values
 // ------------------------------------------------------------------------------------------
+// position of the diagonal within each node row (its first column >= the row)
+__global__ void k_diag(const int64_t* __restrict__ nptr, const int* __restrict__ ncol, int64_t M, int* __restrict__ diag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    int64_t a = nptr[i], c = nptr[i + 1];
+    while (a < c) {
+        const int64_t mid = (a + c) >> 1;
+        if (ncol[mid] < (int)i) a = mid + 1;
+        else c = mid;
+    }
+    diag[i] = (int)(a - nptr[i]);
+}
+
+// rank of column hi in the upper part of row lo with the row's diagonal position known; -1 if
+// the column is missing
+__device__ __forceinline__ int upper_rank_d(const int64_t* __restrict__ nptr, const int* __restrict__ ncol,
+                                            const int* __restrict__ diag, int lo, int hi) {
+    const int64_t b = nptr[lo] + diag[lo], e = nptr[lo + 1];
+    int64_t a = b, c = e;
+    while (a < c) {
+        const int64_t mid = (a + c) >> 1;
+        if (ncol[mid] < hi) a = mid + 1;
+        else c = mid;
+    }
+    if (a >= e || ncol[a] != hi) return -1;
+    return (int)(a - b);
+}
+
 __global__ void k_epos(const int4* __restrict__ T, int64_t K, const int64_t* __restrict__ nptr,
                        const int* __restrict__ ncol, const int64_t* __restrict__ up_start, int* __restrict__ epos,
                        int* ovf) {
@@ -745,7 +799,7 @@ __global__ void k_epos(const int4* __restrict__ T, int64_t K, const int64_t* __r
 
 __global__ void k_klr(const int* __restrict__ ids, int64_t n, const int* __restrict__ pk, const int* __restrict__ pl,
                       const int4* __restrict__ T, const int64_t* __restrict__ nptr, const int* __restrict__ ncol,
-                      uint16_t* __restrict__ klr, int* ovf) {
+                      const int* __restrict__ diag, uint16_t* __restrict__ klr, int* ovf) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int p = ids[i];
@@ -754,7 +808,7 @@ __global__ void k_klr(const int* __restrict__ ids, int64_t n, const int* __restr
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
             const int x = kn[a], y = ln[b];
-            const int r = upper_rank(nptr, ncol, min(x, y), max(x, y));
+            const int r = upper_rank_d(nptr, ncol, diag, min(x, y), max(x, y));
             if (r < 0) atomicOr(ovf, 1);
             if (r > 65535) atomicOr(ovf, 2);
             klr[(int64_t)(a * 3 + b) * n + i] = (uint16_t)min(max(r, 0), 65535);
@@ -776,14 +830,18 @@ void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st) {
     NLFEM_LAUNCH_CHECK();
     pc.klr_whole.alloc(pc.nwhole * 9, st);
     pc.klr_cut.alloc(pc.ncut * 9, st);
+    DBuf<int> diag;
+    diag.alloc(m.M, st);
+    k_diag<<<nblk(m.M, 256), 256, 0, st>>>(pc.nrow_ptr.p, pc.ncol.p, m.M, diag.p);
+    NLFEM_LAUNCH_CHECK();
     if (pc.nwhole > 0) {
         k_klr<<<nblk(pc.nwhole, 256), 256, 0, st>>>(pc.whole_ids.p, pc.nwhole, pc.pk.p, pc.pl.p, m.T.p, pc.nrow_ptr.p,
-                                                    pc.ncol.p, pc.klr_whole.p, ovf.p);
+                                                    pc.ncol.p, diag.p, pc.klr_whole.p, ovf.p);
         NLFEM_LAUNCH_CHECK();
     }
     if (pc.ncut > 0) {
         k_klr<<<nblk(pc.ncut, 256), 256, 0, st>>>(pc.cut_ids.p, pc.ncut, pc.pk.p, pc.pl.p, m.T.p, pc.nrow_ptr.p,
-                                                  pc.ncol.p, pc.klr_cut.p, ovf.p);
+                                                  pc.ncol.p, diag.p, pc.klr_cut.p, ovf.p);
         NLFEM_LAUNCH_CHECK();
     }
     // bound on the values added into one entry: every pair with the node in E_k or in E_l
