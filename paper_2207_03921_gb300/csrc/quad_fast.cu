@@ -90,50 +90,67 @@ __device__ __forceinline__ void tri_quad(const FastRule& R, const FastReq& Q, In
                                          float bx, float by, float b1, float b2, float cx, float cy, float c1,
                                          float c2) {
     const float dT = fabsf((bx - ax) * (cy - ay) - (by - ay) * (cx - ax));
-    const float a0 = 1.f - a1 - a2, b0 = 1.f - b1 - b2, c0 = 1.f - c1 - c2;
+    // the basis functions sum to one (Q0 = 1 - Q1 - Q2), so per point only the sums of w,
+    // w Q1, w Q2, w Q1^2, w Q1 Q2 and w Q2^2 are formed; h0 and the m entries with Q0 follow
+    // from them per triangle (the same quadrature sums, rearranged)
+    float g[NC], h1[NC], h2[NC], m11[NC], m12[NC], m22[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) g[c] = h1[c] = h2[c] = m11[c] = m12[c] = m22[c] = 0.f;
 #pragma unroll
     for (int q = 0; q < NQI; ++q) {
         const float l0 = R.il[q][0], l1 = R.il[q][1], l2 = R.il[q][2];
-        const float zx = l0 * ax + l1 * bx + l2 * cx;
-        const float zy = l0 * ay + l1 * by + l2 * cy;
-        const float Q0 = l0 * a0 + l1 * b0 + l2 * c0;
         const float Q1 = l0 * a1 + l1 * b1 + l2 * c1;
         const float Q2 = l0 * a2 + l1 * b2 + l2 * c2;
         const float wq = R.iw[q] * dT;
         float wc[NC];
         if (KER == NLFEM_KERNEL_CONSTANT) {
             wc[0] = wq * Q.c;
-        } else if (KER == NLFEM_KERNEL_FRACTIONAL) {
-            const float r2 = zx * zx + zy * zy;
-            if (Q.s == 0.5f) {
-                const float r = rsqrtf(r2);
-                wc[0] = wq * Q.c * r * r * r;
-            } else {
-                wc[0] = wq * Q.c * exp2f(log2f(r2) * (-1.f - Q.s));
-            }
         } else {
+            const float zx = l0 * ax + l1 * bx + l2 * cx;
+            const float zy = l0 * ay + l1 * by + l2 * cy;
             const float r2 = zx * zx + zy * zy;
-            const float r = rsqrtf(r2);
-            const float sc = wq * Q.c * r * r * r;
-            wc[0] = sc * zx * zx;
-            wc[1 % NC] = sc * zx * zy;
-            wc[2 % NC] = sc * zy * zy;
+            if (KER == NLFEM_KERNEL_FRACTIONAL) {
+                if (Q.s == 0.5f) {
+                    const float r = rsqrtf(r2);
+                    wc[0] = wq * Q.c * r * r * r;
+                } else {
+                    wc[0] = wq * Q.c * exp2f(log2f(r2) * (-1.f - Q.s));
+                }
+            } else {
+                const float r = rsqrtf(r2);
+                const float sc = wq * Q.c * r * r * r;
+                wc[0] = sc * zx * zx;
+                wc[1 % NC] = sc * zx * zy;
+                wc[2 % NC] = sc * zy * zy;
+            }
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const float w = wc[c];
-            I.g[c] += w;
-            const float w0 = w * Q0, w1 = w * Q1, w2 = w * Q2;
-            I.h[0][c] += w0;
-            I.h[1][c] += w1;
-            I.h[2][c] += w2;
-            I.m[0][c] += w0 * Q0;
-            I.m[1][c] += w0 * Q1;
-            I.m[2][c] += w0 * Q2;
-            I.m[3][c] += w1 * Q1;
-            I.m[4][c] += w1 * Q2;
-            I.m[5][c] += w2 * Q2;
+            const float w1 = w * Q1, w2 = w * Q2;
+            g[c] += w;
+            h1[c] += w1;
+            h2[c] += w2;
+            m11[c] += w1 * Q1;
+            m12[c] += w1 * Q2;
+            m22[c] += w2 * Q2;
         }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float h0 = g[c] - h1[c] - h2[c];
+        const float m01 = h1[c] - m11[c] - m12[c];
+        const float m02 = h2[c] - m12[c] - m22[c];
+        I.g[c] += g[c];
+        I.h[0][c] += h0;
+        I.h[1][c] += h1[c];
+        I.h[2][c] += h2[c];
+        I.m[0][c] += h0 - m01 - m02;
+        I.m[1][c] += m01;
+        I.m[2][c] += m02;
+        I.m[3][c] += m11[c];
+        I.m[4][c] += m12[c];
+        I.m[5][c] += m22[c];
     }
 }
 
@@ -285,13 +302,24 @@ __device__ __forceinline__ EdgesF edges_of(float4 El) {
     return g;
 }
 
+// WARP: all 32 lanes call it (skip = the lane's result is not needed); when every lane's
+// inner element is inside the ball the edge work is skipped for the whole warp
+template <bool WARP = false>
 __device__ __forceinline__ bool decide_flat(const float Rx[3], const float Ry[3], const float C[3], const EdgesF& E,
-                                            float eps, float floor2, float d2, GeoF& g) {
+                                            float eps, float floor2, float d2, GeoF& g, bool skip = false) {
     bool ok = true;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
         ok &= fabsf(C[m]) > floor2 + 2.f * (fabsf(Rx[m]) + fabsf(Ry[m])) * eps;
         g.in[m] = C[m] < 0.f;
+    }
+    if (WARP && __all_sync(0xffffffffu, skip || (g.in[0] && g.in[1] && g.in[2]))) {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            g.nc[e] = 0;
+            g.ta[e] = g.tb[e] = 0.f;
+        }
+        return ok;
     }
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
@@ -436,7 +464,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
 #pragma unroll
                 for (int m = 0; m < 3; ++m) Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - Q.d2;
                 GeoF G;
-                bool ok = decide_flat(Rx, Ry, Cc, Ed, eps, floor2, Q.d2, G);
+                bool ok = decide_flat<true>(Rx, Ry, Cc, Ed, eps, floor2, Q.d2, G, !valid);
                 int n = 0;
                 if (!CAPS) {
                     // vertices inside and crossings in boundary order; predicated stores
