@@ -5,4 +5,4 @@ cpu_baseline / reference legs of bench.py. It shares no code with the CUDA
 library and does not import it.
 """
 from .oracle import (KERNELS, BALLS, CLOSE_RULES, OracleSystem, assemble, build, clip,  # noqa: F401
-                     pair_block, pairs, solve_dirichlet, l2_error, lib_path)
+                     pair_block, pairs, solve_dirichlet, solve_neumann, null_space, l2_error, lib_path)

@@ -236,6 +236,37 @@ def solve_dirichlet(system: OracleSystem, g_nodal) -> np.ndarray:
     return u
 
 
+def null_space(verts, ndof: int) -> np.ndarray:
+    """Columns spanning the null space of the full (Neumann-type) matrix: the constants for a
+    scalar kernel, the rigid motions (two translations, the rotation (-y, x)) for the vector
+    peridynamic kernel (Sec. 2, symmetrised form, Remark on asymmetry due to quadrature)."""
+    X = np.asarray(verts, dtype=np.float64)
+    M = X.shape[0]
+    if ndof == 1:
+        return np.ones((M, 1))
+    Z = np.zeros((M, 2, 3))
+    Z[:, 0, 0] = 1.0
+    Z[:, 1, 1] = 1.0
+    Z[:, 0, 2] = -X[:, 1]
+    Z[:, 1, 2] = X[:, 0]
+    return Z.reshape(2 * M, 3)
+
+
+def solve_neumann(system: OracleSystem, verts) -> np.ndarray:
+    """Pure Neumann-type problem on the full matrix: the minimum-norm u with A u = F - P F,
+    P the orthogonal projector onto the null space N of A. Solved as the bordered system
+    [[A, Z], [Z^T, 0]] [u; lam] = [F; 0] with Z spanning N (dense, small meshes only)."""
+    Z = null_space(verts, system.ndof)
+    A = system.dense()
+    n, m = Z.shape
+    K = np.zeros((n + m, n + m))
+    K[:n, :n] = A
+    K[:n, n:] = Z
+    K[n:, :n] = Z.T
+    rhs = np.concatenate([system.F, np.zeros(m)])
+    return np.linalg.solve(K, rhs)[:n]
+
+
 def l2_error(mesh, u_h, u_exact, ndof: int = 1) -> float:
     """||u_h - u||_{L2(Omega)} with the 7-point rule on the Omega elements."""
     q = R.rule7()
