@@ -38,7 +38,7 @@
 #endif
 
 enum { ORC_K_CONST = 0, ORC_K_FRAC = 1, ORC_K_PERI = 2 };
-enum { ORC_BALL_NOCAPS = 0, ORC_BALL_APPROXCAPS = 1 };
+enum { ORC_BALL_NOCAPS = 0, ORC_BALL_APPROXCAPS = 1, ORC_BALL_INF = 2 };
 enum { ORC_CLOSE_AUTO = 0, ORC_CLOSE_DUFFY = 1, ORC_CLOSE_NOZERODIV = 2, ORC_CLOSE_STANDARD = 3 };
 enum { ORC_PAIRS_BFS = 0, ORC_PAIRS_BRUTE = 1 };
 
@@ -224,6 +224,76 @@ int orc_clip_ball(const double V[3][2], double cx, double cy, double delta, doub
 }
 
 /* ---------------------------------------------------------------------------------------
+ * Infinity norm ball (Sec. 2.2, Def. of the infinity norm ball): E_l cut by the closed square
+ * {y : |y - c|_inf <= delta} exactly. Sutherland-Hodgman clipping of the CCW triangle by the
+ * four half-planes x <= delta, y <= delta, x >= -delta, y >= -delta, in this order, in
+ * coordinates relative to c:
+ *   p = (vx - cx, vy - cy) per vertex, each difference rounded once;
+ *   half-plane (axis a, sign s): inside iff s * p[a] <= delta;
+ *   one pass walks S -> E over consecutive points, starting with S = the last point and
+ *   E = the first; where S and E lie on different sides it emits the crossing
+ *     t = (s*delta - S[a]) / (E[a] - S[a]),  X[a] = s*delta,  X[b] = S[b] + t * (E[b] - S[b])
+ *   (b the other axis), then E itself if E is inside.
+ * Afterwards consecutive points that coincide exactly (also the last and the first) are
+ * merged; fewer than 3 points mean an empty intersection. full = every vertex inside all four
+ * half-planes (the element is integrated whole with its own rule). The points are returned
+ * in absolute coordinates c + p.
+ * ------------------------------------------------------------------------------------- */
+static int sh_pass(double in[][2], int n, int a, double s, double delta, double out[][2])
+{
+    int m = 0;
+    if (n == 0) return 0;
+    const int b = 1 - a;
+    const double *S = in[n - 1];
+    int s_in = s * S[a] <= delta;
+    for (int i = 0; i < n; ++i) {
+        const double *E = in[i];
+        int e_in = s * E[a] <= delta;
+        if (e_in != s_in) {
+            double t = (s * delta - S[a]) / (E[a] - S[a]);
+            out[m][a] = s * delta;
+            out[m][b] = S[b] + t * (E[b] - S[b]);
+            ++m;
+        }
+        if (e_in) { out[m][0] = E[0]; out[m][1] = E[1]; ++m; }
+        S = E;
+        s_in = e_in;
+    }
+    return m;
+}
+
+int orc_clip_square(const double V[3][2], double cx, double cy, double delta, double out[][2], int *full)
+{
+    double A[MAXPOLY][2], B[MAXPOLY][2];
+    int all_in = 1;
+    for (int v = 0; v < 3; ++v) {
+        A[v][0] = V[v][0] - cx;
+        A[v][1] = V[v][1] - cy;
+        all_in &= fabs(A[v][0]) <= delta && fabs(A[v][1]) <= delta;
+    }
+    if (all_in) {
+        *full = 1;
+        for (int v = 0; v < 3; ++v) { out[v][0] = V[v][0]; out[v][1] = V[v][1]; }
+        return 3;
+    }
+    *full = 0;
+    int n = 3;
+    n = sh_pass(A, n, 0, 1.0, delta, B);
+    n = sh_pass(B, n, 1, 1.0, delta, A);
+    n = sh_pass(A, n, 0, -1.0, delta, B);
+    n = sh_pass(B, n, 1, -1.0, delta, A);
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        if (m > 0 && A[i][0] == B[m - 1][0] && A[i][1] == B[m - 1][1]) continue;
+        B[m][0] = A[i][0]; B[m][1] = A[i][1]; ++m;
+    }
+    while (m >= 2 && B[m - 1][0] == B[0][0] && B[m - 1][1] == B[0][1]) --m;
+    if (m < 3) return 0;
+    for (int i = 0; i < m; ++i) { out[i][0] = cx + B[i][0]; out[i][1] = cy + B[i][1]; }
+    return m;
+}
+
+/* ---------------------------------------------------------------------------------------
  * Kernels (Sec. 3): value of gamma (scalar) or the 2x2 matrix Gamma (peridynamics)
  * at z = y - x.
  * ------------------------------------------------------------------------------------- */
@@ -304,7 +374,9 @@ static int pair_truncation(const mesh_t *m, const params_t *P, int k, int l, int
         double xp, yp;
         map_point(Vk, P->ro.l[p], &xp, &yp);
         int full = 0;
-        int np = orc_clip_ball(Vl, xp, yp, P->delta, P->delta2, P->ball == ORC_BALL_APPROXCAPS, poly, &full);
+        int np = P->ball == ORC_BALL_INF
+                     ? orc_clip_square(Vl, xp, yp, P->delta, poly, &full)
+                     : orc_clip_ball(Vl, xp, yp, P->delta, P->delta2, P->ball == ORC_BALL_APPROXCAPS, poly, &full);
         if (np < 3) continue;
         interacts = 1;
         if (!accumulate) return 1;
@@ -691,6 +763,8 @@ static void set_params(params_t *P, int kernel, double delta, double s, double k
     P->kernel = kernel; P->ball = ball; P->close_rule = close_rule; P->ndof = ndof;
     P->delta = delta; P->delta2 = delta * delta; P->s = s;
     if (!isnan(kconst)) P->c = kconst;
+    else if (kernel == ORC_K_CONST && ball == ORC_BALL_INF)
+        P->c = 3.0 / (4.0 * delta * delta * delta * delta);   /* c_delta^inf of Sec. 3.3 */
     else if (kernel == ORC_K_CONST) P->c = 4.0 / (M_PI * delta * delta * delta * delta);
     else if (kernel == ORC_K_FRAC) P->c = (2.0 - 2.0 * s) / (M_PI * pow(delta, 2.0 - 2.0 * s));
     else P->c = 3.0 / (delta * delta * delta);
@@ -952,11 +1026,13 @@ int orc_pair_block(int M, const double *X, int K, const int *T, int kernel, doub
 }
 
 /* Clip test hook: V is 3x2, out receives up to 16 points. Returns count, *full flag. */
-int orc_clip(const double *V6, double cx, double cy, double delta, int caps, double *out, int *full)
+/* ball: 0 nocaps, 1 approxcaps, 2 infinity norm ball */
+int orc_clip(const double *V6, double cx, double cy, double delta, int ball, double *out, int *full)
 {
     double V[3][2] = {{V6[0], V6[1]}, {V6[2], V6[3]}, {V6[4], V6[5]}};
     double P[MAXPOLY][2];
-    int n = orc_clip_ball(V, cx, cy, delta, delta * delta, caps, P, full);
+    int n = ball == ORC_BALL_INF ? orc_clip_square(V, cx, cy, delta, P, full)
+                                 : orc_clip_ball(V, cx, cy, delta, delta * delta, ball == ORC_BALL_APPROXCAPS, P, full);
     for (int i = 0; i < n; ++i) { out[2 * i] = P[i][0]; out[2 * i + 1] = P[i][1]; }
     return n;
 }

@@ -31,7 +31,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liborc.so")
 
 KERNELS = {"constant": 0, "fractional": 1, "peridynamic": 2}
-BALLS = {"nocaps": 0, "approxcaps": 1}
+BALLS = {"nocaps": 0, "approxcaps": 1, "infinity": 2}
 CLOSE_RULES = {"auto": 0, "duffy": 1, "nozerodiv": 2, "standard": 3}
 
 _lock = threading.Lock()
@@ -209,13 +209,15 @@ def pair_block(mesh, k: int, l: int, kernel="constant", delta=0.1, s=-1.0, kcons
     return node[:U].copy(), blk[:n * n].reshape(n, n).copy(), r > 0
 
 
-def clip(V, c, delta: float, caps: bool):
-    """E_l (3x2 vertices) cut by the nocaps / approxcaps ball around c. Returns (points [n,2], full)."""
+def clip(V, c, delta: float, caps: bool = False, ball=None):
+    """E_l (3x2 vertices) cut by the ball around c: nocaps / approxcaps (caps) or, with
+    ball="infinity", the infinity norm ball. Returns (points [n,2], full)."""
     lib = _load()
     V = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(6))
     out = np.zeros(32, dtype=np.float64)
     full = C.c_int(0)
-    n = lib.orc_clip(_p(V, C.c_double), float(c[0]), float(c[1]), float(delta), int(bool(caps)),
+    b = BALLS[ball] if ball is not None else int(bool(caps))
+    n = lib.orc_clip(_p(V, C.c_double), float(c[0]), float(c[1]), float(delta), b,
                      _p(out, C.c_double), C.byref(full))
     return out[:2 * n].reshape(n, 2).copy(), bool(full.value)
 

@@ -27,11 +27,12 @@ GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_t
 
 
 @pytest.mark.parametrize("mesh_kind,ball,nq", [("structured", "nocaps", 7), ("jittered", "approxcaps", 7),
-                                              ("jittered", "nocaps", 16), ("structured", "approxcaps", 16)])
+                                              ("jittered", "nocaps", 16), ("structured", "approxcaps", 16),
+                                              ("structured", "infinity", 7), ("jittered", "infinity", 16)])
 def test_bfs_pairs_equal_brute_force(mesh_kind, ball, nq):
     m = meshes.structured(0.0, 1.0, 7) if mesh_kind == "structured" else \
         meshes.jittered_delaunay(0.0, 1.0, 7, 0.1, seed=3)
-    delta = 2.0 / 7
+    delta = 2.0 / 7 if ball != "infinity" else 1.5 / 7   # square sides on mesh lines when structured
     a = oracle.pairs(m, kernel="constant", delta=delta, ball=ball, quad_outer=nq, mode="bfs")
     b = oracle.pairs(m, kernel="constant", delta=delta, ball=ball, quad_outer=nq, mode="brute")
     assert len(a) == len(b) > m.K
@@ -51,6 +52,8 @@ def test_classification_counts_structured():
 
 CASES = [
     dict(kernel="constant", delta=0.3, ball="nocaps"),
+    dict(kernel="constant", delta=0.3, ball="infinity"),
+    dict(kernel="fractional", s=0.25, delta=0.2, ball="infinity"),
     dict(kernel="constant", delta=0.3, ball="approxcaps", quad_outer=16, quad_inner=16),
     dict(kernel="fractional", s=0.5, delta=0.3, ball="approxcaps"),
     dict(kernel="fractional", s=0.75, delta=0.3, ball="nocaps", quad_outer=16, quad_inner=7),
@@ -151,6 +154,32 @@ def test_paper_E1_fractional_rates():
 def test_paper_E3_peridynamic_rates():
     runs = [_e3(k) for k in range(3)]
     _check(GOLD["E3_peridynamics_cg"], runs)
+
+
+def _e6(level):
+    # Sec. 3.3, delta = 2a (h = sqrt(2) a the element diameter): u = sin(4 pi x) sin(4 pi y),
+    # f = -Delta u given at the nodes, constant kernel c = 3 / (4 delta^4) on the infinity ball
+    a = 0.1 / 2 ** level              # printed h = sqrt(2) a
+    delta = GOLD["E6_infinity_delta_h"]["delta"][level]
+    m = meshes.paper_square(delta, a)
+    ue = lambda x, y: np.sin(4 * math.pi * x) * np.sin(4 * math.pi * y)
+    x, y = m.verts[:, 0], m.verts[:, 1]
+    S = oracle.assemble(m, kernel="constant", delta=delta, ball="infinity",
+                        f_nodal=32 * math.pi ** 2 * ue(x, y))
+    u = oracle.solve_dirichlet(S, ue(x, y))
+    return oracle.l2_error(m, u, ue)
+
+
+def test_paper_E6_infinity_ball_rates():
+    tab = GOLD["E6_infinity_delta_h"]
+    errs = [_e6(k) for k in range(4)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    for i, r in enumerate(rates):
+        assert abs(r - tab["rate"][i + 1]) < 0.15, (rates, errs)
+    # the printed errors include the paper's (unstated) load quadrature of the oscillating f;
+    # with f given at the nodes they come out about 20% larger: the magnitude is pinned
+    for i, e in enumerate(errs):
+        assert 0.5 * tab["l2"][i] < e < 2.0 * tab["l2"][i], (errs, tab["l2"])
 
 
 @pytest.mark.slow
