@@ -42,6 +42,8 @@ extern "C" {
 /* ball approximations of the Euclidean ball (Sec. 2.2) */
 #define NLFEM_BALL_NOCAPS 0         /* Def. 2.1 */
 #define NLFEM_BALL_APPROXCAPS 1     /* Def. 2.2 */
+#define NLFEM_BALL_INFINITY 2       /* the infinity norm ball |x - y|_inf <= delta, cut exactly (Sec. 2.2);
+                                       constant kernel default c = 3 / (4 delta^4) (Sec. 3.3) */
 
 /* rule on intersecting element pairs (Tab. 1) */
 #define NLFEM_CLOSE_AUTO 0          /* club for 0 < s < 1, diamond for -1 < s <= 0 and peridynamics, heart otherwise */
@@ -214,6 +216,20 @@ int nlfem_mesh_pairs(nlfem_mesh_t mesh, const int32_t** k, const int32_t** l, in
  */
 int nlfem_solve(nlfem_system_t sys, const double* g_nodal, double tol_rel, int max_iter,
                 double* u_out, nlfem_solve_info* info, void* stream);
+
+/*
+ * Pure Neumann-type problem on the full matrix (every dof unknown, Dirichlet flags
+ * ignored). A annihilates its null space N up to rounding: the constants for scalar
+ * kernels, the rigid motions (two translations and the rotation (-y, x)) for the
+ * peridynamic kernel (Sec. 1 and Rem. 2.4: the symmetrised form keeps N exact). Returns the
+ * u orthogonal to N with P A u = P F, P the orthogonal projector onto the complement of N
+ * (for an exact null space: the minimum-norm solution of A u = F - (the part of F in N)).
+ * Projected FP32 conjugate gradients inside FP64 residual refinement until
+ * ||P (F - A u)|| <= tol_rel ||P F||. u_out [nrows], device, caller-owned.
+ * Errors: INVALID_ARG, NOT_CONVERGED (u_out holds the last iterate), OOM, CUDA.
+ */
+int nlfem_solve_neumann(nlfem_system_t sys, double tol_rel, int max_iter, double* u_out,
+                        nlfem_solve_info* info, void* stream);
 
 /*
  * Work of the assembly that produced sys, counted on the device with the canonical FP64

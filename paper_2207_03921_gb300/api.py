@@ -118,6 +118,13 @@ class System:
         info = B.nlfem_solve(self.handle, g, tol_rel, max_iter, u, stream)
         return u, info
 
+    def solve_neumann(self, tol_rel=1e-10, max_iter=20000, stream=None):
+        """u orthogonal to the null space N of A with P A u = P F (nlfem_solve_neumann)."""
+        torch = _torch()
+        u = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        info = B.nlfem_solve_neumann(self.handle, tol_rel, max_iter, u, stream)
+        return u, info
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h and getattr(self, "_owner", None) is None:

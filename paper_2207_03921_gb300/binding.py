@@ -23,7 +23,7 @@ NLFEM_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "BAD_MESH", -3: "OOM", -4: "BUDGET", -5: "CUDA", -6: "NOT_CONVERGED",
           -7: "TIMEOUT", -8: "UNSUPPORTED"}
 KERNELS = {"constant": 0, "fractional": 1, "peridynamic": 2}
-BALLS = {"nocaps": 0, "approxcaps": 1}
+BALLS = {"nocaps": 0, "approxcaps": 1, "infinity": 2}
 CLOSE_RULES = {"auto": 0, "duffy": 1, "nozerodiv": 2, "standard": 3}
 PRECISIONS = {"fp64": 0, "fp32_bulk": 1}
 
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
         lib.nlfem_system_info.argtypes = [vp, C.POINTER(nlfem_assembly_info)]
         lib.nlfem_mesh_pairs.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
         lib.nlfem_solve.argtypes = [vp, vp, dp, ip, vp, C.POINTER(nlfem_solve_info), vp]
+        lib.nlfem_solve_neumann.argtypes = [vp, dp, ip, vp, C.POINTER(nlfem_solve_info), vp]
         lib.nlfem_system_census.argtypes = [vp, C.POINTER(C.c_int64), vp]
         lib.nlfem_system_destroy.argtypes = [vp]
         lib.nlfem_system_destroy.restype = None
@@ -246,6 +247,17 @@ def nlfem_solve(sys, g_nodal, tol_rel, max_iter, u_out, stream=None) -> dict:
     info = nlfem_solve_info()
     code = load().nlfem_solve(sys, _ptr(g_nodal), float(tol_rel), int(max_iter), _ptr(u_out),
                               C.byref(info), _stream(stream))
+    out = {"iterations": info.iterations, "refinements": info.refinements, "rel_residual": info.rel_residual,
+           "status": code}
+    if code not in (NLFEM_OK, -6):
+        _check(code)
+    return out
+
+
+def nlfem_solve_neumann(sys, tol_rel, max_iter, u_out, stream=None) -> dict:
+    info = nlfem_solve_info()
+    code = load().nlfem_solve_neumann(sys, float(tol_rel), int(max_iter), _ptr(u_out), C.byref(info),
+                                      _stream(stream))
     out = {"iterations": info.iterations, "refinements": info.refinements, "rel_residual": info.rel_residual,
            "status": code}
     if code not in (NLFEM_OK, -6):

@@ -85,8 +85,8 @@ static void fill_gauss(DuffyRule& d, int n) {
 static Params make_params(const nlfem_params& p, int ndof) {
     NLFEM_CHECK(p.kernel >= 0 && p.kernel <= 2, NLFEM_ERR_INVALID_ARG, "unknown kernel");
     NLFEM_CHECK(p.delta > 0 && std::isfinite(p.delta), NLFEM_ERR_INVALID_ARG, "delta must be > 0");
-    NLFEM_CHECK(p.ball == NLFEM_BALL_NOCAPS || p.ball == NLFEM_BALL_APPROXCAPS, NLFEM_ERR_INVALID_ARG,
-                "unknown ball approximation");
+    NLFEM_CHECK(p.ball == NLFEM_BALL_NOCAPS || p.ball == NLFEM_BALL_APPROXCAPS || p.ball == NLFEM_BALL_INFINITY,
+                NLFEM_ERR_INVALID_ARG, "unknown ball");
     NLFEM_CHECK((p.quad_outer == 7 || p.quad_outer == 16) && (p.quad_inner == 7 || p.quad_inner == 16),
                 NLFEM_ERR_INVALID_ARG, "quadrature rules must have 7 or 16 points");
     NLFEM_CHECK(p.close_rule >= 0 && p.close_rule <= 3, NLFEM_ERR_INVALID_ARG, "unknown close-pair rule");
@@ -109,6 +109,8 @@ static Params make_params(const nlfem_params& p, int ndof) {
     P.delta2 = p.delta * p.delta;
     P.s = p.kernel == NLFEM_KERNEL_FRACTIONAL ? p.s : (p.kernel == NLFEM_KERNEL_PERIDYNAMIC ? -0.5 : -1.0);
     if (!std::isnan(p.kconst)) P.c = p.kconst;
+    else if (p.kernel == NLFEM_KERNEL_CONSTANT && p.ball == NLFEM_BALL_INFINITY)
+        P.c = 3.0 / (4.0 * p.delta * p.delta * p.delta * p.delta);  // c_delta^inf (Sec. 3.3)
     else if (p.kernel == NLFEM_KERNEL_CONSTANT) P.c = 4.0 / (M_PI * p.delta * p.delta * p.delta * p.delta);
     else if (p.kernel == NLFEM_KERNEL_FRACTIONAL) P.c = (2.0 - 2.0 * p.s) / (M_PI * std::pow(p.delta, 2.0 - 2.0 * p.s));
     else P.c = 3.0 / (p.delta * p.delta * p.delta);
@@ -797,6 +799,17 @@ int nlfem_solve(nlfem_system_t sys, const double* g_nodal, double tol_rel, int m
         }
     }
     return solve_system(sys->s, g, tol_rel, max_iter, u_out, info, st);
+    NLFEM_API_END
+}
+
+int nlfem_solve_neumann(nlfem_system_t sys, double tol_rel, int max_iter, double* u_out, nlfem_solve_info* info,
+                        void* stream) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(sys && u_out, NLFEM_ERR_INVALID_ARG, "NULL argument");
+    NLFEM_CHECK(tol_rel > 0 && max_iter > 0, NLFEM_ERR_INVALID_ARG, "need tol_rel > 0 and max_iter > 0");
+    NLFEM_CHECK(is_device_ptr(u_out), NLFEM_ERR_INVALID_ARG, "u_out must be device memory");
+    return solve_neumann(sys->s, tol_rel, max_iter, u_out, info, (cudaStream_t)stream);
     NLFEM_API_END
 }
 

@@ -314,6 +314,7 @@ void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st)
 inline int close_mode(const Params& P) { return P.singular ? 1 : (P.nozerodiv ? 2 : 0); }
 int solve_system(System& S, const double* g, double tol, int max_iter, double* u_out, nlfem_solve_info* info,
                  cudaStream_t st);
+int solve_neumann(System& S, double tol, int max_iter, double* u_out, nlfem_solve_info* info, cudaStream_t st);
 
 // exclusive scan of int64 counts in place (n values -> n + 1 offsets in out)
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
@@ -481,6 +482,102 @@ __device__ __forceinline__ int nl_clip(const double2 V[3], double2 c, double del
         }
     }
     return m;
+}
+
+// ------------------------------------------------------------------------------------------
+// Infinity norm ball (Sec. 2.2, Def. of the infinity norm ball): E_l cut exactly by the closed
+// square |y - c|_inf <= delta. Canonical FP64 operation order, in coordinates relative to c:
+//   p = (vx - cx, vy - cy) per vertex, each difference rounded once; full = every vertex has
+//   |px| <= delta and |py| <= delta;
+//   Sutherland-Hodgman passes by x <= delta, y <= delta, x >= -delta, y >= -delta (in this
+//   order); half-plane (axis a, sign s): inside iff s * p[a] <= delta; a pass walks S -> E over
+//   consecutive points from S = the last point, E = the first, and emits the crossing
+//     t = (s delta - S[a]) / (E[a] - S[a]),  X[a] = s delta,  X[b] = S[b] + t (E[b] - S[b])
+//   where S and E lie on different sides, then E if E is inside;
+//   consecutive points that coincide exactly (also the last and the first) are merged;
+//   fewer than 3 points = empty.
+// ------------------------------------------------------------------------------------------
+#define NLFEM_MAXSQ 8
+
+__device__ __forceinline__ int nl_sh_pass(const double2* in, int n, int a, double s, double delta, double2* out) {
+    if (n == 0) return 0;
+    int m = 0;
+    double2 S = in[n - 1];
+    double sa = a ? S.y : S.x;
+    bool s_in = __dmul_rn(s, sa) <= delta;
+    for (int i = 0; i < n; ++i) {
+        const double2 E = in[i];
+        const double ea = a ? E.y : E.x;
+        const bool e_in = __dmul_rn(s, ea) <= delta;
+        if (e_in != s_in) {
+            const double sb = a ? S.x : S.y, eb = a ? E.x : E.y;
+            const double sd = __dmul_rn(s, delta);
+            const double t = __ddiv_rn(__dsub_rn(sd, sa), __dsub_rn(ea, sa));
+            const double xb = __dadd_rn(sb, __dmul_rn(t, __dsub_rn(eb, sb)));
+            if (m < NLFEM_MAXSQ) out[m] = a ? make_double2(xb, sd) : make_double2(sd, xb);
+            ++m;
+        }
+        if (e_in) {
+            if (m < NLFEM_MAXSQ) out[m] = E;
+            ++m;
+        }
+        S = E;
+        sa = ea;
+        s_in = e_in;
+    }
+    return m < NLFEM_MAXSQ ? m : NLFEM_MAXSQ;  // a triangle by four half-planes: at most 7
+}
+
+// Polygon of the square cut in coordinates relative to c (rel, up to NLFEM_MAXSQ points);
+// returns the point count (0 when empty, 3 with full = true for the whole element).
+__device__ __forceinline__ int nl_clip_square_rel(const double2 V[3], double2 c, double delta, double2* rel,
+                                                  bool& full) {
+    double2 A[NLFEM_MAXSQ], B[NLFEM_MAXSQ];
+    bool all_in = true;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        A[v] = make_double2(__dsub_rn(V[v].x, c.x), __dsub_rn(V[v].y, c.y));
+        all_in &= fabs(A[v].x) <= delta && fabs(A[v].y) <= delta;
+    }
+    full = all_in;
+    if (all_in) {
+        for (int v = 0; v < 3; ++v) rel[v] = A[v];
+        return 3;
+    }
+    int n = nl_sh_pass(A, 3, 0, 1.0, delta, B);
+    n = nl_sh_pass(B, n, 1, 1.0, delta, A);
+    n = nl_sh_pass(A, n, 0, -1.0, delta, B);
+    n = nl_sh_pass(B, n, 1, -1.0, delta, A);
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        if (m > 0 && A[i].x == rel[m - 1].x && A[i].y == rel[m - 1].y) continue;
+        rel[m++] = A[i];
+    }
+    while (m >= 2 && rel[m - 1].x == rel[0].x && rel[m - 1].y == rel[0].y) --m;
+    return m >= 3 ? m : 0;
+}
+
+// The same cut as CPt points (absolute coordinates c + p, barycentric coordinates in E_l);
+// out == nullptr: count only.
+__device__ __forceinline__ int nl_clip_square(const double2 V[3], double2 c, double delta, CPt* out, bool& full) {
+    double2 rel[NLFEM_MAXSQ];
+    const int n = nl_clip_square_rel(V, c, delta, rel, full);
+    if (!out || full) return n;
+    const double ex1 = V[1].x - V[0].x, ey1 = V[1].y - V[0].y, ex2 = V[2].x - V[0].x, ey2 = V[2].y - V[0].y;
+    const double dj = ex1 * ey2 - ey1 * ex2;
+    for (int i = 0; i < n; ++i) {
+        const double x = __dadd_rn(c.x, rel[i].x), y = __dadd_rn(c.y, rel[i].y);
+        const double px = x - V[0].x, py = y - V[0].y;
+        out[i] = CPt{x, y, (px * ey2 - py * ex2) / dj, (ex1 * py - ey1 * px) / dj, -1, 0.0, 0};
+    }
+    return n;
+}
+
+// Dispatch on the ball: Euclidean approximations (nocaps / approxcaps) or the infinity ball.
+__device__ __forceinline__ int nl_clip_ball(int ball, const double2 V[3], double2 c, double delta, double delta2,
+                                            CPt* out, bool& full) {
+    if (ball == NLFEM_BALL_INFINITY) return nl_clip_square(V, c, delta, out, full);
+    return nl_clip(V, c, delta, delta2, ball == NLFEM_BALL_APPROXCAPS, out, full);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -20,7 +20,10 @@ struct SolveState {
     DBuf<double> b, x, r64, y64;
     DBuf<float> r, p, q, d;
     DBuf<double> part;    // partial sums of dot products
-    DBuf<double> sc;      // device scalars: [0] rho, [1] p.q, [2] rho_new, [3] |r64|^2, [4] |b|^2
+    DBuf<double> sc;      // device scalars: [0] rho, [1] p.q, [2] rho_new, [3] |r64|^2, [4] |b|^2,
+                          // [8..10] null-space coefficients, [11] Gram-Schmidt scratch
+    DBuf<double> Z;       // orthonormal null-space basis of the full matrix [nz][N] (Neumann solve)
+    int nz = 0;
 };
 
 static constexpr int DOT_BLOCKS = 1024;
@@ -43,11 +46,12 @@ __global__ void k_spmv(const int64_t* rp, const int* col, const V* val, const T*
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (i >= N) return;
+    const bool fr = !freem || freem[i];   // freem == nullptr: every dof is unknown (Neumann solve)
     T s = 0;
-    if (freem[i])
+    if (fr)
         for (int64_t t = rp[i] + lane; t < rp[i + 1]; t += 32) s += (T)val[t] * x[col[t]];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[i] = freem[i] ? s : (T)0;
+    if (lane == 0) y[i] = fr ? s : (T)0;
 }
 
 // b = F - A x with x = g at Dirichlet dofs and 0 elsewhere; zero at Dirichlet rows
@@ -141,25 +145,179 @@ __global__ void k_final_u(const double* x, const double* g, const int8_t* freem,
     if (i < n) u[i] = freem[i] ? x[i] : (g ? g[i] : 0.0);
 }
 
-int solve_system(System& S, const double* g, double tol, int max_iter, double* u_out, nlfem_solve_info* info,
-                 cudaStream_t st) {
+// ---- pure Neumann-type solve on the full matrix ------------------------------------------
+// The full matrix annihilates the constants (scalar kernels) and the rigid motions (vector
+// peridynamic kernel) up to rounding: the symmetrised form of Rem. 2.4. The solve returns the
+// u orthogonal to that null space N with P A u = P F, P the orthogonal projector onto the
+// complement of N, by conjugate gradients on P A P (every residual projected) inside the same
+// FP64 refinement as the Dirichlet solve.
+
+// raw basis: ones, or for two dofs per node the translations and the rotation (-(y - cy), x - cx)
+__global__ void k_null_raw(const double2* X, int64_t M, int ndof, double cx, double cy, double* Z, int64_t N) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    if (ndof == 1) {
+        Z[i] = 1.0;
+        return;
+    }
+    const double x = X[i].x - cx, y = X[i].y - cy;
+    Z[2 * i] = 1.0;
+    Z[2 * i + 1] = 0.0;
+    Z[N + 2 * i] = 0.0;
+    Z[N + 2 * i + 1] = 1.0;
+    Z[2 * N + 2 * i] = -y;
+    Z[2 * N + 2 * i + 1] = x;
+}
+
+// a -= c b with c read from the device (Gram-Schmidt step)
+__global__ void k_axpy_dev(double* a, const double* b, const double* c, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] -= *c * b[i];
+}
+
+__global__ void k_normalise(double* a, const double* nn, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] /= sqrt(*nn);
+}
+
+// v -= sum_j c_j Z_j, the coefficients c_j = Z_j . v read from the device
+template <typename T>
+__global__ void k_project_out(T* v, const double* Z, const double* c, int nz, int64_t N) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double s = (double)v[i];
+    for (int j = 0; j < nz; ++j) s -= c[j] * Z[(int64_t)j * N + i];
+    v[i] = (T)s;
+}
+
+template <typename T>
+static void project_out(SolveState& W, T* v, cudaStream_t st) {
+    for (int j = 0; j < W.nz; ++j) dot(W.Z.p + (int64_t)j * W.N, v, W.N, W.part.p, W.sc.p + 8 + j, st);
+    k_project_out<T><<<nblk(W.N, 256), 256, 0, st>>>(v, W.Z.p, W.sc.p + 8, W.nz, W.N);
+}
+
+static int ensure_solver(System& S, cudaStream_t st) {
+    if (S.solver) return NLFEM_OK;
+    const int64_t N = S.N;
+    auto ss = std::make_shared<SolveState>();
+    ss->N = N;
+    ss->val32.alloc(S.nnz, st);
+    k_to_f32<<<nblk(S.nnz, 256), 256, 0, st>>>(S.val.p, ss->val32.p, S.nnz);
+    NLFEM_LAUNCH_CHECK();
+    ss->freem.alloc(N, st);
+    k_freemask<<<nblk(N, 256), 256, 0, st>>>(S.mesh->dir.p, N, S.prm.ndof, ss->freem.p);
+    NLFEM_LAUNCH_CHECK();
+    ss->b.alloc(N, st); ss->x.alloc(N, st); ss->r64.alloc(N, st); ss->y64.alloc(N, st);
+    ss->r.alloc(N, st); ss->p.alloc(N, st); ss->q.alloc(N, st); ss->d.alloc(N, st);
+    ss->part.alloc(DOT_BLOCKS, st);
+    ss->sc.alloc(16, st);
+    S.solver = ss;
+    return NLFEM_OK;
+}
+
+int solve_neumann(System& S, double tol, int max_iter, double* u_out, nlfem_solve_info* info, cudaStream_t st) {
+    int rc = ensure_solver(S, st);
+    if (rc) return rc;
     const int64_t N = S.N;
     PairCache& pc = *S.pc;
-    if (!S.solver) {
-        auto ss = std::make_shared<SolveState>();
-        ss->N = N;
-        ss->val32.alloc(S.nnz, st);
-        k_to_f32<<<nblk(S.nnz, 256), 256, 0, st>>>(S.val.p, ss->val32.p, S.nnz);
+    SolveState& W = *S.solver;
+    const unsigned gw = nblk(N * 32, 256), ge = nblk(N, 256);
+    if (!W.nz) {
+        const Mesh& m = *S.mesh;
+        W.nz = S.prm.ndof == 1 ? 1 : 3;
+        W.Z.alloc((size_t)W.nz * N, st);
+        k_null_raw<<<nblk(m.M, 256), 256, 0, st>>>(m.X.p, m.M, S.prm.ndof, 0.5 * (m.bbox[0] + m.bbox[2]),
+                                                 0.5 * (m.bbox[1] + m.bbox[3]), W.Z.p, N);
         NLFEM_LAUNCH_CHECK();
-        ss->freem.alloc(N, st);
-        k_freemask<<<nblk(N, 256), 256, 0, st>>>(S.mesh->dir.p, N, S.prm.ndof, ss->freem.p);
-        NLFEM_LAUNCH_CHECK();
-        ss->b.alloc(N, st); ss->x.alloc(N, st); ss->r64.alloc(N, st); ss->y64.alloc(N, st);
-        ss->r.alloc(N, st); ss->p.alloc(N, st); ss->q.alloc(N, st); ss->d.alloc(N, st);
-        ss->part.alloc(DOT_BLOCKS, st);
-        ss->sc.alloc(8, st);
-        S.solver = ss;
+        // modified Gram-Schmidt in FP64
+        for (int k = 0; k < W.nz; ++k) {
+            double* zk = W.Z.p + (int64_t)k * N;
+            for (int j = 0; j < k; ++j) {
+                const double* zj = W.Z.p + (int64_t)j * N;
+                dot(zj, zk, N, W.part.p, W.sc.p + 11, st);
+                k_axpy_dev<<<ge, 256, 0, st>>>(zk, zj, W.sc.p + 11, N);
+            }
+            dot(zk, zk, N, W.part.p, W.sc.p + 11, st);
+            k_normalise<<<ge, 256, 0, st>>>(zk, W.sc.p + 11, N);
+            NLFEM_LAUNCH_CHECK();
+        }
     }
+    // b = P F
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(W.b.p, S.F.p, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    project_out(W, W.b.p, st);
+    W.x.zero(st);
+    dot(W.b.p, W.b.p, N, W.part.p, W.sc.p + 4, st);
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(W.r64.p, W.b.p, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    NLFEM_LAUNCH_CHECK();
+    double bb = 0;
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&bb, W.sc.p + 4, sizeof bb, cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    const double bnorm = std::sqrt(bb);
+    int iters = 0, refs = 0;
+    double rel = bnorm > 0 ? 1.0 : 0.0;
+    const int CHECK_EVERY = 8;
+    while (rel > tol && iters < max_iter) {
+        k_start<<<ge, 256, 0, st>>>(W.r.p, W.p.p, W.d.p, W.r64.p, N);
+        NLFEM_LAUNCH_CHECK();
+        dot(W.r.p, W.r.p, N, W.part.p, W.sc.p + 0, st);
+        double rho0 = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&rho0, W.sc.p, sizeof rho0, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        const double inner_tol2 = rho0 * 1e-8;
+        int it = 0;
+        while (iters < max_iter) {
+            k_spmv<float, float><<<gw, 256, 0, st>>>(pc.row_ptr.p, pc.col.p, W.val32.p, W.p.p, W.q.p, nullptr, N);
+            dot(W.p.p, W.q.p, N, W.part.p, W.sc.p + 1, st);
+            k_cg_update<<<ge, 256, 0, st>>>(W.d.p, W.r.p, W.p.p, W.q.p, W.sc.p, N);
+            project_out(W, W.r.p, st);
+            dot(W.r.p, W.r.p, N, W.part.p, W.sc.p + 2, st);
+            k_cg_dir<<<ge, 256, 0, st>>>(W.p.p, W.r.p, W.sc.p, N);
+            k_roll<<<1, 1, 0, st>>>(W.sc.p);
+            NLFEM_LAUNCH_CHECK();
+            ++it;
+            ++iters;
+            if (it % CHECK_EVERY == 0) {
+                double rho = 0;
+                NLFEM_CUDA_TRY(cudaMemcpyAsync(&rho, W.sc.p, sizeof rho, cudaMemcpyDeviceToHost, st));
+                NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+                if (!(rho > inner_tol2) || it >= 2000) break;
+            }
+        }
+        // x += d, kept orthogonal to N; r64 = P (b - A x) in FP64
+        k_add_corr<<<ge, 256, 0, st>>>(W.x.p, W.d.p, N);
+        project_out(W, W.x.p, st);
+        k_spmv<double, double><<<gw, 256, 0, st>>>(pc.row_ptr.p, pc.col.p, S.val.p, W.x.p, W.y64.p, nullptr, N);
+        k_sub<<<ge, 256, 0, st>>>(W.b.p, W.y64.p, W.r64.p, N);
+        project_out(W, W.r64.p, st);
+        NLFEM_LAUNCH_CHECK();
+        dot(W.r64.p, W.r64.p, N, W.part.p, W.sc.p + 3, st);
+        double rr = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&rr, W.sc.p + 3, sizeof rr, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        rel = bnorm > 0 ? std::sqrt(rr) / bnorm : 0.0;
+        ++refs;
+        if (refs > 50) break;
+    }
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(u_out, W.x.p, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (info) {
+        info->iterations = iters;
+        info->refinements = refs;
+        info->rel_residual = rel;
+    }
+    if (rel > tol) {
+        set_error("projected CG did not reach the tolerance: relative residual " + std::to_string(rel));
+        return NLFEM_ERR_NOT_CONVERGED;
+    }
+    return NLFEM_OK;
+}
+
+int solve_system(System& S, const double* g, double tol, int max_iter, double* u_out, nlfem_solve_info* info,
+                 cudaStream_t st) {
+    int rc = ensure_solver(S, st);
+    if (rc) return rc;
+    const int64_t N = S.N;
+    PairCache& pc = *S.pc;
     SolveState& W = *S.solver;
     const unsigned gw = nblk(N * 32, 256), ge = nblk(N, 256);
     k_rhs<<<gw, 256, 0, st>>>(pc.row_ptr.p, pc.col.p, S.val.p, g, S.F.p, W.freem.p, W.b.p, N);
