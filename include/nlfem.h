@@ -136,7 +136,7 @@ void nlfem_params_default(nlfem_params* p, int kernel);
  * outer rule and close-pair class (see nlfem_assembly_info.cached).
  * Work is ordered on stream; the call returns after the result is complete on the
  * device. The system handle is owned by the library until nlfem_system_destroy.
- * Errors: INVALID_ARG, UNSUPPORTED (more than 8192 partners per element, or a row
+ * Errors: INVALID_ARG, UNSUPPORTED (more than 32768 partners per element, or a row
  * referring to more than 2^32 / 84 pairs), BUDGET, OOM, CUDA.
  */
 int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* f_nodal,

@@ -118,17 +118,20 @@ __global__ void k_segsort(int* keys, int* vals, const int64_t* ptr, int cap) {
 void segmented_sort_i32(int* keys, int* vals, const int64_t* ptr, int64_t nseg, int max_len,
                         cudaStream_t st) {
     if (nseg <= 0 || max_len <= 1) return;
-    NLFEM_CHECK(max_len <= 8192, NLFEM_ERR_UNSUPPORTED,
-                "segment of " + std::to_string(max_len) + " entries exceeds the sort capacity 8192");
+    // the whole segment sits in shared memory: 128 KB of keys (and values)
+    const int limit = vals ? 16384 : 32768;
+    NLFEM_CHECK(max_len <= limit, NLFEM_ERR_UNSUPPORTED,
+                "segment of " + std::to_string(max_len) + " entries exceeds the sort capacity " +
+                    std::to_string(limit));
     int cap = 1;
     while (cap < max_len) cap <<= 1;
     size_t smem = (size_t)cap * sizeof(int) * (vals ? 2 : 1);
     int threads = std::min(cap / 2 < 32 ? 32 : cap / 2, 512);
     if (vals) {
-        NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_segsort<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+        NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_segsort<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_segsort<true><<<(unsigned)nseg, threads, smem, st>>>(keys, vals, ptr, cap);
     } else {
-        NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_segsort<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+        NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_segsort<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_segsort<false><<<(unsigned)nseg, threads, smem, st>>>(keys, nullptr, ptr, cap);
     }
     NLFEM_LAUNCH_CHECK();

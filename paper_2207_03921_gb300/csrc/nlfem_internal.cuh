@@ -182,7 +182,7 @@ struct PairCache {
     DBuf<int> col;           // [nnz]
     DBuf<int64_t> tpos;      // [nnz] position of the transposed entry
     DBuf<int64_t> seg_ptr;   // [nnz + 1] contribution segments per CSR slot (upper slots only)
-    DBuf<uint32_t> idx;      // [ncontrib] packed (pair - pbase[row]) * NE + entry
+    DBuf<uint64_t> idx;      // [ncontrib] packed ((pair - pbase[row]) << 6) | transposed << 5 | entry
     DBuf<int64_t> pbase;     // [M] first pair id a node row refers to
     int64_t ncontrib = 0;
     DBuf<int64_t> up_pos;    // node-level upper entries (i, j >= i): pattern position

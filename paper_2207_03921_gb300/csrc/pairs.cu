@@ -63,6 +63,7 @@ struct SearchArgs {
     int64_t K;
     double delta, delta2;
     int caps;
+    int ball;
     Rule ro;
 };
 
@@ -72,6 +73,20 @@ __device__ bool interacts(const SearchArgs& a, int k, int l, int4 tk, const doub
     const double2 cl = a.cen[l];
     const double rl = a.rad[l];
     const double cdx = cl.x - ck.x, cdy = cl.y - ck.y;
+    if (a.ball == NLFEM_BALL_INFINITY) {
+        // infinity ball: centroid tests against the square's circumradius sqrt(2) delta and,
+        // for the whole element, its half side; then the canonical FP64 cut per outer point
+        const double dist = sqrt(cdx * cdx + cdy * cdy);
+        if (dist - rk - rl > a.delta * 1.4142135623730951 * (1.0 + 1e-9)) return false;
+        if (fmax(fabs(cdx), fabs(cdy)) + rk + rl <= a.delta * (1.0 - 1e-9)) return true;
+        const double2 Vl[3] = {a.X[tl.x], a.X[tl.y], a.X[tl.z]};
+        for (int p = 0; p < a.ro.n; ++p) {
+            const double2 xp = nl_map(Vk, a.ro.l[p][0], a.ro.l[p][1], a.ro.l[p][2]);
+            bool full;
+            if (nl_clip_square(Vl, xp, a.delta, nullptr, full) >= 3) return true;
+        }
+        return false;
+    }
     // centroid tests: decided in FP32 on squared distances when the margin (1e-5 relative,
     // far above the FP32 error of about 3e-7) allows, else by the FP64 expressions below
     const float d2f = (float)cdx * (float)cdx + (float)cdy * (float)cdy;
@@ -224,9 +239,10 @@ __global__ void k_flag_duffy(const int8_t* cls, int64_t P, int std_close, int64_
 // of the outer element: the largest vertex-to-vertex distance is below delta with a
 // relative margin of 1e-6 (far above FP64 rounding), so the canonical clip finds all three
 // vertices inside at every outer point. flag_whole / flag_cut select the two lists.
+// For the infinity ball the same test runs on the largest coordinate difference against delta.
 __global__ void k_flag_whole(const int* pk, const int* pl, const int8_t* cls, int64_t P, const double2* X,
                              const int4* T, const ElemRec* rec, double delta2, int std_close, int64_t* flag_whole,
-                             int64_t* flag_cut) {
+                             int64_t* flag_cut, int inf = 0, double delta = 0.0) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     int64_t w = 0, c = 0;
@@ -243,9 +259,9 @@ __global__ void k_flag_whole(const int* pk, const int* pl, const int8_t* cls, in
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) {
                 const float dx = lx[j] - kx[i], dy = ly[j] - ky[i];
-                mxf = fmaxf(mxf, dx * dx + dy * dy);
+                mxf = fmaxf(mxf, inf ? fmaxf(fabsf(dx), fabsf(dy)) : dx * dx + dy * dy);
             }
-        const float thr = (float)(delta2 * (1.0 - 1e-6));
+        const float thr = (float)((inf ? delta : delta2) * (1.0 - 1e-6));
         bool whole;
         if (mxf < thr * (1.f - 1e-4f)) whole = true;
         else if (mxf > thr * (1.f + 1e-4f)) whole = false;
@@ -256,9 +272,9 @@ __global__ void k_flag_whole(const int* pk, const int* pl, const int8_t* cls, in
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j) {
                     const double dx = vb[j].x - va[i].x, dy = vb[j].y - va[i].y;
-                    mx = fmax(mx, dx * dx + dy * dy);
+                    mx = fmax(mx, inf ? fmax(fabs(dx), fabs(dy)) : dx * dx + dy * dy);
                 }
-            whole = mx <= delta2 * (1.0 - 1e-6);
+            whole = mx <= (inf ? delta : delta2) * (1.0 - 1e-6);
         }
         if (whole) w = 1;
         else c = 1;
@@ -294,7 +310,9 @@ int64_t max_segment_i64(const int64_t* ptr, int64_t n, cudaStream_t st) {
 void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     const int64_t K = m.K;
     Grid g;
-    g.cs = (prm.delta + 2.0 * m.rmax) * (1.0 + 1e-9) + 1e-300;
+    // candidates lie within delta (sqrt(2) delta for the infinity ball) + 2 r_max of the centroid
+    const double reach = prm.ball == NLFEM_BALL_INFINITY ? prm.delta * 1.4142135623730951 : prm.delta;
+    g.cs = (reach + 2.0 * m.rmax) * (1.0 + 1e-9) + 1e-300;
     double W = m.bbox[2] - m.bbox[0], H = m.bbox[3] - m.bbox[1];
     g.nx = std::max(1, (int)std::ceil(W / g.cs));
     g.ny = std::max(1, (int)std::ceil(H / g.cs));
@@ -326,6 +344,7 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     a.X = m.X.p; a.T = m.T.p; a.cen = m.cen.p; a.rad = m.rad.p; a.cell_of = cell_of.p;
     a.cell_start = cstart.p; a.cell_list = clist.p; a.g = g; a.K = K;
     a.delta = prm.delta; a.delta2 = prm.delta2; a.caps = prm.ball == NLFEM_BALL_APPROXCAPS; a.ro = prm.ro;
+    a.ball = prm.ball;
     a.E32 = m.E32.p;
     for (int i = 0; i < 16; ++i) {
         a.ol[i][0] = i < prm.ro.n ? (float)prm.ro.l[i][1] : 0.f;
@@ -419,7 +438,8 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
         pw.alloc(P + 1, st);
         pcut.alloc(P + 1, st);
         k_flag_whole<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, pc.pcls.p, P, m.X.p, m.T.p, m.rec.p,
-                                                   prm.delta2, close_mode(prm) == 0, fw.p, fc.p);
+                                                   prm.delta2, close_mode(prm) == 0, fw.p, fc.p,
+                                                   prm.ball == NLFEM_BALL_INFINITY, prm.delta);
         NLFEM_LAUNCH_CHECK();
         exclusive_scan_i64(fw.p, pw.p, P, st);
         exclusive_scan_i64(fc.p, pcut.p, P, st);
@@ -640,8 +660,8 @@ extern "C" int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t
                         std::to_string(K) + " triangles, " + std::to_string(M) +
                         " vertices); use nlfem_mesh_create and nlfem_assemble for larger meshes");
         NLFEM_CHECK(delta > 0 && std::isfinite(delta), NLFEM_ERR_INVALID_ARG, "delta must be > 0");
-        NLFEM_CHECK(ball == NLFEM_BALL_NOCAPS || ball == NLFEM_BALL_APPROXCAPS, NLFEM_ERR_INVALID_ARG,
-                    "unknown ball approximation");
+        NLFEM_CHECK(ball == NLFEM_BALL_NOCAPS || ball == NLFEM_BALL_APPROXCAPS || ball == NLFEM_BALL_INFINITY,
+                    NLFEM_ERR_INVALID_ARG, "unknown ball");
         NLFEM_CHECK(quad_outer == 7 || quad_outer == 16, NLFEM_ERR_INVALID_ARG, "quad_outer must be 7 or 16");
         const void* devp[4] = {verts, elems, out_k, out_l};
         for (const void* q : devp) {
@@ -682,7 +702,8 @@ extern "C" int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t
 
         // grid over the element centroids, at most NOALLOC_MAX_CELLS cells
         Grid g;
-        g.cs = (delta + 2.0 * hs[0]) * (1.0 + 1e-9) + 1e-300;
+        const double reach = ball == NLFEM_BALL_INFINITY ? delta * 1.4142135623730951 : delta;
+        g.cs = (reach + 2.0 * hs[0]) * (1.0 + 1e-9) + 1e-300;
         const double W = hs[3] - hs[1], H = hs[4] - hs[2];
         g.nx = std::max(1, (int)std::ceil(W / g.cs));
         g.ny = std::max(1, (int)std::ceil(H / g.cs));
@@ -706,6 +727,7 @@ extern "C" int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t
         SearchArgs a;
         a.X = X; a.T = T; a.cen = cen; a.rad = rad; a.cell_of = cell_of; a.cell_start = cstart; a.cell_list = clist;
         a.g = g; a.K = K; a.delta = delta; a.delta2 = delta * delta; a.caps = ball == NLFEM_BALL_APPROXCAPS;
+        a.ball = ball;
         a.ro.n = quad_outer;
         const double(*tab)[4] = quad_outer == 7 ? NLFEM_RULE7 : NLFEM_RULE16;
         for (int i = 0; i < 16; ++i) {

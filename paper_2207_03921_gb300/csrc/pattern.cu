@@ -254,7 +254,7 @@ __global__ void k_expand_cols(const int64_t* nptr, const int* ncol, int64_t M, i
 // ------------------------------------------------------------------------------------------
 template <bool FILL>
 __global__ void k_slots(RowEnum R, int64_t M, const int64_t* nptr, const int* ncol, int maxrow,
-                        int64_t* seg_cnt, const int64_t* seg_ptr, uint32_t* idx, int64_t* pbase,
+                        int64_t* seg_cnt, const int64_t* seg_ptr, uint64_t* idx, int64_t* pbase,
                         int* overflow) {
     extern __shared__ int sm[];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -322,9 +322,9 @@ __global__ void k_slots(RowEnum R, int64_t M, const int64_t* nptr, const int* nc
                         tflag = 1;
                     }
                     int64_t rel = (int64_t)p - pb;
-                    if (rel < 0 || rel >= (1ll << 26)) bad = true;
+                    if (rel < 0) bad = true;
                     idx[seg_ptr[rb + key] + base + rank] =
-                        ((uint32_t)rel << 6) | (tflag << 5) | (uint32_t)c_E1[a][bb];
+                        ((uint64_t)rel << 6) | ((uint64_t)tflag << 5) | (uint64_t)c_E1[a][bb];
                 }
             }
             __syncwarp();
@@ -388,7 +388,7 @@ template <typename R, int NDOF>
 __global__ void __launch_bounds__(256) k_reduce(int64_t n_upper, const int64_t* __restrict__ up_pos,
                                                 const int* __restrict__ up_row, const int64_t* __restrict__ nptr,
                                                 const int* __restrict__ ncol, const int64_t* __restrict__ seg_ptr,
-                                                const uint32_t* __restrict__ idx, const int64_t* __restrict__ pbase,
+                                                const uint64_t* __restrict__ idx, const int64_t* __restrict__ pbase,
                                                 const R* __restrict__ contrib, const int64_t* __restrict__ row_ptr,
                                                 const int64_t* __restrict__ tpos, double* __restrict__ val) {
     constexpr int SUB = 16;
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(256) k_reduce(int64_t n_upper, const int64_t* 
         if constexpr (sizeof(R) == 4) acc[k] = CSum{0.f, 0.f};
         else acc[k] = 0.0;
     }
-    auto load = [&](uint32_t e, R (&x)[NCOMP]) {
+    auto load = [&](uint64_t e, R (&x)[NCOMP]) {
         const R* cp = contrib + (pb + (int64_t)(e >> 6)) * NS + (e & 31) * NCOMP;
         if constexpr (NDOF == 1) {
             x[0] = cp[0];
@@ -441,11 +441,11 @@ __global__ void __launch_bounds__(256) k_reduce(int64_t n_upper, const int64_t* 
         }
     };
     {
-        uint32_t e[UNR];
+        uint64_t e[UNR];
 #pragma unroll
         for (int r = 0; r < UNR; ++r) {
             const int64_t q = s0 + sl + (int64_t)SUB * r;
-            e[r] = q < s1 ? idx[q] : 0u;
+            e[r] = q < s1 ? idx[q] : 0ull;
         }
         R x[UNR][NCOMP];
 #pragma unroll
@@ -690,7 +690,7 @@ void build_slots(Mesh& m, PairCache& pc, cudaStream_t st) {
     NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, ovf.p, sizeof h, cudaMemcpyDeviceToHost, st));
     NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
     NLFEM_CHECK(!(h & 2), NLFEM_ERR_UNSUPPORTED,
-                "a CSR row refers to pairs more than 2^26 apart (or misses a column)");
+                "the slot index misses a column of a CSR row");
     // node-level upper entries, the work items of the reduction, in 2D tile order of the rows
     DBuf<int> order;
     order.alloc(M, st);

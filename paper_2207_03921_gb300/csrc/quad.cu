@@ -94,7 +94,6 @@ __global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contr
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
     constexpr int NS = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? NLFEM_REC2 : NLFEM_REC1;  // record stride
     const Params& P = A.prm;
-    const bool caps = P.ball == NLFEM_BALL_APPROXCAPS;
     for (int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pi < A.npairs;
          pi += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = A.ids ? (int64_t)A.ids[pi] : pi;
@@ -120,7 +119,7 @@ __global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contr
             const double2 xp = nl_map(Vk, P.ro.l[q0][0], P.ro.l[q0][1], P.ro.l[q0][2]);
             CPt poly[NLFEM_MAXPOLY];
             bool full;
-            const int np = nl_clip(Vl, xp, P.delta, P.delta2, caps, poly, full);
+            const int np = nl_clip_ball(P.ball, Vl, xp, P.delta, P.delta2, poly, full);
             if (np < 3) continue;
             // inner sums for this x_p: g = sum w, h_j = sum w Q_j, m_ij = sum w Q_i Q_j
             R g[NC], h[3][NC], mm[6][NC];
@@ -700,7 +699,7 @@ void bulk_redo(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStrea
 // [2, 3] fused whole-pair launches, [3, 4] fused cut-pair launches, [4, 5] element sums and
 // close-list adds.
 static int64_t class_key(const Params& p) {
-    return ((int64_t)p.kernel * 64 + p.ro.n) * 64 * 8 + (int64_t)p.ri.n * 8 + (p.ball == NLFEM_BALL_APPROXCAPS);
+    return ((int64_t)p.kernel * 64 + p.ro.n) * 64 * 8 + (int64_t)p.ri.n * 8 + p.ball;
 }
 
 void BatchExec::prepare(cudaStream_t st) {
@@ -840,7 +839,6 @@ __device__ __forceinline__ void warp_add(unsigned long long* c, unsigned long lo
 
 __global__ void k_census(QuadArgs A, unsigned long long* cnt) {
     const Params& P = A.prm;
-    const bool caps = P.ball == NLFEM_BALL_APPROXCAPS;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n_iter = (A.npairs + stride - 1) / stride;
     for (int64_t it = 0; it < n_iter; ++it) {
@@ -860,7 +858,7 @@ __global__ void k_census(QuadArgs A, unsigned long long* cnt) {
                 for (int q0 = 0; q0 < P.ro.n; ++q0) {
                     const double2 xp = nl_map(Vk, P.ro.l[q0][0], P.ro.l[q0][1], P.ro.l[q0][2]);
                     bool f;
-                    const int np = nl_clip(Vl, xp, P.delta, P.delta2, caps, nullptr, f);
+                    const int np = nl_clip_ball(P.ball, Vl, xp, P.delta, P.delta2, nullptr, f);
                     ++outer;
                     if (np < 3) { ++empty; continue; }
                     if (f) { ++full; evals += P.ri.n; }

@@ -53,7 +53,7 @@ struct FastReq {
     const ElemRec* rec;
     float delta, d2, c, s;
     double delta64, delta2_64;
-    int caps;
+    int ball;     // NLFEM_BALL_*
     // fixed-point accumulation into the upper CSR entries (see accumulate_pair)
     unsigned long long* acc;  // [n_upper][NC] int64 two's complement sums
     float* kkll;              // [2][P][6 NC] kk, then ll, of every pair, by pair id
@@ -370,6 +370,20 @@ __device__ __noinline__ int clip_canonical(const double2* __restrict__ X, int4 t
     return n;
 }
 
+// Infinity ball: the canonical FP64 cut of one outer point for every lane (no FP32 decision
+// path), written relative to x_p as FP32 points
+__device__ __noinline__ int clip_square_f32(const double2* __restrict__ X, int4 tk, int4 tl, double o0, double o1,
+                                            double o2, double delta, float2* dst) {
+    const double2 Vk[3] = {X[tk.x], X[tk.y], X[tk.z]};
+    const double2 Vl[3] = {X[tl.x], X[tl.y], X[tl.z]};
+    const double2 xp = nl_map(Vk, o0, o1, o2);
+    double2 rel[NLFEM_MAXSQ];
+    bool full;
+    const int n = nl_clip_square_rel(Vl, xp, delta, rel, full);
+    for (int m = 0; m < n && m < 7; ++m) dst[m * FAST_THREADS] = make_float2((float)rel[m].x, (float)rel[m].y);
+    return n < 7 ? n : 7;
+}
+
 // Cut pairs: the outer points are processed in chunks of CHUNK. Phase A sets up every
 // outer point of the chunk in lockstep across the warp (decisions, polygon points relative
 // to x_p into shared memory; 4 bits per outer point record the number of points). Phase B
@@ -380,11 +394,14 @@ __device__ __noinline__ int clip_canonical(const double2* __restrict__ X, int4 t
 // lanes of a warp drain about the same number of triangles.
 static constexpr int CHUNK = 8;
 
-template <int KER, int NQI, bool CAPS, bool BATCH>
+template <int KER, int NQI, int BALL, bool BATCH>
 __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_constant__ FastRule R,
                                                            const __grid_constant__ FastLaunch L) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
-    constexpr int MAXP = CAPS ? 9 : 6;  // polygon points: 6 raw, plus up to 3 cap centres
+    constexpr bool CAPS = BALL == NLFEM_BALL_APPROXCAPS;
+    constexpr bool SQUARE = BALL == NLFEM_BALL_INFINITY;
+    // polygon points: 6 raw plus up to 3 cap centres; a triangle cut by a square: at most 7
+    constexpr int MAXP = CAPS ? 9 : (SQUARE ? 7 : 6);
     extern __shared__ float2 s_pts[];   // [CHUNK][MAXP][FAST_THREADS]
     float2* my = s_pts + threadIdx.x;
     auto put = [&](int q, int slot, float x, float y) { my[(q * MAXP + slot) * FAST_THREADS] = make_float2(x, y); };
@@ -456,6 +473,13 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
 #pragma unroll 1
             for (int q = 0; q < qn; ++q) {
                 const int q0 = qb + q;
+                if (SQUARE) {
+                    const int n = valid ? clip_square_f32(Q.X, tk, tl, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2],
+                                                          Q.delta64, my + q * MAXP * FAST_THREADS)
+                                        : 0;
+                    counts |= (unsigned long long)(n < 3 ? 0 : n) << (4 * q);
+                    continue;
+                }
                 const float l1o = R.ol[q0][1], l2o = R.ol[q0][2];
                 const float Xx = l1o * Ek.x + l2o * Ek.z;  // x_p - v0_k
                 const float Xy = l1o * Ek.y + l2o * Ek.w;
@@ -573,6 +597,17 @@ __global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key) {
     const float Wx[3] = {dx, dx + El.x, dx + El.z}, Wy[3] = {dy, dy + El.y, dy + El.w};
     const int nqo = R.nqo;
     int tris = 0;
+    if (Q.ball == NLFEM_BALL_INFINITY) {  // the canonical cut (the cut kernel uses it too)
+        const double2 Vk[3] = {v0k, Q.X[tk.y], Q.X[tk.z]}, Vl[3] = {v0l, Q.X[tl.y], Q.X[tl.z]};
+        for (int q0 = 0; q0 < nqo; ++q0) {
+            bool full;
+            const int n = nl_clip_square(Vl, nl_map(Vk, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2]), Q.delta64, nullptr,
+                                         full);
+            tris += n >= 3 ? n - 2 : 0;
+        }
+        key[pi] = tris;
+        return;
+    }
     for (int q0 = 0; q0 < nqo; ++q0) {
         const float Xx = R.ol[q0][1] * Ek.x + R.ol[q0][2] * Ek.z;
         const float Xy = R.ol[q0][1] * Ek.y + R.ol[q0][2] * Ek.w;
@@ -586,7 +621,7 @@ __global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key) {
         decide_flat(Rx, Ry, Cc, edges_of(El), 0.f, 0.f, Q.d2, G);
         int n = 0;
         for (int e = 0; e < 3; ++e) n += (int)G.in[e] + G.nc[e];
-        if (Q.caps && n >= 2 && !(G.in[0] && G.in[1] && G.in[2])) n += 1;  // at least one cap
+        if (Q.ball == NLFEM_BALL_APPROXCAPS && n >= 2 && !(G.in[0] && G.in[1] && G.in[2])) n += 1;  // a cap
         tris += n >= 3 ? n - 2 : 0;
     }
     key[pi] = tris;
@@ -709,7 +744,7 @@ FastReq make_req(Mesh& m, PairCache& pc, const Params& prm, int list) {
     q.s = (float)prm.s;
     q.delta64 = prm.delta;
     q.delta2_64 = prm.delta2;
-    q.caps = prm.ball == NLFEM_BALL_APPROXCAPS;
+    q.ball = prm.ball;
     q.npairs_all = pc.npairs;
     q.up_start = pc.up_start.p;
     q.epos = pc.epos.p;
@@ -742,27 +777,31 @@ void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st)
     segmented_sort_i32(key.p, pc.cut_ids.p, ptr.p, nwin, (int)std::min<int64_t>(n, W), st);
 }
 
-template <int KER, int NQI, bool CAPS, bool BATCH>
-static void launch_cut(const FastRule& r, const FastLaunch& L, unsigned grid, cudaStream_t st) {
-    constexpr int MAXP = CAPS ? 9 : 6;
-    const size_t smem = sizeof(float2) * CHUNK * MAXP * FAST_THREADS;
-    k_trunc_cut<KER, NQI, CAPS, BATCH><<<grid, FAST_THREADS, smem, st>>>(r, L);
+template <int BALL>
+static constexpr size_t cut_smem() {
+    return sizeof(float2) * CHUNK * FAST_THREADS *
+           (BALL == NLFEM_BALL_APPROXCAPS ? 9 : (BALL == NLFEM_BALL_INFINITY ? 7 : 6));
 }
 
-template <int KER, int NQI, bool CAPS, bool BATCH>
+template <int KER, int NQI, int BALL, bool BATCH>
+static void launch_cut(const FastRule& r, const FastLaunch& L, unsigned grid, cudaStream_t st) {
+    k_trunc_cut<KER, NQI, BALL, BATCH><<<grid, FAST_THREADS, cut_smem<BALL>(), st>>>(r, L);
+}
+
+template <int KER, int NQI, int BALL, bool BATCH>
 static void cut_attr() {
-    constexpr int MAXP = CAPS ? 9 : 6;
-    const size_t smem = sizeof(float2) * CHUNK * MAXP * FAST_THREADS;
-    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_cut<KER, NQI, CAPS, BATCH>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_trunc_cut<KER, NQI, BALL, BATCH>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cut_smem<BALL>()));
 }
 
 template <int KER, int NQI>
 static void cut_attrs() {
-    cut_attr<KER, NQI, false, false>();
-    cut_attr<KER, NQI, true, false>();
-    cut_attr<KER, NQI, false, true>();
-    cut_attr<KER, NQI, true, true>();
+    cut_attr<KER, NQI, NLFEM_BALL_NOCAPS, false>();
+    cut_attr<KER, NQI, NLFEM_BALL_APPROXCAPS, false>();
+    cut_attr<KER, NQI, NLFEM_BALL_INFINITY, false>();
+    cut_attr<KER, NQI, NLFEM_BALL_NOCAPS, true>();
+    cut_attr<KER, NQI, NLFEM_BALL_APPROXCAPS, true>();
+    cut_attr<KER, NQI, NLFEM_BALL_INFINITY, true>();
 }
 
 // cudaFuncSetAttribute is not a stream operation: done once per device, outside any capture
@@ -783,26 +822,27 @@ void set_fast_attributes() {
 }
 
 template <int KER, int NQI, bool BATCH>
-static void launch_class(int list, bool caps, const FastRule& r, const FastLaunch& L, unsigned grid,
+static void launch_class(int list, int ball, const FastRule& r, const FastLaunch& L, unsigned grid,
                          cudaStream_t st) {
     if (list == 0) k_trunc_whole<KER, NQI, BATCH><<<grid, FAST_THREADS, 0, st>>>(r, L);
-    else if (caps) launch_cut<KER, NQI, true, BATCH>(r, L, grid, st);
-    else launch_cut<KER, NQI, false, BATCH>(r, L, grid, st);
+    else if (ball == NLFEM_BALL_APPROXCAPS) launch_cut<KER, NQI, NLFEM_BALL_APPROXCAPS, BATCH>(r, L, grid, st);
+    else if (ball == NLFEM_BALL_INFINITY) launch_cut<KER, NQI, NLFEM_BALL_INFINITY, BATCH>(r, L, grid, st);
+    else launch_cut<KER, NQI, NLFEM_BALL_NOCAPS, BATCH>(r, L, grid, st);
 }
 
 template <bool BATCH>
 static void launch_kernel(const Params& prm, int list, const FastRule& r, const FastLaunch& L, unsigned grid,
                           cudaStream_t st) {
-    const bool caps = prm.ball == NLFEM_BALL_APPROXCAPS;
+    const int ball = prm.ball;
     if (prm.kernel == NLFEM_KERNEL_CONSTANT) {
-        if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_CONSTANT, 7, BATCH>(list, caps, r, L, grid, st);
-        else launch_class<NLFEM_KERNEL_CONSTANT, 16, BATCH>(list, caps, r, L, grid, st);
+        if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_CONSTANT, 7, BATCH>(list, ball, r, L, grid, st);
+        else launch_class<NLFEM_KERNEL_CONSTANT, 16, BATCH>(list, ball, r, L, grid, st);
     } else if (prm.kernel == NLFEM_KERNEL_FRACTIONAL) {
-        if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_FRACTIONAL, 7, BATCH>(list, caps, r, L, grid, st);
-        else launch_class<NLFEM_KERNEL_FRACTIONAL, 16, BATCH>(list, caps, r, L, grid, st);
+        if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_FRACTIONAL, 7, BATCH>(list, ball, r, L, grid, st);
+        else launch_class<NLFEM_KERNEL_FRACTIONAL, 16, BATCH>(list, ball, r, L, grid, st);
     } else {
-        if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_PERIDYNAMIC, 7, BATCH>(list, caps, r, L, grid, st);
-        else launch_class<NLFEM_KERNEL_PERIDYNAMIC, 16, BATCH>(list, caps, r, L, grid, st);
+        if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_PERIDYNAMIC, 7, BATCH>(list, ball, r, L, grid, st);
+        else launch_class<NLFEM_KERNEL_PERIDYNAMIC, 16, BATCH>(list, ball, r, L, grid, st);
     }
     NLFEM_LAUNCH_CHECK();
 }
@@ -824,8 +864,7 @@ static std::mutex g_tune_mu;
 static std::vector<std::pair<int64_t, int>> g_tune;  // (kernel class and list, blocks per SM)
 
 int64_t fast_tune_key(const Params& prm, int list) {
-    return ((((int64_t)prm.kernel * 64 + prm.ro.n) * 64 + prm.ri.n) * 2 + (prm.ball == NLFEM_BALL_APPROXCAPS)) * 2 +
-           list;
+    return ((((int64_t)prm.kernel * 64 + prm.ro.n) * 64 + prm.ri.n) * 4 + prm.ball) * 2 + list;
 }
 
 int fast_blocks_per_sm(int64_t key) {
