@@ -406,6 +406,10 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
     float2* my = s_pts + threadIdx.x;
     auto put = [&](int q, int slot, float x, float y) { my[(q * MAXP + slot) * FAST_THREADS] = make_float2(x, y); };
     __shared__ FastReq sq[BATCH ? FAST_WARPS : 1];
+    // infinity ball: per-thread element triples and per-warp job lists of the canonical cuts
+    __shared__ int4 s_tk[SQUARE ? FAST_THREADS : 1], s_tl[SQUARE ? FAST_THREADS : 1];
+    __shared__ unsigned char s_job[SQUARE ? FAST_WARPS * 32 * CHUNK : 1];
+    __shared__ unsigned char s_cnt[SQUARE ? FAST_THREADS * CHUNK : 1];
     const int nqo = R.nqo;
     const bool pilot = L.pilot > 0;
     const int warp = threadIdx.x >> 5;
@@ -470,14 +474,39 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
             const int qn = min(CHUNK, nqo - qb);
             // ---- phase A: polygons of outer points qb .. qb + qn - 1, in lockstep
             unsigned long long counts = 0;  // 4 bits per outer point: number of polygon points
+            unsigned need = 0;              // infinity ball: outer points left to the canonical cut
 #pragma unroll 1
             for (int q = 0; q < qn; ++q) {
                 const int q0 = qb + q;
                 if (SQUARE) {
-                    const int n = valid ? clip_square_f32(Q.X, tk, tl, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2],
-                                                          Q.delta64, my + q * MAXP * FAST_THREADS)
-                                        : 0;
-                    counts |= (unsigned long long)(n < 3 ? 0 : n) << (4 * q);
+                    // FP32 vertex tests with a margin decide the whole element (every vertex inside
+                    // the square) and the empty cut (every vertex beyond one side); the rest takes
+                    // the canonical FP64 cut
+                    int n = 0;
+                    if (valid) {
+                        const float Xx = R.ol[q0][1] * Ek.x + R.ol[q0][2] * Ek.z;
+                        const float Xy = R.ol[q0][1] * Ek.y + R.ol[q0][2] * Ek.w;
+                        const float Rx[3] = {W0x - Xx, W1x - Xx, W2x - Xx}, Ry[3] = {W0y - Xy, W1y - Xy, W2y - Xy};
+                        const float lo = Q.delta - eps - 1e-6f * Q.delta, hi = Q.delta + eps + 1e-6f * Q.delta;
+                        bool allin = true;
+                        int oxp = 0, oxm = 0, oyp = 0, oym = 0;
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) {
+                            allin &= fabsf(Rx[m]) < lo && fabsf(Ry[m]) < lo;
+                            oxp += Rx[m] > hi;
+                            oxm += Rx[m] < -hi;
+                            oyp += Ry[m] > hi;
+                            oym += Ry[m] < -hi;
+                        }
+                        if (allin) {
+#pragma unroll
+                            for (int m = 0; m < 3; ++m) put(q, m, Rx[m], Ry[m]);
+                            n = 3;
+                        } else if (oxp < 3 && oxm < 3 && oyp < 3 && oym < 3) {
+                            need |= 1u << q;
+                        }
+                    }
+                    counts |= (unsigned long long)n << (4 * q);
                     continue;
                 }
                 const float l1o = R.ol[q0][1], l2o = R.ol[q0][2];
@@ -537,6 +566,39 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                     n = clip_canonical(Q.X, tk, tl, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2], Q.delta64, Q.delta2_64,
                                        CAPS, my + q * MAXP * FAST_THREADS, MAXP);
                 counts |= (unsigned long long)(n < 3 ? 0 : n) << (4 * q);
+            }
+            if (SQUARE) {
+                // the canonical cuts of the chunk spread over the warp's lanes: job j of the warp
+                // is (owner lane, outer point); its polygon goes to the owner's slots
+                const int lane = threadIdx.x & 31, wbase = warp * 32;
+                s_tk[threadIdx.x] = tk;
+                s_tl[threadIdx.x] = tl;
+                const int mine = __popc(need);
+                int incl = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                int j = incl - mine;
+                for (unsigned b = need; b; b &= b - 1) s_job[wbase * CHUNK + j++] =
+                    (unsigned char)((lane << 3) | (__ffs(b) - 1));
+                __syncwarp();
+                for (int jj = lane; jj < total; jj += 32) {
+                    const int code = s_job[wbase * CHUNK + jj];
+                    const int owner = code >> 3, q = code & 7, q0 = qb + q;
+                    const int n = clip_square_f32(Q.X, s_tk[wbase + owner], s_tl[wbase + owner], R.ro[q0][0],
+                                                  R.ro[q0][1], R.ro[q0][2], Q.delta64,
+                                                  s_pts + wbase + owner + q * MAXP * FAST_THREADS);
+                    s_cnt[(wbase + owner) * CHUNK + q] = (unsigned char)(n < 3 ? 0 : n);
+                }
+                __syncwarp();
+                for (unsigned b = need; b; b &= b - 1) {
+                    const int q = __ffs(b) - 1;
+                    counts |= (unsigned long long)s_cnt[threadIdx.x * CHUNK + q] << (4 * q);
+                }
+                __syncwarp();
             }
             // ---- phase B: one fan triangle per lane and iteration
             int qc = 0, sc = 2;
