@@ -825,7 +825,8 @@ orc_sys *orc_assemble(int M, const double *X, int K, const int *T, const signed 
                       int nqo, const double *qo, int nqi, const double *qi, int close_rule,
                       int ng, const double *gx, const double *gw, int ndof,
                       const double *f_nodal, int mode, int nthreads,
-                      int n_subset, const int *elem_subset)
+                      int n_subset, const int *elem_subset,
+                      const signed char *mat, int nmat, const double *mscale)
 {
     mesh_t m;
     build_mesh(&m, M, X, K, T, lab);
@@ -927,12 +928,16 @@ orc_sys *orc_assemble(int M, const double *X, int K, const int *T, const signed 
         for (long long pq = p0; pq < p1; ++pq) {
             block_t *B = &blocks[pq - p0];
             int n = B->U * ndof;
+            /* label-dependent kernel (Sec. 1): Psi on E_k x E_l scaled by s[mat_k][mat_l] */
+            double fm = 1.0;
+            if (mat && mscale) fm = mscale[mat[S->pairs[2 * pq]] * nmat + mat[S->pairs[2 * pq + 1]]];
             for (int u = 0; u < n; ++u) {
                 int gi = B->node[u / ndof] * ndof + u % ndof;
                 for (int v = u; v < n; ++v) {
                     int gj = B->node[v / ndof] * ndof + v % ndof;
                     /* (i,j) and (j,i) receive the same value at the same moment */
                     double x = v == u ? B->blk[u * n + v] : 0.5 * (B->blk[u * n + v] + B->blk[v * n + u]);
+                    x *= fm;
                     if (v == u) { S->val[find_slot(S, gi, gi)] += x; }
                     else { S->val[find_slot(S, gi, gj)] += x; S->val[find_slot(S, gj, gi)] += x; }
                 }

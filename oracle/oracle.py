@@ -67,7 +67,7 @@ def _load():
             lib.orc_assemble.restype = C.c_void_p
             lib.orc_assemble.argtypes = [C.c_int, dp, C.c_int, ip, cp, C.c_int, C.c_double, C.c_double,
                                          C.c_double, C.c_int, C.c_int, dp, C.c_int, dp, C.c_int, C.c_int,
-                                         dp, dp, C.c_int, dp, C.c_int, C.c_int, C.c_int, ip]
+                                         dp, dp, C.c_int, dp, C.c_int, C.c_int, C.c_int, ip, cp, C.c_int, dp]
             lib.orc_sys_sizes.argtypes = [C.c_void_p, lp]
             lib.orc_sys_copy.argtypes = [C.c_void_p, lp, ip, dp, dp, ip, cp, cp, lp]
             lib.orc_sys_free.argtypes = [C.c_void_p]
@@ -129,7 +129,10 @@ def _kernel_args(kernel, delta, s, kconst, ball, quad_outer, quad_inner, close_r
 def assemble(mesh, kernel: str = "constant", delta: float = 0.1, s: float = -1.0, kconst=None,
              ball: str = "nocaps", quad_outer: int = 7, quad_inner: int = 7, close_rule: str = "auto",
              duffy_n: int = 5, f_nodal=None, pairs_mode: str = "bfs", threads: int = 0,
-             elem_subset=None) -> OracleSystem:
+             elem_subset=None, materials=None, material_scale=None) -> OracleSystem:
+    """FP64 assembly of A_h^# and F. materials [K] (0..n-1) with the symmetric n x n table
+    material_scale make the kernel label dependent: Psi on E_k x E_l times
+    material_scale[materials[k], materials[l]] (Sec. 1, interface problems)."""
     lib = _load()
     ndof = 2 if kernel == "peridynamic" else 1
     (kid, delta, s, kc, bid, qo, qi, cid, gx, gw) = _kernel_args(
@@ -140,6 +143,13 @@ def assemble(mesh, kernel: str = "constant", delta: float = 0.1, s: float = -1.0
     f = None
     if f_nodal is not None:
         f = np.ascontiguousarray(np.asarray(f_nodal, dtype=np.float64).reshape(mesh.M * ndof))
+    mat = msc = None
+    nmat = 0
+    if materials is not None:
+        mat = np.ascontiguousarray(materials, dtype=np.int8)
+        msc = np.ascontiguousarray(material_scale, dtype=np.float64)
+        nmat = int(msc.shape[0])
+        assert msc.shape == (nmat, nmat) and mat.shape == (mesh.K,) and 0 <= mat.min() and mat.max() < nmat
     sub = None
     nsub = 0
     if elem_subset is not None:
@@ -150,7 +160,9 @@ def assemble(mesh, kernel: str = "constant", delta: float = 0.1, s: float = -1.0
                          _p(gx, C.c_double), _p(gw, C.c_double), ndof,
                          _p(f, C.c_double) if f is not None else None,
                          0 if pairs_mode == "bfs" else 1, int(threads), nsub,
-                         _p(sub, C.c_int) if sub is not None else None)
+                         _p(sub, C.c_int) if sub is not None else None,
+                         _p(mat, C.c_byte) if mat is not None else None, nmat,
+                         _p(msc, C.c_double) if msc is not None else None)
     sz = np.zeros(3, dtype=np.int64)
     lib.orc_sys_sizes(h, _p(sz, C.c_longlong))
     N, nnz, npairs = (int(v) for v in sz)
