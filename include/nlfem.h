@@ -72,6 +72,12 @@ typedef struct {
     int close_rule;          /* NLFEM_CLOSE_* */
     int precision;           /* NLFEM_PREC_* */
     int64_t mem_budget_bytes;/* 0 = unlimited; else the assembly fails with NLFEM_ERR_BUDGET beyond it */
+    /* label-dependent kernel (Sec. 1, interface problems): with n_materials > 0 the kernel on
+     * E_k x E_l is multiplied by material_scale[m_k * n_materials + m_l], m the material labels
+     * of nlfem_mesh_set_materials. The table (host memory, n_materials^2 doubles, read during
+     * the call) must be symmetric so that A stays symmetric. 0 / NULL = no labels. */
+    int n_materials;         /* 0..16 */
+    const double* material_scale;
 } nlfem_params;
 
 typedef struct {
@@ -98,6 +104,15 @@ typedef struct {
     int refinements;         /* FP64 residual refinement steps */
     double rel_residual;     /* ||b - A_FF u_F|| / ||b|| in FP64 at exit */
 } nlfem_solve_info;
+
+/*
+ * Material labels of the elements for label-dependent kernels (Sec. 1: the kernel may depend
+ * on element labels, which assembles interface problems monolithically). material [K] int8
+ * in 0..15, host or device, copied; NULL removes the labels. Independent of the Omega /
+ * Omega_D labels of nlfem_mesh_create; the pair list and pattern do not depend on them.
+ * Errors: INVALID_ARG (a label outside 0..15), CUDA, OOM.
+ */
+int nlfem_mesh_set_materials(nlfem_mesh_t mesh, const int8_t* material, void* stream);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* nlfem_last_error(void);

@@ -62,6 +62,12 @@ class Mesh:
     def device_bytes(self) -> int:
         return B.nlfem_mesh_device_bytes(self.handle)
 
+    def set_materials(self, material, stream=None) -> None:
+        """Material labels [K] (0..15) of a label-dependent kernel (nlfem_mesh_set_materials)."""
+        torch = _torch()
+        self.material = None if material is None else _as_dev(material, torch.int8)
+        B.nlfem_mesh_set_materials(self.handle, self.material, stream)
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h:
@@ -134,11 +140,12 @@ class System:
 
 def assemble(mesh: Mesh, kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7,
              quad_inner=7, duffy_gauss=5, close_rule="auto", precision="fp64", f_nodal=None,
-             mem_budget_bytes=0, stream=None) -> System:
-    """Assemble A_h^# and F on the GPU (nlfem_assemble)."""
+             mem_budget_bytes=0, stream=None, material_scale=None) -> System:
+    """Assemble A_h^# and F on the GPU (nlfem_assemble). material_scale: symmetric table of a
+    label-dependent kernel over the labels of Mesh.set_materials."""
     torch = _torch()
     p = B.make_params(kernel, delta, s, kconst, ball, quad_outer, quad_inner, duffy_gauss, close_rule,
-                      precision, mem_budget_bytes)
+                      precision, mem_budget_bytes, material_scale)
     f = None if f_nodal is None else _as_dev(f_nodal, torch.float64).reshape(-1)
     h = B.nlfem_assemble(mesh.handle, p, f, stream)
     return System(mesh, h)
@@ -164,11 +171,11 @@ def _params_list(params):
     ps = []
     for p in params:
         q = dict(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7, quad_inner=7,
-                 duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0)
+                 duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0, material_scale=None)
         q.update(p)
         ps.append(B.make_params(q["kernel"], q["delta"], q["s"], q["kconst"], q["ball"], q["quad_outer"],
                                 q["quad_inner"], q["duffy_gauss"], q["close_rule"], q["precision"],
-                                q["mem_budget_bytes"]))
+                                q["mem_budget_bytes"], q["material_scale"]))
     return ps
 
 

@@ -37,7 +37,8 @@ class NlfemError(RuntimeError):
 class nlfem_params(C.Structure):
     _fields_ = [("kernel", C.c_int), ("delta", C.c_double), ("s", C.c_double), ("kconst", C.c_double),
                 ("ball", C.c_int), ("quad_outer", C.c_int), ("quad_inner", C.c_int), ("duffy_gauss", C.c_int),
-                ("close_rule", C.c_int), ("precision", C.c_int), ("mem_budget_bytes", C.c_int64)]
+                ("close_rule", C.c_int), ("precision", C.c_int), ("mem_budget_bytes", C.c_int64),
+                ("n_materials", C.c_int), ("material_scale", C.c_void_p)]
 
 
 class nlfem_assembly_info(C.Structure):
@@ -89,6 +90,7 @@ def load(build_if_missing: bool = True):
         lib.nlfem_mesh_pairs.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
         lib.nlfem_solve.argtypes = [vp, vp, dp, ip, vp, C.POINTER(nlfem_solve_info), vp]
         lib.nlfem_solve_neumann.argtypes = [vp, dp, ip, vp, C.POINTER(nlfem_solve_info), vp]
+        lib.nlfem_mesh_set_materials.argtypes = [vp, vp, vp]
         lib.nlfem_system_census.argtypes = [vp, C.POINTER(C.c_int64), vp]
         lib.nlfem_system_destroy.argtypes = [vp]
         lib.nlfem_system_destroy.restype = None
@@ -305,6 +307,10 @@ def nlfem_pairs_noalloc(verts, elems, delta, ball, quad_outer, out_k, out_l, str
     return n.value
 
 
+def nlfem_mesh_set_materials(mesh, material, stream=None) -> None:
+    _check(load().nlfem_mesh_set_materials(mesh, _ptr(material), _stream(stream)))
+
+
 def nlfem_last_error() -> str:
     return load().nlfem_last_error().decode()
 
@@ -314,7 +320,10 @@ def nlfem_version() -> str:
 
 
 def make_params(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7, quad_inner=7,
-                duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0) -> nlfem_params:
+                duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0,
+                material_scale=None) -> nlfem_params:
+    """nlfem_params; material_scale: symmetric n x n table of a label-dependent kernel (the
+    returned struct keeps the array alive for the calls it is passed to)."""
     p = nlfem_params()
     p.kernel = KERNELS[kernel]
     p.delta = float(delta)
@@ -327,4 +336,13 @@ def make_params(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps",
     p.close_rule = CLOSE_RULES[close_rule]
     p.precision = PRECISIONS[precision]
     p.mem_budget_bytes = int(mem_budget_bytes)
+    p.n_materials = 0
+    p.material_scale = None
+    if material_scale is not None:
+        import numpy as np
+        tab = np.ascontiguousarray(material_scale, dtype=np.float64)
+        assert tab.ndim == 2 and tab.shape[0] == tab.shape[1]
+        p._keep = tab
+        p.n_materials = int(tab.shape[0])
+        p.material_scale = tab.ctypes.data
     return p

@@ -92,6 +92,14 @@ static Params make_params(const nlfem_params& p, int ndof) {
     NLFEM_CHECK(p.close_rule >= 0 && p.close_rule <= 3, NLFEM_ERR_INVALID_ARG, "unknown close-pair rule");
     NLFEM_CHECK(p.precision == NLFEM_PREC_FP64 || p.precision == NLFEM_PREC_FP32_BULK, NLFEM_ERR_INVALID_ARG,
                 "unknown precision");
+    NLFEM_CHECK(p.n_materials >= 0 && p.n_materials <= 16 && (p.n_materials == 0 || p.material_scale),
+                NLFEM_ERR_INVALID_ARG, "n_materials must be 0..16 with a material_scale table");
+    for (int a = 0; a < p.n_materials; ++a)
+        for (int b = 0; b < p.n_materials; ++b) {
+            const double x = p.material_scale[a * p.n_materials + b];
+            NLFEM_CHECK(std::isfinite(x) && x == p.material_scale[b * p.n_materials + a], NLFEM_ERR_INVALID_ARG,
+                        "material_scale must be finite and symmetric");
+        }
     NLFEM_CHECK(p.duffy_gauss >= 1 && p.duffy_gauss <= 32, NLFEM_ERR_INVALID_ARG,
                 "duffy_gauss must be in 1..32");
     int need = p.kernel == NLFEM_KERNEL_PERIDYNAMIC ? 2 : 1;
@@ -202,6 +210,8 @@ void nlfem_params_default(nlfem_params* p, int kernel) {
     p->close_rule = NLFEM_CLOSE_AUTO;
     p->precision = NLFEM_PREC_FP64;
     p->mem_budget_bytes = 0;
+    p->n_materials = 0;
+    p->material_scale = nullptr;
 }
 
 // The library allocates its working buffers from the device's default memory pool
@@ -277,6 +287,33 @@ void nlfem_mesh_destroy(nlfem_mesh_t mesh) {
 
 int64_t nlfem_mesh_device_bytes(nlfem_mesh_t mesh) { return mesh ? mesh->m.device_bytes() : 0; }
 
+int nlfem_mesh_set_materials(nlfem_mesh_t mesh, const int8_t* material, void* stream) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(mesh != nullptr, NLFEM_ERR_INVALID_ARG, "NULL mesh");
+    Mesh& m = mesh->m;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!material) {
+        m.mat.release();
+        m.mat_max = -1;
+        return NLFEM_OK;
+    }
+    std::vector<int8_t> h((size_t)m.K);
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(h.data(), material, (size_t)m.K,
+                                   is_device_ptr(material) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    int mx = -1;
+    for (int8_t v : h) {
+        NLFEM_CHECK(v >= 0 && v < 16, NLFEM_ERR_INVALID_ARG, "material labels must be in 0..15");
+        mx = v > mx ? v : mx;
+    }
+    upload(m.mat, h.data(), (size_t)m.K, st);
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    m.mat_max = mx;
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
 int nlfem_mesh_pairs(nlfem_mesh_t mesh, const int32_t** k, const int32_t** l, int64_t* npairs) {
     NLFEM_API_BEGIN
     NLFEM_CHECK(mesh && k && l && npairs, NLFEM_ERR_INVALID_ARG, "NULL argument");
@@ -318,6 +355,26 @@ static std::shared_ptr<PairCache> ensure_cache(Mesh& m, const Params& P, cudaStr
     pc->t_pattern_ms = t_pattern;
     m.cache = pc;
     return pc;
+}
+
+// Label-dependent kernel: the scale table goes to the device with the system, and the
+// system's parameters point at it and at the mesh's material labels.
+static void attach_materials(System& S, const nlfem_params& p, const Mesh& m, cudaStream_t st) {
+    if (p.n_materials <= 0) return;
+    NLFEM_CHECK(m.mat.p && m.mat_max >= 0, NLFEM_ERR_INVALID_ARG,
+                "n_materials > 0 needs material labels (nlfem_mesh_set_materials)");
+    NLFEM_CHECK(m.mat_max < p.n_materials, NLFEM_ERR_INVALID_ARG,
+                "a material label is >= n_materials");
+    const int n2 = p.n_materials * p.n_materials;
+    std::vector<float> t32(n2);
+    for (int i = 0; i < n2; ++i) t32[i] = (float)p.material_scale[i];
+    upload(S.msc64, p.material_scale, (size_t)n2, st);
+    upload(S.msc32, t32.data(), (size_t)n2, st);
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));  // t32 is a host temporary
+    S.prm.nmat = p.n_materials;
+    S.prm.mat = m.mat.p;
+    S.prm.msc64 = S.msc64.p;
+    S.prm.msc32 = S.msc32.p;
 }
 
 // device bytes an assembly of (m, pc, P) needs beyond what the mesh handle holds
@@ -379,6 +436,8 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
         S.mesh = &m;
         S.pc = pc;
         S.prm = P;
+        attach_materials(S, *params, m, st);
+        P = S.prm;
         S.N = pc->N;
         S.nnz = pc->nnz;
         S.val.alloc(pc->nnz, st);
@@ -481,6 +540,8 @@ int nlfem_batch_assemble(const nlfem_mesh_t* meshes, const nlfem_params* params,
         S.mesh = &m;
         S.pc = pcs[i];
         S.prm = P[i];
+        attach_materials(S, params[i], m, st);
+        P[i] = S.prm;
         S.N = pcs[i]->N;
         S.nnz = pcs[i]->nnz;
         S.val.alloc(pcs[i]->nnz, st);
@@ -604,7 +665,7 @@ int nlfem_batch_create(const nlfem_mesh_t* meshes, const nlfem_params* params, c
     std::vector<char> cached(n);
     for (int i = 0; i < n; ++i) {
         Mesh& m = meshes[i]->m;
-        const Params P = make_params(params[i], m.ndof);
+        Params P = make_params(params[i], m.ndof);
         bool c = false;
         std::shared_ptr<PairCache> pc = ensure_cache(m, P, st, ev, tp[i], tq[i], c);
         cached[i] = c;
@@ -617,6 +678,8 @@ int nlfem_batch_create(const nlfem_mesh_t* meshes, const nlfem_params* params, c
         S.mesh = &m;
         S.pc = pc;
         S.prm = P;
+        attach_materials(S, params[i], m, st);
+        P = S.prm;
         S.N = pc->N;
         S.nnz = pc->nnz;
         S.val.alloc(pc->nnz, st);

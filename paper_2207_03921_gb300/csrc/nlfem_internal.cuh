@@ -128,6 +128,8 @@ struct Mesh {
     DBuf<float> det32;    // |det J_k| in FP32 [K]
     DBuf<ElemRec> rec;    // packed element records [K]
     DBuf<double> rad;     // radii [K]
+    DBuf<int8_t> mat;     // material labels of a label-dependent kernel [K] (empty: none)
+    int mat_max = -1;     // largest material label
     std::shared_ptr<PairCache> cache;  // pair list, pattern and slot index of the last (delta, ball, rule)
     int64_t device_bytes() const;
 };
@@ -153,7 +155,17 @@ struct Params {
     DuffyRule dr;
     bool singular;    // Tab. 1 club rule on intersecting pairs
     bool nozerodiv;   // Tab. 1 diamond rule on intersecting pairs
+    // label-dependent kernel: factor msc[mat[k] * nmat + mat[l]] on pair (k, l); nmat = 0: none
+    int nmat;
+    const int8_t* mat;
+    const double* msc64;
+    const float* msc32;
 };
+
+// kernel factor of the ordered pair (k, l) for label-dependent kernels
+__device__ __forceinline__ double pair_factor64(const Params& P, int k, int l) {
+    return P.nmat ? P.msc64[P.mat[k] * P.nmat + P.mat[l]] : 1.0;
+}
 
 // Interaction graph, CSR pattern and reduction index of one (mesh, delta, ball, outer rule, ndof).
 struct PairCache {
@@ -234,6 +246,8 @@ struct System {
     DBuf<unsigned long long> acc;  // FP32 bulk: fixed-point upper entries [n_upper * NC]
     DBuf<float> kkll;        // FP32 bulk: kk and ll of every pair [P * 12 NC]
     DBuf<FixState> fix;      // FP32 bulk: the fixed-point scale
+    DBuf<double> msc64;      // label-dependent kernel: the scale table on the device
+    DBuf<float> msc32;
     nlfem_assembly_info info;
     std::shared_ptr<SolveState> solver;
 };

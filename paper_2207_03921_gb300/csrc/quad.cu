@@ -222,10 +222,12 @@ __global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contr
                 for (int j = 0; j < 6; ++j) acc.ll[j][c] += ap * mm[j][c];
             }
         }
-        // fold the four blocks into the union block and write its upper triangle
+        // fold the four blocks into the union block and write its upper triangle (times the
+        // pair's factor of a label-dependent kernel)
         int posl[3], u[6];
         union_pos(tk, tl, posl, u);
         R* out = contrib + (A.compact ? pi : p) * NS;
+        const R fm = (R)pair_factor64(P, k, l);
         R blk[6][6][NC];
 #pragma unroll
         for (int a = 0; a < 6; ++a)
@@ -249,14 +251,14 @@ __global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contr
 #pragma unroll
             for (int b = a; b < 6; ++b) {
                 if (NC == 1) {
-                    out[q_E1[a][b]] = blk[a][b][0];
+                    out[q_E1[a][b]] = fm * blk[a][b][0];
                 } else {
                     // components (c1, c2) of Gamma: xx, xy, yx, yy
                     R* o = out + q_E1[a][b] * 4;
-                    o[0] = blk[a][b][0];
-                    o[1] = blk[a][b][1 % NC];
-                    o[2] = blk[a][b][1 % NC];
-                    o[3] = blk[a][b][2 % NC];
+                    o[0] = fm * blk[a][b][0];
+                    o[1] = fm * blk[a][b][1 % NC];
+                    o[2] = fm * blk[a][b][1 % NC];
+                    o[3] = fm * blk[a][b][2 % NC];
                 }
             }
     }
@@ -449,10 +451,11 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
                 ++e;
             }
         const int64_t r = A.compact ? wi : (int64_t)p;
+        const double fm = pair_factor64(P, k, l);
         for (int a = 0; a < 6; ++a)
             for (int b = a; b < 6; ++b) {
-                if (contrib64) contrib64[r * NLFEM_REC1 + q_E1[a][b]] = blk[a][b];
-                else contrib32[r * NLFEM_REC1 + q_E1[a][b]] = (float)blk[a][b];
+                if (contrib64) contrib64[r * NLFEM_REC1 + q_E1[a][b]] = fm * blk[a][b];
+                else contrib32[r * NLFEM_REC1 + q_E1[a][b]] = (float)(fm * blk[a][b]);
             }
     }
 }

@@ -54,6 +54,9 @@ struct FastReq {
     float delta, d2, c, s;
     double delta64, delta2_64;
     int ball;     // NLFEM_BALL_*
+    int nmat;     // label-dependent kernel: factor msc[mat[k] * nmat + mat[l]] (0: none)
+    const int8_t* mat;
+    const float* msc;
     // fixed-point accumulation into the upper CSR entries (see accumulate_pair)
     unsigned long long* acc;  // [n_upper][NC] int64 two's complement sums
     float* kkll;              // [2][P][6 NC] kk, then ll, of every pair, by pair id
@@ -196,9 +199,22 @@ __device__ __forceinline__ long long to_fixed(float sc, float v, float& vmax) {
 template <int NC>
 __device__ __forceinline__ void accumulate_pair(const FastReq& Q, bool pilot, float sc, int64_t pi, int64_t p, int4 tk,
                                                 int4 tl, const int* upos,
-                                                const float (&kk)[6][NC], const float (&kl)[9][NC],
-                                                const float (&ll)[6][NC], float& vmax) {
+                                                float (&kk)[6][NC], float (&kl)[9][NC],
+                                                float (&ll)[6][NC], float& vmax, int k, int l) {
     const int kn[3] = {tk.x, tk.y, tk.z}, ln[3] = {tl.x, tl.y, tl.z};
+    if (Q.nmat) {  // label-dependent kernel: the pair's factor
+        const float fm = Q.msc[Q.mat[k] * Q.nmat + Q.mat[l]];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+#pragma unroll
+            for (int e = 0; e < 6; ++e) {
+                kk[e][c] *= fm;
+                ll[e][c] *= fm;
+            }
+#pragma unroll
+            for (int e = 0; e < 9; ++e) kl[e][c] *= fm;
+        }
+    }
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -640,7 +656,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                 }
             }
         }
-        if (valid) accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, nullptr, kk, kl, ll, vmax);
+        if (valid) accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, nullptr, kk, kl, ll, vmax, k, l);
     }
     if (vdst) flush_max(vdst, vmax);
 }
@@ -770,7 +786,7 @@ __global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(const __grid_const
                                        dx + El.z - Xx, dy + El.w - Xy, 0.f, 1.f);
                 outer_update<NC>(R, q0, dk, I, kk, kl, ll);
             }
-            accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, upos, kk, kl, ll, vmax);
+            accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, upos, kk, kl, ll, vmax, k, l);
         }
     }
     if (vdst) flush_max(vdst, vmax);
@@ -807,6 +823,9 @@ FastReq make_req(Mesh& m, PairCache& pc, const Params& prm, int list) {
     q.delta64 = prm.delta;
     q.delta2_64 = prm.delta2;
     q.ball = prm.ball;
+    q.nmat = prm.nmat;
+    q.mat = prm.mat;
+    q.msc = prm.msc32;
     q.npairs_all = pc.npairs;
     q.up_start = pc.up_start.p;
     q.epos = pc.epos.p;

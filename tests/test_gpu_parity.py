@@ -285,3 +285,34 @@ def test_paper_E5_infinity_ball_on_gpu():
         assert 1.8 < r < 2.6, (rates, errs)
     for i, e in enumerate(errs):
         assert 0.5 * tab["l2"][i] < e < 2.0 * tab["l2"][i], (errs, tab["l2"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_label_dependent_kernel_matches_oracle(precision):
+    # four materials in the quadrants, a symmetric scale table (Sec. 1: kernels depending on
+    # element labels, interface problems)
+    m = meshes.jittered_delaunay(-0.2, 1.2, 16, 0.05, seed=23)
+    c = m.verts[m.elems].mean(1)
+    mat = ((c[:, 0] > 0.5).astype(np.int8) + 2 * (c[:, 1] > 0.5)).astype(np.int8)
+    tab = np.array([[1.0, 0.5, 0.3, 0.2], [0.5, 2.0, 0.4, 0.1], [0.3, 0.4, 3.0, 0.6], [0.2, 0.1, 0.6, 0.7]])
+    for kw in (dict(kernel="constant", delta=0.2, ball="approxcaps"),
+               dict(kernel="fractional", s=0.5, delta=0.2, ball="nocaps"),
+               dict(kernel="peridynamic", delta=0.2, ball="infinity")):
+        ndof = 2 if kw["kernel"] == "peridynamic" else 1
+        ref = oracle.assemble(m, materials=mat, material_scale=tab, **kw)
+        mesh = Mesh.from_synth(m, ndof)
+        mesh.set_materials(mat)
+        S = assemble(mesh, precision=precision, material_scale=tab, **kw)
+        if precision == "fp64":
+            rp, col, val = check_fp64(S, ref)
+        else:
+            rp, col, val = check_bulk(S, ref)
+        assert symmetric_bitwise(rp, col, val)
+    # the table must be symmetric, and labels must exist and fit the table
+    with pytest.raises(NlfemError):
+        assemble(mesh, precision=precision, material_scale=tab + np.triu(np.ones((4, 4)), 1), **kw)
+    with pytest.raises(NlfemError):
+        assemble(mesh, precision=precision, material_scale=np.ones((2, 2)), **kw)
+    fresh = Mesh.from_synth(m, ndof)
+    with pytest.raises(NlfemError):
+        assemble(fresh, precision=precision, material_scale=tab, **kw)
