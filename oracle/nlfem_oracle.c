@@ -37,7 +37,8 @@
 #include <omp.h>
 #endif
 
-enum { ORC_K_CONST = 0, ORC_K_FRAC = 1, ORC_K_PERI = 2 };
+enum { ORC_K_CONST = 0, ORC_K_FRAC = 1, ORC_K_PERI = 2, ORC_K_TAB = 3 };
+#define MAXTAB 1024
 enum { ORC_BALL_NOCAPS = 0, ORC_BALL_APPROXCAPS = 1, ORC_BALL_INF = 2 };
 enum { ORC_CLOSE_AUTO = 0, ORC_CLOSE_DUFFY = 1, ORC_CLOSE_NOZERODIV = 2, ORC_CLOSE_STANDARD = 3 };
 enum { ORC_PAIRS_BFS = 0, ORC_PAIRS_BRUTE = 1 };
@@ -59,6 +60,8 @@ typedef struct {
     rule_t ro, ri;        /* outer (x) and inner (y) rules */
     int ng;               /* Gauss-Legendre points per direction on (0,1) for the transforms */
     double gx[64], gw[64];
+    int ntab;             /* user kernel: values g(r_i) at r_i = i delta / (ntab - 1) */
+    double tab[MAXTAB];
 } params_t;
 
 typedef struct {
@@ -297,9 +300,23 @@ int orc_clip_square(const double V[3][2], double cx, double cy, double delta, do
  * Kernels (Sec. 3): value of gamma (scalar) or the 2x2 matrix Gamma (peridynamics)
  * at z = y - x.
  * ------------------------------------------------------------------------------------- */
+/* User-defined radial kernel gamma = c g(|z|), g interpolated linearly between its values at
+ * r_i = i delta / (n - 1) and held at g(delta) beyond delta (the Conclusion: kernels supplied
+ * by the user; here as a table instead of compiled code). */
+static double gamma_table(const params_t *P, double zx, double zy)
+{
+    double r = sqrt(zx * zx + zy * zy);
+    double t = r * ((double)(P->ntab - 1) / P->delta);
+    int i = (int)t;
+    if (i >= P->ntab - 1) return P->c * P->tab[P->ntab - 1];
+    double w = t - i;
+    return P->c * ((1.0 - w) * P->tab[i] + w * P->tab[i + 1]);
+}
+
 static double gamma_scalar(const params_t *P, double zx, double zy)
 {
     if (P->kernel == ORC_K_CONST) return P->c;
+    if (P->kernel == ORC_K_TAB) return gamma_table(P, zx, zy);
     double r2 = zx * zx + zy * zy;
     return P->c * pow(r2, -1.0 - P->s); /* c |z|^(-2-2s) */
 }
@@ -766,6 +783,7 @@ static void set_params(params_t *P, int kernel, double delta, double s, double k
     else if (kernel == ORC_K_CONST && ball == ORC_BALL_INF)
         P->c = 3.0 / (4.0 * delta * delta * delta * delta);   /* c_delta^inf of Sec. 3.3 */
     else if (kernel == ORC_K_CONST) P->c = 4.0 / (M_PI * delta * delta * delta * delta);
+    else if (kernel == ORC_K_TAB) P->c = 1.0;
     else if (kernel == ORC_K_FRAC) P->c = (2.0 - 2.0 * s) / (M_PI * pow(delta, 2.0 - 2.0 * s));
     else P->c = 3.0 / (delta * delta * delta);
     set_rule(&P->ro, nqo, qo);
@@ -826,12 +844,15 @@ orc_sys *orc_assemble(int M, const double *X, int K, const int *T, const signed 
                       int ng, const double *gx, const double *gw, int ndof,
                       const double *f_nodal, int mode, int nthreads,
                       int n_subset, const int *elem_subset,
-                      const signed char *mat, int nmat, const double *mscale)
+                      const signed char *mat, int nmat, const double *mscale,
+                      int ntab, const double *tab)
 {
     mesh_t m;
     build_mesh(&m, M, X, K, T, lab);
     params_t P;
     set_params(&P, kernel, delta, s, kconst, ball, nqo, qo, nqi, qi, close_rule, ng, gx, gw, ndof);
+    P.ntab = ntab < MAXTAB ? ntab : MAXTAB;
+    for (int i = 0; i < P.ntab; ++i) P.tab[i] = tab[i];
     orc_sys *S = calloc(1, sizeof(orc_sys));
     S->M = M; S->K = K; S->ndof = ndof; S->N = M * ndof;
     int nk = n_subset > 0 ? n_subset : K;

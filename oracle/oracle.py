@@ -30,7 +30,7 @@ SRC = os.path.join(HERE, "nlfem_oracle.c")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liborc.so")
 
-KERNELS = {"constant": 0, "fractional": 1, "peridynamic": 2}
+KERNELS = {"constant": 0, "fractional": 1, "peridynamic": 2, "tabulated": 3}
 BALLS = {"nocaps": 0, "approxcaps": 1, "infinity": 2}
 CLOSE_RULES = {"auto": 0, "duffy": 1, "nozerodiv": 2, "standard": 3}
 
@@ -67,7 +67,8 @@ def _load():
             lib.orc_assemble.restype = C.c_void_p
             lib.orc_assemble.argtypes = [C.c_int, dp, C.c_int, ip, cp, C.c_int, C.c_double, C.c_double,
                                          C.c_double, C.c_int, C.c_int, dp, C.c_int, dp, C.c_int, C.c_int,
-                                         dp, dp, C.c_int, dp, C.c_int, C.c_int, C.c_int, ip, cp, C.c_int, dp]
+                                         dp, dp, C.c_int, dp, C.c_int, C.c_int, C.c_int, ip, cp, C.c_int, dp,
+                                         C.c_int, dp]
             lib.orc_sys_sizes.argtypes = [C.c_void_p, lp]
             lib.orc_sys_copy.argtypes = [C.c_void_p, lp, ip, dp, dp, ip, cp, cp, lp]
             lib.orc_sys_free.argtypes = [C.c_void_p]
@@ -129,10 +130,12 @@ def _kernel_args(kernel, delta, s, kconst, ball, quad_outer, quad_inner, close_r
 def assemble(mesh, kernel: str = "constant", delta: float = 0.1, s: float = -1.0, kconst=None,
              ball: str = "nocaps", quad_outer: int = 7, quad_inner: int = 7, close_rule: str = "auto",
              duffy_n: int = 5, f_nodal=None, pairs_mode: str = "bfs", threads: int = 0,
-             elem_subset=None, materials=None, material_scale=None) -> OracleSystem:
+             elem_subset=None, materials=None, material_scale=None, kernel_table=None) -> OracleSystem:
     """FP64 assembly of A_h^# and F. materials [K] (0..n-1) with the symmetric n x n table
     material_scale make the kernel label dependent: Psi on E_k x E_l times
-    material_scale[materials[k], materials[l]] (Sec. 1, interface problems)."""
+    material_scale[materials[k], materials[l]] (Sec. 1, interface problems). kernel="tabulated"
+    takes the user kernel c g(|z|) from kernel_table (g at r_i = i delta / (n - 1), linear in
+    between, held beyond delta; c = kconst, default 1)."""
     lib = _load()
     ndof = 2 if kernel == "peridynamic" else 1
     (kid, delta, s, kc, bid, qo, qi, cid, gx, gw) = _kernel_args(
@@ -143,6 +146,10 @@ def assemble(mesh, kernel: str = "constant", delta: float = 0.1, s: float = -1.0
     f = None
     if f_nodal is not None:
         f = np.ascontiguousarray(np.asarray(f_nodal, dtype=np.float64).reshape(mesh.M * ndof))
+    tab = None
+    if kernel == "tabulated":
+        tab = np.ascontiguousarray(kernel_table, dtype=np.float64).reshape(-1)
+        assert 2 <= len(tab) <= 1024
     mat = msc = None
     nmat = 0
     if materials is not None:
@@ -162,7 +169,8 @@ def assemble(mesh, kernel: str = "constant", delta: float = 0.1, s: float = -1.0
                          0 if pairs_mode == "bfs" else 1, int(threads), nsub,
                          _p(sub, C.c_int) if sub is not None else None,
                          _p(mat, C.c_byte) if mat is not None else None, nmat,
-                         _p(msc, C.c_double) if msc is not None else None)
+                         _p(msc, C.c_double) if msc is not None else None,
+                         len(tab) if tab is not None else 0, _p(tab, C.c_double) if tab is not None else None)
     sz = np.zeros(3, dtype=np.int64)
     lib.orc_sys_sizes(h, _p(sz, C.c_longlong))
     N, nnz, npairs = (int(v) for v in sz)
