@@ -38,6 +38,10 @@ extern "C" {
 #define NLFEM_KERNEL_CONSTANT 0     /* gamma = c, c = 4 / (pi delta^4) by default */
 #define NLFEM_KERNEL_FRACTIONAL 1   /* gamma = c |x-y|^(-2-2s), c = (2-2s)/(pi delta^(2-2s)) (eq. fractional-scaling) */
 #define NLFEM_KERNEL_PERIDYNAMIC 2  /* Psi = c (x-y)(x-y)^T / |x-y|^3, c = 3 / delta^3 (eq. ker:peridynamics), 2 dofs per node */
+#define NLFEM_KERNEL_TABULATED 3    /* user-defined radial kernel gamma = c g(|x-y|) (the Conclusion's user kernels):
+                                       g given by params.kernel_table at r_i = i delta / (n - 1), linear
+                                       in between, held at g(delta) beyond; c = kconst, default 1;
+                                       bounded kernels only: intersecting pairs take the standard rule */
 
 /* ball approximations of the Euclidean ball (Sec. 2.2) */
 #define NLFEM_BALL_NOCAPS 0         /* Def. 2.1 */
@@ -78,6 +82,9 @@ typedef struct {
      * the call) must be symmetric so that A stays symmetric. 0 / NULL = no labels. */
     int n_materials;         /* 0..16 */
     const double* material_scale;
+    /* NLFEM_KERNEL_TABULATED: table_size (2..1024) values of g, host memory, read during the call */
+    int table_size;
+    const double* kernel_table;
 } nlfem_params;
 
 typedef struct {

@@ -140,12 +140,13 @@ class System:
 
 def assemble(mesh: Mesh, kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7,
              quad_inner=7, duffy_gauss=5, close_rule="auto", precision="fp64", f_nodal=None,
-             mem_budget_bytes=0, stream=None, material_scale=None) -> System:
+             mem_budget_bytes=0, stream=None, material_scale=None, kernel_table=None) -> System:
     """Assemble A_h^# and F on the GPU (nlfem_assemble). material_scale: symmetric table of a
-    label-dependent kernel over the labels of Mesh.set_materials."""
+    label-dependent kernel over the labels of Mesh.set_materials; kernel_table: the values of
+    g for kernel="tabulated"."""
     torch = _torch()
     p = B.make_params(kernel, delta, s, kconst, ball, quad_outer, quad_inner, duffy_gauss, close_rule,
-                      precision, mem_budget_bytes, material_scale)
+                      precision, mem_budget_bytes, material_scale, kernel_table)
     f = None if f_nodal is None else _as_dev(f_nodal, torch.float64).reshape(-1)
     h = B.nlfem_assemble(mesh.handle, p, f, stream)
     return System(mesh, h)
@@ -171,11 +172,12 @@ def _params_list(params):
     ps = []
     for p in params:
         q = dict(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7, quad_inner=7,
-                 duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0, material_scale=None)
+                 duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0, material_scale=None,
+                 kernel_table=None)
         q.update(p)
         ps.append(B.make_params(q["kernel"], q["delta"], q["s"], q["kconst"], q["ball"], q["quad_outer"],
                                 q["quad_inner"], q["duffy_gauss"], q["close_rule"], q["precision"],
-                                q["mem_budget_bytes"], q["material_scale"]))
+                                q["mem_budget_bytes"], q["material_scale"], q["kernel_table"]))
     return ps
 
 

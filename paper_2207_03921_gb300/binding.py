@@ -22,7 +22,7 @@ _lock = threading.Lock()
 NLFEM_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "BAD_MESH", -3: "OOM", -4: "BUDGET", -5: "CUDA", -6: "NOT_CONVERGED",
           -7: "TIMEOUT", -8: "UNSUPPORTED"}
-KERNELS = {"constant": 0, "fractional": 1, "peridynamic": 2}
+KERNELS = {"constant": 0, "fractional": 1, "peridynamic": 2, "tabulated": 3}
 BALLS = {"nocaps": 0, "approxcaps": 1, "infinity": 2}
 CLOSE_RULES = {"auto": 0, "duffy": 1, "nozerodiv": 2, "standard": 3}
 PRECISIONS = {"fp64": 0, "fp32_bulk": 1}
@@ -38,7 +38,8 @@ class nlfem_params(C.Structure):
     _fields_ = [("kernel", C.c_int), ("delta", C.c_double), ("s", C.c_double), ("kconst", C.c_double),
                 ("ball", C.c_int), ("quad_outer", C.c_int), ("quad_inner", C.c_int), ("duffy_gauss", C.c_int),
                 ("close_rule", C.c_int), ("precision", C.c_int), ("mem_budget_bytes", C.c_int64),
-                ("n_materials", C.c_int), ("material_scale", C.c_void_p)]
+                ("n_materials", C.c_int), ("material_scale", C.c_void_p),
+                ("table_size", C.c_int), ("kernel_table", C.c_void_p)]
 
 
 class nlfem_assembly_info(C.Structure):
@@ -321,9 +322,10 @@ def nlfem_version() -> str:
 
 def make_params(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7, quad_inner=7,
                 duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0,
-                material_scale=None) -> nlfem_params:
-    """nlfem_params; material_scale: symmetric n x n table of a label-dependent kernel (the
-    returned struct keeps the array alive for the calls it is passed to)."""
+                material_scale=None, kernel_table=None) -> nlfem_params:
+    """nlfem_params; material_scale: symmetric n x n table of a label-dependent kernel;
+    kernel_table: values of g for kernel="tabulated" (the returned struct keeps both arrays
+    alive for the calls it is passed to)."""
     p = nlfem_params()
     p.kernel = KERNELS[kernel]
     p.delta = float(delta)
@@ -345,4 +347,12 @@ def make_params(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps",
         p._keep = tab
         p.n_materials = int(tab.shape[0])
         p.material_scale = tab.ctypes.data
+    p.table_size = 0
+    p.kernel_table = None
+    if kernel_table is not None:
+        import numpy as np
+        kt = np.ascontiguousarray(kernel_table, dtype=np.float64).reshape(-1)
+        p._keep_table = kt
+        p.table_size = int(kt.size)
+        p.kernel_table = kt.ctypes.data
     return p

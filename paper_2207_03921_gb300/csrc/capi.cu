@@ -83,7 +83,13 @@ static void fill_gauss(DuffyRule& d, int n) {
 }
 
 static Params make_params(const nlfem_params& p, int ndof) {
-    NLFEM_CHECK(p.kernel >= 0 && p.kernel <= 2, NLFEM_ERR_INVALID_ARG, "unknown kernel");
+    NLFEM_CHECK(p.kernel >= 0 && p.kernel <= 3, NLFEM_ERR_INVALID_ARG, "unknown kernel");
+    if (p.kernel == NLFEM_KERNEL_TABULATED) {
+        NLFEM_CHECK(p.kernel_table && p.table_size >= 2 && p.table_size <= 1024, NLFEM_ERR_INVALID_ARG,
+                    "the tabulated kernel needs a table of 2..1024 values");
+        for (int i = 0; i < p.table_size; ++i)
+            NLFEM_CHECK(std::isfinite(p.kernel_table[i]), NLFEM_ERR_INVALID_ARG, "kernel_table must be finite");
+    }
     NLFEM_CHECK(p.delta > 0 && std::isfinite(p.delta), NLFEM_ERR_INVALID_ARG, "delta must be > 0");
     NLFEM_CHECK(p.ball == NLFEM_BALL_NOCAPS || p.ball == NLFEM_BALL_APPROXCAPS || p.ball == NLFEM_BALL_INFINITY,
                 NLFEM_ERR_INVALID_ARG, "unknown ball");
@@ -121,7 +127,12 @@ static Params make_params(const nlfem_params& p, int ndof) {
         P.c = 3.0 / (4.0 * p.delta * p.delta * p.delta * p.delta);  // c_delta^inf (Sec. 3.3)
     else if (p.kernel == NLFEM_KERNEL_CONSTANT) P.c = 4.0 / (M_PI * p.delta * p.delta * p.delta * p.delta);
     else if (p.kernel == NLFEM_KERNEL_FRACTIONAL) P.c = (2.0 - 2.0 * p.s) / (M_PI * std::pow(p.delta, 2.0 - 2.0 * p.s));
+    else if (p.kernel == NLFEM_KERNEL_TABULATED) P.c = 1.0;
     else P.c = 3.0 / (p.delta * p.delta * p.delta);
+    if (p.kernel == NLFEM_KERNEL_TABULATED) {
+        P.ntab = p.table_size;
+        P.tinv = (double)(p.table_size - 1) / p.delta;
+    }
     fill_rule(P.ro, p.quad_outer);
     fill_rule(P.ri, p.quad_inner);
     fill_gauss(P.dr, p.duffy_gauss);
@@ -147,6 +158,8 @@ static Params make_params(const nlfem_params& p, int ndof) {
     }
     NLFEM_CHECK(!(P.singular && ndof == 2), NLFEM_ERR_UNSUPPORTED,
                 "the singular rule is implemented for scalar kernels only");
+    NLFEM_CHECK(!(P.singular && p.kernel == NLFEM_KERNEL_TABULATED), NLFEM_ERR_UNSUPPORTED,
+                "the singular rule needs a homogeneous kernel; tabulated kernels take the standard rule");
     return P;
 }
 
@@ -212,6 +225,8 @@ void nlfem_params_default(nlfem_params* p, int kernel) {
     p->mem_budget_bytes = 0;
     p->n_materials = 0;
     p->material_scale = nullptr;
+    p->table_size = 0;
+    p->kernel_table = nullptr;
 }
 
 // The library allocates its working buffers from the device's default memory pool
@@ -357,9 +372,24 @@ static std::shared_ptr<PairCache> ensure_cache(Mesh& m, const Params& P, cudaStr
     return pc;
 }
 
-// Label-dependent kernel: the scale table goes to the device with the system, and the
-// system's parameters point at it and at the mesh's material labels.
-static void attach_materials(System& S, const nlfem_params& p, const Mesh& m, cudaStream_t st) {
+// The tables of a user kernel and of a label-dependent kernel go to the device with the
+// system; the system's parameters point at them (and at the mesh's material labels).
+static void attach_tables(System& S, const nlfem_params& p, const Mesh& m, cudaStream_t st);
+
+// The user kernel's table goes to the device into bufs; P points at it.
+static void attach_table(Params& P, const nlfem_params& p, DBuf<double>& t64, DBuf<float>& t32, cudaStream_t st) {
+    if (p.kernel != NLFEM_KERNEL_TABULATED) return;
+    std::vector<float> f(p.table_size);
+    for (int i = 0; i < p.table_size; ++i) f[i] = (float)p.kernel_table[i];
+    upload(t64, p.kernel_table, (size_t)p.table_size, st);
+    upload(t32, f.data(), (size_t)p.table_size, st);
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));  // f is a host temporary
+    P.tab64 = t64.p;
+    P.tab32 = t32.p;
+}
+
+static void attach_tables(System& S, const nlfem_params& p, const Mesh& m, cudaStream_t st) {
+    attach_table(S.prm, p, S.tab64, S.tab32, st);
     if (p.n_materials <= 0) return;
     NLFEM_CHECK(m.mat.p && m.mat_max >= 0, NLFEM_ERR_INVALID_ARG,
                 "n_materials > 0 needs material labels (nlfem_mesh_set_materials)");
@@ -436,7 +466,7 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
         S.mesh = &m;
         S.pc = pc;
         S.prm = P;
-        attach_materials(S, *params, m, st);
+        attach_tables(S, *params, m, st);
         P = S.prm;
         S.N = pc->N;
         S.nnz = pc->nnz;
@@ -540,7 +570,7 @@ int nlfem_batch_assemble(const nlfem_mesh_t* meshes, const nlfem_params* params,
         S.mesh = &m;
         S.pc = pcs[i];
         S.prm = P[i];
-        attach_materials(S, params[i], m, st);
+        attach_tables(S, params[i], m, st);
         P[i] = S.prm;
         S.N = pcs[i]->N;
         S.nnz = pcs[i]->nnz;
@@ -678,7 +708,7 @@ int nlfem_batch_create(const nlfem_mesh_t* meshes, const nlfem_params* params, c
         S.mesh = &m;
         S.pc = pc;
         S.prm = P;
-        attach_materials(S, params[i], m, st);
+        attach_tables(S, params[i], m, st);
         P = S.prm;
         S.N = pc->N;
         S.nnz = pc->nnz;
@@ -756,7 +786,10 @@ int nlfem_autotune(nlfem_mesh_t mesh, const nlfem_params* params, void* stream, 
                 "the autotuner sets the FP32-bulk launch shapes");
     Mesh& m = mesh->m;
     cudaStream_t st = (cudaStream_t)stream;
-    const Params P = make_params(*params, m.ndof);
+    Params P = make_params(*params, m.ndof);
+    DBuf<double> t64;
+    DBuf<float> t32;
+    attach_table(P, *params, t64, t32, st);
     cudaEvent_t ev[12];
     for (int i = 0; i < 12; ++i) NLFEM_CUDA_TRY(cudaEventCreate(&ev[i]));
     struct EvGuard {

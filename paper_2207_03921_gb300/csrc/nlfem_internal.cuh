@@ -160,7 +160,22 @@ struct Params {
     const int8_t* mat;
     const double* msc64;
     const float* msc32;
+    // user-defined radial kernel: g at r_i = i / tinv, i < ntab, on the device
+    int ntab;
+    double tinv;
+    const double* tab64;
+    const float* tab32;
 };
+
+// g(r) of the tabulated kernel, r = sqrt(d2): linear between the table values, held beyond
+template <typename R>
+__device__ __forceinline__ R table_g(const R* __restrict__ tab, int n, R tinv, R d2) {
+    const R t = sqrt(d2) * tinv;
+    const int i = (int)t;
+    if (i >= n - 1) return tab[n - 1];
+    const R w = t - (R)i;
+    return ((R)1 - w) * tab[i] + w * tab[i + 1];
+}
 
 // kernel factor of the ordered pair (k, l) for label-dependent kernels
 __device__ __forceinline__ double pair_factor64(const Params& P, int k, int l) {
@@ -248,6 +263,8 @@ struct System {
     DBuf<FixState> fix;      // FP32 bulk: the fixed-point scale
     DBuf<double> msc64;      // label-dependent kernel: the scale table on the device
     DBuf<float> msc32;
+    DBuf<double> tab64;      // user-defined radial kernel: the table on the device
+    DBuf<float> tab32;
     nlfem_assembly_info info;
     std::shared_ptr<SolveState> solver;
 };

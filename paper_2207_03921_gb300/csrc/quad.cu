@@ -52,6 +52,10 @@ __device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
 template <typename R, int KER>
 __device__ __forceinline__ R gamma_s(R d2, const Params& P) {
     if (KER == NLFEM_KERNEL_CONSTANT) return (R)P.c;
+    if (KER == NLFEM_KERNEL_TABULATED) {
+        if constexpr (sizeof(R) == 4) return (R)P.c * table_g<float>(P.tab32, P.ntab, (float)P.tinv, (float)d2);
+        else return (R)P.c * table_g<double>(P.tab64, P.ntab, P.tinv, (double)d2);
+    }
     if (P.s == 0.5) {
         R r = rsqrt_r<R>(d2);
         return (R)P.c * r * r * r;
@@ -495,6 +499,8 @@ static void launch_trunc(const QuadArgs& a, R* out, cudaStream_t st) {
         if (NQI == 7) NLFEM_TR(NLFEM_KERNEL_CONSTANT, 7); else NLFEM_TR(NLFEM_KERNEL_CONSTANT, 16);
     } else if (K == NLFEM_KERNEL_FRACTIONAL) {
         if (NQI == 7) NLFEM_TR(NLFEM_KERNEL_FRACTIONAL, 7); else NLFEM_TR(NLFEM_KERNEL_FRACTIONAL, 16);
+    } else if (K == NLFEM_KERNEL_TABULATED) {
+        if (NQI == 7) NLFEM_TR(NLFEM_KERNEL_TABULATED, 7); else NLFEM_TR(NLFEM_KERNEL_TABULATED, 16);
     } else {
         if (NQI == 7) NLFEM_TR(NLFEM_KERNEL_PERIDYNAMIC, 7); else NLFEM_TR(NLFEM_KERNEL_PERIDYNAMIC, 16);
     }

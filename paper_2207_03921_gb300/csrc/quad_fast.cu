@@ -57,6 +57,9 @@ struct FastReq {
     int nmat;     // label-dependent kernel: factor msc[mat[k] * nmat + mat[l]] (0: none)
     const int8_t* mat;
     const float* msc;
+    int ntab;     // user-defined radial kernel: table of g at r_i = i / tinv
+    float tinv;
+    const float* tab;
     // fixed-point accumulation into the upper CSR entries (see accumulate_pair)
     unsigned long long* acc;  // [n_upper][NC] int64 two's complement sums
     float* kkll;              // [2][P][6 NC] kk, then ll, of every pair, by pair id
@@ -119,6 +122,8 @@ __device__ __forceinline__ void tri_quad(const FastRule& R, const FastReq& Q, In
                 } else {
                     wc[0] = wq * Q.c * exp2f(log2f(r2) * (-1.f - Q.s));
                 }
+            } else if (KER == NLFEM_KERNEL_TABULATED) {
+                wc[0] = wq * Q.c * table_g<float>(Q.tab, Q.ntab, Q.tinv, r2);
             } else {
                 const float r = rsqrtf(r2);
                 const float sc = wq * Q.c * r * r * r;
@@ -826,6 +831,9 @@ FastReq make_req(Mesh& m, PairCache& pc, const Params& prm, int list) {
     q.nmat = prm.nmat;
     q.mat = prm.mat;
     q.msc = prm.msc32;
+    q.ntab = prm.ntab;
+    q.tinv = (float)prm.tinv;
+    q.tab = prm.tab32;
     q.npairs_all = pc.npairs;
     q.up_start = pc.up_start.p;
     q.epos = pc.epos.p;
@@ -899,6 +907,8 @@ void set_fast_attributes() {
     cut_attrs<NLFEM_KERNEL_FRACTIONAL, 16>();
     cut_attrs<NLFEM_KERNEL_PERIDYNAMIC, 7>();
     cut_attrs<NLFEM_KERNEL_PERIDYNAMIC, 16>();
+    cut_attrs<NLFEM_KERNEL_TABULATED, 7>();
+    cut_attrs<NLFEM_KERNEL_TABULATED, 16>();
     done.push_back(dev);
 }
 
@@ -921,6 +931,9 @@ static void launch_kernel(const Params& prm, int list, const FastRule& r, const 
     } else if (prm.kernel == NLFEM_KERNEL_FRACTIONAL) {
         if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_FRACTIONAL, 7, BATCH>(list, ball, r, L, grid, st);
         else launch_class<NLFEM_KERNEL_FRACTIONAL, 16, BATCH>(list, ball, r, L, grid, st);
+    } else if (prm.kernel == NLFEM_KERNEL_TABULATED) {
+        if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_TABULATED, 7, BATCH>(list, ball, r, L, grid, st);
+        else launch_class<NLFEM_KERNEL_TABULATED, 16, BATCH>(list, ball, r, L, grid, st);
     } else {
         if (prm.ri.n == 7) launch_class<NLFEM_KERNEL_PERIDYNAMIC, 7, BATCH>(list, ball, r, L, grid, st);
         else launch_class<NLFEM_KERNEL_PERIDYNAMIC, 16, BATCH>(list, ball, r, L, grid, st);

@@ -82,6 +82,14 @@ CASES = {
     # infinity ball, peridynamics, delta = 3h
     "infinity_peridynamic": (lambda: meshes.structured(-0.2, 1.2, 20),
                              dict(kernel="peridynamic", delta=0.21, ball="infinity")),
+    # user-defined radial kernel from a table (a Gaussian bump on 33 nodes), approxcaps
+    "tabulated_gaussian": (lambda: meshes.jittered_delaunay(-0.2, 1.2, 20, 0.05, seed=31),
+                           dict(kernel="tabulated", delta=0.2, ball="approxcaps", kconst=50.0,
+                                kernel_table=np.exp(-3.0 * np.linspace(0.0, 1.0, 33) ** 2))),
+    # user-defined kernel on the infinity ball (held beyond delta), 16-point inner rule, ties
+    "tabulated_infinity": (lambda: meshes.structured(-0.2, 1.2, 28),
+                           dict(kernel="tabulated", delta=0.1, ball="infinity", quad_inner=16,
+                                kernel_table=np.array([2.0, 1.5, 0.5, 0.25, 0.1]))),
 }
 
 
