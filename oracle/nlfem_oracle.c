@@ -71,7 +71,8 @@ typedef struct {
     double *det;       /* |det J_k| = 2 |E_k| */
     signed char *lab;  /* 1 = Omega */
     signed char *dir;  /* node is Dirichlet */
-    int *ne_ptr, *ne_idx; /* node -> elements */
+    int *ne_ptr, *ne_idx; /* position -> elements (nodes at the same point share one entry) */
+    int *pos;          /* node -> its position: the smallest node id with the same coordinates */
 } mesh_t;
 
 typedef struct {
@@ -593,10 +594,14 @@ static void pair_duffy(const mesh_t *m, const params_t *P, int k, int l, int sha
 /* ---------------------------------------------------------------------------------------
  * Alg. 1 for one ordered pair. Returns 1 if the pair interacts.
  * ------------------------------------------------------------------------------------- */
+/* Shared vertices of E_k and E_l as points (Sec. 2.3: intersecting pairs), so that a mesh whose
+ * elements carry their own copies of the vertices (a discontinuous ansatz) classifies its pairs
+ * like the continuous one. */
 static int shared_count(const mesh_t *m, int k, int l)
 {
     int c = 0;
-    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) c += m->T[3 * k + a] == m->T[3 * l + b];
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b)
+        c += m->pos[m->T[3 * k + a]] == m->pos[m->T[3 * l + b]];
     return c;
 }
 
@@ -690,6 +695,7 @@ static void neighbours_of(const mesh_t *m, int e, ivec_t *out, int *mark, int st
     out->n = 0;
     for (int a = 0; a < 3; ++a) {
         int v = m->T[3 * e + a];
+        v = m->pos[v];
         for (int t = m->ne_ptr[v]; t < m->ne_ptr[v + 1]; ++t) {
             int f = m->ne_idx[t];
             if (mark[f] != stamp) { mark[f] = stamp; ivec_push(out, f); }
@@ -729,6 +735,16 @@ static void search_partners(const mesh_t *m, const params_t *P, int k, int mode,
 /* ---------------------------------------------------------------------------------------
  * Public entry points (ctypes)
  * ------------------------------------------------------------------------------------- */
+typedef struct { double x, y; int id; } xyid_t;
+
+static int cmp_xyid(const void *pa, const void *pb)
+{
+    const xyid_t *a = pa, *b = pb;
+    if (a->x != b->x) return a->x < b->x ? -1 : 1;
+    if (a->y != b->y) return a->y < b->y ? -1 : 1;
+    return a->id - b->id;
+}
+
 static void build_mesh(mesh_t *m, int M, const double *X, int K, const int *T, const signed char *lab)
 {
     m->M = M; m->K = K; m->X = X;
@@ -746,13 +762,30 @@ static void build_mesh(mesh_t *m, int M, const double *X, int K, const int *T, c
         m->lab[k] = lab ? lab[k] : 1;
         if (!m->lab[k]) { m->dir[t0] = 1; m->dir[t1] = 1; m->dir[t2] = 1; }
     }
+    /* positions: nodes with equal coordinates, found by sorting the nodes by (x, y) */
+    m->pos = malloc(sizeof(int) * ((size_t)M + 1));
+    {
+        xyid_t *ord = malloc(sizeof(xyid_t) * ((size_t)M + 1));
+        for (int v = 0; v < M; ++v) { ord[v].x = X[2 * v]; ord[v].y = X[2 * v + 1]; ord[v].id = v; }
+        qsort(ord, (size_t)M, sizeof(xyid_t), cmp_xyid);
+        for (int i = 0; i < M;) {
+            int j = i, lo = ord[i].id;
+            while (j < M && ord[j].x == ord[i].x && ord[j].y == ord[i].y) {
+                if (ord[j].id < lo) lo = ord[j].id;
+                ++j;
+            }
+            for (int t = i; t < j; ++t) m->pos[ord[t].id] = lo;
+            i = j;
+        }
+        free(ord);
+    }
     m->ne_ptr = calloc((size_t)M + 1, sizeof(int));
-    for (int k = 0; k < K; ++k) for (int a = 0; a < 3; ++a) m->ne_ptr[m->T[3 * k + a] + 1]++;
+    for (int k = 0; k < K; ++k) for (int a = 0; a < 3; ++a) m->ne_ptr[m->pos[m->T[3 * k + a]] + 1]++;
     for (int v = 0; v < M; ++v) m->ne_ptr[v + 1] += m->ne_ptr[v];
     m->ne_idx = malloc(sizeof(int) * 3 * (size_t)K + 4);
     int *fill = calloc((size_t)M + 1, sizeof(int));
     for (int k = 0; k < K; ++k) for (int a = 0; a < 3; ++a) {
-        int v = m->T[3 * k + a];
+        int v = m->pos[m->T[3 * k + a]];
         m->ne_idx[m->ne_ptr[v] + fill[v]++] = k;
     }
     free(fill);
@@ -760,7 +793,7 @@ static void build_mesh(mesh_t *m, int M, const double *X, int K, const int *T, c
 
 static void free_mesh(mesh_t *m)
 {
-    free(m->T); free(m->det); free(m->lab); free(m->dir); free(m->ne_ptr); free(m->ne_idx);
+    free(m->T); free(m->det); free(m->lab); free(m->dir); free(m->ne_ptr); free(m->ne_idx); free(m->pos);
 }
 
 static void set_rule(rule_t *r, int n, const double *q)

@@ -161,6 +161,15 @@ def paper_square(delta: float, a: float) -> Mesh:
                       name=f"paper_square_d{delta}_a{a}")
 
 
+def discontinuous(mesh: Mesh) -> Mesh:
+    """The same triangles with their own copies of the vertices (the P1-DG ansatz of Sec. 2.2:
+    J = 3K nodes, node 3k + a = vertex a of element k as given in mesh.elems)."""
+    K = mesh.K
+    verts = np.ascontiguousarray(mesh.verts[mesh.elems].reshape(3 * K, 2))
+    elems = np.arange(3 * K, dtype=np.int32).reshape(K, 3)
+    return Mesh(verts, elems, mesh.elem_label.copy(), mesh.h, name=mesh.name + "_dg", meta=dict(mesh.meta))
+
+
 def nodal(mesh: Mesh, fn) -> np.ndarray:
     """Evaluate fn(x, y) at the nodes; returns float64 [M] or [M, n]."""
     v = fn(mesh.verts[:, 0], mesh.verts[:, 1])

@@ -1,0 +1,82 @@
+"""Pins of the oracle's discontinuous P1 ansatz (Sec. 2.2, J = n (d+1) K; the factored local
+terms of eq. case-one-factoredOut): every element carries its own copy of its vertices.
+
+- Embedding: a continuous function is a DG function whose copies of a vertex agree, so with the
+  prolongation P (DG node 3k + a takes the value of vertex a of element k) the continuous
+  matrix is P^T A_DG P and the continuous load vector P^T F_DG, for every kernel whose
+  intersecting pairs take the truncation rule (constant, peridynamic with the diamond rule,
+  user tables): the pairs, the quadrature points and the cut polygons are the same.
+- A_DG is bitwise symmetric and annihilates the constants (DG copies included).
+- Sec. 3.2's DG table: second-order rates and the printed magnitudes. The printed counts of
+  free dofs are 3 n (K_Omega - 2); ours are 3 n K_Omega (every dof of an Omega element free).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from synth import meshes
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+
+def prolongation(m, ndof):
+    K = m.K
+    rows = np.arange(3 * K)
+    P = sp.csr_matrix((np.ones(3 * K), (rows, m.elems.reshape(-1))), shape=(3 * K, m.M))
+    return sp.kron(P, sp.identity(ndof)).tocsr()
+
+
+@pytest.mark.parametrize("kw", [dict(kernel="constant", delta=0.3, ball="approxcaps"),
+                                dict(kernel="peridynamic", delta=0.3, ball="nocaps"),
+                                dict(kernel="tabulated", delta=0.3, ball="infinity",
+                                     kernel_table=np.array([3.0, 2.0, 1.0]))],
+                         ids=lambda k: k["kernel"])
+def test_continuous_matrix_is_the_restriction_of_the_dg_matrix(kw):
+    m = meshes.jittered_delaunay(0.0, 1.0, 7, 0.1, seed=27)
+    d = meshes.discontinuous(m)
+    ndof = 2 if kw["kernel"] == "peridynamic" else 1
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal(m.M * ndof)
+    A = oracle.assemble(m, f_nodal=f, **kw)
+    P = prolongation(m, ndof)
+    D = oracle.assemble(d, f_nodal=P @ f, **kw)
+    assert D.N == 3 * m.K * ndof
+    R = (P.T @ D.scipy() @ P).toarray()
+    Ad = A.dense()
+    assert np.abs(R - Ad).max() <= 1e-13 * np.abs(Ad).max()
+    assert np.abs(P.T @ D.F - A.F).max() <= 1e-13 * np.abs(A.F).max()
+    S = D.scipy()
+    assert (S != S.T).nnz == 0
+    if ndof == 1:
+        assert np.abs(S @ np.ones(D.N)).max() <= 1e-13 * np.abs(D.val).max()
+    # the DG matrix is not the continuous one: it couples the copies of a vertex
+    assert len(D.val) > len(A.val)
+
+
+def _e4(level):
+    a = GOLD["E4_peridynamics_dg"]["a"][level]
+    m = meshes.discontinuous(meshes.paper_square(0.1, a))
+    x, y = m.verts[:, 0], m.verts[:, 1]
+    f = -0.5 * math.pi * np.stack([1.0 + 2.0 * x, y], 1)
+    S = oracle.assemble(m, kernel="peridynamic", delta=0.1, ball="approxcaps", f_nodal=f)
+    g = np.stack([y * y, x * x * y], 1).reshape(-1)
+    u = oracle.solve_dirichlet(S, g)
+    ue = lambda x, y: np.stack([y * y, x * x * y])
+    return int((~np.repeat(S.dirichlet, 2)).sum()), oracle.l2_error(m, u, ue, ndof=2)
+
+
+def test_paper_E4_peridynamic_dg_rates():
+    tab = GOLD["E4_peridynamics_dg"]
+    runs = [_e4(k) for k in range(2)] + ([_e4(2)] if os.environ.get("NLFEM_SLOW") == "1" else [])
+    for i, (dof, _) in enumerate(runs):
+        assert dof == 6 * (tab["dof"][i] // 6 + 2)          # 3 n K_Omega against 3 n (K_Omega - 2)
+    errs = [e for _, e in runs]
+    for i in range(len(errs) - 1):
+        assert 1.7 < math.log2(errs[i] / errs[i + 1]) < 2.3, errs
+    for i, e in enumerate(errs):
+        assert 0.4 * tab["l2"][i] < e < 2.5 * tab["l2"][i], (errs, tab["l2"])
