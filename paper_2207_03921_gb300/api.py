@@ -37,19 +37,22 @@ def _as_dev(x, dtype):
 class Mesh:
     """A triangle mesh of the base domain uploaded to the GPU (nlfem_mesh_create)."""
 
-    def __init__(self, verts, elems, elem_label=None, ndof_per_node=1, stream=None):
+    def __init__(self, verts, elems, elem_label=None, ndof_per_node=1, stream=None, dg=False):
+        """dg=True: discontinuous P1 ansatz, node 3k + a = vertex a of element k
+        (nlfem_mesh_create_dg); the mesh then has 3K nodes."""
         torch = _torch()
         self.verts = _as_dev(verts, torch.float64)
         self.elems = _as_dev(elems, torch.int32)
         self.elem_label = None if elem_label is None else _as_dev(elem_label, torch.int8)
-        self.M = int(self.verts.shape[0])
         self.K = int(self.elems.shape[0])
+        self.M = 3 * self.K if dg else int(self.verts.shape[0])
         self.ndof = int(ndof_per_node)
-        self.handle = B.nlfem_mesh_create(self.verts, self.elems, self.elem_label, self.ndof, stream)
+        self.dg = bool(dg)
+        self.handle = B.nlfem_mesh_create(self.verts, self.elems, self.elem_label, self.ndof, stream, dg=dg)
 
     @classmethod
-    def from_synth(cls, m, ndof_per_node=1, stream=None):
-        return cls(m.verts, m.elems, m.elem_label, ndof_per_node, stream)
+    def from_synth(cls, m, ndof_per_node=1, stream=None, dg=False):
+        return cls(m.verts, m.elems, m.elem_label, ndof_per_node, stream, dg=dg)
 
     def pairs(self):
         """(k, l) int32 tensors of the cached interaction graph (copies)."""

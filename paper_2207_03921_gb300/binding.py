@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True):
         lib.nlfem_last_error.restype = C.c_char_p
         lib.nlfem_version.restype = C.c_char_p
         lib.nlfem_mesh_create.argtypes = [vp, i64, vp, i64, vp, ip, vp, C.POINTER(vp)]
+        lib.nlfem_mesh_create_dg.argtypes = [vp, i64, vp, i64, vp, ip, vp, C.POINTER(vp)]
         lib.nlfem_mesh_destroy.argtypes = [vp]
         lib.nlfem_mesh_destroy.restype = None
         lib.nlfem_params_default.argtypes = [C.POINTER(nlfem_params), ip]
@@ -142,13 +143,13 @@ def _stream(stream):
 
 # ---- the C ABI, one Python function per C function ----------------------------------------
 
-def nlfem_mesh_create(verts, elems, elem_label=None, ndof_per_node=1, stream=None):
+def nlfem_mesh_create(verts, elems, elem_label=None, ndof_per_node=1, stream=None, dg=False):
     lib = load()
     h = C.c_void_p()
     M = int(verts.shape[0])
     K = int(elems.shape[0])
-    _check(lib.nlfem_mesh_create(_ptr(verts), M, _ptr(elems), K, _ptr(elem_label), int(ndof_per_node),
-                                 _stream(stream), C.byref(h)))
+    fn = lib.nlfem_mesh_create_dg if dg else lib.nlfem_mesh_create
+    _check(fn(_ptr(verts), M, _ptr(elems), K, _ptr(elem_label), int(ndof_per_node), _stream(stream), C.byref(h)))
     return h
 
 
@@ -306,6 +307,10 @@ def nlfem_pairs_noalloc(verts, elems, delta, ball, quad_outer, out_k, out_l, str
         err.npairs = n.value
         raise err
     return n.value
+
+
+def nlfem_mesh_create_dg(verts, elems, elem_label=None, ndof_per_node=1, stream=None):
+    return nlfem_mesh_create(verts, elems, elem_label, ndof_per_node, stream, dg=True)
 
 
 def nlfem_mesh_set_materials(mesh, material, stream=None) -> None:

@@ -294,6 +294,39 @@ int nlfem_mesh_create(const double* verts, int64_t M, const int32_t* elems, int6
     NLFEM_API_END
 }
 
+int nlfem_mesh_create_dg(const double* verts, int64_t M, const int32_t* elems, int64_t K,
+                         const int8_t* elem_label, int ndof_per_node, void* stream, nlfem_mesh_t* out) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(out != nullptr, NLFEM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    NLFEM_CHECK(verts && elems, NLFEM_ERR_INVALID_ARG, "verts and elems must not be NULL");
+    NLFEM_CHECK(M >= 3 && K >= 1, NLFEM_ERR_INVALID_ARG, "need M >= 3 vertices and K >= 1 triangles");
+    NLFEM_CHECK(M < (1ll << 31) && K < (1ll << 31) / 3, NLFEM_ERR_UNSUPPORTED, "mesh too large for 32-bit indices");
+    NLFEM_CHECK(ndof_per_node == 1 || ndof_per_node == 2, NLFEM_ERR_INVALID_ARG, "ndof_per_node must be 1 or 2");
+    cudaStream_t st = (cudaStream_t)stream;
+    keep_pool_memory();
+    nlfem_mesh_s* h = new nlfem_mesh_s();
+    try {
+        Mesh& m = h->m;
+        m.K = K;
+        m.ndof = ndof_per_node;
+        DBuf<double2> X;
+        upload(X, verts, (size_t)M, st);
+        DBuf<int> T3;
+        upload(T3, elems, (size_t)(3 * K), st);
+        DBuf<int8_t> lab;
+        if (elem_label) upload(lab, elem_label, (size_t)K, st);
+        mesh_make_dg(m, X.p, M, T3.p, elem_label ? lab.p : nullptr, st);
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    *out = h;
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
 void nlfem_mesh_destroy(nlfem_mesh_t mesh) {
     if (!mesh) return;
     mesh->m.cache.reset();
@@ -389,6 +422,9 @@ static void attach_table(Params& P, const nlfem_params& p, DBuf<double>& t64, DB
 }
 
 static void attach_tables(System& S, const nlfem_params& p, const Mesh& m, cudaStream_t st) {
+    NLFEM_CHECK(!(m.dg && S.prm.singular), NLFEM_ERR_UNSUPPORTED,
+                "the singular rule needs a continuous ansatz (Sec. 2.3.2); on a discontinuous mesh use "
+                "the diamond or standard rule");
     attach_table(S.prm, p, S.tab64, S.tab32, st);
     if (p.n_materials <= 0) return;
     NLFEM_CHECK(m.mat.p && m.mat_max >= 0, NLFEM_ERR_INVALID_ARG,

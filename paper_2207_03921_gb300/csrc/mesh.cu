@@ -253,7 +253,8 @@ __global__ void k_max_seg(const int64_t* ptr, int64_t n, int* out) {
 
 int64_t Mesh::device_bytes() const {
     int64_t b = X.bytes() + T.bytes() + det.bytes() + lab.bytes() + dir.bytes() + ne_ptr.bytes() +
-                ne_idx.bytes() + cen.bytes() + rad.bytes() + E32.bytes() + det32.bytes() + rec.bytes();
+                ne_idx.bytes() + cen.bytes() + rad.bytes() + E32.bytes() + det32.bytes() + rec.bytes() +
+                Tpos.bytes() + mat.bytes();
     if (cache) {
         const PairCache& c = *cache;
         b += c.pair_ptr.bytes() + c.pk.bytes() + c.pl.bytes() + c.pcls.bytes() + c.pT_ptr.bytes() +
@@ -273,6 +274,53 @@ __global__ void k_orphans(const int64_t* cnt, int64_t M, int8_t* dir) {
 }
 
 // Upload done by the caller: m.X holds the vertices; T3_dev the raw triangles.
+// discontinuous ansatz: node 3k + a is a copy of vertex a of element k (as given)
+__global__ void k_dg_copy(const double2* X, const int* T3, int64_t K, int64_t M, double2* Xd, int* Td, int* orig,
+                          int* err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * K) return;
+    int v = T3[i];
+    if (v < 0 || v >= M) {
+        atomicOr(err, 1);
+        v = 0;
+    }
+    Xd[i] = X[v];
+    Td[i] = (int)i;
+    orig[i] = v;
+}
+
+// position triples of the (oriented) elements: the original vertex of every copy
+__global__ void k_dg_tpos(const int4* T, const int* orig, int64_t K, int4* Tpos) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int4 t = T[k];
+    Tpos[k] = make_int4(orig[t.x], orig[t.y], orig[t.z], 0);
+}
+
+void mesh_make_dg(Mesh& m, const double2* X_dev, int64_t M_in, const int* T3_dev, const int8_t* lab_dev,
+                  cudaStream_t st) {
+    const int64_t K = m.K;
+    m.M = 3 * K;
+    m.dg = true;
+    m.X.alloc(3 * K, st);
+    DBuf<int> Td, orig, err;
+    Td.alloc(3 * K, st);
+    orig.alloc(3 * K, st);
+    err.alloc(1, st);
+    err.zero(st);
+    k_dg_copy<<<nblk(3 * K, 256), 256, 0, st>>>(X_dev, T3_dev, K, M_in, m.X.p, Td.p, orig.p, err.p);
+    NLFEM_LAUNCH_CHECK();
+    int herr = 0;
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, st));
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    NLFEM_CHECK(!herr, NLFEM_ERR_BAD_MESH, "triangle vertex index out of range");
+    mesh_prepare(m, Td.p, lab_dev, st);
+    m.Tpos.alloc(K, st);
+    k_dg_tpos<<<nblk(K, 256), 256, 0, st>>>(m.T.p, orig.p, K, m.Tpos.p);
+    NLFEM_LAUNCH_CHECK();
+    NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
 void mesh_prepare(Mesh& m, const int* T3_dev, const int8_t* lab_dev, cudaStream_t st) {
     const int64_t K = m.K, M = m.M;
     m.T.alloc(K, st);

@@ -129,6 +129,11 @@ struct Mesh {
     DBuf<ElemRec> rec;    // packed element records [K]
     DBuf<double> rad;     // radii [K]
     DBuf<int8_t> mat;     // material labels of a label-dependent kernel [K] (empty: none)
+    // discontinuous ansatz: every element has its own copies of its vertices (nodes 3k + a);
+    // Tpos holds the original vertex ids, which classify the pairs (shared vertices as points)
+    bool dg = false;
+    DBuf<int4> Tpos;
+    const int4* tpos() const { return Tpos.p ? Tpos.p : T.p; }
     int mat_max = -1;     // largest material label
     std::shared_ptr<PairCache> cache;  // pair list, pattern and slot index of the last (delta, ball, rule)
     int64_t device_bytes() const;
@@ -273,6 +278,8 @@ struct System {
 // host-side entry points of the translation units
 // ------------------------------------------------------------------------------------------
 void mesh_prepare(Mesh& m, const int* T3_dev, const int8_t* lab_dev, cudaStream_t st);
+void mesh_make_dg(Mesh& m, const double2* X_dev, int64_t M_in, const int* T3_dev, const int8_t* lab_dev,
+                  cudaStream_t st);
 void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st);
 void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st);
 // ev[0..5] are recorded on st: [0, 1] around the close-list kernel (singular or diamond

@@ -64,12 +64,13 @@ struct SearchArgs {
     double delta, delta2;
     int caps;
     int ball;
+    const int4* Tp;  // vertex positions of the elements (shared vertices decide intersecting pairs)
     Rule ro;
 };
 
 __device__ bool interacts(const SearchArgs& a, int k, int l, int4 tk, const double2 Vk[3], double2 ck, double rk) {
     int4 tl = a.T[l];
-    if (shared_count(tk, tl) > 0) return true;
+    if (shared_count(a.Tp[k], a.Tp[l]) > 0) return true;
     const double2 cl = a.cen[l];
     const double rl = a.rad[l];
     const double cdx = cl.x - ck.x, cdy = cl.y - ck.y;
@@ -345,6 +346,7 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     a.cell_start = cstart.p; a.cell_list = clist.p; a.g = g; a.K = K;
     a.delta = prm.delta; a.delta2 = prm.delta2; a.caps = prm.ball == NLFEM_BALL_APPROXCAPS; a.ro = prm.ro;
     a.ball = prm.ball;
+    a.Tp = m.tpos();
     a.E32 = m.E32.p;
     for (int i = 0; i < 16; ++i) {
         a.ol[i][0] = i < prm.ro.n ? (float)prm.ro.l[i][1] : 0.f;
@@ -407,7 +409,7 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     tcount.alloc(K, st);
     tcount.zero(st);
     if (P) {
-        k_classify<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, P, m.T.p, pc.pcls.p, counts.p, tcount.p);
+        k_classify<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, P, m.tpos(), pc.pcls.p, counts.p, tcount.p);
         NLFEM_LAUNCH_CHECK();
     }
     pc.pT_ptr.alloc(K + 1, st);
@@ -728,6 +730,7 @@ extern "C" int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t
         a.X = X; a.T = T; a.cen = cen; a.rad = rad; a.cell_of = cell_of; a.cell_start = cstart; a.cell_list = clist;
         a.g = g; a.K = K; a.delta = delta; a.delta2 = delta * delta; a.caps = ball == NLFEM_BALL_APPROXCAPS;
         a.ball = ball;
+        a.Tp = T;
         a.ro.n = quad_outer;
         const double(*tab)[4] = quad_outer == 7 ? NLFEM_RULE7 : NLFEM_RULE16;
         for (int i = 0; i < 16; ++i) {

@@ -324,3 +324,53 @@ def test_label_dependent_kernel_matches_oracle(precision):
     fresh = Mesh.from_synth(m, ndof)
     with pytest.raises(NlfemError):
         assemble(fresh, precision=precision, material_scale=tab, **kw)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_dg_matches_oracle(precision):
+    # discontinuous P1 ansatz: the GPU mesh copies the vertices per element (node 3k + a), the
+    # oracle assembles the same copied mesh; pairs are classified by vertex positions
+    m = meshes.jittered_delaunay(-0.2, 1.2, 14, 0.05, seed=35)
+    d = meshes.discontinuous(m)
+    rng = np.random.default_rng(4)
+    for kw in (dict(kernel="constant", delta=0.25, ball="approxcaps"),
+               dict(kernel="peridynamic", delta=0.25, ball="nocaps"),
+               dict(kernel="tabulated", delta=0.25, ball="infinity", kernel_table=np.array([2.0, 1.0, 0.5]))):
+        ndof = 2 if kw["kernel"] == "peridynamic" else 1
+        f = rng.standard_normal(d.M * ndof)
+        ref = oracle.assemble(d, f_nodal=f, **kw)
+        mesh = Mesh.from_synth(m, ndof, dg=True)
+        S = assemble(mesh, precision=precision, f_nodal=f, **kw)
+        rp, col, val = check_fp64(S, ref) if precision == "fp64" else check_bulk(S, ref)
+        assert symmetric_bitwise(rp, col, val)
+        F = S.rhs().cpu().numpy()
+        assert np.abs(F - ref.F).max() <= 1e-12 * np.abs(ref.F).max()
+        assert np.array_equal(S.dirichlet().cpu().numpy().astype(bool), ref.dirichlet)
+    with pytest.raises(NlfemError):
+        assemble(Mesh.from_synth(m, 1, dg=True), kernel="fractional", s=0.5, delta=0.25, precision=precision)
+
+
+def test_paper_E4_peridynamic_dg_on_gpu():
+    """Sec. 3.2's DG table for bond-based peridynamics (delta = 0.1), assembled and solved on the
+    GPU on all five grids: second-order rates and the printed magnitudes."""
+    import json, math, os
+    tab = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+    tab = tab["E4_peridynamics_dg"]
+    errs = []
+    for a in tab["a"]:
+        m = meshes.paper_square(0.1, a)
+        d = meshes.discontinuous(m)
+        x, y = d.verts[:, 0], d.verts[:, 1]
+        f = -0.5 * math.pi * np.stack([1.0 + 2.0 * x, y], 1).reshape(-1)
+        g = np.stack([y * y, x * x * y], 1).reshape(-1)
+        S = assemble(Mesh.from_synth(m, 2, dg=True), kernel="peridynamic", delta=0.1, ball="approxcaps",
+                     precision="fp32_bulk", f_nodal=f)
+        u, info = S.solve(g, tol_rel=1e-10)
+        assert info["status"] == 0, info
+        ue = lambda x, y: np.stack([y * y, x * x * y])
+        errs.append(oracle.l2_error(d, u.cpu().numpy(), ue, ndof=2))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    for r in rates:
+        assert 1.7 < r < 2.4, (rates, errs)
+    for i, e in enumerate(errs):
+        assert 0.4 * tab["l2"][i] < e < 2.5 * tab["l2"][i], (errs, tab["l2"])
