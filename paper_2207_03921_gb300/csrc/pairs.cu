@@ -68,19 +68,43 @@ struct SearchArgs {
     Rule ro;
 };
 
-__device__ bool interacts(const SearchArgs& a, int k, int l, int4 tk, const double2 Vk[3], double2 ck, double rk) {
-    int4 tl = a.T[l];
-    if (shared_count(a.Tp[k], a.Tp[l]) > 0) return true;
+// Centroid tests of the candidate (k, l): 0 = not a partner, 1 = a partner, 2 = the cut of
+// E_l by the balls of E_k's outer points decides (interacts_clip).
+__device__ int interacts_centroid(const SearchArgs& a, int k, int l, double2 ck, double rk) {
+    if (shared_count(a.Tp[k], a.Tp[l]) > 0) return 1;
     const double2 cl = a.cen[l];
     const double rl = a.rad[l];
     const double cdx = cl.x - ck.x, cdy = cl.y - ck.y;
     if (a.ball == NLFEM_BALL_INFINITY) {
-        // infinity ball: centroid tests against the square's circumradius sqrt(2) delta and,
-        // for the whole element, its half side; then the canonical FP64 cut per outer point
+        // infinity ball: the square's circumradius sqrt(2) delta and, for the whole element,
+        // its half side
         const double dist = sqrt(cdx * cdx + cdy * cdy);
-        if (dist - rk - rl > a.delta * 1.4142135623730951 * (1.0 + 1e-9)) return false;
-        if (fmax(fabs(cdx), fabs(cdy)) + rk + rl <= a.delta * (1.0 - 1e-9)) return true;
-        const double2 Vl[3] = {a.X[tl.x], a.X[tl.y], a.X[tl.z]};
+        if (dist - rk - rl > a.delta * 1.4142135623730951 * (1.0 + 1e-9)) return 0;
+        if (fmax(fabs(cdx), fabs(cdy)) + rk + rl <= a.delta * (1.0 - 1e-9)) return 1;
+        return 2;
+    }
+    // decided in FP32 on squared distances when the margin (1e-5 relative, far above the FP32
+    // error of about 3e-7) allows, else by the FP64 expressions below
+    const float d2f = (float)cdx * (float)cdx + (float)cdy * (float)cdy;
+    const float far = (float)(rk + rl + a.delta * (1.0 + 1e-9));
+    const double inner = a.delta * (1.0 - 1e-9) - rk - rl;
+    const float nearf = inner > 0 ? (float)inner : -1.f;
+    if (d2f > far * far * (1.f + 1e-5f)) return 0;
+    if (nearf > 0.f && d2f < nearf * nearf * (1.f - 1e-5f)) return 1;  // E_l inside the ball of every x in E_k
+    if (d2f >= far * far * (1.f - 1e-5f) || (nearf > 0.f && d2f <= nearf * nearf * (1.f + 1e-5f))) {
+        const double dist = sqrt(cdx * cdx + cdy * cdy);
+        if (dist - rk - rl > a.delta * (1.0 + 1e-9)) return 0;
+        if (dist + rk + rl <= a.delta * (1.0 - 1e-9)) return 1;
+    }
+    return 2;
+}
+
+// The cut decides: some outer point x_p of E_k sees a polygon of >= 3 points.
+__device__ bool interacts_clip(const SearchArgs& a, int k, int l, const double2 Vk[3]) {
+    const int4 tl = a.T[l];
+    const double2 v0l = a.X[tl.x];
+    if (a.ball == NLFEM_BALL_INFINITY) {
+        const double2 Vl[3] = {v0l, a.X[tl.y], a.X[tl.z]};
         for (int p = 0; p < a.ro.n; ++p) {
             const double2 xp = nl_map(Vk, a.ro.l[p][0], a.ro.l[p][1], a.ro.l[p][2]);
             bool full;
@@ -88,28 +112,23 @@ __device__ bool interacts(const SearchArgs& a, int k, int l, int4 tk, const doub
         }
         return false;
     }
-    // centroid tests: decided in FP32 on squared distances when the margin (1e-5 relative,
-    // far above the FP32 error of about 3e-7) allows, else by the FP64 expressions below
-    const float d2f = (float)cdx * (float)cdx + (float)cdy * (float)cdy;
-    const float far = (float)(rk + rl + a.delta * (1.0 + 1e-9));
-    const double inner = a.delta * (1.0 - 1e-9) - rk - rl;
-    const float nearf = inner > 0 ? (float)inner : -1.f;
-    if (d2f > far * far * (1.f + 1e-5f)) return false;
-    if (nearf > 0.f && d2f < nearf * nearf * (1.f - 1e-5f)) return true;  // E_l inside the ball of every x in E_k
-    // within the margin of either threshold: the FP64 tests decide
-    if (d2f >= far * far * (1.f - 1e-5f) || (nearf > 0.f && d2f <= nearf * nearf * (1.f + 1e-5f))) {
-        const double dist = sqrt(cdx * cdx + cdy * cdy);
-        if (dist - rk - rl > a.delta * (1.0 + 1e-9)) return false;
-        if (dist + rk + rl <= a.delta * (1.0 - 1e-9)) return true;
-    }
     // FP32 geometry with exact decisions; the canonical FP64 clip only for near ties
-    const double2 v0l = a.X[tl.x];
     const float dx = (float)(v0l.x - Vk[0].x), dy = (float)(v0l.y - Vk[0].y);
     const float4 Ek = a.E32[k], El = a.E32[l];
     const float span = fabsf(dx) + fabsf(dy) + fabsf(Ek.x) + fabsf(Ek.y) + fabsf(Ek.z) + fabsf(Ek.w) +
                        fabsf(El.x) + fabsf(El.y) + fabsf(El.z) + fabsf(El.w);
     const float eps = 4.8e-7f * span, floor2 = 1e-5f * a.d2f;
     const float Wx[3] = {dx, dx + El.x, dx + El.z}, Wy[3] = {dy, dy + El.y, dy + El.w};
+    // a vertex of E_l strictly inside some ball: that polygon has the vertex and a point on
+    // each of its two edges, so >= 3 points
+    for (int p = 0; p < a.ro.n; ++p) {
+        const float Xx = a.ol[p][0] * Ek.x + a.ol[p][1] * Ek.z, Xy = a.ol[p][0] * Ek.y + a.ol[p][1] * Ek.w;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float rx = Wx[m] - Xx, ry = Wy[m] - Xy;
+            if (rx * rx + ry * ry - a.d2f < -(floor2 + 2.f * (fabsf(rx) + fabsf(ry)) * eps)) return true;
+        }
+    }
     for (int p = 0; p < a.ro.n; ++p) {
         const float Xx = a.ol[p][0] * Ek.x + a.ol[p][1] * Ek.z, Xy = a.ol[p][0] * Ek.y + a.ol[p][1] * Ek.w;
         float Rx[3], Ry[3], C[3];
@@ -136,7 +155,9 @@ __device__ bool interacts(const SearchArgs& a, int k, int l, int4 tk, const doub
 // SLOTS: write them at k * cap (cap = the largest candidate count) and count them, in one
 // pass; k_compact_slots then packs the slots.
 template <bool FILL, bool SLOTS = false>
-__global__ void k_search(SearchArgs a, int64_t* count, const int64_t* ptr, int* out_l, int64_t cap = 0) {
+__global__ void __launch_bounds__(128) k_search(SearchArgs a, int64_t* count, const int64_t* ptr, int* out_l,
+                                                int64_t cap = 0) {
+    __shared__ int s_queue[4 * 64];  // launched with 128 threads: 4 warps, 64 queue slots each
     int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (k >= a.K) return;
@@ -148,6 +169,26 @@ __global__ void k_search(SearchArgs a, int64_t* count, const int64_t* ptr, int* 
     int cx = cell % a.g.nx, cy = cell / a.g.nx;
     int64_t n = 0;
     int64_t base = SLOTS ? k * cap : (FILL ? ptr[k] : 0);
+    // candidates the centroid tests leave open wait in a per-warp queue and are cut 32 at a
+    // time with every lane busy (the partners' order does not matter: the lists are sorted)
+    int* q = s_queue + (threadIdx.x >> 5) * 64;
+    int qn = 0;  // warp-uniform
+    auto emit = [&](bool ok, int l) {
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if ((FILL || SLOTS) && ok) out_l[base + n + __popc(m & ((1u << lane) - 1u))] = l;
+        n += __popc(m);
+    };
+    auto drain = [&](int cnt) {  // cut the first cnt (<= 32) queued candidates, keep the rest
+        const int l = lane < cnt ? q[lane] : -1;
+        const bool ok = lane < cnt && interacts_clip(a, (int)k, l, Vk);
+        emit(ok, l);
+        const int rest = qn - cnt;
+        const int v = lane < rest ? q[cnt + lane] : 0;
+        __syncwarp();
+        if (lane < rest) q[lane] = v;
+        __syncwarp();
+        qn = rest;
+    };
     for (int dyc = -1; dyc <= 1; ++dyc) {
         int yy = cy + dyc;
         if (yy < 0 || yy >= a.g.ny) continue;
@@ -158,18 +199,22 @@ __global__ void k_search(SearchArgs a, int64_t* count, const int64_t* ptr, int* 
             int64_t s = a.cell_start[c], e = a.cell_start[c + 1];
             for (int64_t j0 = s; j0 < e; j0 += 32) {
                 int64_t j = j0 + lane;
-                bool ok = false;
+                int r = 0;
                 int l = -1;
                 if (j < e) {
                     l = a.cell_list[j];
-                    ok = interacts(a, (int)k, l, tk, Vk, ck, rk);
+                    r = interacts_centroid(a, (int)k, l, ck, rk);
                 }
-                unsigned m = __ballot_sync(0xffffffffu, ok);
-                if ((FILL || SLOTS) && ok) out_l[base + n + __popc(m & ((1u << lane) - 1u))] = l;
-                n += __popc(m);
+                emit(r == 1, l);
+                const unsigned mb = __ballot_sync(0xffffffffu, r == 2);
+                if (r == 2) q[qn + __popc(mb & ((1u << lane) - 1u))] = l;
+                qn += __popc(mb);
+                __syncwarp();
+                if (qn >= 32) drain(32);
             }
         }
     }
+    while (qn > 0) drain(qn < 32 ? qn : 32);
     if ((!FILL || SLOTS) && lane == 0) count[k] = n;
 }
 
