@@ -55,6 +55,13 @@ WORKLOADS = {
                    desc="Sec. 3.3 infinity-ball problem at its largest horizon: structured spacing 0.00625 on "
                         "[-0.2,0.7]^2 (41,472 triangles), constant kernel c=3/(4 delta^4), delta=0.2, "
                         "infinity norm ball cut exactly, 7-point rules"),
+    "inf_jit": dict(mesh="paper_e5_jit", kernel="constant", delta=0.2, ball="infinity", quad_outer=7, quad_inner=7,
+                    desc="the inf_e5 problem on a jittered Delaunay mesh (spacing 0.00625 on [-0.2,0.7]^2, "
+                         "3% jitter, about 41,500 triangles): infinity ball without grid-aligned sides"),
+    "inf_small": dict(mesh="paper_e5_small", kernel="constant", delta=0.1, ball="infinity", quad_outer=7,
+                      quad_inner=7,
+                      desc="Sec. 3.3 infinity-ball problem at delta=0.1: structured spacing 0.00625 on [-0.1,0.6]^2 "
+                           "(25,088 triangles), constant kernel c=3/(4 delta^4), infinity norm ball, 7-point rules"),
 }
 
 # algorithmic work per unit (FMA = 2 flops, a MUFU op = 1): the fixed weights of the
@@ -75,6 +82,10 @@ def make_mesh(name):
         return meshes.structured(-0.01, 1.01, 200, name="structured200")
     if name == "paper_e5":
         return meshes.paper_square(0.2, 0.00625)
+    if name == "paper_e5_jit":
+        return meshes.jittered_delaunay(-0.2, 0.7, 144, 0.03, seed=2207039216)
+    if name == "paper_e5_small":
+        return meshes.paper_square(0.1, 0.00625)
     return {"cfg720k": meshes.cfg720k_mesh, "cfg5": meshes.cfg5_mesh, "cfg2": meshes.cfg2_mesh,
             "cfg3": meshes.cfg3_mesh, "cfg1": meshes.cfg1_mesh}[name]()
 

@@ -221,6 +221,7 @@ struct PairCache {
     DBuf<int> up_row;        //   and row i (built with the slot index, for the ordered reduction)
     int64_t n_upper = 0;
     bool slots_built = false;
+    int sq32 = 1;  // infinity ball: few vertices on the squares' sides, the FP32 passes pay off
     // FP32-bulk accumulation index: upper entries numbered row by row in node order
     DBuf<int64_t> up_start;  // [M + 1] first upper entry of each node row
     DBuf<int> epos;          // [K * 6] upper entry of each node pair of an element

@@ -54,6 +54,7 @@ struct FastReq {
     float delta, d2, c, s;
     double delta64, delta2_64;
     int ball;     // NLFEM_BALL_*
+    int sq32;     // infinity ball: try the FP32 passes before the canonical cut
     int nmat;     // label-dependent kernel: factor msc[mat[k] * nmat + mat[l]] (0: none)
     const int8_t* mat;
     const float* msc;
@@ -405,6 +406,82 @@ __device__ __noinline__ int clip_square_f32(const double2* __restrict__ X, int4 
     return n < 7 ? n : 7;
 }
 
+// Infinity ball in FP32 with exact decisions: the canonical Sutherland-Hodgman passes
+// (x <= d, y <= d, x >= -d, y >= -d) on FP32 points that carry a bound e on the absolute
+// difference of both coordinates from the canonical FP64 values. An inside test is taken only
+// if its margin exceeds that bound (plus the rounding of delta and of the test itself), so
+// every decision equals the canonical one; with all decisions strict no two points coincide,
+// which is checked as well (two points closer than their bounds: undecided). Returns the
+// number of polygon points written to dst (0 = empty), or -1 when some decision is too close
+// to call (the caller then takes the canonical FP64 cut).
+__device__ __forceinline__ int sh_pass32(const float* ix, const float* iy, const float* ie, int n, int a, float s,
+                                         float d, float* ox, float* oy, float* oe, bool& ok) {
+    if (n == 0) return 0;
+    int m = 0;
+    float Sx = ix[n - 1], Sy = iy[n - 1], Se = ie[n - 1];
+    float Sa = a ? Sy : Sx;
+    float mS = s * Sa - d;  // > 0: outside
+    ok &= fabsf(mS) > Se + 2.4e-7f * (d + fabsf(Sa));
+    bool s_in = mS <= 0.f;
+    for (int i = 0; i < n; ++i) {
+        const float Ex = ix[i], Ey = iy[i], Ee = ie[i];
+        const float Ea = a ? Ey : Ex;
+        const float mE = s * Ea - d;
+        ok &= fabsf(mE) > Ee + 2.4e-7f * (d + fabsf(Ea));
+        const bool e_in = mE <= 0.f;
+        if (e_in != s_in) {
+            const float Sb = a ? Sx : Sy, Eb = a ? Ex : Ey;
+            const float num = s * d - Sa, den = Ea - Sa;
+            const float t = num / den;
+            const float db = Eb - Sb;
+            const float xb = fmaf(t, db, Sb);
+            // error: the ends' bounds, the slope times the error of t, the roundings
+            const float et = (Se + 1.2e-7f * (d + fabsf(Sa)) + t * (Se + Ee + 1.2e-7f * fabsf(den))) / fabsf(den) +
+                             2.4e-7f * t;
+            const float eb = Se + t * (Se + Ee) + et * fabsf(db) + 2.4e-7f * (fabsf(Sb) + fabsf(db));
+            const float e = fmaxf(eb, 1.2e-7f * d) * 1.5f;
+            if (m < 8) {
+                ox[m] = a ? xb : s * d;
+                oy[m] = a ? s * d : xb;
+                oe[m] = e;
+            }
+            ++m;
+        }
+        if (e_in) {
+            if (m < 8) {
+                ox[m] = Ex;
+                oy[m] = Ey;
+                oe[m] = Ee;
+            }
+            ++m;
+        }
+        Sx = Ex; Sy = Ey; Se = Ee; Sa = Ea; s_in = e_in;
+    }
+    return m < 8 ? m : 8;
+}
+
+__device__ __noinline__ int clip_square_fast(const float Rx[3], const float Ry[3], float eps, float d, float2* dst) {
+    float Ax[8], Ay[8], Ae[8], Bx[8], By[8], Be[8];
+    for (int v = 0; v < 3; ++v) {
+        Ax[v] = Rx[v];
+        Ay[v] = Ry[v];
+        Ae[v] = eps;
+    }
+    bool ok = true;
+    int n = sh_pass32(Ax, Ay, Ae, 3, 0, 1.f, d, Bx, By, Be, ok);
+    n = sh_pass32(Bx, By, Be, n, 1, 1.f, d, Ax, Ay, Ae, ok);
+    n = sh_pass32(Ax, Ay, Ae, n, 0, -1.f, d, Bx, By, Be, ok);
+    n = sh_pass32(Bx, By, Be, n, 1, -1.f, d, Ax, Ay, Ae, ok);
+    if (!ok || n > 7) return -1;
+    for (int i = 0; i < n; ++i) {  // no two consecutive points may coincide (all decisions strict)
+        const int j = i + 1 < n ? i + 1 : 0;
+        if (n > 1 && fabsf(Ax[i] - Ax[j]) + fabsf(Ay[i] - Ay[j]) <= 2.f * (Ae[i] + Ae[j])) return -1;
+    }
+    if (n < 3) return 0;
+    for (int i = 0; i < n; ++i) dst[i * FAST_THREADS] = make_float2(Ax[i], Ay[i]);
+    return n;
+}
+
 // Cut pairs: the outer points are processed in chunks of CHUNK. Phase A sets up every
 // outer point of the chunk in lockstep across the warp (decisions, polygon points relative
 // to x_p into shared memory; 4 bits per outer point record the number of points). Phase B
@@ -509,7 +586,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                         const float Xy = R.ol[q0][1] * Ek.y + R.ol[q0][2] * Ek.w;
                         const float Rx[3] = {W0x - Xx, W1x - Xx, W2x - Xx}, Ry[3] = {W0y - Xy, W1y - Xy, W2y - Xy};
                         const float lo = Q.delta - eps - 1e-6f * Q.delta, hi = Q.delta + eps + 1e-6f * Q.delta;
-                        bool allin = true;
+                        bool allin = true, tie = false;
                         int oxp = 0, oxm = 0, oyp = 0, oym = 0;
 #pragma unroll
                         for (int m = 0; m < 3; ++m) {
@@ -518,13 +595,23 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                             oxm += Rx[m] < -hi;
                             oyp += Ry[m] > hi;
                             oym += Ry[m] < -hi;
+                            tie |= (fabsf(Rx[m]) >= lo && fabsf(Rx[m]) <= hi) || (fabsf(Ry[m]) >= lo && fabsf(Ry[m]) <= hi);
                         }
                         if (allin) {
 #pragma unroll
                             for (int m = 0; m < 3; ++m) put(q, m, Rx[m], Ry[m]);
                             n = 3;
                         } else if (oxp < 3 && oxm < 3 && oyp < 3 && oym < 3) {
-                            need |= 1u << q;
+                            // a vertex on a side of the square goes to the canonical cut at once, and
+                            // so does every open cut on meshes whose grid lines the square's sides
+                            // follow (Q.sq32 = 0: the FP32 passes would mostly end undecided); the
+                            // others try the FP32 passes first
+                            n = (tie || !Q.sq32) ? -1
+                                                 : clip_square_fast(Rx, Ry, eps, Q.delta, my + q * MAXP * FAST_THREADS);
+                            if (n < 0) {
+                                n = 0;
+                                need |= 1u << q;
+                            }
                         }
                     }
                     counts |= (unsigned long long)n << (4 * q);
@@ -668,7 +755,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
 
 // Fan triangles of a cut pair summed over its outer points, from the same FP32 decisions
 // (an undecided outer point counts its FP32 outcome; the count only orders the work).
-__global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key) {
+__global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key, unsigned long long* ties) {
     const int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pi >= Q.npairs) return;
     const int64_t p = Q.ids[pi];
@@ -682,13 +769,20 @@ __global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key) {
     int tris = 0;
     if (Q.ball == NLFEM_BALL_INFINITY) {  // the canonical cut (the cut kernel uses it too)
         const double2 Vk[3] = {v0k, Q.X[tk.y], Q.X[tk.z]}, Vl[3] = {v0l, Q.X[tl.y], Q.X[tl.z]};
+        unsigned long long nt = 0;  // outer points with a vertex on a side of the square
         for (int q0 = 0; q0 < nqo; ++q0) {
+            const double2 xp = nl_map(Vk, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2]);
             bool full;
-            const int n = nl_clip_square(Vl, nl_map(Vk, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2]), Q.delta64, nullptr,
-                                         full);
+            const int n = nl_clip_square(Vl, xp, Q.delta64, nullptr, full);
             tris += n >= 3 ? n - 2 : 0;
+            bool tie = false;
+            for (int v = 0; v < 3; ++v)
+                tie |= fabs(fabs(Vl[v].x - xp.x) - Q.delta64) <= 1e-9 * Q.delta64 ||
+                       fabs(fabs(Vl[v].y - xp.y) - Q.delta64) <= 1e-9 * Q.delta64;
+            nt += tie;
         }
         key[pi] = tris;
+        atomicAdd(ties, nt);
         return;
     }
     for (int q0 = 0; q0 < nqo; ++q0) {
@@ -828,6 +922,7 @@ FastReq make_req(Mesh& m, PairCache& pc, const Params& prm, int list) {
     q.delta64 = prm.delta;
     q.delta2_64 = prm.delta2;
     q.ball = prm.ball;
+    q.sq32 = pc.sq32;
     q.nmat = prm.nmat;
     q.mat = prm.mat;
     q.msc = prm.msc32;
@@ -854,8 +949,19 @@ void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st)
     const FastReq q = make_req(m, pc, prm, 1);
     DBuf<int> key;
     key.alloc(n, st);
-    k_cut_tris<<<nblk(n, 256), 256, 0, st>>>(r, q, key.p);
+    DBuf<unsigned long long> ties;
+    ties.alloc(1, st);
+    ties.zero(st);
+    k_cut_tris<<<nblk(n, 256), 256, 0, st>>>(r, q, key.p, ties.p);
     NLFEM_LAUNCH_CHECK();
+    if (prm.ball == NLFEM_BALL_INFINITY) {
+        // when more than a quarter of the cut outer points have a vertex on a side of the square
+        // (grids aligned with the square), the FP32 passes mostly end undecided: skip them
+        unsigned long long h = 0;
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, ties.p, sizeof h, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        pc.sq32 = (double)h <= 0.25 * (double)n * prm.ro.n;
+    }
     k_window_key<<<nblk(n, 256), 256, 0, st>>>(key.p, n, WBITS);
     NLFEM_LAUNCH_CHECK();
     const int64_t nwin = (n + W - 1) / W;
