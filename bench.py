@@ -422,7 +422,8 @@ def main():
     flops_whole = census["evals_whole"] * fpe + (census["evals_whole"] // nqi) * FLOPS_PER_OUTER
     flops_cut = (census["evals_cut"] * fpe + census["nonempty_points_cut"] * FLOPS_PER_OUTER
                  + census["outer_points_cut"] * FLOPS_VERTEX_TESTS
-                 + census["cut_points_cut"] * (FLOPS_EDGES + (FLOPS_CAPS if wl["ball"] == "approxcaps" else 0))
+                 + census["cut_points_cut"] * (0 if wl["ball"] == "infinity" else
+                                               FLOPS_EDGES + (FLOPS_CAPS if wl["ball"] == "approxcaps" else 0))
                  + census["subtri_evals_cut"] * FLOPS_SUBTRI_POINT)
     flops_duffy = census["duffy_points"] * FLOPS_DUFFY_POINT
     nc = 1 if ndof == 1 else 3
@@ -448,6 +449,10 @@ def main():
                               "achieved": rate(flops_duffy, ms_close, 1e12), "peak": fp64_peak, "unit": "TFLOP/s"}
     for k in kernels.values():
         k["frac"] = k["achieved"] / k["peak"]
+    if wl["ball"] == "infinity":
+        kernels["k_trunc_cut"]["note"] = ("FP32 quadrature work only: the square's Sutherland-Hodgman cut runs in "
+                                          "FP32 with exact decisions or, near ties, in FP64 (FP64-pipe bound on "
+                                          "grids aligned with the square)")
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     peak_src = {"alu": "derived: 152 SMs x (128 FP32 | 2 FP64) lanes x 2 x max SM clock",
