@@ -248,7 +248,7 @@ __global__ void k_i64_to_i32(const int64_t* a, int* b, int64_t n) {
 
 __global__ void k_max_seg(const int64_t* ptr, int64_t n, int* out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicMax(out, (int)(ptr[i + 1] - ptr[i]));
+    warp_atomic_max(out, i < n ? (int)(ptr[i + 1] - ptr[i]) : 0);
 }
 
 int64_t Mesh::device_bytes() const {

@@ -182,6 +182,19 @@ __device__ __forceinline__ R table_g(const R* __restrict__ tab, int n, R tinv, R
     return ((R)1 - w) * tab[i] + w * tab[i + 1];
 }
 
+// maximum of v over the warp, then one atomicMax per warp (every lane of the warp must call it)
+__device__ __forceinline__ void warp_atomic_max(int* out, int v) {
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+}
+__device__ __forceinline__ void warp_atomic_max(unsigned long long* out, unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+}
+
 // kernel factor of the ordered pair (k, l) for label-dependent kernels
 __device__ __forceinline__ double pair_factor64(const Params& P, int k, int l) {
     return P.nmat ? P.msc64[P.mat[k] * P.nmat + P.mat[l]] : 1.0;

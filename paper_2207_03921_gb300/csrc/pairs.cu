@@ -222,16 +222,17 @@ __global__ void __launch_bounds__(128) k_search(SearchArgs a, int64_t* count, co
 __global__ void k_max_cand(const int* cell_of, int64_t K, Grid g, const int64_t* cell_start,
                            unsigned long long* out) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    const int cell = cell_of[k];
-    const int cx = cell % g.nx, cy = cell / g.nx;
     int64_t n = 0;
-    for (int yy = max(cy - 1, 0); yy <= min(cy + 1, g.ny - 1); ++yy)
-        for (int xx = max(cx - 1, 0); xx <= min(cx + 1, g.nx - 1); ++xx) {
-            const int c = yy * g.nx + xx;
-            n += cell_start[c + 1] - cell_start[c];
-        }
-    atomicMax(out, (unsigned long long)n);
+    if (k < K) {
+        const int cell = cell_of[k];
+        const int cx = cell % g.nx, cy = cell / g.nx;
+        for (int yy = max(cy - 1, 0); yy <= min(cy + 1, g.ny - 1); ++yy)
+            for (int xx = max(cx - 1, 0); xx <= min(cx + 1, g.nx - 1); ++xx) {
+                const int c = yy * g.nx + xx;
+                n += cell_start[c + 1] - cell_start[c];
+            }
+    }
+    warp_atomic_max(out, (unsigned long long)n);
 }
 
 // pack the per-element slots into the pair list (warp per element, order kept)
@@ -335,8 +336,8 @@ __global__ void k_compact_duffy(const int64_t* flag, const int64_t* pos, int64_t
 }
 
 __global__ void k_max_seg64(const int64_t* ptr, int64_t n, unsigned long long* out) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicMax(out, (unsigned long long)(ptr[i + 1] - ptr[i]));
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    warp_atomic_max(out, i < n ? (unsigned long long)(ptr[i + 1] - ptr[i]) : 0ull);
 }
 
 int64_t max_segment_i64(const int64_t* ptr, int64_t n, cudaStream_t st) {

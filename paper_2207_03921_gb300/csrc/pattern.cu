@@ -560,7 +560,7 @@ __global__ void k_upper_fill(const int64_t* nptr, const int* ncol, int64_t M, co
 
 __global__ void k_row_max(const int64_t* ptr, int64_t n, int* out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicMax(out, (int)(ptr[i + 1] - ptr[i]));
+    warp_atomic_max(out, i < n ? (int)(ptr[i + 1] - ptr[i]) : 0);
 }
 
 void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
@@ -817,7 +817,7 @@ __global__ void k_klr(const int* __restrict__ ids, int64_t n, const int* __restr
 
 __global__ void k_max_deg(const int* ne_ptr, int64_t M, int* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < M) atomicMax(out, ne_ptr[i + 1] - ne_ptr[i]);
+    warp_atomic_max(out, i < M ? ne_ptr[i + 1] - ne_ptr[i] : 0);
 }
 
 void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st) {

@@ -89,3 +89,47 @@ def test_autotune_keeps_results():
     assert all(b in (2, 4, 8, 16, 32, 64) for b in best)
     after = assemble(mesh, **kw).csr()[2].cpu().numpy()
     assert np.array_equal(before, after)
+
+
+def _items_extended():
+    """Infinity ball (FP32 cut passes on a jittered mesh, FP64 on a grid the square follows), a
+    tabulated user kernel, a discontinuous peridynamic mesh and a label-dependent kernel."""
+    jm = meshes.jittered_delaunay(-0.2, 1.2, 22, 0.05, seed=41)
+    sm = meshes.structured(-0.2, 1.2, 28, name="s28")
+    c = jm.verts[jm.elems].mean(1)
+    mat = (c[:, 0] > 0.5).astype(np.int8)
+    return [
+        (jm, 1, dict(kernel="constant", delta=0.15, ball="infinity", precision="fp32_bulk"), {}),
+        (sm, 1, dict(kernel="constant", delta=0.1, ball="infinity", precision="fp32_bulk"), {}),
+        (jm, 1, dict(kernel="tabulated", delta=0.15, ball="approxcaps", precision="fp32_bulk",
+                     kernel_table=np.array([1.0, 0.7, 0.2])), {}),
+        (sm, 2, dict(kernel="peridynamic", delta=0.15, ball="nocaps", precision="fp32_bulk"), {"dg": True}),
+        (jm, 1, dict(kernel="constant", delta=0.15, ball="nocaps", precision="fp32_bulk",
+                     material_scale=np.array([[1.0, 0.4], [0.4, 2.5]])), {"mat": mat}),
+    ]
+
+
+def _mesh(m, nd, extra):
+    mesh = Mesh.from_synth(m, nd, dg=extra.get("dg", False))
+    if "mat" in extra:
+        mesh.set_materials(extra["mat"])
+    return mesh
+
+
+def test_batch_and_graph_with_infinity_ball_dg_and_user_kernels():
+    items = _items_extended()
+    fs = [np.linspace(-1.0, 1.0, _mesh(m, nd, ex).M * nd) for m, nd, _, ex in items]
+    single = [_host(assemble(_mesh(m, nd, ex), f_nodal=f, **kw)) for (m, nd, kw, ex), f in zip(items, fs)]
+    ms = [_mesh(m, nd, ex) for m, nd, _, ex in items]
+    systems = assemble_batch(ms, [kw for _, _, kw, _ in items], fs)
+    for (rp0, col0, val0, F0), S in zip(single, systems):
+        rp, col, val, F = _host(S)
+        assert np.array_equal(rp, rp0) and np.array_equal(col, col0)
+        assert np.array_equal(val, val0) and np.array_equal(F, F0)
+    from paper_2207_03921_gb300 import BatchPlan
+    plan = BatchPlan([_mesh(m, nd, ex) for m, nd, _, ex in items], [kw for _, _, kw, _ in items], fs)
+    for rep in range(2):
+        plan.run()
+        for (rp0, col0, val0, F0), S in zip(single, plan.systems):
+            rp, col, val, F = _host(S)
+            assert np.array_equal(val, val0) and np.array_equal(F, F0)
