@@ -115,9 +115,87 @@ __global__ void k_segsort(int* keys, int* vals, const int64_t* ptr, int cap) {
     }
 }
 
+// Short segments (up to 32 * NPL keys): one warp per segment, bitonic network in registers.
+// Element e of the padded segment sits in lane e % 32, register e / 32; compare-exchanges
+// at strides below 32 go through shuffles, the others stay inside a lane.
+template <bool WITH_VALS, int NPL>
+__global__ void __launch_bounds__(256) k_segsort_warp(int* keys, int* vals, const int64_t* ptr, int64_t nseg) {
+    const int64_t sg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sg >= nseg) return;  // whole warps
+    const int64_t b = ptr[sg];
+    const int len = (int)(ptr[sg + 1] - b);
+    if (len <= 1) return;
+    int v[NPL], w[NPL];
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int e = i * 32 + lane;
+        v[i] = e < len ? keys[b + e] : INT_MAX;
+        if (WITH_VALS) w[i] = e < len ? vals[b + e] : 0;
+    }
+#pragma unroll
+    for (int size = 2; size <= 32 * NPL; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int s = stride >> 5;
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    if (i & s) continue;
+                    const int j = i | s;
+                    const bool up = ((i * 32 + lane) & size) == 0;
+                    if ((v[i] > v[j]) == up) {
+                        const int t = v[i]; v[i] = v[j]; v[j] = t;
+                        if (WITH_VALS) { const int u = w[i]; w[i] = w[j]; w[j] = u; }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const int e = i * 32 + lane;
+                    const int pv = __shfl_xor_sync(0xffffffffu, v[i], stride);
+                    const int pw = WITH_VALS ? __shfl_xor_sync(0xffffffffu, w[i], stride) : 0;
+                    const bool up = (e & size) == 0, lower = (e & stride) == 0;
+                    // the lower element keeps the smaller key on an ascending run; ties keep the
+                    // lower element's own pair so that equal keys never duplicate a value
+                    const bool take = lower == up ? (pv < v[i]) : (pv > v[i]);
+                    if (take) {
+                        v[i] = pv;
+                        if (WITH_VALS) w[i] = pw;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int e = i * 32 + lane;
+        if (e < len) {
+            keys[b + e] = v[i];
+            if (WITH_VALS) vals[b + e] = w[i];
+        }
+    }
+}
+
+template <bool WITH_VALS>
+static void segsort_warp(int* keys, int* vals, const int64_t* ptr, int64_t nseg, int max_len, cudaStream_t st) {
+    const unsigned grid = (unsigned)((nseg * 32 + 255) / 256);
+    if (max_len <= 32) k_segsort_warp<WITH_VALS, 1><<<grid, 256, 0, st>>>(keys, vals, ptr, nseg);
+    else if (max_len <= 64) k_segsort_warp<WITH_VALS, 2><<<grid, 256, 0, st>>>(keys, vals, ptr, nseg);
+    else if (max_len <= 128) k_segsort_warp<WITH_VALS, 4><<<grid, 256, 0, st>>>(keys, vals, ptr, nseg);
+    else if (max_len <= 256) k_segsort_warp<WITH_VALS, 8><<<grid, 256, 0, st>>>(keys, vals, ptr, nseg);
+    else k_segsort_warp<WITH_VALS, 16><<<grid, 256, 0, st>>>(keys, vals, ptr, nseg);
+    NLFEM_LAUNCH_CHECK();
+}
+
 void segmented_sort_i32(int* keys, int* vals, const int64_t* ptr, int64_t nseg, int max_len,
                         cudaStream_t st) {
     if (nseg <= 0 || max_len <= 1) return;
+    if (max_len <= 512) {  // every segment fits one warp's registers
+        if (vals) segsort_warp<true>(keys, vals, ptr, nseg, max_len, st);
+        else segsort_warp<false>(keys, nullptr, ptr, nseg, max_len, st);
+        return;
+    }
     // the whole segment sits in shared memory: 128 KB of keys (and values)
     const int limit = vals ? 16384 : 32768;
     NLFEM_CHECK(max_len <= limit, NLFEM_ERR_UNSUPPORTED,
