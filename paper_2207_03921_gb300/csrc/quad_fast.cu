@@ -817,9 +817,10 @@ __global__ void k_window_ptr(int64_t* ptr, int64_t nwin, int64_t n, int w) {
 
 // Pairs with E_l inside the ball of every point of E_k: the whole inner element at every
 // outer point, no geometry at all.
+// Scalar kernels with the 7-point inner rule fit 80 registers without spills: 6 blocks per SM.
 template <int KER, int NQI, bool BATCH>
-__global__ void __launch_bounds__(FAST_THREADS) k_trunc_whole(const __grid_constant__ FastRule R,
-                                                             const __grid_constant__ FastLaunch L) {
+__global__ void __launch_bounds__(FAST_THREADS, (KER != NLFEM_KERNEL_PERIDYNAMIC && !BATCH && NQI == 7) ? 6 : 1)
+    k_trunc_whole(const __grid_constant__ FastRule R, const __grid_constant__ FastLaunch L) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
     __shared__ FastReq sq[BATCH ? FAST_WARPS : 1];
     const int nqo = R.nqo;
