@@ -70,8 +70,9 @@ struct SearchArgs {
 
 // Centroid tests of the candidate (k, l): 0 = not a partner, 1 = a partner, 2 = the cut of
 // E_l by the balls of E_k's outer points decides (interacts_clip).
+// Elements sharing a vertex have centroids at most rk + rl apart, so the far tests come first
+// and the vertex triples are read only for the candidates that pass them.
 __device__ int interacts_centroid(const SearchArgs& a, int k, int l, double2 ck, double rk) {
-    if (shared_count(a.Tp[k], a.Tp[l]) > 0) return 1;
     const double2 cl = a.cen[l];
     const double rl = a.rad[l];
     const double cdx = cl.x - ck.x, cdy = cl.y - ck.y;
@@ -80,6 +81,7 @@ __device__ int interacts_centroid(const SearchArgs& a, int k, int l, double2 ck,
         // its half side
         const double dist = sqrt(cdx * cdx + cdy * cdy);
         if (dist - rk - rl > a.delta * 1.4142135623730951 * (1.0 + 1e-9)) return 0;
+        if (shared_count(a.Tp[k], a.Tp[l]) > 0) return 1;
         if (fmax(fabs(cdx), fabs(cdy)) + rk + rl <= a.delta * (1.0 - 1e-9)) return 1;
         return 2;
     }
@@ -90,6 +92,7 @@ __device__ int interacts_centroid(const SearchArgs& a, int k, int l, double2 ck,
     const double inner = a.delta * (1.0 - 1e-9) - rk - rl;
     const float nearf = inner > 0 ? (float)inner : -1.f;
     if (d2f > far * far * (1.f + 1e-5f)) return 0;
+    if (shared_count(a.Tp[k], a.Tp[l]) > 0) return 1;
     if (nearf > 0.f && d2f < nearf * nearf * (1.f - 1e-5f)) return 1;  // E_l inside the ball of every x in E_k
     if (d2f >= far * far * (1.f - 1e-5f) || (nearf > 0.f && d2f <= nearf * nearf * (1.f + 1e-5f))) {
         const double dist = sqrt(cdx * cdx + cdy * cdy);
