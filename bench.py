@@ -170,13 +170,20 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """The largest x over the ranks (the slowest replica's time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(units_per_rank, ws, ms_max):
+    """Whole-job throughput of ws independent replicas: all ranks' units over the slowest time."""
+    return units_per_rank * ws / (ms_max * 1e-3)
 
 
 def time_steps(fn, steps, warmup, ws, stream):
@@ -355,7 +362,7 @@ def main():
         ms, _ = time_steps(step, args.steps, args.warmup, ws, stream)
     timed = infos[args.warmup:]
     ms_step = ms / args.steps
-    value = npairs * ws / (ms_step * 1e-3)
+    value = replica_value(npairs, ws, ms_step)
     quad_ms = statistics.mean(i["ms_quadrature"] for i in timed)
     red_ms = statistics.mean(i["ms_reduce"] for i in timed)
 
@@ -401,7 +408,7 @@ def main():
         return None
 
     e2e_ms, _ = time_steps(e2e_step, e2e_steps, 1, ws, stream)
-    e2e_value = npairs * ws / (e2e_ms / e2e_steps * 1e-3)
+    e2e_value = replica_value(npairs, ws, e2e_ms / e2e_steps)
 
     # roofline of the dominant kernel: the longest of the bulk quadrature kernels (FP32 ALU),
     # the close-list kernel (FP64 ALU, singular rule), the per-element sums and the conversion
