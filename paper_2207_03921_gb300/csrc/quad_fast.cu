@@ -164,11 +164,12 @@ __device__ __forceinline__ void tri_quad(const FastRule& R, const FastReq& Q, In
 }
 
 // kk += a_p g P P^T, kl -= a_p P h^T, ll += a_p m for outer point q0 (P = its barycentrics)
+// o = (l0, l1, l2, w) of the outer point
 template <int NC>
-__device__ __forceinline__ void outer_update(const FastRule& R, int q0, float dk, const Inner<NC>& I,
-                                             float (&kk)[6][NC], float (&kl)[9][NC], float (&ll)[6][NC]) {
-    const float ap = R.ow[q0] * dk;
-    const float Pa[3] = {R.ol[q0][0], R.ol[q0][1], R.ol[q0][2]};
+__device__ __forceinline__ void outer_update(float4 o, float dk, const Inner<NC>& I, float (&kk)[6][NC],
+                                             float (&kl)[9][NC], float (&ll)[6][NC]) {
+    const float ap = o.w * dk;
+    const float Pa[3] = {o.x, o.y, o.z};
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const float ag = ap * I.g[c];
@@ -508,6 +509,10 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
     __shared__ int4 s_tk[SQUARE ? FAST_THREADS : 1], s_tl[SQUARE ? FAST_THREADS : 1];
     __shared__ unsigned char s_job[SQUARE ? FAST_WARPS * 32 * CHUNK : 1];
     __shared__ unsigned char s_cnt[SQUARE ? FAST_THREADS * CHUNK : 1];
+    __shared__ float4 s_orule[16];  // outer rule (l0, l1, l2, w)
+    for (int i = threadIdx.x; i < 16; i += blockDim.x)
+        s_orule[i] = make_float4(R.ol[i][0], R.ol[i][1], R.ol[i][2], R.ow[i]);
+    __syncthreads();
     const int nqo = R.nqo;
     const bool pilot = L.pilot > 0;
     const int warp = threadIdx.x >> 5;
@@ -714,7 +719,10 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
             while (__any_sync(0xffffffffu, qc < qn)) {
                 if (qc < qn) {
                     const int q0 = qb + qc;
-                    const float l1o = R.ol[q0][1], l2o = R.ol[q0][2];
+                    // lanes sit at different outer points here: the rule comes from shared memory
+                    // (a parameter-space read at per-lane indices would serialise)
+                    const float4 orule = s_orule[q0];
+                    const float l1o = orule.y, l2o = orule.z;
                     // x_p - v0_l, for the barycentric coordinates of the points
                     const float Bx = l1o * Ek.x + l2o * Ek.z - W0x, By = l1o * Ek.y + l2o * Ek.w - W0y;
                     float px[3], py[3], b1[3], b2[3];
@@ -739,7 +747,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                     }
                     tri_quad<KER, NQI, NC>(R, Q, I, px[0], py[0], b1[0], b2[0], px[1], py[1], b1[1], b2[1], px[2], py[2],
                                            b1[2], b2[2]);
-                    outer_update<NC>(R, q0, dk, I, kk, kl, ll);
+                    outer_update<NC>(orule, dk, I, kk, kl, ll);
                     if (++sc >= (int)((counts >> (4 * qc)) & 15)) {
                         sc = 2;
                         ++qc;
@@ -884,7 +892,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (KER != NLFEM_KERNEL_PERIDYNAMIC
                 }
                 tri_quad<KER, NQI, NC>(R, Q, I, dx - Xx, dy - Xy, 0.f, 0.f, dx + El.x - Xx, dy + El.y - Xy, 1.f, 0.f,
                                        dx + El.z - Xx, dy + El.w - Xy, 0.f, 1.f);
-                outer_update<NC>(R, q0, dk, I, kk, kl, ll);
+                outer_update<NC>(make_float4(R.ol[q0][0], R.ol[q0][1], R.ol[q0][2], R.ow[q0]), dk, I, kk, kl, ll);
             }
             accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, upos, kk, kl, ll, vmax, k, l);
         }
