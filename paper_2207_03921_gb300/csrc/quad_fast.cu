@@ -100,18 +100,21 @@ __device__ __forceinline__ void tri_quad(const FastRule& R, const FastReq& Q, In
     // the basis functions sum to one (Q0 = 1 - Q1 - Q2), so per point only the sums of w,
     // w Q1, w Q2, w Q1^2, w Q1 Q2 and w Q2^2 are formed; h0 and the m entries with Q0 follow
     // from them per triangle (the same quadrature sums, rearranged)
+    // the weights' common factor |det| c of the triangle is applied once to the six sums; the
+    // basis values are interpolated from vertex a along the two edge differences
     float g[NC], h1[NC], h2[NC], m11[NC], m12[NC], m22[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) g[c] = h1[c] = h2[c] = m11[c] = m12[c] = m22[c] = 0.f;
+    const float d1b = b1 - a1, d1c = c1 - a1, d2b = b2 - a2, d2c = c2 - a2;
 #pragma unroll
     for (int q = 0; q < NQI; ++q) {
         const float l0 = R.il[q][0], l1 = R.il[q][1], l2 = R.il[q][2];
-        const float Q1 = l0 * a1 + l1 * b1 + l2 * c1;
-        const float Q2 = l0 * a2 + l1 * b2 + l2 * c2;
-        const float wq = R.iw[q] * dT;
+        const float Q1 = fmaf(l2, d1c, fmaf(l1, d1b, a1));
+        const float Q2 = fmaf(l2, d2c, fmaf(l1, d2b, a2));
+        const float wq = R.iw[q];
         float wc[NC];
         if (KER == NLFEM_KERNEL_CONSTANT) {
-            wc[0] = wq * Q.c;
+            wc[0] = wq;
         } else {
             const float zx = l0 * ax + l1 * bx + l2 * cx;
             const float zy = l0 * ay + l1 * by + l2 * cy;
@@ -119,15 +122,15 @@ __device__ __forceinline__ void tri_quad(const FastRule& R, const FastReq& Q, In
             if (KER == NLFEM_KERNEL_FRACTIONAL) {
                 if (Q.s == 0.5f) {
                     const float r = rsqrtf(r2);
-                    wc[0] = wq * Q.c * r * r * r;
+                    wc[0] = wq * r * r * r;
                 } else {
-                    wc[0] = wq * Q.c * exp2f(log2f(r2) * (-1.f - Q.s));
+                    wc[0] = wq * exp2f(log2f(r2) * (-1.f - Q.s));
                 }
             } else if (KER == NLFEM_KERNEL_TABULATED) {
-                wc[0] = wq * Q.c * table_g<float>(Q.tab, Q.ntab, Q.tinv, r2);
+                wc[0] = wq * table_g<float>(Q.tab, Q.ntab, Q.tinv, r2);
             } else {
                 const float r = rsqrtf(r2);
-                const float sc = wq * Q.c * r * r * r;
+                const float sc = wq * r * r * r;
                 wc[0] = sc * zx * zx;
                 wc[1 % NC] = sc * zx * zy;
                 wc[2 % NC] = sc * zy * zy;
@@ -145,8 +148,15 @@ __device__ __forceinline__ void tri_quad(const FastRule& R, const FastReq& Q, In
             m22[c] += w2 * Q2;
         }
     }
+    const float f = dT * Q.c;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
+        g[c] *= f;
+        h1[c] *= f;
+        h2[c] *= f;
+        m11[c] *= f;
+        m12[c] *= f;
+        m22[c] *= f;
         const float h0 = g[c] - h1[c] - h2[c];
         const float m01 = h1[c] - m11[c] - m12[c];
         const float m02 = h2[c] - m12[c] - m22[c];
