@@ -368,11 +368,11 @@ __device__ __forceinline__ bool decide_flat(const float Rx[3], const float Ry[3]
         const float bound = 2.f * fabsf(Bq) * (u1n + 2.f * e1n) * eps + Aq * (2.f * e1n * eps + 1e-6f * d2) +
                             fabsf(Cq) * 4.f * u1n * eps + 1e-6f * (Bq * Bq + fabsf(Aq * Cq));
         ok &= !(out2 && fabsf(disc) <= bound);
-        // stable roots; qq != 0 whenever a crossing exists (disc > 0)
+        // roots (-B -+ sqrt(disc)) / A: near a root at 0 the cancellation leaves an absolute error
+        // of about eps |R| in the crossing point, the size of the coordinates' own error
         const float sq = sqrtf(fmaxf(disc, 0.f));
-        const float qq = -(Bq + copysignf(sq, Bq));
-        const float r1 = __fdividef(qq, Aq), r2 = __fdividef(Cq, qq);
-        const float lo = fminf(r1, r2), hi = fmaxf(r1, r2);
+        const float iA = __fdividef(1.f, Aq);
+        const float lo = (-Bq - sq) * iA, hi = (-Bq + sq) * iA;
         const bool two = out2 && disc > 0.f && Bq < 0.f && -Bq < Aq;
         g.nc[e] = one ? 1 : (two ? 2 : 0);
         g.ta[e] = (one && g.in[e]) ? hi : lo;
