@@ -68,7 +68,9 @@ typedef struct {
     int kernel;              /* NLFEM_KERNEL_* */
     double delta;            /* horizon, > 0 */
     double s;                /* fractional order s in (0,1) for NLFEM_KERNEL_FRACTIONAL; ignored otherwise */
-    double kconst;           /* kernel constant; NaN selects the constant of Sec. 3 for the kernel */
+    double kconst;           /* kernel constant; NaN selects the constant of Sec. 3 for the kernel
+                                (constant kernel: 4/(pi delta^4), on the infinity ball 3/(4 delta^4);
+                                tabulated kernel: 1) */
     int ball;                /* NLFEM_BALL_* */
     int quad_outer;          /* 7 (Sec. 3.1 rule) or 16 (degree-7 conical product rule) */
     int quad_inner;          /* 7 or 16 */
