@@ -57,8 +57,9 @@ extern "C" {
 
 /* arithmetic of the separated-pair quadrature */
 #define NLFEM_PREC_FP64 0           /* everything in FP64 */
-#define NLFEM_PREC_FP32_BULK 1      /* truncation quadrature in FP32 (FP64 geometry decisions and
-                                       singular pairs), FP64 result */
+#define NLFEM_PREC_FP32_BULK 1      /* quadrature in FP32 (geometry decisions equal to FP64 ones; the
+                                       singular rule's points in FP32, its sums reduced in FP64),
+                                       FP64 result */
 
 typedef struct nlfem_mesh_s* nlfem_mesh_t;
 typedef struct nlfem_system_s* nlfem_system_t;

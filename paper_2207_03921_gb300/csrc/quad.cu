@@ -296,8 +296,27 @@ __device__ __forceinline__ double gamma_d(double d2, const Params& P) {
     return P.c * exp2((-1.0 - P.s) * log2(d2));
 }
 
+// the same in FP32 for the FP32-bulk path (relative error of a few 1e-7): rsqrt powers for
+// s in {1/4, 1/2, 3/4}, exp2 / log2 otherwise
+__device__ __forceinline__ float gamma_f(float d2, const Params& P, float c) {
+    if (P.kernel == NLFEM_KERNEL_CONSTANT) return c;
+    const float r = rsqrtf(d2);  // |z|^-1
+    if (P.s == 0.5) return c * r * r * r;
+    if (P.s == 0.25) return c * r * r * sqrtf(r);
+    if (P.s == 0.75) return c * r * r * r * sqrtf(r);
+    return c * exp2f(log2f(d2) * (float)(-1.0 - P.s));
+}
+
+template <typename R>
+__device__ __forceinline__ R gamma_r(R d2, const Params& P, R c);
+template <>
+__device__ __forceinline__ double gamma_r<double>(double d2, const Params& P, double) { return gamma_d(d2, P); }
+template <>
+__device__ __forceinline__ float gamma_r<float>(float d2, const Params& P, float c) { return gamma_f(d2, P, c); }
+
 // add w * D D^T (scalar) into the packed upper union block
-__device__ __forceinline__ void duffy_add(double* acc, const double* D, int U, double w) {
+template <typename R>
+__device__ __forceinline__ void duffy_add(R* acc, const R* D, int U, R w) {
     int e = 0;
     for (int a = 0; a < 5; ++a)
         for (int b = a; b < 5; ++b) {
@@ -306,12 +325,22 @@ __device__ __forceinline__ void duffy_add(double* acc, const double* D, int U, d
         }
 }
 
+// R = double: the FP64 path; R = float: the FP32-bulk path (the points in FP32, each lane's
+// partial sums reduced across the warp in FP64). The 1D Gauss rule sits in shared memory:
+// lanes read it at different indices.
+template <typename R>
 __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__ contrib64,
                                                float* __restrict__ contrib32) {
+    __shared__ R s_x[32], s_w[32];
+    const Params& P = A.prm;
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) {
+        s_x[i] = (R)(i < P.dr.n ? P.dr.x[i] : 0.0);
+        s_w[i] = (R)(i < P.dr.n ? P.dr.w[i] : 0.0);
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wi >= A.n) return;
-    const Params& P = A.prm;
     const int p = A.ids[wi];
     const int k = A.pk[p], l = A.pl[p];
     const int4 tk4 = A.T[k], tl4 = A.T[l];
@@ -357,13 +386,15 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
         for (int v = 0; v < U; ++v)
             if (u[v] == uorder[a]) upos[a] = v;
     }
-    const double scale = A.det[k] * A.det[l];
-    const double e10x = Av[1].x - Av[0].x, e10y = Av[1].y - Av[0].y;
-    const double e21x = Av[2].x - Av[1].x, e21y = Av[2].y - Av[1].y;
+    const R scale = (R)(A.det[k] * A.det[l]);
+    const R cR = (R)P.c;
+    // element edge vectors: FP64 differences, rounded once to R
+    const R e10x = (R)(Av[1].x - Av[0].x), e10y = (R)(Av[1].y - Av[0].y);
+    const R e21x = (R)(Av[2].x - Av[1].x), e21y = (R)(Av[2].y - Av[1].y);
     const int n = P.dr.n;
-    double acc[15];
-    for (int e = 0; e < 15; ++e) acc[e] = 0.0;
-    double D[5];
+    R acc[15];
+    for (int e = 0; e < 15; ++e) acc[e] = (R)0;
+    R D[5];
     // z, the basis differences D and the Jacobian are powers of xi times functions of the
     // other coordinates, and gamma is homogeneous (gamma(xi w) = xi^alpha gamma(w)), so the xi
     // sum of the tensor rule factors out: P.dr.sxi[case] = sum_i w_i xi_i^(e + alpha) (1 - xi_i)^m
@@ -371,74 +402,78 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
     // with z / xi and D / xi: the same tensor sum, reordered.
     if (shared == 3) {
         // identical: the integrand depends on (xi, e1) only; e2, e3 sum to sum_wx * sum_w
-        const double fac = P.dr.sum_wx * P.dr.sum_w * P.dr.sxi[0];
+        const R fac = (R)(P.dr.sum_wx * P.dr.sum_w * P.dr.sxi[0]);
         const int npts = 6 * n;
         for (int t = lane; t < npts; t += 32) {
             const int r = t / n, i1 = t % n;
-            const double e1 = P.dr.x[i1];
-            const double w = P.dr.w[i1] * fac;
+            const R e1 = s_x[i1];
+            const R w = s_w[i1] * fac;
             // (P_r, Q_r): the six triangles tiling the hexagon S - S
-            const double PQ[6][4] = {{0, 1, 1, 1}, {1, 0, 1, 1}, {1, 0, 0, -1},
-                                     {0, 1, -1, 0}, {-1, 0, -1, -1}, {0, -1, -1, -1}};
-            const double h1 = (1.0 - e1) * PQ[r][0] + e1 * PQ[r][2];
-            const double h2 = (1.0 - e1) * PQ[r][1] + e1 * PQ[r][3];
-            const double zx = h1 * e10x + h2 * e21x, zy = h1 * e10y + h2 * e21y;
-            D[0] = D[1] = D[2] = D[3] = D[4] = 0.0;
+            const R PQ[6][4] = {{0, 1, 1, 1}, {1, 0, 1, 1}, {1, 0, 0, -1},
+                                {0, 1, -1, 0}, {-1, 0, -1, -1}, {0, -1, -1, -1}};
+            const R h1 = ((R)1 - e1) * PQ[r][0] + e1 * PQ[r][2];
+            const R h2 = ((R)1 - e1) * PQ[r][1] + e1 * PQ[r][3];
+            const R zx = h1 * e10x + h2 * e21x, zy = h1 * e10y + h2 * e21y;
+            D[0] = D[1] = D[2] = D[3] = D[4] = (R)0;
             D[upos[0]] = h1;
             D[upos[1]] = h2 - h1;
             D[upos[2]] = -h2;
-            const double g = gamma_d(zx * zx + zy * zy, P);
-            duffy_add(acc, D, U, w * scale * g);
+            const R g = gamma_r<R>(zx * zx + zy * zy, P, cR);
+            duffy_add<R>(acc, D, U, w * scale * g);
         }
     } else if (shared == 2) {
         // common edge: constant along e3
-        const double fx = Bv[2].x - Av[1].x, fy = Bv[2].y - Av[1].y;
-        const double fac = P.dr.sum_w * P.dr.sxi[1];
+        const R fx = (R)(Bv[2].x - Av[1].x), fy = (R)(Bv[2].y - Av[1].y);
+        const R fac = (R)(P.dr.sum_w * P.dr.sxi[1]);
         const int npts = 4 * n * n;
         for (int t = lane; t < npts; t += 32) {
             const int r = t / (n * n), i1 = (t / n) % n, i2 = t % n;
-            const double e1 = P.dr.x[i1], e2 = P.dr.x[i2];
-            const double w = P.dr.w[i1] * P.dr.w[i2] * fac;
-            double hu, hx2, hy2, wr;
-            if (r == 0) { hu = 1.0 - e1; hx2 = e1; hy2 = e2; wr = 1.0; }
-            else if (r == 1) { hu = e1 * (1.0 - e2); hx2 = e1 * e2; hy2 = 1.0; wr = e1; }
-            else if (r == 2) { hu = -e1 * (1.0 - e2); hx2 = 1.0; hy2 = e1 * e2; wr = e1; }
-            else { hu = e1 - 1.0; hx2 = e2; hy2 = e1; wr = 1.0; }
-            const double zx = hu * e10x + hy2 * fx - hx2 * e21x;
-            const double zy = hu * e10y + hy2 * fy - hx2 * e21y;
-            D[0] = D[1] = D[2] = D[3] = D[4] = 0.0;
+            const R e1 = s_x[i1], e2 = s_x[i2];
+            const R w = s_w[i1] * s_w[i2] * fac;
+            R hu, hx2, hy2, wr;
+            if (r == 0) { hu = (R)1 - e1; hx2 = e1; hy2 = e2; wr = (R)1; }
+            else if (r == 1) { hu = e1 * ((R)1 - e2); hx2 = e1 * e2; hy2 = (R)1; wr = e1; }
+            else if (r == 2) { hu = -e1 * ((R)1 - e2); hx2 = (R)1; hy2 = e1 * e2; wr = e1; }
+            else { hu = e1 - (R)1; hx2 = e2; hy2 = e1; wr = (R)1; }
+            const R zx = hu * e10x + hy2 * fx - hx2 * e21x;
+            const R zy = hu * e10y + hy2 * fy - hx2 * e21y;
+            D[0] = D[1] = D[2] = D[3] = D[4] = (R)0;
             D[upos[0]] = hu;
             D[upos[1]] = -hu - hx2 + hy2;
             D[upos[2]] = hx2;
             D[upos[3]] = -hy2;
-            const double g = gamma_d(zx * zx + zy * zy, P);
-            duffy_add(acc, D, U, w * scale * wr * g);
+            const R g = gamma_r<R>(zx * zx + zy * zy, P, cR);
+            duffy_add<R>(acc, D, U, w * scale * wr * g);
         }
     } else {
         // common vertex: all four directions matter
-        const double g10x = Bv[1].x - Av[0].x, g10y = Bv[1].y - Av[0].y;
-        const double g21x = Bv[2].x - Bv[1].x, g21y = Bv[2].y - Bv[1].y;
+        const R g10x = (R)(Bv[1].x - Av[0].x), g10y = (R)(Bv[1].y - Av[0].y);
+        const R g21x = (R)(Bv[2].x - Bv[1].x), g21y = (R)(Bv[2].y - Bv[1].y);
+        const R sxi2 = (R)P.dr.sxi[2];
         const int npts = 2 * n * n * n;
         for (int t = lane; t < npts; t += 32) {
             const int r = t / (n * n * n);
             const int i1 = (t / (n * n)) % n, i2 = (t / n) % n, i3 = t % n;
-            const double e1 = P.dr.x[i1], e2 = P.dr.x[i2], e3 = P.dr.x[i3];
-            const double w = P.dr.w[i1] * P.dr.w[i2] * P.dr.w[i3] * P.dr.sxi[2];
-            const double hx1 = r == 0 ? 1.0 : e2, hy1 = r == 0 ? e2 : 1.0;
-            const double zx = hy1 * (g10x + e3 * g21x) - hx1 * (e10x + e1 * e21x);
-            const double zy = hy1 * (g10y + e3 * g21y) - hx1 * (e10y + e1 * e21y);
+            const R e1 = s_x[i1], e2 = s_x[i2], e3 = s_x[i3];
+            const R w = s_w[i1] * s_w[i2] * s_w[i3] * sxi2;
+            const R hx1 = r == 0 ? (R)1 : e2, hy1 = r == 0 ? e2 : (R)1;
+            const R zx = hy1 * (g10x + e3 * g21x) - hx1 * (e10x + e1 * e21x);
+            const R zy = hy1 * (g10y + e3 * g21y) - hx1 * (e10y + e1 * e21y);
             D[upos[0]] = hy1 - hx1;
-            D[upos[1]] = hx1 * (1.0 - e1);
+            D[upos[1]] = hx1 * ((R)1 - e1);
             D[upos[2]] = hx1 * e1;
-            D[upos[3]] = -hy1 * (1.0 - e3);
+            D[upos[3]] = -hy1 * ((R)1 - e3);
             D[upos[4]] = -hy1 * e3;
-            const double g = gamma_d(zx * zx + zy * zy, P);
-            duffy_add(acc, D, U, w * scale * e2 * g);
+            const R g = gamma_r<R>(zx * zx + zy * zy, P, cR);
+            duffy_add<R>(acc, D, U, w * scale * e2 * g);
         }
     }
-    // warp reduction in a fixed tree (deterministic)
-    for (int e = 0; e < 15; ++e)
-        for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+    // warp reduction in a fixed tree (deterministic), in FP64
+    double accd[15];
+    for (int e = 0; e < 15; ++e) {
+        accd[e] = (double)acc[e];
+        for (int o = 16; o > 0; o >>= 1) accd[e] += __shfl_xor_sync(0xffffffffu, accd[e], o);
+    }
     if (lane == 0) {
         int e;
         // write all 21 entries of the union block (unused ones are zero)
@@ -449,8 +484,8 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
         for (int a = 0; a < 5; ++a)
             for (int b = a; b < 5; ++b) {
                 if (a < U && b < U) {
-                    blk[a][b] = acc[e];
-                    blk[b][a] = acc[e];
+                    blk[a][b] = accd[e];
+                    blk[b][a] = accd[e];
                 }
                 ++e;
             }
@@ -675,7 +710,7 @@ static void run_bulk(Mesh& m, PairCache& pc, const Params& prm, System& sys, cud
         sys.contrib32.alloc(pc.nduffy * contrib_entries(pc.ndof), st);
         if (prm.singular) {
             DuffyArgs d{pc.duffy_ids.p, pc.nduffy, 1, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
-            k_duffy<<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, nullptr, sys.contrib32.p);
+            k_duffy<float><<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, nullptr, sys.contrib32.p);
             NLFEM_LAUNCH_CHECK();
         } else {
             QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nduffy, pc.duffy_ids.p, 1, m.X.p, m.T.p, m.det.p, prm};
@@ -756,7 +791,7 @@ void BatchExec::record(cudaStream_t st, cudaEvent_t* ev, bool finish, const std:
         if (pc.nduffy > 0) {
             if (prm.singular) {
                 DuffyArgs d{pc.duffy_ids.p, pc.nduffy, 1, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
-                k_duffy<<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, nullptr, sys.contrib32.p);
+                k_duffy<float><<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, nullptr, sys.contrib32.p);
                 NLFEM_LAUNCH_CHECK();
             } else {
                 QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nduffy, pc.duffy_ids.p, 1, m.X.p, m.T.p,
@@ -817,7 +852,7 @@ void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cuda
     NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
     if (prm.singular && pc.nduffy > 0) {
         DuffyArgs d{pc.duffy_ids.p, pc.nduffy, 0, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
-        k_duffy<<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, sys.contrib64.p, nullptr);
+        k_duffy<double><<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, sys.contrib64.p, nullptr);
         NLFEM_LAUNCH_CHECK();
     }
     NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
