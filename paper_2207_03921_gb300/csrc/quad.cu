@@ -325,9 +325,8 @@ __device__ __forceinline__ void duffy_add(R* acc, const R* D, int U, R w) {
         }
 }
 
-// R = double: the FP64 path; R = float: the FP32-bulk path (the points in FP32, each lane's
-// partial sums reduced across the warp in FP64). The 1D Gauss rule sits in shared memory:
-// lanes read it at different indices.
+// R = double: the FP64 path; R = float: the FP32-bulk path (points and sums in FP32). The
+// 1D Gauss rule sits in shared memory: lanes read it at different indices.
 template <typename R>
 __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__ contrib64,
                                                float* __restrict__ contrib32) {
@@ -468,11 +467,14 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
             duffy_add<R>(acc, D, U, w * scale * e2 * g);
         }
     }
-    // warp reduction in a fixed tree (deterministic), in FP64
+    // warp reduction in a fixed tree (deterministic), in R: five levels of additions add a
+    // relative error of a few R ulps to the lane sums (the FP64 pipe's 1/64 rate would make
+    // an FP64 tree the costliest part of the FP32 kernel)
     double accd[15];
     for (int e = 0; e < 15; ++e) {
-        accd[e] = (double)acc[e];
-        for (int o = 16; o > 0; o >>= 1) accd[e] += __shfl_xor_sync(0xffffffffu, accd[e], o);
+        R v = acc[e];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        accd[e] = (double)v;
     }
     if (lane == 0) {
         int e;
