@@ -115,28 +115,6 @@ typedef struct {
     double rel_residual;     /* ||b - A_FF u_F|| / ||b|| in FP64 at exit */
 } nlfem_solve_info;
 
-/*
- * Discontinuous P1 ansatz (Sec. 2.2, J = n (d+1) K): the same mesh with every element
- * carrying its own copies of its vertices. Node 3k + a of the handle is vertex a of element k
- * as given in elems (k < K, a < 3), so the handle has 3K nodes: f_nodal, g_nodal and u are
- * given per copy, dof (3k + a) * ndof + c. Pairs are found and classified by the vertices'
- * positions, as for the continuous mesh. Intersecting pairs cannot take the singular rule
- * (Sec. 2.3.2 restricts it to continuous ansatz functions): nlfem_assemble then fails with
- * UNSUPPORTED; the constant, peridynamic and tabulated kernels assemble as usual.
- * Arguments, ownership and errors as nlfem_mesh_create.
- */
-int nlfem_mesh_create_dg(const double* verts, int64_t M, const int32_t* elems, int64_t K,
-                         const int8_t* elem_label, int ndof_per_node, void* stream, nlfem_mesh_t* out);
-
-/*
- * Material labels of the elements for label-dependent kernels (Sec. 1: the kernel may depend
- * on element labels, which assembles interface problems monolithically). material [K] int8
- * in 0..15, host or device, copied; NULL removes the labels. Independent of the Omega /
- * Omega_D labels of nlfem_mesh_create; the pair list and pattern do not depend on them.
- * Errors: INVALID_ARG (a label outside 0..15), CUDA, OOM.
- */
-int nlfem_mesh_set_materials(nlfem_mesh_t mesh, const int8_t* material, void* stream);
-
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* nlfem_last_error(void);
 
@@ -160,6 +138,28 @@ int nlfem_mesh_create(const double* verts, int64_t M, const int32_t* elems, int6
                       nlfem_mesh_t* out);
 
 void nlfem_mesh_destroy(nlfem_mesh_t mesh);
+
+/*
+ * Discontinuous P1 ansatz (Sec. 2.2, J = n (d+1) K): the same mesh with every element
+ * carrying its own copies of its vertices. Node 3k + a of the handle is vertex a of element k
+ * as given in elems (k < K, a < 3), so the handle has 3K nodes: f_nodal, g_nodal and u are
+ * given per copy, dof (3k + a) * ndof + c. Pairs are found and classified by the vertices'
+ * positions, as for the continuous mesh. Intersecting pairs cannot take the singular rule
+ * (Sec. 2.3.2 restricts it to continuous ansatz functions): nlfem_assemble then fails with
+ * UNSUPPORTED; the constant, peridynamic and tabulated kernels assemble as usual.
+ * Arguments, ownership and errors as nlfem_mesh_create.
+ */
+int nlfem_mesh_create_dg(const double* verts, int64_t M, const int32_t* elems, int64_t K,
+                         const int8_t* elem_label, int ndof_per_node, void* stream, nlfem_mesh_t* out);
+
+/*
+ * Material labels of the elements for label-dependent kernels (Sec. 1: the kernel may depend
+ * on element labels, which assembles interface problems monolithically). material [K] int8
+ * in 0..15, host or device, copied; NULL removes the labels. Independent of the Omega /
+ * Omega_D labels of nlfem_mesh_create; the pair list and pattern do not depend on them.
+ * Errors: INVALID_ARG (a label outside 0..15), CUDA, OOM.
+ */
+int nlfem_mesh_set_materials(nlfem_mesh_t mesh, const int8_t* material, void* stream);
 
 /* Fill p with the defaults of Sec. 3.1 for the given kernel: delta = 0.1, nocaps,
  * 7-point rules, 5 Gauss points, automatic close-pair rule, FP64. */
