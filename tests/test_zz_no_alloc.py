@@ -17,7 +17,7 @@ from paper_2207_03921_gb300 import Mesh, NlfemError, assemble, binding  # noqa: 
 from synth import meshes  # noqa: E402
 
 
-@pytest.mark.parametrize("ball,nq,delta", [("approxcaps", 16, 0.12), ("nocaps", 7, 0.1)])
+@pytest.mark.parametrize("ball,nq,delta", [("approxcaps", 16, 0.12), ("nocaps", 7, 0.1), ("infinity", 7, 0.1)])
 def test_pairs_noalloc_matches_the_regular_pair_search(ball, nq, delta):
     m = meshes.jittered_delaunay(-0.1, 1.1, 30, 0.03, seed=2207039219)
     mesh = Mesh.from_synth(m)
