@@ -506,6 +506,9 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         rate, desc, cores, dt = oracle_sample(m, wl)
         line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc}
+        # the same oracle on one core, a smaller sample
+        rate1, desc1, _, _ = oracle_sample(m, wl, seconds_target=8.0, threads=1)
+        line["cpu_baseline"]["single_core"] = {"value": rate1, "sample": desc1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
