@@ -490,10 +490,10 @@ def main():
         "census": census,
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "pinned host mesh -> nlfem_mesh_create -> nlfem_assemble (cold) -> CSR values and F to host"},
-        # per step: pilot and main whole-pair and cut-pair kernels, the scale pick and check, two
-        # element sums, fixed point to CSR, load vector (10, as in the ncu launch list); with a
-        # close list also its kernel and two close-record passes
-        "gpu_launches": args.steps * (10 + (3 if census["singular_pairs"] or census["evals_canonical"] else 0)),
+        # per timed step: whole-pair and cut-pair kernels, the scale check, two element sums,
+        # fixed point to CSR, load vector (7; the pilot pass and the scale pick ran once, at the
+        # first assembly on the pattern); with a close list also its kernel and its records' pass
+        "gpu_launches": args.steps * (7 + (2 if census["singular_pairs"] or census["evals_canonical"] else 0)),
         "clocks": clk_sum,
     }
     if not args.no_serving:

@@ -200,6 +200,8 @@ __device__ __forceinline__ double pair_factor64(const Params& P, int k, int l) {
     return P.nmat ? P.msc64[P.mat[k] * P.nmat + P.mat[l]] : 1.0;
 }
 
+struct FixState;
+
 // Interaction graph, CSR pattern and reduction index of one (mesh, delta, ball, outer rule, ndof).
 struct PairCache {
     double delta = -1;
@@ -235,6 +237,11 @@ struct PairCache {
     int64_t n_upper = 0;
     bool slots_built = false;
     int sq32 = 1;  // infinity ball: few vertices on the squares' sides, the FP32 passes pay off
+    // FP32 bulk: the fixed-point scale the pilot pass picked for the parameters with this key
+    // (a function of the pattern and the parameters alone, so a later assembly reuses it)
+    uint64_t scale_key = 0;
+    bool scale_memo_valid = false;
+    DBuf<FixState> scale_memo;
     // FP32-bulk accumulation index: upper entries numbered row by row in node order
     DBuf<int64_t> up_start;  // [M + 1] first upper entry of each node row
     DBuf<int> epos;          // [K * 6] upper entry of each node pair of an element
