@@ -458,6 +458,11 @@ static int pair_truncation(const mesh_t *m, const params_t *P, int k, int l, int
  *    x1 = max(x2, y2 - u) + L e3, L = 1 - xi.
  *  common vertex (2 regions), A0 = B0: x = x1 (1, e1), y = y1 (1, e3),
  *    (x1, y1) = (xi, xi e2) or (xi e2, xi); weight xi^3 e2.
+ *
+ * On a discontinuous ansatz (eq. case-one-factoredOut, admissible for s <= 1/2) the shared
+ * vertices of a touching pair carry different dofs on the two elements: the integrand's
+ * vector over the six dofs is (phi^k(x), -phi^l(y)), so its outer product holds the local,
+ * nonlocal and primed terms of that equation. The maps and points are those above.
  * ------------------------------------------------------------------------------------- */
 static void duffy_eval(const params_t *P, int U, const double *D, double zx, double zy,
                        double w, block_t *B)
@@ -477,23 +482,25 @@ static void pair_duffy(const mesh_t *m, const params_t *P, int k, int l, int sha
                        block_t *B, counts_t *cnt)
 {
     const int *tk = &m->T[3 * k], *tl = &m->T[3 * l];
-    /* Reorder so that the shared vertices come first, in the same order in both. */
-    int ak[3], bl[3];
+    /* Reorder so that the shared vertices come first, in the same order in both. Vertices are
+     * matched by position; on a discontinuous ansatz the matched dofs differ (split). */
+    int ak[3], bl[3] = {0, 1, 2};
     if (shared == 3) {
         for (int a = 0; a < 3; ++a) { ak[a] = a; }
     } else if (shared == 2) {
         int s0 = -1, s1 = -1, sl0 = -1, sl1 = -1;
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) if (tk[a] == tl[b]) {
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) if (m->pos[tk[a]] == m->pos[tl[b]]) {
             if (s0 < 0) { s0 = a; sl0 = b; } else { s1 = a; sl1 = b; }
         }
         ak[0] = s0; ak[1] = s1; ak[2] = 3 - s0 - s1;
         bl[0] = sl0; bl[1] = sl1; bl[2] = 3 - sl0 - sl1;
     } else {
         int s0 = -1, sl0 = -1;
-        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) if (tk[a] == tl[b]) { s0 = a; sl0 = b; }
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) if (m->pos[tk[a]] == m->pos[tl[b]]) { s0 = a; sl0 = b; }
         ak[0] = s0; ak[1] = (s0 + 1) % 3; ak[2] = (s0 + 2) % 3;
         bl[0] = sl0; bl[1] = (sl0 + 1) % 3; bl[2] = (sl0 + 2) % 3;
     }
+    const int split = shared < 3 && tk[ak[0]] != tl[bl[0]];
     double A[3][2], Bv[3][2];
     for (int a = 0; a < 3; ++a) {
         A[a][0] = m->X[2 * tk[ak[a]]]; A[a][1] = m->X[2 * tk[ak[a]] + 1];
@@ -510,6 +517,12 @@ static void pair_duffy(const mesh_t *m, const params_t *P, int k, int l, int sha
     for (int u = 0; u < U; ++u) {
         upos[u] = -1;
         for (int v = 0; v < B->U; ++v) if (B->node[v] == uorder[u]) upos[u] = v;
+    }
+    /* split pairs: block positions of E_k's dofs (A0, A1, A2) and E_l's (B0, B1, B2) */
+    int kpos[3] = {0, 0, 0}, lpos[3] = {0, 0, 0};
+    if (split) for (int a = 0; a < 3; ++a) for (int v = 0; v < B->U; ++v) {
+        if (B->node[v] == tk[ak[a]]) kpos[a] = v;
+        if (B->node[v] == tl[bl[a]]) lpos[a] = v;
     }
     double scale = m->det[k] * m->det[l];
     double e10x = A[1][0] - A[0][0], e10y = A[1][1] - A[0][1];
@@ -558,14 +571,19 @@ static void pair_duffy(const mesh_t *m, const params_t *P, int k, int l, int sha
                 double u = xi * hu, x2 = xi * hx2, y2 = xi * hy2;
                 double lo = x2 > (y2 - u) ? x2 : (y2 - u);
                 double x1 = lo + L * e3;
-                (void)x1;
                 double zx = xi * (hu * e10x + hy2 * fx - hx2 * e21x);
                 double zy = xi * (hu * e10y + hy2 * fy - hx2 * e21y);
                 double D[6] = {0, 0, 0, 0, 0, 0};
-                D[upos[0]] = u;                 /* y1 - x1 */
-                D[upos[1]] = -u - x2 + y2;      /* (x1 - x2) - (y1 - y2) */
-                D[upos[2]] = x2;
-                D[upos[3]] = -y2;
+                if (split) {
+                    double y1 = x1 + u;
+                    D[kpos[0]] = 1.0 - x1; D[kpos[1]] = x1 - x2; D[kpos[2]] = x2;
+                    D[lpos[0]] = -(1.0 - y1); D[lpos[1]] = -(y1 - y2); D[lpos[2]] = -y2;
+                } else {
+                    D[upos[0]] = u;                 /* y1 - x1 */
+                    D[upos[1]] = -u - x2 + y2;      /* (x1 - x2) - (y1 - y2) */
+                    D[upos[2]] = x2;
+                    D[upos[3]] = -y2;
+                }
                 duffy_eval(P, U, D, zx, zy, wq * scale * xi * xi * L * wr, B);
                 cnt->duffy_points++;
             }
@@ -579,11 +597,16 @@ static void pair_duffy(const mesh_t *m, const params_t *P, int k, int l, int sha
                 double zx = y1 * (g10x + w2 * g21x) - x1 * (e10x + w1 * e21x);
                 double zy = y1 * (g10y + w2 * g21y) - x1 * (e10y + w1 * e21y);
                 double D[6] = {0, 0, 0, 0, 0, 0};
-                D[upos[0]] = y1 - x1;
-                D[upos[1]] = x1 * (1.0 - w1);
-                D[upos[2]] = x1 * w1;
-                D[upos[3]] = -y1 * (1.0 - w2);
-                D[upos[4]] = -y1 * w2;
+                if (split) {
+                    D[kpos[0]] = 1.0 - x1; D[kpos[1]] = x1 * (1.0 - w1); D[kpos[2]] = x1 * w1;
+                    D[lpos[0]] = -(1.0 - y1); D[lpos[1]] = -y1 * (1.0 - w2); D[lpos[2]] = -y1 * w2;
+                } else {
+                    D[upos[0]] = y1 - x1;
+                    D[upos[1]] = x1 * (1.0 - w1);
+                    D[upos[2]] = x1 * w1;
+                    D[upos[3]] = -y1 * (1.0 - w2);
+                    D[upos[4]] = -y1 * w2;
+                }
                 duffy_eval(P, U, D, zx, zy, wq * scale * xi * xi * xi * e2, B);
                 cnt->duffy_points++;
             }
