@@ -144,9 +144,11 @@ void nlfem_mesh_destroy(nlfem_mesh_t mesh);
  * carrying its own copies of its vertices. Node 3k + a of the handle is vertex a of element k
  * as given in elems (k < K, a < 3), so the handle has 3K nodes: f_nodal, g_nodal and u are
  * given per copy, dof (3k + a) * ndof + c. Pairs are found and classified by the vertices'
- * positions, as for the continuous mesh. Intersecting pairs cannot take the singular rule
- * (Sec. 2.3.2 restricts it to continuous ansatz functions): nlfem_assemble then fails with
- * UNSUPPORTED; the constant, peridynamic and tabulated kernels assemble as usual.
+ * positions, as for the continuous mesh. Touching pairs under the singular rule take the
+ * factored form of eq. case-one-factoredOut (the six dofs of the pair, the same regularising
+ * maps with the Gauss rule in every direction), which Tab. 1 admits for s <= 1/2 only: a
+ * fractional kernel with s > 1/2 makes nlfem_assemble fail with UNSUPPORTED. The constant,
+ * peridynamic and tabulated kernels assemble as usual.
  * Arguments, ownership and errors as nlfem_mesh_create.
  */
 int nlfem_mesh_create_dg(const double* verts, int64_t M, const int32_t* elems, int64_t K,

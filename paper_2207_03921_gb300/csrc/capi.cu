@@ -422,9 +422,11 @@ static void attach_table(Params& P, const nlfem_params& p, DBuf<double>& t64, DB
 }
 
 static void attach_tables(System& S, const nlfem_params& p, const Mesh& m, cudaStream_t st) {
-    NLFEM_CHECK(!(m.dg && S.prm.singular), NLFEM_ERR_UNSUPPORTED,
-                "the singular rule needs a continuous ansatz (Sec. 2.3.2); on a discontinuous mesh use "
-                "the diamond or standard rule");
+    // Tab. 1: discontinuous ansatz functions for s <= 1/2 only (the factored form of
+    // eq. case-one-factoredOut is not admissible on intersecting pairs for s > 1/2)
+    NLFEM_CHECK(!(m.dg && S.prm.singular && p.kernel == NLFEM_KERNEL_FRACTIONAL && p.s > 0.5),
+                NLFEM_ERR_UNSUPPORTED,
+                "a discontinuous ansatz takes singular kernels with s <= 1/2 only (Sec. 2.3.2, Tab. 1)");
     attach_table(S.prm, p, S.tab64, S.tab32, st);
     if (p.n_materials <= 0) return;
     NLFEM_CHECK(m.mat.p && m.mat_max >= 0, NLFEM_ERR_INVALID_ARG,

@@ -281,6 +281,8 @@ struct DuffyArgs {
     const int4* T;
     const double* det;
     Params prm;
+    const int4* Tp;  // vertex positions (original vertex ids of a discontinuous mesh)
+    int dg;          // discontinuous mesh: touching pairs (k != l) take k_duffy_split
 };
 
 // c |z|^(-2-2s) from d2 = |z|^2: square roots for s in {1/4, 1/2, 3/4} (each correctly rounded),
@@ -342,6 +344,7 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
     if (wi >= A.n) return;
     const int p = A.ids[wi];
     const int k = A.pk[p], l = A.pl[p];
+    if (A.dg && k != l) return;  // the warp's pair is split (k_duffy_split)
     const int4 tk4 = A.T[k], tl4 = A.T[l];
     const int tk[3] = {tk4.x, tk4.y, tk4.z}, tl[3] = {tl4.x, tl4.y, tl4.z};
     int shared = 0;
@@ -498,6 +501,153 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
                 if (contrib64) contrib64[r * NLFEM_REC1 + q_E1[a][b]] = fm * blk[a][b];
                 else contrib32[r * NLFEM_REC1 + q_E1[a][b]] = (float)(fm * blk[a][b]);
             }
+    }
+}
+
+// Touching pairs of a discontinuous mesh (eq. case-one-factoredOut, admissible for s <= 1/2):
+// the shared vertices carry one dof per element, so the integrand's vector over the six dofs
+// of the pair is (phi^k(x), -phi^l(y)) and its outer product holds the local, nonlocal and
+// primed terms of that equation. The maps and weights are k_duffy's (common edge: 4 regions,
+// common vertex: 2), but the basis values do not vanish with xi, so xi is summed with the
+// Gauss rule like the other directions: n^4 points per region. Warp per pair, lanes over the
+// points, a fixed shuffle tree in R; the record is the 6 x 6 block over (E_k's dofs, E_l's).
+template <typename R>
+__global__ void __launch_bounds__(128) k_duffy_split(DuffyArgs A, double* __restrict__ contrib64,
+                                                     float* __restrict__ contrib32) {
+    __shared__ R s_x[32], s_w[32];
+    const Params& P = A.prm;
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) {
+        s_x[i] = (R)(i < P.dr.n ? P.dr.x[i] : 0.0);
+        s_w[i] = (R)(i < P.dr.n ? P.dr.w[i] : 0.0);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wi >= A.n) return;
+    const int p = A.ids[wi];
+    const int k = A.pk[p], l = A.pl[p];
+    if (k == l) return;  // identical pairs: k_duffy
+    const int4 tk4 = A.T[k], tl4 = A.T[l];
+    const int4 pk4 = A.Tp[k], pl4 = A.Tp[l];
+    const int tk[3] = {tk4.x, tk4.y, tk4.z}, tl[3] = {tl4.x, tl4.y, tl4.z};
+    const int qk[3] = {pk4.x, pk4.y, pk4.z}, ql[3] = {pl4.x, pl4.y, pl4.z};
+    // shared vertices by position, in the same order in both elements
+    int shared = 0, s0 = -1, s1 = -1, sl0 = -1, sl1 = -1;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (qk[a] == ql[b]) {
+                if (s0 < 0) { s0 = a; sl0 = b; } else { s1 = a; sl1 = b; }
+                ++shared;
+            }
+    if (shared < 1 || shared > 2) {
+        // two elements on the same three points (a mesh with a duplicated triangle): no
+        // admissible factored form; the record is zero
+        if (lane == 0 && shared == 3) {
+            const int64_t rr = A.compact ? wi : (int64_t)p;
+            for (int e = 0; e < 21; ++e) {
+                if (contrib64) contrib64[rr * NLFEM_REC1 + e] = 0.0;
+                else contrib32[rr * NLFEM_REC1 + e] = 0.f;
+            }
+        }
+        return;
+    }
+    int ak[3], bl[3];
+    if (shared == 2) {
+        ak[0] = s0; ak[1] = s1; ak[2] = 3 - s0 - s1;
+        bl[0] = sl0; bl[1] = sl1; bl[2] = 3 - sl0 - sl1;
+    } else {
+        ak[0] = s0; ak[1] = (s0 + 1) % 3; ak[2] = (s0 + 2) % 3;
+        bl[0] = sl0; bl[1] = (sl0 + 1) % 3; bl[2] = (sl0 + 2) % 3;
+    }
+    double2 Av[3], Bv[3];
+    for (int a = 0; a < 3; ++a) {
+        Av[a] = A.X[tk[ak[a]]];
+        Bv[a] = A.X[tl[bl[a]]];
+    }
+    const R scale = (R)(A.det[k] * A.det[l]);
+    const R cR = (R)P.c;
+    const R e10x = (R)(Av[1].x - Av[0].x), e10y = (R)(Av[1].y - Av[0].y);
+    const R e21x = (R)(Av[2].x - Av[1].x), e21y = (R)(Av[2].y - Av[1].y);
+    const int n = P.dr.n, n2 = n * n, n4 = n2 * n2;
+    R acc[21];
+    for (int e = 0; e < 21; ++e) acc[e] = (R)0;
+    R D[6];  // (phi^k_A0, phi^k_A1, phi^k_A2)(x), -(phi^l_B0, phi^l_B1, phi^l_B2)(y)
+    const int npts = (shared == 2 ? 4 : 2) * n4;
+    for (int t = lane; t < npts; t += 32) {
+        const int r = t / n4, i0 = (t / (n2 * n)) % n, i1 = (t / n2) % n, i2 = (t / n) % n, i3 = t % n;
+        const R xi = s_x[i0], e1 = s_x[i1], e2 = s_x[i2], e3 = s_x[i3];
+        const R wq = s_w[i0] * s_w[i1] * s_w[i2] * s_w[i3];
+        R zx, zy, w;
+        if (shared == 2) {
+            const R fx = (R)(Bv[2].x - Av[1].x), fy = (R)(Bv[2].y - Av[1].y);
+            const R L = (R)1 - xi;
+            R hu, hx2, hy2, wr;
+            if (r == 0) { hu = (R)1 - e1; hx2 = e1; hy2 = e2; wr = (R)1; }
+            else if (r == 1) { hu = e1 * ((R)1 - e2); hx2 = e1 * e2; hy2 = (R)1; wr = e1; }
+            else if (r == 2) { hu = -e1 * ((R)1 - e2); hx2 = (R)1; hy2 = e1 * e2; wr = e1; }
+            else { hu = e1 - (R)1; hx2 = e2; hy2 = e1; wr = (R)1; }
+            const R u = xi * hu, x2 = xi * hx2, y2 = xi * hy2;
+            const R x1 = (x2 > y2 - u ? x2 : y2 - u) + L * e3;
+            const R y1 = x1 + u;
+            zx = xi * (hu * e10x + hy2 * fx - hx2 * e21x);
+            zy = xi * (hu * e10y + hy2 * fy - hx2 * e21y);
+            w = wq * scale * xi * xi * L * wr;
+            D[0] = (R)1 - x1; D[1] = x1 - x2; D[2] = x2;
+            D[3] = -((R)1 - y1); D[4] = -(y1 - y2); D[5] = -y2;
+        } else {
+            const R g10x = (R)(Bv[1].x - Av[0].x), g10y = (R)(Bv[1].y - Av[0].y);
+            const R g21x = (R)(Bv[2].x - Bv[1].x), g21y = (R)(Bv[2].y - Bv[1].y);
+            const R x1 = xi * (r == 0 ? (R)1 : e2), y1 = xi * (r == 0 ? e2 : (R)1);
+            zx = y1 * (g10x + e3 * g21x) - x1 * (e10x + e1 * e21x);
+            zy = y1 * (g10y + e3 * g21y) - x1 * (e10y + e1 * e21y);
+            w = wq * scale * xi * xi * xi * e2;
+            D[0] = (R)1 - x1; D[1] = x1 * ((R)1 - e1); D[2] = x1 * e1;
+            D[3] = -((R)1 - y1); D[4] = -y1 * ((R)1 - e3); D[5] = -y1 * e3;
+        }
+        const R wg = w * gamma_r<R>(zx * zx + zy * zy, P, cR);
+        int e = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            const R wa = wg * D[a];
+#pragma unroll
+            for (int b = a; b < 6; ++b) acc[e++] += wa * D[b];
+        }
+    }
+    double accd[21];
+    for (int e = 0; e < 21; ++e) {
+        R v = acc[e];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        accd[e] = (double)v;
+    }
+    if (lane == 0) {
+        // acc runs over (a <= b) of D's order; the record's block is over (E_k's dofs as
+        // given, then E_l's): vertex A_a sits at ak[a], vertex B_b at 3 + bl[b]
+        const int bpos[6] = {ak[0], ak[1], ak[2], 3 + bl[0], 3 + bl[1], 3 + bl[2]};
+        const int64_t rr = A.compact ? wi : (int64_t)p;
+        const double fm = pair_factor64(P, k, l);
+        int e = 0;
+        for (int a = 0; a < 6; ++a)
+            for (int b = a; b < 6; ++b, ++e) {
+                const int lo = min(bpos[a], bpos[b]), hi = max(bpos[a], bpos[b]);
+                if (contrib64) contrib64[rr * NLFEM_REC1 + q_E1[lo][hi]] = fm * accd[e];
+                else contrib32[rr * NLFEM_REC1 + q_E1[lo][hi]] = (float)(fm * accd[e]);
+            }
+    }
+}
+
+// the singular rule over the close list: k_duffy, and k_duffy_split for the touching pairs of
+// a discontinuous mesh
+template <typename R>
+static void launch_duffy(const Mesh& m, const PairCache& pc, const Params& prm, int compact, double* out64,
+                         float* out32, cudaStream_t st) {
+    DuffyArgs d{pc.duffy_ids.p, pc.nduffy, compact, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm,
+                m.tpos(), m.dg ? 1 : 0};
+    const unsigned g = nblk(pc.nduffy * 32, 128);
+    k_duffy<R><<<g, 128, 0, st>>>(d, out64, out32);
+    NLFEM_LAUNCH_CHECK();
+    if (m.dg) {
+        k_duffy_split<R><<<g, 128, 0, st>>>(d, out64, out32);
+        NLFEM_LAUNCH_CHECK();
     }
 }
 
@@ -726,9 +876,7 @@ static void run_bulk(Mesh& m, PairCache& pc, const Params& prm, System& sys, cud
     if (pc.nduffy > 0) {
         sys.contrib32.alloc(pc.nduffy * contrib_entries(pc.ndof), st);
         if (prm.singular) {
-            DuffyArgs d{pc.duffy_ids.p, pc.nduffy, 1, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
-            k_duffy<float><<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, nullptr, sys.contrib32.p);
-            NLFEM_LAUNCH_CHECK();
+            launch_duffy<float>(m, pc, prm, 1, nullptr, sys.contrib32.p, st);
         } else {
             QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nduffy, pc.duffy_ids.p, 1, m.X.p, m.T.p, m.det.p, prm};
             launch_trunc<float>(c, sys.contrib32.p, st);
@@ -820,9 +968,7 @@ void BatchExec::record(cudaStream_t st, cudaEvent_t* ev, bool finish, const std:
         const Params& prm = it.prm;
         if (pc.nduffy > 0) {
             if (prm.singular) {
-                DuffyArgs d{pc.duffy_ids.p, pc.nduffy, 1, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
-                k_duffy<float><<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, nullptr, sys.contrib32.p);
-                NLFEM_LAUNCH_CHECK();
+                launch_duffy<float>(m, pc, prm, 1, nullptr, sys.contrib32.p, st);
             } else {
                 QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nduffy, pc.duffy_ids.p, 1, m.X.p, m.T.p,
                            m.det.p, prm};
@@ -880,11 +1026,7 @@ void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cuda
     launch_trunc<double>(a, sys.contrib64.p, st);
     NLFEM_CUDA_TRY(cudaEventRecord(ev[4], st));
     NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
-    if (prm.singular && pc.nduffy > 0) {
-        DuffyArgs d{pc.duffy_ids.p, pc.nduffy, 0, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm};
-        k_duffy<double><<<nblk(pc.nduffy * 32, 128), 128, 0, st>>>(d, sys.contrib64.p, nullptr);
-        NLFEM_LAUNCH_CHECK();
-    }
+    if (prm.singular && pc.nduffy > 0) launch_duffy<double>(m, pc, prm, 0, sys.contrib64.p, nullptr, st);
     NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
     NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
 }
@@ -989,10 +1131,11 @@ void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStr
     NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
     // singular-rule kernel evaluations: 6 n (identical), 4 n^2 (edge), 2 n^3 (vertex); the
     // xi direction (and the directions along which the integrand is constant) are summed in
-    // closed form
+    // closed form. Touching pairs of a discontinuous mesh: 4 n^4 (edge), 2 n^4 (vertex).
     const int64_t n = prm.dr.n;
     int64_t duffy = 0;
-    if (prm.singular) duffy = pc.counts[3] * 6 * n + pc.counts[2] * 4 * n * n + pc.counts[1] * 2 * n * n * n;
+    if (prm.singular && m.dg) duffy = pc.counts[3] * 6 * n + (pc.counts[2] * 4 + pc.counts[1] * 2) * n * n * n * n;
+    else if (prm.singular) duffy = pc.counts[3] * 6 * n + pc.counts[2] * 4 * n * n + pc.counts[1] * 2 * n * n * n;
     h[4] = (unsigned long long)duffy;
     for (int i = 0; i < 16; ++i) out[i] = (int64_t)h[i];
 }

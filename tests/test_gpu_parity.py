@@ -335,7 +335,11 @@ def test_dg_matches_oracle(precision):
     rng = np.random.default_rng(4)
     for kw in (dict(kernel="constant", delta=0.25, ball="approxcaps"),
                dict(kernel="peridynamic", delta=0.25, ball="nocaps"),
-               dict(kernel="tabulated", delta=0.25, ball="infinity", kernel_table=np.array([2.0, 1.0, 0.5]))):
+               dict(kernel="tabulated", delta=0.25, ball="infinity", kernel_table=np.array([2.0, 1.0, 0.5])),
+               # singular kernels with s <= 1/2: touching pairs in the factored form (Tab. 1)
+               dict(kernel="fractional", s=0.5, delta=0.25, ball="approxcaps"),
+               dict(kernel="fractional", s=0.25, delta=0.25, ball="nocaps"),
+               dict(kernel="constant", delta=0.25, ball="nocaps", close_rule="duffy")):
         ndof = 2 if kw["kernel"] == "peridynamic" else 1
         f = rng.standard_normal(d.M * ndof)
         ref = oracle.assemble(d, f_nodal=f, **kw)
@@ -346,8 +350,33 @@ def test_dg_matches_oracle(precision):
         F = S.rhs().cpu().numpy()
         assert np.abs(F - ref.F).max() <= 1e-12 * np.abs(ref.F).max()
         assert np.array_equal(S.dirichlet().cpu().numpy().astype(bool), ref.dirichlet)
+    # Tab. 1: no discontinuous ansatz for s > 1/2
     with pytest.raises(NlfemError):
-        assemble(Mesh.from_synth(m, 1, dg=True), kernel="fractional", s=0.5, delta=0.25, precision=precision)
+        assemble(Mesh.from_synth(m, 1, dg=True), kernel="fractional", s=0.75, delta=0.25, precision=precision)
+
+
+def test_paper_E2_fractional_dg_on_gpu():
+    """Sec. 3.1's DG table for the truncated fractional kernel (s = 1/2, delta = 0.2, approxcaps),
+    assembled (FP32 bulk) and solved on the GPU on the first four grids: second-order rates and
+    the printed magnitudes. (The fifth grid's DG pattern holds about 2.6e9 entries.)"""
+    import json, math, os
+    tab = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+    tab = tab["E2_fractional_dg"]
+    errs = []
+    for a in tab["a"][:4]:
+        m = meshes.paper_square(0.2, a)
+        d = meshes.discontinuous(m)
+        S = assemble(Mesh.from_synth(m, 1, dg=True), kernel="fractional", s=0.5, delta=0.2, ball="approxcaps",
+                     precision="fp32_bulk", f_nodal=-2.0 * (d.verts[:, 1] + 1.0))
+        ue = lambda x, y: x * x * y + y * y
+        u, info = S.solve(ue(d.verts[:, 0], d.verts[:, 1]), tol_rel=1e-10)
+        assert info["status"] == 0, info
+        errs.append(oracle.l2_error(d, u.cpu().numpy(), ue))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    for r in rates:
+        assert 1.7 < r < 2.4, (rates, errs)
+    for i, e in enumerate(errs):
+        assert 0.4 * tab["l2"][i] < e < 2.5 * tab["l2"][i], (errs, tab["l2"])
 
 
 def test_paper_E4_peridynamic_dg_on_gpu():
