@@ -10,9 +10,9 @@
  * approximate bilinear form (eq. biFormApprox)
  *     A_h^#(phi_j, phi_i) = sum_k sum_l int_{E_k} int_{E_l} 1_{B^#(x)}(y)
  *                           (phi_i(x) - phi_i(y))^T Psi(x,y) (phi_j(x) - phi_j(y)) dy dx
- * over all ordered element pairs of the base domain, with P1 continuous basis
- * functions (Sec. 2.2), the ball approximations nocaps / approxcaps (Defs. 2.1, 2.2)
- * and the quadrature of Alg. 1 and Tab. 1 (Sec. 2.3).
+ * over all ordered element pairs of the base domain, with P1 continuous or discontinuous
+ * basis functions (Sec. 2.2), the ball approximations nocaps / approxcaps (Defs. 2.1, 2.2)
+ * or the infinity-norm ball, and the quadrature of Alg. 1 and Tab. 1 (Sec. 2.3).
  */
 #ifndef NLFEM_H
 #define NLFEM_H
@@ -32,7 +32,10 @@ extern "C" {
 #define NLFEM_ERR_CUDA (-5)         /* a CUDA runtime call failed */
 #define NLFEM_ERR_NOT_CONVERGED (-6)/* nlfem_solve reached max_iter */
 #define NLFEM_ERR_TIMEOUT (-7)      /* a bounded device wait ran out */
-#define NLFEM_ERR_UNSUPPORTED (-8)  /* a size limit of this implementation was exceeded */
+#define NLFEM_ERR_UNSUPPORTED (-8)  /* a size limit of this implementation was exceeded, or a
+                                       combination it does not provide (the singular rule for
+                                       peridynamics or a tabulated kernel, a discontinuous mesh
+                                       with s > 1/2, an FP64 item where FP32 bulk is required) */
 
 /* kernels of Sec. 3 */
 #define NLFEM_KERNEL_CONSTANT 0     /* gamma = c, c = 4 / (pi delta^4) by default */
@@ -58,8 +61,9 @@ extern "C" {
 /* arithmetic of the separated-pair quadrature */
 #define NLFEM_PREC_FP64 0           /* everything in FP64 */
 #define NLFEM_PREC_FP32_BULK 1      /* quadrature in FP32 (geometry decisions equal to FP64 ones; the
-                                       singular rule's points in FP32, its sums reduced in FP64),
-                                       FP64 result */
+                                       singular rule's points and sums in FP32), sums over pairs in
+                                       exact fixed point, FP64 result; within 1e-5 relative
+                                       (Frobenius) of the FP64 result */
 
 typedef struct nlfem_mesh_s* nlfem_mesh_t;
 typedef struct nlfem_system_s* nlfem_system_t;
@@ -237,6 +241,8 @@ int nlfem_system_rhs(nlfem_system_t sys, const double** F);
 /* Borrowed device pointer to the Dirichlet node flags [M] (int8, 1 = Dirichlet). */
 int nlfem_system_dirichlet(nlfem_system_t sys, const int8_t** flags);
 
+/* Counts and timings of the assembly that produced sys (nlfem_assembly_info above), copied
+ * to the caller's info (host). Errors: INVALID_ARG (NULL). */
 int nlfem_system_info(nlfem_system_t sys, nlfem_assembly_info* info);
 
 /* Device pointers to the interaction graph of the cached pair list: k [npairs], l [npairs]
