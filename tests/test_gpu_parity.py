@@ -355,6 +355,42 @@ def test_dg_matches_oracle(precision):
         assemble(Mesh.from_synth(m, 1, dg=True), kernel="fractional", s=0.75, delta=0.25, precision=precision)
 
 
+def test_dg_singular_rule_variants():
+    """The factored singular rule on a DG mesh (k_duffy_split) with other Gauss orders (3, 8), with
+    material labels (the pair factor of its records), and inside a batched assembly (the close
+    list of a fused batch), against the oracle and against single assemblies."""
+    from paper_2207_03921_gb300 import assemble_batch
+    m = meshes.jittered_delaunay(-0.2, 1.2, 10, 0.05, seed=36)
+    d = meshes.discontinuous(m)
+    rng = np.random.default_rng(6)
+    f = rng.standard_normal(d.M)
+    for n, kw in ((3, dict(kernel="fractional", s=0.3, delta=0.3, ball="nocaps")),
+                  (8, dict(kernel="fractional", s=0.5, delta=0.3, ball="approxcaps"))):
+        ref = oracle.assemble(d, f_nodal=f, duffy_n=n, **kw)
+        S = assemble(Mesh.from_synth(m, 1, dg=True), precision="fp64", f_nodal=f, duffy_gauss=n, **kw)
+        rp, col, val = check_fp64(S, ref)
+        assert symmetric_bitwise(rp, col, val)
+    c = m.verts[m.elems].mean(1)
+    mat = ((c[:, 0] > 0.5).astype(np.int8) + 2 * (c[:, 1] > 0.5)).astype(np.int8)
+    tab = np.array([[1.0, 0.5, 0.3, 0.2], [0.5, 2.0, 0.4, 0.1], [0.3, 0.4, 3.0, 0.6], [0.2, 0.1, 0.6, 0.7]])
+    kw = dict(kernel="fractional", s=0.5, delta=0.3, ball="approxcaps")
+    ref = oracle.assemble(d, materials=mat, material_scale=tab, **kw)
+    for precision in ("fp64", "fp32_bulk"):
+        mesh = Mesh.from_synth(m, 1, dg=True)
+        mesh.set_materials(mat)
+        S = assemble(mesh, precision=precision, material_scale=tab, **kw)
+        rp, col, val = check_fp64(S, ref) if precision == "fp64" else check_bulk(S, ref)
+        assert symmetric_bitwise(rp, col, val)
+    # batched: a DG item under the singular rule beside a continuous one
+    kwb = dict(kw, precision="fp32_bulk")
+    m2 = meshes.structured(-0.1, 1.1, 16, name="s16")
+    single = [assemble(Mesh.from_synth(m, 1, dg=True), **kwb), assemble(Mesh.from_synth(m2, 1), **kwb)]
+    batch = assemble_batch([Mesh.from_synth(m, 1, dg=True), Mesh.from_synth(m2, 1)], [kwb, kwb])
+    for S0, S1 in zip(single, batch):
+        for a, b in zip(S0.csr(), S1.csr()):
+            assert torch.equal(a, b)
+    check_bulk(batch[0], oracle.assemble(d, **kw))
+
 def test_paper_E2_fractional_dg_on_gpu():
     """Sec. 3.1's DG table for the truncated fractional kernel (s = 1/2, delta = 0.2, approxcaps),
     assembled (FP32 bulk) and solved on the GPU on the first four grids: second-order rates and
