@@ -13,7 +13,8 @@ terms of eq. case-one-factoredOut): every element carries its own copy of its ve
   of the pair under the regularising maps. Pinned by the embedding identity (against the
   continuous singular rule, itself pinned by the polar evaluation), by the constant kernel's
   closed form (with every pair inside the ball, A_DG = 2c|Omega~| M - 2c m m^T with the DG mass
-  matrix M and m_i = integral of phi_i), and by Sec. 3.1's DG table (s = 1/2).
+  matrix M and m_i = integral of phi_i), by convergence to an independent polar evaluation of a
+  touching pair's integral (s = 1/4, -1/4), and by Sec. 3.1's DG table (s = 1/2).
 """
 import json
 import math
@@ -136,3 +137,41 @@ def test_paper_E2_fractional_dg_rates():
         assert 1.7 < math.log2(errs[i] / errs[i + 1]) < 2.3, errs
     for i, e in enumerate(errs):
         assert 0.4 * tab["l2"][i] < e < 2.5 * tab["l2"][i], (errs, tab["l2"])
+
+
+def _touching_pairs(mesh):
+    T = mesh.elems
+    k = int(np.argmin(np.linalg.norm(mesh.verts[T].mean(1) - 0.5, axis=1)))
+    out = {}
+    for l in range(mesh.K):
+        sh = len(set(T[k]) & set(T[l]))
+        if sh in (1, 2) and sh not in out:
+            out[sh] = (k, l)
+    return out
+
+
+@pytest.mark.parametrize("s", [0.25, -0.25])
+@pytest.mark.parametrize("shared", [2, 1])
+def test_dg_singular_rule_converges_to_independent_polar_integral(s, shared):
+    # the split integrand (phi^k(x), -phi^l(y)) of a touching pair against the polar evaluation of
+    # the same pair integral (int gamma(z) G(z) dz, G exact over the overlap of E_k and E_l - z);
+    # at s = 1/4 the local terms of an edge pair carry xi^(-1/2) at the shared edge, where the
+    # Gauss rule converges like 1/n; elsewhere the rule converges fast
+    from test_oracle_duffy import MESH, Polar
+    d = meshes.discontinuous(MESH)
+    k, l = _touching_pairs(MESH)[shared]
+    delta = 10.0
+    c = (2 - 2 * s) / (math.pi * delta ** (2 - 2 * s))
+    node, _, _ = oracle.pair_block(d, k, l, kernel="fractional", s=s, delta=delta, close_rule="duffy")
+    assert len(node) == 6
+    ref = Polar(d, k, l, node).integrate(c, s)
+    scale = np.abs(ref).max()
+    errs = []
+    for n in (5, 12, 24):
+        _, b, _ = oracle.pair_block(d, k, l, kernel="fractional", s=s, delta=delta, duffy_n=n, close_rule="duffy")
+        errs.append(np.abs(b - ref).max() / scale)
+    assert errs[0] > errs[1] > errs[2], errs
+    if s > 0 and shared == 2:
+        assert 3.0 < errs[0] / errs[2] < 8.0 and errs[2] < 0.05, errs     # first order in 1/n
+    else:
+        assert errs[2] < 1e-4, errs
