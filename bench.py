@@ -408,7 +408,32 @@ def main():
         return None
 
     e2e_ms, _ = time_steps(e2e_step, e2e_steps, 1, ws, stream)
-    e2e_value = replica_value(npairs, ws, e2e_ms / e2e_steps)
+    e2e_cold_value = replica_value(npairs, ws, e2e_ms / e2e_steps)
+    h2d_cold, d2h_cold = h2d, d2h
+
+    # the steady step end to end: a mesh handle uploaded once from the pinned host arrays (its
+    # first assembly, untimed, builds the pair list and pattern), then per step the load data
+    # from pinned host memory -> nlfem_assemble -> CSR values and F to pinned host memory
+    mh_res = binding.nlfem_mesh_create(hv, he, hl, ndof, stream)
+
+    def e2e_cached_step():
+        nonlocal out_val, out_F, d2h
+        sh = binding.nlfem_assemble(mh_res, p, hf, stream)
+        rp, col, val, n, nnz = binding.nlfem_system_csr(sh)
+        from paper_2207_03921_gb300.api import _DevView
+        vv = torch.as_tensor(_DevView(val, nnz, "<f8", None), device="cuda")
+        fv = torch.as_tensor(_DevView(binding.nlfem_system_rhs(sh), n, "<f8", None), device="cuda")
+        out_val.copy_(vv, non_blocking=True)
+        out_F.copy_(fv, non_blocking=True)
+        torch.cuda.synchronize()
+        d2h = nnz * 8 + n * 8
+        binding.nlfem_system_destroy(sh)
+        return None
+
+    e2e_ms, _ = time_steps(e2e_cached_step, max(3, min(10, args.steps)), 2, ws, stream)
+    e2e_value = replica_value(npairs, ws, e2e_ms / max(3, min(10, args.steps)))
+    binding.nlfem_mesh_destroy(mh_res)
+    h2d = hf.numel() * 8
 
     # roofline of the dominant kernel: the longest of the bulk quadrature kernels (FP32 ALU),
     # the close-list kernel (FP64 ALU, singular rule), the per-element sums and the conversion
@@ -489,7 +514,12 @@ def main():
         "cold": {"value": npairs / (cold_ms * 1e-3), "ms": cold_ms},
         "census": census,
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "path": "pinned host mesh -> nlfem_mesh_create -> nlfem_assemble (cold) -> CSR values and F to host"},
+                "path": "pinned host load data -> nlfem_assemble on a resident mesh handle (pair list and "
+                        "pattern cached) -> CSR values and F to pinned host memory",
+                "cold": {"value": e2e_cold_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d_cold,
+                         "d2h_bytes_per_step": d2h_cold,
+                         "path": "pinned host mesh -> nlfem_mesh_create -> nlfem_assemble (pair search, "
+                                 "pattern, values) -> CSR values and F to pinned host memory"}},
         # per timed step: whole-pair and cut-pair kernels, the scale check, two element sums,
         # fixed point to CSR, load vector (7; the pilot pass and the scale pick ran once, at the
         # first assembly on the pattern); with a close list also its kernel and its records' pass
