@@ -8,8 +8,9 @@ nlfem_assemble on the resident mesh with its cached pair list and pattern (value
 only: quadrature of every ordered pair, segmented reduction into CSR, load vector).
 The pair list, contributions and index (tens of GB) are far larger than L2, so every
 step streams from HBM. Also reported: the same step in plain FP64, the cold assembly
-(pair search + pattern + values), an end-to-end step through the C ABI with host
-buffers, the roofline of the quadrature kernel and the FP64 CPU oracle on a sample.
+(pair search + pattern + values), the step end to end through the C ABI with host
+buffers (steady on a resident mesh, and cold from the host mesh), the roofline of the
+quadrature kernel and the FP64 CPU oracle on a sample.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 Under torchrun (N > 1) every rank assembles its own replica of the workload (no
@@ -104,20 +105,28 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, exe="nvidia-smi", first_wait_s=3.0):
         self.index = index
+        self.exe = exe
+        self.first_wait_s = first_wait_s
         self.proc = None
         self.lines = []
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+            self.proc = subprocess.Popen([self.exe, f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
+            return self
+        # the sampler takes a moment to start: let its first sample arrive before the timed
+        # region begins, so that the samples cover that region (bounded wait)
+        t0 = time.perf_counter()
+        while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < self.first_wait_s:
+            time.sleep(0.01)
         return self
 
     def _read(self):
@@ -291,7 +300,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="720k", choices=list(WORKLOADS))
