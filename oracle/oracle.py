@@ -39,27 +39,35 @@ _lib = None
 
 
 def lib_path() -> str:
-    return LIB
+    return os.environ.get("NLFEM_ORACLE_LIB") or LIB
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (gcc, FP64, no FMA contraction)."""
+    """Compile the oracle shared library (gcc, FP64, no FMA contraction). With NLFEM_ORACLE_LIB
+    set, that prebuilt library is used instead (the tests that check the pins against copies of
+    the oracle with planted mistakes)."""
+    if os.environ.get("NLFEM_ORACLE_LIB"):
+        return os.environ["NLFEM_ORACLE_LIB"]
     os.makedirs(BUILD, exist_ok=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-               "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
-        subprocess.check_call(cmd)
+        compile_source(SRC, tmp)
         os.replace(tmp, LIB)
     return LIB
+
+
+def compile_source(src: str, out: str) -> None:
+    """gcc of one oracle source file into a shared library (the flags of the oracle's build)."""
+    cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-o", out, src, "-lm"]
+    subprocess.check_call(cmd)
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = C.CDLL(LIB)
+            lib = C.CDLL(build())
             dp = C.POINTER(C.c_double)
             ip = C.POINTER(C.c_int)
             lp = C.POINTER(C.c_longlong)

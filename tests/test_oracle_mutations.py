@@ -1,0 +1,86 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake in a copy of the
+oracle's C source (a flipped sign, a wrong index, a dropped factor, a transposed operand, a
+swapped basis function), builds that copy, and runs the fast pins against it in a child
+process, which must fail; the unchanged source, built the same way, must pass.
+
+Pins run: the DG closed form and the embedding identity, the invariants (symmetry, A 1 = 0,
+rigid motions), the singular rule's closed form and polar evaluation, the clip tests, the load
+vector's closed form, the row-wise reproduction of -Delta and the Sec. 3.1 rates.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+from oracle import oracle as orc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+PINS = [
+    "tests/test_oracle_dg.py::test_dg_singular_rule_constant_kernel_closed_form",
+    "tests/test_oracle_dg.py::test_continuous_matrix_is_the_restriction_of_the_dg_matrix",
+    "tests/test_oracle_system.py::test_invariants",
+    "tests/test_oracle_system.py::test_load_vector_closed_form_for_linear_f",
+    "tests/test_oracle_duffy.py",
+    "tests/test_oracle_clip.py",
+    "tests/test_oracle_system.py::test_constant_kernel_reproduces_laplacian_rowwise",
+    "tests/test_oracle_system.py::test_paper_E1_fractional_rates",
+]
+
+# (name, text of the oracle source, the same text with the mistake)
+MUTATIONS = [
+    ("inner basis sign", "for (int b = 0; b < 3; ++b) D[posl[b]] -= Q[b];",
+     "for (int b = 0; b < 3; ++b) D[posl[b]] += Q[b];"),
+    ("inner basis index", "for (int b = 0; b < 3; ++b) D[posl[b]] -= Q[b];",
+     "for (int b = 0; b < 3; ++b) D[b] -= Q[b];"),
+    ("sub-triangle Jacobian dropped", "double w = ap * (P->ri.w[q] * dT);",
+     "double w = ap * P->ri.w[q];"),
+    ("basis of the wrong element", "else barycentric(Vl, yx, yy, Q);",
+     "else barycentric(Vk, yx, yy, Q);"),
+    ("kernel exponent sign", "return P->c * pow(r2, -1.0 - P->s);",
+     "return P->c * pow(r2, -1.0 + P->s);"),
+    ("peridynamic tensor component", "G[1] = P->c * zx * zy / r3;",
+     "G[1] = P->c * zx * zx / r3;"),
+    ("cap centre on the wrong side",
+     "out[m][0] = cx + delta * (qy / len);\n                    out[m][1] = cy + delta * (-qx / len);",
+     "out[m][0] = cx + delta * (-qy / len);\n                    out[m][1] = cy + delta * (qx / len);"),
+    ("edge-pair Duffy weight", "wq * scale * xi * xi * L * wr", "wq * scale * xi * L * wr"),
+    ("vertex-pair Duffy basis", "D[upos[3]] = -y1 * (1.0 - w2);", "D[upos[3]] = -y1 * w2;"),
+    ("identical-pair Duffy difference", "D1 = xi * (h2 - h1)", "D1 = xi * (h1 - h2)"),
+    ("DG split basis transposed",
+     "D[lpos[0]] = -(1.0 - y1); D[lpos[1]] = -(y1 - y2); D[lpos[2]] = -y2;",
+     "D[lpos[0]] = -(1.0 - y1); D[lpos[1]] = -y2; D[lpos[2]] = -(y1 - y2);"),
+    ("load vector basis transposed", "+= ap * fx * P.ro.l[p][a];", "+= ap * fx * P.ro.l[p][(a + 1) % 3];"),
+    ("outer point map", "*x = (l[0] * V[0][0] + l[1] * V[1][0]) + l[2] * V[2][0];",
+     "*x = (l[0] * V[0][0] + l[2] * V[1][0]) + l[1] * V[2][0];"),
+]
+
+
+def _run_pins(lib):
+    env = dict(os.environ, NLFEM_ORACLE_LIB=lib, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"))
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-W", "ignore", "-m", "not gpu"]
+    return subprocess.run(cmd + PINS, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def _build(tmp_path, src_text, name):
+    src = tmp_path / f"{name}.c"
+    src.write_text(src_text)
+    lib = str(tmp_path / f"lib{name}.so")
+    orc.compile_source(str(src), lib)
+    return lib
+
+
+def test_pins_pass_on_the_unchanged_oracle(tmp_path):
+    text = open(orc.SRC).read()
+    r = _run_pins(_build(tmp_path, text, "orig"))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_a_planted_mistake_fails_a_pin(tmp_path, name, old, new):
+    text = open(orc.SRC).read()
+    assert text.count(old) == 1, f"mutation site not unique or missing: {old!r}"
+    r = _run_pins(_build(tmp_path, text.replace(old, new), "mut"))
+    assert r.returncode == 1, f"{name}: no pin failed\n{r.stdout[-2000:]}"

@@ -108,6 +108,23 @@ def test_load_vector_partition_of_unity():
     assert np.all(S.F[S.dirichlet & ~np.isin(np.arange(m.M), m.elems[m.elem_label == 1])] == 0)
 
 
+def test_load_vector_closed_form_for_linear_f():
+    # F_i = sum over Omega elements E of int_E f phi_i, and for f in P1 with nodal values f_a
+    # the element integral is |E| (2 f_a + f_b + f_c) / 12 (exact for the 7- and 16-point rules)
+    m = meshes.jittered_delaunay(-0.2, 1.2, 10, 0.1, seed=9)
+    f = 2.0 + 3.0 * m.verts[:, 0] - 5.0 * m.verts[:, 1]
+    want = np.zeros(m.M)
+    for e in np.flatnonzero(m.elem_label == 1):
+        t = m.elems[e]
+        P = m.verts[t]
+        area = 0.5 * abs((P[1, 0] - P[0, 0]) * (P[2, 1] - P[0, 1]) - (P[1, 1] - P[0, 1]) * (P[2, 0] - P[0, 0]))
+        for a in range(3):
+            want[t[a]] += area * (2.0 * f[t[a]] + f[t[(a + 1) % 3]] + f[t[(a + 2) % 3]]) / 12.0
+    for nq in (7, 16):
+        S = oracle.assemble(m, kernel="constant", delta=0.3, f_nodal=f, quad_outer=nq)
+        assert np.abs(S.F - want).max() < 1e-14 * np.abs(want).max()
+
+
 def _e1(level):
     a = GOLD["E1_fractional_cg"]["a"][level]
     m = meshes.paper_square(0.2, a)
