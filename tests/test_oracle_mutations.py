@@ -4,8 +4,9 @@ swapped basis function), builds that copy, and runs the fast pins against it in 
 process, which must fail; the unchanged source, built the same way, must pass.
 
 Pins run: the DG closed form and the embedding identity, the invariants (symmetry, A 1 = 0,
-rigid motions), the singular rule's closed form and polar evaluation, the clip tests, the load
-vector's closed form, the row-wise reproduction of -Delta and the Sec. 3.1 rates.
+rigid motions), the load vector's closed form, the singular rule's closed form and polar
+evaluation, the clip tests (both balls), the label-dependent and tabulated kernels' closed
+forms, the row-wise reproduction of -Delta and the Sec. 3.1 rates.
 """
 import os
 import subprocess
@@ -25,6 +26,9 @@ PINS = [
     "tests/test_oracle_system.py::test_load_vector_closed_form_for_linear_f",
     "tests/test_oracle_duffy.py",
     "tests/test_oracle_clip.py",
+    "tests/test_oracle_clip_square.py",
+    "tests/test_oracle_materials.py",
+    "tests/test_oracle_tabulated.py",
     "tests/test_oracle_system.py::test_constant_kernel_reproduces_laplacian_rowwise",
     "tests/test_oracle_system.py::test_paper_E1_fractional_rates",
 ]
@@ -55,6 +59,10 @@ MUTATIONS = [
     ("load vector basis transposed", "+= ap * fx * P.ro.l[p][a];", "+= ap * fx * P.ro.l[p][(a + 1) % 3];"),
     ("outer point map", "*x = (l[0] * V[0][0] + l[1] * V[1][0]) + l[2] * V[2][0];",
      "*x = (l[0] * V[0][0] + l[2] * V[1][0]) + l[1] * V[2][0];"),
+    ("material of the wrong element", "fm = mscale[mat[S->pairs[2 * pq]] * nmat + mat[S->pairs[2 * pq + 1]]];",
+     "fm = mscale[mat[S->pairs[2 * pq]] * nmat + mat[S->pairs[2 * pq]]];"),
+    ("table interpolation weight", "double w = t - i;", "double w = 1.0 - (t - i);"),
+    ("square clip half-plane", "n = sh_pass(B, n, 1, -1.0, delta, A);", "n = sh_pass(B, n, 1, 1.0, delta, A);"),
 ]
 
 

@@ -6,6 +6,7 @@ linear between table values at r_i = i delta / (n - 1) (the Conclusion: user-def
 - The matrix is linear in the table values; symmetry and A 1 = 0 hold for any table.
 - Tables of g(r) = r^2 with 2, 4, 8, 16 intervals: the interpolation error is at most
   (delta / (n - 1))^2 / 4, so successive matrices approach each other at second order.
+- A table of g(r) = r is interpolated exactly: it reproduces c |z|^(-2-2s) at s = -3/2.
 """
 import numpy as np
 import pytest
@@ -53,3 +54,15 @@ def test_piecewise_linear_table_converges_second_order(mesh):
     diffs = [np.abs(vals[i + 1] - vals[i]).max() for i in range(3)]
     rates = [np.log2(diffs[i] / diffs[i + 1]) for i in range(2)]
     assert all(1.7 < q < 2.3 for q in rates), (diffs, rates)
+
+
+def test_linear_table_is_the_power_kernel(mesh):
+    # g(r) = r is interpolated exactly by the table, and c |z|^(-2-2s) with s = -3/2 is c |z|:
+    # both assemblies agree to rounding wherever every point lies within delta (Euclidean balls)
+    d = 0.3
+    for ball in ("nocaps", "approxcaps"):
+        A = oracle.assemble(mesh, kernel="fractional", s=-1.5, delta=d, ball=ball, kconst=2.0)
+        B = oracle.assemble(mesh, kernel="tabulated", delta=d, ball=ball, kconst=2.0,
+                            kernel_table=np.linspace(0.0, d, 7))
+        assert np.array_equal(A.col, B.col)
+        assert np.abs(A.val - B.val).max() < 1e-13 * np.abs(A.val).max()
