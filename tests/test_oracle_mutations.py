@@ -11,10 +11,8 @@ forms, the row-wise reproduction of -Delta and the Sec. 3.1 rates.
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
-import pytest
-
-import oracle
 from oracle import oracle as orc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -31,6 +29,7 @@ PINS = [
     "tests/test_oracle_tabulated.py",
     "tests/test_oracle_system.py::test_constant_kernel_reproduces_laplacian_rowwise",
     "tests/test_oracle_system.py::test_paper_E1_fractional_rates",
+    "tests/test_oracle_system.py::test_peridynamic_kernel_reproduces_navier_rowwise",
 ]
 
 # (name, text of the oracle source, the same text with the mistake)
@@ -63,32 +62,34 @@ MUTATIONS = [
      "fm = mscale[mat[S->pairs[2 * pq]] * nmat + mat[S->pairs[2 * pq]]];"),
     ("table interpolation weight", "double w = t - i;", "double w = 1.0 - (t - i);"),
     ("square clip half-plane", "n = sh_pass(B, n, 1, -1.0, delta, A);", "n = sh_pass(B, n, 1, 1.0, delta, A);"),
+    ("circle crossing root", "t2 = (-B + r) / A;", "t2 = (B + r) / A;"),
+    ("edge quadratic term", "double B = ex * ux + ey * uy;", "double B = ex * ux - ey * uy;"),
+    ("vertex on the circle", "inside[a] = (dx * dx + dy * dy) <= delta2;", "inside[a] = (dx * dx + dy * dy) < delta2;"),
+    ("peridynamic kernel power", "double r3 = r2 * sqrt(r2);", "double r3 = r2 * r2;"),
 ]
 
 
 def _run_pins(lib):
-    env = dict(os.environ, NLFEM_ORACLE_LIB=lib, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"))
+    env = dict(os.environ, NLFEM_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
     cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-W", "ignore", "-m", "not gpu"]
-    return subprocess.run(cmd + PINS, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return subprocess.run(cmd + PINS, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
 
 
-def _build(tmp_path, src_text, name):
-    src = tmp_path / f"{name}.c"
-    src.write_text(src_text)
-    lib = str(tmp_path / f"lib{name}.so")
-    orc.compile_source(str(src), lib)
-    return lib
-
-
-def test_pins_pass_on_the_unchanged_oracle(tmp_path):
+def test_planted_mistakes_fail_a_pin_and_the_oracle_passes(tmp_path):
     text = open(orc.SRC).read()
-    r = _run_pins(_build(tmp_path, text, "orig"))
-    assert r.returncode == 0, r.stdout[-2000:]
-
-
-@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_a_planted_mistake_fails_a_pin(tmp_path, name, old, new):
-    text = open(orc.SRC).read()
-    assert text.count(old) == 1, f"mutation site not unique or missing: {old!r}"
-    r = _run_pins(_build(tmp_path, text.replace(old, new), "mut"))
-    assert r.returncode == 1, f"{name}: no pin failed\n{r.stdout[-2000:]}"
+    jobs = [("unchanged", text)]
+    for name, old, new in MUTATIONS:
+        assert text.count(old) == 1, f"mutation site not unique or missing: {old!r}"
+        jobs.append((name, text.replace(old, new)))
+    libs = []
+    for i, (_, src_text) in enumerate(jobs):
+        src = tmp_path / f"v{i}.c"
+        src.write_text(src_text)
+        libs.append(str(tmp_path / f"libv{i}.so"))
+        orc.compile_source(str(src), libs[-1])
+    # the children run in parallel (each pin run stops at its first failure)
+    with ThreadPoolExecutor(max_workers=max(1, min(6, (os.cpu_count() or 2) // 2))) as ex:
+        runs = list(ex.map(_run_pins, libs))
+    assert runs[0].returncode == 0, runs[0].stdout[-2000:]
+    missed = [name for (name, _), r in zip(jobs[1:], runs[1:]) if r.returncode != 1]
+    assert not missed, f"no pin failed for: {missed}"

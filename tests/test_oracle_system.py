@@ -9,7 +9,8 @@
   and the diagonal is positive.
 - P7: with the constants of Sec. 3 the discrete operator reproduces -Delta on
   x^2 + y^2 row by row, up to the O(h^2) ball approximation error (Z1: the
-  factor 2 of eq. strongL).
+  factor 2 of eq. strongL), and the peridynamic one -(pi/4) Delta u - (pi/2) grad div u
+  on u = (y^2, x^2 y).
 - P6: the manufactured solutions of Sec. 3.1 / 3.2 converge at second order
   (Tabs. tab:hto0fractionalCG and tab:hto0peridynamicsCG).
 """
@@ -95,6 +96,25 @@ def test_constant_kernel_reproduces_laplacian_rowwise():
     assert errs[-1] < 0.05
     assert math.log2(errs[0] / errs[1]) > 1.5 and math.log2(errs[1] / errs[2]) > 1.5, errs
 
+
+def test_peridynamic_kernel_reproduces_navier_rowwise():
+    # P7 for peridynamics: with c = 3 / delta^3 the operator is -(pi/4) Delta u - (pi/2) grad div u
+    # (the factor-2 reading of eq. strongL); for u = (y^2, x^2 y) that is -(pi/2) (1 + 2x, y), and
+    # (A I_h u)_i / int phi_i approaches it row by row at second order (fixed delta)
+    delta = 0.2
+    errs = []
+    for n in (8, 16, 32):
+        m = meshes.structured(-delta, 1 + delta, int(round((1 + 2 * delta) * n)))
+        x, y = m.verts[:, 0], m.verts[:, 1]
+        S = oracle.assemble(m, kernel="peridynamic", delta=delta, ball="approxcaps",
+                            f_nodal=np.stack([np.ones(m.M), np.ones(m.M)], 1))
+        g = np.stack([y * y, x * x * y], 1).reshape(-1)
+        inner = (x > 0.3) & (x < 0.7) & (y > 0.3) & (y < 0.7)
+        r = (S.scipy() @ g).reshape(-1, 2)[inner] / S.F.reshape(-1, 2)[inner]
+        want = -0.5 * math.pi * np.stack([1.0 + 2.0 * x, y], 1)[inner]
+        errs.append(np.max(np.abs(r - want)))
+    assert errs[-1] < 0.05, errs
+    assert math.log2(errs[0] / errs[1]) > 1.5 and math.log2(errs[1] / errs[2]) > 1.5, errs
 
 def test_load_vector_partition_of_unity():
     m = meshes.jittered_delaunay(-0.2, 1.2, 10, 0.1, seed=9)
