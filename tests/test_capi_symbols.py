@@ -39,3 +39,24 @@ def test_library_is_in_tree_and_not_a_cpu_fallback():
     assert os.path.dirname(os.path.dirname(path)).endswith("paper_2207_03921_gb300")
     lib = ctypes.CDLL(path)
     assert hasattr(lib, "nlfem_assemble")
+
+
+def test_null_handles_fail_with_invalid_arg_and_a_thread_local_message():
+    # host-side argument checks: no CUDA call is made before them
+    import threading
+    lib = binding.load()
+    info = binding.nlfem_assembly_info()
+    assert lib.nlfem_system_info(None, ctypes.byref(info)) == -1 and binding.ERRORS[-1] == "INVALID_ARG"
+    msg = binding.nlfem_last_error()
+    assert "NULL" in msg
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(binding.nlfem_last_error()))
+    t.start()
+    t.join()
+    assert seen == [""]                      # the message belongs to the failing thread
+    assert binding.nlfem_last_error() == msg
+    # destroying a NULL handle is a no-op
+    lib.nlfem_mesh_destroy(None)
+    lib.nlfem_system_destroy(None)
+    lib.nlfem_batch_destroy(None)
+    assert lib.nlfem_mesh_device_bytes(None) == 0
