@@ -7,6 +7,8 @@
   conical product of a 4-point Gauss-Jacobi rule (weight 1 - u on [0, 1]) and a
   4-point Gauss-Legendre rule, exact for total degree <= 7. Nodes are polished
   by Newton's method in 50-digit decimal arithmetic and rounded once to double.
+  Parity unpinned against the paper, which prints no 16-point rule: the rule is pinned
+  to its own definition only (exact for total degree <= 7, positive weights, points inside).
 - Gauss-Legendre rules on [0, 1] for the tensor rule of the regularising
   transforms (Sec. 3.1: a tensor product of a 5-point Gauss rule).
 
