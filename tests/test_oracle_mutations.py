@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible mistakes: each case plants one mistake in a copy of the
 oracle's C source (a flipped sign, a wrong index, a dropped factor, a transposed operand, a
-swapped basis function), builds that copy, and runs the fast pins against it in a child
-process, which must fail; the unchanged source, built the same way, must pass.
+swapped basis function) or of its Python part (the Dirichlet split, the null space, the error
+norm, a rule weight), and runs the fast pins against it in a child process, which must fail;
+the unchanged oracle must pass.
 
 Pins run: the DG closed form and the embedding identity, the invariants (symmetry, A 1 = 0,
 rigid motions), the load vector's closed form, the singular rule's closed form and polar
@@ -30,6 +31,9 @@ PINS = [
     "tests/test_oracle_system.py::test_constant_kernel_reproduces_laplacian_rowwise",
     "tests/test_oracle_system.py::test_paper_E1_fractional_rates",
     "tests/test_oracle_system.py::test_peridynamic_kernel_reproduces_navier_rowwise",
+    "tests/test_oracle_system.py::test_l2_error_closed_forms",
+    "tests/test_oracle_neumann.py",
+    "tests/test_oracle_rules.py",
 ]
 
 # (name, text of the oracle source, the same text with the mistake)
@@ -69,27 +73,61 @@ MUTATIONS = [
 ]
 
 
-def _run_pins(lib):
-    env = dict(os.environ, NLFEM_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
+# mistakes in the oracle's Python part: (file of the oracle package, name, text, mistake)
+PY_MUTATIONS = [
+    ("oracle.py", "Dirichlet column split sign", "b = system.F[free] - A[free][:, dof_d] @ g[dof_d]",
+     "b = system.F[free] + A[free][:, dof_d] @ g[dof_d]"),
+    ("oracle.py", "rotation mode of the null space", "Z[:, 0, 2] = -X[:, 1]", "Z[:, 0, 2] = X[:, 1]"),
+    ("oracle.py", "L2 error Jacobian", "err += np.sum(w * det *", "err += np.sum(w * 0.5 * det *"),
+    ("rules.py", "7-point rule weight", "(third, third, third, 27.0 / 120.0)", "(third, third, third, 27.0 / 60.0)"),
+]
+
+
+def _run_pins(job):
+    """The pins in a child process against a copy of the oracle package (the child's working
+    directory holds it, so it is imported first) and a build of the oracle's C source."""
+    cwd, lib = job
+    env = dict(os.environ, NLFEM_ORACLE_LIB=lib, OMP_NUM_THREADS="2", PYTHONPATH=ROOT)
     cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-W", "ignore", "-m", "not gpu"]
-    return subprocess.run(cmd + PINS, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    return subprocess.run(cmd + [os.path.join(ROOT, p) for p in PINS], cwd=cwd, env=env,
+                          capture_output=True, text=True, timeout=900)
+
+
+def _package_copy(root, mutation=None):
+    pkg = os.path.dirname(orc.SRC)
+    d = root / "oracle"
+    d.mkdir(parents=True)
+    for f in ("__init__.py", "oracle.py", "rules.py"):
+        t = open(os.path.join(pkg, f)).read()
+        if mutation and f == mutation[0]:
+            assert t.count(mutation[2]) == 1, f"mutation site not unique or missing: {mutation[2]!r}"
+            t = t.replace(mutation[2], mutation[3])
+        (d / f).write_text(t)
+    return str(root)
 
 
 def test_planted_mistakes_fail_a_pin_and_the_oracle_passes(tmp_path):
     text = open(orc.SRC).read()
-    jobs = [("unchanged", text)]
+    base = _package_copy(tmp_path / "base")
+    jobs = []                                    # (name, C source text, package directory)
+    jobs.append(("unchanged", text, base))
     for name, old, new in MUTATIONS:
         assert text.count(old) == 1, f"mutation site not unique or missing: {old!r}"
-        jobs.append((name, text.replace(old, new)))
-    libs = []
-    for i, (_, src_text) in enumerate(jobs):
-        src = tmp_path / f"v{i}.c"
-        src.write_text(src_text)
-        libs.append(str(tmp_path / f"libv{i}.so"))
-        orc.compile_source(str(src), libs[-1])
+        jobs.append((name, text.replace(old, new), base))
+    for i, mu in enumerate(PY_MUTATIONS):
+        jobs.append((mu[1], text, _package_copy(tmp_path / f"py{i}", mu)))
+    built = {}
+    runs_in = []
+    for i, (name, src_text, cwd) in enumerate(jobs):
+        if src_text not in built:
+            src = tmp_path / f"v{i}.c"
+            src.write_text(src_text)
+            built[src_text] = str(tmp_path / f"libv{i}.so")
+            orc.compile_source(str(src), built[src_text])
+        runs_in.append((cwd, built[src_text]))
     # the children run in parallel (each pin run stops at its first failure)
     with ThreadPoolExecutor(max_workers=max(1, min(6, (os.cpu_count() or 2) // 2))) as ex:
-        runs = list(ex.map(_run_pins, libs))
+        runs = list(ex.map(_run_pins, runs_in))
     assert runs[0].returncode == 0, runs[0].stdout[-2000:]
-    missed = [name for (name, _), r in zip(jobs[1:], runs[1:]) if r.returncode != 1]
+    missed = [name for (name, _, _), r in zip(jobs[1:], runs[1:]) if r.returncode != 1]
     assert not missed, f"no pin failed for: {missed}"

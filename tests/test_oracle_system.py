@@ -223,3 +223,17 @@ def test_paper_E6_infinity_ball_rates():
 def test_paper_E1_fractional_rates_level3():
     runs = [_e1(k) for k in range(4)]
     _check(GOLD["E1_fractional_cg"], runs)
+
+
+def test_l2_error_closed_forms():
+    # the error norm of the convergence pins: Omega = (0, 1)^2 exactly (grid lines at 0 and 1),
+    # ||1|| = 1, ||x|| = 1/sqrt(3), ||(1, x)|| = 2/sqrt(3) (the 7-point rule is exact for degree 2),
+    # and a linear function is reproduced by its P1 interpolant
+    m = meshes.structured(-0.2, 1.2, 14)
+    x, y = m.verts[:, 0], m.verts[:, 1]
+    z = np.zeros(m.M)
+    assert abs(oracle.l2_error(m, z, lambda x, y: 1.0 + 0 * x) - 1.0) < 1e-14
+    assert abs(oracle.l2_error(m, z, lambda x, y: x) - 1.0 / math.sqrt(3.0)) < 1e-14
+    assert abs(oracle.l2_error(m, np.zeros(2 * m.M), lambda x, y: np.stack([1.0 + 0 * x, x]), ndof=2)
+               - 2.0 / math.sqrt(3.0)) < 1e-14
+    assert oracle.l2_error(m, 2.0 - 3.0 * x + 5.0 * y, lambda x, y: 2.0 - 3.0 * x + 5.0 * y) < 1e-13
