@@ -22,6 +22,7 @@ PINS = [
     "tests/test_oracle_dg.py::test_dg_singular_rule_constant_kernel_closed_form",
     "tests/test_oracle_dg.py::test_continuous_matrix_is_the_restriction_of_the_dg_matrix",
     "tests/test_oracle_system.py::test_invariants",
+    "tests/test_oracle_system.py::test_bfs_pairs_equal_brute_force",
     "tests/test_oracle_system.py::test_load_vector_closed_form_for_linear_f",
     "tests/test_oracle_duffy.py",
     "tests/test_oracle_clip.py",
@@ -70,6 +71,8 @@ MUTATIONS = [
     ("edge quadratic term", "double B = ex * ux + ey * uy;", "double B = ex * ux - ey * uy;"),
     ("vertex on the circle", "inside[a] = (dx * dx + dy * dy) <= delta2;", "inside[a] = (dx * dx + dy * dy) < delta2;"),
     ("peridynamic kernel power", "double r3 = r2 * sqrt(r2);", "double r3 = r2 * r2;"),
+    ("traversal stops after the first layer", "{ ivec_push(&queue, l); ivec_push(res, l); }",
+     "{ if (e == k) ivec_push(&queue, l); ivec_push(res, l); }"),
 ]
 
 
