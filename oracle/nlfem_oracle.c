@@ -893,7 +893,10 @@ void orc_free(void *p) { free(p); }
 
 /* Full assembly: A_h^# over all nodes of the base domain (block per ordered pair,
  * summed into CSR in (k, l, p, q) order), F over Omega elements. If elem_subset is
- * given (n_subset outer elements), only pairs with k in the subset are assembled. */
+ * given (n_subset outer elements), only pairs with k in the subset are assembled. If
+ * node_keep is given (M flags), only pairs with a flagged node among the vertices of E_k
+ * or E_l are kept: every pair that writes into the row of a flagged node is one of them, so
+ * those rows are the full assembly's rows, summed in the same (k, l, p, q) order. */
 orc_sys *orc_assemble(int M, const double *X, int K, const int *T, const signed char *lab,
                       int kernel, double delta, double s, double kconst, int ball,
                       int nqo, const double *qo, int nqi, const double *qi, int close_rule,
@@ -901,7 +904,7 @@ orc_sys *orc_assemble(int M, const double *X, int K, const int *T, const signed 
                       const double *f_nodal, int mode, int nthreads,
                       int n_subset, const int *elem_subset,
                       const signed char *mat, int nmat, const double *mscale,
-                      int ntab, const double *tab)
+                      int ntab, const double *tab, const signed char *node_keep)
 {
     mesh_t m;
     build_mesh(&m, M, X, K, T, lab);
@@ -929,6 +932,16 @@ orc_sys *orc_assemble(int M, const double *X, int K, const int *T, const signed 
         for (int i = 0; i < nk; ++i) {
             int k = n_subset > 0 ? elem_subset[i] : i;
             search_partners(&m, &P, k, mode, &lists[i], visited, &vs, nbmark, &ns, &cnt);
+            if (node_keep) {
+                int kk = 0;
+                for (int t = 0; t < lists[i].n; ++t) {
+                    const int l = lists[i].v[t];
+                    int hit = 0;
+                    for (int a = 0; a < 3; ++a) hit |= node_keep[m.T[3 * k + a]] | node_keep[m.T[3 * l + a]];
+                    if (hit) lists[i].v[kk++] = l;
+                }
+                lists[i].n = kk;
+            }
         }
         free(visited); free(nbmark);
     }

@@ -76,7 +76,7 @@ def _load():
             lib.orc_assemble.argtypes = [C.c_int, dp, C.c_int, ip, cp, C.c_int, C.c_double, C.c_double,
                                          C.c_double, C.c_int, C.c_int, dp, C.c_int, dp, C.c_int, C.c_int,
                                          dp, dp, C.c_int, dp, C.c_int, C.c_int, C.c_int, ip, cp, C.c_int, dp,
-                                         C.c_int, dp]
+                                         C.c_int, dp, cp]
             lib.orc_sys_sizes.argtypes = [C.c_void_p, lp]
             lib.orc_sys_copy.argtypes = [C.c_void_p, lp, ip, dp, dp, ip, cp, cp, lp]
             lib.orc_sys_free.argtypes = [C.c_void_p]
@@ -138,12 +138,15 @@ def _kernel_args(kernel, delta, s, kconst, ball, quad_outer, quad_inner, close_r
 def assemble(mesh, kernel: str = "constant", delta: float = 0.1, s: float = -1.0, kconst=None,
              ball: str = "nocaps", quad_outer: int = 7, quad_inner: int = 7, close_rule: str = "auto",
              duffy_n: int = 5, f_nodal=None, pairs_mode: str = "bfs", threads: int = 0,
-             elem_subset=None, materials=None, material_scale=None, kernel_table=None) -> OracleSystem:
+             elem_subset=None, materials=None, material_scale=None, kernel_table=None,
+             node_keep=None) -> OracleSystem:
     """FP64 assembly of A_h^# and F. materials [K] (0..n-1) with the symmetric n x n table
     material_scale make the kernel label dependent: Psi on E_k x E_l times
     material_scale[materials[k], materials[l]] (Sec. 1, interface problems). kernel="tabulated"
     takes the user kernel c g(|z|) from kernel_table (g at r_i = i delta / (n - 1), linear in
-    between, held beyond delta; c = kconst, default 1)."""
+    between, held beyond delta; c = kconst, default 1). node_keep [M] (bool): keep only the
+    pairs with a flagged node among the vertices of E_k or E_l; the rows of the flagged nodes
+    are then those of the full assembly (every pair writing into them is kept)."""
     lib = _load()
     ndof = 2 if kernel == "peridynamic" else 1
     (kid, delta, s, kc, bid, qo, qi, cid, gx, gw) = _kernel_args(
@@ -165,6 +168,10 @@ def assemble(mesh, kernel: str = "constant", delta: float = 0.1, s: float = -1.0
         msc = np.ascontiguousarray(material_scale, dtype=np.float64)
         nmat = int(msc.shape[0])
         assert msc.shape == (nmat, nmat) and mat.shape == (mesh.K,) and 0 <= mat.min() and mat.max() < nmat
+    keep = None
+    if node_keep is not None:
+        keep = np.ascontiguousarray(np.asarray(node_keep).reshape(-1).astype(np.int8))
+        assert keep.shape == (mesh.M,)
     sub = None
     nsub = 0
     if elem_subset is not None:
@@ -178,7 +185,8 @@ def assemble(mesh, kernel: str = "constant", delta: float = 0.1, s: float = -1.0
                          _p(sub, C.c_int) if sub is not None else None,
                          _p(mat, C.c_byte) if mat is not None else None, nmat,
                          _p(msc, C.c_double) if msc is not None else None,
-                         len(tab) if tab is not None else 0, _p(tab, C.c_double) if tab is not None else None)
+                         len(tab) if tab is not None else 0, _p(tab, C.c_double) if tab is not None else None,
+                         _p(keep, C.c_byte) if keep is not None else None)
     sz = np.zeros(3, dtype=np.int64)
     lib.orc_sys_sizes(h, _p(sz, C.c_longlong))
     N, nnz, npairs = (int(v) for v in sz)
