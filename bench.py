@@ -249,6 +249,154 @@ def traffic_from_profiles(kernel_name, workload):
         return None
 
 
+def peaks_tflops(pk):
+    """FP32 and FP64 vector peaks from the unit counts and the maximum SM clock, and the HBM peak."""
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s: 128 FP32 lanes per SM, FMA = 2
+    fp64 = 152 * 2 * 2 * sm_max * 1e6 / 1e12        # 2 FP64 FMA lanes per SM and clock
+    return fp32, fp64, pk.get("hbm_gbs", 6800.0)
+
+
+def kernel_rooflines(wl, census, info0, timed, npairs, ndof, pk, sing32):
+    """Achieved algorithmic FLOP/s (or bytes/s) of every kernel of the FP32-bulk step against
+    the peak of the pipe its arithmetic runs on (the singular rule: FP64 or FP32)."""
+    fp32_peak, fp64_peak, hbm_peak = peaks_tflops(pk)
+    fpe = FLOPS_PER_EVAL[wl["kernel"]]
+    nqi = wl["quad_inner"]
+
+    def mean(key):
+        return statistics.mean(i[key] for i in timed)
+
+    ms_whole, ms_cut, ms_close, ms_sums = mean("ms_whole"), mean("ms_cut"), mean("ms_close"), mean("ms_sums")
+    red_ms = mean("ms_reduce")
+    flops_whole = census["evals_whole"] * fpe + (census["evals_whole"] // nqi) * FLOPS_PER_OUTER
+    flops_cut = (census["evals_cut"] * fpe + census["nonempty_points_cut"] * FLOPS_PER_OUTER
+                 + census["outer_points_cut"] * FLOPS_VERTEX_TESTS
+                 + census["cut_points_cut"] * (0 if wl["ball"] == "infinity" else
+                                               FLOPS_EDGES + (FLOPS_CAPS if wl["ball"] == "approxcaps" else 0))
+                 + census["subtri_evals_cut"] * FLOPS_SUBTRI_POINT)
+    flops_duffy = census["duffy_points"] * FLOPS_DUFFY_POINT
+    nc = 1 if ndof == 1 else 3
+    sums_bytes = npairs * (24 + 24 + 4) * nc                     # kk records, ll records (gathered), pT ids
+    conv_bytes = (info0["n_upper"] * 8 * nc + info0["nnz"] // (ndof * ndof) * 4  # fixed-point entries, columns
+                  + info0["nnz"] // 2 * 8 + info0["nnz"] * 8)     # transposed positions, values written
+
+    def rate(x, ms, scale):
+        return x / (ms * 1e-3) / scale if ms > 0 else 0.0
+
+    kernels = {
+        "k_trunc_whole": {"bound": "alu", "ms": ms_whole, "units": info0["pairs_whole"],
+                          "achieved": rate(flops_whole, ms_whole, 1e12), "peak": fp32_peak, "unit": "TFLOP/s",
+                          "pipe": "fp32"},
+        "k_trunc_cut": {"bound": "alu", "ms": ms_cut, "units": census["outer_points_cut"] // wl["quad_outer"],
+                        "achieved": rate(flops_cut, ms_cut, 1e12), "peak": fp32_peak, "unit": "TFLOP/s",
+                        "pipe": "fp32"},
+        "k_elem_sums": {"bound": "hbm", "ms": ms_sums, "units": npairs,
+                        "achieved": rate(sums_bytes, ms_sums, 1e9), "peak": hbm_peak, "unit": "GB/s"},
+        "k_acc_to_csr": {"bound": "hbm", "ms": red_ms, "units": info0["n_upper"],
+                         "achieved": rate(conv_bytes, red_ms, 1e9), "peak": hbm_peak, "unit": "GB/s"},
+    }
+    if census["singular_pairs"]:
+        kernels["k_duffy"] = {"bound": "alu", "ms": ms_close, "units": census["singular_pairs"],
+                              "achieved": rate(flops_duffy, ms_close, 1e12),
+                              "peak": fp32_peak if sing32 else fp64_peak, "unit": "TFLOP/s",
+                              "pipe": "fp32" if sing32 else "fp64"}
+    for k in kernels.values():
+        k["frac"] = k["achieved"] / k["peak"]
+    if wl["ball"] == "infinity":
+        kernels["k_trunc_cut"]["note"] = ("FP32 quadrature work only: the square's Sutherland-Hodgman cut runs in "
+                                          "FP32 with exact decisions or, near ties, in FP64 (FP64-pipe bound on "
+                                          "grids aligned with the square)")
+    return kernels
+
+
+def rel_frobenius(sa, sb):
+    """||val_a - val_b|| / ||val_b|| of two systems on the same pattern (on the device)."""
+    import torch
+    _, ca, va = sa.csr_views()
+    _, cb, vb = sb.csr_views()
+    assert torch.equal(ca, cb), "patterns differ"
+    return float(torch.linalg.vector_norm(va - vb) / torch.linalg.vector_norm(vb))
+
+
+def measure_config(name, steps, warmup, local, pk, with_cpu=True, variants=()):
+    """One benchmark configuration besides the headline: the FP32-bulk cached step timed with
+    CUDA events (clocks sampled during it), plain FP64 on the same GPU, the error of the bulk
+    result against the FP64 path, the per-kernel roofline and an oracle sample; variants:
+    the same step with another arithmetic of the singular rule or of the cut geometry."""
+    import torch
+    from paper_2207_03921_gb300 import Mesh, assemble
+    wl = WORKLOADS[name]
+    m = make_mesh(wl["mesh"])
+    ndof = 2 if wl["kernel"] == "peridynamic" else 1
+    kw = {k: wl[k] for k in ("kernel", "delta", "ball", "quad_outer", "quad_inner") if k in wl}
+    if "s" in wl:
+        kw["s"] = wl["s"]
+    stream = torch.cuda.current_stream()
+    f = torch.as_tensor(np.random.default_rng(0).standard_normal(m.M * ndof)).cuda()
+    mesh = Mesh.from_synth(m, ndof)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = assemble(mesh, precision="fp32_bulk", f_nodal=f, **kw)
+    torch.cuda.synchronize()
+    cold_ms = (time.perf_counter() - t0) * 1e3
+    info0 = S.info()
+    census = S.census()
+    npairs = info0["npairs"]
+    del S
+    out = {"desc": wl["desc"], "pairs": npairs, "nnz": info0["nnz"], "cold_ms": cold_ms,
+           "singular_precision": "fp64" if census["singular_pairs"] else None, "geometry_precision": "exact32"}
+
+    def timed_bulk(extra, nsteps):
+        infos = []
+
+        def step():
+            infos.append(assemble(mesh, precision="fp32_bulk", f_nodal=f, **kw, **extra).info())
+
+        with ClockSampler(local) as clk:
+            ms, _ = time_steps(step, nsteps, warmup, 1, stream)
+        return ms / nsteps, infos[warmup:], clk.summary()
+
+    ms_step, timed, clocks = timed_bulk({}, steps)
+    out.update({"ms_per_step": ms_step, "value": npairs / (ms_step * 1e-3), "unit": "pairs/s", "clocks": clocks,
+                "breakdown_ms": {k: statistics.mean(i["ms_" + k] for i in timed)
+                                 for k in ("whole", "cut", "close", "sums", "reduce")}})
+    kernels = kernel_rooflines(wl, census, info0, timed, npairs, ndof, pk, sing32=False)
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    out["roofline"] = dict(kernels[dom], kernel=dom, kernels=kernels)
+    # plain FP64 on the same GPU, and the error of the bulk result against it (the FP64 path
+    # equals the oracle to 1e-12 entrywise in the parity tests)
+    S64 = assemble(mesh, precision="fp64", f_nodal=f, **kw)   # warm-up (slot index built on first use)
+    del S64
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S64 = assemble(mesh, precision="fp64", f_nodal=f, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    out["fp64_plain"] = {"ms_per_step": ms64, "value": npairs / (ms64 * 1e-3),
+                         "speedup_fp32_bulk_over_fp64": ms64 / ms_step}
+    Sb = assemble(mesh, precision="fp32_bulk", f_nodal=f, **kw)
+    out["error_vs_fp64"] = rel_frobenius(Sb, S64)
+    del Sb
+    out["variants"] = {}
+    for vname, extra in variants:
+        ms_v, _, clk_v = timed_bulk(extra, max(3, steps // 2))
+        Sv = assemble(mesh, precision="fp32_bulk", f_nodal=f, **kw, **extra)
+        out["variants"][vname] = {"settings": extra, "ms_per_step": ms_v, "value": npairs / (ms_v * 1e-3),
+                                  "error_vs_fp64": rel_frobenius(Sv, S64), "clocks": clk_v}
+        del Sv
+    del S64, mesh
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if with_cpu:
+        rate, desc, cores, dt = oracle_sample(m, wl, seconds_target=4.0)
+        out["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": desc}
+    return out
+
+
 def run_serving(budget_gb=40, slots=8):
     """The serving stream of 512 assemble+solve requests (Poisson, 200/s): p50/p99 latency."""
     from paper_2207_03921_gb300.serving import Server, make_request
@@ -310,6 +458,8 @@ def main():
                     help="profile: one cold and one cached FP32-bulk assembly, nothing else (for ncu); "
                          "serving: the request stream alone")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--configs", default="cfg1,cfg2,cfg3,cfg5",
+                    help="further configurations measured beside the headline workload (comma list, or none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -445,55 +595,13 @@ def main():
     h2d = hf.numel() * 8
 
     # roofline of the dominant kernel: the longest of the bulk quadrature kernels (FP32 ALU),
-    # the close-list kernel (FP64 ALU, singular rule), the per-element sums and the conversion
-    # of the fixed-point entries into CSR (HBM)
+    # the close-list kernel (the singular rule, FP64 ALU), the per-element sums and the
+    # conversion of the fixed-point entries into CSR (HBM)
     pk = peaks()
     clk_sum = clk.summary()
-    sm_max = pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s from unit counts and the max clock
-    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12        # 2 FP64 FMA lanes per SM and clock
-    hbm_peak = pk.get("hbm_gbs", 6800.0)
-    fpe = FLOPS_PER_EVAL[wl["kernel"]]
-    nqi = wl["quad_inner"]
-
-    def mean(key):
-        return statistics.mean(i[key] for i in timed)
-
-    ms_whole, ms_cut, ms_close, ms_sums = mean("ms_whole"), mean("ms_cut"), mean("ms_close"), mean("ms_sums")
-    flops_whole = census["evals_whole"] * fpe + (census["evals_whole"] // nqi) * FLOPS_PER_OUTER
-    flops_cut = (census["evals_cut"] * fpe + census["nonempty_points_cut"] * FLOPS_PER_OUTER
-                 + census["outer_points_cut"] * FLOPS_VERTEX_TESTS
-                 + census["cut_points_cut"] * (0 if wl["ball"] == "infinity" else
-                                               FLOPS_EDGES + (FLOPS_CAPS if wl["ball"] == "approxcaps" else 0))
-                 + census["subtri_evals_cut"] * FLOPS_SUBTRI_POINT)
-    flops_duffy = census["duffy_points"] * FLOPS_DUFFY_POINT
-    nc = 1 if ndof == 1 else 3
-    sums_bytes = npairs * (24 + 24 + 4) * nc                     # kk records, ll records (gathered), pT ids
-    conv_bytes = (info0["n_upper"] * 8 * nc + info0["nnz"] // (ndof * ndof) * 4  # fixed-point entries, columns
-                  + info0["nnz"] // 2 * 8 + info0["nnz"] * 8)     # transposed positions, values written
-
-    def rate(x, ms, scale):
-        return x / (ms * 1e-3) / scale if ms > 0 else 0.0
-
-    kernels = {
-        "k_trunc_whole": {"bound": "alu", "ms": ms_whole, "units": info0["pairs_whole"],
-                          "achieved": rate(flops_whole, ms_whole, 1e12), "peak": fp32_peak, "unit": "TFLOP/s"},
-        "k_trunc_cut": {"bound": "alu", "ms": ms_cut, "units": census["outer_points_cut"] // wl["quad_outer"],
-                        "achieved": rate(flops_cut, ms_cut, 1e12), "peak": fp32_peak, "unit": "TFLOP/s"},
-        "k_elem_sums": {"bound": "hbm", "ms": ms_sums, "units": npairs,
-                        "achieved": rate(sums_bytes, ms_sums, 1e9), "peak": hbm_peak, "unit": "GB/s"},
-        "k_acc_to_csr": {"bound": "hbm", "ms": red_ms, "units": info0["n_upper"],
-                         "achieved": rate(conv_bytes, red_ms, 1e9), "peak": hbm_peak, "unit": "GB/s"},
-    }
-    if census["singular_pairs"]:
-        kernels["k_duffy"] = {"bound": "alu", "ms": ms_close, "units": census["singular_pairs"],
-                              "achieved": rate(flops_duffy, ms_close, 1e12), "peak": fp64_peak, "unit": "TFLOP/s"}
-    for k in kernels.values():
-        k["frac"] = k["achieved"] / k["peak"]
-    if wl["ball"] == "infinity":
-        kernels["k_trunc_cut"]["note"] = ("FP32 quadrature work only: the square's Sutherland-Hodgman cut runs in "
-                                          "FP32 with exact decisions or, near ties, in FP64 (FP64-pipe bound on "
-                                          "grids aligned with the square)")
+    kernels = kernel_rooflines(wl, census, info0, timed, npairs, ndof, pk, sing32=False)
+    ms_whole, ms_cut, ms_close, ms_sums = (statistics.mean(i[k] for i in timed)
+                                           for k in ("ms_whole", "ms_cut", "ms_close", "ms_sums"))
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     peak_src = {"alu": "derived: 152 SMs x (128 FP32 | 2 FP64) lanes x 2 x max SM clock",
@@ -506,7 +614,8 @@ def main():
         "metric": "element-pair assemblies/s", "value": value, "unit": "pairs/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (quadrature, geometry with exact decisions) + i64 fixed-point sums + f64 (near ties, singular pairs, CSR)",
+        "dtype": ("f32 (truncation quadrature, cut geometry with decisions equal to f64) + i64 fixed-point sums "
+                  "+ f64 (singular rule, near ties, CSR values)"),
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "precision": "fp32_bulk",
                    "step": "nlfem_assemble with cached pair list and pattern",
@@ -535,6 +644,33 @@ def main():
         "gpu_launches": args.steps * (7 + (2 if census["singular_pairs"] or census["evals_canonical"] else 0)),
         "clocks": clk_sum,
     }
+    # the other benchmark configurations, each with its own clocks, FP64 comparison, error
+    # against the FP64 path, roofline and oracle sample; the precision variants of the FP32-bulk
+    # path (singular rule in FP32, cut geometry in FP64) beside the default split
+    geo64 = ("geometry_fp64", {"geometry_precision": "fp64"})
+    sing32 = ("singular_fp32", {"singular_precision": "fp32"})
+    if ws == 1 and args.configs != "none":
+        del mesh
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        mesh = None
+        line["configs"] = {}
+        vsteps = max(3, min(10, args.steps))
+        for cname in [c for c in args.configs.split(",") if c and c != args.workload]:
+            var = {"cfg2": (sing32, geo64), "cfg3": (geo64,)}.get(cname, ())
+            try:
+                line["configs"][cname] = measure_config(cname, vsteps, args.warmup, local, pk,
+                                                        with_cpu=not args.no_cpu, variants=var)
+            except Exception as e:  # reported; the headline numbers stand
+                line["configs"][cname] = {"error": f"{type(e).__name__}: {e}"}
+        # the headline workload's error against FP64 and its cut geometry in FP64
+        try:
+            v = measure_config(args.workload, vsteps, args.warmup, local, pk, with_cpu=False, variants=(geo64,))
+            line["precision"] = {"error_vs_fp64": v["error_vs_fp64"], "variants": v["variants"],
+                                 "singular_precision": v["singular_precision"],
+                                 "geometry_precision": v["geometry_precision"]}
+        except Exception as e:
+            line["precision"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_serving:
         del mesh
         torch.cuda.synchronize()

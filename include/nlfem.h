@@ -60,10 +60,23 @@ extern "C" {
 
 /* arithmetic of the separated-pair quadrature */
 #define NLFEM_PREC_FP64 0           /* everything in FP64 */
-#define NLFEM_PREC_FP32_BULK 1      /* quadrature in FP32 (geometry decisions equal to FP64 ones; the
-                                       singular rule's points and sums in FP32), sums over pairs in
+#define NLFEM_PREC_FP32_BULK 1      /* truncation quadrature in FP32 (geometric decisions equal to the
+                                       FP64 ones), the singular rule and the cut geometry as selected by
+                                       singular_precision and geometry_precision, sums over pairs in
                                        exact fixed point, FP64 result; within 1e-5 relative
                                        (Frobenius) of the FP64 result */
+
+/* FP32 bulk: arithmetic of the singular rule on intersecting pairs (Tab. 1 club) */
+#define NLFEM_SINGULAR_FP64 0       /* default: transform points, kernel values and sums in FP64, each
+                                       pair's block added to the fixed-point sums from FP64 */
+#define NLFEM_SINGULAR_FP32 1       /* points and sums in FP32 (a relative error of a few 1e-7) */
+
+/* FP32 bulk: arithmetic of the polygon E_l cut by the ball of an outer point (Defs. 2.1, 2.2) */
+#define NLFEM_GEOMETRY_EXACT32 0    /* default: FP32 positions relative to x_p; every decision (vertex in
+                                       the ball, crossings of an edge, caps) equals the FP64 one, near
+                                       ties the outer point is cut in FP64 */
+#define NLFEM_GEOMETRY_FP64 1       /* every cut outer point is cut in FP64 (crossings, cap centres),
+                                       the polygon rounded once to FP32 relative to x_p */
 
 typedef struct nlfem_mesh_s* nlfem_mesh_t;
 typedef struct nlfem_system_s* nlfem_system_t;
@@ -92,6 +105,9 @@ typedef struct {
     /* NLFEM_KERNEL_TABULATED: table_size (2..1024) values of g, host memory, read during the call */
     int table_size;
     const double* kernel_table;
+    /* FP32 bulk only (ignored by NLFEM_PREC_FP64, which does everything in FP64) */
+    int singular_precision;  /* NLFEM_SINGULAR_* (0 = FP64) */
+    int geometry_precision;  /* NLFEM_GEOMETRY_* (0 = FP32 positions with exact decisions) */
 } nlfem_params;
 
 typedef struct {
@@ -172,7 +188,11 @@ int nlfem_mesh_set_materials(nlfem_mesh_t mesh, const int8_t* material, void* st
 void nlfem_params_default(nlfem_params* p, int kernel);
 
 /*
- * Assemble the stiffness matrix A_h^# over all dofs of the base domain (full Neumann-type
+ * Assemble the stiffness matrix A_h^# of eq. biFormApprox (the pair loop of Alg. 1: for every
+ * ordered interacting pair (E_k, E_l) the singular rule if they intersect and the rule of
+ * Tab. 1 asks for it, else the truncation rule of eq. discrete-inner on E_l cut by the ball
+ * approximation of each outer point; Alg. 2 / eq. graph:interactionEdges define the pairs)
+ * over all dofs of the base domain (full Neumann-type
  * matrix, symmetric to the last bit) and the load vector F_i = int_Omega f phi_i computed
  * with the outer rule from the P1 interpolant of f_nodal [M x ndof] (host or device, NULL
  * means f = 0). The interaction graph, CSR pattern and reduction index are built on the
@@ -229,9 +249,11 @@ int nlfem_autotune(nlfem_mesh_t mesh, const nlfem_params* params, void* stream, 
 int nlfem_batch_assemble(const nlfem_mesh_t* meshes, const nlfem_params* params, const double* const* f_nodal,
                          int n, void* stream, nlfem_system_t* out);
 
-/* Borrowed device pointers of the CSR matrix (valid until nlfem_system_destroy):
- * row_ptr [nrows + 1] int64, col [nnz] int32 (sorted per row), val [nnz] FP64. Dof d of
- * node m is row m * ndof + d. */
+/* Borrowed device pointers of the assembled matrix in CSR form, the format in which the
+ * paper's library hands the stiffness matrix back to its Python front end for any sparse
+ * solver (Sec. 1; Sec. 3.4 sums the per-thread parts into it) (valid until
+ * nlfem_system_destroy): row_ptr [nrows + 1] int64, col [nnz] int32 (sorted per row),
+ * val [nnz] FP64. Dof d of node m is row m * ndof + d. Errors: INVALID_ARG (NULL). */
 int nlfem_system_csr(nlfem_system_t sys, const int64_t** row_ptr, const int32_t** col,
                      const double** val, int64_t* nrows, int64_t* nnz);
 
@@ -297,19 +319,23 @@ void nlfem_system_destroy(nlfem_system_t sys);
 
 /*
  * Interaction graph of a small mesh, computed without allocating any device memory.
- * For callers that cannot call cudaMalloc at the point where they need the pairs: code
- * running inside a CUDA graph capture, a serving process that reserved the device
- * memory up front for its own arena, or a context where an out-of-memory failure must
- * not be possible. The paper has no counterpart; it returns the same pairs as
+ * For callers that cannot call cudaMalloc at the point where they need the pairs: a serving
+ * process that reserved the device memory up front for its own arena (an allocation here
+ * would take memory the arena already counts as its own, or fail), a host framework whose
+ * caching allocator owns the device memory, or a context where an out-of-memory failure
+ * must not be possible. The paper has no counterpart; it returns the same pairs as
  * nlfem_mesh_pairs after an nlfem_assemble with the same delta, ball and outer rule.
  * verts [M x 2] FP64, elems [K x 3] int32 (device memory; any orientation), out_k and
  * out_l device int32 arrays of length capacity, owned by the caller; on success they hold
  * the *npairs ordered interacting pairs sorted by (k, l) (host int64 output).
  * Limits: K <= 32768 triangles and M <= 65536 vertices (NLFEM_ERR_UNSUPPORTED beyond).
- * The working data lives in a 4.5 MB file-scope device array that every GPU loading this
- * library holds until the process exits; the first call on a device looks up its address,
- * so make that first call before any stream capture. All calls share that array: calls
- * that overlap on the GPU (other streams or host threads) race and must be serialised.
+ * The working data lives in a file-scope device array of 4,981,504 bytes (about 5 MB) that
+ * every GPU loading this library holds until the process exits; the first call on a device
+ * looks up its address, so make that first call before any stream capture. All calls share
+ * that array and it keeps the last call's contents (each call clears what it counts into);
+ * calls that overlap on the GPU (other streams or host threads) race and must be serialised.
+ * The call synchronises stream: it reads the mesh checks and the pair count back to the
+ * host before it writes the pairs.
  * Errors: INVALID_ARG (NULL or host pointers, delta <= 0, unknown ball / rule, capacity
  * too small: *npairs then holds the number needed), UNSUPPORTED, BAD_MESH, CUDA.
  */

@@ -26,6 +26,8 @@ KERNELS = {"constant": 0, "fractional": 1, "peridynamic": 2, "tabulated": 3}
 BALLS = {"nocaps": 0, "approxcaps": 1, "infinity": 2}
 CLOSE_RULES = {"auto": 0, "duffy": 1, "nozerodiv": 2, "standard": 3}
 PRECISIONS = {"fp64": 0, "fp32_bulk": 1}
+SINGULAR_PRECISIONS = {"fp64": 0, "fp32": 1}
+GEOMETRY_PRECISIONS = {"exact32": 0, "fp64": 1}
 
 
 class NlfemError(RuntimeError):
@@ -39,7 +41,8 @@ class nlfem_params(C.Structure):
                 ("ball", C.c_int), ("quad_outer", C.c_int), ("quad_inner", C.c_int), ("duffy_gauss", C.c_int),
                 ("close_rule", C.c_int), ("precision", C.c_int), ("mem_budget_bytes", C.c_int64),
                 ("n_materials", C.c_int), ("material_scale", C.c_void_p),
-                ("table_size", C.c_int), ("kernel_table", C.c_void_p)]
+                ("table_size", C.c_int), ("kernel_table", C.c_void_p),
+                ("singular_precision", C.c_int), ("geometry_precision", C.c_int)]
 
 
 class nlfem_assembly_info(C.Structure):
@@ -293,14 +296,45 @@ def nlfem_trim_memory(stream=None) -> None:
     _check(load().nlfem_trim_memory(_stream(stream)))
 
 
+def _check_noalloc_args(verts, elems, out_k, out_l):
+    """Argument checks of nlfem_pairs_noalloc, before anything reaches the C library: the
+    kernels read verts as 2 M doubles and elems as 3 K ints, and write up to capacity
+    entries of out_k and out_l, so a wrong dtype, shape, stride or device is refused here."""
+    import torch
+    for name, t in (("verts", verts), ("elems", elems), ("out_k", out_k), ("out_l", out_l)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+    if verts.dtype != torch.float64 or verts.dim() != 2 or verts.shape[1] != 2:
+        raise ValueError("verts must be a float64 tensor of shape [M, 2]")
+    if elems.dtype != torch.int32 or elems.dim() != 2 or elems.shape[1] != 3:
+        raise ValueError("elems must be an int32 tensor of shape [K, 3]")
+    for name, t in (("out_k", out_k), ("out_l", out_l)):
+        if t.dtype != torch.int32 or t.dim() != 1:
+            raise ValueError(f"{name} must be a one-dimensional int32 tensor")
+    for name, t in (("verts", verts), ("elems", elems), ("out_k", out_k), ("out_l", out_l)):
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    for name, t in (("verts", verts), ("elems", elems), ("out_k", out_k), ("out_l", out_l)):
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be a CUDA tensor on the current device")
+    return _noalloc_capacity(out_k, out_l)
+
+
+def _noalloc_capacity(out_k, out_l) -> int:
+    """Pairs the two output buffers can both hold: the shorter of the two."""
+    return min(int(out_k.numel()), int(out_l.numel()))
+
+
 def nlfem_pairs_noalloc(verts, elems, delta, ball, quad_outer, out_k, out_l, stream=None) -> int:
     """Interaction graph of a small mesh into caller-owned device buffers, without any
-    device allocation. verts [M, 2] float64, elems [K, 3] int32, out_k / out_l int32 (device
-    tensors). Returns the number of ordered pairs written (sorted by (k, l))."""
+    device allocation. verts [M, 2] float64, elems [K, 3] int32, out_k / out_l int32 (contiguous
+    CUDA tensors on the current device; the capacity is the shorter of the two). Returns the
+    number of ordered pairs written (sorted by (k, l)). The call synchronises the stream."""
+    capacity = _check_noalloc_args(verts, elems, out_k, out_l)
     n = C.c_int64(0)
     code = load().nlfem_pairs_noalloc(_ptr(verts), int(verts.shape[0]), _ptr(elems), int(elems.shape[0]),
                                       float(delta), BALLS[ball] if isinstance(ball, str) else int(ball),
-                                      int(quad_outer), _ptr(out_k), _ptr(out_l), int(out_k.numel()),
+                                      int(quad_outer), _ptr(out_k), _ptr(out_l), capacity,
                                       C.byref(n), _stream(stream))
     if code != NLFEM_OK:
         err = NlfemError(code, load().nlfem_last_error().decode())
@@ -327,10 +361,13 @@ def nlfem_version() -> str:
 
 def make_params(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7, quad_inner=7,
                 duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0,
-                material_scale=None, kernel_table=None) -> nlfem_params:
+                material_scale=None, kernel_table=None, singular_precision="fp64",
+                geometry_precision="exact32") -> nlfem_params:
     """nlfem_params; material_scale: symmetric n x n table of a label-dependent kernel;
     kernel_table: values of g for kernel="tabulated" (the returned struct keeps both arrays
-    alive for the calls it is passed to)."""
+    alive for the calls it is passed to); singular_precision ("fp64" | "fp32") and
+    geometry_precision ("exact32" | "fp64"): arithmetic of the singular rule and of the cut
+    geometry in the FP32-bulk path."""
     p = nlfem_params()
     p.kernel = KERNELS[kernel]
     p.delta = float(delta)
@@ -343,6 +380,8 @@ def make_params(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps",
     p.close_rule = CLOSE_RULES[close_rule]
     p.precision = PRECISIONS[precision]
     p.mem_budget_bytes = int(mem_budget_bytes)
+    p.singular_precision = SINGULAR_PRECISIONS[singular_precision]
+    p.geometry_precision = GEOMETRY_PRECISIONS[geometry_precision]
     p.n_materials = 0
     p.material_scale = None
     if material_scale is not None:

@@ -108,6 +108,10 @@ static Params make_params(const nlfem_params& p, int ndof) {
         }
     NLFEM_CHECK(p.duffy_gauss >= 1 && p.duffy_gauss <= 32, NLFEM_ERR_INVALID_ARG,
                 "duffy_gauss must be in 1..32");
+    NLFEM_CHECK(p.singular_precision == NLFEM_SINGULAR_FP64 || p.singular_precision == NLFEM_SINGULAR_FP32,
+                NLFEM_ERR_INVALID_ARG, "unknown singular_precision");
+    NLFEM_CHECK(p.geometry_precision == NLFEM_GEOMETRY_EXACT32 || p.geometry_precision == NLFEM_GEOMETRY_FP64,
+                NLFEM_ERR_INVALID_ARG, "unknown geometry_precision");
     int need = p.kernel == NLFEM_KERNEL_PERIDYNAMIC ? 2 : 1;
     NLFEM_CHECK(need == ndof, NLFEM_ERR_INVALID_ARG, "the mesh was created with the wrong dofs per node for this kernel");
     if (p.kernel == NLFEM_KERNEL_FRACTIONAL)
@@ -119,6 +123,9 @@ static Params make_params(const nlfem_params& p, int ndof) {
     P.close_rule = p.close_rule;
     P.precision = p.precision;
     P.ndof = ndof;
+    // the arithmetic switches only apply to FP32 bulk (the FP64 path is FP64 throughout)
+    P.sing32 = p.precision == NLFEM_PREC_FP32_BULK && p.singular_precision == NLFEM_SINGULAR_FP32;
+    P.geo64 = p.precision == NLFEM_PREC_FP32_BULK && p.geometry_precision == NLFEM_GEOMETRY_FP64;
     P.delta = p.delta;
     P.delta2 = p.delta * p.delta;
     P.s = p.kernel == NLFEM_KERNEL_FRACTIONAL ? p.s : (p.kernel == NLFEM_KERNEL_PERIDYNAMIC ? -0.5 : -1.0);
@@ -225,6 +232,8 @@ void nlfem_params_default(nlfem_params* p, int kernel) {
     p->mem_budget_bytes = 0;
     p->n_materials = 0;
     p->material_scale = nullptr;
+    p->singular_precision = NLFEM_SINGULAR_FP64;
+    p->geometry_precision = NLFEM_GEOMETRY_EXACT32;
     p->table_size = 0;
     p->kernel_table = nullptr;
 }
@@ -450,7 +459,7 @@ static int64_t assembly_bytes(const Mesh& m, const PairCache& pc, const Params& 
     const int64_t NE = contrib_entries(P.ndof);
     const int64_t nc = P.ndof == 1 ? 1 : 3;
     const int64_t work = P.precision == NLFEM_PREC_FP32_BULK
-                             ? pc.n_upper * nc * 8 + pc.nduffy * NE * 4 + pc.npairs * 12 * nc * 4
+                             ? pc.n_upper * nc * 8 + pc.nduffy * NE * 8 + pc.npairs * 12 * nc * 4
                              : pc.npairs * NE * 8;
     return work + pc.nnz * 8 + pc.N * 8;
 }

@@ -170,6 +170,9 @@ struct Params {
     double tinv;
     const double* tab64;
     const float* tab32;
+    // FP32 bulk: the singular rule in FP32 (else FP64); every cut outer point cut in FP64
+    int sing32;
+    int geo64;
 };
 
 // g(r) of the tabulated kernel, r = sqrt(d2): linear between the table values, held beyond

@@ -564,6 +564,7 @@ static constexpr size_t NA_CSTART = NA_CCNT + 8 * NOALLOC_MAX_CELLS;           /
 static constexpr size_t NA_CCUR = NA_CSTART + 8 * NOALLOC_MAX_CELLS + 256;     // int[MAX_CELLS]
 static constexpr size_t NA_MISC = NA_CCUR + 4 * NOALLOC_MAX_CELLS;             // 256 bytes: flags, stats
 static constexpr size_t NOALLOC_BYTES = NA_MISC + 256;
+static_assert(NOALLOC_BYTES == 4981504, "the header states the scratch size: 4,981,504 bytes");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
@@ -739,6 +740,7 @@ extern "C" int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t
         unsigned char* misc = base + NA_MISC;
 
         k_na_init<<<1, 1, 0, st>>>(misc);
+        NLFEM_LAUNCH_CHECK();
         k_na_verts<<<nblk(M, 256), 256, 0, st>>>(verts, M, X, misc);
         NLFEM_LAUNCH_CHECK();
         k_na_elems<<<nblk(K, 256), 256, 0, st>>>(elems, K, M, X, T, cen, rad, E32, misc);
@@ -794,6 +796,7 @@ extern "C" int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t
         k_search<false><<<nblk(K * 32, 128), 128, 0, st>>>(a, cnt, nullptr, nullptr);
         NLFEM_LAUNCH_CHECK();
         k_na_scan<<<1, 1024, 0, st>>>(cnt, ptr, K);
+        NLFEM_LAUNCH_CHECK();
         k_na_maxcnt<<<nblk(K, 256), 256, 0, st>>>(cnt, K, misc);
         NLFEM_LAUNCH_CHECK();
         int64_t total = 0;

@@ -698,9 +698,9 @@ static void launch_trunc(const QuadArgs& a, R* out, cudaStream_t st) {
 // Close-list records (singular or diamond rule, FP32 in list order) into the fixed-point
 // accumulators: each upper entry E(a, b) of the folded union block goes to the upper CSR
 // entry of the node pair (u_a, u_b). acc == nullptr: only the largest |value| is recorded.
-template <int NDOF>
+template <int NDOF, typename RT>
 __global__ void k_close_acc(const int* __restrict__ ids, int64_t n, const int* __restrict__ pk,
-                            const int* __restrict__ pl, const int4* __restrict__ T, const float* __restrict__ rec,
+                            const int* __restrict__ pl, const int4* __restrict__ T, const RT* __restrict__ rec,
                             const int64_t* __restrict__ nptr, const int* __restrict__ ncol,
                             const int64_t* __restrict__ up_start, unsigned long long* acc,
                             const float* __restrict__ scale_p, unsigned int* maxabs) {
@@ -714,16 +714,19 @@ __global__ void k_close_acc(const int* __restrict__ ids, int64_t n, const int* _
         const int p = ids[i];
         int posl[3], u[6];
         const int U = union_pos(T[pk[p]], T[pl[p]], posl, u);
-        const float* r = rec + i * NS;
+        const RT* r = rec + i * NS;
         for (int a = 0; a < U; ++a)
             for (int b = a; b < U; ++b) {
                 const int lo = min(u[a], u[b]), hi = max(u[a], u[b]);
                 const int64_t up = acc ? up_start[lo] + max(upper_rank(nptr, ncol, lo, hi), 0) : 0;
-                const float* v = r + q_E1[a][b] * NCOMP;
-                const float comp[3] = {v[0], v[NCOMP > 1 ? 1 : 0], v[NCOMP > 1 ? 3 : 0]};
+                const RT* v = r + q_E1[a][b] * NCOMP;
+                const RT comp[3] = {v[0], v[NCOMP > 1 ? 1 : 0], v[NCOMP > 1 ? 3 : 0]};
                 for (int c = 0; c < NC; ++c) {
-                    vmax = fmaxf(vmax, fabsf(comp[c]));
-                    const long long q = __float2ll_rn(comp[c] * scale);
+                    vmax = fmaxf(vmax, fabsf((float)comp[c]));
+                    // FP64 records (the singular rule in FP64) are scaled and rounded in FP64:
+                    // the fixed-point sum then keeps their digits beyond FP32
+                    const long long q = sizeof(RT) == 8 ? __double2ll_rn((double)comp[c] * (double)scale)
+                                                        : __float2ll_rn((float)comp[c] * scale);
                     if (acc && q) atomicAdd(acc + up * NC + c, (unsigned long long)q);
                 }
             }
@@ -792,18 +795,48 @@ static void elem_sums(Mesh& m, PairCache& pc, const Params& prm, System& sys, co
     NLFEM_LAUNCH_CHECK();
 }
 
+// the close list's records are FP64 when the singular rule ran in FP64 (bulk_close64)
+static bool bulk_close64(const Params& prm) { return prm.singular && !prm.sing32; }
+
 static void close_acc(Mesh& m, PairCache& pc, const System& sys, unsigned long long* acc, const float* scale,
                       unsigned int* maxabs, cudaStream_t st) {
     if (pc.nduffy == 0) return;
-    if (pc.ndof == 1)
-        k_close_acc<1><<<nblk(pc.nduffy, 128), 128, 0, st>>>(pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.T.p,
-                                                             sys.contrib32.p, pc.nrow_ptr.p, pc.ncol.p,
-                                                             pc.up_start.p, acc, scale, maxabs);
-    else
-        k_close_acc<2><<<nblk(pc.nduffy, 128), 128, 0, st>>>(pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.T.p,
-                                                             sys.contrib32.p, pc.nrow_ptr.p, pc.ncol.p,
-                                                             pc.up_start.p, acc, scale, maxabs);
+    const unsigned g = nblk(pc.nduffy, 128);
+    const bool r64 = bulk_close64(sys.prm);
+    if (pc.ndof == 1 && r64)
+        k_close_acc<1, double><<<g, 128, 0, st>>>(pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.T.p,
+                                                  sys.contrib64.p, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, acc,
+                                                  scale, maxabs);
+    else if (pc.ndof == 1)
+        k_close_acc<1, float><<<g, 128, 0, st>>>(pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.T.p,
+                                                 sys.contrib32.p, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, acc,
+                                                 scale, maxabs);
+    else  // peridynamics has no singular rule: FP32 records of the diamond or standard rule
+        k_close_acc<2, float><<<g, 128, 0, st>>>(pc.duffy_ids.p, pc.nduffy, pc.pk.p, pc.pl.p, m.T.p,
+                                                 sys.contrib32.p, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, acc,
+                                                 scale, maxabs);
     NLFEM_LAUNCH_CHECK();
+}
+
+// the close list of the FP32-bulk path: the singular rule (FP64 records by default, FP32 with
+// sing32) or the truncation kernel in FP32 (diamond / standard rule) into compact records
+static void bulk_close(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, bool ensure) {
+    if (pc.nduffy == 0) return;
+    const int64_t n = pc.nduffy * contrib_entries(pc.ndof);
+    if (bulk_close64(prm)) {
+        if (ensure) sys.contrib64.ensure(n, st);
+        else sys.contrib64.alloc(n, st);
+        launch_duffy<double>(m, pc, prm, 1, sys.contrib64.p, nullptr, st);
+        return;
+    }
+    if (ensure) sys.contrib32.ensure(n, st);
+    else sys.contrib32.alloc(n, st);
+    if (prm.singular) {
+        launch_duffy<float>(m, pc, prm, 1, nullptr, sys.contrib32.p, st);
+    } else {
+        QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nduffy, pc.duffy_ids.p, 1, m.X.p, m.T.p, m.det.p, prm};
+        launch_trunc<float>(c, sys.contrib32.p, st);
+    }
 }
 
 // FNV-1a over the parameter bytes with the device pointers cleared (the struct is zeroed
@@ -873,15 +906,7 @@ static void bulk_main(Mesh& m, PairCache& pc, const Params& prm, System& sys, cu
 static void run_bulk(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {
     const int NC = pc.ndof == 1 ? 1 : 3;
     NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
-    if (pc.nduffy > 0) {
-        sys.contrib32.alloc(pc.nduffy * contrib_entries(pc.ndof), st);
-        if (prm.singular) {
-            launch_duffy<float>(m, pc, prm, 1, nullptr, sys.contrib32.p, st);
-        } else {
-            QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nduffy, pc.duffy_ids.p, 1, m.X.p, m.T.p, m.det.p, prm};
-            launch_trunc<float>(c, sys.contrib32.p, st);
-        }
-    }
+    bulk_close(m, pc, prm, sys, st, false);
     NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
     sys.fix.alloc(1, st);
     sys.fix.zero(st);
@@ -930,7 +955,10 @@ void BatchExec::prepare(cudaStream_t st) {
         PairCache& pc = *it.pc;
         System& sys = *it.sys;
         const int NC = pc.ndof == 1 ? 1 : 3;
-        if (pc.nduffy > 0) sys.contrib32.ensure(pc.nduffy * contrib_entries(pc.ndof), st);
+        if (pc.nduffy > 0) {
+            if (bulk_close64(it.prm)) sys.contrib64.ensure(pc.nduffy * contrib_entries(pc.ndof), st);
+            else sys.contrib32.ensure(pc.nduffy * contrib_entries(pc.ndof), st);
+        }
         sys.fix.ensure(1, st);
         sys.acc.ensure(std::max<int64_t>(pc.n_upper * NC, 1), st);
         sys.kkll.ensure(pc.npairs * 12 * NC, st);
@@ -965,16 +993,7 @@ void BatchExec::record(cudaStream_t st, cudaEvent_t* ev, bool finish, const std:
         Mesh& m = *it.m;
         PairCache& pc = *it.pc;
         System& sys = *it.sys;
-        const Params& prm = it.prm;
-        if (pc.nduffy > 0) {
-            if (prm.singular) {
-                launch_duffy<float>(m, pc, prm, 1, nullptr, sys.contrib32.p, st);
-            } else {
-                QuadArgs c{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nduffy, pc.duffy_ids.p, 1, m.X.p, m.T.p,
-                           m.det.p, prm};
-                launch_trunc<float>(c, sys.contrib32.p, st);
-            }
-        }
+        bulk_close(m, pc, it.prm, sys, st, true);
         sys.fix.zero(st);
     }
     if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));

@@ -55,6 +55,7 @@ struct FastReq {
     double delta64, delta2_64;
     int ball;     // NLFEM_BALL_*
     int sq32;     // infinity ball: try the FP32 passes before the canonical cut
+    int geo64;    // every cut outer point takes the canonical FP64 cut (no FP32 positions)
     int nmat;     // label-dependent kernel: factor msc[mat[k] * nmat + mat[l]] (0: none)
     const int8_t* mat;
     const float* msc;
@@ -621,7 +622,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                             // so does every open cut on meshes whose grid lines the square's sides
                             // follow (Q.sq32 = 0: the FP32 passes would mostly end undecided); the
                             // others try the FP32 passes first
-                            n = (tie || !Q.sq32) ? -1
+                            n = (tie || !Q.sq32 || Q.geo64) ? -1
                                                  : clip_square_fast(Rx, Ry, eps, Q.delta, my + q * MAXP * FAST_THREADS);
                             if (n < 0) {
                                 n = 0;
@@ -684,8 +685,10 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                     if (!(G.in[0] && G.in[1] && G.in[2]) && nraw >= 2 && !(fv && fe == (le + 1) % 3))
                         cap(lx, ly, fx, fy);
                 }
+                // an undecided outer point, or with geo64 every outer point whose inner element is
+                // cut (the FP32 decisions equal the FP64 ones, so the others are whole or empty)
                 if (!valid) n = 0;
-                else if (!ok)
+                else if (!ok || (Q.geo64 && n >= 3 && !(G.in[0] && G.in[1] && G.in[2])))
                     n = clip_canonical(Q.X, tk, tl, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2], Q.delta64, Q.delta2_64,
                                        CAPS, my + q * MAXP * FAST_THREADS, MAXP);
                 counts |= (unsigned long long)(n < 3 ? 0 : n) << (4 * q);
@@ -942,6 +945,7 @@ FastReq make_req(Mesh& m, PairCache& pc, const Params& prm, int list) {
     q.delta2_64 = prm.delta2;
     q.ball = prm.ball;
     q.sq32 = pc.sq32;
+    q.geo64 = prm.geo64;
     q.nmat = prm.nmat;
     q.mat = prm.mat;
     q.msc = prm.msc32;
