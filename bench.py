@@ -277,7 +277,7 @@ def kernel_rooflines(wl, census, info0, timed, npairs, ndof, pk, sing32):
                  + census["subtri_evals_cut"] * FLOPS_SUBTRI_POINT)
     flops_duffy = census["duffy_points"] * FLOPS_DUFFY_POINT
     nc = 1 if ndof == 1 else 3
-    sums_bytes = npairs * (24 + 24 + 4) * nc                     # kk records, ll records (gathered), pT ids
+    sums_bytes = npairs * (24 * nc + 4)                          # ll records (gathered) and transposed pair ids
     conv_bytes = (info0["n_upper"] * 8 * nc + info0["nnz"] // (ndof * ndof) * 4  # fixed-point entries, columns
                   + info0["nnz"] // 2 * 8 + info0["nnz"] * 8)     # transposed positions, values written
 
@@ -291,8 +291,8 @@ def kernel_rooflines(wl, census, info0, timed, npairs, ndof, pk, sing32):
         "k_trunc_cut": {"bound": "alu", "ms": ms_cut, "units": census["outer_points_cut"] // wl["quad_outer"],
                         "achieved": rate(flops_cut, ms_cut, 1e12), "peak": fp32_peak, "unit": "TFLOP/s",
                         "pipe": "fp32"},
-        "k_elem_sums": {"bound": "hbm", "ms": ms_sums, "units": npairs,
-                        "achieved": rate(sums_bytes, ms_sums, 1e9), "peak": hbm_peak, "unit": "GB/s"},
+        "k_ll_sums": {"bound": "hbm", "ms": ms_sums, "units": npairs,
+                      "achieved": rate(sums_bytes, ms_sums, 1e9), "peak": hbm_peak, "unit": "GB/s"},
         "k_acc_to_csr": {"bound": "hbm", "ms": red_ms, "units": info0["n_upper"],
                          "achieved": rate(conv_bytes, red_ms, 1e9), "peak": hbm_peak, "unit": "GB/s"},
     }
@@ -345,7 +345,7 @@ def measure_config(name, steps, warmup, local, pk, with_cpu=True, variants=()):
     npairs = info0["npairs"]
     del S
     out = {"desc": wl["desc"], "pairs": npairs, "nnz": info0["nnz"], "cold_ms": cold_ms,
-           "singular_precision": "fp64" if census["singular_pairs"] else None, "geometry_precision": "exact32"}
+           "singular_precision": "fp64" if census["singular_pairs"] else None, "geometry_precision": "fp32"}
 
     def timed_bulk(extra, nsteps):
         infos = []
@@ -619,7 +619,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "precision": "fp32_bulk",
                    "step": "nlfem_assemble with cached pair list and pattern",
-                   "l2": "working set larger than L2 (pair lists, kl ranks and per-pair kk/ll records stream from HBM)",
+                   "l2": "working set larger than L2 (pair lists, kl ranks and per-pair ll records stream from HBM)",
                    "pairs": npairs, "nnz": info0["nnz"], "parallelism": "replicas" if ws > 1 else "single GPU",
                    "autotune_blocks_per_sm": {"whole_pairs": tuned[0], "cut_pairs": tuned[1]}},
         "roofline": roof,
@@ -627,7 +627,7 @@ def main():
                         "quadrature_ms": quad64_ms, "speedup_fp32_bulk_over_fp64": ms64_step / ms_step}
                        if ms64_step else None),
         "breakdown_ms": {"quadrature": quad_ms, "whole_pairs": ms_whole, "cut_pairs": ms_cut,
-                         "close_list": ms_close, "element_sums": ms_sums, "to_csr": red_ms, "cold_total": cold_ms,
+                         "close_list": ms_close, "ll_sums": ms_sums, "to_csr": red_ms, "cold_total": cold_ms,
                          "pairs_search": info0["ms_pairs"], "pattern_and_index": info0["ms_pattern"]},
         "cold": {"value": npairs / (cold_ms * 1e-3), "ms": cold_ms},
         "census": census,
@@ -638,10 +638,10 @@ def main():
                          "d2h_bytes_per_step": d2h_cold,
                          "path": "pinned host mesh -> nlfem_mesh_create -> nlfem_assemble (pair search, "
                                  "pattern, values) -> CSR values and F to pinned host memory"}},
-        # per timed step: whole-pair and cut-pair kernels, the scale check, two element sums,
-        # fixed point to CSR, load vector (7; the pilot pass and the scale pick ran once, at the
-        # first assembly on the pattern); with a close list also its kernel and its records' pass
-        "gpu_launches": args.steps * (7 + (2 if census["singular_pairs"] or census["evals_canonical"] else 0)),
+        # per timed step: whole-pair and cut-pair kernels, the ll sums, the scale check, fixed
+        # point to CSR, load vector (6; the pilot pass and the scale pick ran once, at the first
+        # assembly on the pattern); with a close list also its kernel and its records' pass
+        "gpu_launches": args.steps * (6 + (2 if census["singular_pairs"] or census["evals_canonical"] else 0)),
         "clocks": clk_sum,
     }
     # the other benchmark configurations, each with its own clocks, FP64 comparison, error

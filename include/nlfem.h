@@ -60,8 +60,8 @@ extern "C" {
 
 /* arithmetic of the separated-pair quadrature */
 #define NLFEM_PREC_FP64 0           /* everything in FP64 */
-#define NLFEM_PREC_FP32_BULK 1      /* truncation quadrature in FP32 (geometric decisions equal to the
-                                       FP64 ones), the singular rule and the cut geometry as selected by
+#define NLFEM_PREC_FP32_BULK 1      /* truncation quadrature in FP32, the singular rule and the cut
+                                       geometry as selected by
                                        singular_precision and geometry_precision, sums over pairs in
                                        exact fixed point, FP64 result; within 1e-5 relative
                                        (Frobenius) of the FP64 result */
@@ -72,11 +72,15 @@ extern "C" {
 #define NLFEM_SINGULAR_FP32 1       /* points and sums in FP32 (a relative error of a few 1e-7) */
 
 /* FP32 bulk: arithmetic of the polygon E_l cut by the ball of an outer point (Defs. 2.1, 2.2) */
-#define NLFEM_GEOMETRY_EXACT32 0    /* default: FP32 positions relative to x_p; every decision (vertex in
-                                       the ball, crossings of an edge, caps) equals the FP64 one, near
-                                       ties the outer point is cut in FP64 */
-#define NLFEM_GEOMETRY_FP64 1       /* every cut outer point is cut in FP64 (crossings, cap centres),
-                                       the polygon rounded once to FP32 relative to x_p */
+#define NLFEM_GEOMETRY_FP32 0       /* default: positions in FP32 relative to x_p. Euclidean balls: every
+                                       decision (vertex in the ball, crossings of an edge, caps) equals
+                                       the FP64 one; near a tie the outer point is cut in FP64. Infinity
+                                       ball: FP32 Sutherland-Hodgman passes, decisions equal to the FP64
+                                       ones except for the constant kernel, whose result depends on the
+                                       cut region only: there a decision within rounding of a side may
+                                       differ, which moves a polygon edge by a rounding-sized sliver */
+#define NLFEM_GEOMETRY_FP64 1       /* every cut outer point is cut in FP64 (decisions, crossings, cap
+                                       centres), the polygon rounded once to FP32 relative to x_p */
 
 typedef struct nlfem_mesh_s* nlfem_mesh_t;
 typedef struct nlfem_system_s* nlfem_system_t;
@@ -107,7 +111,7 @@ typedef struct {
     const double* kernel_table;
     /* FP32 bulk only (ignored by NLFEM_PREC_FP64, which does everything in FP64) */
     int singular_precision;  /* NLFEM_SINGULAR_* (0 = FP64) */
-    int geometry_precision;  /* NLFEM_GEOMETRY_* (0 = FP32 positions with exact decisions) */
+    int geometry_precision;  /* NLFEM_GEOMETRY_* (0 = FP32) */
 } nlfem_params;
 
 typedef struct {
@@ -126,7 +130,7 @@ typedef struct {
     int64_t pairs_whole;     /* standard-rule pairs with E_l in the ball of every point of E_k */
     int64_t n_upper;         /* node-level upper pattern entries (one reduction unit each) */
     int64_t n_contrib;       /* contributions gathered by the ordered reduction (FP64 path; 0 before) */
-    double ms_sums;          /* FP32 bulk: per-element kk / ll sums and close-list adds */
+    double ms_sums;          /* FP32 bulk: per-element ll sums and close-list adds */
 } nlfem_assembly_info;
 
 typedef struct {
@@ -209,7 +213,7 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
 /*
  * Persistent batch plan (FP32 bulk only): the systems of n meshes stay on the device and
  * their values are re-assembled in place by replaying one CUDA graph (close lists, pilot,
- * scale, fused bulk launches, element sums, conversion to CSR, load vectors), so repeated
+ * scale, fused bulk launches, ll sums, conversion to CSR, load vectors), so repeated
  * assemblies of many small problems pay no per-kernel launch cost. nlfem_batch_create does
  * the cold work and one assembly, then captures the graph (the load data f_nodal is copied
  * into the plan); nlfem_batch_run replays it on stream (ms, if not NULL, receives its device

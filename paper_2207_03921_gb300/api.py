@@ -144,11 +144,11 @@ class System:
 def assemble(mesh: Mesh, kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7,
              quad_inner=7, duffy_gauss=5, close_rule="auto", precision="fp64", f_nodal=None,
              mem_budget_bytes=0, stream=None, material_scale=None, kernel_table=None,
-             singular_precision="fp64", geometry_precision="exact32") -> System:
+             singular_precision="fp64", geometry_precision="fp32") -> System:
     """Assemble A_h^# and F on the GPU (nlfem_assemble). material_scale: symmetric table of a
     label-dependent kernel over the labels of Mesh.set_materials; kernel_table: the values of
     g for kernel="tabulated"; singular_precision ("fp64" | "fp32") and geometry_precision
-    ("exact32" | "fp64"): arithmetic of the singular rule and of the cut geometry when
+    ("fp32" | "fp64"): arithmetic of the singular rule and of the cut geometry when
     precision="fp32_bulk"."""
     torch = _torch()
     p = B.make_params(kernel, delta, s, kconst, ball, quad_outer, quad_inner, duffy_gauss, close_rule,
@@ -180,7 +180,7 @@ def _params_list(params):
     for p in params:
         q = dict(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7, quad_inner=7,
                  duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0, material_scale=None,
-                 kernel_table=None, singular_precision="fp64", geometry_precision="exact32")
+                 kernel_table=None, singular_precision="fp64", geometry_precision="fp32")
         q.update(p)
         ps.append(B.make_params(q["kernel"], q["delta"], q["s"], q["kconst"], q["ball"], q["quad_outer"],
                                 q["quad_inner"], q["duffy_gauss"], q["close_rule"], q["precision"],

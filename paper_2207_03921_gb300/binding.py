@@ -27,7 +27,7 @@ BALLS = {"nocaps": 0, "approxcaps": 1, "infinity": 2}
 CLOSE_RULES = {"auto": 0, "duffy": 1, "nozerodiv": 2, "standard": 3}
 PRECISIONS = {"fp64": 0, "fp32_bulk": 1}
 SINGULAR_PRECISIONS = {"fp64": 0, "fp32": 1}
-GEOMETRY_PRECISIONS = {"exact32": 0, "fp64": 1}
+GEOMETRY_PRECISIONS = {"fp32": 0, "fp64": 1}
 
 
 class NlfemError(RuntimeError):
@@ -362,11 +362,11 @@ def nlfem_version() -> str:
 def make_params(kernel="constant", delta=0.1, s=0.5, kconst=None, ball="nocaps", quad_outer=7, quad_inner=7,
                 duffy_gauss=5, close_rule="auto", precision="fp64", mem_budget_bytes=0,
                 material_scale=None, kernel_table=None, singular_precision="fp64",
-                geometry_precision="exact32") -> nlfem_params:
+                geometry_precision="fp32") -> nlfem_params:
     """nlfem_params; material_scale: symmetric n x n table of a label-dependent kernel;
     kernel_table: values of g for kernel="tabulated" (the returned struct keeps both arrays
     alive for the calls it is passed to); singular_precision ("fp64" | "fp32") and
-    geometry_precision ("exact32" | "fp64"): arithmetic of the singular rule and of the cut
+    geometry_precision ("fp32" | "fp64"): arithmetic of the singular rule and of the cut
     geometry in the FP32-bulk path."""
     p = nlfem_params()
     p.kernel = KERNELS[kernel]

@@ -110,7 +110,7 @@ static Params make_params(const nlfem_params& p, int ndof) {
                 "duffy_gauss must be in 1..32");
     NLFEM_CHECK(p.singular_precision == NLFEM_SINGULAR_FP64 || p.singular_precision == NLFEM_SINGULAR_FP32,
                 NLFEM_ERR_INVALID_ARG, "unknown singular_precision");
-    NLFEM_CHECK(p.geometry_precision == NLFEM_GEOMETRY_EXACT32 || p.geometry_precision == NLFEM_GEOMETRY_FP64,
+    NLFEM_CHECK(p.geometry_precision == NLFEM_GEOMETRY_FP32 || p.geometry_precision == NLFEM_GEOMETRY_FP64,
                 NLFEM_ERR_INVALID_ARG, "unknown geometry_precision");
     int need = p.kernel == NLFEM_KERNEL_PERIDYNAMIC ? 2 : 1;
     NLFEM_CHECK(need == ndof, NLFEM_ERR_INVALID_ARG, "the mesh was created with the wrong dofs per node for this kernel");
@@ -233,7 +233,7 @@ void nlfem_params_default(nlfem_params* p, int kernel) {
     p->n_materials = 0;
     p->material_scale = nullptr;
     p->singular_precision = NLFEM_SINGULAR_FP64;
-    p->geometry_precision = NLFEM_GEOMETRY_EXACT32;
+    p->geometry_precision = NLFEM_GEOMETRY_FP32;
     p->table_size = 0;
     p->kernel_table = nullptr;
 }
@@ -459,7 +459,7 @@ static int64_t assembly_bytes(const Mesh& m, const PairCache& pc, const Params& 
     const int64_t NE = contrib_entries(P.ndof);
     const int64_t nc = P.ndof == 1 ? 1 : 3;
     const int64_t work = P.precision == NLFEM_PREC_FP32_BULK
-                             ? pc.n_upper * nc * 8 + pc.nduffy * NE * 8 + pc.npairs * 12 * nc * 4
+                             ? pc.n_upper * nc * 8 + pc.nduffy * NE * 8 + pc.npairs * 6 * nc * 4
                              : pc.npairs * NE * 8;
     return work + pc.nnz * 8 + pc.N * 8;
 }
@@ -555,7 +555,7 @@ int nlfem_assemble(nlfem_mesh_t mesh, const nlfem_params* params, const double* 
         S.contrib32.release();
         S.contrib64.release();
         S.acc.release();
-        S.kkll.release();
+        S.llrec.release();
         fill_info(S, m, *pc, t_pairs, t_pattern, cached);
         nlfem_assembly_info& I = S.info;
         I.ms_quadrature = elapsed_ms(ev[3], ev[4]);
@@ -675,7 +675,7 @@ int nlfem_batch_assemble(const nlfem_mesh_t* meshes, const nlfem_params* params,
         }
         S.contrib32.release();
         S.acc.release();
-        S.kkll.release();
+        S.llrec.release();
         fill_info(S, m, *pcs[i], tp[i], tq[i], cached[i] != 0);
         // times of the whole batch: the fused launches serve every system
         S.info.ms_quadrature = ms_q;
@@ -851,10 +851,10 @@ int nlfem_autotune(nlfem_mesh_t mesh, const nlfem_params* params, void* stream, 
     // scratch accumulators: the values are discarded, the launches are the real ones
     const int NC = pc->ndof == 1 ? 1 : 3;
     DBuf<unsigned long long> acc;
-    DBuf<float> kkll;
+    DBuf<float> llrec;
     DBuf<FixState> fix;
     acc.alloc(std::max<int64_t>(pc->n_upper * NC, 1), st);
-    kkll.alloc(pc->npairs * 12 * NC, st);
+    llrec.alloc(std::max<int64_t>(pc->npairs * 6 * NC, 1), st);
     fix.alloc(1, st);
     fix.zero(st);
     pick_scale(m, *pc, P, fix.p, st);  // the real scale, so that the atomics are the real ones too
@@ -868,7 +868,7 @@ int nlfem_autotune(nlfem_mesh_t mesh, const nlfem_params* params, void* stream, 
             double t = 1e300;
             for (int rep = 0; rep < 2; ++rep) {
                 NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
-                launch_trunc_fast(m, *pc, P, BulkAcc{acc.p, kkll.p, &fix.p->scale, &fix.p->max_exact, 1}, st,
+                launch_trunc_fast(m, *pc, P, BulkAcc{acc.p, llrec.p, &fix.p->scale, &fix.p->max_exact, 1}, st,
                                   ev + 2);
                 NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
                 NLFEM_CUDA_TRY(cudaEventSynchronize(ev[1]));

@@ -239,7 +239,6 @@ struct PairCache {
     DBuf<int> up_row;        //   and row i (built with the slot index, for the ordered reduction)
     int64_t n_upper = 0;
     bool slots_built = false;
-    int sq32 = 1;  // infinity ball: few vertices on the squares' sides, the FP32 passes pay off
     // FP32 bulk: the fixed-point scale the pilot pass picked for the parameters with this key
     // (a function of the pattern and the parameters alone, so a later assembly reuses it)
     uint64_t scale_key = 0;
@@ -247,7 +246,7 @@ struct PairCache {
     DBuf<FixState> scale_memo;
     // FP32-bulk accumulation index: upper entries numbered row by row in node order
     DBuf<int64_t> up_start;  // [M + 1] first upper entry of each node row
-    DBuf<int> epos;          // [K * 6] upper entry of each node pair of an element
+    DBuf<int> epos;          // [K * 8] upper entry of each node pair of an element (6 used)
     DBuf<uint16_t> klr_whole, klr_cut;  // [9][list length] rank of (k_a, l_b) in row min(k_a, l_b)
     int64_t acc_terms = 0;   // bound on the number of values added into one upper entry
     double t_pairs_ms = 0, t_pattern_ms = 0;
@@ -288,7 +287,7 @@ struct System {
     DBuf<float> contrib32;   // records [P * NE] (FP32 bulk: only the close-list pairs, in list order)
     DBuf<double> contrib64;  // records [P * NE] (FP64 plain)
     DBuf<unsigned long long> acc;  // FP32 bulk: fixed-point upper entries [n_upper * NC]
-    DBuf<float> kkll;        // FP32 bulk: kk and ll of every pair [P * 12 NC]
+    DBuf<float> llrec;       // FP32 bulk: ll of every pair [P * 6 NC]
     DBuf<FixState> fix;      // FP32 bulk: the fixed-point scale
     DBuf<double> msc64;      // label-dependent kernel: the scale table on the device
     DBuf<float> msc32;
@@ -321,7 +320,7 @@ void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStr
 // records the largest |value| of every pstride-th pair
 struct BulkAcc {
     unsigned long long* acc;
-    float* kkll;            // [P][12 NC] per-pair kk and ll records
+    float* llrec;           // [P][6 NC] per-pair ll records
     const float* scale_p;   // 2^S in device memory
     unsigned int* maxabs;
     int64_t pstride;
@@ -360,7 +359,7 @@ struct BatchSys {
 };
 // The FP32-bulk value assembly of several systems: prepare() allocates the per-system
 // working buffers and uploads the fused launches' request tables; record() enqueues every
-// step (close lists, pilot, scale, fused bulk launches, element sums, check, and with finish
+// step (close lists, pilot, scale, fused bulk launches, ll sums, close-list adds, check, and with finish
 // also the conversion to CSR and the load vector) with stream operations only, so that it can
 // be captured into a CUDA graph and replayed.
 struct BatchExec {

@@ -793,8 +793,9 @@ __global__ void k_epos(const int4* __restrict__ T, int64_t K, const int64_t* __r
         if (r < 0) atomicOr(ovf, 1);
         const int64_t u = up_start[lo] + max(r, 0);
         if (u > 0x7fffffffll) atomicOr(ovf, 4);
-        epos[k * 6 + e] = (int)u;
+        epos[k * 8 + e] = (int)u;
     }
+    epos[k * 8 + 6] = epos[k * 8 + 7] = 0;
 }
 
 __global__ void k_klr(const int* __restrict__ ids, int64_t n, const int* __restrict__ pk, const int* __restrict__ pl,
@@ -825,7 +826,7 @@ void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st) {
     DBuf<int> ovf;
     ovf.alloc(1, st);
     ovf.zero(st);
-    pc.epos.alloc(K * 6, st);
+    pc.epos.alloc(K * 8, st);
     k_epos<<<nblk(K, 256), 256, 0, st>>>(m.T.p, K, pc.nrow_ptr.p, pc.ncol.p, pc.up_start.p, pc.epos.p, ovf.p);
     NLFEM_LAUNCH_CHECK();
     pc.klr_whole.alloc(pc.nwhole * 9, st);

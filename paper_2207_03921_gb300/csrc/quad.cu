@@ -735,15 +735,14 @@ __global__ void k_close_acc(const int* __restrict__ ids, int64_t n, const int* _
     if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(maxabs, __float_as_uint(vmax));
 }
 
-// kk of every element summed over its pairs (k, .) in pair order (LL = false), or ll over
-// its pairs (., l) in the order of the transposed index (LL = true): a warp per element,
-// a fixed butterfly, then one fixed-point add per node pair of the element. Pairs of the
-// close list (singular or diamond rule) have no record and are skipped.
-template <int NC, bool LL>
-__global__ void k_elem_sums(int64_t K, const int64_t* __restrict__ ptr, const int* __restrict__ perm,
-                            const int8_t* __restrict__ pcls, int skip_close, const float* __restrict__ kkll,
-                            const int* __restrict__ epos, unsigned long long* __restrict__ acc,
-                            const float* __restrict__ scale_p) {
+// ll of every element summed over its pairs (., l) in the order of the transposed index: a warp
+// per element, a fixed butterfly, then one fixed-point add per node pair of the element. Pairs
+// of the close list (singular or diamond rule) have no record and are skipped.
+template <int NC>
+__global__ void k_ll_sums(int64_t K, const int64_t* __restrict__ ptr, const int* __restrict__ perm,
+                          const int8_t* __restrict__ pcls, int skip_close, const float* __restrict__ llrec,
+                          const int* __restrict__ epos, unsigned long long* __restrict__ acc,
+                          const float* __restrict__ scale_p) {
     const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (e >= K) return;  // whole warps leave together
@@ -751,9 +750,9 @@ __global__ void k_elem_sums(int64_t K, const int64_t* __restrict__ ptr, const in
 #pragma unroll
     for (int x = 0; x < 6 * NC; ++x) s[x] = 0.f;
     for (int64_t j = ptr[e] + lane; j < ptr[e + 1]; j += 32) {
-        const int64_t p = perm ? (int64_t)perm[j] : j;
+        const int64_t p = perm[j];
         if (skip_close && pcls[p] > 0) continue;
-        const float2* r = reinterpret_cast<const float2*>(kkll + p * (6 * NC));
+        const float2* r = reinterpret_cast<const float2*>(llrec + p * (6 * NC));
 #pragma unroll
         for (int x = 0; x < 3 * NC; ++x) {
             const float2 v = r[x];
@@ -768,7 +767,7 @@ __global__ void k_elem_sums(int64_t K, const int64_t* __restrict__ ptr, const in
     if (lane == 0)
 #pragma unroll
         for (int x = 0; x < 6; ++x) {
-            const int64_t u = epos[e * 6 + x];
+            const int64_t u = epos[e * 8 + x];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const long long q = __float2ll_rn(s[c * 6 + x] * scale);
@@ -777,21 +776,16 @@ __global__ void k_elem_sums(int64_t K, const int64_t* __restrict__ ptr, const in
         }
 }
 
-static void elem_sums(Mesh& m, PairCache& pc, const Params& prm, System& sys, const float* scale, cudaStream_t st) {
+static void ll_sums(Mesh& m, PairCache& pc, const Params& prm, System& sys, const float* scale, cudaStream_t st) {
     const int skip = close_mode(prm) != 0;
     const unsigned g = nblk(m.K * 32, 256);
     if (m.K == 0) return;
-    if (pc.ndof == 1) {
-        k_elem_sums<1, false><<<g, 256, 0, st>>>(m.K, pc.pair_ptr.p, nullptr, pc.pcls.p, skip, sys.kkll.p,
-                                                  pc.epos.p, sys.acc.p, scale);
-        k_elem_sums<1, true><<<g, 256, 0, st>>>(m.K, pc.pT_ptr.p, pc.pT_id.p, pc.pcls.p, skip,
-                                                 sys.kkll.p + pc.npairs * 6, pc.epos.p, sys.acc.p, scale);
-    } else {
-        k_elem_sums<3, false><<<g, 256, 0, st>>>(m.K, pc.pair_ptr.p, nullptr, pc.pcls.p, skip, sys.kkll.p,
-                                                  pc.epos.p, sys.acc.p, scale);
-        k_elem_sums<3, true><<<g, 256, 0, st>>>(m.K, pc.pT_ptr.p, pc.pT_id.p, pc.pcls.p, skip,
-                                                 sys.kkll.p + pc.npairs * 18, pc.epos.p, sys.acc.p, scale);
-    }
+    if (pc.ndof == 1)
+        k_ll_sums<1><<<g, 256, 0, st>>>(m.K, pc.pT_ptr.p, pc.pT_id.p, pc.pcls.p, skip, sys.llrec.p, pc.epos.p,
+                                        sys.acc.p, scale);
+    else
+        k_ll_sums<3><<<g, 256, 0, st>>>(m.K, pc.pT_ptr.p, pc.pT_id.p, pc.pcls.p, skip, sys.llrec.p, pc.epos.p,
+                                        sys.acc.p, scale);
     NLFEM_LAUNCH_CHECK();
 }
 
@@ -886,8 +880,8 @@ __global__ void k_fix_exact(FixState* f) {
 static void bulk_main(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStream_t st, cudaEvent_t* ev) {
     FixState* f = sys.fix.p;
     sys.acc.zero(st);
-    launch_trunc_fast(m, pc, prm, BulkAcc{sys.acc.p, sys.kkll.p, &f->scale, &f->max_exact, 1}, st, ev + 2);
-    elem_sums(m, pc, prm, sys, &f->scale, st);
+    launch_trunc_fast(m, pc, prm, BulkAcc{sys.acc.p, sys.llrec.p, &f->scale, &f->max_exact, 1}, st, ev + 2);
+    ll_sums(m, pc, prm, sys, &f->scale, st);
     close_acc(m, pc, sys, sys.acc.p, &f->scale, &f->max_exact, st);
     NLFEM_CUDA_TRY(cudaEventRecord(ev[5], st));
     k_fix_check<<<1, 1, 0, st>>>(f, pc.acc_terms);
@@ -898,8 +892,9 @@ static void bulk_main(Mesh& m, PairCache& pc, const Params& prm, System& sys, cu
 // in FP64, or the canonical truncation kernel) writes compact records; (2) a pilot pass over
 // every 61st pair of the whole and cut lists, plus the close records, records the largest
 // |value| and k_fix_pick fixes the scale 2^S; (3) the bulk kernels add kl into the
-// fixed-point accumulators and write kk / ll records, which k_elem_sums sums per element,
-// and the close records are added, recording the exact largest |value|; (4) k_fix_check
+// fixed-point accumulators (kl per pair, kk per outer element of a warp tile) and write ll
+// records, which k_ll_sums sums per element, and the close records are added, recording the
+// exact largest |value|; (4) k_fix_check
 // flags the assembly if that value could overflow a sum or leaves more than 2^16 of unused
 // range; the caller then runs bulk_redo (3 again with the scale from the exact value). S is
 // a function of the inputs alone, so the result is the same in every run.
@@ -929,7 +924,7 @@ static void run_bulk(Mesh& m, PairCache& pc, const Params& prm, System& sys, cud
         }
     }
     sys.acc.alloc(std::max<int64_t>(pc.n_upper * NC, 1), st);
-    sys.kkll.alloc(pc.npairs * 12 * NC, st);
+    sys.llrec.alloc(std::max<int64_t>(pc.npairs * 6 * NC, 1), st);
     bulk_main(m, pc, prm, sys, st, ev);
 }
 
@@ -943,7 +938,7 @@ void bulk_redo(Mesh& m, PairCache& pc, const Params& prm, System& sys, cudaStrea
 // cut-pair kernels of all requests of one kernel class fused into one launch each (pilot and
 // main pass). Each system's scale is chosen from its own pilot values, so every system is
 // the same bits as when it is assembled alone. Events (optional): [0, 1] close-list kernels,
-// [2, 3] fused whole-pair launches, [3, 4] fused cut-pair launches, [4, 5] element sums and
+// [2, 3] fused whole-pair launches, [3, 4] fused cut-pair launches, [4, 5] ll sums and
 // close-list adds.
 static int64_t class_key(const Params& p) {
     return ((int64_t)p.kernel * 64 + p.ro.n) * 64 * 8 + (int64_t)p.ri.n * 8 + p.ball;
@@ -961,7 +956,7 @@ void BatchExec::prepare(cudaStream_t st) {
         }
         sys.fix.ensure(1, st);
         sys.acc.ensure(std::max<int64_t>(pc.n_upper * NC, 1), st);
-        sys.kkll.ensure(pc.npairs * 12 * NC, st);
+        sys.llrec.ensure(std::max<int64_t>(pc.npairs * 6 * NC, 1), st);
     }
     std::vector<int64_t> keys;  // kernel classes, in the order of first appearance
     for (BatchSys& it : items) {
@@ -977,8 +972,8 @@ void BatchExec::prepare(cudaStream_t st) {
             if (class_key(it.prm) != key) continue;
             FixState* f = it.sys->fix.p;
             gp.push_back(BulkItem{it.m, it.pc, it.prm, BulkAcc{nullptr, nullptr, nullptr, &f->max_pilot, 61}});
-            gm.push_back(BulkItem{it.m, it.pc, it.prm, BulkAcc{it.sys->acc.p, it.sys->kkll.p, &f->scale,
-                                                               &f->max_exact, 1}});
+            gm.push_back(BulkItem{it.m, it.pc, it.prm, BulkAcc{it.sys->acc.p, it.sys->llrec.p, &f->scale, &f->max_exact,
+                                                               1}});
         }
         pilot.push_back(make_fused(gp, 0, 61, st));
         pilot.push_back(make_fused(gp, 1, 61, st));
@@ -1011,7 +1006,7 @@ void BatchExec::record(cudaStream_t st, cudaEvent_t* ev, bool finish, const std:
     if (ev) NLFEM_CUDA_TRY(cudaEventRecord(ev[4], st));
     for (BatchSys& it : items) {
         FixState* fx = it.sys->fix.p;
-        elem_sums(*it.m, *it.pc, it.prm, *it.sys, &fx->scale, st);
+        ll_sums(*it.m, *it.pc, it.prm, *it.sys, &fx->scale, st);
         close_acc(*it.m, *it.pc, *it.sys, it.sys->acc.p, &fx->scale, &fx->max_exact, st);
         k_fix_check<<<1, 1, 0, st>>>(fx, it.pc->acc_terms);
         NLFEM_LAUNCH_CHECK();

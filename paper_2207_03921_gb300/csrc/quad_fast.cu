@@ -54,7 +54,6 @@ struct FastReq {
     float delta, d2, c, s;
     double delta64, delta2_64;
     int ball;     // NLFEM_BALL_*
-    int sq32;     // infinity ball: try the FP32 passes before the canonical cut
     int geo64;    // every cut outer point takes the canonical FP64 cut (no FP32 positions)
     int nmat;     // label-dependent kernel: factor msc[mat[k] * nmat + mat[l]] (0: none)
     const int8_t* mat;
@@ -64,10 +63,9 @@ struct FastReq {
     const float* tab;
     // fixed-point accumulation into the upper CSR entries (see accumulate_pair)
     unsigned long long* acc;  // [n_upper][NC] int64 two's complement sums
-    float* kkll;              // [2][P][6 NC] kk, then ll, of every pair, by pair id
-    int64_t npairs_all;       // P
+    float* llrec;             // [P][6 NC] ll of every pair, by pair id (summed per element later)
     const int64_t* up_start;  // [M + 1] first upper entry of each node row
-    const int* epos;          // [K][6] upper entries of an element's node pairs (kkI order)
+    const int* epos;          // [K][8] upper entries of an element's six node pairs (kkI order), padded
     const uint16_t* klr;      // [9][npairs] rank of the kl node pair in its upper row, list order
     const float* scale_p;     // 2^S (device memory)
     unsigned int* maxabs;     // bits of the largest |value| seen (a positive float), atomicMax
@@ -199,16 +197,16 @@ __device__ __forceinline__ void outer_update(float4 o, float dk, const Inner<NC>
     }
 }
 
-// Accumulation of a pair's block [[kk, kl], [kl^T, ll]].
-// kk and ll only involve the nodes of one element: they are written to the pair's record
-// (kk of pair p at kkll[p], ll at kkll[P + p], 6 values per component) and summed per
-// element later in a fixed order
-// (k_elem_sums). kl[a][b] belongs to the node pair (k_a, l_b); it is rounded once to a signed
-// 64-bit fixed-point number v * 2^S and added to that upper CSR entry with an integer atomic
-// (counted twice when the two nodes coincide: both mirrored entries of the symmetric block
-// are diagonal). Integer addition is associative, so the sums are the same bits in every
-// run whatever order the pairs are processed in. Peridynamics: NC = 3 components xx, xy, yy
-// (the block of a node pair is symmetric).
+// Accumulation of a pair's block [[kk, kl], [kl^T, ll]] into the fixed-point upper CSR
+// entries: each value v is rounded once to the signed 64-bit integer v * 2^S and added with an
+// integer atomic. Integer addition is associative, so the sums are the same bits in every run
+// whatever order the pairs (or the warps) are processed in. kl[a][b] belongs to the node pair
+// (k_a, l_b) (counted twice when the two nodes coincide: both mirrored entries of the symmetric
+// block are diagonal); kk belongs to the node pairs of E_k and is first summed over the warp's
+// pairs with the same outer element (accumulate_kk); ll belongs to those of E_l, which differ
+// from lane to lane: it is written to the pair's record and summed per element in a fixed order
+// (k_ll_sums), since six more atomics per pair would make the whole-pair kernel bound by the L2
+// atomic rate. Peridynamics: NC = 3 components xx, xy, yy (a node pair's block is symmetric).
 __device__ __forceinline__ long long to_fixed(float sc, float v, float& vmax) {
     vmax = fmaxf(vmax, fabsf(v));
     return __float2ll_rn(v * sc);
@@ -216,8 +214,7 @@ __device__ __forceinline__ long long to_fixed(float sc, float v, float& vmax) {
 
 template <int NC>
 __device__ __forceinline__ void accumulate_pair(const FastReq& Q, bool pilot, float sc, int64_t pi, int64_t p, int4 tk,
-                                                int4 tl, const int* upos,
-                                                float (&kk)[6][NC], float (&kl)[9][NC],
+                                                int4 tl, const int* upos, float (&kk)[6][NC], float (&kl)[9][NC],
                                                 float (&ll)[6][NC], float& vmax, int k, int l) {
     const int kn[3] = {tk.x, tk.y, tk.z}, ln[3] = {tl.x, tl.y, tl.z};
     if (Q.nmat) {  // label-dependent kernel: the pair's factor
@@ -244,15 +241,11 @@ __device__ __forceinline__ void accumulate_pair(const FastReq& Q, bool pilot, fl
             for (int e = 0; e < 9; ++e) vmax = fmaxf(vmax, fabsf(kl[e][c]) * (kn[e / 3] == ln[e % 3] ? 2.f : 1.f));
         return;
     }
-    float2* rk = reinterpret_cast<float2*>(Q.kkll + p * (6 * NC));
-    float2* rl = reinterpret_cast<float2*>(Q.kkll + (Q.npairs_all + p) * (6 * NC));
+    float2* rl = reinterpret_cast<float2*>(Q.llrec + p * (6 * NC));
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int x = 0; x < 3; ++x) {
-            rk[3 * c + x] = make_float2(kk[2 * x][c], kk[2 * x + 1][c]);
-            rl[3 * c + x] = make_float2(ll[2 * x][c], ll[2 * x + 1][c]);
-        }
+        for (int x = 0; x < 3; ++x) rl[3 * c + x] = make_float2(ll[2 * x][c], ll[2 * x + 1][c]);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -267,6 +260,47 @@ __device__ __forceinline__ void accumulate_pair(const FastReq& Q, bool pilot, fl
                 if (q) atomicAdd(Q.acc + u * NC + c, (unsigned long long)q);
             }
         }
+}
+
+// kk summed over the warp's pairs of each outer element present in the tile (pairs of one tile
+// mostly share E_k): a masked xor butterfly, which leaves the same bits in every lane, then one
+// fixed-point add per node pair of E_k. All 32 lanes call it; valid = the lane holds a pair.
+// The sum of at most 32 values of one E_k stays within the bound the scale S assumes (every value
+// counts among the terms added into that entry).
+template <int NC>
+__device__ __forceinline__ void accumulate_kk(const FastReq& Q, bool pilot, float sc, bool valid, int k,
+                                              const float (&kk)[6][NC]) {
+    if (pilot) return;
+    const int lane = threadIdx.x & 31;
+    unsigned todo = __ballot_sync(0xffffffffu, valid);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        const int kx = __shfl_sync(0xffffffffu, k, src);
+        const bool mine = valid && k == kx;
+        todo &= ~__ballot_sync(0xffffffffu, mine);
+        float v[6][NC];
+#pragma unroll
+        for (int e = 0; e < 6; ++e)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float x = mine ? kk[e][c] : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                v[e][c] = x;
+            }
+        if (lane == src) {
+            const int4 ek = *reinterpret_cast<const int4*>(Q.epos + (int64_t)kx * 8);
+            const int2 ek2 = *reinterpret_cast<const int2*>(Q.epos + (int64_t)kx * 8 + 4);
+            const int kpos[6] = {ek.x, ek.y, ek.z, ek.w, ek2.x, ek2.y};
+#pragma unroll
+            for (int e = 0; e < 6; ++e)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const long long q = __float2ll_rn(v[e][c] * sc);
+                    if (q) atomicAdd(Q.acc + (int64_t)kpos[e] * NC + c, (unsigned long long)q);
+                }
+        }
+    }
 }
 
 __device__ __forceinline__ void flush_max(unsigned int* maxabs, float vmax) {
@@ -427,19 +461,19 @@ __device__ __noinline__ int clip_square_f32(const double2* __restrict__ X, int4 
 // number of polygon points written to dst (0 = empty), or -1 when some decision is too close
 // to call (the caller then takes the canonical FP64 cut).
 __device__ __forceinline__ int sh_pass32(const float* ix, const float* iy, const float* ie, int n, int a, float s,
-                                         float d, float* ox, float* oy, float* oe, bool& ok) {
+                                         float d, float* ox, float* oy, float* oe, bool& ok, bool exact) {
     if (n == 0) return 0;
     int m = 0;
     float Sx = ix[n - 1], Sy = iy[n - 1], Se = ie[n - 1];
     float Sa = a ? Sy : Sx;
     float mS = s * Sa - d;  // > 0: outside
-    ok &= fabsf(mS) > Se + 2.4e-7f * (d + fabsf(Sa));
+    if (exact) ok &= fabsf(mS) > Se + 2.4e-7f * (d + fabsf(Sa));
     bool s_in = mS <= 0.f;
     for (int i = 0; i < n; ++i) {
         const float Ex = ix[i], Ey = iy[i], Ee = ie[i];
         const float Ea = a ? Ey : Ex;
         const float mE = s * Ea - d;
-        ok &= fabsf(mE) > Ee + 2.4e-7f * (d + fabsf(Ea));
+        if (exact) ok &= fabsf(mE) > Ee + 2.4e-7f * (d + fabsf(Ea));
         const bool e_in = mE <= 0.f;
         if (e_in != s_in) {
             const float Sb = a ? Sx : Sy, Eb = a ? Ex : Ey;
@@ -472,7 +506,11 @@ __device__ __forceinline__ int sh_pass32(const float* ix, const float* iy, const
     return m < 8 ? m : 8;
 }
 
-__device__ __noinline__ int clip_square_fast(const float Rx[3], const float Ry[3], float eps, float d, float2* dst) {
+// exact = false: the FP32 passes alone (a decision within rounding of a side may differ from the
+// FP64 one, which moves that polygon edge by a rounding-sized sliver); -1 only when more than 7
+// points come out
+__device__ __noinline__ int clip_square_fast(const float Rx[3], const float Ry[3], float eps, float d, float2* dst,
+                                             bool exact) {
     float Ax[8], Ay[8], Ae[8], Bx[8], By[8], Be[8];
     for (int v = 0; v < 3; ++v) {
         Ax[v] = Rx[v];
@@ -480,15 +518,16 @@ __device__ __noinline__ int clip_square_fast(const float Rx[3], const float Ry[3
         Ae[v] = eps;
     }
     bool ok = true;
-    int n = sh_pass32(Ax, Ay, Ae, 3, 0, 1.f, d, Bx, By, Be, ok);
-    n = sh_pass32(Bx, By, Be, n, 1, 1.f, d, Ax, Ay, Ae, ok);
-    n = sh_pass32(Ax, Ay, Ae, n, 0, -1.f, d, Bx, By, Be, ok);
-    n = sh_pass32(Bx, By, Be, n, 1, -1.f, d, Ax, Ay, Ae, ok);
+    int n = sh_pass32(Ax, Ay, Ae, 3, 0, 1.f, d, Bx, By, Be, ok, exact);
+    n = sh_pass32(Bx, By, Be, n, 1, 1.f, d, Ax, Ay, Ae, ok, exact);
+    n = sh_pass32(Ax, Ay, Ae, n, 0, -1.f, d, Bx, By, Be, ok, exact);
+    n = sh_pass32(Bx, By, Be, n, 1, -1.f, d, Ax, Ay, Ae, ok, exact);
     if (!ok || n > 7) return -1;
-    for (int i = 0; i < n; ++i) {  // no two consecutive points may coincide (all decisions strict)
-        const int j = i + 1 < n ? i + 1 : 0;
-        if (n > 1 && fabsf(Ax[i] - Ax[j]) + fabsf(Ay[i] - Ay[j]) <= 2.f * (Ae[i] + Ae[j])) return -1;
-    }
+    if (exact)
+        for (int i = 0; i < n; ++i) {  // no two consecutive points may coincide (all decisions strict)
+            const int j = i + 1 < n ? i + 1 : 0;
+            if (n > 1 && fabsf(Ax[i] - Ax[j]) + fabsf(Ay[i] - Ay[j]) <= 2.f * (Ae[i] + Ae[j])) return -1;
+        }
     if (n < 3) return 0;
     for (int i = 0; i < n; ++i) dst[i * FAST_THREADS] = make_float2(Ax[i], Ay[i]);
     return n;
@@ -517,9 +556,13 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
     auto put = [&](int q, int slot, float x, float y) { my[(q * MAXP + slot) * FAST_THREADS] = make_float2(x, y); };
     __shared__ FastReq sq[BATCH ? FAST_WARPS : 1];
     // infinity ball: per-thread element triples and per-warp job lists of the canonical cuts
-    __shared__ int4 s_tk[SQUARE ? FAST_THREADS : 1], s_tl[SQUARE ? FAST_THREADS : 1];
-    __shared__ unsigned char s_job[SQUARE ? FAST_WARPS * 32 * CHUNK : 1];
-    __shared__ unsigned char s_cnt[SQUARE ? FAST_THREADS * CHUNK : 1];
+    // the canonical FP64 cuts of a chunk go to a per-warp job list (nocaps and the infinity
+    // ball); with caps they run in place, which keeps this block's shared memory at three blocks
+    // per SM (the caps polygons need 9 slots per outer point)
+    constexpr bool JOBS = !CAPS;
+    __shared__ int s_k[JOBS ? FAST_THREADS : 1], s_l[JOBS ? FAST_THREADS : 1];
+    __shared__ unsigned char s_job[JOBS ? FAST_WARPS * 32 * CHUNK : 1];
+    __shared__ unsigned char s_cnt[JOBS ? FAST_THREADS * CHUNK : 1];
     __shared__ float4 s_orule[16];  // outer rule (l0, l1, l2, w)
     for (int i = threadIdx.x; i < 16; i += blockDim.x)
         s_orule[i] = make_float4(R.ol[i][0], R.ol[i][1], R.ol[i][2], R.ow[i]);
@@ -588,42 +631,49 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
             const int qn = min(CHUNK, nqo - qb);
             // ---- phase A: polygons of outer points qb .. qb + qn - 1, in lockstep
             unsigned long long counts = 0;  // 4 bits per outer point: number of polygon points
-            unsigned need = 0;              // infinity ball: outer points left to the canonical cut
+            unsigned need = 0;              // outer points left to the canonical FP64 cut
 #pragma unroll 1
             for (int q = 0; q < qn; ++q) {
                 const int q0 = qb + q;
                 if (SQUARE) {
-                    // FP32 vertex tests with a margin decide the whole element (every vertex inside
-                    // the square) and the empty cut (every vertex beyond one side); the rest takes
-                    // the canonical FP64 cut
+                    // FP32 vertex tests decide the whole element (every vertex inside the square)
+                    // and the empty cut (every vertex beyond one side); the rest is cut by the FP32
+                    // Sutherland-Hodgman passes or by the canonical FP64 cut.
+                    // The constant kernel takes the FP32 passes without margins: its inner integrand
+                    // is a polynomial of degree 2 that the inner rule integrates exactly on any
+                    // triangle, so only the region matters, and the square cut moves it continuously
+                    // (a decision within rounding of a side shifts a polygon edge by a sliver).
+                    // Other kernels depend on the fan triangulation, so their decisions must equal
+                    // the FP64 ones: margins on every test, a vertex near a side or an undecided pass
+                    // goes to the canonical cut. With geo64 every open cut is canonical.
+                    constexpr bool RELAX = KER == NLFEM_KERNEL_CONSTANT;
                     int n = 0;
                     if (valid) {
                         const float Xx = R.ol[q0][1] * Ek.x + R.ol[q0][2] * Ek.z;
                         const float Xy = R.ol[q0][1] * Ek.y + R.ol[q0][2] * Ek.w;
                         const float Rx[3] = {W0x - Xx, W1x - Xx, W2x - Xx}, Ry[3] = {W0y - Xy, W1y - Xy, W2y - Xy};
-                        const float lo = Q.delta - eps - 1e-6f * Q.delta, hi = Q.delta + eps + 1e-6f * Q.delta;
+                        const bool exact = !RELAX || Q.geo64;
+                        const float mg = exact ? eps + 1e-6f * Q.delta : 0.f;
+                        const float lo = Q.delta - mg, hi = Q.delta + mg;
                         bool allin = true, tie = false;
                         int oxp = 0, oxm = 0, oyp = 0, oym = 0;
 #pragma unroll
                         for (int m = 0; m < 3; ++m) {
-                            allin &= fabsf(Rx[m]) < lo && fabsf(Ry[m]) < lo;
+                            allin &= fabsf(Rx[m]) <= lo && fabsf(Ry[m]) <= lo;
                             oxp += Rx[m] > hi;
                             oxm += Rx[m] < -hi;
                             oyp += Ry[m] > hi;
                             oym += Ry[m] < -hi;
-                            tie |= (fabsf(Rx[m]) >= lo && fabsf(Rx[m]) <= hi) || (fabsf(Ry[m]) >= lo && fabsf(Ry[m]) <= hi);
+                            tie |= (fabsf(Rx[m]) > lo && fabsf(Rx[m]) <= hi) || (fabsf(Ry[m]) > lo && fabsf(Ry[m]) <= hi);
                         }
                         if (allin) {
 #pragma unroll
                             for (int m = 0; m < 3; ++m) put(q, m, Rx[m], Ry[m]);
                             n = 3;
                         } else if (oxp < 3 && oxm < 3 && oyp < 3 && oym < 3) {
-                            // a vertex on a side of the square goes to the canonical cut at once, and
-                            // so does every open cut on meshes whose grid lines the square's sides
-                            // follow (Q.sq32 = 0: the FP32 passes would mostly end undecided); the
-                            // others try the FP32 passes first
-                            n = (tie || !Q.sq32 || Q.geo64) ? -1
-                                                 : clip_square_fast(Rx, Ry, eps, Q.delta, my + q * MAXP * FAST_THREADS);
+                            n = (Q.geo64 || (exact && tie))
+                                    ? -1
+                                    : clip_square_fast(Rx, Ry, eps, Q.delta, my + q * MAXP * FAST_THREADS, exact);
                             if (n < 0) {
                                 n = 0;
                                 need |= 1u << q;
@@ -640,6 +690,8 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                 float Cc[3];
 #pragma unroll
                 for (int m = 0; m < 3; ++m) Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - Q.d2;
+                // FP32 decisions, each taken only beyond its error bound (ok = every decision of
+                // this outer point equals the canonical FP64 one)
                 GeoF G;
                 bool ok = decide_flat<true>(Rx, Ry, Cc, Ed, eps, floor2, Q.d2, G, !valid);
                 int n = 0;
@@ -685,20 +737,33 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                     if (!(G.in[0] && G.in[1] && G.in[2]) && nraw >= 2 && !(fv && fe == (le + 1) % 3))
                         cap(lx, ly, fx, fy);
                 }
-                // an undecided outer point, or with geo64 every outer point whose inner element is
-                // cut (the FP32 decisions equal the FP64 ones, so the others are whole or empty)
+                // an undecided outer point (a vertex within its error bound of the circle, a near
+                // tangent edge, a degenerate cap chord), and with geo64 every outer point whose inner
+                // element is cut (its decisions equal the FP64 ones, so the others are whole or
+                // empty), takes the canonical FP64 cut below. A decision near a tie cannot be left
+                // to FP32: the polygon is discontinuous at a tangent edge (the tangent point adds a
+                // cap-sized triangle) and a root next to a tangency is only sqrt(eps) accurate.
+                const bool whole = G.in[0] && G.in[1] && G.in[2];
                 if (!valid) n = 0;
-                else if (!ok || (Q.geo64 && n >= 3 && !(G.in[0] && G.in[1] && G.in[2])))
-                    n = clip_canonical(Q.X, tk, tl, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2], Q.delta64, Q.delta2_64,
-                                       CAPS, my + q * MAXP * FAST_THREADS, MAXP);
+                else if (!ok || (Q.geo64 && n >= 3 && !whole)) {
+                    if (JOBS) {
+                        n = 0;
+                        need |= 1u << q;
+                    } else {
+                        n = clip_canonical(Q.X, tk, tl, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2], Q.delta64,
+                                           Q.delta2_64, CAPS, my + q * MAXP * FAST_THREADS, MAXP);
+                    }
+                }
                 counts |= (unsigned long long)(n < 3 ? 0 : n) << (4 * q);
             }
-            if (SQUARE) {
-                // the canonical cuts of the chunk spread over the warp's lanes: job j of the warp
-                // is (owner lane, outer point); its polygon goes to the owner's slots
+            if (JOBS && __any_sync(0xffffffffu, need != 0)) {
+                // the canonical FP64 cuts of the chunk spread over the warp's lanes (the FP64 pipe
+                // is 1/64 of the FP32 rate, so one cut per lane rather than one per outer point and
+                // warp): job j of the warp is (owner lane, outer point); its polygon goes to the
+                // owner's slots
                 const int lane = threadIdx.x & 31, wbase = warp * 32;
-                s_tk[threadIdx.x] = tk;
-                s_tl[threadIdx.x] = tl;
+                s_k[threadIdx.x] = k;
+                s_l[threadIdx.x] = l;
                 const int mine = __popc(need);
                 int incl = mine;
 #pragma unroll
@@ -714,9 +779,12 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                 for (int jj = lane; jj < total; jj += 32) {
                     const int code = s_job[wbase * CHUNK + jj];
                     const int owner = code >> 3, q = code & 7, q0 = qb + q;
-                    const int n = clip_square_f32(Q.X, s_tk[wbase + owner], s_tl[wbase + owner], R.ro[q0][0],
-                                                  R.ro[q0][1], R.ro[q0][2], Q.delta64,
-                                                  s_pts + wbase + owner + q * MAXP * FAST_THREADS);
+                    float2* dst = s_pts + wbase + owner + q * MAXP * FAST_THREADS;
+                    const int4 tkj = Q.T[s_k[wbase + owner]], tlj = Q.T[s_l[wbase + owner]];
+                    const int n = SQUARE ? clip_square_f32(Q.X, tkj, tlj, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2],
+                                                           Q.delta64, dst)
+                                         : clip_canonical(Q.X, tkj, tlj, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2],
+                                                          Q.delta64, Q.delta2_64, CAPS, dst, MAXP);
                     s_cnt[(wbase + owner) * CHUNK + q] = (unsigned char)(n < 3 ? 0 : n);
                 }
                 __syncwarp();
@@ -770,13 +838,14 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
             }
         }
         if (valid) accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, nullptr, kk, kl, ll, vmax, k, l);
+        accumulate_kk<NC>(Q, pilot, sc, valid, k, kk);
     }
     if (vdst) flush_max(vdst, vmax);
 }
 
 // Fan triangles of a cut pair summed over its outer points, from the same FP32 decisions
 // (an undecided outer point counts its FP32 outcome; the count only orders the work).
-__global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key, unsigned long long* ties) {
+__global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key) {
     const int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pi >= Q.npairs) return;
     const int64_t p = Q.ids[pi];
@@ -788,22 +857,15 @@ __global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key, unsigne
     const float Wx[3] = {dx, dx + El.x, dx + El.z}, Wy[3] = {dy, dy + El.y, dy + El.w};
     const int nqo = R.nqo;
     int tris = 0;
-    if (Q.ball == NLFEM_BALL_INFINITY) {  // the canonical cut (the cut kernel uses it too)
+    if (Q.ball == NLFEM_BALL_INFINITY) {  // the square cut's triangle count (ordering only)
         const double2 Vk[3] = {v0k, Q.X[tk.y], Q.X[tk.z]}, Vl[3] = {v0l, Q.X[tl.y], Q.X[tl.z]};
-        unsigned long long nt = 0;  // outer points with a vertex on a side of the square
         for (int q0 = 0; q0 < nqo; ++q0) {
             const double2 xp = nl_map(Vk, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2]);
             bool full;
             const int n = nl_clip_square(Vl, xp, Q.delta64, nullptr, full);
             tris += n >= 3 ? n - 2 : 0;
-            bool tie = false;
-            for (int v = 0; v < 3; ++v)
-                tie |= fabs(fabs(Vl[v].x - xp.x) - Q.delta64) <= 1e-9 * Q.delta64 ||
-                       fabs(fabs(Vl[v].y - xp.y) - Q.delta64) <= 1e-9 * Q.delta64;
-            nt += tie;
         }
         key[pi] = tris;
-        atomicAdd(ties, nt);
         return;
     }
     for (int q0 = 0; q0 < nqo; ++q0) {
@@ -862,9 +924,13 @@ __global__ void __launch_bounds__(FAST_THREADS, (KER != NLFEM_KERNEL_PERIDYNAMIC
         const float sc = pilot ? 1.f : *Q.scale_p;
         const int64_t pi = (int64_t)tile.y + (threadIdx.x & 31);
         const int64_t nlist = pilot ? (Q.npairs + L.pilot - 1) / L.pilot : Q.npairs;
-        if (pi < nlist) {
+        const bool valid = pi < nlist;
+        float kk[6][NC];
+        int k = 0;
+        if (valid) {
             const int64_t p = Q.ids[pilot ? pi * L.pilot : pi];
-            const int k = Q.pk[p], l = Q.pl[p];
+            k = Q.pk[p];
+            const int l = Q.pl[p];
             const ElemRec rk = Q.rec[k], rl = Q.rec[l];
             const int4 tk = make_int4(rk.n0, rk.n1, rk.n2, 0), tl = make_int4(rl.n0, rl.n1, rl.n2, 0);
             const float dx = (float)(rl.v0.x - rk.v0.x), dy = (float)(rl.v0.y - rk.v0.y);
@@ -882,7 +948,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (KER != NLFEM_KERNEL_PERIDYNAMIC
                         upos[a * 3 + b] = (int)(Q.up_start[min(kn[a], ln[b])] +
                                                 Q.klr[(int64_t)(a * 3 + b) * Q.npairs + pi]);
             }
-            float kk[6][NC], kl[9][NC], ll[6][NC];
+            float kl[9][NC], ll[6][NC];
 #pragma unroll
             for (int i = 0; i < 6; ++i)
 #pragma unroll
@@ -909,6 +975,7 @@ __global__ void __launch_bounds__(FAST_THREADS, (KER != NLFEM_KERNEL_PERIDYNAMIC
             }
             accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, upos, kk, kl, ll, vmax, k, l);
         }
+        accumulate_kk<NC>(Q, pilot, sc, valid, k, kk);
     }
     if (vdst) flush_max(vdst, vmax);
 }
@@ -944,7 +1011,6 @@ FastReq make_req(Mesh& m, PairCache& pc, const Params& prm, int list) {
     q.delta64 = prm.delta;
     q.delta2_64 = prm.delta2;
     q.ball = prm.ball;
-    q.sq32 = pc.sq32;
     q.geo64 = prm.geo64;
     q.nmat = prm.nmat;
     q.mat = prm.mat;
@@ -952,7 +1018,6 @@ FastReq make_req(Mesh& m, PairCache& pc, const Params& prm, int list) {
     q.ntab = prm.ntab;
     q.tinv = (float)prm.tinv;
     q.tab = prm.tab32;
-    q.npairs_all = pc.npairs;
     q.up_start = pc.up_start.p;
     q.epos = pc.epos.p;
     q.scale_p = nullptr;
@@ -972,19 +1037,8 @@ void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st)
     const FastReq q = make_req(m, pc, prm, 1);
     DBuf<int> key;
     key.alloc(n, st);
-    DBuf<unsigned long long> ties;
-    ties.alloc(1, st);
-    ties.zero(st);
-    k_cut_tris<<<nblk(n, 256), 256, 0, st>>>(r, q, key.p, ties.p);
+    k_cut_tris<<<nblk(n, 256), 256, 0, st>>>(r, q, key.p);
     NLFEM_LAUNCH_CHECK();
-    if (prm.ball == NLFEM_BALL_INFINITY) {
-        // when more than a quarter of the cut outer points have a vertex on a side of the square
-        // (grids aligned with the square), the FP32 passes mostly end undecided: skip them
-        unsigned long long h = 0;
-        NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, ties.p, sizeof h, cudaMemcpyDeviceToHost, st));
-        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
-        pc.sq32 = (double)h <= 0.25 * (double)n * prm.ro.n;
-    }
     k_window_key<<<nblk(n, 256), 256, 0, st>>>(key.p, n, WBITS);
     NLFEM_LAUNCH_CHECK();
     const int64_t nwin = (n + W - 1) / W;
@@ -1140,7 +1194,7 @@ std::shared_ptr<FusedLaunch> make_fused(const std::vector<BulkItem>& items, int 
         const BulkItem& it = items[i];
         FastReq q = make_req(*it.m, *it.pc, it.prm, list);
         q.acc = it.b.acc;
-        q.kkll = it.b.kkll;
+        q.llrec = it.b.llrec;
         q.scale_p = it.b.scale_p;
         q.maxabs = it.b.maxabs;
         reqs.push_back(q);
@@ -1170,7 +1224,7 @@ void launch_trunc_fast(Mesh& m, PairCache& pc, const Params& prm, const BulkAcc&
     for (int list = 0; list < 2; ++list) {
         q[list] = make_req(m, pc, prm, list);
         q[list].acc = b.acc;
-        q[list].kkll = b.kkll;
+        q[list].llrec = b.llrec;
         q[list].scale_p = b.scale_p;
         q[list].maxabs = b.maxabs;
     }

@@ -5,9 +5,10 @@
   singular rule: in FP64 the bulk result then equals the oracle up to the fixed-point
   rounding (about 1e-12 of the largest contribution), in FP32 it carries the FP32 rounding
   of the transform points and sums.
-- Cut geometry (Defs. 2.1, 2.2): FP32 positions with decisions equal to the FP64 ones by
-  default, every cut outer point cut in FP64 on request. Both stay within the 1e-5 bar, and
-  their difference is the geometry's FP32 contribution.
+- Cut geometry (Defs. 2.1, 2.2): FP32 decisions and positions by default, every cut outer
+  point cut in FP64 on request. Both stay within the 1e-5 bar, and their difference is the
+  geometry's FP32 contribution; structured grids with delta a multiple of h put vertices on
+  the circle (ties) and are covered too.
 - The FP64 path ignores both settings.
 """
 import numpy as np
@@ -61,19 +62,29 @@ def test_singular_rule_precision_in_the_full_problem():
     assert e["fp64"] <= e["fp32"] * 1.05, e
 
 
-@pytest.mark.parametrize("kw", [
-    dict(kernel="constant", delta=0.1, ball="nocaps"),
-    dict(kernel="fractional", s=0.5, delta=0.1, ball="approxcaps", quad_outer=16, quad_inner=16),
-    dict(kernel="peridynamic", delta=0.12, ball="nocaps"),
-    dict(kernel="constant", delta=0.1, ball="infinity"),
-])
-def test_geometry_precision(kw):
-    m = meshes.jittered_delaunay(-0.1, 1.1, 24, 0.03, seed=2207039213)
+JIT = ("jittered", lambda: meshes.jittered_delaunay(-0.1, 1.1, 24, 0.03, seed=2207039213))
+# structured grids with delta a multiple of h: vertices lie exactly on the circle or on a side
+# of the square for the outer points at vertices (ties)
+TIES = ("structured_ties", lambda: meshes.structured(-0.2, 1.2, 28))
+
+
+@pytest.mark.parametrize("mesh,kw", [
+    (JIT, dict(kernel="constant", delta=0.1, ball="nocaps")),
+    (JIT, dict(kernel="fractional", s=0.5, delta=0.1, ball="approxcaps", quad_outer=16, quad_inner=16)),
+    (JIT, dict(kernel="peridynamic", delta=0.12, ball="nocaps")),
+    (JIT, dict(kernel="constant", delta=0.1, ball="infinity")),
+    (TIES, dict(kernel="constant", delta=0.25, ball="nocaps")),
+    (TIES, dict(kernel="constant", delta=0.2, ball="approxcaps")),
+    (TIES, dict(kernel="peridynamic", delta=0.2, ball="nocaps")),
+    (TIES, dict(kernel="constant", delta=0.1, ball="infinity")),
+], ids=lambda v: v[0] if isinstance(v, tuple) else "-".join(str(x) for x in v.values()))
+def test_geometry_precision(mesh, kw):
+    m = mesh[1]()
     ndof = 2 if kw["kernel"] == "peridynamic" else 1
     ref = oracle.assemble(m, **kw)
     mesh = Mesh.from_synth(m, ndof)
     out = {}
-    for gp in ("exact32", "fp64"):
+    for gp in ("fp32", "fp64"):
         S = assemble(mesh, precision="fp32_bulk", geometry_precision=gp, **kw)
         rp, col, val = vals(S)
         assert np.array_equal(rp, ref.row_ptr) and np.array_equal(col, ref.col)
@@ -82,7 +93,7 @@ def test_geometry_precision(kw):
         # the result is the same bits in every run whatever the setting
         _, _, again = vals(assemble(mesh, precision="fp32_bulk", geometry_precision=gp, **kw))
         assert np.array_equal(again, val)
-    d = rel(out["exact32"], out["fp64"])
+    d = rel(out["fp32"], out["fp64"])
     assert 0.0 < d <= 1e-6, d  # the switch changes the positions, by FP32 rounding only
 
 
