@@ -89,13 +89,13 @@ struct Inner {
     float g[NC], h[3][NC], m[6][NC];
 };
 
-// the inner rule on triangle (a, b, c): positions relative to x_p, barycentric (b1, b2) w.r.t. E_l
+// the inner rule on triangle (a, b, c) of area dT / 2: positions relative to x_p (read by kernels
+// other than the constant one), barycentric (b1, b2) w.r.t. E_l
 template <int KER, int NQI, int NC>
-__device__ __forceinline__ void tri_quad(const FastRule& R, const FastReq& Q, Inner<NC>& I, float ax, float ay,
-                                         float a1, float a2,
+__device__ __forceinline__ void tri_quad(const FastRule& R, const FastReq& Q, Inner<NC>& I, float dT, float ax,
+                                         float ay, float a1, float a2,
                                          float bx, float by, float b1, float b2, float cx, float cy, float c1,
                                          float c2) {
-    const float dT = fabsf((bx - ax) * (cy - ay) - (by - ay) * (cx - ax));
     // the basis functions sum to one (Q0 = 1 - Q1 - Q2), so per point only the sums of w,
     // w Q1, w Q2, w Q1^2, w Q1 Q2 and w Q2^2 are formed; h0 and the m entries with Q0 follow
     // from them per triangle (the same quadrature sums, rearranged)
@@ -288,17 +288,18 @@ __device__ __forceinline__ void accumulate_kk(const FastReq& Q, bool pilot, floa
                 for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
                 v[e][c] = x;
             }
-        if (lane == src) {
-            const int4 ek = *reinterpret_cast<const int4*>(Q.epos + (int64_t)kx * 8);
-            const int2 ek2 = *reinterpret_cast<const int2*>(Q.epos + (int64_t)kx * 8 + 4);
-            const int kpos[6] = {ek.x, ek.y, ek.z, ek.w, ek2.x, ek2.y};
+        // every lane holds the sums: lane e NC + c converts and adds value (e, c), so the 6 NC
+        // float-to-int64 conversions (a 1/64-rate pipe) take one warp instruction
+        float mv = 0.f;
 #pragma unroll
-            for (int e = 0; e < 6; ++e)
+        for (int e = 0; e < 6; ++e)
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const long long q = __float2ll_rn(v[e][c] * sc);
-                    if (q) atomicAdd(Q.acc + (int64_t)kpos[e] * NC + c, (unsigned long long)q);
-                }
+            for (int c = 0; c < NC; ++c)
+                if (lane == e * NC + c) mv = v[e][c];
+        if (lane < 6 * NC) {
+            const int e = lane / NC, c = lane - e * NC;
+            const long long q = __float2ll_rn(mv * sc);
+            if (q) atomicAdd(Q.acc + (int64_t)Q.epos[(int64_t)kx * 8 + e] * NC + c, (unsigned long long)q);
         }
     }
 }
@@ -416,8 +417,14 @@ __device__ __forceinline__ bool decide_flat(const float Rx[3], const float Ry[3]
     return ok;
 }
 
-// canonical FP64 clip of one outer point (near ties), written relative to x_p; kept out of
-// line so that its registers do not weigh on the common path
+// Polygon points are stored as barycentric coordinates (b1, b2) of E_l (b0 = 1 - b1 - b2): the
+// drain needs them for the basis values, the sub-triangle's area is |det E_l| times their own
+// area, and positions relative to x_p (kernels other than the constant one) follow with two
+// FMAs per coordinate.
+
+// canonical FP64 clip of one outer point (near ties); the canonical routine carries the
+// barycentric coordinates of its points in FP64, rounded once here. Out of line, so that its
+// registers do not weigh on the common path.
 __device__ __noinline__ int clip_canonical(const double2* __restrict__ X, int4 tk, int4 tl, double o0, double o1,
                                            double o2, double delta, double delta2, bool caps, float2* dst,
                                            int maxp) {
@@ -428,18 +435,18 @@ __device__ __noinline__ int clip_canonical(const double2* __restrict__ X, int4 t
     bool full;
     int n = nl_clip(Vl, xp, delta, delta2, caps, poly, full);
     if (full) {
-        for (int m = 0; m < 3; ++m)
-            dst[m * FAST_THREADS] = make_float2((float)(Vl[m].x - xp.x), (float)(Vl[m].y - xp.y));
+        dst[0] = make_float2(0.f, 0.f);
+        dst[FAST_THREADS] = make_float2(1.f, 0.f);
+        dst[2 * FAST_THREADS] = make_float2(0.f, 1.f);
         return 3;
     }
     n = min(n, maxp);
-    for (int m = 0; m < n; ++m)
-        dst[m * FAST_THREADS] = make_float2((float)(poly[m].x - xp.x), (float)(poly[m].y - xp.y));
+    for (int m = 0; m < n; ++m) dst[m * FAST_THREADS] = make_float2((float)poly[m].b1, (float)poly[m].b2);
     return n;
 }
 
-// Infinity ball: the canonical FP64 cut of one outer point for every lane (no FP32 decision
-// path), written relative to x_p as FP32 points
+// Infinity ball: the canonical FP64 cut of one outer point, its points mapped to barycentric
+// coordinates of E_l in FP64 and rounded once
 __device__ __noinline__ int clip_square_f32(const double2* __restrict__ X, int4 tk, int4 tl, double o0, double o1,
                                             double o2, double delta, float2* dst) {
     const double2 Vk[3] = {X[tk.x], X[tk.y], X[tk.z]};
@@ -448,7 +455,13 @@ __device__ __noinline__ int clip_square_f32(const double2* __restrict__ X, int4 
     double2 rel[NLFEM_MAXSQ];
     bool full;
     const int n = nl_clip_square_rel(Vl, xp, delta, rel, full);
-    for (int m = 0; m < n && m < 7; ++m) dst[m * FAST_THREADS] = make_float2((float)rel[m].x, (float)rel[m].y);
+    const double e1x = Vl[1].x - Vl[0].x, e1y = Vl[1].y - Vl[0].y, e2x = Vl[2].x - Vl[0].x, e2y = Vl[2].y - Vl[0].y;
+    const double ij = 1.0 / (e1x * e2y - e1y * e2x);
+    const double ox = xp.x - Vl[0].x, oy = xp.y - Vl[0].y;  // x_p - v0_l
+    for (int m = 0; m < n && m < 7; ++m) {
+        const double px = rel[m].x + ox, py = rel[m].y + oy;
+        dst[m * FAST_THREADS] = make_float2((float)((px * e2y - py * e2x) * ij), (float)((e1x * py - e1y * px) * ij));
+    }
     return n < 7 ? n : 7;
 }
 
@@ -509,8 +522,10 @@ __device__ __forceinline__ int sh_pass32(const float* ix, const float* iy, const
 // exact = false: the FP32 passes alone (a decision within rounding of a side may differ from the
 // FP64 one, which moves that polygon edge by a rounding-sized sliver); -1 only when more than 7
 // points come out
+// (the polygon is written as barycentric coordinates of E_l: El its edge vectors, idet the
+// inverse of their determinant; Rx[0], Ry[0] is v0_l relative to x_p)
 __device__ __noinline__ int clip_square_fast(const float Rx[3], const float Ry[3], float eps, float d, float2* dst,
-                                             bool exact) {
+                                             bool exact, float4 El, float idet) {
     float Ax[8], Ay[8], Ae[8], Bx[8], By[8], Be[8];
     for (int v = 0; v < 3; ++v) {
         Ax[v] = Rx[v];
@@ -529,39 +544,134 @@ __device__ __noinline__ int clip_square_fast(const float Rx[3], const float Ry[3
             if (n > 1 && fabsf(Ax[i] - Ax[j]) + fabsf(Ay[i] - Ay[j]) <= 2.f * (Ae[i] + Ae[j])) return -1;
         }
     if (n < 3) return 0;
-    for (int i = 0; i < n; ++i) dst[i * FAST_THREADS] = make_float2(Ax[i], Ay[i]);
+    for (int i = 0; i < n; ++i) {
+        const float rx = Ax[i] - Rx[0], ry = Ay[i] - Ry[0];
+        dst[i * FAST_THREADS] = make_float2((rx * El.w - ry * El.z) * idet, (El.x * ry - El.y * rx) * idet);
+    }
     return n;
 }
 
-// Cut pairs: the outer points are processed in chunks of CHUNK. Phase A sets up every
-// outer point of the chunk in lockstep across the warp (decisions, polygon points relative
-// to x_p into shared memory; 4 bits per outer point record the number of points). Phase B
-// drains the fan triangles: each iteration integrates one triangle per lane, walking
-// through the lane's outer points in order, and applies that triangle's inner sums with its
-// outer point's factors. Barycentric coordinates are recomputed from positions with E_l's
-// inverse map. The cut list is ordered by fan-triangle count (order_cut_pairs), so the
-// lanes of a warp drain about the same number of triangles.
-static constexpr int CHUNK = 8;
+// Cut pairs: the outer points are processed in chunks of at most CHUNK (8; 7 with caps, whose
+// polygons need 9 slots per outer point). Phase A1 decides, in lockstep across the warp, every
+// outer point of the chunk whose inner element is whole (every vertex inside the ball) or empty
+// (every vertex outside and, for the Euclidean ball, the point of each edge closest to x_p
+// outside that edge: then no edge reaches the ball), each test taken only beyond its FP32 error
+// bound. The other outer points are cut, not all lanes have one, so they go to a per-warp job
+// list: phase A2 cuts them one per lane and round, writing the polygon into the owner's slots,
+// and jobs whose decisions are too close to call go to a second list that phase A3 cuts in FP64
+// with the canonical routine (with geo64 every cut outer point does). Polygon points are
+// barycentric coordinates of E_l; 4 bits per outer point record their number. Phase B drains
+// the fan triangles: each iteration integrates one triangle per lane, walking through the lane's
+// outer points in order, and applies that triangle's inner sums with its outer point's factors.
+// The cut list is ordered by fan-triangle count (order_cut_pairs), so the lanes of a warp drain
+// about the same number of triangles.
+template <int BALL>
+struct CutShape {
+    static constexpr bool CAPS = BALL == NLFEM_BALL_APPROXCAPS;
+    static constexpr bool SQUARE = BALL == NLFEM_BALL_INFINITY;
+    // polygon points: 6 raw plus up to 3 cap centres; a triangle cut by a square: at most 7
+    static constexpr int MAXP = CAPS ? 9 : (SQUARE ? 7 : 6);
+    // With caps the polygons need 9 slots per outer point, and the job lists' shared memory would
+    // cost the block its third slot per SM: caps cut every outer point in lockstep (chunks of 8),
+    // the others use the job lists (chunks of 7, the 7-point rule in one chunk, four blocks per SM
+    // without caps)
+    static constexpr bool JOBS = !CAPS;
+    static constexpr int CHUNK = CAPS ? 8 : 7;
+};
+
+// Phase A2 for the Euclidean ball: the cut of one outer point from its relative coordinates,
+// written as barycentric coordinates to dst (stride FAST_THREADS). Returns the number of points,
+// or -1 if a decision is too close to call (the canonical FP64 cut then takes it).
+// whole: every vertex inside the ball (valid when the result is not -1)
+template <bool CAPS>
+__device__ __forceinline__ int cut_euclid(const float Rx[3], const float Ry[3], const EdgesF& Ed, float4 El,
+                                          float idet, float eps, float floor2, float d2, float delta, float2* dst,
+                                          bool& whole) {
+    constexpr int MAXP = CAPS ? 9 : 6;
+    float Cc[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - d2;
+    GeoF G;
+    bool ok = decide_flat(Rx, Ry, Cc, Ed, eps, floor2, d2, G);
+    whole = G.in[0] && G.in[1] && G.in[2];
+    // barycentric coordinates of the vertices: v0 (0, 0), v1 (1, 0), v2 (0, 1); edge e runs from
+    // vertex e to vertex e + 1
+    const float vb1[3] = {0.f, 1.f, 0.f}, vb2[3] = {0.f, 0.f, 1.f};
+    int n = 0;
+    auto put = [&](int slot, float b1, float b2) { dst[min(slot, MAXP - 1) * FAST_THREADS] = make_float2(b1, b2); };
+    if (!CAPS) {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int b = (e + 1) % 3;
+            const float d1 = vb1[b] - vb1[e], d2e = vb2[b] - vb2[e];
+            if (G.in[e]) put(n, vb1[e], vb2[e]);
+            n += G.in[e];
+            if (G.nc[e] >= 1) put(n, fmaf(G.ta[e], d1, vb1[e]), fmaf(G.ta[e], d2e, vb2[e]));
+            n += G.nc[e] >= 1;
+            if (G.nc[e] >= 2) put(n, fmaf(G.tb[e], d1, vb1[e]), fmaf(G.tb[e], d2e, vb2[e]));
+            n += G.nc[e] >= 2;
+        }
+    } else if (ok) {
+        // with caps: a cap centre between consecutive points not joined along an edge; the cap
+        // logic runs on positions relative to x_p, the cap centre's barycentric coordinates come
+        // from E_l's inverse map
+        int nraw = 0, fe = 0, fv = 0, le = 0;
+        float fx = 0, fy = 0, lx = 0, ly = 0;
+        auto cap = [&](float px, float py, float qx, float qy) {
+            const float cx = qx - px, cy = qy - py;
+            const float len = sqrtf(cx * cx + cy * cy);
+            ok &= len > 1e-6f * delta;
+            const float sc = __fdividef(delta, len);
+            const float rx = sc * cy - Rx[0], ry = -sc * cx - Ry[0];  // cap centre - v0_l
+            put(n, (rx * El.w - ry * El.z) * idet, (El.x * ry - El.y * rx) * idet);
+            ++n;
+        };
+        auto raw = [&](float x, float y, float b1, float b2, int e, int v) {
+            if (nraw >= 1 && !((e == le) || (v && e == (le + 1) % 3))) cap(lx, ly, x, y);
+            put(n, b1, b2);
+            ++n;
+            if (nraw == 0) { fx = x; fy = y; fe = e; fv = v; }
+            lx = x; ly = y; le = e;
+            ++nraw;
+        };
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int b = (e + 1) % 3;
+            const float ux = Ed.ux[e], uy = Ed.uy[e];
+            const float d1 = vb1[b] - vb1[e], d2e = vb2[b] - vb2[e];
+            if (G.in[e]) raw(Rx[e], Ry[e], vb1[e], vb2[e], e, 1);
+            if (G.nc[e] >= 1)
+                raw(fmaf(G.ta[e], ux, Rx[e]), fmaf(G.ta[e], uy, Ry[e]), fmaf(G.ta[e], d1, vb1[e]),
+                    fmaf(G.ta[e], d2e, vb2[e]), e, 0);
+            if (G.nc[e] >= 2)
+                raw(fmaf(G.tb[e], ux, Rx[e]), fmaf(G.tb[e], uy, Ry[e]), fmaf(G.tb[e], d1, vb1[e]),
+                    fmaf(G.tb[e], d2e, vb2[e]), e, 0);
+        }
+        if (!(G.in[0] && G.in[1] && G.in[2]) && nraw >= 2 && !(fv && fe == (le + 1) % 3)) cap(lx, ly, fx, fy);
+    }
+    if (!ok) return -1;
+    return n < 3 ? 0 : n;
+}
 
 template <int KER, int NQI, int BALL, bool BATCH>
 __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_constant__ FastRule R,
                                                            const __grid_constant__ FastLaunch L) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
-    constexpr bool CAPS = BALL == NLFEM_BALL_APPROXCAPS;
-    constexpr bool SQUARE = BALL == NLFEM_BALL_INFINITY;
-    // polygon points: 6 raw plus up to 3 cap centres; a triangle cut by a square: at most 7
-    constexpr int MAXP = CAPS ? 9 : (SQUARE ? 7 : 6);
-    extern __shared__ float2 s_pts[];   // [CHUNK][MAXP][FAST_THREADS]
+    constexpr bool CAPS = CutShape<BALL>::CAPS;
+    constexpr bool SQUARE = CutShape<BALL>::SQUARE;
+    constexpr int MAXP = CutShape<BALL>::MAXP;
+    constexpr int CHUNK = CutShape<BALL>::CHUNK;
+    constexpr bool JOBS = CutShape<BALL>::JOBS;
+    extern __shared__ float2 s_pts[];   // [CHUNK][MAXP][FAST_THREADS] barycentric coordinates
     float2* my = s_pts + threadIdx.x;
-    auto put = [&](int q, int slot, float x, float y) { my[(q * MAXP + slot) * FAST_THREADS] = make_float2(x, y); };
     __shared__ FastReq sq[BATCH ? FAST_WARPS : 1];
-    // infinity ball: per-thread element triples and per-warp job lists of the canonical cuts
-    // the canonical FP64 cuts of a chunk go to a per-warp job list (nocaps and the infinity
-    // ball); with caps they run in place, which keeps this block's shared memory at three blocks
-    // per SM (the caps polygons need 9 slots per outer point)
-    constexpr bool JOBS = !CAPS;
-    __shared__ int s_k[JOBS ? FAST_THREADS : 1], s_l[JOBS ? FAST_THREADS : 1];
-    __shared__ unsigned char s_job[JOBS ? FAST_WARPS * 32 * CHUNK : 1];
+    // per lane: its pair's elements and v0_l - v0_k with the error bound of the relative
+    // coordinates (for the jobs other lanes run on its behalf); per warp: the job lists of the
+    // FP32 cuts and of the canonical cuts (owner lane << 3 | outer point), the jobs' point counts
+    constexpr int NJ = JOBS ? FAST_THREADS : 1;
+    __shared__ int s_k[NJ], s_l[NJ];
+    __shared__ float4 s_pd[NJ], s_ek[NJ], s_el[NJ];
+    __shared__ unsigned char s_job[JOBS ? FAST_WARPS * 32 * CHUNK : 1], s_job64[JOBS ? FAST_WARPS * 32 * CHUNK : 1];
     __shared__ unsigned char s_cnt[JOBS ? FAST_THREADS * CHUNK : 1];
     __shared__ float4 s_orule[16];  // outer rule (l0, l1, l2, w)
     for (int i = threadIdx.x; i < 16; i += blockDim.x)
@@ -569,7 +679,8 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
     __syncthreads();
     const int nqo = R.nqo;
     const bool pilot = L.pilot > 0;
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wbase = warp * 32;
+    const unsigned lanes_below = (1u << lane) - 1u;
     int cur = -1;
     float vmax = 0.f;            // largest |value| of this warp's pairs of request cur
     unsigned int* vdst = nullptr;
@@ -583,7 +694,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
         const FastReq& Q = BATCH ? sq[warp] : L.one;
         vdst = Q.maxabs;
         const float sc = pilot ? 1.f : *Q.scale_p;
-        const int64_t pi = (int64_t)tile.y + (threadIdx.x & 31);
+        const int64_t pi = (int64_t)tile.y + lane;
         const int64_t nlist = pilot ? (Q.npairs + L.pilot - 1) / L.pilot : Q.npairs;
         const bool valid = pi < nlist;
         const int64_t p = valid ? (int64_t)Q.ids[pilot ? pi * L.pilot : pi] : 0;
@@ -607,14 +718,25 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
             El = rl.E;
             dk = rk.det;
         }
-        const float idet = 1.f / (El.x * El.w - El.y * El.z);
+        const float dl = fabsf(El.x * El.w - El.y * El.z);  // |det E_l|: sub-triangle area factor
         const float W0x = dx, W0y = dy;
         const float W1x = dx + El.x, W1y = dy + El.y, W2x = dx + El.z, W2y = dy + El.w;
         const float span = fabsf(dx) + fabsf(dy) + fabsf(Ek.x) + fabsf(Ek.y) + fabsf(Ek.z) + fabsf(Ek.w) +
                            fabsf(El.x) + fabsf(El.y) + fabsf(El.z) + fabsf(El.w);
         const float eps = 4.8e-7f * span;    // bound on the FP32 error of the relative coordinates
         const float floor2 = 1e-5f * Q.d2;   // floor of the vertex margin (see nl_decide32)
-        const EdgesF Ed = edges_of(El);
+        if (JOBS) {
+            s_k[threadIdx.x] = k;
+            s_l[threadIdx.x] = l;
+            s_pd[threadIdx.x] = make_float4(W0x, W0y, eps, 0.f);
+            s_ek[threadIdx.x] = Ek;
+            s_el[threadIdx.x] = El;
+        }
+        const EdgesF Ed = edges_of(El);  // caps: the lockstep cut's edge data
+        // Euclidean ball: squared edge lengths of E_l (the closest-point test of phase A1)
+        const float A0 = El.x * El.x + El.y * El.y;
+        const float A1 = (El.z - El.x) * (El.z - El.x) + (El.w - El.y) * (El.w - El.y);
+        const float A2 = El.z * El.z + El.w * El.w;
 
         float kk[6][NC], kl[9][NC], ll[6][NC];
 #pragma unroll
@@ -629,155 +751,138 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
 #pragma unroll 1
         for (int qb = 0; qb < nqo; qb += CHUNK) {
             const int qn = min(CHUNK, nqo - qb);
-            // ---- phase A: polygons of outer points qb .. qb + qn - 1, in lockstep
+            // ---- phase A1: whole and empty outer points in lockstep, the others become jobs
             unsigned long long counts = 0;  // 4 bits per outer point: number of polygon points
-            unsigned need = 0;              // outer points left to the canonical FP64 cut
+            unsigned need = 0;              // outer points to cut (jobs)
 #pragma unroll 1
             for (int q = 0; q < qn; ++q) {
                 const int q0 = qb + q;
-                if (SQUARE) {
-                    // FP32 vertex tests decide the whole element (every vertex inside the square)
-                    // and the empty cut (every vertex beyond one side); the rest is cut by the FP32
-                    // Sutherland-Hodgman passes or by the canonical FP64 cut.
-                    // The constant kernel takes the FP32 passes without margins: its inner integrand
-                    // is a polynomial of degree 2 that the inner rule integrates exactly on any
-                    // triangle, so only the region matters, and the square cut moves it continuously
-                    // (a decision within rounding of a side shifts a polygon edge by a sliver).
-                    // Other kernels depend on the fan triangulation, so their decisions must equal
-                    // the FP64 ones: margins on every test, a vertex near a side or an undecided pass
-                    // goes to the canonical cut. With geo64 every open cut is canonical.
-                    constexpr bool RELAX = KER == NLFEM_KERNEL_CONSTANT;
+                const float Xx = R.ol[q0][1] * Ek.x + R.ol[q0][2] * Ek.z;  // x_p - v0_k
+                const float Xy = R.ol[q0][1] * Ek.y + R.ol[q0][2] * Ek.w;
+                const float Rx[3] = {W0x - Xx, W1x - Xx, W2x - Xx}, Ry[3] = {W0y - Xy, W1y - Xy, W2y - Xy};
+                if (!JOBS) {
+                    // caps: the cut of every outer point in lockstep, the canonical FP64 cut in place
+                    // for an undecided one (and with geo64 for every cut one)
                     int n = 0;
                     if (valid) {
-                        const float Xx = R.ol[q0][1] * Ek.x + R.ol[q0][2] * Ek.z;
-                        const float Xy = R.ol[q0][1] * Ek.y + R.ol[q0][2] * Ek.w;
-                        const float Rx[3] = {W0x - Xx, W1x - Xx, W2x - Xx}, Ry[3] = {W0y - Xy, W1y - Xy, W2y - Xy};
-                        const bool exact = !RELAX || Q.geo64;
-                        const float mg = exact ? eps + 1e-6f * Q.delta : 0.f;
-                        const float lo = Q.delta - mg, hi = Q.delta + mg;
-                        bool allin = true, tie = false;
-                        int oxp = 0, oxm = 0, oyp = 0, oym = 0;
-#pragma unroll
-                        for (int m = 0; m < 3; ++m) {
-                            allin &= fabsf(Rx[m]) <= lo && fabsf(Ry[m]) <= lo;
-                            oxp += Rx[m] > hi;
-                            oxm += Rx[m] < -hi;
-                            oyp += Ry[m] > hi;
-                            oym += Ry[m] < -hi;
-                            tie |= (fabsf(Rx[m]) > lo && fabsf(Rx[m]) <= hi) || (fabsf(Ry[m]) > lo && fabsf(Ry[m]) <= hi);
-                        }
-                        if (allin) {
-#pragma unroll
-                            for (int m = 0; m < 3; ++m) put(q, m, Rx[m], Ry[m]);
-                            n = 3;
-                        } else if (oxp < 3 && oxm < 3 && oyp < 3 && oym < 3) {
-                            n = (Q.geo64 || (exact && tie))
-                                    ? -1
-                                    : clip_square_fast(Rx, Ry, eps, Q.delta, my + q * MAXP * FAST_THREADS, exact);
-                            if (n < 0) {
-                                n = 0;
-                                need |= 1u << q;
-                            }
-                        }
+                        const float idet = 1.f / (El.x * El.w - El.y * El.z);
+                        bool wh = false;
+                        n = cut_euclid<CAPS>(Rx, Ry, Ed, El, idet, eps, floor2, Q.d2, Q.delta,
+                                             my + q * MAXP * FAST_THREADS, wh);
+                        if (n < 0 || (Q.geo64 && n >= 3 && !wh))
+                            n = clip_canonical(Q.X, tk, tl, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2], Q.delta64,
+                                               Q.delta2_64, CAPS, my + q * MAXP * FAST_THREADS, MAXP);
                     }
-                    counts |= (unsigned long long)n << (4 * q);
+                    counts |= (unsigned long long)(n < 3 ? 0 : n) << (4 * q);
                     continue;
                 }
-                const float l1o = R.ol[q0][1], l2o = R.ol[q0][2];
-                const float Xx = l1o * Ek.x + l2o * Ek.z;  // x_p - v0_k
-                const float Xy = l1o * Ek.y + l2o * Ek.w;
-                const float Rx[3] = {W0x - Xx, W1x - Xx, W2x - Xx}, Ry[3] = {W0y - Xy, W1y - Xy, W2y - Xy};
-                float Cc[3];
+                bool whole, empty;
+                if (SQUARE) {
+                    // vertex tests against the square's sides; the constant kernel decides in FP32
+                    // without margins (its result depends on the cut region only, which the
+                    // square cut moves continuously), the others only beyond the error bound
+                    const bool exact = KER != NLFEM_KERNEL_CONSTANT || Q.geo64;
+                    const float mg = exact ? eps + 1e-6f * Q.delta : 0.f;
+                    const float lo = Q.delta - mg, hi = Q.delta + mg;
+                    bool allin = true;
+                    int oxp = 0, oxm = 0, oyp = 0, oym = 0;
 #pragma unroll
-                for (int m = 0; m < 3; ++m) Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - Q.d2;
-                // FP32 decisions, each taken only beyond its error bound (ok = every decision of
-                // this outer point equals the canonical FP64 one)
-                GeoF G;
-                bool ok = decide_flat<true>(Rx, Ry, Cc, Ed, eps, floor2, Q.d2, G, !valid);
+                    for (int m = 0; m < 3; ++m) {
+                        allin &= fabsf(Rx[m]) <= lo && fabsf(Ry[m]) <= lo;
+                        oxp += Rx[m] > hi;
+                        oxm += Rx[m] < -hi;
+                        oyp += Ry[m] > hi;
+                        oym += Ry[m] < -hi;
+                    }
+                    whole = allin;
+                    empty = oxp == 3 || oxm == 3 || oyp == 3 || oym == 3;
+                } else {
+                    // every vertex decided inside: the whole element; every vertex decided outside
+                    // and, on every edge, the point closest to x_p (parameter -B/A) outside the
+                    // edge: the distance along each edge grows from its outside ends, so no edge
+                    // reaches the ball (a sign of B within rounding cannot matter: the vertex margin
+                    // exceeds B^2 / A there)
+                    bool okv = true, in0, in1, in2;
+                    float Cc[3];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        Cc[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - Q.d2;
+                        okv &= fabsf(Cc[m]) > floor2 + 2.f * (fabsf(Rx[m]) + fabsf(Ry[m])) * eps;
+                    }
+                    in0 = Cc[0] < 0.f;
+                    in1 = Cc[1] < 0.f;
+                    in2 = Cc[2] < 0.f;
+                    const float B0 = Rx[0] * El.x + Ry[0] * El.y;
+                    const float B1 = Rx[1] * (El.z - El.x) + Ry[1] * (El.w - El.y);
+                    const float B2 = -(Rx[2] * El.z + Ry[2] * El.w);
+                    const bool apart = !(B0 < 0.f && -B0 < A0) && !(B1 < 0.f && -B1 < A1) && !(B2 < 0.f && -B2 < A2);
+                    whole = okv && in0 && in1 && in2;
+                    empty = okv && !in0 && !in1 && !in2 && apart;
+                }
                 int n = 0;
-                if (!CAPS) {
-                    // vertices inside and crossings in boundary order; predicated stores
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const float ux = Ed.ux[e], uy = Ed.uy[e];
-                        if (G.in[e]) put(q, n, Rx[e], Ry[e]);
-                        n += G.in[e];
-                        if (G.nc[e] >= 1) put(q, n, fmaf(G.ta[e], ux, Rx[e]), fmaf(G.ta[e], uy, Ry[e]));
-                        n += G.nc[e] >= 1;
-                        if (G.nc[e] >= 2) put(q, n, fmaf(G.tb[e], ux, Rx[e]), fmaf(G.tb[e], uy, Ry[e]));
-                        n += G.nc[e] >= 2;
-                    }
-                } else if (ok) {
-                    // with caps: a cap centre between consecutive points not joined along an edge
-                    int nraw = 0, fe = 0, fv = 0, le = 0;
-                    float fx = 0, fy = 0, lx = 0, ly = 0;
-                    auto cap = [&](float px, float py, float qx, float qy) {
-                        const float cx = qx - px, cy = qy - py;
-                        const float len = sqrtf(cx * cx + cy * cy);
-                        ok &= len > 1e-6f * Q.delta;
-                        const float sc = __fdividef(Q.delta, len);
-                        put(q, min(n, MAXP - 1), sc * cy, -sc * cx);
-                        ++n;
-                    };
-                    auto raw = [&](float x, float y, int e, int v) {
-                        if (nraw >= 1 && !((e == le) || (v && e == (le + 1) % 3))) cap(lx, ly, x, y);
-                        put(q, min(n, MAXP - 1), x, y);
-                        ++n;
-                        if (nraw == 0) { fx = x; fy = y; fe = e; fv = v; }
-                        lx = x; ly = y; le = e;
-                        ++nraw;
-                    };
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const float ux = Ed.ux[e], uy = Ed.uy[e];
-                        if (G.in[e]) raw(Rx[e], Ry[e], e, 1);
-                        if (G.nc[e] >= 1) raw(fmaf(G.ta[e], ux, Rx[e]), fmaf(G.ta[e], uy, Ry[e]), e, 0);
-                        if (G.nc[e] >= 2) raw(fmaf(G.tb[e], ux, Rx[e]), fmaf(G.tb[e], uy, Ry[e]), e, 0);
-                    }
-                    if (!(G.in[0] && G.in[1] && G.in[2]) && nraw >= 2 && !(fv && fe == (le + 1) % 3))
-                        cap(lx, ly, fx, fy);
+                if (valid && whole) {
+                    my[(q * MAXP + 0) * FAST_THREADS] = make_float2(0.f, 0.f);
+                    my[(q * MAXP + 1) * FAST_THREADS] = make_float2(1.f, 0.f);
+                    my[(q * MAXP + 2) * FAST_THREADS] = make_float2(0.f, 1.f);
+                    n = 3;
+                } else if (valid && !empty) {
+                    need |= 1u << q;
                 }
-                // an undecided outer point (a vertex within its error bound of the circle, a near
-                // tangent edge, a degenerate cap chord), and with geo64 every outer point whose inner
-                // element is cut (its decisions equal the FP64 ones, so the others are whole or
-                // empty), takes the canonical FP64 cut below. A decision near a tie cannot be left
-                // to FP32: the polygon is discontinuous at a tangent edge (the tangent point adds a
-                // cap-sized triangle) and a root next to a tangency is only sqrt(eps) accurate.
-                const bool whole = G.in[0] && G.in[1] && G.in[2];
-                if (!valid) n = 0;
-                else if (!ok || (Q.geo64 && n >= 3 && !whole)) {
-                    if (JOBS) {
-                        n = 0;
-                        need |= 1u << q;
-                    } else {
-                        n = clip_canonical(Q.X, tk, tl, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2], Q.delta64,
-                                           Q.delta2_64, CAPS, my + q * MAXP * FAST_THREADS, MAXP);
-                    }
-                }
-                counts |= (unsigned long long)(n < 3 ? 0 : n) << (4 * q);
+                counts |= (unsigned long long)n << (4 * q);
             }
             if (JOBS && __any_sync(0xffffffffu, need != 0)) {
-                // the canonical FP64 cuts of the chunk spread over the warp's lanes (the FP64 pipe
-                // is 1/64 of the FP32 rate, so one cut per lane rather than one per outer point and
-                // warp): job j of the warp is (owner lane, outer point); its polygon goes to the
-                // owner's slots
-                const int lane = threadIdx.x & 31, wbase = warp * 32;
-                s_k[threadIdx.x] = k;
-                s_l[threadIdx.x] = l;
-                const int mine = __popc(need);
-                int incl = mine;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
+                // the jobs of the chunk, outer point by outer point and in lane order within one: job j
+                // of the warp is (owner lane, outer point). A round of 32 jobs then mostly holds distinct
+                // owners, whose polygon slots lie in distinct shared-memory banks.
+                int total = 0;
+#pragma unroll 1
+                for (int q = 0; q < qn; ++q) {
+                    const unsigned m = __ballot_sync(0xffffffffu, (need >> q) & 1u);
+                    if ((need >> q) & 1u) s_job[wbase * CHUNK + total + __popc(m & lanes_below)] =
+                        (unsigned char)((lane << 3) | q);
+                    total += __popc(m);
                 }
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                int j = incl - mine;
-                for (unsigned b = need; b; b &= b - 1) s_job[wbase * CHUNK + j++] =
-                    (unsigned char)((lane << 3) | (__ffs(b) - 1));
                 __syncwarp();
-                for (int jj = lane; jj < total; jj += 32) {
-                    const int code = s_job[wbase * CHUNK + jj];
+                // ---- phase A2: one cut per lane and round in FP32; undecided ones to the FP64 list
+                int n64 = 0;
+#pragma unroll 1
+                for (int jb = 0; jb < total; jb += 32) {
+                    const int jj = jb + lane;
+                    const bool act = jj < total;
+                    const int code = act ? s_job[wbase * CHUNK + jj] : 0;
+                    const int owner = code >> 3, q = code & 7, q0 = qb + q;
+                    int n = 0;
+                    bool und = false;
+                    if (act) {
+                        const float4 pd = s_pd[wbase + owner];
+                        const float4 Ejk = s_ek[wbase + owner], Ejl = s_el[wbase + owner];
+                        const float4 orule = s_orule[q0];
+                        const float Xx = orule.y * Ejk.x + orule.z * Ejk.z;
+                        const float Xy = orule.y * Ejk.y + orule.z * Ejk.w;
+                        const float Rx[3] = {pd.x - Xx, pd.x + Ejl.x - Xx, pd.x + Ejl.z - Xx};
+                        const float Ry[3] = {pd.y - Xy, pd.y + Ejl.y - Xy, pd.y + Ejl.w - Xy};
+                        const float ijd = 1.f / (Ejl.x * Ejl.w - Ejl.y * Ejl.z);
+                        float2* dst = s_pts + wbase + owner + q * MAXP * FAST_THREADS;
+                        if (Q.geo64) {
+                            und = true;
+                        } else if (SQUARE) {
+                            n = clip_square_fast(Rx, Ry, pd.z, Q.delta, dst, KER != NLFEM_KERNEL_CONSTANT, Ejl, ijd);
+                            und = n < 0;
+                        } else {
+                            bool wh = false;
+                            n = cut_euclid<CAPS>(Rx, Ry, edges_of(Ejl), Ejl, ijd, pd.z, floor2, Q.d2, Q.delta, dst, wh);
+                            und = n < 0;
+                        }
+                    }
+                    const unsigned um = __ballot_sync(0xffffffffu, und);
+                    if (und) s_job64[wbase * CHUNK + n64 + __popc(um & lanes_below)] = (unsigned char)code;
+                    n64 += __popc(um);
+                    if (act) s_cnt[(wbase + owner) * CHUNK + q] = (unsigned char)(und || n < 3 ? 0 : n);
+                }
+                __syncwarp();
+                // ---- phase A3: the canonical FP64 cuts, one per lane
+                for (int jj = lane; jj < n64; jj += 32) {
+                    const int code = s_job64[wbase * CHUNK + jj];
                     const int owner = code >> 3, q = code & 7, q0 = qb + q;
                     float2* dst = s_pts + wbase + owner + q * MAXP * FAST_THREADS;
                     const int4 tkj = Q.T[s_k[wbase + owner]], tlj = Q.T[s_l[wbase + owner]];
@@ -803,19 +908,28 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                     // lanes sit at different outer points here: the rule comes from shared memory
                     // (a parameter-space read at per-lane indices would serialise)
                     const float4 orule = s_orule[q0];
-                    const float l1o = orule.y, l2o = orule.z;
-                    // x_p - v0_l, for the barycentric coordinates of the points
-                    const float Bx = l1o * Ek.x + l2o * Ek.z - W0x, By = l1o * Ek.y + l2o * Ek.w - W0y;
-                    float px[3], py[3], b1[3], b2[3];
+                    float b1[3], b2[3], px[3], py[3];
                     const int slot[3] = {0, sc - 1, sc};
 #pragma unroll
                     for (int t = 0; t < 3; ++t) {
                         const float2 pt = my[(qc * MAXP + slot[t]) * FAST_THREADS];
-                        px[t] = pt.x;
-                        py[t] = pt.y;
-                        const float rx = pt.x + Bx, ry = pt.y + By;
-                        b1[t] = (rx * El.w - ry * El.z) * idet;
-                        b2[t] = (El.x * ry - El.y * rx) * idet;
+                        b1[t] = pt.x;
+                        b2[t] = pt.y;
+                    }
+                    // the triangle's area: |det E_l| times its area in barycentric coordinates
+                    const float dT = dl * fabsf((b1[1] - b1[0]) * (b2[2] - b2[0]) - (b2[1] - b2[0]) * (b1[2] - b1[0]));
+                    if (KER != NLFEM_KERNEL_CONSTANT) {
+                        // positions relative to x_p: v0_l - x_p + b1 (v1_l - v0_l) + b2 (v2_l - v0_l)
+                        const float R0x = W0x - (orule.y * Ek.x + orule.z * Ek.z);
+                        const float R0y = W0y - (orule.y * Ek.y + orule.z * Ek.w);
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) {
+                            px[t] = fmaf(b2[t], El.z, fmaf(b1[t], El.x, R0x));
+                            py[t] = fmaf(b2[t], El.w, fmaf(b1[t], El.y, R0y));
+                        }
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) px[t] = py[t] = 0.f;
                     }
                     Inner<NC> I;
 #pragma unroll
@@ -826,8 +940,8 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
 #pragma unroll
                         for (int j = 0; j < 6; ++j) I.m[j][c] = 0.f;
                     }
-                    tri_quad<KER, NQI, NC>(R, Q, I, px[0], py[0], b1[0], b2[0], px[1], py[1], b1[1], b2[1], px[2], py[2],
-                                           b1[2], b2[2]);
+                    tri_quad<KER, NQI, NC>(R, Q, I, dT, px[0], py[0], b1[0], b2[0], px[1], py[1], b1[1], b2[1], px[2],
+                                           py[2], b1[2], b2[2]);
                     outer_update<NC>(orule, dk, I, kk, kl, ll);
                     if (++sc >= (int)((counts >> (4 * qc)) & 15)) {
                         sc = 2;
@@ -969,8 +1083,10 @@ __global__ void __launch_bounds__(FAST_THREADS, (KER != NLFEM_KERNEL_PERIDYNAMIC
 #pragma unroll
                     for (int j = 0; j < 6; ++j) I.m[j][c] = 0.f;
                 }
-                tri_quad<KER, NQI, NC>(R, Q, I, dx - Xx, dy - Xy, 0.f, 0.f, dx + El.x - Xx, dy + El.y - Xy, 1.f, 0.f,
-                                       dx + El.z - Xx, dy + El.w - Xy, 0.f, 1.f);
+                const float ax = dx - Xx, ay = dy - Xy, bx = dx + El.x - Xx, by = dy + El.y - Xy;
+                const float cx = dx + El.z - Xx, cy = dy + El.w - Xy;
+                const float dT = fabsf((bx - ax) * (cy - ay) - (by - ay) * (cx - ax));
+                tri_quad<KER, NQI, NC>(R, Q, I, dT, ax, ay, 0.f, 0.f, bx, by, 1.f, 0.f, cx, cy, 0.f, 1.f);
                 outer_update<NC>(make_float4(R.ol[q0][0], R.ol[q0][1], R.ol[q0][2], R.ow[q0]), dk, I, kk, kl, ll);
             }
             accumulate_pair<NC>(Q, pilot, sc, pi, p, tk, tl, upos, kk, kl, ll, vmax, k, l);
@@ -1051,8 +1167,7 @@ void order_cut_pairs(Mesh& m, PairCache& pc, const Params& prm, cudaStream_t st)
 
 template <int BALL>
 static constexpr size_t cut_smem() {
-    return sizeof(float2) * CHUNK * FAST_THREADS *
-           (BALL == NLFEM_BALL_APPROXCAPS ? 9 : (BALL == NLFEM_BALL_INFINITY ? 7 : 6));
+    return sizeof(float2) * CutShape<BALL>::CHUNK * FAST_THREADS * CutShape<BALL>::MAXP;
 }
 
 template <int KER, int NQI, int BALL, bool BATCH>
