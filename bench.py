@@ -621,7 +621,8 @@ def main():
                    "step": "nlfem_assemble with cached pair list and pattern",
                    "l2": "working set larger than L2 (pair lists, kl ranks and per-pair ll records stream from HBM)",
                    "pairs": npairs, "nnz": info0["nnz"], "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "autotune_blocks_per_sm": {"whole_pairs": tuned[0], "cut_pairs": tuned[1]}},
+                   "autotune_shape": {"whole_pairs_blocks_per_sm": tuned[0], "cut_pairs_blocks_per_sm": tuned[1],
+                                      "cut_pairs_outer_points_per_chunk": tuned[2]}},
         "roofline": roof,
         "fp64_plain": ({"value": npairs * ws / (ms64_step * 1e-3), "ms_per_step": ms64_step,
                         "quadrature_ms": quad64_ms, "speedup_fp32_bulk_over_fp64": ms64_step / ms_step}

@@ -231,12 +231,25 @@ void nlfem_batch_destroy(nlfem_batch_t batch);
 /*
  * Autotuner of the FP32-bulk launch shape: for the kernel class of params (kernel type,
  * rules, ball) it times the whole-pair and the cut-pair kernels on mesh with every candidate
- * grid size (2 ... 64 resident blocks of 4 warps per SM; each warp takes 32-pair tiles) and
- * keeps the fastest for the rest of the process; best receives the chosen blocks per SM for
- * the whole and the cut list. The results of every assembly are the same bits whatever the
- * grid. The paper has no counterpart. Errors: INVALID_ARG, UNSUPPORTED (FP64), OOM, CUDA.
+ * grid size (2 ... 64 resident blocks of 4 warps per SM; each warp takes 32-pair tiles) and,
+ * for the cut-pair kernel, every candidate number of outer points per chunk (its full chunk,
+ * half of it, 2: the polygons of a chunk are built, then drained one fan triangle per lane),
+ * and keeps the fastest for the rest of the process. best receives [0] the blocks per SM of
+ * the whole-pair kernel, [1] those of the cut-pair kernel and [2] its outer points per chunk.
+ * The results of every assembly are the same bits whatever the shape. The paper has no
+ * counterpart. Errors: INVALID_ARG, UNSUPPORTED (FP64), OOM, CUDA.
  */
-int nlfem_autotune(nlfem_mesh_t mesh, const nlfem_params* params, void* stream, int32_t best[2]);
+int nlfem_autotune(nlfem_mesh_t mesh, const nlfem_params* params, void* stream, int32_t best[3]);
+
+/*
+ * Set the FP32-bulk launch shape of the kernel class of params without timing (for example a
+ * shape nlfem_autotune chose in an earlier process): shape[0] blocks per SM of the whole-pair
+ * kernel (1 ... 64), shape[1] of the cut-pair kernel (1 ... 64), shape[2] its outer points per
+ * chunk (0 = its full chunk, 8 with approxcaps, 7 otherwise, or fewer). Results do not depend
+ * on it. No counterpart in the paper. Errors: INVALID_ARG (NULL, out of range), UNSUPPORTED
+ * (FP64).
+ */
+int nlfem_tune_set(const nlfem_params* params, const int32_t shape[3]);
 
 /*
  * Batched assembly: the same result as n calls of nlfem_assemble (every system is the same

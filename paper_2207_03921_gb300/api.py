@@ -217,9 +217,17 @@ class BatchPlan:
 
 
 def autotune(mesh: Mesh, stream=None, **params) -> tuple:
-    """Pick the FP32-bulk grid size for this kernel class on mesh (nlfem_autotune); returns
-    the blocks per SM chosen for the whole-pair and the cut-pair kernel."""
+    """Pick the FP32-bulk launch shape for this kernel class on mesh (nlfem_autotune); returns
+    (blocks per SM of the whole-pair kernel, of the cut-pair kernel, its outer points per chunk)."""
     q = dict(precision="fp32_bulk")
     q.update(params)
     return B.nlfem_autotune(mesh.handle, _params_list([q])[0], stream)
+
+
+def tune_set(shape, **params) -> None:
+    """Set the FP32-bulk launch shape (whole bps, cut bps, outer points per chunk) of the kernel
+    class of params without timing (nlfem_tune_set)."""
+    q = dict(precision="fp32_bulk")
+    q.update(params)
+    B.nlfem_tune_set(_params_list([q])[0], shape)
 

@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
         lib.nlfem_batch_destroy.argtypes = [vp]
         lib.nlfem_batch_destroy.restype = None
         lib.nlfem_autotune.argtypes = [vp, C.POINTER(nlfem_params), vp, C.POINTER(C.c_int32)]
+        lib.nlfem_tune_set.argtypes = [C.POINTER(nlfem_params), C.POINTER(C.c_int32)]
         lib.nlfem_pairs_noalloc.argtypes = [vp, i64, vp, i64, dp, ip, ip, vp, vp, i64, C.POINTER(i64), vp]
         _lib = lib
     return _lib
@@ -198,9 +199,16 @@ def nlfem_batch_create(meshes, params, f_nodal=None, stream=None):
 
 
 def nlfem_autotune(mesh, params: nlfem_params, stream=None) -> tuple:
-    best = (C.c_int32 * 2)()
+    """(blocks per SM of the whole-pair kernel, of the cut-pair kernel, its outer points per chunk)."""
+    best = (C.c_int32 * 3)()
     _check(load().nlfem_autotune(mesh, C.byref(params), _stream(stream), best))
-    return int(best[0]), int(best[1])
+    return int(best[0]), int(best[1]), int(best[2])
+
+
+def nlfem_tune_set(params: nlfem_params, shape) -> None:
+    """Set the launch shape (whole bps, cut bps, outer points per chunk) of a kernel class."""
+    arr = (C.c_int32 * 3)(*[int(v) for v in shape])
+    _check(load().nlfem_tune_set(C.byref(params), arr))
 
 
 def nlfem_batch_run(batch, stream=None) -> float:

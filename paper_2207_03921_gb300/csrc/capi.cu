@@ -859,29 +859,54 @@ int nlfem_autotune(nlfem_mesh_t mesh, const nlfem_params* params, void* stream, 
     fix.zero(st);
     pick_scale(m, *pc, P, fix.p, st);  // the real scale, so that the atomics are the real ones too
     const int cand[] = {2, 4, 8, 16, 32, 64};
+    const int maxc = fast_max_chunk(P);
     for (int list = 0; list < 2; ++list) {
         const int64_t key = fast_tune_key(P, list);
         double best_ms = 1e300;
-        int best_c = fast_blocks_per_sm(key);
-        for (int c : cand) {
-            set_fast_blocks_per_sm(key, c);
-            double t = 1e300;
-            for (int rep = 0; rep < 2; ++rep) {
-                NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
-                launch_trunc_fast(m, *pc, P, BulkAcc{acc.p, llrec.p, &fix.p->scale, &fix.p->max_exact, 1}, st,
-                                  ev + 2);
-                NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
-                NLFEM_CUDA_TRY(cudaEventSynchronize(ev[1]));
-                t = std::min(t, elapsed_ms(ev[2 + list], ev[3 + list]));
-            }
-            if (t < best_ms) {
-                best_ms = t;
-                best_c = c;
+        int best_c = fast_blocks_per_sm(key), best_k = fast_chunk(key);
+        // the cut-pair kernel also tries smaller chunks of outer points (shorter drains, more of
+        // them); the whole-pair kernel has no chunks
+        const int chunks[3] = {maxc, (maxc + 1) / 2, 2};
+        for (int ci = 0; ci < (list == 1 ? 3 : 1); ++ci) {
+            for (int c : cand) {
+                set_fast_shape(key, c, list == 1 ? chunks[ci] : 0);
+                double t = 1e300;
+                for (int rep = 0; rep < 2; ++rep) {
+                    NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+                    launch_trunc_fast(m, *pc, P, BulkAcc{acc.p, llrec.p, &fix.p->scale, &fix.p->max_exact, 1}, st,
+                                      ev + 2);
+                    NLFEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+                    NLFEM_CUDA_TRY(cudaEventSynchronize(ev[1]));
+                    t = std::min(t, elapsed_ms(ev[2 + list], ev[3 + list]));
+                }
+                if (t < best_ms) {
+                    best_ms = t;
+                    best_c = c;
+                    best_k = list == 1 ? chunks[ci] : 0;
+                }
             }
         }
-        set_fast_blocks_per_sm(key, best_c);
+        set_fast_shape(key, best_c, best_k);
         best[list] = best_c;
+        if (list == 1) best[2] = best_k;
     }
+    return NLFEM_OK;
+    NLFEM_API_END
+}
+
+int nlfem_tune_set(const nlfem_params* params, const int32_t shape[3]) {
+    NLFEM_API_BEGIN
+    set_error("");
+    NLFEM_CHECK(params && shape, NLFEM_ERR_INVALID_ARG, "NULL argument");
+    const int ndof = params->kernel == NLFEM_KERNEL_PERIDYNAMIC ? 2 : 1;
+    Params P = make_params(*params, ndof);
+    NLFEM_CHECK(P.precision == NLFEM_PREC_FP32_BULK, NLFEM_ERR_UNSUPPORTED, "launch shapes apply to FP32 bulk");
+    for (int i = 0; i < 2; ++i)
+        NLFEM_CHECK(shape[i] >= 1 && shape[i] <= 64, NLFEM_ERR_INVALID_ARG, "blocks per SM must be in 1..64");
+    NLFEM_CHECK(shape[2] >= 0 && shape[2] <= fast_max_chunk(P), NLFEM_ERR_INVALID_ARG,
+                "outer points per chunk must be in 0.." + std::to_string(fast_max_chunk(P)));
+    set_fast_shape(fast_tune_key(P, 0), shape[0], 0);
+    set_fast_shape(fast_tune_key(P, 1), shape[1], shape[2]);
     return NLFEM_OK;
     NLFEM_API_END
 }

@@ -350,6 +350,9 @@ void set_fast_attributes();  // shared-memory limits of the cut-pair kernels (on
 int64_t fast_tune_key(const Params& prm, int list);
 int fast_blocks_per_sm(int64_t key);
 void set_fast_blocks_per_sm(int64_t key, int bps);
+int fast_chunk(int64_t key);                       // 0 = the kernel's full chunk
+void set_fast_shape(int64_t key, int bps, int chunk);
+int fast_max_chunk(const Params& prm);             // outer points per chunk of the cut-pair kernel
 // FP32-bulk assembly of several systems with fused bulk launches (quad.cu)
 struct BatchSys {
     Mesh* m;

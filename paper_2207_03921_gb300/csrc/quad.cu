@@ -285,16 +285,16 @@ struct DuffyArgs {
     int dg;          // discontinuous mesh: touching pairs (k != l) take k_duffy_split
 };
 
-// c |z|^(-2-2s) from d2 = |z|^2: square roots for s in {1/4, 1/2, 3/4} (each correctly rounded),
-// exp2 / log2 otherwise (a relative error of a few 1e-15, far below the rule's)
+// c |z|^(-2-2s) from d2 = |z|^2 by reciprocal square roots for s in {1/4, 1/2, 3/4}, with
+// r = d2^(-1/2): r^3 (s = 1/2), r^3 rsqrt(r) (s = 1/4), r^4 rsqrt(r) (s = 3/4) (rsqrt is within
+// 1 ulp, so a few ulps in all; no FP64 division or square root, which cost several times more
+// on the FP64 pipe); exp2 / log2 otherwise (a relative error of a few 1e-15, far below the rule's)
 __device__ __forceinline__ double gamma_d(double d2, const Params& P) {
     if (P.kernel == NLFEM_KERNEL_CONSTANT) return P.c;
-    if (P.s == 0.5) return P.c / (d2 * sqrt(d2));
-    if (P.s == 0.25) return P.c / (d2 * sqrt(sqrt(d2)));
-    if (P.s == 0.75) {
-        const double q = sqrt(d2);
-        return P.c / (d2 * q * sqrt(q));
-    }
+    const double r = rsqrt(d2);
+    if (P.s == 0.5) return P.c * (r * r * r);
+    if (P.s == 0.25) return P.c * (r * r * r * rsqrt(r));
+    if (P.s == 0.75) return P.c * (r * r * r * r * rsqrt(r));
     return P.c * exp2((-1.0 - P.s) * log2(d2));
 }
 

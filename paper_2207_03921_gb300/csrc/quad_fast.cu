@@ -81,6 +81,7 @@ struct FastLaunch {
     int nreq;
     int64_t ntiles;
     int pilot;
+    int chunk;                // cut-pair kernel: outer points per chunk (1 .. CHUNK; 0 = CHUNK)
     FastReq one;              // single-request launches: the request itself (constant bank)
 };
 
@@ -748,9 +749,12 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
 #pragma unroll
             for (int c = 0; c < NC; ++c) kl[i][c] = 0.f;
 
+        // outer points per chunk: the launch shape the autotuner picked (the drain walks a lane's
+        // outer points in the same order whatever the chunk, so the sums are the same bits)
+        const int ck = (L.chunk > 0 && L.chunk < CHUNK) ? L.chunk : CHUNK;
 #pragma unroll 1
-        for (int qb = 0; qb < nqo; qb += CHUNK) {
-            const int qn = min(CHUNK, nqo - qb);
+        for (int qb = 0; qb < nqo; qb += ck) {
+            const int qn = min(ck, nqo - qb);
             // ---- phase A1: whole and empty outer points in lockstep, the others become jobs
             unsigned long long counts = 0;  // 4 bits per outer point: number of polygon points
             unsigned need = 0;              // outer points to cut (jobs)
@@ -1252,8 +1256,14 @@ static int sm_count() {
     return n;
 }
 
+// Launch shape per kernel class and list: resident blocks per SM (grid size) and, for the
+// cut-pair kernel, outer points per chunk
+struct TuneEntry {
+    int64_t key;
+    int bps, chunk;
+};
 static std::mutex g_tune_mu;
-static std::vector<std::pair<int64_t, int>> g_tune;  // (kernel class and list, blocks per SM)
+static std::vector<TuneEntry> g_tune;
 
 int64_t fast_tune_key(const Params& prm, int list) {
     return ((((int64_t)prm.kernel * 64 + prm.ro.n) * 64 + prm.ri.n) * 4 + prm.ball) * 2 + list;
@@ -1262,25 +1272,43 @@ int64_t fast_tune_key(const Params& prm, int list) {
 int fast_blocks_per_sm(int64_t key) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     for (auto& e : g_tune)
-        if (e.first == key) return e.second;
+        if (e.key == key) return e.bps;
     return 64;  // untuned: oversubscribe; warps take 32-pair tiles in a grid-stride loop
 }
 
-void set_fast_blocks_per_sm(int64_t key, int bps) {
+int fast_chunk(int64_t key) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     for (auto& e : g_tune)
-        if (e.first == key) {
-            e.second = bps;
-            return;
-        }
-    g_tune.emplace_back(key, bps);
+        if (e.key == key) return e.chunk;
+    return 0;  // untuned: the full chunk
 }
 
-void launch_fast_list(const Params& prm, int list, const FastLaunch& L, cudaStream_t st) {
+void set_fast_shape(int64_t key, int bps, int chunk) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    for (auto& e : g_tune)
+        if (e.key == key) {
+            e.bps = bps;
+            e.chunk = chunk;
+            return;
+        }
+    g_tune.push_back(TuneEntry{key, bps, chunk});
+}
+
+void set_fast_blocks_per_sm(int64_t key, int bps) { set_fast_shape(key, bps, fast_chunk(key)); }
+
+int fast_max_chunk(const Params& prm) {
+    return prm.ball == NLFEM_BALL_APPROXCAPS ? CutShape<NLFEM_BALL_APPROXCAPS>::CHUNK
+                                             : CutShape<NLFEM_BALL_NOCAPS>::CHUNK;
+}
+
+void launch_fast_list(const Params& prm, int list, const FastLaunch& L0, cudaStream_t st) {
     set_fast_attributes();
-    const int64_t cap = (int64_t)sm_count() * fast_blocks_per_sm(fast_tune_key(prm, list));
-    const unsigned grid = (unsigned)std::min<int64_t>((L.ntiles + FAST_WARPS - 1) / FAST_WARPS, cap);
+    const int64_t key = fast_tune_key(prm, list);
+    const int64_t cap = (int64_t)sm_count() * fast_blocks_per_sm(key);
+    const unsigned grid = (unsigned)std::min<int64_t>((L0.ntiles + FAST_WARPS - 1) / FAST_WARPS, cap);
     if (!grid) return;
+    FastLaunch L = L0;
+    L.chunk = fast_chunk(key);
     const FastRule r = make_rule(prm);
     if (L.reqs) launch_kernel<true>(prm, list, r, L, grid, st);
     else launch_kernel<false>(prm, list, r, L, grid, st);

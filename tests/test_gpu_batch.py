@@ -79,16 +79,28 @@ def test_batch_plan_graph_replay_equals_single():
         BatchPlan(ms[:1], [dict(items[0][2], precision="fp64")])
 
 
-def test_autotune_keeps_results():
-    from paper_2207_03921_gb300 import autotune
-    m = meshes.structured(-0.1, 1.1, 40, name="s40")
+@pytest.mark.parametrize("kw", [dict(kernel="constant", delta=0.1, ball="nocaps"),
+                                dict(kernel="fractional", s=0.5, delta=0.1, ball="approxcaps", quad_outer=16,
+                                     quad_inner=16)])
+def test_autotune_keeps_results(kw):
+    # the launch shape (grid size, outer points per chunk of the cut-pair kernel) changes the
+    # schedule only: every shape gives the same bits
+    from paper_2207_03921_gb300 import autotune, tune_set
+    m = meshes.jittered_delaunay(-0.1, 1.1, 30, 0.03, seed=2207039219)
     mesh = Mesh.from_synth(m)
-    kw = dict(kernel="constant", delta=0.1, precision="fp32_bulk")
+    kw = dict(kw, precision="fp32_bulk")
+    tune_set((64, 64, 0), **kw)
     before = assemble(mesh, **kw).csr()[2].cpu().numpy()
+    for shape in ((2, 3, 1), (8, 4, 2), (16, 1, 5)):   # non-default grids and chunks
+        tune_set(shape, **kw)
+        assert np.array_equal(assemble(mesh, **kw).csr()[2].cpu().numpy(), before), shape
     best = autotune(mesh, **kw)
-    assert all(b in (2, 4, 8, 16, 32, 64) for b in best)
+    assert best[0] in (2, 4, 8, 16, 32, 64) and best[1] in (2, 4, 8, 16, 32, 64)
+    assert 1 <= best[2] <= (8 if kw["ball"] == "approxcaps" else 7)
     after = assemble(mesh, **kw).csr()[2].cpu().numpy()
     assert np.array_equal(before, after)
+    with pytest.raises(NlfemError):
+        tune_set((0, 4, 2), **kw)
 
 
 def _items_extended():
