@@ -1018,9 +1018,11 @@ __global__ void k_window_ptr(int64_t* ptr, int64_t nwin, int64_t n, int w) {
 
 // Pairs with E_l inside the ball of every point of E_k: the whole inner element at every
 // outer point, no geometry at all.
-// Scalar kernels with the 7-point inner rule fit 80 registers without spills: 6 blocks per SM.
+// Scalar kernels with the 7-point inner rule run at 64 registers, 8 blocks per SM: the kernel
+// waits on the dependent loads that start each pair, and 32 warps per SM hide them better than
+// 24 at 80 registers without spills (a few spilled words; 720k: 5.14 -> 4.80 ms, A/B in one run).
 template <int KER, int NQI, bool BATCH>
-__global__ void __launch_bounds__(FAST_THREADS, (KER != NLFEM_KERNEL_PERIDYNAMIC && !BATCH && NQI == 7) ? 6 : 1)
+__global__ void __launch_bounds__(FAST_THREADS, (KER != NLFEM_KERNEL_PERIDYNAMIC && !BATCH && NQI == 7) ? 8 : 1)
     k_trunc_whole(const __grid_constant__ FastRule R, const __grid_constant__ FastLaunch L) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
     __shared__ FastReq sq[BATCH ? FAST_WARPS : 1];
