@@ -5,6 +5,11 @@
 // on A_FF inside an FP64 residual-refinement loop, which recovers FP64 accuracy of u_F.
 // All scalars (alpha, beta, residual norms) stay on the device; the host reads the
 // residual only every CHECK_EVERY iterations. Dot products are reduced in a fixed order.
+// A block of CHECK_EVERY inner iterations is a fixed sequence of launches on fixed buffers:
+// it is captured once per system into a CUDA graph and replayed, which removes the
+// per-launch host cost that dominates small solves; the kernels and their order are the
+// same, so the results are the same bits.
+#include <algorithm>
 #include <cmath>
 
 #include "nlfem_internal.cuh"
@@ -24,7 +29,40 @@ struct SolveState {
                           // [8..10] null-space coefficients, [11] Gram-Schmidt scratch
     DBuf<double> Z;       // orthonormal null-space basis of the full matrix [nz][N] (Neumann solve)
     int nz = 0;
+    cudaStream_t cap = nullptr;                   // private stream the blocks are captured on
+    cudaGraphExec_t blk[2] = {nullptr, nullptr};  // [0] Dirichlet block, [1] Neumann block
+    ~SolveState() {
+        for (auto& g : blk)
+            if (g) cudaGraphExecDestroy(g);
+        if (cap) cudaStreamDestroy(cap);
+    }
 };
+
+// Runs body(stream) on st: the first time it is captured from a private stream into W.blk[kind],
+// every time the graph is launched on st. body must enqueue only kernels on the stream it is
+// given, on buffers that stay in place for the life of W.
+template <typename F>
+static void run_block(SolveState& W, int kind, F&& body, cudaStream_t st) {
+    if (!W.blk[kind]) {
+        if (!W.cap) NLFEM_CUDA_TRY(cudaStreamCreateWithFlags(&W.cap, cudaStreamNonBlocking));
+        NLFEM_CUDA_TRY(cudaStreamBeginCapture(W.cap, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t g = nullptr;
+        try {
+            body(W.cap);
+        } catch (...) {
+            cudaStreamEndCapture(W.cap, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        NLFEM_CUDA_TRY(cudaStreamEndCapture(W.cap, &g));
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        NLFEM_CUDA_TRY(e);
+        W.blk[kind] = ex;
+    }
+    NLFEM_CUDA_TRY(cudaGraphLaunch(W.blk[kind], st));
+}
 
 static constexpr int DOT_BLOCKS = 1024;
 static constexpr int DOT_THREADS = 256;
@@ -264,19 +302,28 @@ int solve_neumann(System& S, double tol, int max_iter, double* u_out, nlfem_solv
         NLFEM_CUDA_TRY(cudaMemcpyAsync(&rho0, W.sc.p, sizeof rho0, cudaMemcpyDeviceToHost, st));
         NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
         const double inner_tol2 = rho0 * 1e-8;
+        auto iterate = [&](cudaStream_t s, int n) {
+            for (int j = 0; j < n; ++j) {
+                k_spmv<float, float><<<gw, 256, 0, s>>>(pc.row_ptr.p, pc.col.p, W.val32.p, W.p.p, W.q.p, nullptr, N);
+                dot(W.p.p, W.q.p, N, W.part.p, W.sc.p + 1, s);
+                k_cg_update<<<ge, 256, 0, s>>>(W.d.p, W.r.p, W.p.p, W.q.p, W.sc.p, N);
+                project_out(W, W.r.p, s);
+                dot(W.r.p, W.r.p, N, W.part.p, W.sc.p + 2, s);
+                k_cg_dir<<<ge, 256, 0, s>>>(W.p.p, W.r.p, W.sc.p, N);
+                k_roll<<<1, 1, 0, s>>>(W.sc.p);
+                NLFEM_LAUNCH_CHECK();
+            }
+        };
         int it = 0;
         while (iters < max_iter) {
-            k_spmv<float, float><<<gw, 256, 0, st>>>(pc.row_ptr.p, pc.col.p, W.val32.p, W.p.p, W.q.p, nullptr, N);
-            dot(W.p.p, W.q.p, N, W.part.p, W.sc.p + 1, st);
-            k_cg_update<<<ge, 256, 0, st>>>(W.d.p, W.r.p, W.p.p, W.q.p, W.sc.p, N);
-            project_out(W, W.r.p, st);
-            dot(W.r.p, W.r.p, N, W.part.p, W.sc.p + 2, st);
-            k_cg_dir<<<ge, 256, 0, st>>>(W.p.p, W.r.p, W.sc.p, N);
-            k_roll<<<1, 1, 0, st>>>(W.sc.p);
-            NLFEM_LAUNCH_CHECK();
-            ++it;
-            ++iters;
-            if (it % CHECK_EVERY == 0) {
+            const int n = std::min(CHECK_EVERY, max_iter - iters);
+            if (n == CHECK_EVERY)
+                run_block(W, 1, [&](cudaStream_t s) { iterate(s, CHECK_EVERY); }, st);
+            else
+                iterate(st, n);
+            it += n;
+            iters += n;
+            if (n == CHECK_EVERY) {
                 double rho = 0;
                 NLFEM_CUDA_TRY(cudaMemcpyAsync(&rho, W.sc.p, sizeof rho, cudaMemcpyDeviceToHost, st));
                 NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -341,18 +388,28 @@ int solve_system(System& S, const double* g, double tol, int max_iter, double* u
         NLFEM_CUDA_TRY(cudaMemcpyAsync(&rho0, W.sc.p, sizeof rho0, cudaMemcpyDeviceToHost, st));
         NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
         const double inner_tol2 = rho0 * 1e-8;
+        auto iterate = [&](cudaStream_t s, int n) {
+            for (int j = 0; j < n; ++j) {
+                k_spmv<float, float><<<gw, 256, 0, s>>>(pc.row_ptr.p, pc.col.p, W.val32.p, W.p.p, W.q.p, W.freem.p,
+                                                        N);
+                dot(W.p.p, W.q.p, N, W.part.p, W.sc.p + 1, s);
+                k_cg_update<<<ge, 256, 0, s>>>(W.d.p, W.r.p, W.p.p, W.q.p, W.sc.p, N);
+                dot(W.r.p, W.r.p, N, W.part.p, W.sc.p + 2, s);
+                k_cg_dir<<<ge, 256, 0, s>>>(W.p.p, W.r.p, W.sc.p, N);
+                k_roll<<<1, 1, 0, s>>>(W.sc.p);
+                NLFEM_LAUNCH_CHECK();
+            }
+        };
         int it = 0;
         while (iters < max_iter) {
-            k_spmv<float, float><<<gw, 256, 0, st>>>(pc.row_ptr.p, pc.col.p, W.val32.p, W.p.p, W.q.p, W.freem.p, N);
-            dot(W.p.p, W.q.p, N, W.part.p, W.sc.p + 1, st);
-            k_cg_update<<<ge, 256, 0, st>>>(W.d.p, W.r.p, W.p.p, W.q.p, W.sc.p, N);
-            dot(W.r.p, W.r.p, N, W.part.p, W.sc.p + 2, st);
-            k_cg_dir<<<ge, 256, 0, st>>>(W.p.p, W.r.p, W.sc.p, N);
-            k_roll<<<1, 1, 0, st>>>(W.sc.p);
-            NLFEM_LAUNCH_CHECK();
-            ++it;
-            ++iters;
-            if (it % CHECK_EVERY == 0) {
+            const int n = std::min(CHECK_EVERY, max_iter - iters);
+            if (n == CHECK_EVERY)
+                run_block(W, 0, [&](cudaStream_t s) { iterate(s, CHECK_EVERY); }, st);
+            else
+                iterate(st, n);
+            it += n;
+            iters += n;
+            if (n == CHECK_EVERY) {
                 double rho = 0;
                 NLFEM_CUDA_TRY(cudaMemcpyAsync(&rho, W.sc.p, sizeof rho, cudaMemcpyDeviceToHost, st));
                 NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
