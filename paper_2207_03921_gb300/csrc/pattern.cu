@@ -111,88 +111,103 @@ __device__ __forceinline__ bool hash_insert(int* tab, int cap, int key, int* cou
     return false;
 }
 
-// FILL = false: count the columns of each row; true: write the sorted columns at rowptr[i],
-// or with SLOTS at i * cap / 2 and count them (one pass; k_compact_rows packs the slots)
-template <bool FILL, bool SLOTS = false>
-__global__ void k_pattern(RowEnum R, int64_t M, int cap, int64_t* rowcnt, const int64_t* rowptr,
-                          int* cols, int* overflow) {
-    extern __shared__ int sm[];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    int* tab = sm + warp * (cap + 1);
-    int* count = tab + cap;
-    if (i >= M) return;
-    for (int t = lane; t < cap; t += 32) tab[t] = -1;
-    if (lane == 0) *count = 0;
-    __syncwarp();
-    RowRanges rr;
-    row_ranges(R, (int)i, rr);
-    int64_t total = rr.cum[2 * rr.nne];
-    bool ok = true;
-    // the union vertices of every pair containing i: the nodes of i's own elements once, and
-    // per pair the nodes of its other element (E_l on the x side, E_k on the y side)
-    for (int t = lane; t < rr.nne; t += 32) {
-        const int4 te = R.T[rr.ne[t]];
-        ok &= hash_insert(tab, cap, te.x, count);
-        ok &= hash_insert(tab, cap, te.y, count);
-        ok &= hash_insert(tab, cap, te.z, count);
-    }
-    for (int64_t f0 = 0; f0 < total; f0 += 32) {
-        int64_t f = f0 + lane;
-        if (f < total) {
-            int p = row_pair(R, rr, f, (int)i);
-            if (p >= 0) {
-                const int4 to = f < rr.cum[rr.nne] ? R.T[R.pl[p]] : R.T[R.pk[p]];
-                ok &= hash_insert(tab, cap, to.x, count);
-                ok &= hash_insert(tab, cap, to.y, count);
-                ok &= hash_insert(tab, cap, to.z, count);
-            }
-        }
-    }
-    __syncwarp();
-    bool good = __all_sync(0xffffffffu, ok) && *count <= cap / 2;
-    if (!good) {
-        if (lane == 0) atomicOr(overflow, 1);
-        return;
-    }
-    int n = *count;
-    if (!FILL || SLOTS) {
-        if (lane == 0) rowcnt[i] = n;
-        if (!FILL) return;
-    }
-    // compact the keys to the front of the table, then bitonic sort them
-    __syncwarp();
-    int w = 0;
-    for (int t0 = 0; t0 < cap; t0 += 32) {
-        int key = tab[t0 + lane];
-        unsigned m = __ballot_sync(0xffffffffu, key != -1);
-        __syncwarp();
-        if (key != -1) tab[w + __popc(m & ((1u << lane) - 1u))] = key;
-        w += __popc(m);
-        __syncwarp();
+// the row's keys gathered from the table (in any order), bitonic-sorted over the next power
+// of two and written to out
+__device__ __forceinline__ void sorted_row(const int* tab, int* keys, int cap, int n, int* out) {
+    __shared__ int wpos;
+    if (threadIdx.x == 0) wpos = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < cap; t += blockDim.x) {
+        const int key = tab[t];
+        if (key != -1) keys[atomicAdd(&wpos, 1)] = key;
     }
     int n2 = 1;
     while (n2 < n) n2 <<= 1;
-    for (int t = n + lane; t < n2; t += 32) tab[t] = 0x7fffffff;
-    __syncwarp();
+    __syncthreads();
+    for (int t = n + threadIdx.x; t < n2; t += blockDim.x) keys[t] = 0x7fffffff;
+    __syncthreads();
     for (int size = 2; size <= n2; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = lane; t < n2; t += 32) {
-                int j = t ^ stride;
+            for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+                const int j = t ^ stride;
                 if (j > t) {
-                    bool up = (t & size) == 0;
-                    int a = tab[t], b = tab[j];
+                    const bool up = (t & size) == 0;
+                    const int a = keys[t], b = keys[j];
                     if ((a > b) == up) {
-                        tab[t] = b;
-                        tab[j] = a;
+                        keys[t] = b;
+                        keys[j] = a;
                     }
                 }
             }
-            __syncwarp();
+            __syncthreads();
         }
     }
-    int64_t base = SLOTS ? i * (int64_t)(cap / 2) : rowptr[i];
-    for (int t = lane; t < n; t += 32) cols[base + t] = tab[t];
+    for (int t = threadIdx.x; t < n; t += blockDim.x) out[t] = keys[t];
+}
+
+// One block per node row: its threads share the row's hash table (cap ints) and a buffer
+// for the compacted keys (cap / 2 ints). A row visits every pair of its node's elements, tens
+// of thousands for wide horizons, through chains of dependent loads; a whole block on one
+// row keeps enough of them in flight.
+// FILL = false: count the columns of each row; true: write the sorted columns at rowptr[i],
+// or with SLOTS at i * cap / 2 and count them (one pass; k_compact_rows packs the slots)
+static constexpr int PAT_THREADS = 256;
+
+template <bool FILL, bool SLOTS = false>
+__global__ void __launch_bounds__(PAT_THREADS) k_pattern(RowEnum R, int64_t M, int cap, int64_t* rowcnt,
+                                                         const int64_t* rowptr, int* cols, int* overflow) {
+    extern __shared__ int sm[];
+    __shared__ RowRanges rr;
+    __shared__ int count, bad;
+    const int64_t i = blockIdx.x;
+    if (i >= M) return;
+    int* tab = sm;
+    int* keys = sm + cap;
+    for (int t = threadIdx.x; t < cap; t += blockDim.x) tab[t] = -1;
+    if (threadIdx.x == 0) {
+        row_ranges(R, (int)i, rr);
+        count = 0;
+        bad = 0;
+    }
+    __syncthreads();
+    const int64_t total = rr.cum[2 * rr.nne];
+    bool ok = true;
+    // the union vertices of every pair containing i: the nodes of i's own elements once, and
+    // per pair the nodes of its other element (E_l on the x side, E_k on the y side)
+    for (int t = threadIdx.x; t < rr.nne; t += blockDim.x) {
+        const int4 te = R.T[rr.ne[t]];
+        ok &= hash_insert(tab, cap, te.x, &count);
+        ok &= hash_insert(tab, cap, te.y, &count);
+        ok &= hash_insert(tab, cap, te.z, &count);
+    }
+    int s = 0;  // range of f: a thread's f only grows, so its range index does too
+    for (int64_t f = threadIdx.x; f < total; f += blockDim.x) {
+        while (rr.cum[s + 1] <= f) ++s;
+        const int64_t off = f - rr.cum[s];
+        int4 to;
+        if (s < rr.nne) {
+            to = R.T[R.pl[R.pair_ptr[rr.ne[s]] + off]];
+        } else {
+            const int e = rr.ne[s - rr.nne];
+            const int p = R.pT_id[R.pT_ptr[e] + off];
+            to = R.T[R.pk[p]];
+            if (to.x == (int)i || to.y == (int)i || to.z == (int)i) continue;  // already on the x side
+        }
+        ok &= hash_insert(tab, cap, to.x, &count);
+        ok &= hash_insert(tab, cap, to.y, &count);
+        ok &= hash_insert(tab, cap, to.z, &count);
+    }
+    if (!ok) bad = 1;
+    __syncthreads();
+    const int n = count;
+    if (bad || n > cap / 2) {
+        if (threadIdx.x == 0) atomicOr(overflow, 1);
+        return;
+    }
+    if (!FILL || SLOTS) {
+        if (threadIdx.x == 0) rowcnt[i] = n;
+    }
+    if constexpr (FILL) sorted_row(tab, keys, cap, n, cols + (SLOTS ? i * (int64_t)(cap / 2) : rowptr[i]));
 }
 
 __global__ void k_compact_rows(const int* slots, int64_t M, int64_t width, const int64_t* ptr, int* out) {
@@ -578,8 +593,7 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
     while (cap < 32768 && cap < 2 * maxp) cap *= 2;
     for (;;) {
         ovf.zero(st);
-        int warps = std::max(1, std::min(8, (int)(160 * 1024 / ((cap + 1) * 4))));
-        size_t smem = (size_t)warps * (cap + 1) * sizeof(int);
+        const size_t smem = (size_t)(cap + cap / 2) * sizeof(int);  // table and compacted keys
         NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_pattern<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         NLFEM_CUDA_TRY(cudaFuncSetAttribute(k_pattern<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         NLFEM_CUDA_TRY(
@@ -589,10 +603,10 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
         DBuf<int> slot_buf;
         if (slots) {
             slot_buf.alloc(M * (int64_t)(cap / 2), st);
-            k_pattern<true, true><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, cap, rowcnt.p, nullptr, slot_buf.p,
-                                                                            ovf.p);
+            k_pattern<true, true><<<(unsigned)M, PAT_THREADS, smem, st>>>(R, M, cap, rowcnt.p, nullptr, slot_buf.p,
+                                                                          ovf.p);
         } else {
-            k_pattern<false><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, cap, rowcnt.p, nullptr, nullptr, ovf.p);
+            k_pattern<false><<<(unsigned)M, PAT_THREADS, smem, st>>>(R, M, cap, rowcnt.p, nullptr, nullptr, ovf.p);
         }
         NLFEM_LAUNCH_CHECK();
         int h = 0;
@@ -606,8 +620,8 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
             if (slots) {
                 k_compact_rows<<<nblk(M * 32, 256), 256, 0, st>>>(slot_buf.p, M, cap / 2, pc.nrow_ptr.p, pc.ncol.p);
             } else {
-                k_pattern<true><<<nblk(M, warps), warps * 32, smem, st>>>(R, M, cap, rowcnt.p, pc.nrow_ptr.p,
-                                                                          pc.ncol.p, ovf.p);
+                k_pattern<true><<<(unsigned)M, PAT_THREADS, smem, st>>>(R, M, cap, rowcnt.p, pc.nrow_ptr.p,
+                                                                        pc.ncol.p, ovf.p);
             }
             NLFEM_LAUNCH_CHECK();
             break;
