@@ -25,6 +25,7 @@ struct SolveState {
     DBuf<double> b, x, r64, y64;
     DBuf<float> r, p, q, d;
     DBuf<double> part;    // partial sums of dot products
+    DBuf<unsigned> ticket;  // blocks done of the running fused CG kernel (0 between launches)
     DBuf<double> sc;      // device scalars: [0] rho, [1] p.q, [2] rho_new, [3] |r64|^2, [4] |b|^2,
                           // [8..10] null-space coefficients, [11] Gram-Schmidt scratch
     DBuf<double> Z;       // orthonormal null-space basis of the full matrix [nz][N] (Neumann solve)
@@ -159,6 +160,98 @@ __global__ void k_cg_dir(float* p, const float* r, double* sc, int64_t n) {
 
 __global__ void k_roll(double* sc) { sc[0] = sc[2]; }
 
+// ---- one CG iteration in three kernels (Dirichlet solve) ----------------------------------
+// Each kernel reduces its dot product in the same launch: every block writes its partial sum,
+// and the last block to finish (a ticket counter) adds the partials in block order, so the
+// sum is the same on every run. The grids depend on N only (the product: one warp per row).
+static constexpr int CG_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = CG_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// partial sum of this block into part[blockIdx.x]; true in every thread of the last block,
+// which then holds in sh the total of all partials (block order, then a fixed tree)
+__device__ __forceinline__ bool reduce_last(double v, double* part, unsigned* ticket, double* sh, double& total) {
+    __shared__ bool last;
+    const double b = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    double t = 0;
+    for (unsigned j = threadIdx.x; j < gridDim.x; j += CG_THREADS) t += __ldcg(part + j);
+    total = block_sum(t, sh);
+    if (threadIdx.x == 0) *ticket = 0;
+    return true;
+}
+
+// q = A_FF p (warp per row), sc[1] = p . q
+__global__ void __launch_bounds__(CG_THREADS) k_cg_spmv_pq(const int64_t* __restrict__ rp, const int* __restrict__ col,
+                                                           const float* __restrict__ val, const float* __restrict__ p,
+                                                           float* __restrict__ q, const int8_t* __restrict__ freem,
+                                                           int64_t N, double* part, unsigned* ticket, double* sc) {
+    __shared__ double sh[CG_THREADS];
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (CG_THREADS / 32);
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * (CG_THREADS / 32) + (threadIdx.x >> 5); i < N; i += nw) {
+        const bool fr = freem[i];
+        float s = 0;
+        if (fr)
+            for (int64_t t = rp[i] + lane; t < rp[i + 1]; t += 32) s += val[t] * p[col[t]];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const float qi = fr ? s : 0.f;
+            q[i] = qi;
+            acc += (double)p[i] * (double)qi;
+        }
+    }
+    double total;
+    if (reduce_last(acc, part, ticket, sh, total) && threadIdx.x == 0) sc[1] = total;
+}
+
+// alpha = sc[0] / sc[1]; d += alpha p; r -= alpha q; rho_new = r . r;
+// then sc[5] = beta = rho_new / sc[0] and sc[0] = rho_new
+__global__ void __launch_bounds__(CG_THREADS) k_cg_update_rr(float* __restrict__ d, float* __restrict__ r,
+                                                             const float* __restrict__ p, const float* __restrict__ q,
+                                                             int64_t N, double* part, unsigned* ticket, double* sc) {
+    __shared__ double sh[CG_THREADS];
+    const double rho = sc[0], pq = sc[1];
+    const float alpha = pq != 0.0 ? (float)(rho / pq) : 0.f;
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * CG_THREADS + threadIdx.x; i < N; i += (int64_t)gridDim.x * CG_THREADS) {
+        d[i] += alpha * p[i];
+        const float ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        acc += (double)ri * (double)ri;
+    }
+    double total;
+    if (reduce_last(acc, part, ticket, sh, total) && threadIdx.x == 0) {
+        sc[2] = total;
+        sc[5] = rho != 0.0 ? total / rho : 0.0;
+        sc[0] = total;
+    }
+}
+
+// p = r + beta p
+__global__ void k_cg_dir_b(float* __restrict__ p, const float* __restrict__ r, const double* __restrict__ sc, int64_t N) {
+    const float beta = (float)sc[5];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = r[i] + beta * p[i];
+}
+
 __global__ void k_start(float* r, float* p, float* d, const double* r64, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -247,7 +340,10 @@ static int ensure_solver(System& S, cudaStream_t st) {
     NLFEM_LAUNCH_CHECK();
     ss->b.alloc(N, st); ss->x.alloc(N, st); ss->r64.alloc(N, st); ss->y64.alloc(N, st);
     ss->r.alloc(N, st); ss->p.alloc(N, st); ss->q.alloc(N, st); ss->d.alloc(N, st);
-    ss->part.alloc(DOT_BLOCKS, st);
+    // partial sums: DOT_BLOCKS for dot(), a block's share of the fused CG kernels (warp per row)
+    ss->part.alloc(std::max<int64_t>(DOT_BLOCKS, nblk(N * 32, CG_THREADS)), st);
+    ss->ticket.alloc(1, st);
+    ss->ticket.zero(st);
     ss->sc.alloc(16, st);
     S.solver = ss;
     return NLFEM_OK;
@@ -388,15 +484,13 @@ int solve_system(System& S, const double* g, double tol, int max_iter, double* u
         NLFEM_CUDA_TRY(cudaMemcpyAsync(&rho0, W.sc.p, sizeof rho0, cudaMemcpyDeviceToHost, st));
         NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
         const double inner_tol2 = rho0 * 1e-8;
+        const unsigned gq = gw, gu = std::min<unsigned>(ge, DOT_BLOCKS);  // one row per warp for the product
         auto iterate = [&](cudaStream_t s, int n) {
             for (int j = 0; j < n; ++j) {
-                k_spmv<float, float><<<gw, 256, 0, s>>>(pc.row_ptr.p, pc.col.p, W.val32.p, W.p.p, W.q.p, W.freem.p,
-                                                        N);
-                dot(W.p.p, W.q.p, N, W.part.p, W.sc.p + 1, s);
-                k_cg_update<<<ge, 256, 0, s>>>(W.d.p, W.r.p, W.p.p, W.q.p, W.sc.p, N);
-                dot(W.r.p, W.r.p, N, W.part.p, W.sc.p + 2, s);
-                k_cg_dir<<<ge, 256, 0, s>>>(W.p.p, W.r.p, W.sc.p, N);
-                k_roll<<<1, 1, 0, s>>>(W.sc.p);
+                k_cg_spmv_pq<<<gq, CG_THREADS, 0, s>>>(pc.row_ptr.p, pc.col.p, W.val32.p, W.p.p, W.q.p, W.freem.p, N,
+                                                       W.part.p, W.ticket.p, W.sc.p);
+                k_cg_update_rr<<<gu, CG_THREADS, 0, s>>>(W.d.p, W.r.p, W.p.p, W.q.p, N, W.part.p, W.ticket.p, W.sc.p);
+                k_cg_dir_b<<<gu, 256, 0, s>>>(W.p.p, W.r.p, W.sc.p, N);
                 NLFEM_LAUNCH_CHECK();
             }
         };

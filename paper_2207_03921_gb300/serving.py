@@ -7,7 +7,10 @@ several requests overlap on the GPU while new requests keep being admitted as sl
 memory free up (continuous batching, not a queue alone). A request uploads its mesh,
 assembles A and F (nlfem_assemble, pair search and pattern included), solves the
 nonlocal Dirichlet problem with FP64 residual refinement (nlfem_solve) and copies u
-back; its latency is completion minus arrival.
+back; its latency is completion minus arrival. Small requests admitted in the same
+scheduling pass are assembled together by nlfem_batch_assemble, which fuses the bulk
+quadrature of all of them into one launch per kernel class; each then solves on its own
+slot's stream and thread.
 
 Meshes with their pair lists and CSR patterns stay on the device in an LRU cache under
 the same budget, so a repeated (mesh, delta, ball) skips the pair search and pattern.
@@ -15,6 +18,7 @@ All device work goes through the C ABI; this module only schedules.
 """
 from __future__ import annotations
 
+import functools
 import hashlib
 import math
 import threading
@@ -31,6 +35,10 @@ BYTES_PER_PAIR = 120
 # bytes per CSR entry: column (4), value (8), transposed position (8), node pattern (4),
 # fixed-point sums (8 per upper entry)
 BYTES_PER_NNZ = 28
+# requests with fewer estimated ordered pairs than this are assembled in batches: a larger one
+# fills the GPU by itself, and alone it keeps its cold path (pair search, pattern) overlapped
+# with the other slots' work
+BATCH_MAX_PAIRS = 4_000_000
 
 
 def estimate_pairs(K: int, area: float, delta: float) -> float:
@@ -87,6 +95,7 @@ class Result:
     rel_residual: float = float("nan")
     error: str | None = None
     cached_mesh: bool = False
+    batched: bool = False     # assembled in a batch with other requests (nlfem_batch_assemble)
     t_mesh: float = 0.0       # upload and mesh preparation (s)
     t_assemble: float = 0.0   # nlfem_assemble (pair search and pattern unless cached)
     t_solve: float = 0.0      # nlfem_solve and the copy of u to the host
@@ -198,6 +207,7 @@ class Stats:
                 "wall_s": self.wall, "requests_per_s": len(ok) / self.wall if self.wall else None,
                 "pairs_per_s": pairs / self.wall if self.wall else None,
                 "max_inflight": self.max_inflight, "max_device_bytes_reserved": self.max_used_bytes,
+                "batched": sum(r.batched for r in ok),
                 "mean_mesh_ms": float(np.mean([r.t_mesh for r in ok]) * 1e3) if ok else None,
                 "mean_assemble_ms": float(np.mean([r.t_assemble for r in ok]) * 1e3) if ok else None,
                 "mean_solve_ms": float(np.mean([r.t_solve for r in ok]) * 1e3) if ok else None,
@@ -211,15 +221,22 @@ class Server:
     budget_bytes: device-memory admission budget; slots: requests in flight at most;
     keep_results: copy u (and optionally the CSR values) back to the host for checking.
     execute: the per-request work (default: upload, assemble, solve); replaceable for
-    host-only tests of the scheduling.
+    host-only tests of the scheduling. batch: assemble the small requests admitted in one
+    scheduling pass together (nlfem_batch_assemble); execute_batch(reqs, results, slots)
+    does it and returns one callable per request that finishes it (default: upload,
+    batched assembly, then per request solve), replaceable like execute.
     """
 
     def __init__(self, budget_bytes: int = 40 << 30, slots: int = 8, keep_values: bool = False,
-                 execute=None, cache_meshes: bool = True, clock=time.perf_counter):
+                 execute=None, cache_meshes: bool = True, clock=time.perf_counter, batch: bool = True,
+                 execute_batch=None):
         self.budget = MemoryBudget(budget_bytes)
         self.slots = slots
         self.keep_values = keep_values
         self.execute = execute or self._execute
+        if execute_batch is None and execute is None:
+            execute_batch = self._execute_batch
+        self.execute_batch = execute_batch if batch else None
         self.cache = MeshCache(self.budget) if cache_meshes and execute is None else None
         self.clock = clock
         self._streams = None
@@ -231,29 +248,32 @@ class Server:
                 self.cache.items.clear()
 
     # ---- per-request device work -------------------------------------------------------
-    def _execute(self, req: Request, res: Result, slot: int):
+    def _prepare(self, req: Request, res: Result, stream):
+        """Mesh handle (cached or uploaded), load f and Dirichlet data g on the device."""
         import torch
-        from .api import Mesh, assemble
+        from .api import Mesh
+        key = (req.key(), 1)
+        mesh = self.cache.get(key) if self.cache else None
+        res.cached_mesh = mesh is not None
+        if mesh is None:
+            mesh = Mesh(req.verts, req.elems, req.labels, 1, stream=stream)
+        x, y = req.verts[:, 0], req.verts[:, 1]
+        f = torch.full((len(x),), -4.0, dtype=torch.float64, device="cuda")
+        g = torch.as_tensor(x * x + y * y, dtype=torch.float64).cuda()
+        return key, mesh, f, g
+
+    @staticmethod
+    def _params(req: Request) -> dict:
+        return dict(kernel=req.kernel, delta=req.delta, s=req.s, ball=req.ball, quad_outer=req.quad_outer,
+                    quad_inner=req.quad_inner, precision=req.precision)
+
+    def _solve_finish(self, req: Request, res: Result, slot: int, key, mesh, g, S):
+        """Solve on the slot's stream, copy u back, hand the mesh to the cache."""
+        import torch
         stream = self._streams[slot]
         clk = time.perf_counter
         with torch.cuda.stream(stream):
-            t = clk()
-            key = (req.key(), 1)
-            mesh = self.cache.get(key) if self.cache else None
-            res.cached_mesh = mesh is not None
-            if mesh is None:
-                mesh = Mesh(req.verts, req.elems, req.labels, 1, stream=stream)
-            x, y = req.verts[:, 0], req.verts[:, 1]
-            f = torch.full((len(x),), -4.0, dtype=torch.float64, device="cuda")
-            g = torch.as_tensor(x * x + y * y, dtype=torch.float64).cuda()
-            stream.synchronize()
-            res.t_mesh = clk() - t
-            t = clk()
-            S = assemble(mesh, kernel=req.kernel, delta=req.delta, s=req.s, ball=req.ball,
-                         quad_outer=req.quad_outer, quad_inner=req.quad_inner, precision=req.precision,
-                         f_nodal=f, stream=stream)
             info = S.info()
-            res.t_assemble = clk() - t
             t = clk()
             u, sinfo = S.solve(g, tol_rel=1e-10, stream=stream)
             res.u = u.cpu().numpy()
@@ -272,6 +292,43 @@ class Server:
             elif self.cache is not None:
                 self.cache.done(key)
             return held
+
+    def _execute(self, req: Request, res: Result, slot: int):
+        import torch
+        from .api import assemble
+        stream = self._streams[slot]
+        clk = time.perf_counter
+        with torch.cuda.stream(stream):
+            t = clk()
+            key, mesh, f, g = self._prepare(req, res, stream)
+            stream.synchronize()
+            res.t_mesh = clk() - t
+            t = clk()
+            S = assemble(mesh, f_nodal=f, stream=stream, **self._params(req))
+            stream.synchronize()
+            res.t_assemble = clk() - t
+        return self._solve_finish(req, res, slot, key, mesh, g, S)
+
+    def _execute_batch(self, reqs: list, ress: list, slots: list) -> list:
+        import torch
+        from .api import assemble_batch
+        stream = self._streams[slots[0]]
+        clk = time.perf_counter
+        with torch.cuda.stream(stream):
+            t = clk()
+            preps = [self._prepare(req, res, stream) for req, res in zip(reqs, ress)]
+            stream.synchronize()
+            t_mesh = (clk() - t) / len(reqs)
+            t = clk()
+            systems = assemble_batch([p[1] for p in preps], [self._params(r) for r in reqs], [p[2] for p in preps],
+                                     stream=stream)
+            stream.synchronize()
+            t_asm = clk() - t
+        conts = []
+        for req, res, slot, (key, mesh, _, g), S in zip(reqs, ress, slots, preps, systems):
+            res.t_mesh, res.t_assemble, res.batched = t_mesh, t_asm, True
+            conts.append(functools.partial(self._solve_finish, req, res, slot, key, mesh, g, S))
+        return conts
 
     # ---- the loop -------------------------------------------------------------------------
     def run(self, requests: list[Request], realtime: bool = True) -> Stats:
@@ -294,12 +351,10 @@ class Server:
         t0 = self.clock()
         nxt = 0
 
-        def worker(req, slot):
+        def finish(req, slot, err=None):
             res = results[req.id]
-            try:
-                self.execute(req, res, slot)
-            except Exception as e:  # a failed request is reported, the loop goes on
-                res.error = f"{type(e).__name__}: {e}"
+            if err is not None:
+                res.error = err
             res.done = self.clock() - t0
             with cv:
                 self.budget.used -= req.est_bytes
@@ -307,13 +362,52 @@ class Server:
                 del inflight[req.id]
                 cv.notify_all()
 
+        def worker(req, slot):
+            try:
+                self.execute(req, results[req.id], slot)
+            except Exception as e:  # a failed request is reported, the loop goes on
+                finish(req, slot, f"{type(e).__name__}: {e}")
+                return
+            finish(req, slot)
+
+        def run_one(req, slot, cont):
+            try:
+                cont()
+            except Exception as e:
+                finish(req, slot, f"{type(e).__name__}: {e}")
+                return
+            finish(req, slot)
+
+        def batch_worker(reqs, slots):
+            try:
+                conts = self.execute_batch(reqs, [results[r.id] for r in reqs], slots)
+            except Exception as e:  # the whole batch failed: each request reports it
+                for r, sl in zip(reqs, slots):
+                    finish(r, sl, f"{type(e).__name__}: {e}")
+                return
+            ths = [threading.Thread(target=run_one, args=a, daemon=True) for a in zip(reqs[1:], slots[1:], conts[1:])]
+            for th in ths:
+                th.start()
+            run_one(reqs[0], slots[0], conts[0])
+            for th in ths:
+                th.join()
+
+        def batchable(req):
+            if self.execute_batch is None:
+                return False
+            lo, hi = req.verts.min(0), req.verts.max(0)
+            area = float((hi[0] - lo[0]) * (hi[1] - lo[1]))
+            return estimate_pairs(len(req.elems), area, req.delta) < BATCH_MAX_PAIRS
+
         with cv:
             while nxt < len(order) or pending or inflight:
                 now = self.clock() - t0
                 while nxt < len(order) and (not realtime or order[nxt].arrival <= now):
                     pending.append(order[nxt])
                     nxt += 1
-                # admit in arrival order while a slot is free and the estimate fits
+                # admit in arrival order while a slot is free and the estimate fits; the small
+                # requests admitted in this pass form one batch
+                group = []
                 while pending and free_slots:
                     req = pending[0]
                     if req.est_bytes > self.budget.budget:
@@ -330,8 +424,22 @@ class Server:
                     self.budget.reserve(req.est_bytes)
                     slot = free_slots.pop()
                     results[req.id].admitted = self.clock() - t0
+                    if batchable(req):
+                        group.append((req, slot))
+                        continue
                     th = threading.Thread(target=worker, args=(req, slot), daemon=True)
                     inflight[req.id] = th
+                    th.start()
+                if len(group) == 1:
+                    req, slot = group[0]
+                    th = threading.Thread(target=worker, args=(req, slot), daemon=True)
+                    inflight[req.id] = th
+                    th.start()
+                elif group:
+                    reqs, slots = [g[0] for g in group], [g[1] for g in group]
+                    th = threading.Thread(target=batch_worker, args=(reqs, slots), daemon=True)
+                    for r in reqs:
+                        inflight[r.id] = th
                     th.start()
                 stats.max_inflight = max(stats.max_inflight, len(inflight))
                 stats.max_used_bytes = max(stats.max_used_bytes, self.budget.used)

@@ -1,5 +1,6 @@
 """Serving loop on the GPU: each result is the same alone and in the mix (bitwise: the FP32
-bulk sums are integer fixed point and each request's work is independent of the others),
+bulk sums are integer fixed point and each request's work is independent of the others; in
+the mix the requests admitted together are assembled as one batch),
 requests overlap, every solve reaches the 1e-10 FP64 relative residual, and a short Poisson
 stream completes with p50 <= p99."""
 import numpy as np
@@ -30,6 +31,7 @@ def test_same_result_alone_and_in_the_mix():
     alone = Server(slots=1, keep_values=True, cache_meshes=False).run(reqs, realtime=False)
     mix = Server(slots=4, keep_values=True, cache_meshes=False).run(reqs, realtime=False)
     assert mix.max_inflight > 1
+    assert not any(r.batched for r in alone.results) and sum(r.batched for r in mix.results) >= 2
     for a, b in zip(alone.results, mix.results):
         assert a.error is None and b.error is None, (a.error, b.error)
         assert a.rel_residual <= 1e-10 and b.rel_residual <= 1e-10

@@ -69,3 +69,69 @@ def test_estimates_grow_with_delta_and_size():
     p = estimate_pairs(720000, 1.02 ** 2, 0.01)
     assert 1.5e8 < p < 3.5e8
     assert estimate_bytes(361201, 720000, 1.02 ** 2, 0.01) > 2e10
+
+
+def _tri_req(i, arrival, nbytes):
+    v = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    e = np.array([[0, 1, 2]], dtype=np.int32)
+    return Request(id=i, arrival=arrival, verts=v, elems=e, labels=np.ones(1, dtype=np.int8), delta=0.1,
+                   est_bytes=nbytes)
+
+
+def test_requests_admitted_together_are_assembled_as_one_batch():
+    groups, singles = [], []
+    lock = threading.Lock()
+
+    def single(req, res, slot):
+        with lock:
+            singles.append(req.id)
+        res.pairs = 1
+
+    def batch(reqs, ress, slots):
+        assert len(set(slots)) == len(slots) == len(reqs) > 1
+        with lock:
+            groups.append([r.id for r in reqs])
+
+        def cont(res):
+            time.sleep(0.002)
+            res.pairs = 1
+        return [lambda res=res: cont(res) for res in ress]
+
+    # a burst of 4 at t = 0 fills the 4 slots in one pass; the later arrivals come one at a time
+    reqs = [_tri_req(i, 0.0, 10) for i in range(4)] + [_tri_req(4 + i, 0.05 + 0.02 * i, 10) for i in range(3)]
+    st = Server(budget_bytes=1000, slots=4, execute=single, execute_batch=batch).run(reqs, realtime=True)
+    assert all(r.error is None and r.pairs == 1 for r in st.results)
+    assert groups and sorted(groups[0]) == [0, 1, 2, 3]
+    assert sorted(sum(groups, []) + singles) == list(range(7))
+    assert st.max_inflight == 4
+
+
+def test_a_failed_batch_fails_its_requests_only():
+    def single(req, res, slot):
+        res.pairs = 1
+
+    def batch(reqs, ress, slots):
+        if 0 in [r.id for r in reqs]:
+            raise RuntimeError("batched assembly failed")
+        return [lambda: None for _ in reqs]
+
+    reqs = [_tri_req(i, 0.0, 10) for i in range(3)] + [_tri_req(3, 0.05, 10)]
+    st = Server(budget_bytes=1000, slots=3, execute=single, execute_batch=batch).run(reqs, realtime=True)
+    errs = {r.id: r.error for r in st.results}
+    assert all(errs[i] and "batched assembly failed" in errs[i] for i in range(3))
+    assert errs[3] is None
+
+
+def test_batching_off_runs_every_request_alone():
+    seen = []
+
+    def single(req, res, slot):
+        seen.append(req.id)
+
+    def batch(reqs, ress, slots):
+        raise AssertionError("batching is off")
+
+    reqs = [_tri_req(i, 0.0, 10) for i in range(4)]
+    st = Server(budget_bytes=1000, slots=4, execute=single, execute_batch=batch, batch=False).run(reqs,
+                                                                                                   realtime=False)
+    assert sorted(seen) == [0, 1, 2, 3] and all(r.error is None for r in st.results)
