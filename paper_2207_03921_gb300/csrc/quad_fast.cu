@@ -446,6 +446,138 @@ __device__ __noinline__ int clip_canonical(const double2* __restrict__ X, int4 t
     return n;
 }
 
+// Phase A3 for the Euclidean ball: an outer point whose FP32 decisions were not all beyond their
+// error bounds. With caps, or when every cut outer point takes the FP64 cut (geo64), the whole
+// canonical cut. Without caps the vertices relative to x_p are formed in FP64 and rounded once to
+// FP32, and each predicate whose margin exceeds its error bound (the bounds of nl_decide32, taken
+// one predicate at a time) keeps the FP32 outcome, which is the canonical one; the others are
+// taken with the canonical clip's FP64 expressions (nl_d2 and the per-edge quadratic of nl_clip,
+// the same operations in the same order, so the same outcomes): the vertex tests near the
+// circle, and the edges at such a vertex or near tangency, whose roots are snapped to the
+// vertices as the canonical clip snaps them. The other edges keep FP32 crossings. Points merge
+// where the canonical clip merges them: one vertex pushed twice in a row, or last and first the
+// same vertex (a crossing never coincides with a vertex: its parameter is at least 1e-12 away).
+// On grids with delta a multiple of h most such outer points have one vertex on the circle, so
+// one vertex test and two edges run in FP64 instead of the whole canonical cut. One call site in
+// the kernel for both cases, and the same arguments as the canonical cut.
+// mode: 0 canonical without caps, 1 canonical with caps, 2 mixed (without caps)
+__device__ __noinline__ int clip_job(const double2* __restrict__ X, int4 tk, int4 tl, double o0, double o1,
+                                     double o2, double delta, double delta2, int mode, float2* dst, int maxp) {
+    if (mode != 2) return clip_canonical(X, tk, tl, o0, o1, o2, delta, delta2, mode == 1, dst, maxp);
+    const double2 Vl[3] = {X[tl.x], X[tl.y], X[tl.z]};
+    // x_p as nl_map forms it; at a vertex of E_k (barycentrics 1, 0, 0 in some order) that sum is
+    // the vertex itself (up to the sign of a zero coordinate, which no product, square or
+    // comparison below can see)
+    // (tested on the bit patterns, so that the test costs no FP64 instructions)
+    const long long b0 = __double_as_longlong(o0), b1 = __double_as_longlong(o1), b2 = __double_as_longlong(o2);
+    const long long one = 0x3FF0000000000000ll;
+    double2 xp;
+    if (b0 == one && b1 == 0 && b2 == 0) xp = X[tk.x];
+    else if (b1 == one && b0 == 0 && b2 == 0) xp = X[tk.y];
+    else if (b2 == one && b0 == 0 && b1 == 0) xp = X[tk.z];
+    else {
+        const double2 Vk[3] = {X[tk.x], X[tk.y], X[tk.z]};
+        xp = nl_map(Vk, o0, o1, o2);
+    }
+    float Rx[3], Ry[3], C[3];
+    bool dec[3], ins[3];
+    float rmax = 0.f;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        Rx[m] = (float)(Vl[m].x - xp.x);
+        Ry[m] = (float)(Vl[m].y - xp.y);
+        rmax = fmaxf(rmax, fmaxf(fabsf(Rx[m]), fabsf(Ry[m])));
+    }
+    // each component is the FP64 difference rounded once: within 2^-24 of its value, plus the
+    // FP64 rounding of x_p and of the difference (far below); 2^-23 of the largest covers both
+    const float eps = 1.2e-7f * rmax;
+    const float d2 = (float)delta2, floor2 = 1e-5f * d2;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        C[m] = Rx[m] * Rx[m] + Ry[m] * Ry[m] - d2;
+        dec[m] = fabsf(C[m]) > floor2 + 2.f * (fabsf(Rx[m]) + fabsf(Ry[m])) * eps;
+        ins[m] = dec[m] ? C[m] < 0.f : nl_d2(Vl[m], xp) <= delta2;
+    }
+    if (ins[0] && ins[1] && ins[2]) {
+        dst[0] = make_float2(0.f, 0.f);
+        dst[FAST_THREADS] = make_float2(1.f, 0.f);
+        dst[2 * FAST_THREADS] = make_float2(0.f, 1.f);
+        return 3;
+    }
+    const float vb1[3] = {0.f, 1.f, 0.f}, vb2[3] = {0.f, 0.f, 1.f};
+    int n = 0, last = -2, first = -2;  // kind of a point: its vertex index, or -1 for a crossing
+    auto put = [&](int kind, float b1, float b2) {
+        if (kind >= 0 && kind == last) return;
+        if (n < maxp) dst[n * FAST_THREADS] = make_float2(b1, b2);
+        if (n == 0) first = kind;
+        last = kind;
+        ++n;
+    };
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int b = (e + 1) % 3;
+        const float d1 = vb1[b] - vb1[e], d2e = vb2[b] - vb2[e];
+        if (ins[e]) put(e, vb1[e], vb2[e]);
+        const bool one = ins[e] != ins[b], out2 = !ins[e] && !ins[b];
+        // the FP32 quadratic of the edge, as nl_decide32 forms it (u from the relative vertices)
+        const float ux = Rx[b] - Rx[e], uy = Ry[b] - Ry[e];
+        const float Aq = ux * ux + uy * uy;
+        const float Bq = Rx[e] * ux + Ry[e] * uy;
+        const float Cq = C[e];
+        const float disc = Bq * Bq - Aq * Cq;
+        bool f32 = dec[e] && dec[b];
+        if (f32 && out2) {
+            const float e1n = fabsf(Rx[e]) + fabsf(Ry[e]), u1n = fabsf(ux) + fabsf(uy);
+            const float bound = 2.f * fabsf(Bq) * (u1n + 2.f * e1n) * eps + Aq * (2.f * e1n * eps + 1e-6f * d2) +
+                                fabsf(Cq) * 4.f * u1n * eps + 1e-6f * (Bq * Bq + fabsf(Aq * Cq));
+            f32 = fabsf(disc) > bound;
+        }
+        if (f32) {
+            // the roots as decide_flat forms them (the vertex of the quadratic in (0, 1) tested as
+            // 0 < -B < A)
+            const float sq = sqrtf(fmaxf(disc, 0.f));
+            const float iA = __fdividef(1.f, Aq);
+            const float lo = (-Bq - sq) * iA, hi = (-Bq + sq) * iA;
+            if (one) {
+                const float t = ins[e] ? hi : lo;
+                put(-1, fmaf(t, d1, vb1[e]), fmaf(t, d2e, vb2[e]));
+            } else if (out2 && disc > 0.f && Bq < 0.f && -Bq < Aq) {
+                put(-1, fmaf(lo, d1, vb1[e]), fmaf(lo, d2e, vb2[e]));
+                put(-1, fmaf(hi, d1, vb1[e]), fmaf(hi, d2e, vb2[e]));
+            }
+        } else {
+            const double2 A_ = Vl[e], B_ = Vl[b];
+            const double uxd = __dsub_rn(B_.x, A_.x), uyd = __dsub_rn(B_.y, A_.y);
+            const double ex = __dsub_rn(A_.x, xp.x), ey = __dsub_rn(A_.y, xp.y);
+            const double A = __dadd_rn(__dmul_rn(uxd, uxd), __dmul_rn(uyd, uyd));
+            const double B = __dadd_rn(__dmul_rn(ex, uxd), __dmul_rn(ey, uyd));
+            const double Cd = __dsub_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), delta2);
+            const double dd = __dsub_rn(__dmul_rn(B, B), __dmul_rn(A, Cd));
+            if (dd > 0.0) {
+                const double r = __dsqrt_rn(dd);
+                const double ts[2] = {__ddiv_rn(__dsub_rn(-B, r), A), __ddiv_rn(__dadd_rn(-B, r), A)};
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const double t = ts[j];
+                    if (!(t > 0.0 && t < 1.0)) continue;
+                    if (t < NLFEM_TAU) {
+                        put(e, vb1[e], vb2[e]);
+                    } else if (t > 1.0 - NLFEM_TAU) {
+                        put(b, vb1[b], vb2[b]);
+                    } else {  // a crossing: its position rounded to FP32
+                        const float tf = (float)t;
+                        const float c1 = (e == 1 ? 1.f - tf : 0.f) + (b == 1 ? tf : 0.f);
+                        const float c2 = (e == 2 ? 1.f - tf : 0.f) + (b == 2 ? tf : 0.f);
+                        put(-1, c1, c2);
+                    }
+                }
+            }
+        }
+    }
+    if (n >= 2 && last >= 0 && last == first) --n;
+    return n < 3 ? 0 : min(n, maxp);
+}
+
 // Infinity ball: the canonical FP64 cut of one outer point, its points mapped to barycentric
 // coordinates of E_l in FP64 and rounded once
 __device__ __noinline__ int clip_square_f32(const double2* __restrict__ X, int4 tk, int4 tl, double o0, double o1,
@@ -559,8 +691,9 @@ __device__ __noinline__ int clip_square_fast(const float Rx[3], const float Ry[3
 // outside that edge: then no edge reaches the ball), each test taken only beyond its FP32 error
 // bound. The other outer points are cut, not all lanes have one, so they go to a per-warp job
 // list: phase A2 cuts them one per lane and round, writing the polygon into the owner's slots,
-// and jobs whose decisions are too close to call go to a second list that phase A3 cuts in FP64
-// with the canonical routine (with geo64 every cut outer point does). Polygon points are
+// and jobs whose decisions are too close to call go to a second list for phase A3, which takes
+// the undecided predicates with the canonical FP64 expressions (cut_mixed; the infinity ball and
+// geo64, where every cut outer point goes there, take the whole canonical cut). Polygon points are
 // barycentric coordinates of E_l; 4 bits per outer point record their number. Phase B drains
 // the fan triangles: each iteration integrates one triangle per lane, walking through the lane's
 // outer points in order, and applies that triangle's inner sums with its outer point's factors.
@@ -884,7 +1017,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                     if (act) s_cnt[(wbase + owner) * CHUNK + q] = (unsigned char)(und || n < 3 ? 0 : n);
                 }
                 __syncwarp();
-                // ---- phase A3: the canonical FP64 cuts, one per lane
+                // ---- phase A3: the undecided predicates in FP64 (or the canonical cut), one job per lane
                 for (int jj = lane; jj < n64; jj += 32) {
                     const int code = s_job64[wbase * CHUNK + jj];
                     const int owner = code >> 3, q = code & 7, q0 = qb + q;
@@ -892,8 +1025,8 @@ __global__ void __launch_bounds__(FAST_THREADS, 4) k_trunc_cut(const __grid_cons
                     const int4 tkj = Q.T[s_k[wbase + owner]], tlj = Q.T[s_l[wbase + owner]];
                     const int n = SQUARE ? clip_square_f32(Q.X, tkj, tlj, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2],
                                                            Q.delta64, dst)
-                                         : clip_canonical(Q.X, tkj, tlj, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2],
-                                                          Q.delta64, Q.delta2_64, CAPS, dst, MAXP);
+                                         : clip_job(Q.X, tkj, tlj, R.ro[q0][0], R.ro[q0][1], R.ro[q0][2],
+                                                    Q.delta64, Q.delta2_64, CAPS ? 1 : (Q.geo64 ? 0 : 2), dst, MAXP);
                     s_cnt[(wbase + owner) * CHUNK + q] = (unsigned char)(n < 3 ? 0 : n);
                 }
                 __syncwarp();
