@@ -16,9 +16,13 @@ namespace nlfem {
 
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// Uniform grid over the element centroids. A partner's centroid lies within reach + r_k + r_l
+// of the element's centroid, at most span cells away in each direction (cells of at least
+// (reach + 2 r_max) / span).
 struct Grid {
     double x0, y0, cs;
     int nx, ny;
+    int span;
 };
 
 __global__ void k_bin_count(const double2* cen, int64_t K, Grid g, int64_t* cnt, int* cell_of) {
@@ -61,6 +65,7 @@ struct SearchArgs {
     const int* cell_list;
     Grid g;
     int64_t K;
+    double reach, rmax;  // search radius (delta, or sqrt(2) delta for the infinity ball), largest element radius
     double delta, delta2;
     int caps;
     int ball;
@@ -192,12 +197,22 @@ __global__ void __launch_bounds__(128) k_search(SearchArgs a, int64_t* count, co
         __syncwarp();
         qn = rest;
     };
-    for (int dyc = -1; dyc <= 1; ++dyc) {
+    // with span > 1, cells whose rectangle lies farther than reach + r_k + r_max from the centroid
+    // are skipped: the distance is taken in cell units in FP32 on the centroid's position inside
+    // its cell, with a margin of 1e-3 cells (far above the FP32 error of numbers below span + 1)
+    const int S = a.g.span;
+    const double ics = 1.0 / a.g.cs;
+    const float fx = (float)((ck.x - a.g.x0) * ics - cx), fy = (float)((ck.y - a.g.y0) * ics - cy);
+    const float lim = (float)((a.reach + rk + a.rmax) * (1.0 + 1e-6) * ics) + 1e-3f;
+    for (int dyc = -S; dyc <= S; ++dyc) {
         int yy = cy + dyc;
         if (yy < 0 || yy >= a.g.ny) continue;
-        for (int dxc = -1; dxc <= 1; ++dxc) {
+        const float gy = dyc > 0 ? dyc - fy : (dyc < 0 ? fy - (dyc + 1) : 0.f);
+        for (int dxc = -S; dxc <= S; ++dxc) {
             int xx = cx + dxc;
             if (xx < 0 || xx >= a.g.nx) continue;
+            const float gx = dxc > 0 ? dxc - fx : (dxc < 0 ? fx - (dxc + 1) : 0.f);
+            if (S > 1 && gx * gx + gy * gy > lim * lim) continue;
             int c = yy * a.g.nx + xx;
             int64_t s = a.cell_start[c], e = a.cell_start[c + 1];
             for (int64_t j0 = s; j0 < e; j0 += 32) {
@@ -221,7 +236,7 @@ __global__ void __launch_bounds__(128) k_search(SearchArgs a, int64_t* count, co
     if ((!FILL || SLOTS) && lane == 0) count[k] = n;
 }
 
-// the largest number of candidates of an element (its 3 x 3 cell block)
+// the largest number of candidates of an element (its block of (2 span + 1)^2 cells)
 __global__ void k_max_cand(const int* cell_of, int64_t K, Grid g, const int64_t* cell_start,
                            unsigned long long* out) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -229,8 +244,8 @@ __global__ void k_max_cand(const int* cell_of, int64_t K, Grid g, const int64_t*
     if (k < K) {
         const int cell = cell_of[k];
         const int cx = cell % g.nx, cy = cell / g.nx;
-        for (int yy = max(cy - 1, 0); yy <= min(cy + 1, g.ny - 1); ++yy)
-            for (int xx = max(cx - 1, 0); xx <= min(cx + 1, g.nx - 1); ++xx) {
+        for (int yy = max(cy - g.span, 0); yy <= min(cy + g.span, g.ny - 1); ++yy)
+            for (int xx = max(cx - g.span, 0); xx <= min(cx + g.span, g.nx - 1); ++xx) {
                 const int c = yy * g.nx + xx;
                 n += cell_start[c + 1] - cell_start[c];
             }
@@ -362,13 +377,18 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     Grid g;
     // candidates lie within delta (sqrt(2) delta for the infinity ball) + 2 r_max of the centroid
     const double reach = prm.ball == NLFEM_BALL_INFINITY ? prm.delta * 1.4142135623730951 : prm.delta;
-    g.cs = (reach + 2.0 * m.rmax) * (1.0 + 1e-9) + 1e-300;
+    // cells of half the reach plus two radii, searched over 5 x 5 blocks less the cells out of
+    // reach: about 40% fewer candidates than 3 x 3 blocks of full-size cells
+    const double cs0 = (reach + 2.0 * m.rmax) * (1.0 + 1e-9) + 1e-300;
+    g.cs = 0.5 * cs0;
+    g.span = 2;
     double W = m.bbox[2] - m.bbox[0], H = m.bbox[3] - m.bbox[1];
     g.nx = std::max(1, (int)std::ceil(W / g.cs));
     g.ny = std::max(1, (int)std::ceil(H / g.cs));
     // cap the grid at 2^24 cells by enlarging the cells (coarser cells stay correct)
     while ((int64_t)g.nx * g.ny > (1 << 24)) {
         g.cs *= 2.0;
+        if (g.cs >= cs0) g.span = 1;
         g.nx = std::max(1, (int)std::ceil(W / g.cs));
         g.ny = std::max(1, (int)std::ceil(H / g.cs));
     }
@@ -395,6 +415,8 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     a.cell_start = cstart.p; a.cell_list = clist.p; a.g = g; a.K = K;
     a.delta = prm.delta; a.delta2 = prm.delta2; a.caps = prm.ball == NLFEM_BALL_APPROXCAPS; a.ro = prm.ro;
     a.ball = prm.ball;
+    a.reach = reach;
+    a.rmax = m.rmax;
     a.Tp = m.tpos();
     a.E32 = m.E32.p;
     for (int i = 0; i < 16; ++i) {
@@ -757,6 +779,7 @@ extern "C" int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t
         Grid g;
         const double reach = ball == NLFEM_BALL_INFINITY ? delta * 1.4142135623730951 : delta;
         g.cs = (reach + 2.0 * hs[0]) * (1.0 + 1e-9) + 1e-300;
+        g.span = 1;
         const double W = hs[3] - hs[1], H = hs[4] - hs[2];
         g.nx = std::max(1, (int)std::ceil(W / g.cs));
         g.ny = std::max(1, (int)std::ceil(H / g.cs));
@@ -780,6 +803,7 @@ extern "C" int nlfem_pairs_noalloc(const double* verts, int64_t M, const int32_t
         SearchArgs a;
         a.X = X; a.T = T; a.cen = cen; a.rad = rad; a.cell_of = cell_of; a.cell_start = cstart; a.cell_list = clist;
         a.g = g; a.K = K; a.delta = delta; a.delta2 = delta * delta; a.caps = ball == NLFEM_BALL_APPROXCAPS;
+        a.reach = reach; a.rmax = hs[0];
         a.ball = ball;
         a.Tp = T;
         a.ro.n = quad_outer;
