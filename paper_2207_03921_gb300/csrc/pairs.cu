@@ -294,63 +294,117 @@ __global__ void k_fill_T(const int* pl, int64_t P, const int64_t* tptr, int* cur
     tid[tptr[l] + pos] = (int)p;
 }
 
-__global__ void k_flag_duffy(const int8_t* cls, int64_t P, int std_close, int64_t* flag) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < P) flag[p] = cls[p] > 0 && !std_close;
-}
-
-// Pairs on the standard rule (separated pairs, and intersecting pairs when the close rule
-// is the standard one) split by whether the inner element lies in the ball of every point
-// of the outer element: the largest vertex-to-vertex distance is below delta with a
-// relative margin of 1e-6 (far above FP64 rounding), so the canonical clip finds all three
-// vertices inside at every outer point. flag_whole / flag_cut select the two lists.
-// For the infinity ball the same test runs on the largest coordinate difference against delta.
-__global__ void k_flag_whole(const int* pk, const int* pl, const int8_t* cls, int64_t P, const double2* X,
-                             const int4* T, const ElemRec* rec, double delta2, int std_close, int64_t* flag_whole,
-                             int64_t* flag_cut, int inf = 0, double delta = 0.0) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    int64_t w = 0, c = 0;
-    if (cls[p] == 0 || std_close) {
-        const int k = pk[p], l = pl[p];
-        const ElemRec rk = rec[k], rl = rec[l];
-        // vertices relative to vertex 0 of E_k in FP32 (the offset rounded once from FP64, the
-        // edge vectors as stored): decided there unless within 1e-4 of the threshold, then from
-        // the FP64 vertices
-        const float ox = (float)(rl.v0.x - rk.v0.x), oy = (float)(rl.v0.y - rk.v0.y);
-        const float kx[3] = {0.f, rk.E.x, rk.E.z}, ky[3] = {0.f, rk.E.y, rk.E.w};
-        const float lx[3] = {ox, ox + rl.E.x, ox + rl.E.z}, ly[3] = {oy, oy + rl.E.y, oy + rl.E.w};
-        float mxf = 0.f;
+// The work lists of the quadrature: every pair goes to exactly one of them. Close list (bit 2):
+// intersecting pairs under the singular or the diamond rule. The other pairs take the standard
+// rule, split by whether the inner element lies in the ball of every point of the outer
+// element: whole (bit 0), when the largest vertex-to-vertex distance is below delta with a
+// relative margin of 1e-6 (far above FP64 rounding, so the canonical clip finds all three
+// vertices inside at every outer point), else cut (bit 1). For the infinity ball the same test
+// runs on the largest coordinate difference against delta.
+__device__ __forceinline__ int pair_list(int64_t p, const int* pk, const int* pl, const int8_t* cls, const double2* X,
+                                         const int4* T, const ElemRec* rec, double delta2, int std_close, int inf,
+                                         double delta) {
+    if (cls[p] != 0 && !std_close) return 4;
+    const int k = pk[p], l = pl[p];
+    const ElemRec rk = rec[k], rl = rec[l];
+    // vertices relative to vertex 0 of E_k in FP32 (the offset rounded once from FP64, the edge
+    // vectors as stored): decided there unless within 1e-4 of the threshold, then from the FP64
+    // vertices
+    const float ox = (float)(rl.v0.x - rk.v0.x), oy = (float)(rl.v0.y - rk.v0.y);
+    const float kx[3] = {0.f, rk.E.x, rk.E.z}, ky[3] = {0.f, rk.E.y, rk.E.w};
+    const float lx[3] = {ox, ox + rl.E.x, ox + rl.E.z}, ly[3] = {oy, oy + rl.E.y, oy + rl.E.w};
+    float mxf = 0.f;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const float dx = lx[j] - kx[i], dy = ly[j] - ky[i];
+            mxf = fmaxf(mxf, inf ? fmaxf(fabsf(dx), fabsf(dy)) : dx * dx + dy * dy);
+        }
+    const float thr = (float)((inf ? delta : delta2) * (1.0 - 1e-6));
+    bool whole;
+    if (mxf < thr * (1.f - 1e-4f)) whole = true;
+    else if (mxf > thr * (1.f + 1e-4f)) whole = false;
+    else {
+        const int4 a = T[k], b = T[l];
+        const double2 va[3] = {X[a.x], X[a.y], X[a.z]}, vb[3] = {X[b.x], X[b.y], X[b.z]};
+        double mx = 0.0;
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) {
-                const float dx = lx[j] - kx[i], dy = ly[j] - ky[i];
-                mxf = fmaxf(mxf, inf ? fmaxf(fabsf(dx), fabsf(dy)) : dx * dx + dy * dy);
+                const double dx = vb[j].x - va[i].x, dy = vb[j].y - va[i].y;
+                mx = fmax(mx, inf ? fmax(fabs(dx), fabs(dy)) : dx * dx + dy * dy);
             }
-        const float thr = (float)((inf ? delta : delta2) * (1.0 - 1e-6));
-        bool whole;
-        if (mxf < thr * (1.f - 1e-4f)) whole = true;
-        else if (mxf > thr * (1.f + 1e-4f)) whole = false;
-        else {
-            const int4 a = T[k], b = T[l];
-            const double2 va[3] = {X[a.x], X[a.y], X[a.z]}, vb[3] = {X[b.x], X[b.y], X[b.z]};
-            double mx = 0.0;
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) {
-                    const double dx = vb[j].x - va[i].x, dy = vb[j].y - va[i].y;
-                    mx = fmax(mx, inf ? fmax(fabs(dx), fabs(dy)) : dx * dx + dy * dy);
-                }
-            whole = mx <= (inf ? delta : delta2) * (1.0 - 1e-6);
-        }
-        if (whole) w = 1;
-        else c = 1;
+        whole = mx <= (inf ? delta : delta2) * (1.0 - 1e-6);
     }
-    flag_whole[p] = w;
-    flag_cut[p] = c;
+    return whole ? 1 : 2;
 }
 
-__global__ void k_compact_duffy(const int64_t* flag, const int64_t* pos, int64_t P, int* ids) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < P && flag[p]) ids[pos[p]] = (int)p;
+// Ordered compaction of the three lists in two passes over blocks of LIST_BLOCK pairs: the
+// first writes each pair's list (one byte) and every block's count per list, the counts are
+// scanned, the second writes the pair ids at the block's offsets in pair order.
+static constexpr int LIST_THREADS = 256;
+static constexpr int LIST_BLOCK = 4 * LIST_THREADS;
+
+__global__ void __launch_bounds__(LIST_THREADS) k_list_flags(const int* pk, const int* pl, const int8_t* cls,
+                                                             int64_t P, const double2* X, const int4* T,
+                                                             const ElemRec* rec, double delta2, int std_close,
+                                                             int inf, double delta, int8_t* code, int64_t* bcount) {
+    __shared__ int sc[3];
+    if (threadIdx.x < 3) sc[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * LIST_BLOCK;
+    int c0 = 0, c1 = 0, c2 = 0;
+    for (int j = 0; j < 4; ++j) {
+        const int64_t p = base + j * LIST_THREADS + threadIdx.x;
+        if (p >= P) continue;
+        const int c = pair_list(p, pk, pl, cls, X, T, rec, delta2, std_close, inf, delta);
+        code[p] = (int8_t)c;
+        c0 += c & 1;
+        c1 += (c >> 1) & 1;
+        c2 += (c >> 2) & 1;
+    }
+    c0 = __reduce_add_sync(0xffffffffu, c0);
+    c1 = __reduce_add_sync(0xffffffffu, c1);
+    c2 = __reduce_add_sync(0xffffffffu, c2);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sc[0], c0);
+        atomicAdd(&sc[1], c1);
+        atomicAdd(&sc[2], c2);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) bcount[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = sc[threadIdx.x];
+}
+
+// boff: [3][nb + 1] exclusive scans of the block counts; out[i]: list i (whole, cut, close)
+__global__ void __launch_bounds__(LIST_THREADS) k_list_fill(const int8_t* code, int64_t P, const int64_t* boff,
+                                                            int* out0, int* out1, int* out2) {
+    __shared__ int wsum[3][LIST_THREADS / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nb1 = (int64_t)gridDim.x + 1;
+    int64_t off[3] = {boff[blockIdx.x], boff[nb1 + blockIdx.x], boff[2 * nb1 + blockIdx.x]};
+    int* out[3] = {out0, out1, out2};
+    const int64_t base = (int64_t)blockIdx.x * LIST_BLOCK;
+    for (int j = 0; j < 4; ++j) {
+        // pairs base + j * LIST_THREADS + t, in order of t: a warp's ballot, then the warps' prefix
+        const int64_t p = base + j * LIST_THREADS + threadIdx.x;
+        const int c = p < P ? code[p] : 0;
+        unsigned m[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            m[i] = __ballot_sync(0xffffffffu, (c >> i) & 1);
+            if (lane == 0) wsum[i][warp] = __popc(m[i]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            int before = 0, total = 0;
+            for (int w = 0; w < LIST_THREADS / 32; ++w) {
+                before += w < warp ? wsum[i][w] : 0;
+                total += wsum[i][w];
+            }
+            if ((c >> i) & 1) out[i][off[i] + before + __popc(m[i] & ((1u << lane) - 1u))] = (int)p;
+            off[i] += total;
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void k_max_seg64(const int64_t* ptr, int64_t n, unsigned long long* out) {
@@ -500,48 +554,38 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
     for (int i = 0; i < 4; ++i) pc.counts[i] = (int64_t)hc[i];
 
-    // standard-rule pairs split into wholly-inside pairs and the rest (the bulk kernels' work lists)
-    pc.nwhole = pc.ncut = 0;
+    // the work lists: whole and cut standard-rule pairs (the bulk kernels), intersecting pairs
+    // under the singular rule (k_duffy) or the diamond rule (canonical k_trunc)
+    pc.nwhole = pc.ncut = pc.nduffy = 0;
     pc.whole_ids.release();
     pc.cut_ids.release();
-    if (P) {
-        DBuf<int64_t> fw, fc, pw, pcut;
-        fw.alloc(P, st);
-        fc.alloc(P, st);
-        pw.alloc(P + 1, st);
-        pcut.alloc(P + 1, st);
-        k_flag_whole<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, pc.pcls.p, P, m.X.p, m.T.p, m.rec.p,
-                                                   prm.delta2, close_mode(prm) == 0, fw.p, fc.p,
-                                                   prm.ball == NLFEM_BALL_INFINITY, prm.delta);
-        NLFEM_LAUNCH_CHECK();
-        exclusive_scan_i64(fw.p, pw.p, P, st);
-        exclusive_scan_i64(fc.p, pcut.p, P, st);
-        NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.nwhole, pw.p + P, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        NLFEM_CUDA_TRY(cudaMemcpyAsync(&pc.ncut, pcut.p + P, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
-        pc.whole_ids.alloc(pc.nwhole, st);
-        pc.cut_ids.alloc(pc.ncut, st);
-        k_compact_duffy<<<nblk(P, 256), 256, 0, st>>>(fw.p, pw.p, P, pc.whole_ids.p);
-        k_compact_duffy<<<nblk(P, 256), 256, 0, st>>>(fc.p, pcut.p, P, pc.cut_ids.p);
-        NLFEM_LAUNCH_CHECK();
-    }
-
-    // intersecting pairs under the singular rule (k_duffy) or the diamond rule (canonical k_trunc)
-    pc.nduffy = 0;
     pc.duffy_ids.release();
     if (P) {
-        DBuf<int64_t> flag, pos;
-        flag.alloc(P, st);
-        pos.alloc(P + 1, st);
-        k_flag_duffy<<<nblk(P, 256), 256, 0, st>>>(pc.pcls.p, P, close_mode(prm) == 0, flag.p);
+        const int64_t nb = (P + LIST_BLOCK - 1) / LIST_BLOCK;
+        DBuf<int8_t> code;
+        DBuf<int64_t> bcount, boff;
+        code.alloc(P, st);
+        bcount.alloc(3 * nb, st);
+        boff.alloc(3 * (nb + 1), st);
+        k_list_flags<<<(unsigned)nb, LIST_THREADS, 0, st>>>(pc.pk.p, pc.pl.p, pc.pcls.p, P, m.X.p, m.T.p, m.rec.p,
+                                                            prm.delta2, close_mode(prm) == 0,
+                                                            prm.ball == NLFEM_BALL_INFINITY, prm.delta, code.p,
+                                                            bcount.p);
         NLFEM_LAUNCH_CHECK();
-        exclusive_scan_i64(flag.p, pos.p, P, st);
-        int64_t nd = 0;
-        NLFEM_CUDA_TRY(cudaMemcpyAsync(&nd, pos.p + P, sizeof nd, cudaMemcpyDeviceToHost, st));
+        for (int i = 0; i < 3; ++i) exclusive_scan_i64(bcount.p + i * nb, boff.p + i * (nb + 1), nb, st);
+        int64_t tot[3];
+        for (int i = 0; i < 3; ++i)
+            NLFEM_CUDA_TRY(cudaMemcpyAsync(&tot[i], boff.p + i * (nb + 1) + nb, sizeof(int64_t),
+                                           cudaMemcpyDeviceToHost, st));
         NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
-        pc.nduffy = nd;
-        pc.duffy_ids.alloc(nd, st);
-        k_compact_duffy<<<nblk(P, 256), 256, 0, st>>>(flag.p, pos.p, P, pc.duffy_ids.p);
+        pc.nwhole = tot[0];
+        pc.ncut = tot[1];
+        pc.nduffy = tot[2];
+        pc.whole_ids.alloc(pc.nwhole, st);
+        pc.cut_ids.alloc(pc.ncut, st);
+        pc.duffy_ids.alloc(pc.nduffy, st);
+        k_list_fill<<<(unsigned)nb, LIST_THREADS, 0, st>>>(code.p, P, boff.p, pc.whole_ids.p, pc.cut_ids.p,
+                                                           pc.duffy_ids.p);
         NLFEM_LAUNCH_CHECK();
     }
 }
