@@ -43,6 +43,9 @@ WORKLOADS = {
     "cfg5": dict(mesh="cfg5", kernel="constant", delta=0.01, ball="nocaps", quad_outer=7, quad_inner=7,
                  desc="structured h=0.002 on [-0.01,1.01]^2 (520,200 triangles), constant kernel, delta=0.01, "
                       "nocaps, 7-point rules"),
+    "cfg5_small": dict(mesh="s204", kernel="constant", delta=0.025, ball="nocaps", quad_outer=7, quad_inner=7,
+                       desc="structured 204x204 cells on [-0.01,1.01]^2 (83,232 triangles, h=0.005), constant "
+                            "kernel, delta=0.025=5h (the ties of configuration 5), nocaps, 7-point rules"),
     "cfg2": dict(mesh="cfg2", kernel="fractional", s=0.5, delta=0.1, ball="approxcaps", quad_outer=16,
                  quad_inner=16,
                  desc="jittered Delaunay h=0.01 on [-0.1,1.1]^2 (~29k triangles), fractional s=0.5, delta=0.1, "
@@ -81,6 +84,8 @@ def make_mesh(name):
     from synth import meshes
     if name == "s200":
         return meshes.structured(-0.01, 1.01, 200, name="structured200")
+    if name == "s204":
+        return meshes.structured(-0.01, 1.01, 204, name="structured204")
     if name == "paper_e5":
         return meshes.paper_square(0.2, 0.00625)
     if name == "paper_e5_jit":
