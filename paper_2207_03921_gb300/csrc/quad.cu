@@ -93,7 +93,10 @@ __device__ __forceinline__ int sym3(int a, int b) {  // index of (a, b) in a pac
     return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
 }
 
-template <typename R, int KER, int NQI>
+// WHOLE: a list of pairs whose inner element lies in the ball of every point of the outer
+// element (decided with a margin far above FP64 rounding when the lists are built), for which
+// the canonical clip returns the whole element at every outer point: the clip is not called.
+template <typename R, int KER, int NQI, bool WHOLE = false>
 __global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contrib) {
     constexpr int NC = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? 3 : 1;
     constexpr int NS = (KER == NLFEM_KERNEL_PERIDYNAMIC) ? NLFEM_REC2 : NLFEM_REC1;  // record stride
@@ -122,8 +125,8 @@ __global__ void __launch_bounds__(128) k_trunc(QuadArgs A, R* __restrict__ contr
         for (int q0 = 0; q0 < P.ro.n; ++q0) {
             const double2 xp = nl_map(Vk, P.ro.l[q0][0], P.ro.l[q0][1], P.ro.l[q0][2]);
             CPt poly[NLFEM_MAXPOLY];
-            bool full;
-            const int np = nl_clip_ball(P.ball, Vl, xp, P.delta, P.delta2, poly, full);
+            bool full = true;
+            const int np = WHOLE ? 3 : nl_clip_ball(P.ball, Vl, xp, P.delta, P.delta2, poly, full);
             if (np < 3) continue;
             // inner sums for this x_p: g = sum w, h_j = sum w Q_j, m_ij = sum w Q_i Q_j
             R g[NC], h[3][NC], mm[6][NC];
@@ -675,13 +678,13 @@ __global__ void k_load(int64_t M, int ndof, const int* ne_ptr, const int* ne_idx
     }
 }
 
-template <typename R>
+template <typename R, bool WHOLE = false>
 static void launch_trunc(const QuadArgs& a, R* out, cudaStream_t st) {
     const int NQI = a.prm.ri.n;
     const int K = a.prm.kernel;
     unsigned grid = (unsigned)std::min<int64_t>(nblk(a.npairs, 128), 152 * 64);
     if (grid == 0) return;
-#define NLFEM_TR(KK, NQ) k_trunc<R, KK, NQ><<<grid, 128, 0, st>>>(a, out)
+#define NLFEM_TR(KK, NQ) k_trunc<R, KK, NQ, WHOLE><<<grid, 128, 0, st>>>(a, out)
     if (K == NLFEM_KERNEL_CONSTANT) {
         if (NQI == 7) NLFEM_TR(NLFEM_KERNEL_CONSTANT, 7); else NLFEM_TR(NLFEM_KERNEL_CONSTANT, 16);
     } else if (K == NLFEM_KERNEL_FRACTIONAL) {
@@ -1032,12 +1035,24 @@ void run_quadrature(Mesh& m, PairCache& pc, const Params& prm, System& sys, cuda
         run_bulk(m, pc, prm, sys, st, ev);
         return;
     }
-    // FP64 plain: all pairs in the canonical kernel (reported as the cut-pair time), then
-    // the singular rule on the close list
+    // FP64 plain: the canonical kernel over the whole-pair list (no clip), the cut-pair list and,
+    // under the diamond rule, the close list (reported together as the cut-pair time; every
+    // list's warps then do the same kind of work), then the singular rule on the close list.
+    // Records go to each pair's id, so the reduction does not depend on the split.
     NLFEM_CUDA_TRY(cudaEventRecord(ev[2], st));
     NLFEM_CUDA_TRY(cudaEventRecord(ev[3], st));
-    QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.npairs, nullptr, 0, m.X.p, m.T.p, m.det.p, prm};
-    launch_trunc<double>(a, sys.contrib64.p, st);
+    {
+        QuadArgs a{pc.pk.p, pc.pl.p, pc.pcls.p, nullptr, pc.nwhole, pc.whole_ids.p, 0, m.X.p, m.T.p, m.det.p, prm};
+        launch_trunc<double, true>(a, sys.contrib64.p, st);
+        a.npairs = pc.ncut;
+        a.ids = pc.cut_ids.p;
+        launch_trunc<double>(a, sys.contrib64.p, st);
+        if (!prm.singular && pc.nduffy > 0) {
+            a.npairs = pc.nduffy;
+            a.ids = pc.duffy_ids.p;
+            launch_trunc<double>(a, sys.contrib64.p, st);
+        }
+    }
     NLFEM_CUDA_TRY(cudaEventRecord(ev[4], st));
     NLFEM_CUDA_TRY(cudaEventRecord(ev[0], st));
     if (prm.singular && pc.nduffy > 0) launch_duffy<double>(m, pc, prm, 0, sys.contrib64.p, nullptr, st);
