@@ -224,6 +224,7 @@ struct PairCache {
     // node-level pattern
     DBuf<int64_t> nrow_ptr;  // [M + 1]
     DBuf<int> ncol;          // [nnz_node]
+    DBuf<int> ntpos;         // [nnz_node] rank of the row in the column's row (until the bulk index is built)
     int64_t nnz_node = 0;
     int max_row = 0;
     // dof-level CSR

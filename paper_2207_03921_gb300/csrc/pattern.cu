@@ -241,7 +241,7 @@ __device__ __forceinline__ int64_t find_col(const int* col, int64_t b, int64_t e
 
 // dof columns and the transpose map (thread per node-pattern entry)
 __global__ void k_expand_cols(const int64_t* nptr, const int* ncol, int64_t M, int ndof,
-                              const int64_t* row_ptr, int* col, int64_t* tpos, int* err) {
+                              const int64_t* row_ptr, int* col, int64_t* tpos, int* ntpos, int* err) {
     int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
     if (i >= M) return;
@@ -254,6 +254,7 @@ __global__ void k_expand_cols(const int64_t* nptr, const int* ncol, int64_t M, i
             atomicOr(err, 1);
             rt = 0;
         }
+        ntpos[t] = (int)rt;
         for (int c1 = 0; c1 < ndof; ++c1)
             for (int c2 = 0; c2 < ndof; ++c2) {
                 int64_t s = row_ptr[i * ndof + c1] + ndof * r + c2;
@@ -647,9 +648,10 @@ void build_pattern(Mesh& m, PairCache& pc, cudaStream_t st) {
     NLFEM_LAUNCH_CHECK();
     pc.col.alloc(pc.nnz, st);
     pc.tpos.alloc(pc.nnz, st);
+    pc.ntpos.alloc(pc.nnz_node, st);
     ovf.zero(st);
     k_expand_cols<<<nblk(M, 8), 256, 0, st>>>(pc.nrow_ptr.p, pc.ncol.p, M, nd, pc.row_ptr.p, pc.col.p, pc.tpos.p,
-                                              ovf.p);
+                                              pc.ntpos.p, ovf.p);
     NLFEM_LAUNCH_CHECK();
     {
         int h = 0;
@@ -778,21 +780,6 @@ __global__ void k_diag(const int64_t* __restrict__ nptr, const int* __restrict__
     diag[i] = (int)(a - nptr[i]);
 }
 
-// rank of column hi in the upper part of row lo with the row's diagonal position known; -1 if
-// the column is missing
-__device__ __forceinline__ int upper_rank_d(const int64_t* __restrict__ nptr, const int* __restrict__ ncol,
-                                            const int* __restrict__ diag, int lo, int hi) {
-    const int64_t b = nptr[lo] + diag[lo], e = nptr[lo + 1];
-    int64_t a = b, c = e;
-    while (a < c) {
-        const int64_t mid = (a + c) >> 1;
-        if (ncol[mid] < hi) a = mid + 1;
-        else c = mid;
-    }
-    if (a >= e || ncol[a] != hi) return -1;
-    return (int)(a - b);
-}
-
 __global__ void k_epos(const int4* __restrict__ T, int64_t K, const int64_t* __restrict__ nptr,
                        const int* __restrict__ ncol, const int64_t* __restrict__ up_start, int* __restrict__ epos,
                        int* ovf) {
@@ -812,22 +799,37 @@ __global__ void k_epos(const int4* __restrict__ T, int64_t K, const int64_t* __r
     epos[k * 8 + 6] = epos[k * 8 + 7] = 0;
 }
 
+// kl ranks of a list: for node pair (x, y) = (vertex a of E_k, vertex b of E_l) the rank of the
+// larger node in the upper part of the smaller one's row. Both cases search y in row x, which
+// the warp's pairs (most of them with the same E_k) share: rank = position - diag[x] for y >= x,
+// and ntpos (the rank of x in row y) - diag[y] for y < x.
 __global__ void k_klr(const int* __restrict__ ids, int64_t n, const int* __restrict__ pk, const int* __restrict__ pl,
                       const int4* __restrict__ T, const int64_t* __restrict__ nptr, const int* __restrict__ ncol,
-                      const int* __restrict__ diag, uint16_t* __restrict__ klr, int* ovf) {
+                      const int* __restrict__ ntpos, const int* __restrict__ diag, uint16_t* __restrict__ klr,
+                      int* ovf) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int p = ids[i];
     const int4 a4 = T[pk[p]], b4 = T[pl[p]];
     const int kn[3] = {a4.x, a4.y, a4.z}, ln[3] = {b4.x, b4.y, b4.z};
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
+        const int x = kn[a];
+        const int64_t rb = nptr[x], re = nptr[x + 1];
         for (int b = 0; b < 3; ++b) {
-            const int x = kn[a], y = ln[b];
-            const int r = upper_rank_d(nptr, ncol, diag, min(x, y), max(x, y));
+            const int y = ln[b];
+            int64_t lo = rb, hi = re;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (ncol[mid] < y) lo = mid + 1;
+                else hi = mid;
+            }
+            int r = -1;
+            if (lo < re && ncol[lo] == y) r = y >= x ? (int)(lo - rb) - diag[x] : ntpos[lo] - diag[y];
             if (r < 0) atomicOr(ovf, 1);
             if (r > 65535) atomicOr(ovf, 2);
             klr[(int64_t)(a * 3 + b) * n + i] = (uint16_t)min(max(r, 0), 65535);
         }
+    }
 }
 
 __global__ void k_max_deg(const int* ne_ptr, int64_t M, int* out) {
@@ -851,12 +853,12 @@ void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st) {
     NLFEM_LAUNCH_CHECK();
     if (pc.nwhole > 0) {
         k_klr<<<nblk(pc.nwhole, 256), 256, 0, st>>>(pc.whole_ids.p, pc.nwhole, pc.pk.p, pc.pl.p, m.T.p, pc.nrow_ptr.p,
-                                                    pc.ncol.p, diag.p, pc.klr_whole.p, ovf.p);
+                                                    pc.ncol.p, pc.ntpos.p, diag.p, pc.klr_whole.p, ovf.p);
         NLFEM_LAUNCH_CHECK();
     }
     if (pc.ncut > 0) {
         k_klr<<<nblk(pc.ncut, 256), 256, 0, st>>>(pc.cut_ids.p, pc.ncut, pc.pk.p, pc.pl.p, m.T.p, pc.nrow_ptr.p,
-                                                  pc.ncol.p, diag.p, pc.klr_cut.p, ovf.p);
+                                                  pc.ncol.p, pc.ntpos.p, diag.p, pc.klr_cut.p, ovf.p);
         NLFEM_LAUNCH_CHECK();
     }
     // bound on the values added into one entry: every pair with the node in E_k or in E_l
@@ -875,6 +877,7 @@ void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st) {
     NLFEM_CHECK(!(h[0] & 4), NLFEM_ERR_UNSUPPORTED, "more than 2^31 upper CSR entries");
     const int64_t maxp = std::max(max_segment_i64(pc.pair_ptr.p, K, st), max_segment_i64(pc.pT_ptr.p, K, st));
     pc.acc_terms = 3 * (int64_t)std::max(h[1], 1) * 2 * std::max<int64_t>(maxp, 1);
+    pc.ntpos.release();
 }
 
 // fixed-point upper entries -> CSR values (and their mirrors); warp per node row
