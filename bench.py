@@ -315,6 +315,17 @@ def kernel_rooflines(wl, census, info0, timed, npairs, ndof, pk, sing32):
     return kernels
 
 
+def fp64_roofline(kernels, canon64_ms, pk):
+    """The FP64 path's canonical kernel (every standard-rule pair, whole and cut) does the
+    algorithmic work of the FP32-bulk whole- and cut-pair kernels (the plan's weights), on the
+    FP64 pipe."""
+    _, fp64_peak, _ = peaks_tflops(pk)
+    flops = sum(kernels[k]["achieved"] * kernels[k]["ms"] * 1e9 for k in ("k_trunc_whole", "k_trunc_cut"))
+    achieved = flops / (canon64_ms * 1e-3) / 1e12 if canon64_ms > 0 else 0.0
+    return {"bound": "alu", "kernel": "k_trunc<double>", "ms": canon64_ms, "achieved": achieved,
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "pipe": "fp64"}
+
+
 def rel_frobenius(sa, sb):
     """||val_a - val_b|| / ||val_b|| of two systems on the same pattern (on the device)."""
     import torch
@@ -538,6 +549,7 @@ def main():
                              args.fp64_steps, 1, ws, stream)
         ms64_step = ms64 / args.fp64_steps
         quad64_ms = statistics.mean(i["ms_quadrature"] for i in infos[1:])
+        canon64_ms = statistics.mean(i["ms_cut"] for i in infos[1:])
 
     # end to end through the C ABI with host buffers: pinned verts/elems/labels/f -> mesh, assemble,
     # CSR values + load vector back to pinned host memory
@@ -630,7 +642,8 @@ def main():
                                       "cut_pairs_outer_points_per_chunk": tuned[2]}},
         "roofline": roof,
         "fp64_plain": ({"value": npairs * ws / (ms64_step * 1e-3), "ms_per_step": ms64_step,
-                        "quadrature_ms": quad64_ms, "speedup_fp32_bulk_over_fp64": ms64_step / ms_step}
+                        "quadrature_ms": quad64_ms, "speedup_fp32_bulk_over_fp64": ms64_step / ms_step,
+                        "roofline": fp64_roofline(kernels, canon64_ms, pk)}
                        if ms64_step else None),
         "breakdown_ms": {"quadrature": quad_ms, "whole_pairs": ms_whole, "cut_pairs": ms_cut,
                          "close_list": ms_close, "ll_sums": ms_sums, "to_csr": red_ms, "cold_total": cold_ms,
