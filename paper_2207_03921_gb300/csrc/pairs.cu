@@ -137,8 +137,15 @@ __device__ bool interacts_clip(const SearchArgs& a, int k, int l, const double2 
             if (rx * rx + ry * ry - a.d2f < -(floor2 + 2.f * (fabsf(rx) + fabsf(ry)) * eps)) return true;
         }
     }
+    // E_l lies in the disc of radius r_l about its centroid: an outer point farther than
+    // delta + r_l from it (beyond the FP32 error of the relative coordinates) sees no point of
+    // E_l, so its cut is empty without deciding anything
+    const float gx = (Wx[0] + Wx[1] + Wx[2]) * (1.f / 3.f), gy = (Wy[0] + Wy[1] + Wy[2]) * (1.f / 3.f);
+    const float reach = a.delta32 + (float)a.rad[l] + 8.f * eps;
+    const float reach2 = reach * reach * (1.f + 1e-5f);
     for (int p = 0; p < a.ro.n; ++p) {
         const float Xx = a.ol[p][0] * Ek.x + a.ol[p][1] * Ek.z, Xy = a.ol[p][0] * Ek.y + a.ol[p][1] * Ek.w;
+        if ((gx - Xx) * (gx - Xx) + (gy - Xy) * (gy - Xy) > reach2) continue;
         float Rx[3], Ry[3], C[3];
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
