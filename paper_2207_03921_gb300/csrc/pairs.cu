@@ -243,6 +243,108 @@ __global__ void __launch_bounds__(128) k_search(SearchArgs a, int64_t* count, co
     if ((!FILL || SLOTS) && lane == 0) count[k] = n;
 }
 
+// Ordered search. The candidates of every element of cell c are N(c): the elements of the
+// cells of c's block of (2 span + 1)^2 cells, sorted by id, once per cell. Candidate j of element
+// k owns slot k * cap + j, which receives l when the pair (k, l) interacts and -1 otherwise, at
+// whatever time its decision is taken (the queued ones later); packing the slots in order then
+// gives the partner list sorted by l, so no sort follows.
+__global__ void k_block_count(Grid g, const int64_t* cell_start, int64_t* cnt) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (int64_t)g.nx * g.ny) return;
+    const int cx = (int)(c % g.nx), cy = (int)(c / g.nx);
+    int64_t n = 0;
+    for (int yy = max(cy - g.span, 0); yy <= min(cy + g.span, g.ny - 1); ++yy)
+        for (int xx = max(cx - g.span, 0); xx <= min(cx + g.span, g.nx - 1); ++xx) {
+            const int64_t cc = (int64_t)yy * g.nx + xx;
+            n += cell_start[cc + 1] - cell_start[cc];
+        }
+    cnt[c] = n;
+}
+
+// warp per cell: the elements of its block's cells (sorted afterwards)
+__global__ void k_block_fill(Grid g, const int64_t* cell_start, const int* cell_list, const int64_t* nptr,
+                             int* nlist) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= (int64_t)g.nx * g.ny) return;
+    const int cx = (int)(c % g.nx), cy = (int)(c / g.nx);
+    int64_t o = nptr[c];
+    for (int yy = max(cy - g.span, 0); yy <= min(cy + g.span, g.ny - 1); ++yy)
+        for (int xx = max(cx - g.span, 0); xx <= min(cx + g.span, g.nx - 1); ++xx) {
+            const int64_t cc = (int64_t)yy * g.nx + xx;
+            const int64_t s = cell_start[cc], e = cell_start[cc + 1];
+            for (int64_t j = s + lane; j < e; j += 32) nlist[o + (j - s)] = cell_list[j];
+            o += e - s;
+        }
+}
+
+__global__ void __launch_bounds__(128) k_search_ordered(SearchArgs a, const int64_t* nptr, const int* nlist,
+                                                        int64_t* count, int* slots, int64_t cap) {
+    __shared__ int s_queue[4 * 64];  // launched with 128 threads: 4 warps, 64 queued candidate indices each
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= a.K) return;
+    const int4 tk = a.T[k];
+    const double2 Vk[3] = {a.X[tk.x], a.X[tk.y], a.X[tk.z]};
+    const double2 ck = a.cen[k];
+    const double rk = a.rad[k];
+    const int c = a.cell_of[k];
+    const int64_t start = nptr[c];
+    const int len = (int)(nptr[c + 1] - start);
+    int* const row = slots + k * cap;
+    int* q = s_queue + (threadIdx.x >> 5) * 64;
+    int qn = 0;  // warp-uniform
+    int64_t n = 0;
+    auto drain = [&](int cnt) {  // cut the first cnt (<= 32) queued candidates, keep the rest
+        const int j = lane < cnt ? q[lane] : 0;
+        const int l = lane < cnt ? nlist[start + j] : -1;
+        const bool ok = lane < cnt && interacts_clip(a, (int)k, l, Vk);
+        if (lane < cnt) row[j] = ok ? l : -1;
+        n += __popc(__ballot_sync(0xffffffffu, ok));
+        const int rest = qn - cnt;
+        const int v = lane < rest ? q[cnt + lane] : 0;
+        __syncwarp();
+        if (lane < rest) q[lane] = v;
+        __syncwarp();
+        qn = rest;
+    };
+    for (int j0 = 0; j0 < len; j0 += 32) {
+        const int j = j0 + lane;
+        int r = 0;
+        if (j < len) {
+            const int l = nlist[start + j];
+            r = interacts_centroid(a, (int)k, l, ck, rk);
+            if (r != 2) row[j] = r == 1 ? l : -1;
+        }
+        n += __popc(__ballot_sync(0xffffffffu, r == 1));
+        const unsigned mb = __ballot_sync(0xffffffffu, r == 2);
+        if (r == 2) q[qn + __popc(mb & ((1u << lane) - 1u))] = j;
+        qn += __popc(mb);
+        __syncwarp();
+        if (qn >= 32) drain(32);
+    }
+    while (qn > 0) drain(qn < 32 ? qn : 32);
+    if (lane == 0) count[k] = n;
+}
+
+// pack the candidate-indexed slots into the pair list (warp per element, order kept)
+__global__ void k_compact_ordered(const int* slots, int64_t K, int64_t cap, const int* cell_of, const int64_t* nptr,
+                                  const int64_t* ptr, int* out) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= K) return;
+    const int c = cell_of[k];
+    const int len = (int)(nptr[c + 1] - nptr[c]);
+    int64_t o = ptr[k];
+    for (int j0 = 0; j0 < len; j0 += 32) {
+        const int j = j0 + lane;
+        const int v = j < len ? slots[k * cap + j] : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, v >= 0);
+        if (v >= 0) out[o + __popc(m & ((1u << lane) - 1u))] = v;
+        o += __popc(m);
+    }
+}
+
 // the largest number of candidates of an element (its block of (2 span + 1)^2 cells)
 __global__ void k_max_cand(const int* cell_of, int64_t K, Grid g, const int64_t* cell_start,
                            unsigned long long* out) {
@@ -490,45 +592,83 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     DBuf<int64_t> cnt;
     cnt.alloc(K, st);
     pc.pair_ptr.alloc(K + 1, st);
-    // one pass into per-element slots when they fit (8 GB), else a count pass and a fill pass
-    int64_t cap = 0;
-    {
-        DBuf<unsigned long long> mc;
-        mc.alloc(1, st);
-        mc.zero(st);
-        k_max_cand<<<nblk(K, 256), 256, 0, st>>>(cell_of.p, K, g, cstart.p, mc.p);
-        NLFEM_LAUNCH_CHECK();
-        unsigned long long h = 0;
-        NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, mc.p, sizeof h, cudaMemcpyDeviceToHost, st));
-        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
-        cap = (int64_t)h;
-    }
-    const bool slots = K * cap * (int64_t)sizeof(int) <= ((int64_t)8 << 30);
-    DBuf<int> slot_buf;
-    if (slots) {
-        slot_buf.alloc(std::max<int64_t>(K * cap, 1), st);
-        k_search<false, true><<<nblk(K * 32, 128), 128, 0, st>>>(a, cnt.p, nullptr, slot_buf.p, cap);
-    } else {
-        k_search<false><<<nblk(K * 32, 128), 128, 0, st>>>(a, cnt.p, nullptr, nullptr);
-    }
+    // the sorted candidate list of every cell's block; when the candidate-indexed slots fit
+    // (8 GB) the search writes each partner list in order (no sort)
+    DBuf<int64_t> bcnt, nptr;
+    DBuf<int> nlist;
+    bcnt.alloc(ncell, st);
+    nptr.alloc(ncell + 1, st);
+    k_block_count<<<nblk(ncell, 256), 256, 0, st>>>(g, cstart.p, bcnt.p);
     NLFEM_LAUNCH_CHECK();
-    exclusive_scan_i64(cnt.p, pc.pair_ptr.p, K, st);
-    int64_t P = 0;
-    NLFEM_CUDA_TRY(cudaMemcpyAsync(&P, pc.pair_ptr.p + K, sizeof P, cudaMemcpyDeviceToHost, st));
+    exclusive_scan_i64(bcnt.p, nptr.p, ncell, st);
+    bcnt.release();
+    int64_t ntot = 0;
+    NLFEM_CUDA_TRY(cudaMemcpyAsync(&ntot, nptr.p + ncell, sizeof ntot, cudaMemcpyDeviceToHost, st));
     NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
-    NLFEM_CHECK(P < ((int64_t)1 << 31), NLFEM_ERR_UNSUPPORTED, "more than 2^31 element pairs");
-    pc.npairs = P;
-    pc.pl.alloc(P, st);
-    pc.pk.alloc(P, st);
-    if (slots) {
-        k_compact_slots<<<nblk(K * 32, 128), 128, 0, st>>>(slot_buf.p, K, cap, pc.pair_ptr.p, pc.pl.p);
+    const int64_t ncap = max_segment_i64(nptr.p, ncell, st);
+    const bool ordered = ntot < ((int64_t)1 << 31) && ncap <= 32768 &&
+                         K * ncap * (int64_t)sizeof(int) <= ((int64_t)8 << 30);
+    int64_t P = 0;
+    if (ordered) {
+        nlist.alloc(std::max<int64_t>(ntot, 1), st);
+        k_block_fill<<<nblk(ncell * 32, 256), 256, 0, st>>>(g, cstart.p, clist.p, nptr.p, nlist.p);
+        NLFEM_LAUNCH_CHECK();
+        segmented_sort_i32(nlist.p, nullptr, nptr.p, ncell, (int)ncap, st);
+        DBuf<int> slot_buf;
+        slot_buf.alloc(std::max<int64_t>(K * ncap, 1), st);
+        k_search_ordered<<<nblk(K * 32, 128), 128, 0, st>>>(a, nptr.p, nlist.p, cnt.p, slot_buf.p, ncap);
+        NLFEM_LAUNCH_CHECK();
+        exclusive_scan_i64(cnt.p, pc.pair_ptr.p, K, st);
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&P, pc.pair_ptr.p + K, sizeof P, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        NLFEM_CHECK(P < ((int64_t)1 << 31), NLFEM_ERR_UNSUPPORTED, "more than 2^31 element pairs");
+        pc.npairs = P;
+        pc.pl.alloc(P, st);
+        pc.pk.alloc(P, st);
+        k_compact_ordered<<<nblk(K * 32, 128), 128, 0, st>>>(slot_buf.p, K, ncap, cell_of.p, nptr.p, pc.pair_ptr.p,
+                                                             pc.pl.p);
+        NLFEM_LAUNCH_CHECK();
         slot_buf.release();
     } else {
-        k_search<true><<<nblk(K * 32, 128), 128, 0, st>>>(a, nullptr, pc.pair_ptr.p, pc.pl.p);
+        // one pass into per-element slots when they fit (8 GB), else a count pass and a fill pass
+        int64_t cap = 0;
+        {
+            DBuf<unsigned long long> mc;
+            mc.alloc(1, st);
+            mc.zero(st);
+            k_max_cand<<<nblk(K, 256), 256, 0, st>>>(cell_of.p, K, g, cstart.p, mc.p);
+            NLFEM_LAUNCH_CHECK();
+            unsigned long long h = 0;
+            NLFEM_CUDA_TRY(cudaMemcpyAsync(&h, mc.p, sizeof h, cudaMemcpyDeviceToHost, st));
+            NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+            cap = (int64_t)h;
+        }
+        const bool slots = K * cap * (int64_t)sizeof(int) <= ((int64_t)8 << 30);
+        DBuf<int> slot_buf;
+        if (slots) {
+            slot_buf.alloc(std::max<int64_t>(K * cap, 1), st);
+            k_search<false, true><<<nblk(K * 32, 128), 128, 0, st>>>(a, cnt.p, nullptr, slot_buf.p, cap);
+        } else {
+            k_search<false><<<nblk(K * 32, 128), 128, 0, st>>>(a, cnt.p, nullptr, nullptr);
+        }
+        NLFEM_LAUNCH_CHECK();
+        exclusive_scan_i64(cnt.p, pc.pair_ptr.p, K, st);
+        NLFEM_CUDA_TRY(cudaMemcpyAsync(&P, pc.pair_ptr.p + K, sizeof P, cudaMemcpyDeviceToHost, st));
+        NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
+        NLFEM_CHECK(P < ((int64_t)1 << 31), NLFEM_ERR_UNSUPPORTED, "more than 2^31 element pairs");
+        pc.npairs = P;
+        pc.pl.alloc(P, st);
+        pc.pk.alloc(P, st);
+        if (slots) {
+            k_compact_slots<<<nblk(K * 32, 128), 128, 0, st>>>(slot_buf.p, K, cap, pc.pair_ptr.p, pc.pl.p);
+            slot_buf.release();
+        } else {
+            k_search<true><<<nblk(K * 32, 128), 128, 0, st>>>(a, nullptr, pc.pair_ptr.p, pc.pl.p);
+        }
+        NLFEM_LAUNCH_CHECK();
+        int64_t mx = max_segment_i64(pc.pair_ptr.p, K, st);
+        segmented_sort_i32(pc.pl.p, nullptr, pc.pair_ptr.p, K, (int)std::min<int64_t>(mx, 1 << 30), st);
     }
-    NLFEM_LAUNCH_CHECK();
-    int64_t mx = max_segment_i64(pc.pair_ptr.p, K, st);
-    segmented_sort_i32(pc.pl.p, nullptr, pc.pair_ptr.p, K, (int)std::min<int64_t>(mx, 1 << 30), st);
     k_fill_k<<<nblk(K * 32, 256), 256, 0, st>>>(pc.pair_ptr.p, K, pc.pk.p);
     NLFEM_LAUNCH_CHECK();
 
