@@ -279,7 +279,7 @@ __global__ void k_block_fill(Grid g, const int64_t* cell_start, const int* cell_
 }
 
 __global__ void __launch_bounds__(128) k_search_ordered(SearchArgs a, const int64_t* nptr, const int* nlist,
-                                                        int64_t* count, int* slots, int64_t cap) {
+                                                        int64_t* count, int* slots, int8_t* scls, int64_t cap) {
     __shared__ int s_queue[4 * 64];  // launched with 128 threads: 4 warps, 64 queued candidate indices each
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -292,6 +292,8 @@ __global__ void __launch_bounds__(128) k_search_ordered(SearchArgs a, const int6
     const int64_t start = nptr[c];
     const int len = (int)(nptr[c + 1] - start);
     int* const row = slots + k * cap;
+    int8_t* const crow = scls + k * cap;  // the partners' classes (shared vertices, Tab. 1)
+    const int4 tpk = a.Tp[k];
     int* q = s_queue + (threadIdx.x >> 5) * 64;
     int qn = 0;  // warp-uniform
     int64_t n = 0;
@@ -300,6 +302,7 @@ __global__ void __launch_bounds__(128) k_search_ordered(SearchArgs a, const int6
         const int l = lane < cnt ? nlist[start + j] : -1;
         const bool ok = lane < cnt && interacts_clip(a, (int)k, l, Vk);
         if (lane < cnt) row[j] = ok ? l : -1;
+        if (ok) crow[j] = (int8_t)shared_count(tpk, a.Tp[l]);
         n += __popc(__ballot_sync(0xffffffffu, ok));
         const int rest = qn - cnt;
         const int v = lane < rest ? q[cnt + lane] : 0;
@@ -315,6 +318,7 @@ __global__ void __launch_bounds__(128) k_search_ordered(SearchArgs a, const int6
             const int l = nlist[start + j];
             r = interacts_centroid(a, (int)k, l, ck, rk);
             if (r != 2) row[j] = r == 1 ? l : -1;
+            if (r == 1) crow[j] = (int8_t)shared_count(tpk, a.Tp[l]);
         }
         n += __popc(__ballot_sync(0xffffffffu, r == 1));
         const unsigned mb = __ballot_sync(0xffffffffu, r == 2);
@@ -327,21 +331,38 @@ __global__ void __launch_bounds__(128) k_search_ordered(SearchArgs a, const int6
     if (lane == 0) count[k] = n;
 }
 
-// pack the candidate-indexed slots into the pair list (warp per element, order kept)
-__global__ void k_compact_ordered(const int* slots, int64_t K, int64_t cap, const int* cell_of, const int64_t* nptr,
-                                  const int64_t* ptr, int* out) {
+// pack the candidate-indexed slots into the pair list and its classes (warp per element, order
+// kept); count the pairs of every inner element (the transposed lists' lengths) and of every class
+__global__ void k_compact_ordered(const int* slots, const int8_t* scls, int64_t K, int64_t cap, const int* cell_of,
+                                  const int64_t* nptr, const int64_t* ptr, int* out, int8_t* cls,
+                                  unsigned long long* counts, int64_t* tcount) {
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= K) return;
     const int c = cell_of[k];
     const int len = (int)(nptr[c + 1] - nptr[c]);
     int64_t o = ptr[k];
+    unsigned long long cc[4] = {0, 0, 0, 0};
     for (int j0 = 0; j0 < len; j0 += 32) {
         const int j = j0 + lane;
         const int v = j < len ? slots[k * cap + j] : -1;
         const unsigned m = __ballot_sync(0xffffffffu, v >= 0);
-        if (v >= 0) out[o + __popc(m & ((1u << lane) - 1u))] = v;
+        if (v >= 0) {
+            const int8_t cv = scls[k * cap + j];
+            const int64_t at = o + __popc(m & ((1u << lane) - 1u));
+            out[at] = v;
+            cls[at] = cv;
+            atomicAdd((unsigned long long*)&tcount[v], 1ull);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) cc[t] += cv == t;
+        }
         o += __popc(m);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        unsigned long long x = cc[t];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0 && x) atomicAdd(&counts[t], x);
     }
 }
 
@@ -609,14 +630,20 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     const bool ordered = ntot < ((int64_t)1 << 31) && ncap <= 32768 &&
                          K * ncap * (int64_t)sizeof(int) <= ((int64_t)8 << 30);
     int64_t P = 0;
+    DBuf<unsigned long long> counts;
+    counts.alloc(4, st);
+    DBuf<int64_t> tcount;
+    tcount.alloc(K, st);
     if (ordered) {
         nlist.alloc(std::max<int64_t>(ntot, 1), st);
         k_block_fill<<<nblk(ncell * 32, 256), 256, 0, st>>>(g, cstart.p, clist.p, nptr.p, nlist.p);
         NLFEM_LAUNCH_CHECK();
         segmented_sort_i32(nlist.p, nullptr, nptr.p, ncell, (int)ncap, st);
         DBuf<int> slot_buf;
+        DBuf<int8_t> scls;
         slot_buf.alloc(std::max<int64_t>(K * ncap, 1), st);
-        k_search_ordered<<<nblk(K * 32, 128), 128, 0, st>>>(a, nptr.p, nlist.p, cnt.p, slot_buf.p, ncap);
+        scls.alloc(std::max<int64_t>(K * ncap, 1), st);
+        k_search_ordered<<<nblk(K * 32, 128), 128, 0, st>>>(a, nptr.p, nlist.p, cnt.p, slot_buf.p, scls.p, ncap);
         NLFEM_LAUNCH_CHECK();
         exclusive_scan_i64(cnt.p, pc.pair_ptr.p, K, st);
         NLFEM_CUDA_TRY(cudaMemcpyAsync(&P, pc.pair_ptr.p + K, sizeof P, cudaMemcpyDeviceToHost, st));
@@ -625,10 +652,14 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
         pc.npairs = P;
         pc.pl.alloc(P, st);
         pc.pk.alloc(P, st);
-        k_compact_ordered<<<nblk(K * 32, 128), 128, 0, st>>>(slot_buf.p, K, ncap, cell_of.p, nptr.p, pc.pair_ptr.p,
-                                                             pc.pl.p);
+        pc.pcls.alloc(P, st);
+        counts.zero(st);
+        tcount.zero(st);
+        k_compact_ordered<<<nblk(K * 32, 128), 128, 0, st>>>(slot_buf.p, scls.p, K, ncap, cell_of.p, nptr.p,
+                                                             pc.pair_ptr.p, pc.pl.p, pc.pcls.p, counts.p, tcount.p);
         NLFEM_LAUNCH_CHECK();
         slot_buf.release();
+        scls.release();
     } else {
         // one pass into per-element slots when they fit (8 GB), else a count pass and a fill pass
         int64_t cap = 0;
@@ -672,17 +703,15 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     k_fill_k<<<nblk(K * 32, 256), 256, 0, st>>>(pc.pair_ptr.p, K, pc.pk.p);
     NLFEM_LAUNCH_CHECK();
 
-    // classification and the transposed index
-    pc.pcls.alloc(P, st);
-    DBuf<unsigned long long> counts;
-    counts.alloc(4, st);
-    counts.zero(st);
-    DBuf<int64_t> tcount;
-    tcount.alloc(K, st);
-    tcount.zero(st);
-    if (P) {
-        k_classify<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, P, m.tpos(), pc.pcls.p, counts.p, tcount.p);
-        NLFEM_LAUNCH_CHECK();
+    // classification (the ordered search has done it) and the transposed index
+    if (!ordered) {
+        pc.pcls.alloc(P, st);
+        counts.zero(st);
+        tcount.zero(st);
+        if (P) {
+            k_classify<<<nblk(P, 256), 256, 0, st>>>(pc.pk.p, pc.pl.p, P, m.tpos(), pc.pcls.p, counts.p, tcount.p);
+            NLFEM_LAUNCH_CHECK();
+        }
     }
     pc.pT_ptr.alloc(K + 1, st);
     exclusive_scan_i64(tcount.p, pc.pT_ptr.p, K, st);
