@@ -339,7 +339,8 @@ int64_t Mesh::device_bytes() const {
              c.pT_id.bytes() + c.duffy_ids.bytes() + c.nrow_ptr.bytes() + c.ncol.bytes() +
              c.row_ptr.bytes() + c.col.bytes() + c.tpos.bytes() + c.seg_ptr.bytes() + c.idx.bytes() +
              c.pbase.bytes() + c.up_pos.bytes() + c.up_row.bytes() + c.whole_ids.bytes() + c.cut_ids.bytes() +
-             c.up_start.bytes() + c.epos.bytes() + c.klr_whole.bytes() + c.klr_cut.bytes();
+             c.up_start.bytes() + c.epos.bytes() + c.klr_whole.bytes() + c.klr_cut.bytes() +
+             c.kl_whole.bytes();
     }
     return b;
 }

@@ -249,6 +249,7 @@ struct PairCache {
     DBuf<int64_t> up_start;  // [M + 1] first upper entry of each node row
     DBuf<int> epos;          // [K * 8] upper entry of each node pair of an element (6 used)
     DBuf<uint16_t> klr_whole, klr_cut;  // [9][list length] rank of (k_a, l_b) in row min(k_a, l_b)
+    DBuf<int2> kl_whole;                // [nwhole] the elements (k, l) of every whole-pair list entry
     int64_t acc_terms = 0;   // bound on the number of values added into one upper entry
     double t_pairs_ms = 0, t_pattern_ms = 0;
 };

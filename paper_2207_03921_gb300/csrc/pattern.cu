@@ -832,6 +832,14 @@ __global__ void k_klr(const int* __restrict__ ids, int64_t n, const int* __restr
     }
 }
 
+__global__ void k_list_kl(const int* __restrict__ ids, int64_t n, const int* __restrict__ pk,
+                          const int* __restrict__ pl, int2* __restrict__ kl) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = ids[i];
+    kl[i] = make_int2(pk[p], pl[p]);
+}
+
 __global__ void k_max_deg(const int* ne_ptr, int64_t M, int* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     warp_atomic_max(out, i < M ? ne_ptr[i + 1] - ne_ptr[i] : 0);
@@ -847,6 +855,13 @@ void build_bulk_index(Mesh& m, PairCache& pc, cudaStream_t st) {
     NLFEM_LAUNCH_CHECK();
     pc.klr_whole.alloc(pc.nwhole * 9, st);
     pc.klr_cut.alloc(pc.ncut * 9, st);
+    // the elements of every whole-pair list entry: the whole-pair kernel's first loads then do
+    // not wait on the pair ids (the cut-pair kernel, bound elsewhere, gained nothing from it)
+    pc.kl_whole.alloc(pc.nwhole, st);
+    if (pc.nwhole > 0) {
+        k_list_kl<<<nblk(pc.nwhole, 256), 256, 0, st>>>(pc.whole_ids.p, pc.nwhole, pc.pk.p, pc.pl.p, pc.kl_whole.p);
+        NLFEM_LAUNCH_CHECK();
+    }
     DBuf<int> diag;
     diag.alloc(m.M, st);
     k_diag<<<nblk(m.M, 256), 256, 0, st>>>(pc.nrow_ptr.p, pc.ncol.p, m.M, diag.p);

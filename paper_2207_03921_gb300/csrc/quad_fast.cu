@@ -45,6 +45,7 @@ struct FastReq {
     const int* pl;
     const int8_t* pcls;
     const int* ids;           // the work list (whole or cut pairs)
+    const int2* lkl;          // whole-pair list: (k, l) of every entry (the kernel skips the pk / pl lookups)
     int64_t npairs;           // its length
     const double2* X;
     const int4* T;
@@ -1181,9 +1182,11 @@ __global__ void __launch_bounds__(FAST_THREADS, (KER != NLFEM_KERNEL_PERIDYNAMIC
         float kk[6][NC];
         int k = 0;
         if (valid) {
-            const int64_t p = Q.ids[pilot ? pi * L.pilot : pi];
-            k = Q.pk[p];
-            const int l = Q.pl[p];
+            const int64_t li = pilot ? pi * L.pilot : pi;
+            const int64_t p = Q.ids[li];
+            const int2 kl2 = Q.lkl[li];
+            k = kl2.x;
+            const int l = kl2.y;
             const ElemRec rk = Q.rec[k], rl = Q.rec[l];
             const int4 tk = make_int4(rk.n0, rk.n1, rk.n2, 0), tl = make_int4(rl.n0, rl.n1, rl.n2, 0);
             const float dx = (float)(rl.v0.x - rk.v0.x), dy = (float)(rl.v0.y - rk.v0.y);
@@ -1258,6 +1261,7 @@ FastReq make_req(Mesh& m, PairCache& pc, const Params& prm, int list) {
     q.ids = list == 0 ? pc.whole_ids.p : pc.cut_ids.p;
     q.npairs = list == 0 ? pc.nwhole : pc.ncut;
     q.klr = list == 0 ? pc.klr_whole.p : pc.klr_cut.p;
+    q.lkl = list == 0 ? pc.kl_whole.p : nullptr;
     q.X = m.X.p; q.T = m.T.p; q.E32 = m.E32.p; q.det32 = m.det32.p; q.rec = m.rec.p;
     q.delta = (float)prm.delta;
     q.d2 = (float)prm.delta * (float)prm.delta;

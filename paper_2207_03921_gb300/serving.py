@@ -29,9 +29,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # bytes per ordered pair held during and after a cold FP32-bulk assembly: pair list and class
-# (9), transposed index (4), work lists (4), kl ranks (18), ll records (24), search
-# temporaries (about 60)
-BYTES_PER_PAIR = 120
+# (9), transposed index (4), work lists (4) and the whole pairs' elements (8), kl ranks (18),
+# ll records (24), search temporaries (about 60)
+BYTES_PER_PAIR = 128
 # bytes per CSR entry: column (4), value (8), transposed position (8), node pattern (4),
 # fixed-point sums (8 per upper entry)
 BYTES_PER_NNZ = 28
