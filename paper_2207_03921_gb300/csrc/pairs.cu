@@ -331,16 +331,54 @@ __global__ void __launch_bounds__(128) k_search_ordered(SearchArgs a, const int6
     if (lane == 0) count[k] = n;
 }
 
+// Position of every element in the candidate lists that hold it: element e sits in N(c) for the
+// cells c of its own cell's block; pos[e * bb + b] is its index in N(c) for the block cell b
+// (row-major offsets (dy, dx) from -span to span; bb = (2 span + 1)^2).
+__global__ void k_block_pos(Grid g, const int64_t* nptr, const int* nlist, const int* cell_of, int* pos) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= (int64_t)g.nx * g.ny) return;
+    const int cx = (int)(c % g.nx), cy = (int)(c / g.nx), w = 2 * g.span + 1;
+    const int64_t s = nptr[c], e = nptr[c + 1];
+    for (int64_t j = s + lane; j < e; j += 32) {
+        const int el = nlist[j], ce = cell_of[el];
+        const int dx = cx - ce % g.nx, dy = cy - ce / g.nx;
+        pos[(int64_t)el * w * w + (dy + g.span) * w + (dx + g.span)] = (int)(j - s);
+    }
+}
+
+// The transposed lists in order, the same way: pair (k, l) goes to slot l * cap + (index of k in
+// N(cell(l))), and the slots of l packed in order list its pairs by increasing k, that is by
+// increasing pair id.
+__global__ void k_compact_transposed(const int* tslots, int64_t K, int64_t cap, const int* cell_of,
+                                     const int64_t* nptr, const int64_t* tptr, int* out) {
+    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (l >= K) return;
+    const int c = cell_of[l];
+    const int len = (int)(nptr[c + 1] - nptr[c]);
+    int64_t o = tptr[l];
+    for (int j0 = 0; j0 < len; j0 += 32) {
+        const int j = j0 + lane;
+        const int v = j < len ? tslots[l * cap + j] : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, v >= 0);
+        if (v >= 0) out[o + __popc(m & ((1u << lane) - 1u))] = v;
+        o += __popc(m);
+    }
+}
+
 // pack the candidate-indexed slots into the pair list and its classes (warp per element, order
 // kept); count the pairs of every inner element (the transposed lists' lengths) and of every class
 __global__ void k_compact_ordered(const int* slots, const int8_t* scls, int64_t K, int64_t cap, const int* cell_of,
                                   const int64_t* nptr, const int64_t* ptr, int* out, int8_t* cls,
-                                  unsigned long long* counts, int64_t* tcount) {
+                                  unsigned long long* counts, int64_t* tcount, Grid g, const int* pos,
+                                  int* tslots) {
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= K) return;
     const int c = cell_of[k];
     const int len = (int)(nptr[c + 1] - nptr[c]);
+    const int cx = c % g.nx, cy = c / g.nx, w = 2 * g.span + 1;
     int64_t o = ptr[k];
     unsigned long long cc[4] = {0, 0, 0, 0};
     for (int j0 = 0; j0 < len; j0 += 32) {
@@ -353,6 +391,10 @@ __global__ void k_compact_ordered(const int* slots, const int8_t* scls, int64_t 
             out[at] = v;
             cls[at] = cv;
             atomicAdd((unsigned long long*)&tcount[v], 1ull);
+            // the transposed slot: k's index in N(cell(v)), from k's position table
+            const int cv2 = cell_of[v];
+            const int dx = cv2 % g.nx - cx, dy = cv2 / g.nx - cy;
+            tslots[(int64_t)v * cap + pos[k * w * w + (dy + g.span) * w + (dx + g.span)]] = (int)at;
 #pragma unroll
             for (int t = 0; t < 4; ++t) cc[t] += cv == t;
         }
@@ -630,6 +672,7 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     const bool ordered = ntot < ((int64_t)1 << 31) && ncap <= 32768 &&
                          K * ncap * (int64_t)sizeof(int) <= ((int64_t)8 << 30);
     int64_t P = 0;
+    DBuf<int> bpos, tslots;  // ordered search: positions in the candidate lists, transposed slots
     DBuf<unsigned long long> counts;
     counts.alloc(4, st);
     DBuf<int64_t> tcount;
@@ -643,6 +686,10 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
         DBuf<int8_t> scls;
         slot_buf.alloc(std::max<int64_t>(K * ncap, 1), st);
         scls.alloc(std::max<int64_t>(K * ncap, 1), st);
+        const int bw = 2 * g.span + 1;
+        bpos.alloc(K * bw * bw, st);
+        k_block_pos<<<nblk(ncell * 32, 256), 256, 0, st>>>(g, nptr.p, nlist.p, cell_of.p, bpos.p);
+        NLFEM_LAUNCH_CHECK();
         k_search_ordered<<<nblk(K * 32, 128), 128, 0, st>>>(a, nptr.p, nlist.p, cnt.p, slot_buf.p, scls.p, ncap);
         NLFEM_LAUNCH_CHECK();
         exclusive_scan_i64(cnt.p, pc.pair_ptr.p, K, st);
@@ -655,11 +702,15 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
         pc.pcls.alloc(P, st);
         counts.zero(st);
         tcount.zero(st);
+        tslots.alloc(std::max<int64_t>(K * ncap, 1), st);
+        NLFEM_CUDA_TRY(cudaMemsetAsync(tslots.p, 0xff, tslots.bytes(), st));  // -1: no pair
         k_compact_ordered<<<nblk(K * 32, 128), 128, 0, st>>>(slot_buf.p, scls.p, K, ncap, cell_of.p, nptr.p,
-                                                             pc.pair_ptr.p, pc.pl.p, pc.pcls.p, counts.p, tcount.p);
+                                                             pc.pair_ptr.p, pc.pl.p, pc.pcls.p, counts.p, tcount.p,
+                                                             g, bpos.p, tslots.p);
         NLFEM_LAUNCH_CHECK();
         slot_buf.release();
         scls.release();
+        bpos.release();
     } else {
         // one pass into per-element slots when they fit (8 GB), else a count pass and a fill pass
         int64_t cap = 0;
@@ -716,15 +767,22 @@ void build_pairs(Mesh& m, const Params& prm, PairCache& pc, cudaStream_t st) {
     pc.pT_ptr.alloc(K + 1, st);
     exclusive_scan_i64(tcount.p, pc.pT_ptr.p, K, st);
     pc.pT_id.alloc(P, st);
-    DBuf<int> tcur;
-    tcur.alloc(K, st);
-    tcur.zero(st);
-    if (P) {
-        k_fill_T<<<nblk(P, 256), 256, 0, st>>>(pc.pl.p, P, pc.pT_ptr.p, tcur.p, pc.pT_id.p);
+    if (ordered) {  // the transposed slots packed in order: lists by increasing pair id
+        k_compact_transposed<<<nblk(K * 32, 128), 128, 0, st>>>(tslots.p, K, ncap, cell_of.p, nptr.p, pc.pT_ptr.p,
+                                                                pc.pT_id.p);
         NLFEM_LAUNCH_CHECK();
+        tslots.release();
+    } else {  // placed by atomics, then sorted
+        DBuf<int> tcur;
+        tcur.alloc(K, st);
+        tcur.zero(st);
+        if (P) {
+            k_fill_T<<<nblk(P, 256), 256, 0, st>>>(pc.pl.p, P, pc.pT_ptr.p, tcur.p, pc.pT_id.p);
+            NLFEM_LAUNCH_CHECK();
+        }
+        int64_t mxT = max_segment_i64(pc.pT_ptr.p, K, st);
+        segmented_sort_i32(pc.pT_id.p, nullptr, pc.pT_ptr.p, K, (int)std::min<int64_t>(mxT, 1 << 30), st);
     }
-    int64_t mxT = max_segment_i64(pc.pT_ptr.p, K, st);
-    segmented_sort_i32(pc.pT_id.p, nullptr, pc.pT_ptr.p, K, (int)std::min<int64_t>(mxT, 1 << 30), st);
     unsigned long long hc[4];
     NLFEM_CUDA_TRY(cudaMemcpyAsync(hc, counts.p, sizeof hc, cudaMemcpyDeviceToHost, st));
     NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
