@@ -77,7 +77,7 @@ struct SearchArgs {
 // E_l by the balls of E_k's outer points decides (interacts_clip).
 // Elements sharing a vertex have centroids at most rk + rl apart, so the far tests come first
 // and the vertex triples are read only for the candidates that pass them.
-__device__ int interacts_centroid(const SearchArgs& a, int k, int l, double2 ck, double rk) {
+__device__ int interacts_centroid(const SearchArgs& a, int k, int l, double2 ck, double rk, float rkf) {
     const double2 cl = a.cen[l];
     const double rl = a.rad[l];
     const double cdx = cl.x - ck.x, cdy = cl.y - ck.y;
@@ -91,11 +91,15 @@ __device__ int interacts_centroid(const SearchArgs& a, int k, int l, double2 ck,
         return 2;
     }
     // decided in FP32 on squared distances when the margin (1e-5 relative, far above the FP32
-    // error of about 3e-7) allows, else by the FP64 expressions below
+    // error of about 3e-7) allows, else by the FP64 expressions below. The FP32 bounds are
+    // widened by 1e-6 of delta (far up, near down), above the rounding of their FP32 sums, so
+    // that an FP32 decision is one the FP64 bounds also take; the band between goes to the
+    // FP64 tests or to the cut, which agree with them.
     const float d2f = (float)cdx * (float)cdx + (float)cdy * (float)cdy;
-    const float far = (float)(rk + rl + a.delta * (1.0 + 1e-9));
-    const double inner = a.delta * (1.0 - 1e-9) - rk - rl;
-    const float nearf = inner > 0 ? (float)inner : -1.f;
+    const float rlf = (float)rl;
+    const float far = rkf + rlf + a.delta32 * (1.f + 1e-6f);
+    const float innerf = a.delta32 * (1.f - 1e-6f) - rkf - rlf;
+    const float nearf = innerf > 0.f ? innerf : -1.f;
     if (d2f > far * far * (1.f + 1e-5f)) return 0;
     if (shared_count(a.Tp[k], a.Tp[l]) > 0) return 1;
     if (nearf > 0.f && d2f < nearf * nearf * (1.f - 1e-5f)) return 1;  // E_l inside the ball of every x in E_k
@@ -180,6 +184,7 @@ __global__ void __launch_bounds__(128) k_search(SearchArgs a, int64_t* count, co
     double2 Vk[3] = {a.X[tk.x], a.X[tk.y], a.X[tk.z]};
     double2 ck = a.cen[k];
     double rk = a.rad[k];
+    const float rkf = (float)rk;
     int cell = a.cell_of[k];
     int cx = cell % a.g.nx, cy = cell / a.g.nx;
     int64_t n = 0;
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(128) k_search(SearchArgs a, int64_t* count, co
                 int l = -1;
                 if (j < e) {
                     l = a.cell_list[j];
-                    r = interacts_centroid(a, (int)k, l, ck, rk);
+                    r = interacts_centroid(a, (int)k, l, ck, rk, rkf);
                 }
                 emit(r == 1, l);
                 const unsigned mb = __ballot_sync(0xffffffffu, r == 2);
@@ -288,6 +293,7 @@ __global__ void __launch_bounds__(128) k_search_ordered(SearchArgs a, const int6
     const double2 Vk[3] = {a.X[tk.x], a.X[tk.y], a.X[tk.z]};
     const double2 ck = a.cen[k];
     const double rk = a.rad[k];
+    const float rkf = (float)rk;
     const int c = a.cell_of[k];
     const int64_t start = nptr[c];
     const int len = (int)(nptr[c + 1] - start);
@@ -316,7 +322,7 @@ __global__ void __launch_bounds__(128) k_search_ordered(SearchArgs a, const int6
         int r = 0;
         if (j < len) {
             const int l = nlist[start + j];
-            r = interacts_centroid(a, (int)k, l, ck, rk);
+            r = interacts_centroid(a, (int)k, l, ck, rk, rkf);
             if (r != 2) row[j] = r == 1 ? l : -1;
             if (r == 1) crow[j] = (int8_t)shared_count(tpk, a.Tp[l]);
         }

@@ -814,17 +814,22 @@ __global__ void k_klr(const int* __restrict__ ids, int64_t n, const int* __restr
     const int kn[3] = {a4.x, a4.y, a4.z}, ln[3] = {b4.x, b4.y, b4.z};
     for (int a = 0; a < 3; ++a) {
         const int x = kn[a];
-        const int64_t rb = nptr[x], re = nptr[x + 1];
+        const int64_t rb = nptr[x];
+        const int len = (int)(nptr[x + 1] - rb);
+        const int* const row = ncol + rb;
+        // the largest power of two not above the row length: a branch-free bisection in 32-bit
+        // offsets (the kernel is bound by its integer pipe)
+        const int top = len > 0 ? 1 << (31 - __clz(len)) : 0;
         for (int b = 0; b < 3; ++b) {
             const int y = ln[b];
-            int64_t lo = rb, hi = re;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (ncol[mid] < y) lo = mid + 1;
-                else hi = mid;
-            }
+            // lower bound of y in row[0, len)
+            int lo = 0;
+            if (top && row[top - 1] < y) lo = len - top;
+            for (int step = top >> 1; step > 0; step >>= 1)
+                if (row[lo + step - 1] < y) lo += step;
+            if (top && lo < len && row[lo] < y) ++lo;
             int r = -1;
-            if (lo < re && ncol[lo] == y) r = y >= x ? (int)(lo - rb) - diag[x] : ntpos[lo] - diag[y];
+            if (lo < len && row[lo] == y) r = y >= x ? lo - diag[x] : ntpos[rb + lo] - diag[y];
             if (r < 0) atomicOr(ovf, 1);
             if (r > 65535) atomicOr(ovf, 2);
             klr[(int64_t)(a * 3 + b) * n + i] = (uint16_t)min(max(r, 0), 65535);
