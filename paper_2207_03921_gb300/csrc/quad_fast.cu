@@ -1120,9 +1120,16 @@ __global__ void k_cut_tris(FastRule R, FastReq Q, int* __restrict__ key) {
         key[pi] = tris;
         return;
     }
+    // an outer point farther than delta + r_l from E_l's centroid (with a margin of 1e-4) sees no
+    // point of E_l: no triangles, without deciding anything (r_l from the vertices in FP32)
+    const float gx = (Wx[0] + Wx[1] + Wx[2]) * (1.f / 3.f), gy = (Wy[0] + Wy[1] + Wy[2]) * (1.f / 3.f);
+    float rl2 = 0.f;
+    for (int m = 0; m < 3; ++m) rl2 = fmaxf(rl2, (Wx[m] - gx) * (Wx[m] - gx) + (Wy[m] - gy) * (Wy[m] - gy));
+    const float reach = (Q.delta + sqrtf(rl2)) * (1.f + 1e-4f);
     for (int q0 = 0; q0 < nqo; ++q0) {
         const float Xx = R.ol[q0][1] * Ek.x + R.ol[q0][2] * Ek.z;
         const float Xy = R.ol[q0][1] * Ek.y + R.ol[q0][2] * Ek.w;
+        if ((gx - Xx) * (gx - Xx) + (gy - Xy) * (gy - Xy) > reach * reach) continue;
         float Rx[3], Ry[3], Cc[3];
         for (int m = 0; m < 3; ++m) {
             Rx[m] = Wx[m] - Xx;
