@@ -335,12 +335,19 @@ __device__ __forceinline__ void duffy_add(R* acc, const R* D, int U, R w) {
 template <typename R>
 __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__ contrib64,
                                                float* __restrict__ contrib32) {
-    __shared__ R s_x[32], s_w[32];
+    // the 1D rule, 1 - x, and for the common vertex the weight products w_i1 w_i3 (with the
+    // xi factor) and w_i2 x_i2 tabulated once per block
+    __shared__ R s_x[32], s_w[32], s_1m[32], s_wx[32], s_w13[32 * 32];
     const Params& P = A.prm;
+    const int nr = P.dr.n;
     for (int i = threadIdx.x; i < 32; i += blockDim.x) {
-        s_x[i] = (R)(i < P.dr.n ? P.dr.x[i] : 0.0);
-        s_w[i] = (R)(i < P.dr.n ? P.dr.w[i] : 0.0);
+        s_x[i] = (R)(i < nr ? P.dr.x[i] : 0.0);
+        s_w[i] = (R)(i < nr ? P.dr.w[i] : 0.0);
+        s_1m[i] = (R)(i < nr ? 1.0 - P.dr.x[i] : 0.0);
+        s_wx[i] = (R)(i < nr ? P.dr.w[i] * P.dr.x[i] : 0.0);
     }
+    for (int i = threadIdx.x; i < nr * nr; i += blockDim.x)
+        s_w13[i] = (R)(P.dr.w[i / nr] * P.dr.w[i % nr] * P.dr.sxi[2]);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -424,7 +431,7 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
             D[upos[1]] = h2 - h1;
             D[upos[2]] = -h2;
             const R g = gamma_r<R>(zx * zx + zy * zy, P, cR);
-            duffy_add<R>(acc, D, U, w * scale * g);
+            duffy_add<R>(acc, D, U, w * g);
         }
     } else if (shared == 2) {
         // common edge: constant along e3
@@ -448,31 +455,32 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
             D[upos[2]] = hx2;
             D[upos[3]] = -hy2;
             const R g = gamma_r<R>(zx * zx + zy * zy, P, cR);
-            duffy_add<R>(acc, D, U, w * scale * wr * g);
+            duffy_add<R>(acc, D, U, w * wr * g);
         }
     } else {
         // common vertex: all four directions matter
         const R g10x = (R)(Bv[1].x - Av[0].x), g10y = (R)(Bv[1].y - Av[0].y);
         const R g21x = (R)(Bv[2].x - Bv[1].x), g21y = (R)(Bv[2].y - Bv[1].y);
-        const R sxi2 = (R)P.dr.sxi[2];
         const int npts = 2 * n * n * n;
         for (int t = lane; t < npts; t += 32) {
             const int r = t / (n * n * n);
             const int i1 = (t / (n * n)) % n, i2 = (t / n) % n, i3 = t % n;
             const R e1 = s_x[i1], e2 = s_x[i2], e3 = s_x[i3];
-            const R w = s_w[i1] * s_w[i2] * s_w[i3] * sxi2;
+            const R w = s_w13[i1 * n + i3] * s_wx[i2];  // w_i1 w_i2 w_i3 sxi e2
             const R hx1 = r == 0 ? (R)1 : e2, hy1 = r == 0 ? e2 : (R)1;
             const R zx = hy1 * (g10x + e3 * g21x) - hx1 * (e10x + e1 * e21x);
             const R zy = hy1 * (g10y + e3 * g21y) - hx1 * (e10y + e1 * e21y);
             D[upos[0]] = hy1 - hx1;
-            D[upos[1]] = hx1 * ((R)1 - e1);
+            D[upos[1]] = hx1 * s_1m[i1];
             D[upos[2]] = hx1 * e1;
-            D[upos[3]] = -hy1 * ((R)1 - e3);
+            D[upos[3]] = -hy1 * s_1m[i3];
             D[upos[4]] = -hy1 * e3;
             const R g = gamma_r<R>(zx * zx + zy * zy, P, cR);
-            duffy_add<R>(acc, D, U, w * scale * e2 * g);
+            duffy_add<R>(acc, D, U, w * g);
         }
     }
+    // the pair's factor det_k det_l, once on the lane sums
+    for (int e = 0; e < 15; ++e) acc[e] *= scale;
     // warp reduction in a fixed tree (deterministic), in R: five levels of additions add a
     // relative error of a few R ulps to the lane sums (the FP64 pipe's 1/64 rate would make
     // an FP64 tree the costliest part of the FP32 kernel)
