@@ -27,7 +27,8 @@ struct SolveState {
     DBuf<double> part;    // partial sums of dot products
     DBuf<unsigned> ticket;  // blocks done of the running fused CG kernel (0 between launches)
     DBuf<double> sc;      // device scalars: [0] rho, [1] p.q, [2] rho_new, [3] |r64|^2, [4] |b|^2,
-                          // [8..10] null-space coefficients, [11] Gram-Schmidt scratch
+                          // [5] beta (Dirichlet iteration), [8..10] null-space coefficients,
+                          // [11] Gram-Schmidt scratch
     DBuf<double> Z;       // orthonormal null-space basis of the full matrix [nz][N] (Neumann solve)
     int nz = 0;
     cudaStream_t cap = nullptr;                   // private stream the blocks are captured on
