@@ -659,8 +659,10 @@ def main():
                                  "pattern, values) -> CSR values and F to pinned host memory"}},
         # per timed step: whole-pair and cut-pair kernels, the ll sums, the scale check, fixed
         # point to CSR, load vector (6; the pilot pass and the scale pick ran once, at the first
-        # assembly on the pattern); with a close list also its kernel and its records' pass
-        "gpu_launches": args.steps * (6 + (2 if census["singular_pairs"] or census["evals_canonical"] else 0)),
+        # assembly on the pattern); with a close list also its kernel and its records' pass, and
+        # under the singular rule the copy of the mirrored orders' blocks
+        "gpu_launches": args.steps * (6 + (3 if census["singular_pairs"] else
+                                           2 if census["evals_canonical"] else 0)),
         "clocks": clk_sum,
     }
     # the other benchmark configurations, each with its own clocks, FP64 comparison, error

@@ -286,7 +286,45 @@ struct DuffyArgs {
     Params prm;
     const int4* Tp;  // vertex positions (original vertex ids of a discontinuous mesh)
     int dg;          // discontinuous mesh: touching pairs (k != l) take k_duffy_split
+    const int64_t* pair_ptr;  // [K + 1] rows of the pair list (each sorted by its second element)
 };
+
+// Record index of the pair (l, k) whose singular-rule block the pair (k, l) takes, or -1 when
+// (k, l) evaluates its own. With x and y exchanged, the rule's points for (l, k) are those of
+// (k, l) (the two regions of a common vertex trade places, as do the four of a common edge) with
+// the same weights and D -> -D, so D D^T is the same matrix over the union's nodes; that holds
+// for a common vertex always, and for a common edge when both orders run along the edge in the
+// same direction (the first shared vertex of each element's list is the same node: sl0 < sl1
+// below). Reversing the edge changes the result by the rule's error, so such pairs evaluate
+// both orders. Of each mirrored couple the order with k < l evaluates, the other copies.
+__device__ __forceinline__ int64_t duffy_mirror(const DuffyArgs& A, int k, int l, int4 tk4, int4 tl4) {
+    if (A.dg || k <= l) return -1;
+    const int tk[3] = {tk4.x, tk4.y, tk4.z}, tl[3] = {tl4.x, tl4.y, tl4.z};
+    int shared = 0, sl0 = -1, sl1 = -1;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (tk[a] == tl[b]) {
+                if (shared == 0) sl0 = b; else sl1 = b;
+                ++shared;
+            }
+    if (!(shared == 1 || (shared == 2 && sl0 < sl1))) return -1;
+    // the pair id of (l, k) in row l
+    const int64_t end = A.pair_ptr[l + 1];
+    int64_t lo = A.pair_ptr[l], hi = end;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (A.pl[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    if (lo == end || A.pl[lo] != k) return -1;
+    if (!A.compact) return lo;
+    // its position in the close list (pair ids in increasing order)
+    int64_t a = 0, b = A.n;
+    while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if (A.ids[mid] < lo) a = mid + 1; else b = mid;
+    }
+    return a < A.n && A.ids[a] == lo ? a : -1;
+}
 
 // c |z|^(-2-2s) from d2 = |z|^2 by reciprocal square roots for s in {1/4, 1/2, 3/4}, with
 // r = d2^(-1/2): r^3 (s = 1/2), r^3 rsqrt(r) (s = 1/4), r^4 rsqrt(r) (s = 3/4) (rsqrt is within
@@ -356,6 +394,7 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
     const int k = A.pk[p], l = A.pl[p];
     if (A.dg && k != l) return;  // the warp's pair is split (k_duffy_split)
     const int4 tk4 = A.T[k], tl4 = A.T[l];
+    if (duffy_mirror(A, k, l, tk4, tl4) >= 0) return;  // k_duffy_mirror copies (l, k)'s block
     const int tk[3] = {tk4.x, tk4.y, tk4.z}, tl[3] = {tl4.x, tl4.y, tl4.z};
     int shared = 0;
     for (int a = 0; a < 3; ++a)
@@ -646,16 +685,49 @@ __global__ void __launch_bounds__(128) k_duffy_split(DuffyArgs A, double* __rest
     }
 }
 
-// the singular rule over the close list: k_duffy, and k_duffy_split for the touching pairs of
-// a discontinuous mesh
+// The blocks k_duffy left to the mirrored order (duffy_mirror): each entry (a, b) of the pair's
+// union block is the mirror's entry for the same two nodes. Thread per close-list entry; the
+// mirrors (k < l) are only read.
+template <typename RT>
+__global__ void k_duffy_mirror(DuffyArgs A, RT* __restrict__ rec) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    const int p = A.ids[i];
+    const int k = A.pk[p], l = A.pl[p];
+    const int4 tk4 = A.T[k], tl4 = A.T[l];
+    const int64_t j = duffy_mirror(A, k, l, tk4, tl4);
+    if (j < 0) return;
+    int posl[3], u[6], v[6];
+    const int U = union_pos(tk4, tl4, posl, u);
+    union_pos(tl4, tk4, posl, v);
+    int pm[6];  // position in the mirror's union of each node of this pair's union
+    for (int a = 0; a < 6; ++a) {
+        pm[a] = 0;
+        for (int b = 0; b < U; ++b)
+            if (a < U && v[b] == u[a]) pm[a] = b;
+    }
+    const RT* src = rec + j * NLFEM_REC1;
+    RT* dst = rec + (A.compact ? i : (int64_t)p) * NLFEM_REC1;
+    for (int a = 0; a < 6; ++a)
+        for (int b = a; b < 6; ++b)
+            dst[q_E1[a][b]] = a < U && b < U ? src[q_E1[min(pm[a], pm[b])][max(pm[a], pm[b])]] : (RT)0;
+}
+
+// the singular rule over the close list: k_duffy (and k_duffy_mirror for the orders it leaves
+// to their mirrors), and k_duffy_split for the touching pairs of a discontinuous mesh
 template <typename R>
 static void launch_duffy(const Mesh& m, const PairCache& pc, const Params& prm, int compact, double* out64,
                          float* out32, cudaStream_t st) {
     DuffyArgs d{pc.duffy_ids.p, pc.nduffy, compact, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm,
-                m.tpos(), m.dg ? 1 : 0};
+                m.tpos(), m.dg ? 1 : 0, pc.pair_ptr.p};
     const unsigned g = nblk(pc.nduffy * 32, 128);
     k_duffy<R><<<g, 128, 0, st>>>(d, out64, out32);
     NLFEM_LAUNCH_CHECK();
+    if (!m.dg) {
+        if (out64) k_duffy_mirror<double><<<nblk(pc.nduffy, 128), 128, 0, st>>>(d, out64);
+        else k_duffy_mirror<float><<<nblk(pc.nduffy, 128), 128, 0, st>>>(d, out32);
+        NLFEM_LAUNCH_CHECK();
+    }
     if (m.dg) {
         k_duffy_split<R><<<g, 128, 0, st>>>(d, out64, out32);
         NLFEM_LAUNCH_CHECK();
@@ -1137,6 +1209,26 @@ __global__ void k_census(QuadArgs A, unsigned long long* cnt) {
     }
 }
 
+// close-list pairs that take their block from the mirrored order (duffy_mirror): [0] common
+// edge, [1] common vertex
+__global__ void k_mirror_count(DuffyArgs A, unsigned long long* cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long e = 0, v = 0;
+    if (i < A.n) {
+        const int p = A.ids[i];
+        const int k = A.pk[p], l = A.pl[p];
+        const int4 tk = A.T[k], tl = A.T[l];
+        if (duffy_mirror(A, k, l, tk, tl) >= 0) {
+            const int shared = (tk.x == tl.x) + (tk.x == tl.y) + (tk.x == tl.z) + (tk.y == tl.x) + (tk.y == tl.y) +
+                               (tk.y == tl.z) + (tk.z == tl.x) + (tk.z == tl.y) + (tk.z == tl.z);
+            e = shared == 2;
+            v = shared == 1;
+        }
+    }
+    warp_add(&cnt[0], e);
+    warp_add(&cnt[1], v);
+}
+
 __global__ void k_mark(const int* ids, int64_t n, int8_t v, int8_t* flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) flag[ids[i]] = v;
@@ -1144,7 +1236,7 @@ __global__ void k_mark(const int* ids, int64_t n, int8_t v, int8_t* flag) {
 
 void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStream_t st) {
     DBuf<unsigned long long> c;
-    c.alloc(16, st);
+    c.alloc(18, st);  // the census, then the mirrored common-edge and common-vertex pairs
     c.zero(st);
     DBuf<int8_t> wflag;
     wflag.alloc(pc.npairs, st);
@@ -1163,16 +1255,25 @@ void run_census(Mesh& m, PairCache& pc, const Params& prm, int64_t* out, cudaStr
         k_census<<<grid, 256, 0, st>>>(a, c.p);
         NLFEM_LAUNCH_CHECK();
     }
-    unsigned long long h[16];
+    if (prm.singular && !m.dg && pc.nduffy > 0) {
+        DuffyArgs d{pc.duffy_ids.p, pc.nduffy, 1, pc.pk.p, pc.pl.p, m.X.p, m.T.p, m.det.p, prm,
+                    m.tpos(), 0, pc.pair_ptr.p};
+        k_mirror_count<<<nblk(pc.nduffy, 256), 256, 0, st>>>(d, c.p + 16);
+        NLFEM_LAUNCH_CHECK();
+    }
+    unsigned long long h[18];
     NLFEM_CUDA_TRY(cudaMemcpyAsync(h, c.p, sizeof h, cudaMemcpyDeviceToHost, st));
     NLFEM_CUDA_TRY(cudaStreamSynchronize(st));
-    // singular-rule kernel evaluations: 6 n (identical), 4 n^2 (edge), 2 n^3 (vertex); the
-    // xi direction (and the directions along which the integrand is constant) are summed in
-    // closed form. Touching pairs of a discontinuous mesh: 4 n^4 (edge), 2 n^4 (vertex).
+    // singular-rule kernel evaluations: 6 n (identical), 4 n^2 (edge), 2 n^3 (vertex), for the
+    // pairs that evaluate (the mirrored orders copy); the xi direction (and the directions along
+    // which the integrand is constant) are summed in closed form. Touching pairs of a
+    // discontinuous mesh: 4 n^4 (edge), 2 n^4 (vertex).
     const int64_t n = prm.dr.n;
     int64_t duffy = 0;
     if (prm.singular && m.dg) duffy = pc.counts[3] * 6 * n + (pc.counts[2] * 4 + pc.counts[1] * 2) * n * n * n * n;
-    else if (prm.singular) duffy = pc.counts[3] * 6 * n + pc.counts[2] * 4 * n * n + pc.counts[1] * 2 * n * n * n;
+    else if (prm.singular)
+        duffy = pc.counts[3] * 6 * n + (pc.counts[2] - (int64_t)h[16]) * 4 * n * n +
+                (pc.counts[1] - (int64_t)h[17]) * 2 * n * n * n;
     h[4] = (unsigned long long)duffy;
     for (int i = 0; i < 16; ++i) out[i] = (int64_t)h[i];
 }

@@ -255,3 +255,32 @@ def test_polar_reference_reproduces_gamma1(shared):
     ref = Polar(MESH, k, l, node).integrate(1.0, -1.0, nth=16)
     want = closed_form_gamma1(MESH, k, l, node)
     assert np.max(np.abs(ref - want)) < 2e-8 * np.max(np.abs(want))
+
+
+def test_exchanged_order_gives_the_same_block():
+    """The pair integral is symmetric under exchanging E_k and E_l (x <-> y turns D into -D), and
+    so is the transform rule wherever the exchanged order lands on the same points: for a common
+    vertex always (its two regions trade places), for a common edge when both orders run along
+    the edge in the same direction (the first shared vertex of E_k's list is also the first of
+    E_l's). Run the other way along the edge, the two orders differ by the rule's error. The
+    FP32-bulk and FP64 singular kernels evaluate one order of each such couple and copy it."""
+    T = MESH.elems
+    seen = {1: 0, 2: 0, "reversed": 0}
+    for k in range(MESH.K):
+        for l in range(k + 1, MESH.K):
+            shared = len(set(T[k]) & set(T[l]))
+            if shared not in (1, 2):
+                continue
+            n1, b1, _ = oracle.pair_block(MESH, k, l, kernel="fractional", s=0.5, delta=10.0)
+            n2, b2, _ = oracle.pair_block(MESH, l, k, kernel="fractional", s=0.5, delta=10.0)
+            assert sorted(n1) == sorted(n2)
+            pm = [list(n2).index(v) for v in n1]
+            d = np.max(np.abs(b1 - b2[np.ix_(pm, pm)])) / np.max(np.abs(b1))
+            match = [(a, b) for a in range(3) for b in range(3) if T[k][a] == T[l][b]]
+            if shared == 1 or match[0][1] < match[1][1]:
+                assert d < 1e-14, (k, l, d)
+                seen[shared] += 1
+            else:
+                assert d > 1e-8, (k, l, d)  # the rule's error, not rounding
+                seen["reversed"] += 1
+    assert min(seen.values()) > 10
