@@ -357,15 +357,16 @@ __device__ __forceinline__ double gamma_r<double>(double d2, const Params& P, do
 template <>
 __device__ __forceinline__ float gamma_r<float>(float d2, const Params& P, float c) { return gamma_f(d2, P, c); }
 
-// add w * D D^T (scalar) into the packed upper union block
-template <typename R>
-__device__ __forceinline__ void duffy_add(R* acc, const R* D, int U, R w) {
+// add w * D D^T over the first M basis differences into the packed upper block (row-major)
+template <typename R, int M>
+__device__ __forceinline__ void duffy_add(R* acc, const R* D, R w) {
     int e = 0;
-    for (int a = 0; a < 5; ++a)
-        for (int b = a; b < 5; ++b) {
-            if (a < U && b < U) acc[e] += w * D[a] * D[b];
-            ++e;
-        }
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        const R wa = w * D[a];
+#pragma unroll
+        for (int b = a; b < M; ++b) acc[e++] += wa * D[b];
+    }
 }
 
 // R = double: the FP64 path; R = float: the FP32-bulk path (points and sums in FP32). The
@@ -443,9 +444,13 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
     const R e10x = (R)(Av[1].x - Av[0].x), e10y = (R)(Av[1].y - Av[0].y);
     const R e21x = (R)(Av[2].x - Av[1].x), e21y = (R)(Av[2].y - Av[1].y);
     const int n = P.dr.n;
-    R acc[15];
-    for (int e = 0; e < 15; ++e) acc[e] = (R)0;
-    R D[5];
+    // The block is accumulated over the union's vertices in the order of the maps (uorder),
+    // for the first U - 1 of them only: the basis differences of the union sum to zero (both
+    // elements' basis functions sum to one), so every row of D D^T sums to zero and the last
+    // row and column follow from the others once the points are summed.
+    R acc[10];
+    for (int e = 0; e < 10; ++e) acc[e] = (R)0;
+    R D[4];
     // z, the basis differences D and the Jacobian are powers of xi times functions of the
     // other coordinates, and gamma is homogeneous (gamma(xi w) = xi^alpha gamma(w)), so the xi
     // sum of the tensor rule factors out: P.dr.sxi[case] = sum_i w_i xi_i^(e + alpha) (1 - xi_i)^m
@@ -465,12 +470,10 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
             const R h1 = ((R)1 - e1) * PQ[r][0] + e1 * PQ[r][2];
             const R h2 = ((R)1 - e1) * PQ[r][1] + e1 * PQ[r][3];
             const R zx = h1 * e10x + h2 * e21x, zy = h1 * e10y + h2 * e21y;
-            D[0] = D[1] = D[2] = D[3] = D[4] = (R)0;
-            D[upos[0]] = h1;
-            D[upos[1]] = h2 - h1;
-            D[upos[2]] = -h2;
+            D[0] = h1;
+            D[1] = h2 - h1;  // the third difference is -h2
             const R g = gamma_r<R>(zx * zx + zy * zy, P, cR);
-            duffy_add<R>(acc, D, U, w * g);
+            duffy_add<R, 2>(acc, D, w * g);
         }
     } else if (shared == 2) {
         // common edge: constant along e3
@@ -488,13 +491,11 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
             else { hu = e1 - (R)1; hx2 = e2; hy2 = e1; wr = (R)1; }
             const R zx = hu * e10x + hy2 * fx - hx2 * e21x;
             const R zy = hu * e10y + hy2 * fy - hx2 * e21y;
-            D[0] = D[1] = D[2] = D[3] = D[4] = (R)0;
-            D[upos[0]] = hu;
-            D[upos[1]] = -hu - hx2 + hy2;
-            D[upos[2]] = hx2;
-            D[upos[3]] = -hy2;
+            D[0] = hu;
+            D[1] = -hu - hx2 + hy2;
+            D[2] = hx2;  // the fourth difference is -hy2
             const R g = gamma_r<R>(zx * zx + zy * zy, P, cR);
-            duffy_add<R>(acc, D, U, w * wr * g);
+            duffy_add<R, 3>(acc, D, w * wr * g);
         }
     } else {
         // common vertex: all four directions matter
@@ -509,41 +510,52 @@ __global__ void __launch_bounds__(128) k_duffy(DuffyArgs A, double* __restrict__
             const R hx1 = r == 0 ? (R)1 : e2, hy1 = r == 0 ? e2 : (R)1;
             const R zx = hy1 * (g10x + e3 * g21x) - hx1 * (e10x + e1 * e21x);
             const R zy = hy1 * (g10y + e3 * g21y) - hx1 * (e10y + e1 * e21y);
-            D[upos[0]] = hy1 - hx1;
-            D[upos[1]] = hx1 * s_1m[i1];
-            D[upos[2]] = hx1 * e1;
-            D[upos[3]] = -hy1 * s_1m[i3];
-            D[upos[4]] = -hy1 * e3;
+            D[0] = hy1 - hx1;
+            D[1] = hx1 * s_1m[i1];
+            D[2] = hx1 * e1;
+            D[3] = -hy1 * s_1m[i3];  // the fifth difference is -hy1 e3
             const R g = gamma_r<R>(zx * zx + zy * zy, P, cR);
-            duffy_add<R>(acc, D, U, w * g);
+            duffy_add<R, 4>(acc, D, w * g);
         }
     }
     // the pair's factor det_k det_l, once on the lane sums
-    for (int e = 0; e < 15; ++e) acc[e] *= scale;
+    const int L = U - 1, na = L * (L + 1) / 2;  // accumulated rows and entries
+    for (int e = 0; e < 10; ++e) acc[e] *= scale;
     // warp reduction in a fixed tree (deterministic), in R: five levels of additions add a
     // relative error of a few R ulps to the lane sums (the FP64 pipe's 1/64 rate would make
     // an FP64 tree the costliest part of the FP32 kernel)
-    double accd[15];
-    for (int e = 0; e < 15; ++e) {
+    double accd[10];
+    for (int e = 0; e < 10; ++e) {
         R v = acc[e];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (e < na)
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         accd[e] = (double)v;
     }
     if (lane == 0) {
-        int e;
+        // the block over the maps' vertex order: the accumulated rows, then the last row and
+        // column from the zero row sums
+        double mu[5][5];
+        int e = 0;
+        for (int a = 0; a < L; ++a)
+            for (int b = a; b < L; ++b, ++e) {
+                mu[a][b] = accd[e];
+                mu[b][a] = accd[e];
+            }
+        double last = 0.0;
+        for (int a = 0; a < L; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < L; ++b) s += mu[a][b];
+            mu[a][L] = -s;
+            mu[L][a] = -s;
+            last += s;
+        }
+        mu[L][L] = last;
         // write all 21 entries of the union block (unused ones are zero)
         double blk[6][6];
         for (int a = 0; a < 6; ++a)
             for (int b = 0; b < 6; ++b) blk[a][b] = 0.0;
-        e = 0;
-        for (int a = 0; a < 5; ++a)
-            for (int b = a; b < 5; ++b) {
-                if (a < U && b < U) {
-                    blk[a][b] = accd[e];
-                    blk[b][a] = accd[e];
-                }
-                ++e;
-            }
+        for (int a = 0; a < U; ++a)
+            for (int b = 0; b < U; ++b) blk[upos[a]][upos[b]] = mu[a][b];
         const int64_t r = A.compact ? wi : (int64_t)p;
         const double fm = pair_factor64(P, k, l);
         for (int a = 0; a < 6; ++a)
