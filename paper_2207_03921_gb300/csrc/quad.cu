@@ -11,7 +11,8 @@
 // k_duffy: the singular rule (Tab. 1 "club") for intersecting pairs: regularising maps
 //   of S x S to (0,1)^4 and a tensor Gauss rule, in FP64. One warp per pair.
 //   Directions along which the integrand is constant are summed in closed form (the
-//   same tensor sum, reordered).
+//   same tensor sum, reordered). Of two exchanged orders (k, l), (l, k) that the rule maps
+//   onto the same points only one is evaluated; k_duffy_mirror copies its block.
 // k_load: F_i = sum over Omega elements of sum_p a_p f(x_p) phi_i(x_p), thread per node.
 #include <algorithm>
 
