@@ -284,3 +284,15 @@ def test_exchanged_order_gives_the_same_block():
                 assert d > 1e-8, (k, l, d)  # the rule's error, not rounding
                 seen["reversed"] += 1
     assert min(seen.values()) > 10
+
+
+@pytest.mark.parametrize("s", [0.25, 0.5, 0.75])
+def test_singular_blocks_have_zero_row_sums(s):
+    """At every transform point the union's basis differences sum to zero (both elements' basis
+    functions sum to one), so each row of a singular-rule block sums to zero up to rounding, for
+    any kernel. The singular kernels accumulate all but the last row and column and complete the
+    block from this property."""
+    for shared, (k, l) in PAIRS.items():
+        node, blk, _ = oracle.pair_block(MESH, k, l, kernel="fractional", s=s, delta=10.0)
+        assert len(node) == {3: 3, 2: 4, 1: 5}[shared]
+        assert np.max(np.abs(blk.sum(1))) < 1e-13 * np.max(np.abs(blk)), (shared, blk.sum(1))
